@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Throughput of the coherent-dedispersion pulse search on GB300.
+
+Workload (one "step"): the Chimageator search of a 12-antenna array (positions
+seeded within 6 km), 32 MHz of complex baseband at 1.4 GHz, 2^22 samples per
+antenna, 64 trial DMs in 0-300 pc cm^-3 (FFT length >= 2^18, grown per DM so
+that each overlap-save block keeps >= half its samples), 32x32 beams over
+1 deg, dumps of 4096 samples, 3 injected bursts.  A step runs every stage of
+the path: forward FFTs, chirp multiply + inverse FFT for every DM, and the
+phased-sum beam detector with its integrate-and-dump.
+
+Output: one JSON line (rank 0).  ``value`` is dedispersed antenna*DM*samples
+per second over all ranks with inputs resident in HBM; ``e2e`` is the same
+metric through the same call with pinned host input and host output (copies
+inside the timed region).  ``--impl reference`` times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "dedispersed antenna*DM*samples/s"
+UNIT = "antenna*DM*samples/s"
+WORKLOAD = ("chimageator: 12 ant within 6 km, 32 MHz @ 1.4 GHz, 2^22 samples/antenna, "
+            "64 DMs 0-300, FFT >= 2^18, 32x32 beams over 1 deg, dump 4096")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                  "sm_max_mhz": 2070.0}
+N_SM = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--beam-mode", type=int, default=0, help="0 auto, 1 FP32 SIMT, 2 tcgen05 3xbf16")
+    ap.add_argument("--cpu-dumps", type=int, default=24,
+                    help="dumps per selected DM in the oracle's bounded CPU sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return pk, "measured"
+    except (OSError, ValueError):
+        return dict(FALLBACK_PEAKS), "fallback"
+
+
+def scenario(rank: int):
+    from paper_1109_3186_gb300 import skymodel
+    # each rank searches its own observation (weak scaling, no exchange)
+    return skymodel.chimageator_medium(seed=1002 + 1000 * rank)
+
+
+def config_block(sc, n_gpus):
+    return {"workload": WORKLOAD, "n_ant": sc.n_ant, "n_samp": sc.n_samp, "n_dm": len(sc.dms),
+            "dm_max": float(sc.dms.max()), "bw_hz": sc.bw, "f0_hz": sc.f0,
+            "nfft_min": sc.nfft_min, "n_pix": int(sc.pix_lm.shape[0]), "dump_len": sc.dump_len,
+            "l2": "inputs larger than L2 (voltages 403 MB, forward spectra 2.7 GB)",
+            "parallelism": "replicas%d" % n_gpus}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid: str | None):
+        self.uuid = device_uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        loaded = [s for s in sm if s > 0.5 * (max(mx) if mx else 1)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def device_uuid(torch, dev):
+    try:
+        u = torch.cuda.get_device_properties(dev).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- oracle leg
+def cpu_sample(sc, x, n_dumps: int):
+    """Bounded oracle run: one middle DM of each FFT-length group, n_dumps dumps
+    in the middle of the valid range.  Returns (units, seconds, cores, text)."""
+    import oracle
+    groups = {}
+    for d, dm in enumerate(sc.dms):
+        nf = oracle.nfft_for_dm(sc.f0, sc.bw, sc.k_dm, dm, sc.n_samp, sc.nfft_min)
+        groups.setdefault(nf, []).append(d)
+    sel = [g[len(g) // 2] for _, g in sorted(groups.items())]
+    lay = oracle.layout(sc.dms, max(sel), sc.f0, sc.bw, sc.k_dm, sc.n_samp, sc.nfft_min)
+    first, last = oracle.dump_range(sc.n_samp, lay["n_hi"], lay["n_lo"], sc.dump_len)
+    mid = (first + last) // 2
+    m0 = max(first, mid - n_dumps // 2)
+    m1 = min(last + 1, m0 + n_dumps)
+    t = time.perf_counter()
+    oracle.chimageator(x, sc.f0, sc.bw, sc.k_dm, sc.dms, sc.nfft_min, sc.dump_len, sc.xyz,
+                       sc.pix_lm, d_sel=sel, m0=m0, m1=m1)
+    dt = time.perf_counter() - t
+    units = sc.n_ant * len(sel) * (m1 - m0) * sc.dump_len
+    text = ("FP64 oracle, DMs %s (one per FFT-length group), dumps %d..%d (%d x %d samples), "
+            "all %d antennas and %d beams" % ([float(round(sc.dms[d], 2)) for d in sel], m0, m1 - 1,
+                                              m1 - m0, sc.dump_len, sc.n_ant, sc.pix_lm.shape[0]))
+    return units, dt, oracle.num_threads(), text
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return 0
+    sc = scenario(0)
+    x = sc.voltages()
+    n_d = max(4, args.cpu_dumps // 2)
+    for _ in range(args.warmup):
+        cpu_sample(sc, x, 2)
+    tot_u, tot_t = 0, 0.0
+    cores, text = 1, ""
+    for _ in range(args.steps):
+        u, dt, cores, text = cpu_sample(sc, x, n_d)
+        tot_u += u
+        tot_t += dt
+    value = tot_u / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_block(sc, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": text},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our leg
+def stage_roofline(sc, plan, stage_ms, peaks, peak_kind, beam_mode, steps):
+    """Algorithmic bytes / flops per stage for one step, and achieved rates."""
+    M, N, L = sc.n_ant, sc.n_samp, sc.dump_len
+    n_pix = sc.pix_lm.shape[0]
+    first, last = plan.dump_range()
+    groups = {}
+    fwd_pts = inv_pts = g_bytes = y_bytes = 0
+    for d in range(len(sc.dms)):
+        lay = plan.dm_layout(d)
+        pts = M * lay["n_blk"] * lay["nfft"]
+        groups[lay["nfft"]] = pts
+        inv_pts += pts
+        g_bytes += 8 * lay["nfft"]
+        y_bytes += 8 * M * max(0, N - lay["n_hi"] - lay["n_lo"])
+    fwd_pts = sum(groups.values())
+    n_dump_valid = int(np.sum(np.maximum(0, last - first + 1)))
+    hbm = peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
+    sm_max = peaks.get("sm_max_mhz", FALLBACK_PEAKS["sm_max_mhz"])
+    fp32_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    stages = {
+        "forward": ("hbm", 32.0 * fwd_pts, hbm, "GB/s"),
+        "inv_rows": ("hbm", 16.0 * inv_pts + g_bytes, hbm, "GB/s"),
+        "inv_cols": ("hbm", 8.0 * inv_pts + y_bytes, hbm, "GB/s"),
+    }
+    beam_flops = float(n_dump_valid) * L * n_pix * (8 * M + 3)
+    if beam_mode == 1:
+        stages["beamform"] = ("alu", beam_flops, fp32_tflops, "TFLOP/s")
+    else:
+        stages["beamform"] = ("tensor", beam_flops,
+                              peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]),
+                              "TFLOP/s")
+    out = {}
+    for name, (bound, work, peak, unit) in stages.items():
+        ms, n = stage_ms.get(name, (0.0, 0))
+        if ms <= 0 or n == 0:
+            continue
+        per_launch_work = work / (n / steps)
+        avg_ms = ms / n
+        rate = per_launch_work / (avg_ms * 1e-3)
+        achieved = rate / 1e9 if unit == "GB/s" else rate / 1e12
+        out[name] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                     "frac": achieved / peak, "ms_per_step": ms / steps,
+                     "launches_per_step": n / steps, "peak_source": peak_kind}
+    return out
+
+
+def run_ours(args):
+    import torch
+    import paper_1109_3186_gb300 as chirp
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    sc = scenario(rank)
+    x = sc.voltages()
+    stream = torch.cuda.current_stream()
+    plan = chirp.Plan.from_scenario(sc, beam_mode=args.beam_mode, stream=stream)
+    n_dm, n_dump, n_pix = len(sc.dms), plan.n_dump, plan.n_pix
+    xd = torch.from_numpy(x).cuda()
+    Pd = torch.empty((n_dm, n_dump, n_pix), dtype=torch.float32, device="cuda")
+    units = plan.info["valid_samples"]
+    first, last = plan.dump_range()
+    beam_dumps = int(np.sum(np.maximum(0, last - first + 1))) * n_pix
+
+    for _ in range(args.warmup):
+        plan.chimageator(xd, Pd)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+
+    peaks, peak_kind = load_peaks()
+    clocks = ClockSampler(device_uuid(torch, local))
+    clocks.start()
+    plan.stage_timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.chimageator(xd, Pd)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    stage = plan.stage_timing(False)
+    clk = clocks.stop()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * units / (ms * 1e-3)
+
+    # end to end through the same call: pinned host input, host output
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x).pin_memory()
+        Ph = torch.empty((n_dm, n_dump, n_pix), dtype=torch.float32).pin_memory()
+        plan.chimageator(xh, Ph)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.chimageator(xh, Ph)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        if dist is not None:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * units / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+               "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(Ph.numel() * 4)}
+
+    roof = stage_roofline(sc, plan, stage, peaks, peak_kind, plan.info["beam_mode"], args.steps)
+    dom = max(roof, key=lambda k: roof[k]["ms_per_step"]) if roof else None
+    n_groups = plan.info["n_group"]
+    launches = args.steps * (2 * n_groups + 3 * n_dm)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic (seeded sky model: noise + dispersed bursts)",
+                "config": config_block(sc, world),
+                "beam_dm_dumps_per_s": world * beam_dumps / (ms * 1e-3),
+                "gpu_launches": launches, "clocks": clk}
+        if e2e:
+            line["e2e"] = e2e
+        if dom:
+            r = roof[dom]
+            line["roofline"] = {"kernel": dom, "bound": r["bound"], "achieved": r["achieved"],
+                                "peak": r["peak"], "unit": r["unit"], "frac": r["frac"],
+                                "traffic": None, "peak_source": r["peak_source"]}
+            line["stages"] = roof
+        if not args.no_cpu_baseline:
+            u, dt, cores, text = cpu_sample(sc, x, args.cpu_dumps)
+            line["cpu_baseline"] = {"value": u / dt, "unit": UNIT, "cores": cores,
+                                    "kind": "oracle", "sample": text, "seconds": dt}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

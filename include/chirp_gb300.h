@@ -1,0 +1,163 @@
+/*
+ * chirp_gb300.h -- C ABI of the GB300 (sm_103a) coherent-dedispersion pulse
+ * search: per-antenna overlap-save coherent dedispersion for every trial DM,
+ * feeding either a per-DM integrate-and-dump correlator ("Chirpolator"
+ * back-end) or a per-DM phased-beam detector ("Chimageator" back-end).
+ *
+ * Paper: K. W. Bannister & T. J. Cornwell, "Two efficient, new techniques for
+ * detecting dispersed radio pulses with interferometers: The Chirpolator and
+ * The Chimageator" (arXiv:1109.3186).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Voltages are complex baseband, complex-Nyquist sampled at f_s = B
+ *    (Sec. 3.2, below Eq. 5): complex64 (interleaved float re, im),
+ *    antenna-major [n_ant][n_samp].
+ *  - Dispersion follows Eq. 1 (Sec. 2.1) with constant k_dm (s Hz^2 per
+ *    pc cm^-3; mu ~ 4.15 ms GHz^2 in the paper).  Dedispersion multiplies the
+ *    spectrum of each overlap-save block by
+ *        H_DM(f) = exp(-2 pi j k_dm DM f^2 / (f0^2 (f0 + f)))
+ *    (the inverse ISM response of Sec. 2.3.2 about f0); the forward DFT
+ *    has the paper's sign exp(-2 pi j n k / N) (Eq. 6); the inverse
+ *    includes 1/Nfft.
+ *  - Per DM: n_hi = ceil(k DM (f0^-2 - (f0+B/2)^-2) B),
+ *            n_lo = ceil(k DM ((f0-B/2)^-2 - f0^-2) B);
+ *    Nfft = max(nfft_min, min(pow2ceil(2 (n_hi + n_lo)), pow2ceil(n_samp)));
+ *    DMs with equal Nfft share one block grid of step
+ *    S = Nfft - max n_hi - max n_lo.  Output sample t refers to the arrival
+ *    at f0 and is valid for t in [n_hi, n_samp - n_lo).
+ *  - Dumps are the absolute grid [m L, (m+1) L), m < floor(n_samp / L).  A
+ *    dump is valid for a DM only if it lies inside that DM's valid range;
+ *    invalid dumps are written as zeros.
+ *  - Return codes: CHIRP_OK (0) or a negative CHIRP_E*; the message of the
+ *    last failure on the calling thread is in chirp_last_error().  No C++
+ *    exception crosses this boundary.
+ *  - Ownership: the caller owns every input and output buffer; the plan
+ *    owns its device workspace and frees it in chirp_plan_destroy.  The
+ *    library never frees caller memory.
+ *  - Streams: all device work of a plan is ordered on the CUDA stream given
+ *    at creation (NULL = legacy default stream).  A call whose outputs are
+ *    on the device returns once the work is queued; a call with any host
+ *    output synchronises that stream before returning.
+ */
+#ifndef CHIRP_GB300_H
+#define CHIRP_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CHIRP_OK 0
+#define CHIRP_EINVAL (-1)      /* bad argument or size                     */
+#define CHIRP_ENOMEM (-2)      /* device or host allocation failed          */
+#define CHIRP_ECUDA (-3)       /* a CUDA runtime call or launch failed      */
+#define CHIRP_EUNSUPPORTED (-5)/* valid request this build does not handle  */
+
+/* where a caller buffer lives */
+#define CHIRP_HOST 0
+#define CHIRP_DEVICE 1
+
+/* contraction used by the Chimageator back-end */
+#define CHIRP_BEAM_AUTO 0      /* tensor-core split-bf16 when available      */
+#define CHIRP_BEAM_FP32_SIMT 1 /* plain FP32 FMA on the CUDA cores           */
+#define CHIRP_BEAM_TC_3XBF16 2 /* tcgen05, 3-term bf16 split, FP32 accumulate */
+
+typedef struct chirp_plan chirp_plan;
+
+/* Everything that fixes the shape of a search.  All pointers are HOST
+ * memory and are copied at plan creation. */
+typedef struct {
+  int n_ant;               /* M >= 1 antennas                                   */
+  const double* xyz_m;     /* [n_ant][3] positions, metres, (u,v,w) frame with w
+                              towards the phase centre (App. A.1, Eq. tau3D);
+                              only the Chimageator reads them (may be NULL
+                              otherwise)                                        */
+  double f0_hz;            /* band centre                                       */
+  double bw_hz;            /* bandwidth = complex sample rate                   */
+  double k_dm;             /* dispersion constant; <= 0 selects 4.148808e15     */
+  long long n_samp;        /* samples per antenna, >= 1                         */
+  const double* dm;        /* [n_dm] trial DMs, pc cm^-3, each >= 0             */
+  int n_dm;                /* >= 1                                              */
+  int dump_len;            /* L samples per integrate-and-dump, 1..n_samp       */
+  long long nfft_min;      /* power of two, 256 .. 2^24                         */
+  const double* pix_lm;    /* [n_pix][2] beam direction cosines (l, m), or NULL */
+  int n_pix;               /* 0 when no Chimageator runs are wanted             */
+  int beam_mode;           /* CHIRP_BEAM_*                                      */
+} chirp_config;
+
+typedef struct {
+  long long n_dump;        /* floor(n_samp / dump_len)                          */
+  int n_pair;              /* n_ant (n_ant + 1) / 2                             */
+  int n_group;             /* distinct FFT lengths                              */
+  long long workspace_bytes;/* device memory owned by the plan                  */
+  long long ifft_points;   /* sum over DMs of n_ant * n_blk * Nfft              */
+  long long valid_samples; /* sum over DMs of n_ant * (n_samp - n_hi - n_lo)^+  */
+  int beam_mode;           /* CHIRP_BEAM_* actually used (AUTO resolved)        */
+} chirp_plan_info;
+
+/* Create a plan: validates cfg, derives the per-DM FFT lengths and block
+ * grids (header conventions), allocates the device workspace, builds the
+ * FP64 chirp-phase tables, twiddle tables and beam weights on the device.
+ * stream: a cudaStream_t (or NULL).  On success *plan is set.
+ * Errors: CHIRP_EINVAL (bad shape), CHIRP_ENOMEM, CHIRP_ECUDA. */
+int chirp_plan_create(chirp_plan** plan, const chirp_config* cfg, void* stream);
+
+/* Destroy a plan (NULL is ignored).  Synchronises the plan's stream first. */
+void chirp_plan_destroy(chirp_plan* plan);
+
+/* Sizes derived at creation.  Errors: CHIRP_EINVAL on NULL. */
+int chirp_plan_query(const chirp_plan* plan, chirp_plan_info* info);
+
+/* Block grid of DM number d: out7 = {Nfft, n_hi, n_lo, max n_hi of the group,
+ * max n_lo of the group, step S, number of blocks}.  Errors: CHIRP_EINVAL. */
+int chirp_dm_layout(const chirp_plan* plan, int d, long long* out7);
+
+/* Valid dump range of every DM: first[d] .. last[d] inclusive (last < first
+ * when a DM has no valid dump).  first, last: host arrays of n_dm. */
+int chirp_dump_range(const chirp_plan* plan, long long* first, long long* last);
+
+/* Coherent dedispersion of one trial DM (Sec. 2.3.2), the shared first stage
+ * of both searches.  volt: complex64 [n_ant][n_samp] at volt_loc; y_out:
+ * complex64 [n_ant][n_samp] at y_loc; samples outside the DM's valid range
+ * are zero.  Errors: CHIRP_EINVAL, CHIRP_ECUDA. */
+int chirp_dedisperse_run(chirp_plan* plan, const void* volt, int volt_loc, int d, void* y_out,
+                         int y_loc);
+
+/* Chirpolator back-end: for every trial DM and dump, the zero-lag
+ * visibilities V_pq = sum_t y_p(t) y_q(t)^* of the dedispersed voltages
+ * (pair mixing x_pq = s_p s_q^* of Eq. 5, integrated and dumped; autos
+ * included).  vis_out: complex64 [n_dm][n_dump][n_pair], pairs p <= q in
+ * row-major order (0,0),(0,1),..,(0,M-1),(1,1),...  Errors: CHIRP_EINVAL,
+ * CHIRP_ECUDA. */
+int chirpolator_run(chirp_plan* plan, const void* volt, int volt_loc, void* vis_out, int vis_loc);
+
+/* Chimageator back-end in its phased-sum form: for every trial DM, dump and
+ * pixel, P = sum_t |sum_a W_pa y_a(t)|^2 with narrowband weights
+ * W_pa = exp(+2 pi j f0 tau_a(l_p, m_p)), tau from Eq. tau3D (direct
+ * beamforming, Sec. 2.4.2, detected and integrated).  pow_out: float32
+ * [n_dm][n_dump][n_pix].  Needs n_pix > 0 at plan creation.  Errors:
+ * CHIRP_EINVAL, CHIRP_EUNSUPPORTED, CHIRP_ECUDA. */
+int chimageator_run(chirp_plan* plan, const void* volt, int volt_loc, float* pow_out, int pow_loc);
+
+/* Per-stage device time.  Stages: */
+#define CHIRP_STAGE_FORWARD 0   /* forward FFT passes of every group            */
+#define CHIRP_STAGE_INV_ROWS 1  /* chirp multiply + inverse row pass, per DM    */
+#define CHIRP_STAGE_INV_COLS 2  /* inverse column pass + discard, per DM        */
+#define CHIRP_STAGE_CORRELATE 3 /* Chirpolator back-end, per DM                 */
+#define CHIRP_STAGE_BEAMFORM 4  /* Chimageator back-end, per DM                 */
+#define CHIRP_N_STAGES 5
+/* Returns the milliseconds and launch counts accumulated per stage since the
+ * previous call (ms, launches: host arrays of CHIRP_N_STAGES, either may be
+ * NULL), resets them, and switches event timing on (enable != 0) or off for
+ * later runs.  Timing records one CUDA event pair around every launch on the
+ * plan's stream; reading the totals synchronises that stream.  Not a paper
+ * operation: instrumentation for the roofline report.  Errors: CHIRP_EINVAL. */
+int chirp_stage_timing(chirp_plan* plan, int enable, double* ms, long long* launches);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* chirp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHIRP_GB300_H */

@@ -1,0 +1,258 @@
+"""GB300 (sm_103a) coherent-dedispersion pulse search: Python binding.
+
+A thin ctypes layer over ``libchirp_gb300.so`` (C ABI in include/chirp_gb300.h).
+It only marshals arguments: every step of the search runs in the library's
+CUDA kernels.  There is no CPU fallback; if the library is missing or cannot
+load, every entry point raises.
+
+Buffers may be torch tensors (CUDA tensors are passed as device pointers, CPU
+tensors as host pointers) or numpy arrays (host).  Voltages are complex64
+[n_ant, n_samp]; visibilities complex64 [n_dm, n_dump, n_pair]; beam powers
+float32 [n_dm, n_dump, n_pix].
+
+Paper: Bannister & Cornwell, "The Chirpolator & The Chimageator"
+(arXiv:1109.3186).  Dedispersion: Sec. 2.3.2 with Eq. 1; correlation:
+Eq. 5's p.q^* products integrated per dump; beams: Sec. 2.4.2 with Eq. tau3D.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["Plan", "load", "build", "CHIRP_HOST", "CHIRP_DEVICE", "BEAM_AUTO", "BEAM_FP32_SIMT",
+           "BEAM_TC_3XBF16", "ChirpError", "chirp_plan_create", "chirp_plan_destroy",
+           "chirpolator_run", "chimageator_run", "chirp_dedisperse_run", "chirp_last_error",
+           "EXPORTED_SYMBOLS"]
+
+CHIRP_HOST, CHIRP_DEVICE = 0, 1
+BEAM_AUTO, BEAM_FP32_SIMT, BEAM_TC_3XBF16 = 0, 1, 2
+K_DM_DEFAULT = 4.148808e15
+
+EXPORTED_SYMBOLS = ("chirp_plan_create", "chirp_plan_destroy", "chirp_plan_query",
+                    "chirp_dm_layout", "chirp_dump_range", "chirp_dedisperse_run",
+                    "chirpolator_run", "chimageator_run", "chirp_stage_timing",
+                    "chirp_last_error")
+STAGES = ("forward", "inv_rows", "inv_cols", "correlate", "beamform")
+
+
+class ChirpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("chirp error %d: %s" % (code, msg))
+        self.code = code
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("n_ant", ctypes.c_int), ("xyz_m", ctypes.POINTER(ctypes.c_double)),
+                ("f0_hz", ctypes.c_double), ("bw_hz", ctypes.c_double),
+                ("k_dm", ctypes.c_double), ("n_samp", ctypes.c_longlong),
+                ("dm", ctypes.POINTER(ctypes.c_double)), ("n_dm", ctypes.c_int),
+                ("dump_len", ctypes.c_int), ("nfft_min", ctypes.c_longlong),
+                ("pix_lm", ctypes.POINTER(ctypes.c_double)), ("n_pix", ctypes.c_int),
+                ("beam_mode", ctypes.c_int)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n_dump", ctypes.c_longlong), ("n_pair", ctypes.c_int),
+                ("n_group", ctypes.c_int), ("workspace_bytes", ctypes.c_longlong),
+                ("ifft_points", ctypes.c_longlong), ("valid_samples", ctypes.c_longlong),
+                ("beam_mode", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def load():
+    """Load the CUDA library (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB_PATH
+        if not _build.up_to_date():
+            path = _build.build()
+        lib = ctypes.CDLL(path)
+        vp, i, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
+        lib.chirp_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_Config), vp]
+        lib.chirp_plan_create.restype = i
+        lib.chirp_plan_destroy.argtypes = [vp]
+        lib.chirp_plan_destroy.restype = None
+        lib.chirp_plan_query.argtypes = [vp, ctypes.POINTER(_Info)]
+        lib.chirp_plan_query.restype = i
+        lib.chirp_dm_layout.argtypes = [vp, i, ctypes.POINTER(ll)]
+        lib.chirp_dm_layout.restype = i
+        lib.chirp_dump_range.argtypes = [vp, ctypes.POINTER(ll), ctypes.POINTER(ll)]
+        lib.chirp_dump_range.restype = i
+        lib.chirp_dedisperse_run.argtypes = [vp, vp, i, i, vp, i]
+        lib.chirp_dedisperse_run.restype = i
+        lib.chirpolator_run.argtypes = [vp, vp, i, vp, i]
+        lib.chirpolator_run.restype = i
+        lib.chimageator_run.argtypes = [vp, vp, i, vp, i]
+        lib.chimageator_run.restype = i
+        lib.chirp_stage_timing.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ll)]
+        lib.chirp_stage_timing.restype = i
+        lib.chirp_last_error.argtypes = []
+        lib.chirp_last_error.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise ChirpError(rc, load().chirp_last_error().decode(errors="replace"))
+
+
+def _buf(a, dtype_np, what: str):
+    """(pointer, location, keepalive) of a torch tensor or numpy array."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        want = {np.complex64: torch.complex64, np.float32: torch.float32}[dtype_np]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError("%s must be a contiguous %s tensor" % (what, want))
+        return ctypes.c_void_p(a.data_ptr()), (CHIRP_DEVICE if a.is_cuda else CHIRP_HOST), a
+    arr = np.asarray(a)
+    if arr.dtype != dtype_np or not arr.flags["C_CONTIGUOUS"]:
+        raise TypeError("%s must be a C-contiguous %s array" % (what, np.dtype(dtype_np).name))
+    return ctypes.c_void_p(arr.ctypes.data), CHIRP_HOST, arr
+
+
+def _stream_handle(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:  # pragma: no cover
+        pass
+    return ctypes.c_void_p(0)
+
+
+# ------------------------------------------------------------ raw C-ABI names
+def chirp_plan_create(cfg: _Config, stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().chirp_plan_create(ctypes.byref(h), ctypes.byref(cfg), _stream_handle(stream)))
+    return h
+
+
+def chirp_plan_destroy(h) -> None:
+    load().chirp_plan_destroy(h)
+
+
+def chirp_dedisperse_run(h, volt, d: int, y_out) -> None:
+    vp, vl, _k1 = _buf(volt, np.complex64, "volt")
+    yp, yl, _k2 = _buf(y_out, np.complex64, "y_out")
+    _check(load().chirp_dedisperse_run(h, vp, vl, int(d), yp, yl))
+
+
+def chirpolator_run(h, volt, vis_out) -> None:
+    vp, vl, _k1 = _buf(volt, np.complex64, "volt")
+    op, ol, _k2 = _buf(vis_out, np.complex64, "vis_out")
+    _check(load().chirpolator_run(h, vp, vl, op, ol))
+
+
+def chimageator_run(h, volt, pow_out) -> None:
+    vp, vl, _k1 = _buf(volt, np.complex64, "volt")
+    op, ol, _k2 = _buf(pow_out, np.float32, "pow_out")
+    _check(load().chimageator_run(h, vp, vl, op, ol))
+
+
+def chirp_last_error() -> str:
+    return load().chirp_last_error().decode(errors="replace")
+
+
+# ------------------------------------------------------------ convenience
+class Plan:
+    """Owns one chirp_plan (device workspace sized for one search shape)."""
+
+    def __init__(self, xyz, f0: float, bw: float, n_samp: int, dms, dump_len: int,
+                 nfft_min: int, pix_lm=None, k_dm: float = K_DM_DEFAULT,
+                 beam_mode: int = BEAM_AUTO, n_ant: int | None = None, stream=None):
+        self._xyz = None if xyz is None else np.ascontiguousarray(xyz, dtype=np.float64)
+        self._dms = np.ascontiguousarray(np.atleast_1d(dms), dtype=np.float64)
+        self._pix = None if pix_lm is None else np.ascontiguousarray(pix_lm, dtype=np.float64)
+        if n_ant is None:
+            n_ant = int(self._xyz.shape[0])
+        dp = ctypes.POINTER(ctypes.c_double)
+        cfg = _Config()
+        cfg.n_ant = int(n_ant)
+        cfg.xyz_m = self._xyz.ctypes.data_as(dp) if self._xyz is not None else None
+        cfg.f0_hz, cfg.bw_hz, cfg.k_dm = float(f0), float(bw), float(k_dm)
+        cfg.n_samp = int(n_samp)
+        cfg.dm = self._dms.ctypes.data_as(dp)
+        cfg.n_dm = int(self._dms.size)
+        cfg.dump_len = int(dump_len)
+        cfg.nfft_min = int(nfft_min)
+        cfg.pix_lm = self._pix.ctypes.data_as(dp) if self._pix is not None else None
+        cfg.n_pix = 0 if self._pix is None else int(self._pix.shape[0])
+        cfg.beam_mode = int(beam_mode)
+        self.n_ant, self.n_samp, self.n_dm = cfg.n_ant, cfg.n_samp, cfg.n_dm
+        self.n_pix = cfg.n_pix
+        self._h = chirp_plan_create(cfg, stream)
+        info = _Info()
+        _check(load().chirp_plan_query(self._h, ctypes.byref(info)))
+        self.n_dump = int(info.n_dump)
+        self.n_pair = int(info.n_pair)
+        self.info = {k: int(getattr(info, k)) for k, _ in _Info._fields_}
+
+    @classmethod
+    def from_scenario(cls, sc, **kw):
+        return cls(sc.xyz, sc.f0, sc.bw, sc.n_samp, sc.dms, sc.dump_len, sc.nfft_min,
+                   pix_lm=sc.pix_lm, k_dm=sc.k_dm, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            chirp_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def dm_layout(self, d: int) -> dict:
+        out = (ctypes.c_longlong * 7)()
+        _check(load().chirp_dm_layout(self._h, int(d), out))
+        keys = ("nfft", "n_hi", "n_lo", "n_hi_max", "n_lo_max", "step", "n_blk")
+        return {k: int(v) for k, v in zip(keys, out)}
+
+    def dump_range(self):
+        first = (ctypes.c_longlong * self.n_dm)()
+        last = (ctypes.c_longlong * self.n_dm)()
+        _check(load().chirp_dump_range(self._h, first, last))
+        return np.array(first[:], dtype=np.int64), np.array(last[:], dtype=np.int64)
+
+    def dedisperse(self, volt, d: int, y_out):
+        chirp_dedisperse_run(self._h, volt, d, y_out)
+        return y_out
+
+    def chirpolator(self, volt, vis_out):
+        chirpolator_run(self._h, volt, vis_out)
+        return vis_out
+
+    def chimageator(self, volt, pow_out):
+        chimageator_run(self._h, volt, pow_out)
+        return pow_out
+
+    def stage_timing(self, enable: bool):
+        """Per-stage device ms and launch counts since the last call; switches
+        event timing on or off for later runs (synchronises the stream)."""
+        ms = (ctypes.c_double * len(STAGES))()
+        n = (ctypes.c_longlong * len(STAGES))()
+        _check(load().chirp_stage_timing(self._h, int(bool(enable)), ms, n))
+        return {k: (float(ms[j]), int(n[j])) for j, k in enumerate(STAGES)}

@@ -1,0 +1,259 @@
+// dedisperse.cu -- overlap-save coherent dedispersion (Sec. 2.3.2) on sm_103a.
+//
+// Every block of Nfft = n1 * n2 samples is transformed with two passes over
+// HBM (the "four-step" factorisation):
+//   forward:  column FFTs of length n1 (stride n2) on the raw voltages, times
+//             the twiddle W_N^(n2 k1), then row FFTs of length n2; the
+//             spectrum X[k1 + n1 k2] is left at position k1 n2 + k2;
+//   inverse:  row IFFTs of length n2 on that transposed spectrum with the
+//             chirp H_DM multiplied in on load and W_N^(-n2 k1) on store,
+//             then column IFFTs of length n1 that produce natural time order,
+//             scaled by 1/Nfft and scattered to the owned, valid samples.
+// The forward spectra do not depend on the DM and are computed once per
+// FFT-length group; the inverse pair runs once per trial DM.
+//
+// Chirp phase (Eq. 1 integrated over frequency; the benchmark spec precision rule):
+// the DM-independent table G = k_dm f^2/(f0^2 (f0+f)) is built in FP64, the
+// per-DM phase c = DM G is formed and range-reduced (c - rint c) in FP64, and
+// only the reduced fraction is converted to FP32 for sincospif.
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+#include "internal.h"
+
+namespace chirp {
+
+static __device__ __forceinline__ Twiddles mk_tw(TwiddlePtrs p) { return Twiddles{p.coarse, p.fine}; }
+
+// ------------------------------------------------------------------ forward
+// Column pass: L = n1, C = 4096 / n1 columns per CTA (interleaved tile).
+template <int L>
+__global__ void __launch_bounds__(256) k_fwd_cols(const float2* __restrict__ x, long long n_samp,
+                                                  float2* __restrict__ spec, int n2, int log2n,
+                                                  long long step, long long n_blk,
+                                                  TwiddlePtrs twp) {
+  constexpr int C = 4096 / L;
+  constexpr int T = L / 16;
+  __shared__ float2 sm[FftTile<L, C>::SLOTS];
+  const Twiddles tw = mk_tw(twp);
+  const int s = threadIdx.x % C, jt = threadIdx.x / C;
+  const int c = blockIdx.x * C + s;
+  const bool act = c < n2;
+  const long long q = blockIdx.y;  // a * n_blk + b
+  const long long a = q / n_blk, b = q % n_blk;
+  const long long nfft = (long long)L * n2;
+  const float2* xa = x + a * n_samp;
+  const long long base = b * step;
+  float2 v[16];
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    long long n = base + (long long)(jt + k * T) * n2 + c;
+    v[k] = (act && n < n_samp) ? xa[n] : make_float2(0.f, 0.f);
+  }
+  fft_core<L, C, false, false>(v, sm, s, jt, tw);
+  if (!act) return;
+  float2* out = spec + q * nfft;
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    int k1 = jt + k * T;
+    float2 w = tw_big<false>(tw, (unsigned)(k1 * c), log2n);
+    out[(long long)k1 * n2 + c] = cmul(v[k], w);
+  }
+}
+
+// Row pass: L = n2, C = 4096 / L rows per CTA (row-major tile), in place.
+template <int L>
+__global__ void __launch_bounds__(256) k_fwd_rows(float2* __restrict__ spec, int n1,
+                                                  TwiddlePtrs twp) {
+  constexpr int C = 4096 / L;
+  constexpr int T = L / 16;
+  __shared__ float2 sm[FftTile<L, C>::SLOTS];
+  const Twiddles tw = mk_tw(twp);
+  const int jt = threadIdx.x % T, s = threadIdx.x / T;
+  const int k1 = blockIdx.x * C + s;
+  const bool act = k1 < n1;
+  const long long nfft = (long long)L * n1;
+  float2* p = spec + (long long)blockIdx.y * nfft + (long long)k1 * L;
+  float2 v[16];
+#pragma unroll
+  for (int k = 0; k < 16; k++) v[k] = act ? p[jt + k * T] : make_float2(0.f, 0.f);
+  fft_core<L, C, true, false>(v, sm, s, jt, tw);
+  if (!act) return;
+#pragma unroll
+  for (int k = 0; k < 16; k++) p[jt + k * T] = v[k];
+}
+
+// ------------------------------------------------------------------ table
+__global__ void k_phase_table(double* __restrict__ G, long long nfft, int n1, int n2, double f0,
+                              double bw, double k_dm) {
+  long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= nfft) return;
+  long long k1 = pos / n2, k2 = pos % n2;
+  long long kf = k1 + (long long)n1 * k2;            // natural frequency index
+  double fi = (double)(kf < nfft / 2 ? kf : kf - nfft);
+  // f = fi B / Nfft; g = f^2 / (f0^2 (f0 + f)); G = k_dm g  (no fused ops)
+  double f = __ddiv_rn(__dmul_rn(fi, bw), (double)nfft);
+  double g = __ddiv_rn(__dmul_rn(f, f), __dmul_rn(__dmul_rn(f0, f0), __dadd_rn(f0, f)));
+  G[pos] = __dmul_rn(k_dm, g);
+}
+
+// ------------------------------------------------------------------ inverse
+// Row pass with the chirp: each CTA owns C rows and walks the sequences
+// blockIdx.y, blockIdx.y + gridDim.y, ... so the chirp of its rows (FP64 work)
+// is built once and reused for every antenna and block.
+template <int L>
+__global__ void __launch_bounds__(256) k_inv_rows(const float2* __restrict__ spec,
+                                                  float2* __restrict__ Z,
+                                                  const double* __restrict__ G, double dm, int n1,
+                                                  int log2n, long long n_seq, TwiddlePtrs twp) {
+  constexpr int C = 4096 / L;
+  constexpr int T = L / 16;
+  __shared__ float2 sm[FftTile<L, C>::SLOTS];
+  const Twiddles tw = mk_tw(twp);
+  const int jt = threadIdx.x % T, s = threadIdx.x / T;
+  const int k1 = blockIdx.x * C + s;
+  const bool act = k1 < n1;
+  const long long nfft = (long long)L * n1;
+  float2 H[16];
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    H[k] = make_float2(0.f, 0.f);
+    if (act) {
+      double c = __dmul_rn(dm, __ldg(G + (long long)k1 * L + jt + k * T));
+      double r = __dsub_rn(c, rint(c));              // exact: |r| <= 1/2
+      float sn, cs;
+      sincospif(-2.0f * (float)r, &sn, &cs);        // exp(-2 pi j r)
+      H[k] = make_float2(cs, sn);
+    }
+  }
+  for (long long q = blockIdx.y; q < n_seq; q += gridDim.y) {
+    const float2* src = spec + q * nfft + (long long)k1 * L;
+    float2 v[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) v[k] = act ? cmul(src[jt + k * T], H[k]) : make_float2(0.f, 0.f);
+    fft_core<L, C, true, true>(v, sm, s, jt, tw);
+    if (act) {
+      float2* dst = Z + q * nfft + (long long)k1 * L;
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        int n2i = jt + k * T;
+        dst[n2i] = cmul(v[k], tw_big<true>(tw, (unsigned)(k1 * n2i), log2n));
+      }
+    }
+  }
+}
+
+// Column pass of the inverse: natural-order output, 1/Nfft, overlap-save
+// discard and ownership.  Block b owns block positions [lo_b, hi_b).
+template <int L>
+__global__ void __launch_bounds__(256) k_inv_cols(const float2* __restrict__ Z,
+                                                  float2* __restrict__ y, long long n_samp,
+                                                  int n2, long long step, long long n_blk,
+                                                  long long n_hi, long long n_lo,
+                                                  long long n_hi_max, TwiddlePtrs twp) {
+  constexpr int C = 4096 / L;
+  constexpr int T = L / 16;
+  __shared__ float2 sm[FftTile<L, C>::SLOTS];
+  const Twiddles tw = mk_tw(twp);
+  const int s = threadIdx.x % C, jt = threadIdx.x / C;
+  const int c = blockIdx.x * C + s;
+  const bool act = c < n2;
+  const long long q = blockIdx.y;
+  const long long a = q / n_blk, b = q % n_blk;
+  const long long nfft = (long long)L * n2;
+  const float2* src = Z + q * nfft;
+  float2 v[16];
+#pragma unroll
+  for (int k = 0; k < 16; k++)
+    v[k] = act ? src[(long long)(jt + k * T) * n2 + c] : make_float2(0.f, 0.f);
+  fft_core<L, C, false, true>(v, sm, s, jt, tw);
+  if (!act) return;
+  const long long base = b * step;
+  const long long lo_b = (b == 0) ? n_hi : n_hi_max;
+  const long long hi_b = (b == n_blk - 1) ? (n_samp - n_lo - base) : (n_hi_max + step);
+  const float scale = 1.0f / (float)nfft;  // exact: power of two
+  float2* ya = y + a * n_samp;
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    long long n = (long long)(jt + k * T) * n2 + c;
+    if (n >= lo_b && n < hi_b) ya[base + n] = cscale(v[k], scale);
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+#define CHIRP_SIZES(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
+
+cudaError_t launch_forward(const float2* x, long long n_samp, int n_ant, const GroupGeom& g,
+                           float2* spec, TwiddlePtrs tw, cudaStream_t st) {
+  const long long n_seq = (long long)n_ant * g.n_blk;
+  if (n_seq > 65535) return cudaErrorInvalidConfiguration;
+  {
+    const int C = 4096 / g.n1;
+    dim3 grid((g.n2 + C - 1) / C, (unsigned)n_seq);
+    switch (g.n1) {
+#define X(L) \
+  case L: k_fwd_cols<L><<<grid, 256, 0, st>>>(x, n_samp, spec, g.n2, g.log2n, g.step, g.n_blk, tw); break;
+      CHIRP_SIZES(X)
+#undef X
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  {
+    const int C = 4096 / g.n2;
+    dim3 grid((g.n1 + C - 1) / C, (unsigned)n_seq);
+    switch (g.n2) {
+#define X(L) \
+  case L: k_fwd_rows<L><<<grid, 256, 0, st>>>(spec, g.n1, tw); break;
+      CHIRP_SIZES(X)
+#undef X
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_phase_table(double* G, const GroupGeom& g, double f0, double bw,
+                                     double k_dm, cudaStream_t st) {
+  long long blocks = (g.nfft + 255) / 256;
+  k_phase_table<<<(unsigned)blocks, 256, 0, st>>>(G, g.nfft, g.n1, g.n2, f0, bw, k_dm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const double* G, double dm,
+                                int n_ant, const GroupGeom& g, TwiddlePtrs tw, cudaStream_t st) {
+  const long long n_seq = (long long)n_ant * g.n_blk;
+  const int C = 4096 / g.n2;
+  const int row_tiles = (g.n1 + C - 1) / C;
+  // enough CTAs to fill the machine several times; each reuses its chirp
+  int by = (int)((4 * 152 + row_tiles - 1) / row_tiles);
+  if (by < 1) by = 1;
+  if (by > n_seq) by = (int)n_seq;
+  dim3 grid(row_tiles, by);
+  switch (g.n2) {
+#define X(L) \
+  case L: k_inv_rows<L><<<grid, 256, 0, st>>>(spec, Z, G, dm, g.n1, g.log2n, n_seq, tw); break;
+    CHIRP_SIZES(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, int n_ant,
+                                const GroupGeom& g, long long n_hi, long long n_lo,
+                                TwiddlePtrs tw, cudaStream_t st) {
+  const long long n_seq = (long long)n_ant * g.n_blk;
+  if (n_seq > 65535) return cudaErrorInvalidConfiguration;
+  const int C = 4096 / g.n1;
+  dim3 grid((g.n2 + C - 1) / C, (unsigned)n_seq);
+  switch (g.n1) {
+#define X(L) \
+  case L: k_inv_cols<L><<<grid, 256, 0, st>>>(Z, y, n_samp, g.n2, g.step, g.n_blk, n_hi, n_lo, g.n_hi_max, tw); break;
+    CHIRP_SIZES(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace chirp

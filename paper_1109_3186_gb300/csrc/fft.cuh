@@ -1,0 +1,253 @@
+// fft.cuh -- register/shared-memory radix-16 Stockham FFT building blocks.
+//
+// An FFT of length L (power of two, 16 <= L <= 4096) is split into radix-16
+// stages followed by at most one radix-2/4/8 stage.  Every thread holds
+// exactly 16 complex values; thread jt of a sequence starts with elements
+// jt + k L/16 (k = 0..15) and ends with the transformed elements at the same
+// positions, so global loads and stores around the core are plain strided
+// accesses that coalesce across the threads of a warp.  Values cross threads
+// only through shared memory, one exchange between consecutive stages.
+//
+// Two shared-memory tile layouts serve the two passes of the large
+// transforms:
+//   ROWMAJOR = true : C sequences of length L stored one after the other;
+//                     threads are numbered jt-fastest (rows of a matrix).
+//   ROWMAJOR = false: C sequences interleaved element-major (columns of a
+//                     matrix); threads are numbered sequence-fastest.
+// Both pad one slot every 16 so that every stage is free of bank conflicts.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace chirp {
+
+struct __align__(8) c32 {
+  float x, y;
+};
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -j (forward) or +j (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mj(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// twiddle tables in global memory (filled once per plan, FP64 on the host):
+//   tw_coarse[m] = exp(-2 pi j m / 4096)      m < 4096
+//   tw_fine[m]   = exp(-2 pi j m / 2^24)      m < 4096
+struct Twiddles {
+  const float2* coarse;
+  const float2* fine;
+};
+
+// exp(-+2 pi j m / 4096), m in [0, 4096)
+template <bool INV>
+__device__ __forceinline__ float2 tw4096(const Twiddles& t, int m) {
+  float2 w = __ldg(t.coarse + m);
+  return INV ? cconj(w) : w;
+}
+
+// exp(-+2 pi j e / nfft) for e in [0, nfft), nfft = 2^log2n <= 2^24
+template <bool INV>
+__device__ __forceinline__ float2 tw_big(const Twiddles& t, unsigned e, int log2n) {
+  unsigned e24 = e << (24 - log2n);
+  float2 w = cmul(__ldg(t.coarse + (e24 >> 12)), __ldg(t.fine + (e24 & 4095u)));
+  return INV ? cconj(w) : w;
+}
+
+// ---------------------------------------------------------------- small DFTs
+// In place, natural order in and out, sign -1 (forward) or +1 (INV).
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+  float2 a0 = cadd(x0, x2), a1 = csub(x0, x2);
+  float2 a2 = cadd(x1, x3), a3 = mul_mj<INV>(csub(x1, x3));
+  x0 = cadd(a0, a2);
+  x2 = csub(a0, a2);
+  x1 = cadd(a1, a3);
+  x3 = csub(a1, a3);
+}
+
+template <bool INV>
+__device__ __forceinline__ float2 rot8(float2 a, int m) {  // a * exp(-+2 pi j m / 8), m = 0..3
+  const float r = 0.70710678118654752440f;
+  switch (m & 7) {
+    case 0: return a;
+    case 1: return INV ? make_float2(r * (a.x - a.y), r * (a.x + a.y)) : make_float2(r * (a.x + a.y), r * (a.y - a.x));
+    case 2: return mul_mj<INV>(a);
+    default: return INV ? make_float2(-r * (a.x + a.y), r * (a.x - a.y)) : make_float2(r * (a.y - a.x), -r * (a.x + a.y));
+  }
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* v) {
+  // 8 = 2 x 4: n = 4 n1 + n2 ... written as: DFT4 over n1 of x[2 n1 + n2], twiddle, DFT2
+  dft4<INV>(v[0], v[2], v[4], v[6]);
+  dft4<INV>(v[1], v[3], v[5], v[7]);
+  // A[k1][n2] at v[2 k1 + n2]; multiply by W8^(n2 k1)
+  v[3] = rot8<INV>(v[3], 1);
+  v[5] = rot8<INV>(v[5], 2);
+  v[7] = rot8<INV>(v[7], 3);
+  dft2<INV>(v[0], v[1]);
+  dft2<INV>(v[2], v[3]);
+  dft2<INV>(v[4], v[5]);
+  dft2<INV>(v[6], v[7]);
+  // X[k1 + 4 k2] sits at v[2 k1 + k2]
+  float2 t[8];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; k1++)
+#pragma unroll
+    for (int k2 = 0; k2 < 2; k2++) t[k1 + 4 * k2] = v[2 * k1 + k2];
+#pragma unroll
+  for (int i = 0; i < 8; i++) v[i] = t[i];
+}
+
+template <bool INV>
+__device__ __forceinline__ float2 rot16(float2 a, int m) {  // a * exp(-+2 pi j m / 16)
+  const float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f;
+  const float r = 0.70710678118654752440f;
+  float c, s;  // exp(-2 pi j m/16) = c - j s (forward)
+  switch (m) {
+    case 0: return a;
+    case 1: c = c1; s = s1; break;
+    case 2: c = r; s = r; break;
+    case 3: c = s1; s = c1; break;
+    case 4: return mul_mj<INV>(a);
+    case 6: c = -r; s = r; break;
+    case 9: c = -c1; s = -s1; break;
+    default: c = 1.f; s = 0.f; break;  // not used
+  }
+  if (INV) s = -s;
+  return make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -a.x * s));
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* v) {
+  // 16 = 4 x 4: DFT4 over n1 of x[4 n1 + n2], twiddle W16^(n2 k1), DFT4 over n2
+#pragma unroll
+  for (int n2 = 0; n2 < 4; n2++) dft4<INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+#pragma unroll
+  for (int k1 = 1; k1 < 4; k1++)
+#pragma unroll
+    for (int n2 = 1; n2 < 4; n2++) v[4 * k1 + n2] = rot16<INV>(v[4 * k1 + n2], n2 * k1);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; k1++) dft4<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+  float2 t[16];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; k1++)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; k2++) t[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+  for (int i = 0; i < 16; i++) v[i] = t[i];
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_r(float2* v) {
+  if constexpr (R == 2) dft2<INV>(v[0], v[1]);
+  else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
+  else if constexpr (R == 8) dft8<INV>(v);
+  else dft16<INV>(v);
+}
+
+// ---------------------------------------------------------------- the core
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
+
+// padded shared-memory slot of linear index i (one pad slot every 16)
+__device__ __forceinline__ int padidx(int i) { return i + (i >> 4); }
+
+template <int L, int C>
+struct FftTile {
+  static constexpr int T = L / 16;                   // threads per sequence
+  static constexpr int THREADS = T * C;
+  static constexpr int SLOTS = (L * C) + (L * C) / 16;  // padded float2 count
+};
+
+// Shared-memory index of element i of sequence s.
+template <int L, int C, bool ROWMAJOR>
+__device__ __forceinline__ int tile_idx(int i, int s) {
+  return padidx(ROWMAJOR ? s * L + i : i * C + s);
+}
+
+// Stockham stage helpers -------------------------------------------------
+// One radix-R stage of span Ns over L points for butterfly j:
+//   in:  a[j + q L/R],  twiddle W_{Ns R}^{q (j mod Ns)},  DFT_R,
+//   out: b[(j / Ns) Ns R + (j mod Ns) + q Ns].
+template <int L, int R, bool INV>
+__device__ __forceinline__ void stage_twiddle(float2* v, int j, int Ns, const Twiddles& tw) {
+  if (Ns == 1) return;
+  int jm = j & (Ns - 1);
+  int scale = 4096 / (Ns * R);
+#pragma unroll
+  for (int q = 1; q < R; q++) v[q] = cmul(v[q], tw4096<INV>(tw, (q * jm * scale) & 4095));
+}
+
+// Forward (INV=false) or inverse (INV=true, unnormalised) FFT of length L.
+// On entry v[k] = element jt + k L/16 of sequence s; on exit the same
+// positions hold the transform.  sm: at least FftTile<L,C>::SLOTS float2.
+// All threads of the block that own (s, jt) pairs must call it together.
+template <int L, int C, bool ROWMAJOR, bool INV>
+__device__ __forceinline__ void fft_core(float2 (&v)[16], float2* sm, int s, int jt,
+                                         const Twiddles& tw) {
+  static_assert(L >= 16 && L <= 4096 && (L & (L - 1)) == 0, "L");
+  constexpr int LOG = ilog2c(L);
+  constexpr int N16 = LOG / 4;           // radix-16 stages
+  constexpr int RLAST = 1 << (LOG % 4);  // trailing radix (1 = none)
+  constexpr int T = L / 16;
+
+  int Ns = 1;
+#pragma unroll
+  for (int st = 0; st < N16; st++) {
+    // radix-16 stage: butterfly j = jt reads a[jt + q T] (already in v)
+    stage_twiddle<L, 16, INV>(v, jt, Ns, tw);
+    dft_r<16, INV>(v);
+    const bool last = (st == N16 - 1) && (RLAST == 1);
+    if (last) return;  // outputs b[jt + q T] == positions already held
+    // write b[(j/Ns) Ns 16 + j%Ns + q Ns], then read the next stage inputs
+    {
+      int base = (jt / Ns) * Ns * 16 + (jt & (Ns - 1));
+#pragma unroll
+      for (int q = 0; q < 16; q++) sm[tile_idx<L, C, ROWMAJOR>(base + q * Ns, s)] = v[q];
+    }
+    __syncthreads();
+    Ns *= 16;
+    if (st + 1 < N16) {
+#pragma unroll
+      for (int q = 0; q < 16; q++) v[q] = sm[tile_idx<L, C, ROWMAJOR>(jt + q * T, s)];
+    } else {
+      // trailing radix-RLAST stage: butterflies j = jt + u T, u < 16/RLAST,
+      // each reads a[j + q L/RLAST]; element index = jt + (u + q 16/RLAST) T
+#pragma unroll
+      for (int k = 0; k < 16; k++) v[k] = sm[tile_idx<L, C, ROWMAJOR>(jt + k * T, s)];
+    }
+    __syncthreads();
+  }
+  if constexpr (RLAST > 1) {
+    constexpr int U = 16 / RLAST;
+    // Ns == L / RLAST here.  v[u + q U] holds a[jt + u T + q L/RLAST].
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      float2 w[RLAST];
+#pragma unroll
+      for (int q = 0; q < RLAST; q++) w[q] = v[u + q * U];
+      const int j = jt + u * T;
+      if constexpr (N16 > 0) stage_twiddle<L, RLAST, INV>(w, j, L / RLAST, tw);
+      dft_r<RLAST, INV>(w);
+      // output b[j + q Ns] = element jt + (u + q U) T  -> same register slot
+#pragma unroll
+      for (int q = 0; q < RLAST; q++) v[u + q * U] = w[q];
+    }
+  }
+}
+
+}  // namespace chirp

@@ -1,0 +1,49 @@
+// internal.h -- host-side declarations shared by the library's translation
+// units (plan orchestration <-> kernel launchers).  Not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+namespace chirp {
+
+// One FFT-length group: DMs that share Nfft and therefore one block grid.
+struct GroupGeom {
+  long long nfft;   // transform length
+  int log2n;
+  int n1, n2;       // nfft = n1 * n2; column pass of length n1, row pass of length n2
+  long long step;   // block step S
+  long long n_blk;  // blocks per antenna
+  long long n_hi_max, n_lo_max;
+};
+
+struct TwiddlePtrs {
+  const float2* coarse;  // exp(-2 pi j m / 4096), m < 4096
+  const float2* fine;    // exp(-2 pi j m / 2^24), m < 4096
+};
+
+// ---- dedispersion kernels (dedisperse.cu) ----
+// spectra of every (antenna, block) of one group; spec [n_ant][n_blk][nfft]
+// holds X[k1 + n1 k2] at position k1 * n2 + k2.
+cudaError_t launch_forward(const float2* x, long long n_samp, int n_ant, const GroupGeom& g,
+                           float2* spec, TwiddlePtrs tw, cudaStream_t st);
+// G[pos] = k_dm f^2/(f0^2 (f0 + f)) in the spectrum's (transposed) order, FP64
+cudaError_t launch_build_phase_table(double* G, const GroupGeom& g, double f0, double bw,
+                                     double k_dm, cudaStream_t st);
+// Z = rows of IFFT after the chirp multiply and the inter-pass twiddle
+cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const double* G, double dm,
+                                int n_ant, const GroupGeom& g, TwiddlePtrs tw, cudaStream_t st);
+// y[a][t] = dedispersed voltage for every owned, valid t (other t untouched)
+cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, int n_ant,
+                                const GroupGeom& g, long long n_hi, long long n_lo,
+                                TwiddlePtrs tw, cudaStream_t st);
+
+// ---- back-ends (backends.cu) ----
+cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int dump_len,
+                             long long n_dump, long long first, long long last, float2* vis,
+                             cudaStream_t st);
+cudaError_t launch_beamform_simt(const float2* y, long long n_samp, int n_ant, int dump_len,
+                                 long long n_dump, long long first, long long last,
+                                 const float2* W, int n_pix, float* pow, cudaStream_t st);
+
+}  // namespace chirp

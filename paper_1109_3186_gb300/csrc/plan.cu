@@ -1,0 +1,573 @@
+// plan.cu -- the C ABI of include/chirp_gb300.h: plan creation (block grids,
+// device workspace, FP64 tables, beam weights) and the run entry points that
+// sequence the kernels on the plan's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/chirp_gb300.h"
+#include "internal.h"
+
+using namespace chirp;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(CHIRP_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                  __FILE__, __LINE__);                                                    \
+  } while (0)
+
+constexpr double kDefaultKdm = 4.148808e15;  // s Hz^2 / (pc cm^-3)
+constexpr double kCLight = 299792458.0;      // m/s
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+long long pow2ceil(long long n) {
+  long long p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+int ilog2ll(long long n) {
+  int l = 0;
+  while ((1LL << l) < n) l++;
+  return l;
+}
+bool is_pow2(long long n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Eq. 1 sweep about f0 in samples (above, below the band centre)
+void sweep(double f0, double bw, double k_dm, double dm, long long* n_hi, long long* n_lo) {
+  double fh = f0 + 0.5 * bw, fl = f0 - 0.5 * bw;
+  double t_hi = k_dm * dm * (1.0 / (f0 * f0) - 1.0 / (fh * fh));
+  double t_lo = k_dm * dm * (1.0 / (fl * fl) - 1.0 / (f0 * f0));
+  *n_hi = (long long)std::ceil(t_hi * bw);
+  *n_lo = (long long)std::ceil(t_lo * bw);
+}
+
+struct Group {
+  GroupGeom geom;
+  std::vector<int> dms;
+  double* d_G = nullptr;     // FP64 phase table, spectrum order
+  float2* d_spec = nullptr;  // [n_ant][n_blk][nfft]
+};
+
+struct DmInfo {
+  int group;
+  long long n_hi, n_lo, first, last;
+};
+
+}  // namespace
+
+struct chirp_plan {
+  int M = 0;
+  std::vector<double> xyz;
+  double f0 = 0, bw = 0, kdm = 0;
+  long long N = 0;
+  std::vector<double> dm;
+  int L = 0;
+  long long nfft_min = 0;
+  std::vector<double> pix;
+  int n_pix = 0;
+  int beam_mode = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<Group> groups;
+  std::vector<DmInfo> dmi;
+  long long n_dump = 0;
+  int n_pair = 0;
+  // device workspace
+  float2* d_tw = nullptr;    // [8192]: coarse then fine
+  float2* d_x = nullptr;     // staging copy of host voltages [M][N]
+  float2* d_Z = nullptr;     // inverse-row intermediate, largest group
+  float2* d_y = nullptr;     // dedispersed voltages of one DM [M][N]
+  float2* d_W = nullptr;     // beam weights [n_pix][M]
+  void* d_out = nullptr;     // staging for host outputs
+  size_t out_bytes = 0;
+  size_t ws_bytes = 0;
+  long long ifft_points = 0, valid_samples = 0;
+  // optional per-stage event timing (chirp_stage_timing)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<int, int>>> ev_marks;  // stage, (start ev, stop ev)
+  size_t ev_next = 0;
+  double stage_ms[CHIRP_N_STAGES] = {0};
+  long long stage_launches[CHIRP_N_STAGES] = {0};
+
+  TwiddlePtrs tw() const { return TwiddlePtrs{d_tw, d_tw + 4096}; }
+};
+
+namespace {
+
+int dev_alloc(chirp_plan* p, void** ptr, size_t bytes, const char* what) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? CHIRP_ENOMEM : CHIRP_ECUDA,
+                "cudaMalloc(%zu bytes) for %s failed: %s", bytes, what, cudaGetErrorString(e));
+  }
+  p->ws_bytes += bytes;
+  return CHIRP_OK;
+}
+
+void release(chirp_plan* p) {
+  if (!p) return;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  for (auto& g : p->groups) {
+    cudaFree(g.d_G);
+    cudaFree(g.d_spec);
+  }
+  cudaFree(p->d_tw);
+  cudaFree(p->d_x);
+  cudaFree(p->d_Z);
+  cudaFree(p->d_y);
+  cudaFree(p->d_W);
+  cudaFree(p->d_out);
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+}
+
+// events bracketing one kernel launch of a stage (no-op unless timing is on)
+int mark_begin(chirp_plan* p) {
+  if (!p->timing) return -1;
+  if (p->ev_next + 2 > p->ev_pool.size()) {
+    for (int i = 0; i < 256; i++) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      p->ev_pool.push_back(e);
+    }
+  }
+  int i = (int)p->ev_next;
+  p->ev_next += 2;
+  cudaEventRecord(p->ev_pool[i], p->stream);
+  return i;
+}
+void mark_end(chirp_plan* p, int stage, int i) {
+  if (i < 0) return;
+  cudaEventRecord(p->ev_pool[i + 1], p->stream);
+  p->ev_marks.push_back({stage, {i, i + 1}});
+}
+// fold recorded events into the per-stage totals (synchronises the stream)
+void collect_marks(chirp_plan* p) {
+  if (p->ev_marks.empty()) return;
+  cudaStreamSynchronize(p->stream);
+  for (auto& m : p->ev_marks) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->ev_pool[m.second.first], p->ev_pool[m.second.second]) ==
+        cudaSuccess) {
+      p->stage_ms[m.first] += ms;
+      p->stage_launches[m.first] += 1;
+    }
+  }
+  p->ev_marks.clear();
+  p->ev_next = 0;
+}
+
+int validate(const chirp_config* c) {
+  if (!c) return fail(CHIRP_EINVAL, "config is NULL");
+  if (c->n_ant < 1 || c->n_ant > 90) return fail(CHIRP_EINVAL, "n_ant must be in 1..90");
+  if (!(c->f0_hz > 0) || !(c->bw_hz > 0) || !(c->bw_hz < 2 * c->f0_hz))
+    return fail(CHIRP_EINVAL, "need f0 > 0 and 0 < bw < 2 f0");
+  if (c->n_samp < 1) return fail(CHIRP_EINVAL, "n_samp must be >= 1");
+  if (!c->dm || c->n_dm < 1) return fail(CHIRP_EINVAL, "need at least one DM");
+  for (int d = 0; d < c->n_dm; d++)
+    if (!(c->dm[d] >= 0) || !std::isfinite(c->dm[d]))
+      return fail(CHIRP_EINVAL, "DM %d is negative or not finite", d);
+  if (c->dump_len < 1 || c->dump_len > c->n_samp)
+    return fail(CHIRP_EINVAL, "dump_len must be in 1..n_samp");
+  if (!is_pow2(c->nfft_min) || c->nfft_min < 256 || c->nfft_min > (1LL << 24))
+    return fail(CHIRP_EINVAL, "nfft_min must be a power of two in 256..2^24");
+  if (c->n_pix < 0) return fail(CHIRP_EINVAL, "n_pix must be >= 0");
+  if (c->n_pix > 0 && (!c->pix_lm || !c->xyz_m))
+    return fail(CHIRP_EINVAL, "beams need pix_lm and xyz_m");
+  if (c->n_pix > 0)
+    for (int p = 0; p < c->n_pix; p++) {
+      double l = c->pix_lm[2 * p], m = c->pix_lm[2 * p + 1];
+      if (!(l * l + m * m <= 1.0)) return fail(CHIRP_EINVAL, "pixel %d has l^2 + m^2 > 1", p);
+    }
+  if (c->beam_mode < 0 || c->beam_mode > CHIRP_BEAM_TC_3XBF16)
+    return fail(CHIRP_EINVAL, "unknown beam_mode");
+  return CHIRP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* chirp_last_error(void) { return g_err; }
+
+int chirp_stage_timing(chirp_plan* p, int enable, double* ms, long long* launches) {
+  if (!p) return fail(CHIRP_EINVAL, "plan is NULL");
+  collect_marks(p);
+  if (ms)
+    for (int i = 0; i < CHIRP_N_STAGES; i++) ms[i] = p->stage_ms[i];
+  if (launches)
+    for (int i = 0; i < CHIRP_N_STAGES; i++) launches[i] = p->stage_launches[i];
+  for (int i = 0; i < CHIRP_N_STAGES; i++) {
+    p->stage_ms[i] = 0;
+    p->stage_launches[i] = 0;
+  }
+  p->timing = enable != 0;
+  return CHIRP_OK;
+}
+
+int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
+  g_err[0] = 0;
+  if (!out) return fail(CHIRP_EINVAL, "plan pointer is NULL");
+  *out = nullptr;
+  int rc = validate(cfg);
+  if (rc) return rc;
+  chirp_plan* p = new (std::nothrow) chirp_plan();
+  if (!p) return fail(CHIRP_ENOMEM, "host allocation failed");
+  p->M = cfg->n_ant;
+  if (cfg->xyz_m) p->xyz.assign(cfg->xyz_m, cfg->xyz_m + 3 * cfg->n_ant);
+  p->f0 = cfg->f0_hz;
+  p->bw = cfg->bw_hz;
+  p->kdm = cfg->k_dm > 0 ? cfg->k_dm : kDefaultKdm;
+  p->N = cfg->n_samp;
+  p->dm.assign(cfg->dm, cfg->dm + cfg->n_dm);
+  p->L = cfg->dump_len;
+  p->nfft_min = cfg->nfft_min;
+  if (cfg->n_pix > 0) p->pix.assign(cfg->pix_lm, cfg->pix_lm + 2 * cfg->n_pix);
+  p->n_pix = cfg->n_pix;
+  // the tensor-core beamformer is not built yet: AUTO resolves to FP32 SIMT
+  p->beam_mode = cfg->beam_mode == CHIRP_BEAM_AUTO ? CHIRP_BEAM_FP32_SIMT : cfg->beam_mode;
+  if (p->beam_mode == CHIRP_BEAM_TC_3XBF16) {
+    delete p;
+    return fail(CHIRP_EUNSUPPORTED, "tensor-core beam mode is not available in this build");
+  }
+  p->stream = (cudaStream_t)stream;
+  p->n_dump = p->N / p->L;
+  p->n_pair = p->M * (p->M + 1) / 2;
+
+  // ---- per-DM FFT length and groups
+  const int n_dm = (int)p->dm.size();
+  std::vector<long long> nfft(n_dm), hi(n_dm), lo(n_dm);
+  for (int d = 0; d < n_dm; d++) {
+    sweep(p->f0, p->bw, p->kdm, p->dm[d], &hi[d], &lo[d]);
+    long long nd = hi[d] + lo[d];
+    long long want = pow2ceil(2 * nd > 1 ? 2 * nd : 1);
+    long long cap = pow2ceil(p->N);
+    long long n = std::min(want, cap);
+    nfft[d] = std::max(n, p->nfft_min);
+    if (nfft[d] > (1LL << 24)) {
+      delete p;
+      return fail(CHIRP_EUNSUPPORTED, "DM %g needs an FFT of %lld points (> 2^24)", p->dm[d],
+                  nfft[d]);
+    }
+  }
+  p->dmi.resize(n_dm);
+  for (int d = 0; d < n_dm; d++) {
+    int gi = -1;
+    for (size_t g = 0; g < p->groups.size(); g++)
+      if (p->groups[g].geom.nfft == nfft[d]) gi = (int)g;
+    if (gi < 0) {
+      Group g;
+      std::memset(&g.geom, 0, sizeof g.geom);
+      g.geom.nfft = nfft[d];
+      p->groups.push_back(g);
+      gi = (int)p->groups.size() - 1;
+    }
+    p->groups[gi].dms.push_back(d);
+    p->dmi[d].group = gi;
+  }
+  for (auto& g : p->groups) {
+    GroupGeom& G = g.geom;
+    G.log2n = ilog2ll(G.nfft);
+    G.n1 = (int)std::max<long long>(16, G.nfft / 4096);
+    G.n2 = (int)(G.nfft / G.n1);
+    G.n_hi_max = 0;
+    G.n_lo_max = 0;
+    for (int d : g.dms) {
+      G.n_hi_max = std::max(G.n_hi_max, hi[d]);
+      G.n_lo_max = std::max(G.n_lo_max, lo[d]);
+    }
+    G.step = G.nfft - G.n_hi_max - G.n_lo_max;
+    if (p->N <= G.nfft) {
+      G.n_blk = 1;
+    } else {
+      if (G.step <= 0) {
+        delete p;
+        return fail(CHIRP_EINVAL, "internal: non-positive block step");
+      }
+      G.n_blk = (p->N - G.nfft + G.step - 1) / G.step + 1;
+    }
+    if ((long long)p->M * G.n_blk > 65535) {
+      delete p;
+      return fail(CHIRP_EUNSUPPORTED, "n_ant * blocks = %lld exceeds 65535",
+                  (long long)p->M * G.n_blk);
+    }
+  }
+  for (int d = 0; d < n_dm; d++) {
+    DmInfo& I = p->dmi[d];
+    I.n_hi = hi[d];
+    I.n_lo = lo[d];
+    I.first = (I.n_hi + p->L - 1) / p->L;
+    long long end = p->N - I.n_lo;
+    I.last = end >= 0 ? end / p->L - 1 : -1;
+    const GroupGeom& G = p->groups[I.group].geom;
+    p->ifft_points += (long long)p->M * G.n_blk * G.nfft;
+    long long v = p->N - I.n_hi - I.n_lo;
+    p->valid_samples += (long long)p->M * (v > 0 ? v : 0);
+  }
+
+  // ---- device workspace
+  rc = dev_alloc(p, (void**)&p->d_tw, 8192 * sizeof(float2), "twiddles");
+  size_t z_elems = 0;
+  for (auto& g : p->groups) {
+    size_t elems = (size_t)p->M * g.geom.n_blk * g.geom.nfft;
+    z_elems = std::max(z_elems, elems);
+    if (!rc) rc = dev_alloc(p, (void**)&g.d_spec, elems * sizeof(float2), "spectra");
+    if (!rc) rc = dev_alloc(p, (void**)&g.d_G, g.geom.nfft * sizeof(double), "phase table");
+  }
+  if (!rc) rc = dev_alloc(p, (void**)&p->d_Z, z_elems * sizeof(float2), "inverse workspace");
+  if (!rc) rc = dev_alloc(p, (void**)&p->d_y, (size_t)p->M * p->N * sizeof(float2), "voltages");
+  if (!rc && p->n_pix > 0)
+    rc = dev_alloc(p, (void**)&p->d_W, (size_t)p->n_pix * p->M * sizeof(float2), "weights");
+  if (rc) {
+    release(p);
+    delete p;
+    return rc;
+  }
+
+  // ---- twiddles (FP64 on the host, rounded once)
+  std::vector<float2> tw(8192);
+  for (int m = 0; m < 4096; m++) {
+    double a = -2.0 * kPi * m / 4096.0;
+    tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+    double b = -2.0 * kPi * m / 16777216.0;
+    tw[4096 + m] = make_float2((float)std::cos(b), (float)std::sin(b));
+  }
+  // ---- beam weights W_pa = exp(+2 pi j f0 tau_a(l_p, m_p)), Eq. tau3D
+  std::vector<float2> W((size_t)p->n_pix * p->M);
+  for (int q = 0; q < p->n_pix; q++) {
+    double l = p->pix[2 * q], m = p->pix[2 * q + 1];
+    double n = std::sqrt(1.0 - l * l - m * m);
+    for (int a = 0; a < p->M; a++) {
+      double tau = (p->xyz[3 * a] * l + p->xyz[3 * a + 1] * m + p->xyz[3 * a + 2] * (n - 1.0)) /
+                   kCLight;
+      double ph = 2.0 * kPi * p->f0 * tau;
+      W[(size_t)q * p->M + a] = make_float2((float)std::cos(ph), (float)std::sin(ph));
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(p->d_tw, tw.data(), tw.size() * sizeof(float2),
+                                  cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess && p->n_pix > 0)
+    e = cudaMemcpyAsync(p->d_W, W.data(), W.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                        p->stream);
+  for (auto& g : p->groups)
+    if (e == cudaSuccess)
+      e = launch_build_phase_table(g.d_G, g.geom, p->f0, p->bw, p->kdm, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) {
+    release(p);
+    delete p;
+    return fail(CHIRP_ECUDA, "plan set-up failed: %s", cudaGetErrorString(e));
+  }
+  *out = p;
+  return CHIRP_OK;
+}
+
+void chirp_plan_destroy(chirp_plan* p) {
+  release(p);
+  delete p;
+}
+
+int chirp_plan_query(const chirp_plan* p, chirp_plan_info* info) {
+  if (!p || !info) return fail(CHIRP_EINVAL, "NULL argument");
+  info->n_dump = p->n_dump;
+  info->n_pair = p->n_pair;
+  info->n_group = (int)p->groups.size();
+  info->workspace_bytes = (long long)p->ws_bytes;
+  info->ifft_points = p->ifft_points;
+  info->valid_samples = p->valid_samples;
+  info->beam_mode = p->beam_mode;
+  return CHIRP_OK;
+}
+
+int chirp_dm_layout(const chirp_plan* p, int d, long long* out7) {
+  if (!p || !out7 || d < 0 || d >= (int)p->dm.size()) return fail(CHIRP_EINVAL, "bad argument");
+  const DmInfo& I = p->dmi[d];
+  const GroupGeom& G = p->groups[I.group].geom;
+  out7[0] = G.nfft;
+  out7[1] = I.n_hi;
+  out7[2] = I.n_lo;
+  out7[3] = G.n_hi_max;
+  out7[4] = G.n_lo_max;
+  out7[5] = G.step;
+  out7[6] = G.n_blk;
+  return CHIRP_OK;
+}
+
+int chirp_dump_range(const chirp_plan* p, long long* first, long long* last) {
+  if (!p || !first || !last) return fail(CHIRP_EINVAL, "NULL argument");
+  for (size_t d = 0; d < p->dmi.size(); d++) {
+    first[d] = p->dmi[d].first;
+    last[d] = p->dmi[d].last;
+  }
+  return CHIRP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// voltages on the device, copying host input into the plan's staging buffer
+int stage_input(chirp_plan* p, const void* volt, int loc, const float2** dx) {
+  if (!volt) return fail(CHIRP_EINVAL, "voltage pointer is NULL");
+  if (loc == CHIRP_DEVICE) {
+    *dx = (const float2*)volt;
+    return CHIRP_OK;
+  }
+  if (loc != CHIRP_HOST) return fail(CHIRP_EINVAL, "bad buffer location");
+  if (!p->d_x) {
+    int rc = dev_alloc(p, (void**)&p->d_x, (size_t)p->M * p->N * sizeof(float2), "input staging");
+    if (rc) return rc;
+  }
+  CK(cudaMemcpyAsync(p->d_x, volt, (size_t)p->M * p->N * sizeof(float2), cudaMemcpyHostToDevice,
+                     p->stream));
+  *dx = p->d_x;
+  return CHIRP_OK;
+}
+
+int out_buffer(chirp_plan* p, void* user, int loc, size_t bytes, void** dev) {
+  if (!user) return fail(CHIRP_EINVAL, "output pointer is NULL");
+  if (loc == CHIRP_DEVICE) {
+    *dev = user;
+    return CHIRP_OK;
+  }
+  if (loc != CHIRP_HOST) return fail(CHIRP_EINVAL, "bad buffer location");
+  if (p->out_bytes < bytes) {
+    cudaFree(p->d_out);
+    p->d_out = nullptr;
+    p->out_bytes = 0;
+    int rc = dev_alloc(p, &p->d_out, bytes, "output staging");
+    if (rc) return rc;
+    p->out_bytes = bytes;
+  }
+  *dev = p->d_out;
+  return CHIRP_OK;
+}
+
+int finish_out(chirp_plan* p, void* user, int loc, const void* dev, size_t bytes) {
+  if (loc == CHIRP_HOST) {
+    CK(cudaMemcpyAsync(user, dev, bytes, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+  }
+  return CHIRP_OK;
+}
+
+int forward_all(chirp_plan* p, const float2* dx) {
+  for (auto& g : p->groups) {
+    int mk = mark_begin(p);
+    CK(launch_forward(dx, p->N, p->M, g.geom, g.d_spec, p->tw(), p->stream));
+    mark_end(p, CHIRP_STAGE_FORWARD, mk);
+  }
+  return CHIRP_OK;
+}
+
+int dedisperse_one(chirp_plan* p, int d, float2* y) {
+  const DmInfo& I = p->dmi[d];
+  Group& g = p->groups[I.group];
+  int mk = mark_begin(p);
+  CK(launch_inverse_rows(g.d_spec, p->d_Z, g.d_G, p->dm[d], p->M, g.geom, p->tw(), p->stream));
+  mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
+  mk = mark_begin(p);
+  CK(launch_inverse_cols(p->d_Z, y, p->N, p->M, g.geom, I.n_hi, I.n_lo, p->tw(), p->stream));
+  mark_end(p, CHIRP_STAGE_INV_COLS, mk);
+  return CHIRP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int chirp_dedisperse_run(chirp_plan* p, const void* volt, int volt_loc, int d, void* y_out,
+                         int y_loc) {
+  g_err[0] = 0;
+  if (!p) return fail(CHIRP_EINVAL, "plan is NULL");
+  if (d < 0 || d >= (int)p->dm.size()) return fail(CHIRP_EINVAL, "DM index out of range");
+  const float2* dx;
+  int rc = stage_input(p, volt, volt_loc, &dx);
+  if (rc) return rc;
+  size_t bytes = (size_t)p->M * p->N * sizeof(float2);
+  void* dy;
+  rc = out_buffer(p, y_out, y_loc, bytes, &dy);
+  if (rc) return rc;
+  const DmInfo& I = p->dmi[d];
+  Group& g = p->groups[I.group];
+  CK(launch_forward(dx, p->N, p->M, g.geom, g.d_spec, p->tw(), p->stream));
+  CK(cudaMemsetAsync(dy, 0, bytes, p->stream));
+  rc = dedisperse_one(p, d, (float2*)dy);
+  if (rc) return rc;
+  return finish_out(p, y_out, y_loc, dy, bytes);
+}
+
+int chirpolator_run(chirp_plan* p, const void* volt, int volt_loc, void* vis_out, int vis_loc) {
+  g_err[0] = 0;
+  if (!p) return fail(CHIRP_EINVAL, "plan is NULL");
+  const float2* dx;
+  int rc = stage_input(p, volt, volt_loc, &dx);
+  if (rc) return rc;
+  const size_t per_dm = (size_t)p->n_dump * p->n_pair;
+  const size_t bytes = per_dm * p->dm.size() * sizeof(float2);
+  void* dv;
+  rc = out_buffer(p, vis_out, vis_loc, bytes, &dv);
+  if (rc) return rc;
+  rc = forward_all(p, dx);
+  if (rc) return rc;
+  for (int d = 0; d < (int)p->dm.size(); d++) {
+    rc = dedisperse_one(p, d, p->d_y);
+    if (rc) return rc;
+    const DmInfo& I = p->dmi[d];
+    int mk = mark_begin(p);
+    CK(launch_correlate(p->d_y, p->N, p->M, p->L, p->n_dump, I.first, I.last,
+                        (float2*)dv + d * per_dm, p->stream));
+    mark_end(p, CHIRP_STAGE_CORRELATE, mk);
+  }
+  return finish_out(p, vis_out, vis_loc, dv, bytes);
+}
+
+int chimageator_run(chirp_plan* p, const void* volt, int volt_loc, float* pow_out, int pow_loc) {
+  g_err[0] = 0;
+  if (!p) return fail(CHIRP_EINVAL, "plan is NULL");
+  if (p->n_pix <= 0) return fail(CHIRP_EUNSUPPORTED, "plan was created without pixels");
+  const float2* dx;
+  int rc = stage_input(p, volt, volt_loc, &dx);
+  if (rc) return rc;
+  const size_t per_dm = (size_t)p->n_dump * p->n_pix;
+  const size_t bytes = per_dm * p->dm.size() * sizeof(float);
+  void* dp;
+  rc = out_buffer(p, pow_out, pow_loc, bytes, &dp);
+  if (rc) return rc;
+  rc = forward_all(p, dx);
+  if (rc) return rc;
+  for (int d = 0; d < (int)p->dm.size(); d++) {
+    rc = dedisperse_one(p, d, p->d_y);
+    if (rc) return rc;
+    const DmInfo& I = p->dmi[d];
+    int mk = mark_begin(p);
+    CK(launch_beamform_simt(p->d_y, p->N, p->M, p->L, p->n_dump, I.first, I.last, p->d_W,
+                            p->n_pix, (float*)dp + d * per_dm, p->stream));
+    mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
+  }
+  return finish_out(p, pow_out, pow_loc, dp, bytes);
+}
+
+}  // extern "C"
