@@ -50,7 +50,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--beam-mode", type=int, default=0, help="0 auto, 1 FP32 SIMT, 2 tcgen05 3xbf16")
-    ap.add_argument("--cpu-dumps", type=int, default=24,
+    ap.add_argument("--cpu-dumps", type=int, default=128,
                     help="dumps per selected DM in the oracle's bounded CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
