@@ -54,6 +54,10 @@ def parse_args():
                     help="dumps per selected DM in the oracle's bounded CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dms", type=int, default=0,
+                    help="profiling only: keep this many evenly spaced DMs of the 64")
+    ap.add_argument("--n-samp", type=int, default=0,
+                    help="profiling only: shorter series (samples per antenna)")
     return ap.parse_args()
 
 
@@ -67,14 +71,22 @@ def load_peaks():
         return dict(FALLBACK_PEAKS), "fallback"
 
 
-def scenario(rank: int):
+def scenario(rank: int, args=None):
     from paper_1109_3186_gb300 import skymodel
+    kw = {}
+    if args is not None and args.n_samp:
+        kw["n_samp"] = args.n_samp
     # each rank searches its own observation (weak scaling, no exchange)
-    return skymodel.chimageator_medium(seed=1002 + 1000 * rank)
+    sc = skymodel.chimageator_medium(seed=1002 + 1000 * rank, **kw)
+    if args is not None and args.dms:
+        keep = np.unique(np.linspace(0, len(sc.dms) - 1, args.dms).round().astype(int))
+        sc.dms = sc.dms[keep]
+    return sc
 
 
 def config_block(sc, n_gpus):
-    return {"workload": WORKLOAD, "n_ant": sc.n_ant, "n_samp": sc.n_samp, "n_dm": len(sc.dms),
+    full = sc.n_samp == 1 << 22 and len(sc.dms) == 64
+    return {"workload": WORKLOAD if full else "REDUCED (profiling): " + WORKLOAD, "n_ant": sc.n_ant, "n_samp": sc.n_samp, "n_dm": len(sc.dms),
             "dm_max": float(sc.dms.max()), "bw_hz": sc.bw, "f0_hz": sc.f0,
             "nfft_min": sc.nfft_min, "n_pix": int(sc.pix_lm.shape[0]), "dump_len": sc.dump_len,
             "l2": "inputs larger than L2 (voltages 403 MB, forward spectra 2.7 GB)",
@@ -173,7 +185,7 @@ def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return 0
-    sc = scenario(0)
+    sc = scenario(0, args)
     x = sc.voltages()
     n_d = max(4, args.cpu_dumps // 2)
     for _ in range(args.warmup):
@@ -264,7 +276,7 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    sc = scenario(rank)
+    sc = scenario(rank, args)
     x = sc.voltages()
     stream = torch.cuda.current_stream()
     plan = chirp.Plan.from_scenario(sc, beam_mode=args.beam_mode, stream=stream)
