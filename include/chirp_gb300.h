@@ -154,6 +154,32 @@ int chimageator_run(chirp_plan* plan, const void* volt, int volt_loc, float* pow
  * operation: instrumentation for the roofline report.  Errors: CHIRP_EINVAL. */
 int chirp_stage_timing(chirp_plan* plan, int enable, double* ms, long long* launches);
 
+/* Allocation-free dedispersion of one trial DM.  No counterpart in the
+ * paper: it exists for callers that cannot allocate device memory -- code
+ * running while another library holds the stream in capture (allocation is
+ * illegal there), real-time pipelines that reserve all GPU memory at start-up,
+ * and hosts that must avoid the implicit device synchronisation of
+ * cudaMalloc/cudaFree.  It computes exactly what chirp_dedisperse_run computes
+ * for a plan whose DM list is {dm} alone, with every intermediate kept in a
+ * fixed array of CHIRP_NOALLOC_SCRATCH_BYTES that the library holds on every
+ * GPU that loads it, until the process exits.
+ *  volt:  DEVICE complex64 [n_ant][n_samp];  y_out: DEVICE complex64
+ *         [n_ant][n_samp], zero outside the DM's valid range;
+ *  stream: cudaStream_t (NULL = legacy default stream); work is queued on it.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  The first
+ * call on a device looks up the array's device address and fills its twiddle
+ * tables, synchronising the stream: make that first call before any stream
+ * capture.  All calls share the one array and it keeps the previous call's
+ * contents, so calls whose work overlaps on the GPU (other streams, other
+ * threads) race and corrupt each other; serialise them.
+ * Errors: CHIRP_EINVAL (bad argument, or a shape whose scratch need exceeds
+ * CHIRP_NOALLOC_SCRATCH_BYTES, with the need in the message),
+ * CHIRP_EUNSUPPORTED, CHIRP_ECUDA. */
+#define CHIRP_NOALLOC_SCRATCH_BYTES (32u << 20)
+int chirp_dedisperse_noalloc(const void* volt, int n_ant, long long n_samp, double f0_hz,
+                             double bw_hz, double k_dm, double dm, long long nfft_min, void* y_out,
+                             void* stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* chirp_last_error(void);
 

@@ -102,6 +102,9 @@ def load():
         lib.chirp_stage_timing.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ll)]
         lib.chirp_stage_timing.restype = i
+        lib.chirp_dedisperse_noalloc.argtypes = [vp, i, ll, ctypes.c_double, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.c_double, ll, vp, vp]
+        lib.chirp_dedisperse_noalloc.restype = i
         lib.chirp_last_error.argtypes = []
         lib.chirp_last_error.restype = ctypes.c_char_p
         _lib = lib
@@ -169,6 +172,20 @@ def chimageator_run(h, volt, pow_out) -> None:
     vp, vl, _k1 = _buf(volt, np.complex64, "volt")
     op, ol, _k2 = _buf(pow_out, np.float32, "pow_out")
     _check(load().chimageator_run(h, vp, vl, op, ol))
+
+
+def chirp_dedisperse_noalloc(volt, f0: float, bw: float, k_dm: float, dm: float,
+                             nfft_min: int, y_out, stream=None) -> None:
+    """Allocation-free one-DM dedispersion (device buffers only); see the
+    header for who needs it, its scratch limit and its set-up call."""
+    vp, vl, _k1 = _buf(volt, np.complex64, "volt")
+    yp, yl, _k2 = _buf(y_out, np.complex64, "y_out")
+    if vl != CHIRP_DEVICE or yl != CHIRP_DEVICE:
+        raise TypeError("chirp_dedisperse_noalloc takes device buffers only")
+    n_ant, n_samp = volt.shape
+    _check(load().chirp_dedisperse_noalloc(vp, int(n_ant), int(n_samp), float(f0), float(bw),
+                                           float(k_dm), float(dm), int(nfft_min), yp,
+                                           _stream_handle(stream)))
 
 
 def chirp_last_error() -> str:

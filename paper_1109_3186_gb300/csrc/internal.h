@@ -5,6 +5,9 @@
 
 #include <cstddef>
 
+// Records msg as the calling thread's chirp_last_error() and returns code.
+int chirp_report_error(int code, const char* msg);
+
 namespace chirp {
 
 // One FFT-length group: DMs that share Nfft and therefore one block grid.

@@ -75,6 +75,8 @@ struct DmInfo {
 
 }  // namespace
 
+int chirp_report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 struct chirp_plan {
   int M = 0;
   std::vector<double> xyz;
