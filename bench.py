@@ -236,6 +236,9 @@ def stage_roofline(sc, plan, stage_ms, peaks, peak_kind, beam_mode, steps):
         "inv_cols": ("hbm", 8.0 * inv_pts + y_bytes, hbm, "GB/s"),
     }
     beam_flops = float(n_dump_valid) * L * n_pix * (8 * M + 3)
+    # split: read M complex64 + write the BF16 head/tail image (4 antennas per 16 B row pair)
+    split_bytes = float(n_dump_valid) * L * (8 * M + 32 * ((M + 3) // 4))
+    stages["split"] = ("hbm", split_bytes, hbm, "GB/s")
     if beam_mode == 1:
         stages["beamform"] = ("alu", beam_flops, fp32_tflops, "TFLOP/s")
     else:
@@ -305,6 +308,7 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     stage = plan.stage_timing(False)
+    plan.status()
     clk = clocks.stop()
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
@@ -337,13 +341,15 @@ def run_ours(args):
     roof = stage_roofline(sc, plan, stage, peaks, peak_kind, plan.info["beam_mode"], args.steps)
     dom = max(roof, key=lambda k: roof[k]["ms_per_step"]) if roof else None
     n_groups = plan.info["n_group"]
-    launches = args.steps * (2 * n_groups + 3 * n_dm)
+    per_dm = 4 if plan.info["beam_mode"] == 2 else 3
+    launches = args.steps * (2 * n_groups + per_dm * n_dm)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic (seeded sky model: noise + dispersed bursts)",
+                "dtype": "f32" if plan.info["beam_mode"] == 1 else "f32 (beams: 3xbf16 tensor, f32 acc)",
+                "data": "synthetic (seeded sky model: noise + dispersed bursts)",
                 "config": config_block(sc, world),
                 "beam_dm_dumps_per_s": world * beam_dumps / (ms * 1e-3),
                 "gpu_launches": launches, "clocks": clk}

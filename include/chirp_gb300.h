@@ -51,6 +51,7 @@ extern "C" {
 #define CHIRP_EINVAL (-1)      /* bad argument or size                     */
 #define CHIRP_ENOMEM (-2)      /* device or host allocation failed          */
 #define CHIRP_ECUDA (-3)       /* a CUDA runtime call or launch failed      */
+#define CHIRP_ETIMEOUT (-4)    /* a bounded device wait gave up              */
 #define CHIRP_EUNSUPPORTED (-5)/* valid request this build does not handle  */
 
 /* where a caller buffer lives */
@@ -135,8 +136,11 @@ int chirpolator_run(chirp_plan* plan, const void* volt, int volt_loc, void* vis_
  * pixel, P = sum_t |sum_a W_pa y_a(t)|^2 with narrowband weights
  * W_pa = exp(+2 pi j f0 tau_a(l_p, m_p)), tau from Eq. tau3D (direct
  * beamforming, Sec. 2.4.2, detected and integrated).  pow_out: float32
- * [n_dm][n_dump][n_pix].  Needs n_pix > 0 at plan creation.  Errors:
- * CHIRP_EINVAL, CHIRP_EUNSUPPORTED, CHIRP_ECUDA. */
+ * [n_dm][n_dump][n_pix].  Needs n_pix > 0 at plan creation.  With the
+ * tensor-core mode the contraction runs as three BF16 products (head x head,
+ * head x tail, tail x head) accumulated in FP32.  Errors: CHIRP_EINVAL,
+ * CHIRP_EUNSUPPORTED, CHIRP_ECUDA, CHIRP_ETIMEOUT (host outputs only; see
+ * chirp_plan_status). */
 int chimageator_run(chirp_plan* plan, const void* volt, int volt_loc, float* pow_out, int pow_loc);
 
 /* Per-stage device time.  Stages: */
@@ -145,7 +149,8 @@ int chimageator_run(chirp_plan* plan, const void* volt, int volt_loc, float* pow
 #define CHIRP_STAGE_INV_COLS 2  /* inverse column pass + discard, per DM        */
 #define CHIRP_STAGE_CORRELATE 3 /* Chirpolator back-end, per DM                 */
 #define CHIRP_STAGE_BEAMFORM 4  /* Chimageator back-end, per DM                 */
-#define CHIRP_N_STAGES 5
+#define CHIRP_STAGE_SPLIT 5     /* BF16 head/tail split of the voltages, per DM */
+#define CHIRP_N_STAGES 6
 /* Returns the milliseconds and launch counts accumulated per stage since the
  * previous call (ms, launches: host arrays of CHIRP_N_STAGES, either may be
  * NULL), resets them, and switches event timing on (enable != 0) or off for
@@ -179,6 +184,13 @@ int chirp_stage_timing(chirp_plan* plan, int enable, double* ms, long long* laun
 int chirp_dedisperse_noalloc(const void* volt, int n_ant, long long n_samp, double f0_hz,
                              double bw_hz, double k_dm, double dm, long long nfft_min, void* y_out,
                              void* stream);
+
+/* Synchronises the plan's stream and reports whether any bounded device wait
+ * of an earlier run gave up (the tensor-core beamformer never spins without
+ * a limit).  Returns CHIRP_OK, or CHIRP_ETIMEOUT when outputs of some run are
+ * invalid; the flag stays raised for the plan's lifetime.  Host-output runs
+ * of chimageator_run check it themselves.  Errors: CHIRP_EINVAL, CHIRP_ECUDA. */
+int chirp_plan_status(chirp_plan* plan);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* chirp_last_error(void);

@@ -37,8 +37,8 @@ K_DM_DEFAULT = 4.148808e15
 EXPORTED_SYMBOLS = ("chirp_plan_create", "chirp_plan_destroy", "chirp_plan_query",
                     "chirp_dm_layout", "chirp_dump_range", "chirp_dedisperse_run",
                     "chirpolator_run", "chimageator_run", "chirp_stage_timing",
-                    "chirp_last_error")
-STAGES = ("forward", "inv_rows", "inv_cols", "correlate", "beamform")
+                    "chirp_plan_status", "chirp_last_error")
+STAGES = ("forward", "inv_rows", "inv_cols", "correlate", "beamform", "split")
 
 
 class ChirpError(RuntimeError):
@@ -102,6 +102,8 @@ def load():
         lib.chirp_stage_timing.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ll)]
         lib.chirp_stage_timing.restype = i
+        lib.chirp_plan_status.argtypes = [vp]
+        lib.chirp_plan_status.restype = i
         lib.chirp_dedisperse_noalloc.argtypes = [vp, i, ll, ctypes.c_double, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_double, ll, vp, vp]
         lib.chirp_dedisperse_noalloc.restype = i
@@ -265,6 +267,10 @@ class Plan:
     def chimageator(self, volt, pow_out):
         chimageator_run(self._h, volt, pow_out)
         return pow_out
+
+    def status(self):
+        """Raise ChirpError if a bounded device wait of an earlier run gave up."""
+        _check(load().chirp_plan_status(self._h))
 
     def stage_timing(self, enable: bool):
         """Per-stage device ms and launch counts since the last call; switches

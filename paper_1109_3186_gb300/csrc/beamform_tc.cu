@@ -1,0 +1,433 @@
+// beamform_tc.cu -- Chimageator back-end on the tcgen05 tensor cores.
+//
+// Direct beamforming (Sec. 2.4.2) of the dedispersed voltages with
+// narrowband weights W_pa = exp(+2 pi j f0 tau_a) (Eq. tau3D), detected and
+// integrated per dump:  P[m][p] = sum_{t in dump m} |sum_a W_pa y_a(t)|^2.
+//
+// Complex GEMM in real-block form: row 2p gives Re b_p, row 2p+1 gives Im b_p,
+//   A[2p  ][2a] =  Re W,  A[2p  ][2a+1] = -Im W,
+//   A[2p+1][2a] =  Im W,  A[2p+1][2a+1] =  Re W,    B[2a + c][t] = (Re, Im)_c y_a(t),
+// so D = A B holds the beams and P sums D^2 over both rows of a pixel.
+//
+// FP32 accuracy from BF16 tensor cores: every operand is split into a BF16
+// head and a BF16 tail (x = x_h + x_l + O(2^-16 x)) and
+//   D = A_h B_h + A_h B_l + A_l B_h    (A_l B_l is O(2^-16) and dropped).
+// The three products are packed into ONE contraction: the K axis of the MMA
+// walks [B_h | B_l | B_h] against [A_h | A_h | A_l], and because B_h and B_l
+// sit next to each other in shared memory every 16-wide K step reads two
+// adjacent 8-wide core-matrix columns.  For 12 antennas (24 real K) that is
+// 72 useful of 80 MMA K (5 steps).
+//
+// Layouts (no swizzle, K-major, 8-row x 16-byte core matrices):
+//   A image per 128-row tile: [m-group 16][k-slot 2*ksteps][8 rows][8 bf16]
+//   B tile of NT = 128 samples: [n-group 16][k-group 2G][8 samples][8 bf16]
+//     k-group g < G: heads of real K 8g..8g+7; g >= G: tails of 8(g-G)...
+//     real K index k = 2a + c (antenna a, c = 0 real / 1 imaginary).
+// Both images are written in global memory in exactly this order so that one
+// cp.async.bulk moves a whole tile.
+//
+// Kernel roles (192 threads): warp 0 lane 0 streams B tiles (bulk copies into
+// a 4-stage ring); warp 1 owns TMEM (512 columns = 4 accumulators of 128) and
+// its lane 0 issues the MMAs; warps 2-5 drain accumulators (tcgen05.ld), square
+// and integrate per dump, and write whole-dump powers.  Every wait is bounded;
+// on a timeout the kernel raises *err, drains its own copies and MMAs, frees
+// TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "tc.cuh"
+
+namespace chirp {
+
+namespace {
+
+constexpr int NT = 128;        // samples per B tile = MMA N
+constexpr int NSTAGE = 4;      // B ring depth
+constexpr int NACC = 4;        // TMEM accumulators of NT columns
+constexpr int RMAX = 4;        // row tiles per CTA
+constexpr int THREADS = 192;
+constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, NT);
+
+struct BeamSmemPlan {
+  uint32_t a_bytes, b_stage_bytes, bar_off, total;
+};
+
+__host__ __device__ inline BeamSmemPlan beam_smem_plan(int R, int ksteps, int G) {
+  BeamSmemPlan s;
+  s.a_bytes = (uint32_t)R * ksteps * 4096u;
+  s.b_stage_bytes = (uint32_t)NT * 2u * G * 16u;
+  s.bar_off = s.a_bytes + NSTAGE * s.b_stage_bytes;
+  s.total = s.bar_off + 256;
+  return s;
+}
+
+struct BeamArgs {
+  const uint8_t* b_img;
+  const uint8_t* a_img;
+  float* pow;          // this DM: [n_dump][n_pix]
+  int* err;
+  long long t_begin;   // sample of column 0 of tile 0
+  long long first;     // first valid dump
+  long long n_dumps;   // valid dumps of this DM
+  long long dumps_per_cta;
+  int L, n_pix, n_rowtiles, R, G, ksteps;
+};
+
+__global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const BeamSmemPlan sp = beam_smem_plan(args.R, args.ksteps, args.G);
+  uint8_t* smA = smem;
+  uint8_t* smB = smem + sp.a_bytes;
+  uint64_t* bars = (uint64_t*)(smem + sp.bar_off);
+  uint64_t* full = bars;                 // [NSTAGE]
+  uint64_t* empty = bars + NSTAGE;       // [NSTAGE]
+  uint64_t* accf = bars + 2 * NSTAGE;    // [NACC]
+  uint64_t* acce = accf + NACC;          // [NACC]
+  uint64_t* abar = acce + NACC;          // A images
+  uint64_t* drain = abar + 1;            // teardown of the MMA queue
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int rt0 = blockIdx.x * args.R;
+  const int R_eff = min(args.R, args.n_rowtiles - rt0);
+  // dumps of this CTA: [m_a, m_b) ; samples [ta, tb)
+  const long long m_a = args.first + (long long)blockIdx.y * args.dumps_per_cta;
+  const long long m_b = min(m_a + args.dumps_per_cta, args.first + args.n_dumps);
+  const long long ta = m_a * args.L, tb = m_b * args.L;
+  const long long j_a = (ta - args.t_begin) / NT;
+  const long long j_b = (tb - args.t_begin + NT - 1) / NT;
+  const long long n_tiles = (m_b > m_a && R_eff > 0) ? j_b - j_a : 0;
+  const uint32_t a_tile_bytes = (uint32_t)args.ksteps * 4096u;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; s++) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < NACC; a++) {
+      tc::mbar_init(&accf[a], 1);
+      tc::mbar_init(&acce[a], 4);
+    }
+    tc::mbar_init(abar, 1);
+    tc::mbar_init(drain, 1);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, 512);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto raise = [&]() {
+    *abort_flag = 1;
+    atomicExch(args.err, 1);
+  };
+
+  if (n_tiles > 0) {
+    if (warp == 0 && lane == 0) {
+      // ------------------------------------------------------ producer
+      tc::mbar_arrive_expect_tx(abar, (uint32_t)R_eff * a_tile_bytes);
+      for (int r = 0; r < R_eff; r++)
+        tc::bulk_g2s(smA + r * a_tile_bytes, args.a_img + (size_t)(rt0 + r) * a_tile_bytes,
+                     a_tile_bytes, abar);
+      long long issued = 0;
+      for (long long i = 0; i < n_tiles; i++) {
+        const int s = (int)(i % NSTAGE);
+        const uint32_t ph = (uint32_t)((i / NSTAGE) & 1);
+        if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
+          raise();
+          break;
+        }
+        tc::mbar_arrive_expect_tx(&full[s], sp.b_stage_bytes);
+        tc::bulk_g2s(smB + (size_t)s * sp.b_stage_bytes,
+                     args.b_img + (size_t)(j_a + i) * sp.b_stage_bytes, sp.b_stage_bytes,
+                     &full[s]);
+        issued = i + 1;
+      }
+      if (*abort_flag) {
+        // let every copy this thread issued land before the CTA goes away
+        tc::mbar_wait(abar, 0, nullptr, 1u << 22);
+        for (long long i = issued > NSTAGE ? issued - NSTAGE : 0; i < issued; i++)
+          tc::mbar_wait(&full[i % NSTAGE], (uint32_t)((i / NSTAGE) & 1), nullptr, 1u << 22);
+      }
+    } else if (warp == 1 && lane == 0) {
+      // ------------------------------------------------------ MMA issuer
+      const uint32_t a_base = tc::smem_u32(smA), b_base = tc::smem_u32(smB);
+      const uint32_t a_sbo = 2u * args.ksteps * 128u, b_sbo = 2u * args.G * 128u;
+      bool ok = tc::mbar_wait(abar, 0, abort_flag);
+      if (!ok) raise();
+      long long u = 0;
+      for (long long i = 0; ok && i < n_tiles; i++) {
+        const int s = (int)(i % NSTAGE);
+        const uint32_t ph = (uint32_t)((i / NSTAGE) & 1);
+        if (!tc::mbar_wait(&full[s], ph, abort_flag)) {
+          raise();
+          break;
+        }
+        tc::fence_after();
+        for (int r = 0; r < R_eff; r++, u++) {
+          const int acc = (int)(u % NACC);
+          const uint32_t aph = (uint32_t)((u / NACC) & 1);
+          if (!tc::mbar_wait(&acce[acc], aph ^ 1, abort_flag)) {
+            raise();
+            ok = false;
+            break;
+          }
+          tc::fence_after();
+          const uint32_t d = tmem + (uint32_t)(acc * NT);
+          for (int ks = 0; ks < args.ksteps; ks++) {
+            const int p0 = 2 * ks;
+            const int bg = p0 < 2 * args.G ? p0 : p0 - 2 * args.G;
+            const uint64_t ad = tc::sdesc(a_base + r * a_tile_bytes + ks * 256u, 128u, a_sbo);
+            const uint64_t bd =
+                tc::sdesc(b_base + s * sp.b_stage_bytes + bg * 128u, 128u, b_sbo);
+            tc::mma_bf16(d, ad, bd, IDESC, ks > 0 ? 1u : 0u);
+          }
+          tc::mma_commit(&accf[acc]);
+        }
+        if (!ok) break;
+        tc::mma_commit(&empty[s]);
+      }
+      // nothing may be in flight when TMEM is released
+      tc::mma_commit(drain);
+      tc::mbar_wait(drain, 0, nullptr, 1u << 22);
+    } else if (warp >= 2) {
+      // ------------------------------------------------------ epilogue
+      const int q = warp & 3;               // TMEM lane quarter of this warp
+      const int row = 32 * q + lane;        // row inside a 128-row tile
+      float sum[RMAX];
+      long long next_b[RMAX];
+#pragma unroll
+      for (int r = 0; r < RMAX; r++) {
+        sum[r] = 0.f;
+        next_b[r] = ta + args.L;
+      }
+      auto flush = [&](int r, long long m) {
+        const float other = __shfl_xor_sync(0xffffffffu, sum[r], 1);
+        const int p = ((rt0 + r) * 128 + row) >> 1;
+        if (!(lane & 1) && p < args.n_pix) args.pow[m * args.n_pix + p] = sum[r] + other;
+        sum[r] = 0.f;
+      };
+      long long u = 0;
+      bool ok = true;
+      for (long long i = 0; ok && i < n_tiles; i++) {
+        const long long t0 = args.t_begin + (j_a + i) * NT;
+        const long long tA = t0 > ta ? t0 : ta;
+        const long long tB = (t0 + NT) < tb ? (t0 + NT) : tb;
+#pragma unroll
+        for (int r = 0; r < RMAX; r++) {
+          if (r >= R_eff) break;
+          const int acc = (int)(u % NACC);
+          const uint32_t aph = (uint32_t)((u / NACC) & 1);
+          u++;
+          if (!tc::mbar_wait(&accf[acc], aph, abort_flag)) {
+            raise();
+            ok = false;
+            break;
+          }
+          tc::fence_after();
+#pragma unroll 1
+          for (int c4 = 0; c4 < NT / 32; c4++) {
+            const long long cs = t0 + 32 * c4, ce = cs + 32;
+            if (ce <= tA || cs >= tB) continue;  // warp-uniform
+            float v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * NT + 32 * c4), v);
+            if (cs >= tA && ce <= tB && ce <= next_b[r]) {
+              float part = 0.f;
+#pragma unroll
+              for (int e = 0; e < 32; e++) part = fmaf(v[e], v[e], part);
+              sum[r] += part;
+              if (ce == next_b[r]) {
+                flush(r, next_b[r] / args.L - 1);
+                next_b[r] += args.L;
+              }
+            } else {
+              float part = 0.f;
+              for (int e = 0; e < 32; e++) {
+                const long long t = cs + e;
+                if (t < tA || t >= tB) continue;
+                part = fmaf(v[e], v[e], part);
+                if (t + 1 == next_b[r]) {
+                  sum[r] += part;
+                  part = 0.f;
+                  flush(r, next_b[r] / args.L - 1);
+                  next_b[r] += args.L;
+                }
+              }
+              sum[r] += part;
+            }
+          }
+          tc::fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&acce[acc]);
+        }
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after();
+    tc::tmem_dealloc(tmem, 512);
+  }
+}
+
+// y [n_ant][n_samp] complex64 -> B image tiles (BF16 heads and tails).
+// Thread (u, j): sample t = t_begin + u, real-K group j (antennas 4j..4j+3).
+__global__ void k_split_bf16(const float2* __restrict__ y, long long n_samp, int M, int G,
+                             long long t_begin, long long t_end, long long n_tiles,
+                             uint8_t* __restrict__ b_img) {
+  const long long U = n_tiles * NT;
+  const long long total = U * G;
+  const size_t tile_bytes = (size_t)NT * 2 * G * 16;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / U);
+    const long long u = idx % U;
+    const long long t = t_begin + u;
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const int a = 4 * j + e;
+      float2 s = make_float2(0.f, 0.f);
+      if (a < M && t < t_end) s = y[(long long)a * n_samp + t];
+      v[2 * e] = s.x;
+      v[2 * e + 1] = s.y;
+    }
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+      float2 hf = __bfloat1622float2(h);
+      __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
+      hi[e] = *reinterpret_cast<uint32_t*>(&h);
+      lo[e] = *reinterpret_cast<uint32_t*>(&l);
+    }
+    const long long tile = u / NT;
+    const int n = (int)(u % NT);
+    uint8_t* base = b_img + (size_t)tile * tile_bytes + (size_t)(n / 8) * (2 * G * 128) +
+                    (size_t)(n % 8) * 16;
+    *reinterpret_cast<uint4*>(base + (size_t)j * 128) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4*>(base + (size_t)(G + j) * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  }
+}
+
+uint16_t bf16_bits_rn(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);  // round to nearest even (finite inputs)
+  return (uint16_t)(u >> 16);
+}
+float bf16_to_float(uint16_t h) {
+  uint32_t u = (uint32_t)h << 16;
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+}
+
+}  // namespace
+
+// A image (see the layout notes at the top) from FP64 weights W [n_pix][n_ant]
+// given as interleaved (re, im).  Rows past 2 n_pix and antennas past n_ant
+// are zero, as is the padding k-slot.
+std::vector<uint8_t> build_beam_a_image(const double* W, int n_ant, int n_pix) {
+  const int G = beam_tc_groups(n_ant), ks = beam_tc_ksteps(n_ant);
+  const int n_rowtiles = (2 * n_pix + 127) / 128;
+  const size_t tile_bytes = (size_t)ks * 4096;
+  std::vector<uint8_t> img((size_t)n_rowtiles * tile_bytes, 0);
+  for (int rt = 0; rt < n_rowtiles; rt++)
+    for (int mg = 0; mg < 16; mg++)
+      for (int slot = 0; slot < 2 * ks; slot++) {
+        int part, j;  // part 0 head, 1 tail, 2 zero
+        if (slot < G) { part = 0; j = slot; }
+        else if (slot < 2 * G) { part = 0; j = slot - G; }
+        else if (slot < 3 * G) { part = 1; j = slot - 2 * G; }
+        else { part = 2; j = 0; }
+        for (int r8 = 0; r8 < 8; r8++) {
+          const int row = rt * 128 + mg * 8 + r8;
+          const int p = row / 2, ri = row % 2;
+          for (int e = 0; e < 8; e++) {
+            const int k = 8 * j + e, a = k / 2, comp = k % 2;
+            double v = 0.0;
+            if (part != 2 && p < n_pix && a < n_ant) {
+              const double wr = W[2 * ((size_t)p * n_ant + a)], wi = W[2 * ((size_t)p * n_ant + a) + 1];
+              v = ri == 0 ? (comp == 0 ? wr : -wi) : (comp == 0 ? wi : wr);
+            }
+            const uint16_t h = bf16_bits_rn((float)v);
+            const uint16_t bits = part == 0 ? h : bf16_bits_rn((float)(v - (double)bf16_to_float(h)));
+            const size_t off = (size_t)rt * tile_bytes + (size_t)mg * (2 * ks * 128) +
+                               (size_t)slot * 128 + (size_t)r8 * 16 + (size_t)e * 2;
+            memcpy(&img[off], &bits, 2);
+          }
+        }
+      }
+  return img;
+}
+
+int beam_tc_groups(int n_ant) { return (n_ant + 3) / 4; }
+int beam_tc_ksteps(int n_ant) { return (3 * beam_tc_groups(n_ant) + 1) / 2; }
+long long beam_tc_tile_bytes(int n_ant) { return (long long)NT * 2 * beam_tc_groups(n_ant) * 16; }
+int beam_tc_tile_samples() { return NT; }
+
+cudaError_t launch_split_bf16(const float2* y, long long n_samp, int n_ant, long long t_begin,
+                              long long t_end, uint8_t* b_img, cudaStream_t st) {
+  if (t_end <= t_begin) return cudaSuccess;
+  const int G = beam_tc_groups(n_ant);
+  const long long n_tiles = (t_end - t_begin + NT - 1) / NT;
+  const long long total = n_tiles * NT * G;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_split_bf16<<<(unsigned)blocks, 256, 0, st>>>(y, n_samp, n_ant, G, t_begin, t_end, n_tiles,
+                                                 b_img);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_beam_tc(const uint8_t* b_img, const uint8_t* a_img, int n_ant, int n_pix,
+                           int dump_len, long long first, long long last, float* pow, int* err,
+                           cudaStream_t st) {
+  if (last < first) return cudaSuccess;
+  const int G = beam_tc_groups(n_ant), ks = beam_tc_ksteps(n_ant);
+  const int n_rowtiles = (2 * n_pix + 127) / 128;
+  int R = RMAX;
+  if (R > n_rowtiles) R = n_rowtiles;
+  while (R > 1 && beam_smem_plan(R, ks, G).total > 220 * 1024) R--;
+  const BeamSmemPlan sp = beam_smem_plan(R, ks, G);
+  if (sp.total > 227 * 1024) return cudaErrorInvalidConfiguration;
+  // at least 116 KB so that a second CTA never shares the SM (and its TMEM)
+  const uint32_t smem_bytes = sp.total > 116 * 1024 ? sp.total : 116 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_beam_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes);
+  if (e != cudaSuccess) return e;
+  const int gx = (n_rowtiles + R - 1) / R;
+  const long long n_dumps = last - first + 1;
+  long long gy = (152 + gx - 1) / gx;  // about one CTA per SM
+  if (gy > n_dumps) gy = n_dumps;
+  if (gy < 1) gy = 1;
+  BeamArgs a;
+  a.b_img = b_img;
+  a.a_img = a_img;
+  a.pow = pow;
+  a.err = err;
+  a.t_begin = first * dump_len;
+  a.first = first;
+  a.n_dumps = n_dumps;
+  a.dumps_per_cta = (n_dumps + gy - 1) / gy;
+  gy = (n_dumps + a.dumps_per_cta - 1) / a.dumps_per_cta;
+  a.L = dump_len;
+  a.n_pix = n_pix;
+  a.n_rowtiles = n_rowtiles;
+  a.R = R;
+  a.G = G;
+  a.ksteps = ks;
+  k_beam_tc<<<dim3(gx, (unsigned)gy), THREADS, smem_bytes, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace chirp

@@ -99,6 +99,9 @@ struct chirp_plan {
   float2* d_Z = nullptr;     // inverse-row intermediate, largest group
   float2* d_y = nullptr;     // dedispersed voltages of one DM [M][N]
   float2* d_W = nullptr;     // beam weights [n_pix][M]
+  uint8_t* d_aimg = nullptr; // tensor-core A image (split-BF16 weights)
+  uint8_t* d_bimg = nullptr; // tensor-core B image of one DM (split-BF16 voltages)
+  int* d_err = nullptr;      // device status word (bounded waits that timed out)
   void* d_out = nullptr;     // staging for host outputs
   size_t out_bytes = 0;
   size_t ws_bytes = 0;
@@ -141,6 +144,9 @@ void release(chirp_plan* p) {
   cudaFree(p->d_Z);
   cudaFree(p->d_y);
   cudaFree(p->d_W);
+  cudaFree(p->d_aimg);
+  cudaFree(p->d_bimg);
+  cudaFree(p->d_err);
   cudaFree(p->d_out);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
 }
@@ -248,12 +254,8 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   p->nfft_min = cfg->nfft_min;
   if (cfg->n_pix > 0) p->pix.assign(cfg->pix_lm, cfg->pix_lm + 2 * cfg->n_pix);
   p->n_pix = cfg->n_pix;
-  // the tensor-core beamformer is not built yet: AUTO resolves to FP32 SIMT
-  p->beam_mode = cfg->beam_mode == CHIRP_BEAM_AUTO ? CHIRP_BEAM_FP32_SIMT : cfg->beam_mode;
-  if (p->beam_mode == CHIRP_BEAM_TC_3XBF16) {
-    delete p;
-    return fail(CHIRP_EUNSUPPORTED, "tensor-core beam mode is not available in this build");
-  }
+  // AUTO: tensor cores (split BF16, FP32 accumulate) for the beam GEMM
+  p->beam_mode = cfg->beam_mode == CHIRP_BEAM_AUTO ? CHIRP_BEAM_TC_3XBF16 : cfg->beam_mode;
   p->stream = (cudaStream_t)stream;
   p->n_dump = p->N / p->L;
   p->n_pair = p->M * (p->M + 1) / 2;
@@ -342,6 +344,35 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   if (!rc) rc = dev_alloc(p, (void**)&p->d_y, (size_t)p->M * p->N * sizeof(float2), "voltages");
   if (!rc && p->n_pix > 0)
     rc = dev_alloc(p, (void**)&p->d_W, (size_t)p->n_pix * p->M * sizeof(float2), "weights");
+  if (!rc) rc = dev_alloc(p, (void**)&p->d_err, sizeof(int), "status word");
+  std::vector<uint8_t> aimg;
+  if (!rc && p->n_pix > 0 && p->beam_mode == CHIRP_BEAM_TC_3XBF16) {
+    long long max_tiles = 0;
+    for (const DmInfo& I : p->dmi)
+      if (I.last >= I.first) {
+        long long span = (I.last - I.first + 1) * p->L;
+        long long nt = (span + beam_tc_tile_samples() - 1) / beam_tc_tile_samples();
+        max_tiles = std::max(max_tiles, nt);
+      }
+    rc = dev_alloc(p, (void**)&p->d_bimg, (size_t)std::max(1LL, max_tiles) *
+                                              (size_t)beam_tc_tile_bytes(p->M), "beam B image");
+    if (!rc) {
+      std::vector<double> Wd((size_t)p->n_pix * p->M * 2);
+      for (int q = 0; q < p->n_pix; q++) {
+        double l = p->pix[2 * q], m = p->pix[2 * q + 1];
+        double n = std::sqrt(1.0 - l * l - m * m);
+        for (int a = 0; a < p->M; a++) {
+          double tau = (p->xyz[3 * a] * l + p->xyz[3 * a + 1] * m + p->xyz[3 * a + 2] * (n - 1.0)) /
+                       kCLight;
+          double ph = 2.0 * kPi * p->f0 * tau;
+          Wd[2 * ((size_t)q * p->M + a)] = std::cos(ph);
+          Wd[2 * ((size_t)q * p->M + a) + 1] = std::sin(ph);
+        }
+      }
+      aimg = build_beam_a_image(Wd.data(), p->M, p->n_pix);
+      rc = dev_alloc(p, (void**)&p->d_aimg, aimg.size(), "beam A image");
+    }
+  }
   if (rc) {
     release(p);
     delete p;
@@ -373,6 +404,9 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   if (e == cudaSuccess && p->n_pix > 0)
     e = cudaMemcpyAsync(p->d_W, W.data(), W.size() * sizeof(float2), cudaMemcpyHostToDevice,
                         p->stream);
+  if (e == cudaSuccess && !aimg.empty())
+    e = cudaMemcpyAsync(p->d_aimg, aimg.data(), aimg.size(), cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
   for (auto& g : p->groups)
     if (e == cudaSuccess)
       e = launch_build_phase_table(g.d_G, g.geom, p->f0, p->bw, p->kdm, p->stream);
@@ -560,16 +594,46 @@ int chimageator_run(chirp_plan* p, const void* volt, int volt_loc, float* pow_ou
   if (rc) return rc;
   rc = forward_all(p, dx);
   if (rc) return rc;
+  const bool tcore = p->beam_mode == CHIRP_BEAM_TC_3XBF16;
+  // invalid dumps stay zero; the tensor-core kernel writes only valid ones
+  if (tcore) CK(cudaMemsetAsync(dp, 0, bytes, p->stream));
   for (int d = 0; d < (int)p->dm.size(); d++) {
     rc = dedisperse_one(p, d, p->d_y);
     if (rc) return rc;
     const DmInfo& I = p->dmi[d];
-    int mk = mark_begin(p);
-    CK(launch_beamform_simt(p->d_y, p->N, p->M, p->L, p->n_dump, I.first, I.last, p->d_W,
-                            p->n_pix, (float*)dp + d * per_dm, p->stream));
-    mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
+    float* out = (float*)dp + d * per_dm;
+    if (tcore) {
+      if (I.last < I.first) continue;
+      int mk = mark_begin(p);
+      CK(launch_split_bf16(p->d_y, p->N, p->M, I.first * p->L, (I.last + 1) * p->L, p->d_bimg,
+                           p->stream));
+      mark_end(p, CHIRP_STAGE_SPLIT, mk);
+      mk = mark_begin(p);
+      CK(launch_beam_tc(p->d_bimg, p->d_aimg, p->M, p->n_pix, p->L, I.first, I.last, out,
+                        p->d_err, p->stream));
+      mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
+    } else {
+      int mk = mark_begin(p);
+      CK(launch_beamform_simt(p->d_y, p->N, p->M, p->L, p->n_dump, I.first, I.last, p->d_W,
+                              p->n_pix, out, p->stream));
+      mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
+    }
   }
-  return finish_out(p, pow_out, pow_loc, dp, bytes);
+  if (pow_loc == CHIRP_HOST) {
+    rc = finish_out(p, pow_out, pow_loc, dp, bytes);
+    if (rc) return rc;
+    return chirp_plan_status(p);
+  }
+  return CHIRP_OK;
+}
+
+int chirp_plan_status(chirp_plan* p) {
+  if (!p) return fail(CHIRP_EINVAL, "plan is NULL");
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  if (flag) return fail(CHIRP_ETIMEOUT, "a device wait timed out; outputs of the affected runs are invalid");
+  return CHIRP_OK;
 }
 
 }  // extern "C"

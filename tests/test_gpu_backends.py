@@ -36,24 +36,35 @@ def test_chirpolator_matches_oracle(M, N, L, dms, nfft_min, k_dm):
     assert vis_error(Vg, Vo, M) < TOL_VIS
 
 
-@pytest.mark.parametrize("M,N,L,n_side,dms,nfft_min", [
+BEAM_CASES = [
     (12, 1 << 17, 4096, 8, [0.0, 30.0, 60.0], 1 << 15),
-    (5, 50000, 1000, 3, [0.0, 12.0], 1 << 13),
+    (5, 50000, 1000, 3, [0.0, 12.0], 1 << 13),        # 9 pixels: one padded row tile
     (3, 1 << 14, 512, 1, [7.0], 1 << 12),
-])
-def test_chimageator_simt_matches_oracle(M, N, L, n_side, dms, nfft_min, k_dm):
+    (13, 70000, 777, 12, [0.0, 20.0], 1 << 14),       # dumps straddle 128-sample tiles
+    (12, 1 << 18, 4096, 32, [0.0, 150.0, 300.0], 1 << 17),   # 1024 beams, all row tiles
+]
+
+
+@pytest.mark.parametrize("mode", [chirp.BEAM_FP32_SIMT, chirp.BEAM_TC_3XBF16],
+                         ids=["fp32_simt", "tc_3xbf16"])
+@pytest.mark.parametrize("M,N,L,n_side,dms,nfft_min", BEAM_CASES,
+                         ids=["M%d_N%d_L%d_pix%d" % (c[0], c[1], c[2], c[3] ** 2) for c in BEAM_CASES])
+def test_chimageator_matches_oracle(M, N, L, n_side, dms, nfft_min, mode, k_dm):
     sc = skymodel.chimageator_medium(n_samp=N, n_dm=len(dms), n_ant=M, dm_max=max(dms),
                                      nfft_min=nfft_min, dump_len=L, n_side=n_side, n_pulse=1)
     sc.dms = np.array(dms)
     x = sc.voltages()
-    plan = chirp.Plan.from_scenario(sc, beam_mode=chirp.BEAM_FP32_SIMT)
+    plan = chirp.Plan.from_scenario(sc, beam_mode=mode)
+    assert plan.info["beam_mode"] == mode
     P = torch.empty((len(dms), plan.n_dump, plan.n_pix), dtype=torch.float32, device="cuda")
     plan.chimageator(torch.from_numpy(x).cuda(), P)
     Pg = P.cpu().numpy()
     Po = orc.chimageator(x, sc.f0, sc.bw, k_dm, sc.dms, nfft_min, L, sc.xyz, sc.pix_lm)
+    plan.status()
     first, last = plan.dump_range()
     for d in range(len(dms)):
         assert np.all(Pg[d, :first[d]] == 0) and np.all(Pg[d, last[d] + 1:] == 0)
+        assert np.all(Pg[d, first[d]:last[d] + 1] > 0)
     assert pow_error(Pg, Po) < TOL_POW
 
 
