@@ -232,6 +232,7 @@ def stage_roofline(sc, plan, stage_ms, peaks, peak_kind, beam_mode, steps):
     fp32_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     stages = {
         "forward": ("hbm", 32.0 * fwd_pts, hbm, "GB/s"),
+        "chirp": ("hbm", 2.0 * g_bytes, hbm, "GB/s"),
         "inv_rows": ("hbm", 16.0 * inv_pts + g_bytes, hbm, "GB/s"),
         "inv_cols": ("hbm", 8.0 * inv_pts + y_bytes, hbm, "GB/s"),
     }
@@ -341,7 +342,7 @@ def run_ours(args):
     roof = stage_roofline(sc, plan, stage, peaks, peak_kind, plan.info["beam_mode"], args.steps)
     dom = max(roof, key=lambda k: roof[k]["ms_per_step"]) if roof else None
     n_groups = plan.info["n_group"]
-    per_dm = 4 if plan.info["beam_mode"] == 2 else 3
+    per_dm = 5 if plan.info["beam_mode"] == 2 else 4
     launches = args.steps * (2 * n_groups + per_dm * n_dm)
 
     if rank == 0:

@@ -150,7 +150,8 @@ int chimageator_run(chirp_plan* plan, const void* volt, int volt_loc, float* pow
 #define CHIRP_STAGE_CORRELATE 3 /* Chirpolator back-end, per DM                 */
 #define CHIRP_STAGE_BEAMFORM 4  /* Chimageator back-end, per DM                 */
 #define CHIRP_STAGE_SPLIT 5     /* BF16 head/tail split of the voltages, per DM */
-#define CHIRP_N_STAGES 6
+#define CHIRP_STAGE_CHIRP 6     /* FP64-phase chirp table H_DM, per DM           */
+#define CHIRP_N_STAGES 7
 /* Returns the milliseconds and launch counts accumulated per stage since the
  * previous call (ms, launches: host arrays of CHIRP_N_STAGES, either may be
  * NULL), resets them, and switches event timing on (enable != 0) or off for

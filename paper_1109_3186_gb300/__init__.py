@@ -38,7 +38,7 @@ EXPORTED_SYMBOLS = ("chirp_plan_create", "chirp_plan_destroy", "chirp_plan_query
                     "chirp_dm_layout", "chirp_dump_range", "chirp_dedisperse_run",
                     "chirpolator_run", "chimageator_run", "chirp_stage_timing",
                     "chirp_plan_status", "chirp_last_error")
-STAGES = ("forward", "inv_rows", "inv_cols", "correlate", "beamform", "split")
+STAGES = ("forward", "inv_rows", "inv_cols", "correlate", "beamform", "split", "chirp")
 
 
 class ChirpError(RuntimeError):

@@ -26,9 +26,10 @@
 // Both images are written in global memory in exactly this order so that one
 // cp.async.bulk moves a whole tile.
 //
-// Kernel roles (192 threads): warp 0 lane 0 streams B tiles (bulk copies into
+// Kernel roles (320 threads): warp 0 lane 0 streams B tiles (bulk copies into
 // a 4-stage ring); warp 1 owns TMEM (512 columns = 4 accumulators of 128) and
-// its lane 0 issues the MMAs; warps 2-5 drain accumulators (tcgen05.ld), square
+// its lane 0 issues the MMAs; warps 2-9 form two warpgroups that drain the
+// accumulators of even / odd row tiles (one 128-column tcgen05.ld each), square
 // and integrate per dump, and write whole-dump powers.  Every wait is bounded;
 // on a timeout the kernel raises *err, drains its own copies and MMAs, frees
 // TMEM and returns.
@@ -50,7 +51,8 @@ constexpr int NT = 128;        // samples per B tile = MMA N
 constexpr int NSTAGE = 4;      // B ring depth
 constexpr int NACC = 4;        // TMEM accumulators of NT columns
 constexpr int RMAX = 4;        // row tiles per CTA
-constexpr int THREADS = 192;
+constexpr int EPI_WARPS = 8;   // two warpgroups drain accumulators
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, NT);
 
 struct BeamSmemPlan {
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
     }
     for (int a = 0; a < NACC; a++) {
       tc::mbar_init(&accf[a], 1);
-      tc::mbar_init(&acce[a], 4);
+      tc::mbar_init(&acce[a], 4);  // the four warps of the draining warpgroup
     }
     tc::mbar_init(abar, 1);
     tc::mbar_init(drain, 1);
@@ -200,8 +202,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
       tc::mbar_wait(drain, 0, nullptr, 1u << 22);
     } else if (warp >= 2) {
       // ------------------------------------------------------ epilogue
-      const int q = warp & 3;               // TMEM lane quarter of this warp
-      const int row = 32 * q + lane;        // row inside a 128-row tile
+      const int wg = (warp - 2) / 4;       // warpgroup: row tiles r with r % 2 == wg
+      const int q = warp & 3;              // TMEM lane quarter of this warp
+      const int row = 32 * q + lane;       // row inside a 128-row tile
       float sum[RMAX];
       long long next_b[RMAX];
 #pragma unroll
@@ -215,7 +218,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
         if (!(lane & 1) && p < args.n_pix) args.pow[m * args.n_pix + p] = sum[r] + other;
         sum[r] = 0.f;
       };
-      long long u = 0;
       bool ok = true;
       for (long long i = 0; ok && i < n_tiles; i++) {
         const long long t0 = args.t_begin + (j_a + i) * NT;
@@ -224,36 +226,46 @@ __global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
 #pragma unroll
         for (int r = 0; r < RMAX; r++) {
           if (r >= R_eff) break;
+          if ((r & 1) != wg) continue;
+          const long long u = i * R_eff + r;
           const int acc = (int)(u % NACC);
           const uint32_t aph = (uint32_t)((u / NACC) & 1);
-          u++;
           if (!tc::mbar_wait(&accf[acc], aph, abort_flag)) {
             raise();
             ok = false;
             break;
           }
           tc::fence_after();
-#pragma unroll 1
-          for (int c4 = 0; c4 < NT / 32; c4++) {
-            const long long cs = t0 + 32 * c4, ce = cs + 32;
-            if (ce <= tA || cs >= tB) continue;  // warp-uniform
-            float v[32];
-            tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * NT + 32 * c4), v);
-            if (cs >= tA && ce <= tB && ce <= next_b[r]) {
+          float v[128];
+          tc::tmem_ld128(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * NT), v);
+          // release the accumulator as soon as its values are in registers
+          tc::fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&acce[acc]);
+          if (tA <= t0 && t0 + NT <= tB && t0 + NT <= next_b[r]) {
+            float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+            for (int e = 0; e < 32; e++) {
+              p0 = fmaf(v[e], v[e], p0);
+              p1 = fmaf(v[32 + e], v[32 + e], p1);
+              p2 = fmaf(v[64 + e], v[64 + e], p2);
+              p3 = fmaf(v[96 + e], v[96 + e], p3);
+            }
+            sum[r] += (p0 + p1) + (p2 + p3);
+            if (t0 + NT == next_b[r]) {
+              flush(r, next_b[r] / args.L - 1);
+              next_b[r] += args.L;
+            }
+          } else {
+#pragma unroll
+            for (int c4 = 0; c4 < NT / 32; c4++) {
+              const long long cs = t0 + 32 * c4;
               float part = 0.f;
 #pragma unroll
-              for (int e = 0; e < 32; e++) part = fmaf(v[e], v[e], part);
-              sum[r] += part;
-              if (ce == next_b[r]) {
-                flush(r, next_b[r] / args.L - 1);
-                next_b[r] += args.L;
-              }
-            } else {
-              float part = 0.f;
               for (int e = 0; e < 32; e++) {
-                const long long t = cs + e;
+                const long long t = cs + e;  // warp-uniform
                 if (t < tA || t >= tB) continue;
-                part = fmaf(v[e], v[e], part);
+                part = fmaf(v[32 * c4 + e], v[32 * c4 + e], part);
                 if (t + 1 == next_b[r]) {
                   sum[r] += part;
                   part = 0.f;
@@ -264,9 +276,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
               sum[r] += part;
             }
           }
-          tc::fence_before();
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive(&acce[acc]);
         }
       }
     }

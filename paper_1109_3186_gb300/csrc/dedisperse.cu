@@ -97,15 +97,30 @@ __global__ void k_phase_table(double* __restrict__ G, long long nfft, int n1, in
   G[pos] = __dmul_rn(k_dm, g);
 }
 
+// ------------------------------------------------------------------ chirp
+// H[pos] = exp(-2 pi j frac(DM G[pos])) for one trial DM, in the spectrum's
+// order.  The product DM G and its reduction c - rint(c) are FP64 (the phase
+// reaches ~1e6 cycles at high DM); only the reduced fraction |r| <= 1/2 is
+// rounded to FP32, and the chirp is stored as FP32 complex.
+__global__ void k_chirp_table(const double* __restrict__ G, float2* __restrict__ H, double dm,
+                              long long nfft) {
+  long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= nfft) return;
+  double c = __dmul_rn(dm, G[pos]);
+  double r = __dsub_rn(c, rint(c));  // exact
+  float sn, cs;
+  sincospif(-2.0f * (float)r, &sn, &cs);
+  H[pos] = make_float2(cs, sn);
+}
+
 // ------------------------------------------------------------------ inverse
-// Row pass with the chirp: each CTA owns C rows and walks the sequences
-// blockIdx.y, blockIdx.y + gridDim.y, ... so the chirp of its rows (FP64 work)
-// is built once and reused for every antenna and block.
+// Row pass: X * H on load, IFFT of length L = n2, twiddle W_N^(-n2 k1) on
+// store.  One CTA per (C rows, sequence); H comes from the per-DM table.
 template <int L>
 __global__ void __launch_bounds__(256) k_inv_rows(const float2* __restrict__ spec,
                                                   float2* __restrict__ Z,
-                                                  const double* __restrict__ G, double dm, int n1,
-                                                  int log2n, long long n_seq, TwiddlePtrs twp) {
+                                                  const float2* __restrict__ H, int n1,
+                                                  int log2n, TwiddlePtrs twp) {
   constexpr int C = 4096 / L;
   constexpr int T = L / 16;
   __shared__ float2 sm[FftTile<L, C>::SLOTS];
@@ -114,32 +129,20 @@ __global__ void __launch_bounds__(256) k_inv_rows(const float2* __restrict__ spe
   const int k1 = blockIdx.x * C + s;
   const bool act = k1 < n1;
   const long long nfft = (long long)L * n1;
-  float2 H[16];
+  const long long q = blockIdx.y;
+  const float2* src = spec + q * nfft + (long long)k1 * L;
+  const float2* h = H + (long long)k1 * L;
+  float2 v[16];
+#pragma unroll
+  for (int k = 0; k < 16; k++)
+    v[k] = act ? cmul(src[jt + k * T], __ldg(h + jt + k * T)) : make_float2(0.f, 0.f);
+  fft_core<L, C, true, true>(v, sm, s, jt, tw);
+  if (!act) return;
+  float2* dst = Z + q * nfft + (long long)k1 * L;
 #pragma unroll
   for (int k = 0; k < 16; k++) {
-    H[k] = make_float2(0.f, 0.f);
-    if (act) {
-      double c = __dmul_rn(dm, __ldg(G + (long long)k1 * L + jt + k * T));
-      double r = __dsub_rn(c, rint(c));              // exact: |r| <= 1/2
-      float sn, cs;
-      sincospif(-2.0f * (float)r, &sn, &cs);        // exp(-2 pi j r)
-      H[k] = make_float2(cs, sn);
-    }
-  }
-  for (long long q = blockIdx.y; q < n_seq; q += gridDim.y) {
-    const float2* src = spec + q * nfft + (long long)k1 * L;
-    float2 v[16];
-#pragma unroll
-    for (int k = 0; k < 16; k++) v[k] = act ? cmul(src[jt + k * T], H[k]) : make_float2(0.f, 0.f);
-    fft_core<L, C, true, true>(v, sm, s, jt, tw);
-    if (act) {
-      float2* dst = Z + q * nfft + (long long)k1 * L;
-#pragma unroll
-      for (int k = 0; k < 16; k++) {
-        int n2i = jt + k * T;
-        dst[n2i] = cmul(v[k], tw_big<true>(tw, (unsigned)(k1 * n2i), log2n));
-      }
-    }
+    int n2i = jt + k * T;
+    dst[n2i] = cmul(v[k], tw_big<true>(tw, (unsigned)(k1 * n2i), log2n));
   }
 }
 
@@ -219,19 +222,22 @@ cudaError_t launch_build_phase_table(double* G, const GroupGeom& g, double f0, d
   return cudaGetLastError();
 }
 
-cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const double* G, double dm,
-                                int n_ant, const GroupGeom& g, TwiddlePtrs tw, cudaStream_t st) {
+cudaError_t launch_chirp_table(const double* G, float2* H, double dm, const GroupGeom& g,
+                               cudaStream_t st) {
+  long long blocks = (g.nfft + 255) / 256;
+  k_chirp_table<<<(unsigned)blocks, 256, 0, st>>>(G, H, dm, g.nfft);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, int n_ant,
+                                const GroupGeom& g, TwiddlePtrs tw, cudaStream_t st) {
   const long long n_seq = (long long)n_ant * g.n_blk;
+  if (n_seq > 65535) return cudaErrorInvalidConfiguration;
   const int C = 4096 / g.n2;
-  const int row_tiles = (g.n1 + C - 1) / C;
-  // enough CTAs to fill the machine several times; each reuses its chirp
-  int by = (int)((4 * 152 + row_tiles - 1) / row_tiles);
-  if (by < 1) by = 1;
-  if (by > n_seq) by = (int)n_seq;
-  dim3 grid(row_tiles, by);
+  dim3 grid((g.n1 + C - 1) / C, (unsigned)n_seq);
   switch (g.n2) {
 #define X(L) \
-  case L: k_inv_rows<L><<<grid, 256, 0, st>>>(spec, Z, G, dm, g.n1, g.log2n, n_seq, tw); break;
+  case L: k_inv_rows<L><<<grid, 256, 0, st>>>(spec, Z, H, g.n1, g.log2n, tw); break;
     CHIRP_SIZES(X)
 #undef X
     default: return cudaErrorInvalidValue;

@@ -35,9 +35,12 @@ cudaError_t launch_forward(const float2* x, long long n_samp, int n_ant, const G
 // G[pos] = k_dm f^2/(f0^2 (f0 + f)) in the spectrum's (transposed) order, FP64
 cudaError_t launch_build_phase_table(double* G, const GroupGeom& g, double f0, double bw,
                                      double k_dm, cudaStream_t st);
+// H[pos] = exp(-2 pi j frac(dm G[pos])), FP64 phase, FP32 complex result
+cudaError_t launch_chirp_table(const double* G, float2* H, double dm, const GroupGeom& g,
+                               cudaStream_t st);
 // Z = rows of IFFT after the chirp multiply and the inter-pass twiddle
-cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const double* G, double dm,
-                                int n_ant, const GroupGeom& g, TwiddlePtrs tw, cudaStream_t st);
+cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, int n_ant,
+                                const GroupGeom& g, TwiddlePtrs tw, cudaStream_t st);
 // y[a][t] = dedispersed voltage for every owned, valid t (other t untouched)
 cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, int n_ant,
                                 const GroupGeom& g, long long n_hi, long long n_lo,

@@ -139,10 +139,11 @@ extern "C" int chirp_dedisperse_noalloc(const void* volt, int n_ant, long long n
   if ((long long)n_ant * g.n_blk > 65535)
     return bad(CHIRP_EUNSUPPORTED, "chirp_dedisperse_noalloc: n_ant * blocks exceeds 65535");
 
-  // scratch layout: twiddles | FP64 phase table | spectra | inverse intermediate
+  // scratch layout: twiddles | FP64 phase table | FP32 chirp | spectra | inverse intermediate
   const size_t points = (size_t)n_ant * (size_t)g.n_blk * (size_t)nfft;
   const size_t off_G = kTwiddleBytes;
-  const size_t off_spec = align256(off_G + (size_t)nfft * sizeof(double));
+  const size_t off_H = align256(off_G + (size_t)nfft * sizeof(double));
+  const size_t off_spec = align256(off_H + (size_t)nfft * sizeof(float2));
   const size_t off_Z = align256(off_spec + points * sizeof(float2));
   const size_t need = align256(off_Z + points * sizeof(float2));
   if (need > kScratchBytes) {
@@ -158,6 +159,7 @@ extern "C" int chirp_dedisperse_noalloc(const void* volt, int n_ant, long long n
   if (rc) return rc;
   const TwiddlePtrs tw{(const float2*)base, (const float2*)base + 4096};
   double* G = (double*)(base + off_G);
+  float2* H = (float2*)(base + off_H);
   float2* spec = (float2*)(base + off_spec);
   float2* Z = (float2*)(base + off_Z);
 
@@ -167,7 +169,8 @@ extern "C" int chirp_dedisperse_noalloc(const void* volt, int n_ant, long long n
   if (e == cudaSuccess) e = launch_forward((const float2*)volt, n_samp, n_ant, g, spec, tw, st);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(y_out, 0, (size_t)n_ant * (size_t)n_samp * sizeof(float2), st);
-  if (e == cudaSuccess) e = launch_inverse_rows(spec, Z, G, dm, n_ant, g, tw, st);
+  if (e == cudaSuccess) e = launch_chirp_table(G, H, dm, g, st);
+  if (e == cudaSuccess) e = launch_inverse_rows(spec, Z, H, n_ant, g, tw, st);
   if (e == cudaSuccess)
     e = launch_inverse_cols(Z, (float2*)y_out, n_samp, n_ant, g, n_hi, n_lo, tw, st);
   if (e != cudaSuccess) {

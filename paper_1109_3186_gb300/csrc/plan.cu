@@ -97,6 +97,7 @@ struct chirp_plan {
   float2* d_tw = nullptr;    // [8192]: coarse then fine
   float2* d_x = nullptr;     // staging copy of host voltages [M][N]
   float2* d_Z = nullptr;     // inverse-row intermediate, largest group
+  float2* d_H = nullptr;     // FP32 chirp of the current DM, largest group
   float2* d_y = nullptr;     // dedispersed voltages of one DM [M][N]
   float2* d_W = nullptr;     // beam weights [n_pix][M]
   uint8_t* d_aimg = nullptr; // tensor-core A image (split-BF16 weights)
@@ -142,6 +143,7 @@ void release(chirp_plan* p) {
   cudaFree(p->d_tw);
   cudaFree(p->d_x);
   cudaFree(p->d_Z);
+  cudaFree(p->d_H);
   cudaFree(p->d_y);
   cudaFree(p->d_W);
   cudaFree(p->d_aimg);
@@ -341,6 +343,9 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
     if (!rc) rc = dev_alloc(p, (void**)&g.d_G, g.geom.nfft * sizeof(double), "phase table");
   }
   if (!rc) rc = dev_alloc(p, (void**)&p->d_Z, z_elems * sizeof(float2), "inverse workspace");
+  long long max_nfft = 0;
+  for (auto& g : p->groups) max_nfft = std::max(max_nfft, g.geom.nfft);
+  if (!rc) rc = dev_alloc(p, (void**)&p->d_H, (size_t)max_nfft * sizeof(float2), "chirp table");
   if (!rc) rc = dev_alloc(p, (void**)&p->d_y, (size_t)p->M * p->N * sizeof(float2), "voltages");
   if (!rc && p->n_pix > 0)
     rc = dev_alloc(p, (void**)&p->d_W, (size_t)p->n_pix * p->M * sizeof(float2), "weights");
@@ -522,7 +527,10 @@ int dedisperse_one(chirp_plan* p, int d, float2* y) {
   const DmInfo& I = p->dmi[d];
   Group& g = p->groups[I.group];
   int mk = mark_begin(p);
-  CK(launch_inverse_rows(g.d_spec, p->d_Z, g.d_G, p->dm[d], p->M, g.geom, p->tw(), p->stream));
+  CK(launch_chirp_table(g.d_G, p->d_H, p->dm[d], g.geom, p->stream));
+  mark_end(p, CHIRP_STAGE_CHIRP, mk);
+  mk = mark_begin(p);
+  CK(launch_inverse_rows(g.d_spec, p->d_Z, p->d_H, p->M, g.geom, p->tw(), p->stream));
   mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
   mk = mark_begin(p);
   CK(launch_inverse_cols(p->d_Z, y, p->N, p->M, g.geom, I.n_hi, I.n_lo, p->tw(), p->stream));
