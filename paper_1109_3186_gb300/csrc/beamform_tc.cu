@@ -50,7 +50,7 @@ namespace {
 constexpr int NT = 128;        // samples per B tile = MMA N
 constexpr int NSTAGE = 4;      // B ring depth
 constexpr int NACC = 4;        // TMEM accumulators of NT columns
-constexpr int RMAX = 4;        // row tiles per CTA
+constexpr int RMAX = 8;        // row tiles per CTA (weights resident in smem)
 constexpr int EPI_WARPS = 8;   // two warpgroups drain accumulators
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, NT);
@@ -202,31 +202,34 @@ __global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
       tc::mbar_wait(drain, 0, nullptr, 1u << 22);
     } else if (warp >= 2) {
       // ------------------------------------------------------ epilogue
-      const int wg = (warp - 2) / 4;       // warpgroup: row tiles r with r % 2 == wg
+      // warpgroup wg drains row tiles r = wg, wg + 2, ...; rr = r / 2 indexes
+      // its per-row running dump sums.  All row tiles of a B tile cover the
+      // same samples, so the dump boundary state (next_b) is per warpgroup.
+      const int wg = (warp - 2) / 4;
       const int q = warp & 3;              // TMEM lane quarter of this warp
       const int row = 32 * q + lane;       // row inside a 128-row tile
-      float sum[RMAX];
-      long long next_b[RMAX];
+      constexpr int RH = RMAX / 2;
+      float sum[RH];
 #pragma unroll
-      for (int r = 0; r < RMAX; r++) {
-        sum[r] = 0.f;
-        next_b[r] = ta + args.L;
-      }
-      auto flush = [&](int r, long long m) {
-        const float other = __shfl_xor_sync(0xffffffffu, sum[r], 1);
-        const int p = ((rt0 + r) * 128 + row) >> 1;
-        if (!(lane & 1) && p < args.n_pix) args.pow[m * args.n_pix + p] = sum[r] + other;
-        sum[r] = 0.f;
+      for (int rr = 0; rr < RH; rr++) sum[rr] = 0.f;
+      long long next_b = ta + args.L;      // end of the dump being integrated
+      auto flush = [&](int rr, long long m) {
+        const float other = __shfl_xor_sync(0xffffffffu, sum[rr], 1);
+        const int p = ((rt0 + 2 * rr + wg) * 128 + row) >> 1;
+        if (!(lane & 1) && p < args.n_pix) args.pow[m * args.n_pix + p] = sum[rr] + other;
+        sum[rr] = 0.f;
       };
       bool ok = true;
       for (long long i = 0; ok && i < n_tiles; i++) {
         const long long t0 = args.t_begin + (j_a + i) * NT;
         const long long tA = t0 > ta ? t0 : ta;
         const long long tB = (t0 + NT) < tb ? (t0 + NT) : tb;
+        const bool clean = tA == t0 && tB == t0 + NT && t0 + NT <= next_b;  // warp-uniform
+        long long nb_after = next_b;
 #pragma unroll
-        for (int r = 0; r < RMAX; r++) {
+        for (int rr = 0; rr < RH; rr++) {
+          const int r = 2 * rr + wg;
           if (r >= R_eff) break;
-          if ((r & 1) != wg) continue;
           const long long u = i * R_eff + r;
           const int acc = (int)(u % NACC);
           const uint32_t aph = (uint32_t)((u / NACC) & 1);
@@ -236,46 +239,62 @@ __global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
             break;
           }
           tc::fence_after();
-          float v[128];
-          tc::tmem_ld128(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * NT), v);
-          // release the accumulator as soon as its values are in registers
-          tc::fence_before();
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive(&acce[acc]);
-          if (tA <= t0 && t0 + NT <= tB && t0 + NT <= next_b[r]) {
-            float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+          const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * NT);
+          if (clean) {
+            float part = 0.f;
 #pragma unroll
-            for (int e = 0; e < 32; e++) {
-              p0 = fmaf(v[e], v[e], p0);
-              p1 = fmaf(v[32 + e], v[32 + e], p1);
-              p2 = fmaf(v[64 + e], v[64 + e], p2);
-              p3 = fmaf(v[96 + e], v[96 + e], p3);
+            for (int h = 0; h < 2; h++) {
+              float v[64];
+              tc::tmem_ld64(tbase + 64 * h, v);
+              float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+              for (int e = 0; e < 16; e++) {
+                p0 = fmaf(v[e], v[e], p0);
+                p1 = fmaf(v[16 + e], v[16 + e], p1);
+                p2 = fmaf(v[32 + e], v[32 + e], p2);
+                p3 = fmaf(v[48 + e], v[48 + e], p3);
+              }
+              part += (p0 + p1) + (p2 + p3);
             }
-            sum[r] += (p0 + p1) + (p2 + p3);
-            if (t0 + NT == next_b[r]) {
-              flush(r, next_b[r] / args.L - 1);
-              next_b[r] += args.L;
-            }
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acce[acc]);
+            sum[rr] += part;
+            if (t0 + NT == next_b) flush(rr, next_b / args.L - 1);
           } else {
-#pragma unroll
+            // tile at the edge of this CTA's range or holding a dump boundary
+            long long nb = next_b;
+#pragma unroll 1
             for (int c4 = 0; c4 < NT / 32; c4++) {
               const long long cs = t0 + 32 * c4;
+              if (cs + 32 <= tA || cs >= tB) continue;  // warp-uniform
+              float v[32];
+              tc::tmem_ld32(tbase + 32 * c4, v);
               float part = 0.f;
 #pragma unroll
               for (int e = 0; e < 32; e++) {
                 const long long t = cs + e;  // warp-uniform
                 if (t < tA || t >= tB) continue;
-                part = fmaf(v[32 * c4 + e], v[32 * c4 + e], part);
-                if (t + 1 == next_b[r]) {
-                  sum[r] += part;
+                part = fmaf(v[e], v[e], part);
+                if (t + 1 == nb) {
+                  sum[rr] += part;
                   part = 0.f;
-                  flush(r, next_b[r] / args.L - 1);
-                  next_b[r] += args.L;
+                  flush(rr, nb / args.L - 1);
+                  nb += args.L;
                 }
               }
-              sum[r] += part;
+              sum[rr] += part;
             }
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acce[acc]);
+            nb_after = nb;
           }
+        }
+        if (clean) {
+          if (t0 + NT == next_b) next_b += args.L;
+        } else {
+          next_b = nb_after;
         }
       }
     }

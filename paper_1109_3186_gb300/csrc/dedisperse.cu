@@ -28,7 +28,7 @@ static __device__ __forceinline__ Twiddles mk_tw(TwiddlePtrs p) { return Twiddle
 // ------------------------------------------------------------------ forward
 // Column pass: L = n1, C = 4096 / n1 columns per CTA (interleaved tile).
 template <int L>
-__global__ void __launch_bounds__(256) k_fwd_cols(const float2* __restrict__ x, long long n_samp,
+__global__ void __launch_bounds__(256, 4) k_fwd_cols(const float2* __restrict__ x, long long n_samp,
                                                   float2* __restrict__ spec, int n2, int log2n,
                                                   long long step, long long n_blk,
                                                   TwiddlePtrs twp) {
@@ -53,17 +53,15 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const float2* __restrict__ x, 
   fft_core<L, C, false, false>(v, sm, s, jt, tw);
   if (!act) return;
   float2* out = spec + q * nfft;
+  // twiddle W_N^(c k1), k1 = jt + k T
+  twiddle_run<false>(v, (unsigned)c, (unsigned)jt, (unsigned)T, log2n, tw);
 #pragma unroll
-  for (int k = 0; k < 16; k++) {
-    int k1 = jt + k * T;
-    float2 w = tw_big<false>(tw, (unsigned)(k1 * c), log2n);
-    out[(long long)k1 * n2 + c] = cmul(v[k], w);
-  }
+  for (int k = 0; k < 16; k++) out[(long long)(jt + k * T) * n2 + c] = v[k];
 }
 
 // Row pass: L = n2, C = 4096 / L rows per CTA (row-major tile), in place.
 template <int L>
-__global__ void __launch_bounds__(256) k_fwd_rows(float2* __restrict__ spec, int n1,
+__global__ void __launch_bounds__(256, 4) k_fwd_rows(float2* __restrict__ spec, int n1,
                                                   TwiddlePtrs twp) {
   constexpr int C = 4096 / L;
   constexpr int T = L / 16;
@@ -117,7 +115,7 @@ __global__ void k_chirp_table(const double* __restrict__ G, float2* __restrict__
 // Row pass: X * H on load, IFFT of length L = n2, twiddle W_N^(-n2 k1) on
 // store.  One CTA per (C rows, sequence); H comes from the per-DM table.
 template <int L>
-__global__ void __launch_bounds__(256) k_inv_rows(const float2* __restrict__ spec,
+__global__ void __launch_bounds__(256, 4) k_inv_rows(const float2* __restrict__ spec,
                                                   float2* __restrict__ Z,
                                                   const float2* __restrict__ H, int n1,
                                                   int log2n, TwiddlePtrs twp) {
@@ -139,17 +137,16 @@ __global__ void __launch_bounds__(256) k_inv_rows(const float2* __restrict__ spe
   fft_core<L, C, true, true>(v, sm, s, jt, tw);
   if (!act) return;
   float2* dst = Z + q * nfft + (long long)k1 * L;
+  // twiddle W_N^(-k1 n2), n2 = jt + k T
+  twiddle_run<true>(v, (unsigned)k1, (unsigned)jt, (unsigned)T, log2n, tw);
 #pragma unroll
-  for (int k = 0; k < 16; k++) {
-    int n2i = jt + k * T;
-    dst[n2i] = cmul(v[k], tw_big<true>(tw, (unsigned)(k1 * n2i), log2n));
-  }
+  for (int k = 0; k < 16; k++) dst[jt + k * T] = v[k];
 }
 
 // Column pass of the inverse: natural-order output, 1/Nfft, overlap-save
 // discard and ownership.  Block b owns block positions [lo_b, hi_b).
 template <int L>
-__global__ void __launch_bounds__(256) k_inv_cols(const float2* __restrict__ Z,
+__global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ Z,
                                                   float2* __restrict__ y, long long n_samp,
                                                   int n2, long long step, long long n_blk,
                                                   long long n_hi, long long n_lo,

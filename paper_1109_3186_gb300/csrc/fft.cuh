@@ -179,6 +179,24 @@ __device__ __forceinline__ int tile_idx(int i, int s) {
   return padidx(ROWMAJOR ? s * L + i : i * C + s);
 }
 
+// v[k] *= a w1^k for k = 0..15, given w1 and w4 = w1^4 (exact table values).
+// Powers are formed on the fly as (a w4^b) w1^q with k = 4b + q, so every
+// factor is at most a few products away from a table value (a running product
+// would add one rounding per step) and only a handful of registers are live.
+__device__ __forceinline__ void apply_pow16(float2 (&v)[16], float2 a, float2 w1, float2 w4) {
+  const float2 w2 = cmul(w1, w1);
+  const float2 w3 = cmul(w2, w1);
+  float2 base = a;
+#pragma unroll
+  for (int b = 0; b < 4; b++) {
+    v[4 * b] = cmul(v[4 * b], base);
+    v[4 * b + 1] = cmul(v[4 * b + 1], cmul(base, w1));
+    v[4 * b + 2] = cmul(v[4 * b + 2], cmul(base, w2));
+    v[4 * b + 3] = cmul(v[4 * b + 3], cmul(base, w3));
+    if (b < 3) base = cmul(base, w4);
+  }
+}
+
 // Stockham stage helpers -------------------------------------------------
 // One radix-R stage of span Ns over L points for butterfly j:
 //   in:  a[j + q L/R],  twiddle W_{Ns R}^{q (j mod Ns)},  DFT_R,
@@ -188,8 +206,24 @@ __device__ __forceinline__ void stage_twiddle(float2* v, int j, int Ns, const Tw
   if (Ns == 1) return;
   int jm = j & (Ns - 1);
   int scale = 4096 / (Ns * R);
+  if constexpr (R == 16) {
+    float2 (&vv)[16] = *reinterpret_cast<float2(*)[16]>(v);
+    apply_pow16(vv, make_float2(1.f, 0.f), tw4096<INV>(tw, jm * scale),
+                tw4096<INV>(tw, 4 * jm * scale));
+  } else {
 #pragma unroll
-  for (int q = 1; q < R; q++) v[q] = cmul(v[q], tw4096<INV>(tw, (q * jm * scale) & 4095));
+    for (int q = 1; q < R; q++) v[q] = cmul(v[q], tw4096<INV>(tw, (q * jm * scale) & 4095));
+  }
+}
+
+// v[k] *= W_N^(-+ m (j0 + k T)) for k = 0..15 (N = 2^log2n), from three
+// table look-ups per thread instead of two per element.
+template <bool INV>
+__device__ __forceinline__ void twiddle_run(float2 (&v)[16], unsigned m, unsigned j0, unsigned T,
+                                            int log2n, const Twiddles& tw) {
+  const unsigned mask = (1u << log2n) - 1u;
+  apply_pow16(v, tw_big<INV>(tw, (m * j0) & mask, log2n), tw_big<INV>(tw, (m * T) & mask, log2n),
+              tw_big<INV>(tw, (4u * m * T) & mask, log2n));
 }
 
 // Forward (INV=false) or inverse (INV=true, unnormalised) FFT of length L.
