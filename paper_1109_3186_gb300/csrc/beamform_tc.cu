@@ -47,9 +47,15 @@ namespace chirp {
 
 namespace {
 
-constexpr int NT = 128;        // samples per B tile = MMA N
-constexpr int NSTAGE = 4;      // B ring depth
-constexpr int NACC = 4;        // TMEM accumulators of NT columns
+#ifndef CHIRP_BEAM_NT
+#define CHIRP_BEAM_NT 128
+#endif
+#ifndef CHIRP_BEAM_NSTAGE
+#define CHIRP_BEAM_NSTAGE 4
+#endif
+constexpr int NT = CHIRP_BEAM_NT;          // samples per B tile = MMA N
+constexpr int NSTAGE = CHIRP_BEAM_NSTAGE;  // B ring depth
+constexpr int NACC = 512 / NT;             // TMEM accumulators of NT columns
 constexpr int RMAX = 8;        // row tiles per CTA (weights resident in smem)
 constexpr int EPI_WARPS = 8;   // two warpgroups drain accumulators
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
@@ -86,6 +92,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
   uint8_t* smA = smem;
   uint8_t* smB = smem + sp.a_bytes;
   uint64_t* bars = (uint64_t*)(smem + sp.bar_off);
+  static_assert(2 * NSTAGE + 2 * NACC + 2 <= 28, "barrier area");
+  static_assert(NACC % 2 == 0, "two draining warpgroups need an even accumulator count");
   uint64_t* full = bars;                 // [NSTAGE]
   uint64_t* empty = bars + NSTAGE;       // [NSTAGE]
   uint64_t* accf = bars + 2 * NSTAGE;    // [NACC]
@@ -98,6 +106,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int rt0 = blockIdx.x * args.R;
   const int R_eff = min(args.R, args.n_rowtiles - rt0);
+  // The pipeline always walks an even number of row tiles (a padding tile
+  // is committed without MMAs and drained without reads).  Then accumulator
+  // acc = u % NACC has the parity of r, so each accumulator -- and each of its
+  // mbarriers -- has exactly one draining warpgroup, which can never be two
+  // phases behind (phase parity would alias).
+  const int R_pipe = (R_eff + 1) & ~1;
   // dumps of this CTA: [m_a, m_b) ; samples [ta, tb)
   const long long m_a = args.first + (long long)blockIdx.y * args.dumps_per_cta;
   const long long m_b = min(m_a + args.dumps_per_cta, args.first + args.n_dumps);
@@ -174,7 +188,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
           break;
         }
         tc::fence_after();
-        for (int r = 0; r < R_eff; r++, u++) {
+        for (int r = 0; r < R_pipe; r++, u++) {
           const int acc = (int)(u % NACC);
           const uint32_t aph = (uint32_t)((u / NACC) & 1);
           if (!tc::mbar_wait(&acce[acc], aph ^ 1, abort_flag)) {
@@ -184,7 +198,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
           }
           tc::fence_after();
           const uint32_t d = tmem + (uint32_t)(acc * NT);
-          for (int ks = 0; ks < args.ksteps; ks++) {
+          for (int ks = 0; r < R_eff && ks < args.ksteps; ks++) {
             const int p0 = 2 * ks;
             const int bg = p0 < 2 * args.G ? p0 : p0 - 2 * args.G;
             const uint64_t ad = tc::sdesc(a_base + r * a_tile_bytes + ks * 256u, 128u, a_sbo);
@@ -229,8 +243,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
 #pragma unroll
         for (int rr = 0; rr < RH; rr++) {
           const int r = 2 * rr + wg;
-          if (r >= R_eff) break;
-          const long long u = i * R_eff + r;
+          if (r >= R_pipe) break;
+          const long long u = i * R_pipe + r;
           const int acc = (int)(u % NACC);
           const uint32_t aph = (uint32_t)((u / NACC) & 1);
           if (!tc::mbar_wait(&accf[acc], aph, abort_flag)) {
@@ -239,11 +253,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
             break;
           }
           tc::fence_after();
+          if (r >= R_eff) {  // padding tile: release without reading
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acce[acc]);
+            continue;
+          }
           const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * NT);
           if (clean) {
             float part = 0.f;
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
+            for (int h = 0; h < NT / 64; h++) {
               float v[64];
               tc::tmem_ld64(tbase + 64 * h, v);
               float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;

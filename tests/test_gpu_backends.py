@@ -42,6 +42,8 @@ BEAM_CASES = [
     (3, 1 << 14, 512, 1, [7.0], 1 << 12),
     (13, 70000, 777, 12, [0.0, 20.0], 1 << 14),       # dumps straddle 128-sample tiles
     (12, 1 << 18, 4096, 32, [0.0, 150.0, 300.0], 1 << 17),   # 1024 beams, all row tiles
+    (7, 1 << 16, 2048, 20, [0.0, 25.0], 1 << 14),     # 400 beams: 7 row tiles (odd)
+    (12, 1 << 17, 512, 40, [40.0], 1 << 15),          # 1600 beams: 25 row tiles, 4 CTAs wide
 ]
 
 
