@@ -11,14 +11,14 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  *  - Voltages are complex baseband, complex-Nyquist sampled at f_s = B
- *    (Sec. 3.2, below Eq. 5): complex64 (interleaved float re, im),
+ *    (Sec. 3.2, below Eq. xpq): complex64 (interleaved float re, im),
  *    antenna-major [n_ant][n_samp].
  *  - Dispersion follows Eq. 1 (Sec. 2.1) with constant k_dm (s Hz^2 per
  *    pc cm^-3; mu ~ 4.15 ms GHz^2 in the paper).  Dedispersion multiplies the
  *    spectrum of each overlap-save block by
  *        H_DM(f) = exp(-2 pi j k_dm DM f^2 / (f0^2 (f0 + f)))
  *    (the inverse ISM response of Sec. 2.3.2 about f0); the forward DFT
- *    has the paper's sign exp(-2 pi j n k / N) (Eq. 6); the inverse
+ *    has the paper's sign exp(-2 pi j n k / N) (Eq. dft); the inverse
  *    includes 1/Nfft.
  *  - Per DM: n_hi = ceil(k DM (f0^-2 - (f0+B/2)^-2) B),
  *            n_lo = ceil(k DM ((f0-B/2)^-2 - f0^-2) B);
@@ -126,7 +126,7 @@ int chirp_dedisperse_run(chirp_plan* plan, const void* volt, int volt_loc, int d
 
 /* Chirpolator back-end: for every trial DM and dump, the zero-lag
  * visibilities V_pq = sum_t y_p(t) y_q(t)^* of the dedispersed voltages
- * (pair mixing x_pq = s_p s_q^* of Eq. 5, integrated and dumped; autos
+ * (pair mixing x_pq = s_p s_q^* of Eq. xpq, integrated and dumped; autos
  * included).  vis_out: complex64 [n_dm][n_dump][n_pair], pairs p <= q in
  * row-major order (0,0),(0,1),..,(0,M-1),(1,1),...  Errors: CHIRP_EINVAL,
  * CHIRP_ECUDA. */

@@ -22,11 +22,11 @@
  *     whose group delay -(1/2pi) dPhi/df = k DM (f0^-2 - (f0+f)^-2) undoes
  *     Eq. 1 about f0.  The convolution is done by overlap-save: blocks of
  *     Nfft samples, forward DFT (e^{-2 pi j n k / N}, the paper's sign,
- *     Eq. 6), multiply by H sampled at the Nfft bins, inverse DFT with 1/Nfft,
+ *     Eq. dft), multiply by H sampled at the Nfft bins, inverse DFT with 1/Nfft,
  *     keep the n_hi..Nfft-n_lo-1 circular outputs.
  *  3. Chirpolator back-end: per DM and per dump of L samples, the zero-lag
  *     cross products V_pq = sum_t y_p(t) y_q(t)^*  (the p.q^* convention of
- *     Eq. 5), autocorrelations included, packed upper triangle p <= q.
+ *     Eq. xpq), autocorrelations included, packed upper triangle p <= q.
  *  4. Chimageator back-end: per DM, pixel and dump, the phased sum over
  *     antennas b(t) = sum_a W_pa y_a(t), W_pa = exp(+2 pi j f0 tau_a(l_p,m_p))
  *     with tau from Eq. tau3D (App. A.1) and c = 299792458 m/s, detected as

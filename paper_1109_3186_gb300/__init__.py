@@ -12,7 +12,7 @@ float32 [n_dm, n_dump, n_pix].
 
 Paper: Bannister & Cornwell, "The Chirpolator & The Chimageator"
 (arXiv:1109.3186).  Dedispersion: Sec. 2.3.2 with Eq. 1; correlation:
-Eq. 5's p.q^* products integrated per dump; beams: Sec. 2.4.2 with Eq. tau3D.
+Eq. xpq's p.q^* products integrated per dump; beams: Sec. 2.4.2 with Eq. tau3D.
 """
 
 from __future__ import annotations

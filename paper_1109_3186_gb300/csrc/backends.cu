@@ -2,7 +2,7 @@
 //
 // Chirpolator (correlate): per dump m the zero-lag products
 //   V_pq = sum_{t in dump} y_p(t) y_q(t)^*   (p <= q, autos included),
-// the pair mixing x_pq = s_p s_q^* of Eq. 5 integrated and dumped.
+// the pair mixing x_pq = s_p s_q^* of Eq. xpq integrated and dumped.
 // Chimageator, plain FP32 form: per dump and pixel
 //   P = sum_{t in dump} |sum_a W_pa y_a(t)|^2
 // (direct beamforming, Sec. 2.4.2, detected and integrated).

@@ -1,5 +1,5 @@
 """GPU parity of the two back-ends, through the C ABI, against the FP64
-oracle: Chirpolator visibilities (Eq. 5 products integrated per dump) and
+oracle: Chirpolator visibilities (Eq. xpq products integrated per dump) and
 Chimageator beam powers (Sec. 2.4.2 phased sum, |.|^2, integrated).  FP32
 path tolerance 1e-5 on both metrics."""
 import numpy as np

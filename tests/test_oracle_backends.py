@@ -2,7 +2,7 @@
 
 * Chirpolator: at DM = 0 the per-DM visibilities are the plain zero-lag
   correlator of the raw voltages (Sec. 2.4.3, FX correlation; p.q^* as in
-  Eq. 5); autocorrelations are real and non-negative; exchanging two antennas
+  Eq. xpq); autocorrelations are real and non-negative; exchanging two antennas
   conjugates their visibility (V_qp = V_pq^*).
 * Chimageator: at DM = 0 the beam powers are the plain phased-sum beamformer
   of the raw voltages (Sec. 2.4.2); a narrowband tone from direction (l, m)

@@ -1,6 +1,6 @@
 """Pins of the oracle's DFTs against numpy's FFT (an independent library) and
 Parseval's theorem.  The forward sign is the paper's, exp(-2 pi j n k / N)
-(Sec. 3.2, Eq. 6)."""
+(Sec. 3.2, Eq. dft)."""
 import numpy as np
 import pytest
 
