@@ -47,29 +47,37 @@ namespace chirp {
 
 namespace {
 
-#ifndef CHIRP_BEAM_NT
-#define CHIRP_BEAM_NT 128
-#endif
-#ifndef CHIRP_BEAM_NSTAGE
-#define CHIRP_BEAM_NSTAGE 4
-#endif
-constexpr int NT = CHIRP_BEAM_NT;          // samples per B tile = MMA N
-constexpr int NSTAGE = CHIRP_BEAM_NSTAGE;  // B ring depth
-constexpr int NACC = 512 / NT;             // TMEM accumulators of NT columns
 constexpr int RMAX = 8;        // row tiles per CTA (weights resident in smem)
-constexpr int EPI_WARPS = 8;   // two warpgroups drain accumulators
-constexpr int THREADS = 64 + 32 * EPI_WARPS;
-constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, NT);
 
-struct BeamSmemPlan {
-  uint32_t a_bytes, b_stage_bytes, bar_off, total;
+// Two shapes of the same kernel:
+//  NT = 128 (any dump length): 4 accumulators of 128 columns, two warpgroups
+//    each draining whole accumulators (row tiles of one parity);
+//  NT = 256 (dump length a multiple of 256): 2 accumulators of 256 columns,
+//    four warpgroups each draining a 64-column slice of every accumulator and
+//    releasing it right after the load; the four partial sums of a row are
+//    combined in shared memory once per dump.  The wider MMA halves the
+//    shared-memory operand traffic per flop.
+template <int NT>
+struct BeamCfg {
+  static constexpr int NACC = 512 / NT;           // TMEM accumulators
+  static constexpr int NSTAGE = NT == 256 ? 3 : 4;
+  static constexpr int EPI_WARPS = NT == 256 ? 16 : 8;
+  static constexpr int THREADS = 64 + 32 * EPI_WARPS;
+  static constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, NT);
+  static constexpr uint32_t RED_BYTES = NT == 256 ? 4u * RMAX * 128u * 4u : 0u;
 };
 
+struct BeamSmemPlan {
+  uint32_t a_bytes, b_stage_bytes, red_off, bar_off, total;
+};
+
+template <int NT>
 __host__ __device__ inline BeamSmemPlan beam_smem_plan(int R, int ksteps, int G) {
   BeamSmemPlan s;
   s.a_bytes = (uint32_t)R * ksteps * 4096u;
   s.b_stage_bytes = (uint32_t)NT * 2u * G * 16u;
-  s.bar_off = s.a_bytes + NSTAGE * s.b_stage_bytes;
+  s.red_off = s.a_bytes + BeamCfg<NT>::NSTAGE * s.b_stage_bytes;
+  s.bar_off = s.red_off + BeamCfg<NT>::RED_BYTES;
   s.total = s.bar_off + 256;
   return s;
 }
@@ -86,13 +94,19 @@ struct BeamArgs {
   int L, n_pix, n_rowtiles, R, G, ksteps;
 };
 
-__global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
+template <int NT>
+__global__ void __launch_bounds__(BeamCfg<NT>::THREADS, 1) k_beam_tc(BeamArgs args) {
+  constexpr int NACC = BeamCfg<NT>::NACC;
+  constexpr int NSTAGE = BeamCfg<NT>::NSTAGE;
+  constexpr uint32_t IDESC = BeamCfg<NT>::IDESC;
   extern __shared__ __align__(1024) uint8_t smem[];
-  const BeamSmemPlan sp = beam_smem_plan(args.R, args.ksteps, args.G);
+  const BeamSmemPlan sp = beam_smem_plan<NT>(args.R, args.ksteps, args.G);
+  float* red = (float*)(smem + sp.red_off);  // NT = 256: [4 slices][RMAX][128 rows]
   uint8_t* smA = smem;
   uint8_t* smB = smem + sp.a_bytes;
   uint64_t* bars = (uint64_t*)(smem + sp.bar_off);
   static_assert(2 * NSTAGE + 2 * NACC + 2 <= 28, "barrier area");
+  static_assert(NT == 128 || NT == 256, "tile width");
   static_assert(NACC % 2 == 0, "two draining warpgroups need an even accumulator count");
   uint64_t* full = bars;                 // [NSTAGE]
   uint64_t* empty = bars + NSTAGE;       // [NSTAGE]
@@ -128,7 +142,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
     }
     for (int a = 0; a < NACC; a++) {
       tc::mbar_init(&accf[a], 1);
-      tc::mbar_init(&acce[a], 4);  // the four warps of the draining warpgroup
+      tc::mbar_init(&acce[a], NT == 256 ? 16 : 4);  // every draining warp arrives once
     }
     tc::mbar_init(abar, 1);
     tc::mbar_init(drain, 1);
@@ -215,6 +229,86 @@ __global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
       tc::mma_commit(drain);
       tc::mbar_wait(drain, 0, nullptr, 1u << 22);
     } else if (warp >= 2) {
+      if constexpr (NT == 256) {
+        // ---------------------------------------------------- epilogue, 4 slices
+        // Dumps start on tile boundaries (L % 256 == 0 and the CTA's range is
+        // dump-aligned), so a dump ends only at the end of a tile.
+        const int g = (warp - 2) / 4;        // column slice [64 g, 64 g + 64)
+        const int q = warp & 3;              // TMEM lane quarter of this warp
+        const int row = 32 * q + lane;
+        float sum[RMAX];
+#pragma unroll
+        for (int r = 0; r < RMAX; r++) sum[r] = 0.f;
+        // No warp leaves the tile loop early: the per-dump combine uses a
+        // named barrier, so after a timed-out wait this warp keeps walking
+        // (later waits return at once because the abort flag is up) and all
+        // warps leave together at the next combine point, or at the end.
+        bool aborted = false;
+        for (long long i = 0; i < n_tiles; i++) {
+          const long long t0 = args.t_begin + (j_a + i) * NT;
+#pragma unroll
+          for (int r = 0; r < RMAX; r++) {
+            if (r >= R_pipe) break;
+            const long long u = i * R_pipe + r;
+            const int acc = (int)(u % NACC);
+            const uint32_t aph = (uint32_t)((u / NACC) & 1);
+            if (!aborted && !tc::mbar_wait(&accf[acc], aph, abort_flag)) {
+              raise();
+              aborted = true;
+            }
+            tc::fence_after();
+            float v[64];
+            const bool use = !aborted && r < R_eff;
+            if (use)
+              tc::tmem_ld64(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * NT + 64 * g), v);
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acce[acc]);
+            if (use) {
+              float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+              for (int e = 0; e < 16; e++) {
+                p0 = fmaf(v[e], v[e], p0);
+                p1 = fmaf(v[16 + e], v[16 + e], p1);
+                p2 = fmaf(v[32 + e], v[32 + e], p2);
+                p3 = fmaf(v[48 + e], v[48 + e], p3);
+              }
+              sum[r] += (p0 + p1) + (p2 + p3);
+            }
+          }
+          if ((t0 + NT) % args.L == 0) {  // this tile closes dump m (warp-uniform)
+            const long long m = (t0 + NT) / args.L - 1;
+#pragma unroll
+            for (int r = 0; r < RMAX; r++) {
+              if (r < R_eff) red[(g * RMAX + r) * 128 + row] = sum[r];
+              sum[r] = 0.f;
+            }
+            // barrier with an OR of every epilogue thread's view of the abort
+            // flag, so all warps take the same decision
+            uint32_t stop_u;
+            asm volatile(
+                "{\n\t.reg .pred p, q;\n\t"
+                "setp.ne.u32 p, %1, 0;\n\t"
+                "bar.red.or.pred q, 1, %2, p;\n\t"
+                "selp.u32 %0, 1, 0, q;\n\t}"
+                : "=r"(stop_u)
+                : "r"((uint32_t)(aborted || *abort_flag != 0)), "r"(32 * BeamCfg<NT>::EPI_WARPS)
+                : "memory");
+            const bool stop = stop_u != 0;
+            if (!stop)
+              for (int r = g; r < R_eff; r += 4) {
+                float tot = 0.f;
+#pragma unroll
+                for (int gg = 0; gg < 4; gg++) tot += red[(gg * RMAX + r) * 128 + row];
+                const float other = __shfl_xor_sync(0xffffffffu, tot, 1);
+                const int p = ((rt0 + r) * 128 + row) >> 1;
+                if (!(lane & 1) && p < args.n_pix) args.pow[m * args.n_pix + p] = tot + other;
+              }
+            asm volatile("bar.sync 1, %0;" ::"r"(32 * BeamCfg<NT>::EPI_WARPS) : "memory");
+            if (stop) break;
+          }
+        }
+      } else {
       // ------------------------------------------------------ epilogue
       // warpgroup wg drains row tiles r = wg, wg + 2, ...; rr = r / 2 indexes
       // its per-row running dump sums.  All row tiles of a B tile cover the
@@ -317,6 +411,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
           next_b = nb_after;
         }
       }
+      }
     }
   }
   tc::fence_before();
@@ -330,7 +425,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_beam_tc(BeamArgs args) {
 // y [n_ant][n_samp] complex64 -> B image tiles (BF16 heads and tails).
 // Thread (u, j): sample t = t_begin + u, real-K group j (antennas 4j..4j+3).
 __global__ void k_split_bf16(const float2* __restrict__ y, long long n_samp, int M, int G,
-                             long long t_begin, long long t_end, long long n_tiles,
+                             long long t_begin, long long t_end, long long n_tiles, int NT,
                              uint8_t* __restrict__ b_img) {
   const long long U = n_tiles * NT;
   const long long total = U * G;
@@ -421,36 +516,40 @@ std::vector<uint8_t> build_beam_a_image(const double* W, int n_ant, int n_pix) {
 
 int beam_tc_groups(int n_ant) { return (n_ant + 3) / 4; }
 int beam_tc_ksteps(int n_ant) { return (3 * beam_tc_groups(n_ant) + 1) / 2; }
-long long beam_tc_tile_bytes(int n_ant) { return (long long)NT * 2 * beam_tc_groups(n_ant) * 16; }
-int beam_tc_tile_samples() { return NT; }
+int beam_tc_tile_samples(int dump_len) { return dump_len % 256 == 0 ? 256 : 128; }
+long long beam_tc_tile_bytes(int n_ant, int dump_len) {
+  return (long long)beam_tc_tile_samples(dump_len) * 2 * beam_tc_groups(n_ant) * 16;
+}
 
-cudaError_t launch_split_bf16(const float2* y, long long n_samp, int n_ant, long long t_begin,
-                              long long t_end, uint8_t* b_img, cudaStream_t st) {
+cudaError_t launch_split_bf16(const float2* y, long long n_samp, int n_ant, int dump_len,
+                              long long t_begin, long long t_end, uint8_t* b_img,
+                              cudaStream_t st) {
   if (t_end <= t_begin) return cudaSuccess;
   const int G = beam_tc_groups(n_ant);
+  const int NT = beam_tc_tile_samples(dump_len);
   const long long n_tiles = (t_end - t_begin + NT - 1) / NT;
   const long long total = n_tiles * NT * G;
   long long blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   k_split_bf16<<<(unsigned)blocks, 256, 0, st>>>(y, n_samp, n_ant, G, t_begin, t_end, n_tiles,
-                                                 b_img);
+                                                 NT, b_img);
   return cudaGetLastError();
 }
 
-cudaError_t launch_beam_tc(const uint8_t* b_img, const uint8_t* a_img, int n_ant, int n_pix,
-                           int dump_len, long long first, long long last, float* pow, int* err,
-                           cudaStream_t st) {
-  if (last < first) return cudaSuccess;
+template <int NT>
+static cudaError_t launch_beam_tc_nt(const uint8_t* b_img, const uint8_t* a_img, int n_ant,
+                                     int n_pix, int dump_len, long long first, long long last,
+                                     float* pow, int* err, cudaStream_t st) {
   const int G = beam_tc_groups(n_ant), ks = beam_tc_ksteps(n_ant);
   const int n_rowtiles = (2 * n_pix + 127) / 128;
   int R = RMAX;
   if (R > n_rowtiles) R = n_rowtiles;
-  while (R > 1 && beam_smem_plan(R, ks, G).total > 220 * 1024) R--;
-  const BeamSmemPlan sp = beam_smem_plan(R, ks, G);
+  while (R > 1 && beam_smem_plan<NT>(R, ks, G).total > 220 * 1024) R--;
+  const BeamSmemPlan sp = beam_smem_plan<NT>(R, ks, G);
   if (sp.total > 227 * 1024) return cudaErrorInvalidConfiguration;
   // at least 116 KB so that a second CTA never shares the SM (and its TMEM)
   const uint32_t smem_bytes = sp.total > 116 * 1024 ? sp.total : 116 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_beam_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_beam_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes);
   if (e != cudaSuccess) return e;
   const int gx = (n_rowtiles + R - 1) / R;
@@ -474,8 +573,17 @@ cudaError_t launch_beam_tc(const uint8_t* b_img, const uint8_t* a_img, int n_ant
   a.R = R;
   a.G = G;
   a.ksteps = ks;
-  k_beam_tc<<<dim3(gx, (unsigned)gy), THREADS, smem_bytes, st>>>(a);
+  k_beam_tc<NT><<<dim3(gx, (unsigned)gy), BeamCfg<NT>::THREADS, smem_bytes, st>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_beam_tc(const uint8_t* b_img, const uint8_t* a_img, int n_ant, int n_pix,
+                           int dump_len, long long first, long long last, float* pow, int* err,
+                           cudaStream_t st) {
+  if (last < first) return cudaSuccess;
+  if (dump_len % 256 == 0)
+    return launch_beam_tc_nt<256>(b_img, a_img, n_ant, n_pix, dump_len, first, last, pow, err, st);
+  return launch_beam_tc_nt<128>(b_img, a_img, n_ant, n_pix, dump_len, first, last, pow, err, st);
 }
 
 }  // namespace chirp

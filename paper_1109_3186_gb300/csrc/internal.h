@@ -57,11 +57,12 @@ cudaError_t launch_beamform_simt(const float2* y, long long n_samp, int n_ant, i
 // ---- tensor-core beamformer (beamform_tc.cu) ----
 int beam_tc_groups(int n_ant);           // 8-wide real-K groups per head/tail part
 int beam_tc_ksteps(int n_ant);           // 16-wide MMA K steps
-long long beam_tc_tile_bytes(int n_ant); // bytes of one 128-sample B tile
-int beam_tc_tile_samples();
+int beam_tc_tile_samples(int dump_len);  // 256 when dump_len % 256 == 0, else 128
+long long beam_tc_tile_bytes(int n_ant, int dump_len);  // bytes of one B tile
 std::vector<uint8_t> build_beam_a_image(const double* W, int n_ant, int n_pix);
-cudaError_t launch_split_bf16(const float2* y, long long n_samp, int n_ant, long long t_begin,
-                              long long t_end, uint8_t* b_img, cudaStream_t st);
+cudaError_t launch_split_bf16(const float2* y, long long n_samp, int n_ant, int dump_len,
+                              long long t_begin, long long t_end, uint8_t* b_img,
+                              cudaStream_t st);
 cudaError_t launch_beam_tc(const uint8_t* b_img, const uint8_t* a_img, int n_ant, int n_pix,
                            int dump_len, long long first, long long last, float* pow, int* err,
                            cudaStream_t st);

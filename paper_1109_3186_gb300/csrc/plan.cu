@@ -356,11 +356,11 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
     for (const DmInfo& I : p->dmi)
       if (I.last >= I.first) {
         long long span = (I.last - I.first + 1) * p->L;
-        long long nt = (span + beam_tc_tile_samples() - 1) / beam_tc_tile_samples();
+        long long nt = (span + beam_tc_tile_samples(p->L) - 1) / beam_tc_tile_samples(p->L);
         max_tiles = std::max(max_tiles, nt);
       }
     rc = dev_alloc(p, (void**)&p->d_bimg, (size_t)std::max(1LL, max_tiles) *
-                                              (size_t)beam_tc_tile_bytes(p->M), "beam B image");
+                                              (size_t)beam_tc_tile_bytes(p->M, p->L), "beam B image");
     if (!rc) {
       std::vector<double> Wd((size_t)p->n_pix * p->M * 2);
       for (int q = 0; q < p->n_pix; q++) {
@@ -613,8 +613,8 @@ int chimageator_run(chirp_plan* p, const void* volt, int volt_loc, float* pow_ou
     if (tcore) {
       if (I.last < I.first) continue;
       int mk = mark_begin(p);
-      CK(launch_split_bf16(p->d_y, p->N, p->M, I.first * p->L, (I.last + 1) * p->L, p->d_bimg,
-                           p->stream));
+      CK(launch_split_bf16(p->d_y, p->N, p->M, p->L, I.first * p->L, (I.last + 1) * p->L,
+                           p->d_bimg, p->stream));
       mark_end(p, CHIRP_STAGE_SPLIT, mk);
       mk = mark_begin(p);
       CK(launch_beam_tc(p->d_bimg, p->d_aimg, p->M, p->n_pix, p->L, I.first, I.last, out,
