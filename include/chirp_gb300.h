@@ -62,13 +62,17 @@ extern "C" {
 #define CHIRP_BEAM_AUTO 0      /* tensor-core split-bf16 when available      */
 #define CHIRP_BEAM_FP32_SIMT 1 /* plain FP32 FMA on the CUDA cores           */
 #define CHIRP_BEAM_TC_3XBF16 2 /* tcgen05, 3-term bf16 split, FP32 accumulate */
+#define CHIRP_BEAM_VIS 3       /* exact identity sum_t |w.y|^2 = w^H V w: the
+                                  per-dump visibilities V (Chirpolator output)
+                                  are formed first, then a quadratic form per
+                                  pixel; FP32 CUDA cores                      */
 
 typedef struct chirp_plan chirp_plan;
 
 /* Everything that fixes the shape of a search.  All pointers are HOST
  * memory and are copied at plan creation. */
 typedef struct {
-  int n_ant;               /* M >= 1 antennas                                   */
+  int n_ant;               /* M antennas, 1..84                                  */
   const double* xyz_m;     /* [n_ant][3] positions, metres, (u,v,w) frame with w
                               towards the phase centre (App. A.1, Eq. tau3D);
                               only the Chimageator reads them (may be NULL
@@ -138,7 +142,8 @@ int chirpolator_run(chirp_plan* plan, const void* volt, int volt_loc, void* vis_
  * beamforming, Sec. 2.4.2, detected and integrated).  pow_out: float32
  * [n_dm][n_dump][n_pix].  Needs n_pix > 0 at plan creation.  With the
  * tensor-core mode the contraction runs as three BF16 products (head x head,
- * head x tail, tail x head) accumulated in FP32.  Errors: CHIRP_EINVAL,
+ * head x tail, tail x head) accumulated in FP32; with CHIRP_BEAM_VIS the same
+ * powers come from the per-dump visibility matrix (identical up to rounding).  Errors: CHIRP_EINVAL,
  * CHIRP_EUNSUPPORTED, CHIRP_ECUDA, CHIRP_ETIMEOUT (host outputs only; see
  * chirp_plan_status). */
 int chimageator_run(chirp_plan* plan, const void* volt, int volt_loc, float* pow_out, int pow_loc);

@@ -26,12 +26,12 @@ import numpy as np
 from . import _build
 
 __all__ = ["Plan", "load", "build", "CHIRP_HOST", "CHIRP_DEVICE", "BEAM_AUTO", "BEAM_FP32_SIMT",
-           "BEAM_TC_3XBF16", "ChirpError", "chirp_plan_create", "chirp_plan_destroy",
+           "BEAM_TC_3XBF16", "BEAM_VIS", "ChirpError", "chirp_plan_create", "chirp_plan_destroy",
            "chirpolator_run", "chimageator_run", "chirp_dedisperse_run", "chirp_last_error",
            "EXPORTED_SYMBOLS"]
 
 CHIRP_HOST, CHIRP_DEVICE = 0, 1
-BEAM_AUTO, BEAM_FP32_SIMT, BEAM_TC_3XBF16 = 0, 1, 2
+BEAM_AUTO, BEAM_FP32_SIMT, BEAM_TC_3XBF16, BEAM_VIS = 0, 1, 2, 3
 K_DM_DEFAULT = 4.148808e15
 
 EXPORTED_SYMBOLS = ("chirp_plan_create", "chirp_plan_destroy", "chirp_plan_query",

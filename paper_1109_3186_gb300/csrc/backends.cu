@@ -17,17 +17,19 @@
 namespace chirp {
 
 // ------------------------------------------------------------------ correlate
-// One CTA per dump.  Threads = (pair slot, time slice); each thread walks
-// the pairs slot, slot + n_slot, ... over its slice of every staged chunk.
+// One CTA per dump.  The M x M product is cut into 4 x 4 antenna tiles; each
+// thread owns one tile on or above the diagonal and a slice of the dump's
+// samples, so every staged sample value it loads feeds four complex MACs.
+// Slices are summed through shared memory at the end.
 constexpr int kCorrThreads = 256;
-constexpr int kCorrMaxPairsPerThread = 16;  // n_pair <= 4096 -> n_ant <= 90
+constexpr int kCorrTile = 4;
 
 __global__ void __launch_bounds__(kCorrThreads) k_correlate(const float2* __restrict__ y,
                                                              long long n_samp, int M, int L,
                                                              long long first, long long last,
                                                              float2* __restrict__ vis,
                                                              int chunk) {
-  extern __shared__ float2 sy[];  // [M][chunk]
+  extern __shared__ float2 sy[];  // [Mp][chunk] staged voltages, Mp = M rounded up to 4
   const long long m = blockIdx.x;
   const int n_pair = M * (M + 1) / 2;
   float2* out = vis + m * n_pair;
@@ -35,64 +37,87 @@ __global__ void __launch_bounds__(kCorrThreads) k_correlate(const float2* __rest
     for (int i = threadIdx.x; i < n_pair; i += blockDim.x) out[i] = make_float2(0.f, 0.f);
     return;
   }
-  const int n_slot = n_pair < kCorrThreads ? n_pair : kCorrThreads;
-  const int n_slice = kCorrThreads / n_slot;
-  const int slot = threadIdx.x % n_slot, slice = threadIdx.x / n_slot;
+  const int nt = (M + kCorrTile - 1) / kCorrTile;          // tiles per side
+  const int n_tiles = nt * (nt + 1) / 2;                   // tiles with ti <= tj
+  const int n_slice = kCorrThreads / n_tiles;              // >= 1 for M <= 84
+  const int tile = threadIdx.x % n_tiles, slice = threadIdx.x / n_tiles;
   const bool worker = slice < n_slice;
-  float2 acc[kCorrMaxPairsPerThread];
-  int pp_p[kCorrMaxPairsPerThread], pp_q[kCorrMaxPairsPerThread];
-  int n_mine = 0;
-  for (int k = slot; k < n_pair && n_mine < kCorrMaxPairsPerThread; k += n_slot) {
-    // invert the row-major upper-triangle index k -> (p, q)
-    int p = 0, rem = k;
-    while (rem >= M - p) {
-      rem -= M - p;
-      p++;
-    }
-    pp_p[n_mine] = p;
-    pp_q[n_mine] = p + rem;
-    acc[n_mine] = make_float2(0.f, 0.f);
-    n_mine++;
+  int ti = 0, rem = tile;
+  while (rem >= nt - ti) {
+    rem -= nt - ti;
+    ti++;
   }
+  const int tj = ti + rem;
+  const int Mp = nt * kCorrTile;
+  float2 acc[kCorrTile][kCorrTile];
+#pragma unroll
+  for (int a = 0; a < kCorrTile; a++)
+#pragma unroll
+    for (int b = 0; b < kCorrTile; b++) acc[a][b] = make_float2(0.f, 0.f);
   const long long t0 = m * L;
   for (int c0 = 0; c0 < L; c0 += chunk) {
     const int len = (L - c0) < chunk ? (L - c0) : chunk;
     __syncthreads();
-    for (int i = threadIdx.x; i < M * len; i += blockDim.x) {
+    for (int i = threadIdx.x; i < Mp * len; i += blockDim.x) {
       int a = i / len, t = i % len;
-      sy[a * chunk + t] = y[(long long)a * n_samp + t0 + c0 + t];
+      sy[a * chunk + t] = a < M ? y[(long long)a * n_samp + t0 + c0 + t] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     if (worker) {
-      for (int j = 0; j < n_mine; j++) {
-        const float2* yp = sy + pp_p[j] * chunk;
-        const float2* yq = sy + pp_q[j] * chunk;
-        float2 part = make_float2(0.f, 0.f);
-        for (int t = slice; t < len; t += n_slice) {
-          float2 u = yp[t], w = yq[t];
-          // u * conj(w)
-          part.x = fmaf(u.x, w.x, fmaf(u.y, w.y, part.x));
-          part.y = fmaf(u.y, w.x, fmaf(-u.x, w.y, part.y));
+      float2 part[kCorrTile][kCorrTile];
+#pragma unroll
+      for (int a = 0; a < kCorrTile; a++)
+#pragma unroll
+        for (int b = 0; b < kCorrTile; b++) part[a][b] = make_float2(0.f, 0.f);
+      for (int t = slice; t < len; t += n_slice) {
+        float2 u[kCorrTile], w[kCorrTile];
+#pragma unroll
+        for (int a = 0; a < kCorrTile; a++) {
+          u[a] = sy[(ti * kCorrTile + a) * chunk + t];
+          w[a] = sy[(tj * kCorrTile + a) * chunk + t];
         }
-        acc[j].x += part.x;
-        acc[j].y += part.y;
+#pragma unroll
+        for (int a = 0; a < kCorrTile; a++)
+#pragma unroll
+          for (int b = 0; b < kCorrTile; b++) {  // u_a * conj(w_b)
+            part[a][b].x = fmaf(u[a].x, w[b].x, fmaf(u[a].y, w[b].y, part[a][b].x));
+            part[a][b].y = fmaf(u[a].y, w[b].x, fmaf(-u[a].x, w[b].y, part[a][b].y));
+          }
       }
+#pragma unroll
+      for (int a = 0; a < kCorrTile; a++)
+#pragma unroll
+        for (int b = 0; b < kCorrTile; b++) {
+          acc[a][b].x += part[a][b].x;
+          acc[a][b].y += part[a][b].y;
+        }
     }
   }
-  // reduce over slices through shared memory (reuse the staging buffer)
+  // reduce the slices: red[slice][tile][4][4] in the staging buffer
   __syncthreads();
-  float2* red = sy;  // [n_slice][n_pair]
+  float2* red = sy;
   if (worker)
-    for (int j = 0; j < n_mine; j++) {
-      int k = slot + j * n_slot;
-      red[slice * n_pair + k] = acc[j];
-    }
+#pragma unroll
+    for (int a = 0; a < kCorrTile; a++)
+#pragma unroll
+      for (int b = 0; b < kCorrTile; b++)
+        red[((slice * n_tiles + tile) * kCorrTile + a) * kCorrTile + b] = acc[a][b];
   __syncthreads();
   for (int k = threadIdx.x; k < n_pair; k += blockDim.x) {
+    int p = 0, r2 = k;  // row-major upper-triangle index k -> (p, q)
+    while (r2 >= M - p) {
+      r2 -= M - p;
+      p++;
+    }
+    const int q = p + r2;
+    const int pi = p / kCorrTile, qi = q / kCorrTile;  // pi <= qi
+    const int tk = pi * nt - pi * (pi - 1) / 2 + (qi - pi);
+    const int a = p % kCorrTile, b = q % kCorrTile;
     float2 s = make_float2(0.f, 0.f);
     for (int sl = 0; sl < n_slice; sl++) {
-      s.x += red[sl * n_pair + k].x;
-      s.y += red[sl * n_pair + k].y;
+      float2 v = red[((sl * n_tiles + tk) * kCorrTile + a) * kCorrTile + b];
+      s.x += v.x;
+      s.y += v.y;
     }
     out[k] = s;
   }
@@ -101,16 +126,17 @@ __global__ void __launch_bounds__(kCorrThreads) k_correlate(const float2* __rest
 cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int dump_len,
                              long long n_dump, long long first, long long last, float2* vis,
                              cudaStream_t st) {
-  const int n_pair = n_ant * (n_ant + 1) / 2;
-  const int n_slot = n_pair < kCorrThreads ? n_pair : kCorrThreads;
-  if ((n_pair + n_slot - 1) / n_slot > kCorrMaxPairsPerThread) return cudaErrorInvalidValue;
-  const int n_slice = kCorrThreads / n_slot;
+  const int nt = (n_ant + kCorrTile - 1) / kCorrTile;
+  const int n_tiles = nt * (nt + 1) / 2;
+  if (n_tiles > kCorrThreads) return cudaErrorInvalidValue;
+  const int n_slice = kCorrThreads / n_tiles;
+  const int Mp = nt * kCorrTile;
   // staging chunk: at most 32 KB of voltages; the reduction reuses the buffer
-  int chunk = (32 * 1024) / (8 * n_ant);
+  int chunk = (32 * 1024) / (8 * Mp);
   if (chunk > dump_len) chunk = dump_len;
   if (chunk < 1) chunk = 1;
-  size_t stage = (size_t)n_ant * chunk * sizeof(float2);
-  size_t redb = (size_t)n_slice * n_pair * sizeof(float2);
+  size_t stage = (size_t)Mp * chunk * sizeof(float2);
+  size_t redb = (size_t)n_slice * n_tiles * kCorrTile * kCorrTile * sizeof(float2);
   size_t smem = stage > redb ? stage : redb;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_correlate, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -120,6 +146,56 @@ cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int d
   if (n_dump <= 0) return cudaSuccess;
   k_correlate<<<(unsigned)n_dump, kCorrThreads, smem, st>>>(y, n_samp, n_ant, dump_len, first,
                                                              last, vis, chunk);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ beams from visibilities
+// Exact identity: sum_t |sum_a W_pa y_a(t)|^2 = sum_{a,b} W_pa W_pb^* V_ab with
+// V_ab = sum_t y_a y_b^* (the correlator's output), i.e. for the packed upper
+// triangle  P_p = sum_{a<=b} Re(w_p,ab V_ab),  w_p,ab = c_ab W_pa W_pb^*,
+// c = 1 on the diagonal, 2 above it.  wpair is [n_pair][n_pix] (pixel-fastest).
+constexpr int kVisPix = 128;
+constexpr int kVisDumps = 16;
+
+__global__ void __launch_bounds__(kVisPix) k_beam_from_vis(const float2* __restrict__ V,
+                                                           const float2* __restrict__ wpair,
+                                                           int n_pair, int n_pix, long long first,
+                                                           long long last,
+                                                           float* __restrict__ pow) {
+  extern __shared__ float2 sv[];  // [kVisDumps][n_pair]
+  const long long m0 = first + (long long)blockIdx.x * kVisDumps;
+  const int nd = (int)((last + 1 - m0) < kVisDumps ? (last + 1 - m0) : kVisDumps);
+  const int p = blockIdx.y * kVisPix + threadIdx.x;
+  for (int i = threadIdx.x; i < nd * n_pair; i += blockDim.x) sv[i] = V[m0 * n_pair + i];
+  __syncthreads();
+  if (p >= n_pix) return;
+  float acc[kVisDumps];
+#pragma unroll
+  for (int d = 0; d < kVisDumps; d++) acc[d] = 0.f;
+  for (int k = 0; k < n_pair; k++) {
+    const float2 w = wpair[(long long)k * n_pix + p];
+#pragma unroll
+    for (int d = 0; d < kVisDumps; d++) {
+      const float2 v = sv[d * n_pair + k < nd * n_pair ? d * n_pair + k : 0];
+      acc[d] = fmaf(w.x, v.x, fmaf(-w.y, v.y, acc[d]));
+    }
+  }
+  for (int d = 0; d < nd; d++) pow[(m0 + d) * n_pix + p] = acc[d];
+}
+
+cudaError_t launch_beam_from_vis(const float2* V, const float2* wpair, int n_ant, int n_pix,
+                                 long long first, long long last, float* pow, cudaStream_t st) {
+  if (last < first || n_pix <= 0) return cudaSuccess;
+  const int n_pair = n_ant * (n_ant + 1) / 2;
+  const size_t smem = (size_t)kVisDumps * n_pair * sizeof(float2);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_beam_from_vis,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const long long n = last - first + 1;
+  dim3 grid((unsigned)((n + kVisDumps - 1) / kVisDumps), (n_pix + kVisPix - 1) / kVisPix);
+  k_beam_from_vis<<<grid, kVisPix, smem, st>>>(V, wpair, n_pair, n_pix, first, last, pow);
   return cudaGetLastError();
 }
 

@@ -50,6 +50,8 @@ cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, in
 cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int dump_len,
                              long long n_dump, long long first, long long last, float2* vis,
                              cudaStream_t st);
+cudaError_t launch_beam_from_vis(const float2* V, const float2* wpair, int n_ant, int n_pix,
+                                 long long first, long long last, float* pow, cudaStream_t st);
 cudaError_t launch_beamform_simt(const float2* y, long long n_samp, int n_ant, int dump_len,
                                  long long n_dump, long long first, long long last,
                                  const float2* W, int n_pix, float* pow, cudaStream_t st);

@@ -103,6 +103,8 @@ struct chirp_plan {
   uint8_t* d_aimg = nullptr; // tensor-core A image (split-BF16 weights)
   uint8_t* d_bimg = nullptr; // tensor-core B image of one DM (split-BF16 voltages)
   int* d_err = nullptr;      // device status word (bounded waits that timed out)
+  float2* d_V = nullptr;     // visibilities of one DM [n_dump][n_pair] (beam mode VIS)
+  float2* d_wpair = nullptr; // pair weights [n_pair][n_pix] (beam mode VIS)
   void* d_out = nullptr;     // staging for host outputs
   size_t out_bytes = 0;
   size_t ws_bytes = 0;
@@ -149,6 +151,8 @@ void release(chirp_plan* p) {
   cudaFree(p->d_aimg);
   cudaFree(p->d_bimg);
   cudaFree(p->d_err);
+  cudaFree(p->d_V);
+  cudaFree(p->d_wpair);
   cudaFree(p->d_out);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
 }
@@ -191,7 +195,7 @@ void collect_marks(chirp_plan* p) {
 
 int validate(const chirp_config* c) {
   if (!c) return fail(CHIRP_EINVAL, "config is NULL");
-  if (c->n_ant < 1 || c->n_ant > 90) return fail(CHIRP_EINVAL, "n_ant must be in 1..90");
+  if (c->n_ant < 1 || c->n_ant > 84) return fail(CHIRP_EINVAL, "n_ant must be in 1..84");
   if (!(c->f0_hz > 0) || !(c->bw_hz > 0) || !(c->bw_hz < 2 * c->f0_hz))
     return fail(CHIRP_EINVAL, "need f0 > 0 and 0 < bw < 2 f0");
   if (c->n_samp < 1) return fail(CHIRP_EINVAL, "n_samp must be >= 1");
@@ -211,7 +215,7 @@ int validate(const chirp_config* c) {
       double l = c->pix_lm[2 * p], m = c->pix_lm[2 * p + 1];
       if (!(l * l + m * m <= 1.0)) return fail(CHIRP_EINVAL, "pixel %d has l^2 + m^2 > 1", p);
     }
-  if (c->beam_mode < 0 || c->beam_mode > CHIRP_BEAM_TC_3XBF16)
+  if (c->beam_mode < 0 || c->beam_mode > CHIRP_BEAM_VIS)
     return fail(CHIRP_EINVAL, "unknown beam_mode");
   return CHIRP_OK;
 }
@@ -351,6 +355,36 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
     rc = dev_alloc(p, (void**)&p->d_W, (size_t)p->n_pix * p->M * sizeof(float2), "weights");
   if (!rc) rc = dev_alloc(p, (void**)&p->d_err, sizeof(int), "status word");
   std::vector<uint8_t> aimg;
+  std::vector<float2> wpair;
+  if (!rc && p->n_pix > 0 && p->beam_mode == CHIRP_BEAM_VIS) {
+    rc = dev_alloc(p, (void**)&p->d_V, (size_t)std::max(1LL, p->n_dump) * p->n_pair * sizeof(float2),
+                   "visibilities");
+    if (!rc)
+      rc = dev_alloc(p, (void**)&p->d_wpair, (size_t)p->n_pair * p->n_pix * sizeof(float2),
+                     "pair weights");
+    if (!rc) {
+      wpair.resize((size_t)p->n_pair * p->n_pix);
+      std::vector<double> wr(p->M), wi(p->M);
+      for (int q = 0; q < p->n_pix; q++) {
+        double l = p->pix[2 * q], m = p->pix[2 * q + 1];
+        double n = std::sqrt(1.0 - l * l - m * m);
+        for (int a = 0; a < p->M; a++) {
+          double tau = (p->xyz[3 * a] * l + p->xyz[3 * a + 1] * m + p->xyz[3 * a + 2] * (n - 1.0)) /
+                       kCLight;
+          double ph = 2.0 * kPi * p->f0 * tau;
+          wr[a] = std::cos(ph);
+          wi[a] = std::sin(ph);
+        }
+        int k = 0;
+        for (int a = 0; a < p->M; a++)
+          for (int b = a; b < p->M; b++, k++) {
+            const double c = a == b ? 1.0 : 2.0;  // W_a conj(W_b), doubled above the diagonal
+            wpair[(size_t)k * p->n_pix + q] = make_float2((float)(c * (wr[a] * wr[b] + wi[a] * wi[b])),
+                                                          (float)(c * (wi[a] * wr[b] - wr[a] * wi[b])));
+          }
+      }
+    }
+  }
   if (!rc && p->n_pix > 0 && p->beam_mode == CHIRP_BEAM_TC_3XBF16) {
     long long max_tiles = 0;
     for (const DmInfo& I : p->dmi)
@@ -409,6 +443,9 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   if (e == cudaSuccess && p->n_pix > 0)
     e = cudaMemcpyAsync(p->d_W, W.data(), W.size() * sizeof(float2), cudaMemcpyHostToDevice,
                         p->stream);
+  if (e == cudaSuccess && !wpair.empty())
+    e = cudaMemcpyAsync(p->d_wpair, wpair.data(), wpair.size() * sizeof(float2),
+                        cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess && !aimg.empty())
     e = cudaMemcpyAsync(p->d_aimg, aimg.data(), aimg.size(), cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
@@ -603,14 +640,25 @@ int chimageator_run(chirp_plan* p, const void* volt, int volt_loc, float* pow_ou
   rc = forward_all(p, dx);
   if (rc) return rc;
   const bool tcore = p->beam_mode == CHIRP_BEAM_TC_3XBF16;
-  // invalid dumps stay zero; the tensor-core kernel writes only valid ones
-  if (tcore) CK(cudaMemsetAsync(dp, 0, bytes, p->stream));
+  const bool vis = p->beam_mode == CHIRP_BEAM_VIS;
+  // invalid dumps stay zero; these modes write only valid ones
+  if (tcore || vis) CK(cudaMemsetAsync(dp, 0, bytes, p->stream));
   for (int d = 0; d < (int)p->dm.size(); d++) {
     rc = dedisperse_one(p, d, p->d_y);
     if (rc) return rc;
     const DmInfo& I = p->dmi[d];
     float* out = (float*)dp + d * per_dm;
-    if (tcore) {
+    if (vis) {
+      if (I.last < I.first) continue;
+      int mk = mark_begin(p);
+      CK(launch_correlate(p->d_y, p->N, p->M, p->L, p->n_dump, I.first, I.last, p->d_V,
+                          p->stream));
+      mark_end(p, CHIRP_STAGE_CORRELATE, mk);
+      mk = mark_begin(p);
+      CK(launch_beam_from_vis(p->d_V, p->d_wpair, p->M, p->n_pix, I.first, I.last, out,
+                              p->stream));
+      mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
+    } else if (tcore) {
       if (I.last < I.first) continue;
       int mk = mark_begin(p);
       CK(launch_split_bf16(p->d_y, p->N, p->M, p->L, I.first * p->L, (I.last + 1) * p->L,

@@ -19,6 +19,7 @@ torch = pytest.importorskip("torch")
     (4, 100003, 777, [0.0, 33.0], 1 << 13),     # ragged N and dump length
     (1, 1 << 15, 512, [5.0], 1 << 12),          # one antenna: autos only
     (13, 1 << 15, 256, [0.0, 9.0], 1 << 12),    # 91 pairs
+    (36, 1 << 14, 1024, [0.0, 5.0], 1 << 12),   # 666 pairs, 45 tiles of 4 x 4
 ])
 def test_chirpolator_matches_oracle(M, N, L, dms, nfft_min, k_dm):
     sc = skymodel.chirpolator_small(n_samp=N, n_dm=len(dms), n_ant=M, dm_max=max(dms),
@@ -47,8 +48,8 @@ BEAM_CASES = [
 ]
 
 
-@pytest.mark.parametrize("mode", [chirp.BEAM_FP32_SIMT, chirp.BEAM_TC_3XBF16],
-                         ids=["fp32_simt", "tc_3xbf16"])
+@pytest.mark.parametrize("mode", [chirp.BEAM_FP32_SIMT, chirp.BEAM_TC_3XBF16, chirp.BEAM_VIS],
+                         ids=["fp32_simt", "tc_3xbf16", "vis"])
 @pytest.mark.parametrize("M,N,L,n_side,dms,nfft_min", BEAM_CASES,
                          ids=["M%d_N%d_L%d_pix%d" % (c[0], c[1], c[2], c[3] ** 2) for c in BEAM_CASES])
 def test_chimageator_matches_oracle(M, N, L, n_side, dms, nfft_min, mode, k_dm):
