@@ -240,7 +240,13 @@ def stage_roofline(sc, plan, stage_ms, peaks, peak_kind, beam_mode, steps):
     # split: read M complex64 + write the BF16 head/tail image (4 antennas per 16 B row pair)
     split_bytes = float(n_dump_valid) * L * (8 * M + 32 * ((M + 3) // 4))
     stages["split"] = ("hbm", split_bytes, hbm, "GB/s")
-    if beam_mode == 1:
+    n_pair = M * (M + 1) // 2
+    # correlate: read the dedispersed voltages of every valid dump, write V
+    stages["correlate"] = ("hbm", float(n_dump_valid) * (L * 8 * M + 8 * n_pair), hbm, "GB/s")
+    if beam_mode == 3:
+        # beams from visibilities: 2 FMA per (pair, pixel, dump)
+        stages["beamform"] = ("alu", 4.0 * n_pair * n_pix * n_dump_valid, fp32_tflops, "TFLOP/s")
+    elif beam_mode == 1:
         stages["beamform"] = ("alu", beam_flops, fp32_tflops, "TFLOP/s")
     else:
         stages["beamform"] = ("tensor", beam_flops,

@@ -17,109 +17,90 @@
 namespace chirp {
 
 // ------------------------------------------------------------------ correlate
-// One CTA per dump.  The M x M product is cut into 4 x 4 antenna tiles; each
-// thread owns one tile on or above the diagonal and a slice of the dump's
-// samples, so every staged sample value it loads feeds four complex MACs.
-// Slices are summed through shared memory at the end.
-constexpr int kCorrThreads = 256;
+// The M x M product is cut into 4 x 4 antenna tiles on or above the diagonal.
+// One warp owns one tile of one dump: lane l walks the samples l, l + 32, ...
+// (consecutive lanes read consecutive samples, so every antenna row is read
+// with full coalescing), keeps the 16 complex products of the tile in
+// registers, and the 32 lane partials are summed with warp shuffles.  The
+// warps of a CTA work on the same dump, so the antenna rows they share come
+// from L1.
 constexpr int kCorrTile = 4;
+constexpr int kCorrWarps = 8;
 
-__global__ void __launch_bounds__(kCorrThreads) k_correlate(const float2* __restrict__ y,
-                                                             long long n_samp, int M, int L,
-                                                             long long first, long long last,
-                                                             float2* __restrict__ vis,
-                                                             int chunk) {
-  extern __shared__ float2 sy[];  // [Mp][chunk] staged voltages, Mp = M rounded up to 4
+__global__ void __launch_bounds__(32 * kCorrWarps) k_correlate(const float2* __restrict__ y,
+                                                                long long n_samp, int M, int L,
+                                                                long long first, long long last,
+                                                                float2* __restrict__ vis) {
   const long long m = blockIdx.x;
   const int n_pair = M * (M + 1) / 2;
   float2* out = vis + m * n_pair;
   if (m < first || m > last) {
-    for (int i = threadIdx.x; i < n_pair; i += blockDim.x) out[i] = make_float2(0.f, 0.f);
+    if (blockIdx.y == 0)
+      for (int i = threadIdx.x; i < n_pair; i += blockDim.x) out[i] = make_float2(0.f, 0.f);
     return;
   }
-  const int nt = (M + kCorrTile - 1) / kCorrTile;          // tiles per side
-  const int n_tiles = nt * (nt + 1) / 2;                   // tiles with ti <= tj
-  const int n_slice = kCorrThreads / n_tiles;              // >= 1 for M <= 84
-  const int tile = threadIdx.x % n_tiles, slice = threadIdx.x / n_tiles;
-  const bool worker = slice < n_slice;
+  const int nt = (M + kCorrTile - 1) / kCorrTile;
+  const int n_tiles = nt * (nt + 1) / 2;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int tile = blockIdx.y * kCorrWarps + warp;
+  if (tile >= n_tiles) return;
   int ti = 0, rem = tile;
   while (rem >= nt - ti) {
     rem -= nt - ti;
     ti++;
   }
   const int tj = ti + rem;
-  const int Mp = nt * kCorrTile;
+  const float2* yi[kCorrTile];
+  const float2* yj[kCorrTile];
+  bool vi[kCorrTile], vj[kCorrTile];
+#pragma unroll
+  for (int a = 0; a < kCorrTile; a++) {
+    const int ai = ti * kCorrTile + a, aj = tj * kCorrTile + a;
+    vi[a] = ai < M;
+    vj[a] = aj < M;
+    yi[a] = y + (long long)(vi[a] ? ai : 0) * n_samp + m * L;
+    yj[a] = y + (long long)(vj[a] ? aj : 0) * n_samp + m * L;
+  }
   float2 acc[kCorrTile][kCorrTile];
 #pragma unroll
   for (int a = 0; a < kCorrTile; a++)
 #pragma unroll
     for (int b = 0; b < kCorrTile; b++) acc[a][b] = make_float2(0.f, 0.f);
-  const long long t0 = m * L;
-  for (int c0 = 0; c0 < L; c0 += chunk) {
-    const int len = (L - c0) < chunk ? (L - c0) : chunk;
-    __syncthreads();
-    for (int i = threadIdx.x; i < Mp * len; i += blockDim.x) {
-      int a = i / len, t = i % len;
-      sy[a * chunk + t] = a < M ? y[(long long)a * n_samp + t0 + c0 + t] : make_float2(0.f, 0.f);
+  for (int t = lane; t < L; t += 32) {
+    float2 u[kCorrTile], w[kCorrTile];
+#pragma unroll
+    for (int a = 0; a < kCorrTile; a++) {
+      u[a] = vi[a] ? __ldg(yi[a] + t) : make_float2(0.f, 0.f);
+      w[a] = vj[a] ? __ldg(yj[a] + t) : make_float2(0.f, 0.f);
     }
-    __syncthreads();
-    if (worker) {
-      float2 part[kCorrTile][kCorrTile];
-#pragma unroll
-      for (int a = 0; a < kCorrTile; a++)
-#pragma unroll
-        for (int b = 0; b < kCorrTile; b++) part[a][b] = make_float2(0.f, 0.f);
-      for (int t = slice; t < len; t += n_slice) {
-        float2 u[kCorrTile], w[kCorrTile];
-#pragma unroll
-        for (int a = 0; a < kCorrTile; a++) {
-          u[a] = sy[(ti * kCorrTile + a) * chunk + t];
-          w[a] = sy[(tj * kCorrTile + a) * chunk + t];
-        }
-#pragma unroll
-        for (int a = 0; a < kCorrTile; a++)
-#pragma unroll
-          for (int b = 0; b < kCorrTile; b++) {  // u_a * conj(w_b)
-            part[a][b].x = fmaf(u[a].x, w[b].x, fmaf(u[a].y, w[b].y, part[a][b].x));
-            part[a][b].y = fmaf(u[a].y, w[b].x, fmaf(-u[a].x, w[b].y, part[a][b].y));
-          }
-      }
-#pragma unroll
-      for (int a = 0; a < kCorrTile; a++)
-#pragma unroll
-        for (int b = 0; b < kCorrTile; b++) {
-          acc[a][b].x += part[a][b].x;
-          acc[a][b].y += part[a][b].y;
-        }
-    }
-  }
-  // reduce the slices: red[slice][tile][4][4] in the staging buffer
-  __syncthreads();
-  float2* red = sy;
-  if (worker)
 #pragma unroll
     for (int a = 0; a < kCorrTile; a++)
 #pragma unroll
-      for (int b = 0; b < kCorrTile; b++)
-        red[((slice * n_tiles + tile) * kCorrTile + a) * kCorrTile + b] = acc[a][b];
-  __syncthreads();
-  for (int k = threadIdx.x; k < n_pair; k += blockDim.x) {
-    int p = 0, r2 = k;  // row-major upper-triangle index k -> (p, q)
-    while (r2 >= M - p) {
-      r2 -= M - p;
-      p++;
-    }
-    const int q = p + r2;
-    const int pi = p / kCorrTile, qi = q / kCorrTile;  // pi <= qi
-    const int tk = pi * nt - pi * (pi - 1) / 2 + (qi - pi);
-    const int a = p % kCorrTile, b = q % kCorrTile;
-    float2 s = make_float2(0.f, 0.f);
-    for (int sl = 0; sl < n_slice; sl++) {
-      float2 v = red[((sl * n_tiles + tk) * kCorrTile + a) * kCorrTile + b];
-      s.x += v.x;
-      s.y += v.y;
-    }
-    out[k] = s;
+      for (int b = 0; b < kCorrTile; b++) {  // u_a * conj(w_b)
+        acc[a][b].x = fmaf(u[a].x, w[b].x, fmaf(u[a].y, w[b].y, acc[a][b].x));
+        acc[a][b].y = fmaf(u[a].y, w[b].x, fmaf(-u[a].x, w[b].y, acc[a][b].y));
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < kCorrTile; a++)
+#pragma unroll
+    for (int b = 0; b < kCorrTile; b++)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        acc[a][b].x += __shfl_xor_sync(0xffffffffu, acc[a][b].x, o);
+        acc[a][b].y += __shfl_xor_sync(0xffffffffu, acc[a][b].y, o);
+      }
+  // lane a*4+b writes pair (ti*4+a, tj*4+b) if it is in the upper triangle
+  if (lane < kCorrTile * kCorrTile) {
+    const int a = lane / kCorrTile, b = lane % kCorrTile;
+    const int p = ti * kCorrTile + a, q = tj * kCorrTile + b;
+    float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int aa = 0; aa < kCorrTile; aa++)
+#pragma unroll
+      for (int bb = 0; bb < kCorrTile; bb++)
+        if (aa == a && bb == b) v = acc[aa][bb];
+    if (p < M && q < M && p <= q) out[p * M - p * (p - 1) / 2 + (q - p)] = v;
   }
 }
 
@@ -128,24 +109,9 @@ cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int d
                              cudaStream_t st) {
   const int nt = (n_ant + kCorrTile - 1) / kCorrTile;
   const int n_tiles = nt * (nt + 1) / 2;
-  if (n_tiles > kCorrThreads) return cudaErrorInvalidValue;
-  const int n_slice = kCorrThreads / n_tiles;
-  const int Mp = nt * kCorrTile;
-  // staging chunk: at most 32 KB of voltages; the reduction reuses the buffer
-  int chunk = (32 * 1024) / (8 * Mp);
-  if (chunk > dump_len) chunk = dump_len;
-  if (chunk < 1) chunk = 1;
-  size_t stage = (size_t)Mp * chunk * sizeof(float2);
-  size_t redb = (size_t)n_slice * n_tiles * kCorrTile * kCorrTile * sizeof(float2);
-  size_t smem = stage > redb ? stage : redb;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_correlate, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-  }
   if (n_dump <= 0) return cudaSuccess;
-  k_correlate<<<(unsigned)n_dump, kCorrThreads, smem, st>>>(y, n_samp, n_ant, dump_len, first,
-                                                             last, vis, chunk);
+  dim3 grid((unsigned)n_dump, (n_tiles + kCorrWarps - 1) / kCorrWarps);
+  k_correlate<<<grid, 32 * kCorrWarps, 0, st>>>(y, n_samp, n_ant, dump_len, first, last, vis);
   return cudaGetLastError();
 }
 
