@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(32 * kCorrWarps) k_correlate(const float2* __r
   const int nt = (M + kCorrTile - 1) / kCorrTile;
   const int n_tiles = nt * (nt + 1) / 2;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int tile = blockIdx.y * kCorrWarps + warp;
+  const int tile = blockIdx.y * (blockDim.x / 32) + warp;
   if (tile >= n_tiles) return;
   int ti = 0, rem = tile;
   while (rem >= nt - ti) {
@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(32 * kCorrWarps) k_correlate(const float2* __r
   for (int a = 0; a < kCorrTile; a++)
 #pragma unroll
     for (int b = 0; b < kCorrTile; b++) acc[a][b] = make_float2(0.f, 0.f);
+#pragma unroll 4
   for (int t = lane; t < L; t += 32) {
     float2 u[kCorrTile], w[kCorrTile];
 #pragma unroll
@@ -110,8 +111,9 @@ cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int d
   const int nt = (n_ant + kCorrTile - 1) / kCorrTile;
   const int n_tiles = nt * (nt + 1) / 2;
   if (n_dump <= 0) return cudaSuccess;
-  dim3 grid((unsigned)n_dump, (n_tiles + kCorrWarps - 1) / kCorrWarps);
-  k_correlate<<<grid, 32 * kCorrWarps, 0, st>>>(y, n_samp, n_ant, dump_len, first, last, vis);
+  const int warps = n_tiles < kCorrWarps ? n_tiles : kCorrWarps;
+  dim3 grid((unsigned)n_dump, (n_tiles + warps - 1) / warps);
+  k_correlate<<<grid, 32 * warps, 0, st>>>(y, n_samp, n_ant, dump_len, first, last, vis);
   return cudaGetLastError();
 }
 

@@ -118,7 +118,7 @@ template <int L>
 __global__ void __launch_bounds__(256, 4) k_inv_rows(const float2* __restrict__ spec,
                                                   float2* __restrict__ Z,
                                                   const float2* __restrict__ H, int n1,
-                                                  int log2n, TwiddlePtrs twp) {
+                                                  int log2n, long long q0, TwiddlePtrs twp) {
   constexpr int C = 4096 / L;
   constexpr int T = L / 16;
   __shared__ float2 sm[FftTile<L, C>::SLOTS];
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256, 4) k_inv_rows(const float2* __restrict__ 
   const int k1 = blockIdx.x * C + s;
   const bool act = k1 < n1;
   const long long nfft = (long long)L * n1;
-  const long long q = blockIdx.y;
+  const long long q = q0 + blockIdx.y;  // sequence; Z holds the chunk only
   const float2* src = spec + q * nfft + (long long)k1 * L;
   const float2* h = H + (long long)k1 * L;
   float2 v[16];
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(256, 4) k_inv_rows(const float2* __restrict__ 
     v[k] = act ? cmul(src[jt + k * T], __ldg(h + jt + k * T)) : make_float2(0.f, 0.f);
   fft_core<L, C, true, true>(v, sm, s, jt, tw);
   if (!act) return;
-  float2* dst = Z + q * nfft + (long long)k1 * L;
+  float2* dst = Z + (long long)blockIdx.y * nfft + (long long)k1 * L;
   // twiddle W_N^(-k1 n2), n2 = jt + k T
   twiddle_run<true>(v, (unsigned)k1, (unsigned)jt, (unsigned)T, log2n, tw);
 #pragma unroll
@@ -150,7 +150,8 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ 
                                                   float2* __restrict__ y, long long n_samp,
                                                   int n2, long long step, long long n_blk,
                                                   long long n_hi, long long n_lo,
-                                                  long long n_hi_max, TwiddlePtrs twp) {
+                                                  long long n_hi_max, long long q0,
+                                                  TwiddlePtrs twp) {
   constexpr int C = 4096 / L;
   constexpr int T = L / 16;
   __shared__ float2 sm[FftTile<L, C>::SLOTS];
@@ -158,10 +159,10 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ 
   const int s = threadIdx.x % C, jt = threadIdx.x / C;
   const int c = blockIdx.x * C + s;
   const bool act = c < n2;
-  const long long q = blockIdx.y;
+  const long long q = q0 + blockIdx.y;  // sequence; Z holds the chunk only
   const long long a = q / n_blk, b = q % n_blk;
   const long long nfft = (long long)L * n2;
-  const float2* src = Z + q * nfft;
+  const float2* src = Z + (long long)blockIdx.y * nfft;
   float2 v[16];
 #pragma unroll
   for (int k = 0; k < 16; k++)
@@ -226,15 +227,15 @@ cudaError_t launch_chirp_table(const double* G, float2* H, double dm, const Grou
   return cudaGetLastError();
 }
 
-cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, int n_ant,
-                                const GroupGeom& g, TwiddlePtrs tw, cudaStream_t st) {
-  const long long n_seq = (long long)n_ant * g.n_blk;
-  if (n_seq > 65535) return cudaErrorInvalidConfiguration;
+cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, long long q0,
+                                long long nq, const GroupGeom& g, TwiddlePtrs tw,
+                                cudaStream_t st) {
+  if (nq > 65535 || nq < 1) return cudaErrorInvalidConfiguration;
   const int C = 4096 / g.n2;
-  dim3 grid((g.n1 + C - 1) / C, (unsigned)n_seq);
+  dim3 grid((g.n1 + C - 1) / C, (unsigned)nq);
   switch (g.n2) {
 #define X(L) \
-  case L: k_inv_rows<L><<<grid, 256, 0, st>>>(spec, Z, H, g.n1, g.log2n, tw); break;
+  case L: k_inv_rows<L><<<grid, 256, 0, st>>>(spec, Z, H, g.n1, g.log2n, q0, tw); break;
     CHIRP_SIZES(X)
 #undef X
     default: return cudaErrorInvalidValue;
@@ -242,21 +243,27 @@ cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, int n_ant,
-                                const GroupGeom& g, long long n_hi, long long n_lo,
+cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, long long q0,
+                                long long nq, const GroupGeom& g, long long n_hi, long long n_lo,
                                 TwiddlePtrs tw, cudaStream_t st) {
-  const long long n_seq = (long long)n_ant * g.n_blk;
-  if (n_seq > 65535) return cudaErrorInvalidConfiguration;
+  if (nq > 65535 || nq < 1) return cudaErrorInvalidConfiguration;
   const int C = 4096 / g.n1;
-  dim3 grid((g.n2 + C - 1) / C, (unsigned)n_seq);
+  dim3 grid((g.n2 + C - 1) / C, (unsigned)nq);
   switch (g.n1) {
 #define X(L) \
-  case L: k_inv_cols<L><<<grid, 256, 0, st>>>(Z, y, n_samp, g.n2, g.step, g.n_blk, n_hi, n_lo, g.n_hi_max, tw); break;
+  case L: k_inv_cols<L><<<grid, 256, 0, st>>>(Z, y, n_samp, g.n2, g.step, g.n_blk, n_hi, n_lo, g.n_hi_max, q0, tw); break;
     CHIRP_SIZES(X)
 #undef X
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+long long inverse_chunk_sequences(const GroupGeom& g, long long n_seq) {
+  long long nq = kInverseChunkBytes / (g.nfft * (long long)sizeof(float2));
+  if (nq < 1) nq = 1;
+  if (nq > n_seq) nq = n_seq;
+  return nq;
 }
 
 }  // namespace chirp

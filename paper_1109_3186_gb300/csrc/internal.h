@@ -38,12 +38,21 @@ cudaError_t launch_build_phase_table(double* G, const GroupGeom& g, double f0, d
 // H[pos] = exp(-2 pi j frac(dm G[pos])), FP64 phase, FP32 complex result
 cudaError_t launch_chirp_table(const double* G, float2* H, double dm, const GroupGeom& g,
                                cudaStream_t st);
-// Z = rows of IFFT after the chirp multiply and the inter-pass twiddle
-cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, int n_ant,
-                                const GroupGeom& g, TwiddlePtrs tw, cudaStream_t st);
-// y[a][t] = dedispersed voltage for every owned, valid t (other t untouched)
-cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, int n_ant,
-                                const GroupGeom& g, long long n_hi, long long n_lo,
+// The inverse runs over chunks of (antenna, block) sequences [q0, q0 + nq):
+// Z holds one chunk (nq x nfft) so that the row pass's output is still in L2
+// when the column pass reads it.
+#ifndef CHIRP_INVERSE_CHUNK_BYTES
+#define CHIRP_INVERSE_CHUNK_BYTES (32LL << 20)
+#endif
+constexpr long long kInverseChunkBytes = CHIRP_INVERSE_CHUNK_BYTES;
+long long inverse_chunk_sequences(const GroupGeom& g, long long n_seq);
+// Z[0 .. nq) = rows of IFFT of sequences q0.. after the chirp multiply and twiddle
+cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, long long q0,
+                                long long nq, const GroupGeom& g, TwiddlePtrs tw,
+                                cudaStream_t st);
+// y[a][t] = dedispersed voltage for every owned, valid t of sequences q0.. (other t untouched)
+cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, long long q0,
+                                long long nq, const GroupGeom& g, long long n_hi, long long n_lo,
                                 TwiddlePtrs tw, cudaStream_t st);
 
 // ---- back-ends (backends.cu) ----

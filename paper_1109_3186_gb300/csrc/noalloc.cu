@@ -170,9 +170,10 @@ extern "C" int chirp_dedisperse_noalloc(const void* volt, int n_ant, long long n
   if (e == cudaSuccess)
     e = cudaMemsetAsync(y_out, 0, (size_t)n_ant * (size_t)n_samp * sizeof(float2), st);
   if (e == cudaSuccess) e = launch_chirp_table(G, H, dm, g, st);
-  if (e == cudaSuccess) e = launch_inverse_rows(spec, Z, H, n_ant, g, tw, st);
+  const long long n_seq = (long long)n_ant * g.n_blk;
+  if (e == cudaSuccess) e = launch_inverse_rows(spec, Z, H, 0, n_seq, g, tw, st);
   if (e == cudaSuccess)
-    e = launch_inverse_cols(Z, (float2*)y_out, n_samp, n_ant, g, n_hi, n_lo, tw, st);
+    e = launch_inverse_cols(Z, (float2*)y_out, n_samp, 0, n_seq, g, n_hi, n_lo, tw, st);
   if (e != cudaSuccess) {
     snprintf(g_msg, sizeof g_msg, "chirp_dedisperse_noalloc: launch failed: %s",
              cudaGetErrorString(e));

@@ -342,7 +342,8 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   size_t z_elems = 0;
   for (auto& g : p->groups) {
     size_t elems = (size_t)p->M * g.geom.n_blk * g.geom.nfft;
-    z_elems = std::max(z_elems, elems);
+    z_elems = std::max(z_elems, (size_t)inverse_chunk_sequences(g.geom, (long long)p->M * g.geom.n_blk) *
+                                    (size_t)g.geom.nfft);
     if (!rc) rc = dev_alloc(p, (void**)&g.d_spec, elems * sizeof(float2), "spectra");
     if (!rc) rc = dev_alloc(p, (void**)&g.d_G, g.geom.nfft * sizeof(double), "phase table");
   }
@@ -566,12 +567,17 @@ int dedisperse_one(chirp_plan* p, int d, float2* y) {
   int mk = mark_begin(p);
   CK(launch_chirp_table(g.d_G, p->d_H, p->dm[d], g.geom, p->stream));
   mark_end(p, CHIRP_STAGE_CHIRP, mk);
-  mk = mark_begin(p);
-  CK(launch_inverse_rows(g.d_spec, p->d_Z, p->d_H, p->M, g.geom, p->tw(), p->stream));
-  mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
-  mk = mark_begin(p);
-  CK(launch_inverse_cols(p->d_Z, y, p->N, p->M, g.geom, I.n_hi, I.n_lo, p->tw(), p->stream));
-  mark_end(p, CHIRP_STAGE_INV_COLS, mk);
+  const long long n_seq = (long long)p->M * g.geom.n_blk;
+  const long long nq = inverse_chunk_sequences(g.geom, n_seq);
+  for (long long q0 = 0; q0 < n_seq; q0 += nq) {
+    const long long n = std::min(nq, n_seq - q0);
+    mk = mark_begin(p);
+    CK(launch_inverse_rows(g.d_spec, p->d_Z, p->d_H, q0, n, g.geom, p->tw(), p->stream));
+    mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
+    mk = mark_begin(p);
+    CK(launch_inverse_cols(p->d_Z, y, p->N, q0, n, g.geom, I.n_hi, I.n_lo, p->tw(), p->stream));
+    mark_end(p, CHIRP_STAGE_INV_COLS, mk);
+  }
   return CHIRP_OK;
 }
 
