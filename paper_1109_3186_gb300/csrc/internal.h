@@ -38,11 +38,13 @@ cudaError_t launch_build_phase_table(double* G, const GroupGeom& g, double f0, d
 // H[pos] = exp(-2 pi j frac(dm G[pos])), FP64 phase, FP32 complex result
 cudaError_t launch_chirp_table(const double* G, float2* H, double dm, const GroupGeom& g,
                                cudaStream_t st);
-// The inverse runs over chunks of (antenna, block) sequences [q0, q0 + nq):
+// The inverse can run over chunks of (antenna, block) sequences [q0, q0 + nq)
+// (measured: separate launches per L2-sized chunk lose more to kernel ramp-up
+// than they save, so the default chunk is the whole group):
 // Z holds one chunk (nq x nfft) so that the row pass's output is still in L2
 // when the column pass reads it.
 #ifndef CHIRP_INVERSE_CHUNK_BYTES
-#define CHIRP_INVERSE_CHUNK_BYTES (32LL << 20)
+#define CHIRP_INVERSE_CHUNK_BYTES (1LL << 40)
 #endif
 constexpr long long kInverseChunkBytes = CHIRP_INVERSE_CHUNK_BYTES;
 long long inverse_chunk_sequences(const GroupGeom& g, long long n_seq);
