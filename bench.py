@@ -61,6 +61,30 @@ def parse_args():
     return ap.parse_args()
 
 
+def committed_traffic(kernel_files, key):
+    """Per-unit DRAM traffic of a kernel from its committed ncu summary, or None
+    when the kernel's source changed since that capture (hash mismatch)."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in kernel_files:
+        with open(os.path.join(ROOT, "paper_1109_3186_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    cur = h.hexdigest()[:16]
+    for fn in sorted(os.listdir(os.path.join(ROOT, "profiles"))):
+        if not fn.endswith(".md"):
+            continue
+        txt = open(os.path.join(ROOT, "profiles", fn)).read()
+        m = re.search(r"^(traffic_per_\w+): " + re.escape(key) + r": ([0-9.]+)", txt, re.M)
+        if not m:
+            continue
+        sha = re.search(r"Source hash[^`]*`([0-9a-f]+)`", txt)
+        if sha and sha.group(1) == cur:
+            return float(m.group(2))
+        return None
+    return None
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -364,9 +388,18 @@ def run_ours(args):
             line["e2e"] = e2e
         if dom:
             r = roof[dom]
+            traffic = None
+            if dom == "beamform" and plan.info["beam_mode"] == 2:
+                per = committed_traffic(["beamform_tc.cu", "tc.cuh"], "k_beam_tc<256>")
+                if per is not None:  # bytes per valid-dump DM*sample x samples per launch
+                    traffic = per * beam_dumps / n_pix * sc.dump_len / n_dm
+            elif dom == "inv_rows":
+                per = committed_traffic(["dedisperse.cu", "fft.cuh"], "k_inv_rows<4096>")
+                if per is not None:
+                    traffic = per * plan.info["ifft_points"] / n_dm
             line["roofline"] = {"kernel": dom, "bound": r["bound"], "achieved": r["achieved"],
                                 "peak": r["peak"], "unit": r["unit"], "frac": r["frac"],
-                                "traffic": None, "peak_source": r["peak_source"]}
+                                "traffic": traffic, "peak_source": r["peak_source"]}
             line["stages"] = roof
         if not args.no_cpu_baseline:
             u, dt, cores, text = cpu_sample(sc, x, args.cpu_dumps)
