@@ -88,6 +88,11 @@ typedef struct {
   const double* pix_lm;    /* [n_pix][2] beam direction cosines (l, m), or NULL */
   int n_pix;               /* 0 when no Chimageator runs are wanted             */
   int beam_mode;           /* CHIRP_BEAM_*                                      */
+  /* incoherent filterbank search (chirp_incoherent_run); fb_chan = 0: off    */
+  int fb_chan;             /* channels per antenna, power of two 16..4096       */
+  int fb_int;              /* spectra integrated per filterbank sample, >= 1    */
+  const double* fb_dm;     /* [fb_n_dm] trial DMs of the incoherent search      */
+  int fb_n_dm;
 } chirp_config;
 
 typedef struct {
@@ -98,6 +103,7 @@ typedef struct {
   long long ifft_points;   /* sum over DMs of n_ant * n_blk * Nfft              */
   long long valid_samples; /* sum over DMs of n_ant * (n_samp - n_hi - n_lo)^+  */
   int beam_mode;           /* CHIRP_BEAM_* actually used (AUTO resolved)        */
+  long long fb_samples;    /* T_fb of the incoherent search (0 when off)        */
 } chirp_plan_info;
 
 /* Create a plan: validates cfg, derives the per-DM FFT lengths and block
@@ -148,6 +154,22 @@ int chirpolator_run(chirp_plan* plan, const void* volt, int volt_loc, void* vis_
  * chirp_plan_status). */
 int chimageator_run(chirp_plan* plan, const void* volt, int volt_loc, float* pow_out, int pow_loc);
 
+/* Antenna-incoherent search (Sec. 2.3.1 incoherent dedispersion of the power
+ * beam of Sec. 2.4.1), the cheap stage that proposes where the coherent path
+ * should look.  Each antenna's series is cut into blocks of fb_chan samples
+ * and transformed (e^{-2 pi j n k / L}); channels are in ascending frequency
+ * f_c = f0 + (c - fb_chan/2) B / fb_chan; |X|^2 is summed over antennas and
+ * fb_int blocks:  S[c][tau], tau < T_fb = floor(n_samp / (fb_chan fb_int)).
+ * Then D[d][t] = sum_c S[c][t + s_c(d)] with the Eq. dmdelay lag relative to
+ * f0 in filterbank samples, s_c = floor(k DM (f_c^-2 - f0^-2) / t_fb + 1/2),
+ * t_fb = fb_chan fb_int / B; D is zero outside [-min s, T_fb - max s).
+ *  volt: complex64 [n_ant][n_samp] at volt_loc (not modified);
+ *  S_out: float32 [fb_chan][T_fb] or NULL;  D_out: float32 [fb_n_dm][T_fb];
+ *  both at out_loc.  Needs fb_chan > 0 at plan creation.
+ * Errors: CHIRP_EINVAL, CHIRP_EUNSUPPORTED, CHIRP_ECUDA. */
+int chirp_incoherent_run(chirp_plan* plan, const void* volt, int volt_loc, float* S_out,
+                         float* D_out, int out_loc);
+
 /* Per-stage device time.  Stages: */
 #define CHIRP_STAGE_FORWARD 0   /* forward FFT passes of every group            */
 #define CHIRP_STAGE_INV_ROWS 1  /* chirp multiply + inverse row pass, per DM    */
@@ -156,7 +178,8 @@ int chimageator_run(chirp_plan* plan, const void* volt, int volt_loc, float* pow
 #define CHIRP_STAGE_BEAMFORM 4  /* Chimageator back-end, per DM                 */
 #define CHIRP_STAGE_SPLIT 5     /* BF16 head/tail split of the voltages, per DM */
 #define CHIRP_STAGE_CHIRP 6     /* FP64-phase chirp table H_DM, per DM           */
-#define CHIRP_N_STAGES 7
+#define CHIRP_STAGE_INCOHERENT 7 /* filterbank + incoherent dedispersion        */
+#define CHIRP_N_STAGES 8
 /* Returns the milliseconds and launch counts accumulated per stage since the
  * previous call (ms, launches: host arrays of CHIRP_N_STAGES, either may be
  * NULL), resets them, and switches event timing on (enable != 0) or off for

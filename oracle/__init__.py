@@ -75,6 +75,10 @@ def _load():
                                             _i, _ip, _i, _ll, _ll, _dp]
             lib.orc_chimageator.restype = _i
             lib.orc_num_threads.restype = _i
+            lib.orc_filterbank.argtypes = [_dp, _i, _ll, _i, _i, _dp]
+            lib.orc_channel_shift.argtypes = [_d, _d, _d, _d, _i, _i, _i]
+            lib.orc_channel_shift.restype = _ll
+            lib.orc_incoherent.argtypes = [_dp, _i, _ll, _d, _d, _d, _i, _dp, _i, _dp]
             _lib = lib
     return _lib
 
@@ -218,3 +222,27 @@ def chimageator(x, f0, bw, k_dm, dms, nfft_min, dump_len, xyz, pix_lm, d_sel=Non
     if rc:
         raise ValueError("orc_chimageator failed (%d)" % rc)
     return P
+
+
+def filterbank(x, n_chan, n_int) -> np.ndarray:
+    """Power-beam filterbank S [n_chan, T_fb] (ascending channel frequency)."""
+    xx = _c128(np.atleast_2d(x))
+    n_ant, n_samp = xx.shape
+    T = n_samp // (n_chan * n_int)
+    S = np.empty((n_chan, T), dtype=np.float64)
+    _load().orc_filterbank(_ptr(xx), n_ant, n_samp, n_chan, n_int, _ptr(S))
+    return S
+
+
+def channel_shift(f0, bw, k_dm, dm, n_chan, n_int, c) -> int:
+    return int(_load().orc_channel_shift(f0, bw, k_dm, dm, n_chan, n_int, c))
+
+
+def incoherent(S, f0, bw, k_dm, n_int, dms) -> np.ndarray:
+    """Incoherent dedispersion D [n_dm, T_fb] of a filterbank S [n_chan, T_fb]."""
+    SS = _f64(S)
+    n_chan, T = SS.shape
+    dd = _f64(dms)
+    D = np.empty((dd.size, T), dtype=np.float64)
+    _load().orc_incoherent(_ptr(SS), n_chan, T, f0, bw, k_dm, n_int, _ptr(dd), dd.size, _ptr(D))
+    return D

@@ -434,3 +434,69 @@ int orc_chimageator(const double* x, int n_ant, long long n_samp, double f0, dou
   free(W);
   return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Incoherent path: power-beam filterbank + shift-and-sum dedispersion */
+/* ------------------------------------------------------------------ */
+
+/* Filterbank power of the power beam (Sec. 2.3.1 with power beams, Sec. 2.4.1):
+ * each antenna's series is cut into blocks of n_chan samples and transformed
+ * (e^{-2 pi j n k / n_chan}); channel c holds bin k = (c + n_chan/2) mod n_chan,
+ * i.e. ascending frequency f_c = f0 + (c - n_chan/2) B / n_chan.  The squared
+ * magnitudes are summed over antennas and over n_int consecutive blocks:
+ *   S[c][tau] = sum_a sum_{i < n_int} |X_{a, tau n_int + i}[k(c)]|^2,
+ * tau < T_fb = floor(n_samp / (n_chan n_int)).  S is [n_chan][T_fb]. */
+void orc_filterbank(const double* xin, int n_ant, long long n_samp, int n_chan, int n_int,
+                    double* S) {
+  const cplx* x = (const cplx*)xin;
+  long long T_fb = n_samp / ((long long)n_chan * n_int);
+  memset(S, 0, sizeof(double) * (size_t)n_chan * (size_t)T_fb);
+#pragma omp parallel for schedule(static)
+  for (long long tau = 0; tau < T_fb; tau++) {
+    cplx* X = (cplx*)malloc(sizeof(cplx) * (size_t)n_chan);
+    for (int a = 0; a < n_ant; a++) {
+      for (int i = 0; i < n_int; i++) {
+        const cplx* blk = x + (size_t)a * n_samp + (size_t)(tau * n_int + i) * n_chan;
+        orc_dft((const double*)blk, (double*)X, n_chan, -1);
+        for (int c = 0; c < n_chan; c++) {
+          int k = (c + n_chan / 2) % n_chan;
+          S[(size_t)c * T_fb + tau] += creal(X[k]) * creal(X[k]) + cimag(X[k]) * cimag(X[k]);
+        }
+      }
+    }
+    free(X);
+  }
+}
+
+/* Channel delay of DM in filterbank samples, relative to f0 (Eq. dmdelay):
+ * s_c = floor(k DM (f_c^-2 - f0^-2) / t_fb + 1/2), t_fb = n_chan n_int / B. */
+long long orc_channel_shift(double f0, double bw, double k_dm, double dm, int n_chan, int n_int,
+                            int c) {
+  double fc = f0 + (double)(c - n_chan / 2) * bw / (double)n_chan;
+  double t_fb = (double)n_chan * (double)n_int / bw;
+  double tau = k_dm * dm * (1.0 / (fc * fc) - 1.0 / (f0 * f0));
+  return (long long)floor(tau / t_fb + 0.5);
+}
+
+/* Incoherent dedispersion (Sec. 2.3.1): D[d][t] = sum_c S[c][t + s_c(DM_d)] for
+ * t in [-min_c s_c, T_fb - max_c s_c), zero elsewhere; D is [n_dm][T_fb]. */
+void orc_incoherent(const double* S, int n_chan, long long T_fb, double f0, double bw,
+                    double k_dm, int n_int, const double* dms, int n_dm, double* D) {
+  memset(D, 0, sizeof(double) * (size_t)n_dm * (size_t)T_fb);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int d = 0; d < n_dm; d++) {
+    long long s_min = 0, s_max = 0;
+    long long* s = (long long*)malloc(sizeof(long long) * (size_t)n_chan);
+    for (int c = 0; c < n_chan; c++) {
+      s[c] = orc_channel_shift(f0, bw, k_dm, dms[d], n_chan, n_int, c);
+      if (c == 0 || s[c] < s_min) s_min = s[c];
+      if (c == 0 || s[c] > s_max) s_max = s[c];
+    }
+    for (long long t = -s_min; t < T_fb - s_max; t++) {
+      double acc = 0.0;
+      for (int c = 0; c < n_chan; c++) acc += S[(size_t)c * T_fb + t + s[c]];
+      D[(size_t)d * T_fb + t] = acc;
+    }
+    free(s);
+  }
+}

@@ -37,8 +37,9 @@ K_DM_DEFAULT = 4.148808e15
 EXPORTED_SYMBOLS = ("chirp_plan_create", "chirp_plan_destroy", "chirp_plan_query",
                     "chirp_dm_layout", "chirp_dump_range", "chirp_dedisperse_run",
                     "chirpolator_run", "chimageator_run", "chirp_stage_timing",
-                    "chirp_plan_status", "chirp_last_error")
-STAGES = ("forward", "inv_rows", "inv_cols", "correlate", "beamform", "split", "chirp")
+                    "chirp_plan_status", "chirp_incoherent_run", "chirp_last_error")
+STAGES = ("forward", "inv_rows", "inv_cols", "correlate", "beamform", "split", "chirp",
+          "incoherent")
 
 
 class ChirpError(RuntimeError):
@@ -54,14 +55,15 @@ class _Config(ctypes.Structure):
                 ("dm", ctypes.POINTER(ctypes.c_double)), ("n_dm", ctypes.c_int),
                 ("dump_len", ctypes.c_int), ("nfft_min", ctypes.c_longlong),
                 ("pix_lm", ctypes.POINTER(ctypes.c_double)), ("n_pix", ctypes.c_int),
-                ("beam_mode", ctypes.c_int)]
+                ("beam_mode", ctypes.c_int), ("fb_chan", ctypes.c_int), ("fb_int", ctypes.c_int),
+                ("fb_dm", ctypes.POINTER(ctypes.c_double)), ("fb_n_dm", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
     _fields_ = [("n_dump", ctypes.c_longlong), ("n_pair", ctypes.c_int),
                 ("n_group", ctypes.c_int), ("workspace_bytes", ctypes.c_longlong),
                 ("ifft_points", ctypes.c_longlong), ("valid_samples", ctypes.c_longlong),
-                ("beam_mode", ctypes.c_int)]
+                ("beam_mode", ctypes.c_int), ("fb_samples", ctypes.c_longlong)]
 
 
 _lib = None
@@ -102,6 +104,8 @@ def load():
         lib.chirp_stage_timing.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ll)]
         lib.chirp_stage_timing.restype = i
+        lib.chirp_incoherent_run.argtypes = [vp, vp, i, vp, vp, i]
+        lib.chirp_incoherent_run.restype = i
         lib.chirp_plan_status.argtypes = [vp]
         lib.chirp_plan_status.restype = i
         lib.chirp_dedisperse_noalloc.argtypes = [vp, i, ll, ctypes.c_double, ctypes.c_double,
@@ -200,7 +204,8 @@ class Plan:
 
     def __init__(self, xyz, f0: float, bw: float, n_samp: int, dms, dump_len: int,
                  nfft_min: int, pix_lm=None, k_dm: float = K_DM_DEFAULT,
-                 beam_mode: int = BEAM_AUTO, n_ant: int | None = None, stream=None):
+                 beam_mode: int = BEAM_AUTO, n_ant: int | None = None, stream=None,
+                 fb_chan: int = 0, fb_int: int = 1, fb_dm=None):
         self._xyz = None if xyz is None else np.ascontiguousarray(xyz, dtype=np.float64)
         self._dms = np.ascontiguousarray(np.atleast_1d(dms), dtype=np.float64)
         self._pix = None if pix_lm is None else np.ascontiguousarray(pix_lm, dtype=np.float64)
@@ -219,6 +224,12 @@ class Plan:
         cfg.pix_lm = self._pix.ctypes.data_as(dp) if self._pix is not None else None
         cfg.n_pix = 0 if self._pix is None else int(self._pix.shape[0])
         cfg.beam_mode = int(beam_mode)
+        self._fb_dm = (None if fb_dm is None
+                       else np.ascontiguousarray(np.atleast_1d(fb_dm), dtype=np.float64))
+        cfg.fb_chan = int(fb_chan)
+        cfg.fb_int = int(fb_int)
+        cfg.fb_dm = self._fb_dm.ctypes.data_as(dp) if self._fb_dm is not None else None
+        cfg.fb_n_dm = 0 if self._fb_dm is None else int(self._fb_dm.size)
         self.n_ant, self.n_samp, self.n_dm = cfg.n_ant, cfg.n_samp, cfg.n_dm
         self.n_pix = cfg.n_pix
         self._h = chirp_plan_create(cfg, stream)
@@ -271,6 +282,19 @@ class Plan:
     def status(self):
         """Raise ChirpError if a bounded device wait of an earlier run gave up."""
         _check(load().chirp_plan_status(self._h))
+
+    def incoherent(self, volt, D_out, S_out=None):
+        """Filterbank S [fb_chan, T_fb] (optional) and incoherent dedispersion
+        D [fb_n_dm, T_fb] of the voltages (chirp_incoherent_run)."""
+        vp, vl, _k1 = _buf(volt, np.complex64, "volt")
+        dp_, dl, _k2 = _buf(D_out, np.float32, "D_out")
+        sp_ = ctypes.c_void_p(0)
+        if S_out is not None:
+            sp_, sl, _k3 = _buf(S_out, np.float32, "S_out")
+            if sl != dl:
+                raise TypeError("S_out and D_out must live in the same place")
+        _check(load().chirp_incoherent_run(self._h, vp, vl, sp_, dp_, dl))
+        return D_out
 
     def stage_timing(self, enable: bool):
         """Per-stage device ms and launch counts since the last call; switches

@@ -67,6 +67,13 @@ cudaError_t launch_beamform_simt(const float2* y, long long n_samp, int n_ant, i
                                  long long n_dump, long long first, long long last,
                                  const float2* W, int n_pix, float* pow, cudaStream_t st);
 
+// ---- incoherent filterbank path (incoherent.cu) ----
+// scratch holds a copy of the voltages ([n_ant] rows of seq_stride samples) and
+// is transformed in place; S [n_chan][T_fb], D [n_dm][T_fb]; shift [n_dm][n_chan]
+cudaError_t launch_incoherent(float2* scratch, long long seq_stride, int n_ant, int n_chan,
+                              int n_int, long long T_fb, const int* shift, int n_dm, float* S,
+                              float* D, TwiddlePtrs tw, cudaStream_t st);
+
 // ---- tensor-core beamformer (beamform_tc.cu) ----
 int beam_tc_groups(int n_ant);           // 8-wide real-K groups per head/tail part
 int beam_tc_ksteps(int n_ant);           // 16-wide MMA K steps

@@ -105,6 +105,12 @@ struct chirp_plan {
   int* d_err = nullptr;      // device status word (bounded waits that timed out)
   float2* d_V = nullptr;     // visibilities of one DM [n_dump][n_pair] (beam mode VIS)
   float2* d_wpair = nullptr; // pair weights [n_pair][n_pix] (beam mode VIS)
+  // incoherent filterbank search
+  int fb_chan = 0, fb_int = 0, fb_n_dm = 0;
+  long long T_fb = 0;
+  int* d_fb_shift = nullptr;   // [fb_n_dm][fb_chan]
+  float* d_fb_S = nullptr;     // [fb_chan][T_fb]
+  float* d_fb_D = nullptr;     // staging for host outputs
   void* d_out = nullptr;     // staging for host outputs
   size_t out_bytes = 0;
   size_t ws_bytes = 0;
@@ -153,6 +159,9 @@ void release(chirp_plan* p) {
   cudaFree(p->d_err);
   cudaFree(p->d_V);
   cudaFree(p->d_wpair);
+  cudaFree(p->d_fb_shift);
+  cudaFree(p->d_fb_S);
+  cudaFree(p->d_fb_D);
   cudaFree(p->d_out);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
 }
@@ -217,6 +226,15 @@ int validate(const chirp_config* c) {
     }
   if (c->beam_mode < 0 || c->beam_mode > CHIRP_BEAM_VIS)
     return fail(CHIRP_EINVAL, "unknown beam_mode");
+  if (c->fb_chan != 0) {
+    if (!is_pow2(c->fb_chan) || c->fb_chan < 16 || c->fb_chan > 4096)
+      return fail(CHIRP_EINVAL, "fb_chan must be 0 or a power of two in 16..4096");
+    if (c->fb_int < 1) return fail(CHIRP_EINVAL, "fb_int must be >= 1");
+    if (!c->fb_dm || c->fb_n_dm < 1) return fail(CHIRP_EINVAL, "fb_dm needs at least one DM");
+    for (int d = 0; d < c->fb_n_dm; d++)
+      if (!(c->fb_dm[d] >= 0) || !std::isfinite(c->fb_dm[d]))
+        return fail(CHIRP_EINVAL, "fb_dm %d is negative or not finite", d);
+  }
   return CHIRP_OK;
 }
 
@@ -355,6 +373,26 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   if (!rc && p->n_pix > 0)
     rc = dev_alloc(p, (void**)&p->d_W, (size_t)p->n_pix * p->M * sizeof(float2), "weights");
   if (!rc) rc = dev_alloc(p, (void**)&p->d_err, sizeof(int), "status word");
+  std::vector<int> fb_shift;
+  if (!rc && cfg->fb_chan > 0) {
+    p->fb_chan = cfg->fb_chan;
+    p->fb_int = cfg->fb_int;
+    p->fb_n_dm = cfg->fb_n_dm;
+    p->T_fb = p->N / ((long long)p->fb_chan * p->fb_int);
+    const double t_fb = (double)p->fb_chan * (double)p->fb_int / p->bw;
+    fb_shift.resize((size_t)p->fb_n_dm * p->fb_chan);
+    for (int d = 0; d < p->fb_n_dm; d++)
+      for (int c = 0; c < p->fb_chan; c++) {
+        // Eq. dmdelay lag of channel c relative to f0, in filterbank samples
+        const double fc = p->f0 + (double)(c - p->fb_chan / 2) * p->bw / (double)p->fb_chan;
+        const double tau = p->kdm * cfg->fb_dm[d] * (1.0 / (fc * fc) - 1.0 / (p->f0 * p->f0));
+        fb_shift[(size_t)d * p->fb_chan + c] = (int)std::floor(tau / t_fb + 0.5);
+      }
+    rc = dev_alloc(p, (void**)&p->d_fb_shift, fb_shift.size() * sizeof(int), "fb shifts");
+    if (!rc)
+      rc = dev_alloc(p, (void**)&p->d_fb_S,
+                     (size_t)std::max(1LL, p->T_fb) * p->fb_chan * sizeof(float), "filterbank");
+  }
   std::vector<uint8_t> aimg;
   std::vector<float2> wpair;
   if (!rc && p->n_pix > 0 && p->beam_mode == CHIRP_BEAM_VIS) {
@@ -450,6 +488,9 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   if (e == cudaSuccess && !aimg.empty())
     e = cudaMemcpyAsync(p->d_aimg, aimg.data(), aimg.size(), cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
+  if (e == cudaSuccess && !fb_shift.empty())
+    e = cudaMemcpyAsync(p->d_fb_shift, fb_shift.data(), fb_shift.size() * sizeof(int),
+                        cudaMemcpyHostToDevice, p->stream);
   for (auto& g : p->groups)
     if (e == cudaSuccess)
       e = launch_build_phase_table(g.d_G, g.geom, p->f0, p->bw, p->kdm, p->stream);
@@ -477,6 +518,7 @@ int chirp_plan_query(const chirp_plan* p, chirp_plan_info* info) {
   info->ifft_points = p->ifft_points;
   info->valid_samples = p->valid_samples;
   info->beam_mode = p->beam_mode;
+  info->fb_samples = p->T_fb;
   return CHIRP_OK;
 }
 
@@ -685,6 +727,43 @@ int chimageator_run(chirp_plan* p, const void* volt, int volt_loc, float* pow_ou
     rc = finish_out(p, pow_out, pow_loc, dp, bytes);
     if (rc) return rc;
     return chirp_plan_status(p);
+  }
+  return CHIRP_OK;
+}
+
+int chirp_incoherent_run(chirp_plan* p, const void* volt, int volt_loc, float* S_out,
+                         float* D_out, int out_loc) {
+  g_err[0] = 0;
+  if (!p) return fail(CHIRP_EINVAL, "plan is NULL");
+  if (p->fb_chan <= 0) return fail(CHIRP_EUNSUPPORTED, "plan was created without a filterbank");
+  if (!D_out) return fail(CHIRP_EINVAL, "D_out is NULL");
+  if (out_loc != CHIRP_HOST && out_loc != CHIRP_DEVICE)
+    return fail(CHIRP_EINVAL, "bad buffer location");
+  const float2* dx;
+  int rc = stage_input(p, volt, volt_loc, &dx);
+  if (rc) return rc;
+  const size_t vbytes = (size_t)p->M * p->N * sizeof(float2);
+  const size_t sbytes = (size_t)p->fb_chan * p->T_fb * sizeof(float);
+  const size_t dbytes = (size_t)p->fb_n_dm * p->T_fb * sizeof(float);
+  float* dD = D_out;
+  if (out_loc == CHIRP_HOST) {
+    if (!p->d_fb_D) {
+      rc = dev_alloc(p, (void**)&p->d_fb_D, std::max<size_t>(dbytes, 16), "incoherent output");
+      if (rc) return rc;
+    }
+    dD = p->d_fb_D;
+  }
+  float* dS = (out_loc == CHIRP_DEVICE && S_out) ? S_out : p->d_fb_S;
+  int mk = mark_begin(p);
+  // the filterbank transforms a copy of the voltages in the dedispersion scratch
+  CK(cudaMemcpyAsync(p->d_y, dx, vbytes, cudaMemcpyDeviceToDevice, p->stream));
+  CK(launch_incoherent(p->d_y, p->N, p->M, p->fb_chan, p->fb_int, p->T_fb, p->d_fb_shift,
+                       p->fb_n_dm, dS, dD, p->tw(), p->stream));
+  mark_end(p, CHIRP_STAGE_INCOHERENT, mk);
+  if (out_loc == CHIRP_HOST) {
+    CK(cudaMemcpyAsync(D_out, dD, dbytes, cudaMemcpyDeviceToHost, p->stream));
+    if (S_out) CK(cudaMemcpyAsync(S_out, dS, sbytes, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
   }
   return CHIRP_OK;
 }
