@@ -170,6 +170,45 @@ int chimageator_run(chirp_plan* plan, const void* volt, int volt_loc, float* pow
 int chirp_incoherent_run(chirp_plan* plan, const void* volt, int volt_loc, float* S_out,
                          float* D_out, int out_loc);
 
+/* ---- learned proposer: a 1-D convolutional network over the incoherent
+ * dedispersed power (trial DMs as channels, filterbank samples as time) that
+ * scores every (DM, time) cell; the coherent path then runs only where the
+ * score is high.  Layers: h1 = relu(conv(x, W1, b1, k1/2)), h2 =
+ * relu(conv(h1, W2, b2, k2/2)), z = conv(h2, W3, b3, 0) with width 1, where
+ * conv(x, W, b, pad)[b, o, t] = b[o] + sum_{i,k} W[o, i, k] x[b, i, t + k - pad]
+ * (zero padding).  Loss: mean class-weighted BCE with logits; optimiser Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8).  All FP32, all on the device.  Not an
+ * operation of the paper: the proposal stage of the search.
+ * Parameters are one flat FP32 vector in the order W1 [hidden][n_dm][k1],
+ * b1 [hidden], W2 [hidden][hidden][k2], b2 [hidden], W3 [n_dm][hidden], b3 [n_dm].
+ * Activations x, logits, labels: DEVICE float32 [batch][n_dm][n_time]. */
+typedef struct chirp_propnet chirp_propnet;
+/* k1, k2 odd and <= 15; buffers for up to max_batch segments of n_time. */
+int chirp_propnet_create(chirp_propnet** net, int n_dm, int hidden, int k1, int k2, int max_batch,
+                         int n_time, void* stream);
+void chirp_propnet_destroy(chirp_propnet* net);
+long long chirp_propnet_param_count(const chirp_propnet* net);
+/* host float32 [param_count]; set_params also resets the Adam state */
+int chirp_propnet_set_params(chirp_propnet* net, const float* params);
+int chirp_propnet_get_params(const chirp_propnet* net, float* params);
+/* gradients of the last backward / train step, host float32 [param_count] */
+int chirp_propnet_get_grads(const chirp_propnet* net, float* grads);
+int chirp_propnet_forward(chirp_propnet* net, const float* x, int batch, float* logits);
+/* forward + backward (gradients kept on the device); loss_host may be NULL */
+int chirp_propnet_backward(chirp_propnet* net, const float* x, const float* y, int batch,
+                           float pos_weight, float* loss_host);
+/* forward + backward + one Adam step of learning rate lr */
+int chirp_propnet_train_step(chirp_propnet* net, const float* x, const float* y, int batch,
+                             float pos_weight, float lr, float* loss_host);
+/* x[d][t] = (D[d][t] - mean_d) / std_d over the nonzero (valid) samples of
+ * each row; zeros stay zero.  D, x: DEVICE float32 [n_dm][n_time]. */
+int chirp_propnet_normalize(const float* D, int n_dm, long long n_time, float* x, void* stream);
+/* mask[d][w] = 1 where the largest logit of window w (win samples) of DM d
+ * exceeds thr.  logits: DEVICE float32 [n_dm][n_time]; mask: DEVICE int32
+ * [n_dm][ceil(n_time / win)]. */
+int chirp_propose_windows(const float* logits, int n_dm, long long n_time, int win, float thr,
+                          int* mask, void* stream);
+
 /* Per-stage device time.  Stages: */
 #define CHIRP_STAGE_FORWARD 0   /* forward FFT passes of every group            */
 #define CHIRP_STAGE_INV_ROWS 1  /* chirp multiply + inverse row pass, per DM    */

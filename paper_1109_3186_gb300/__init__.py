@@ -25,7 +25,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["Plan", "load", "build", "CHIRP_HOST", "CHIRP_DEVICE", "BEAM_AUTO", "BEAM_FP32_SIMT",
+__all__ = ["Plan", "PropNet", "load", "build", "CHIRP_HOST", "CHIRP_DEVICE", "BEAM_AUTO", "BEAM_FP32_SIMT",
            "BEAM_TC_3XBF16", "BEAM_VIS", "ChirpError", "chirp_plan_create", "chirp_plan_destroy",
            "chirpolator_run", "chimageator_run", "chirp_dedisperse_run", "chirp_last_error",
            "EXPORTED_SYMBOLS"]
@@ -37,7 +37,12 @@ K_DM_DEFAULT = 4.148808e15
 EXPORTED_SYMBOLS = ("chirp_plan_create", "chirp_plan_destroy", "chirp_plan_query",
                     "chirp_dm_layout", "chirp_dump_range", "chirp_dedisperse_run",
                     "chirpolator_run", "chimageator_run", "chirp_stage_timing",
-                    "chirp_plan_status", "chirp_incoherent_run", "chirp_last_error")
+                    "chirp_plan_status", "chirp_incoherent_run", "chirp_propnet_create",
+                    "chirp_propnet_destroy", "chirp_propnet_param_count",
+                    "chirp_propnet_set_params", "chirp_propnet_get_params",
+                    "chirp_propnet_get_grads", "chirp_propnet_forward", "chirp_propnet_backward",
+                    "chirp_propnet_train_step", "chirp_propnet_normalize", "chirp_propose_windows",
+                    "chirp_last_error")
 STAGES = ("forward", "inv_rows", "inv_cols", "correlate", "beamform", "split", "chirp",
           "incoherent")
 
@@ -106,6 +111,26 @@ def load():
         lib.chirp_stage_timing.restype = i
         lib.chirp_incoherent_run.argtypes = [vp, vp, i, vp, vp, i]
         lib.chirp_incoherent_run.restype = i
+        fp = ctypes.POINTER(ctypes.c_float)
+        lib.chirp_propnet_create.argtypes = [ctypes.POINTER(vp), i, i, i, i, i, i, vp]
+        lib.chirp_propnet_create.restype = i
+        lib.chirp_propnet_destroy.argtypes = [vp]
+        lib.chirp_propnet_destroy.restype = None
+        lib.chirp_propnet_param_count.argtypes = [vp]
+        lib.chirp_propnet_param_count.restype = ll
+        for nm in ("chirp_propnet_set_params", "chirp_propnet_get_params", "chirp_propnet_get_grads"):
+            getattr(lib, nm).argtypes = [vp, fp]
+            getattr(lib, nm).restype = i
+        lib.chirp_propnet_forward.argtypes = [vp, vp, i, vp]
+        lib.chirp_propnet_forward.restype = i
+        lib.chirp_propnet_backward.argtypes = [vp, vp, vp, i, ctypes.c_float, fp]
+        lib.chirp_propnet_backward.restype = i
+        lib.chirp_propnet_train_step.argtypes = [vp, vp, vp, i, ctypes.c_float, ctypes.c_float, fp]
+        lib.chirp_propnet_train_step.restype = i
+        lib.chirp_propnet_normalize.argtypes = [vp, i, ll, vp, vp]
+        lib.chirp_propnet_normalize.restype = i
+        lib.chirp_propose_windows.argtypes = [vp, i, ll, i, ctypes.c_float, vp, vp]
+        lib.chirp_propose_windows.restype = i
         lib.chirp_plan_status.argtypes = [vp]
         lib.chirp_plan_status.restype = i
         lib.chirp_dedisperse_noalloc.argtypes = [vp, i, ll, ctypes.c_double, ctypes.c_double,
@@ -303,3 +328,84 @@ class Plan:
         n = (ctypes.c_longlong * len(STAGES))()
         _check(load().chirp_stage_timing(self._h, int(bool(enable)), ms, n))
         return {k: (float(ms[j]), int(n[j])) for j, k in enumerate(STAGES)}
+
+
+def _dev_f32(t, what):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+            and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous float32 CUDA tensor" % what)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class PropNet:
+    """The learned proposer (chirp_propnet_*): 1-D conv net over the incoherent
+    dedispersed power, trained and run by the library's kernels."""
+
+    def __init__(self, n_dm: int, hidden: int, k1: int, k2: int, max_batch: int, n_time: int,
+                 stream=None):
+        self.n_dm, self.hidden, self.k1, self.k2 = n_dm, hidden, k1, k2
+        self.max_batch, self.n_time = max_batch, n_time
+        self._stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        _check(load().chirp_propnet_create(ctypes.byref(h), n_dm, hidden, k1, k2, max_batch,
+                                           n_time, self._stream))
+        self._h = h
+        self.n_params = int(load().chirp_propnet_param_count(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().chirp_propnet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        assert a.size == self.n_params
+        _check(load().chirp_propnet_set_params(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def params(self) -> np.ndarray:
+        a = np.empty(self.n_params, np.float32)
+        _check(load().chirp_propnet_get_params(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return a
+
+    def grads(self) -> np.ndarray:
+        a = np.empty(self.n_params, np.float32)
+        _check(load().chirp_propnet_get_grads(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return a
+
+    def forward(self, x, logits):
+        _check(load().chirp_propnet_forward(self._h, _dev_f32(x, "x"), int(x.shape[0]),
+                                            _dev_f32(logits, "logits")))
+        return logits
+
+    def backward(self, x, y, pos_weight: float) -> float:
+        loss = ctypes.c_float()
+        _check(load().chirp_propnet_backward(self._h, _dev_f32(x, "x"), _dev_f32(y, "y"),
+                                             int(x.shape[0]), float(pos_weight), ctypes.byref(loss)))
+        return float(loss.value)
+
+    def train_step(self, x, y, pos_weight: float, lr: float) -> float:
+        loss = ctypes.c_float()
+        _check(load().chirp_propnet_train_step(self._h, _dev_f32(x, "x"), _dev_f32(y, "y"),
+                                               int(x.shape[0]), float(pos_weight), float(lr),
+                                               ctypes.byref(loss)))
+        return float(loss.value)
+
+    def normalize(self, D, x):
+        _check(load().chirp_propnet_normalize(_dev_f32(D, "D"), int(D.shape[0]), int(D.shape[1]),
+                                              _dev_f32(x, "x"), self._stream))
+        return x
+
+    def propose(self, logits, win: int, thr: float, mask):
+        import torch
+        assert mask.dtype == torch.int32 and mask.is_cuda
+        _check(load().chirp_propose_windows(_dev_f32(logits, "logits"), int(logits.shape[0]),
+                                            int(logits.shape[1]), int(win), float(thr),
+                                            ctypes.c_void_p(mask.data_ptr()), self._stream))
+        return mask
