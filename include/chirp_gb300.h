@@ -260,6 +260,18 @@ int chirp_dedisperse_noalloc(const void* volt, int n_ant, long long n_samp, doub
  * of chimageator_run check it themselves.  Errors: CHIRP_EINVAL, CHIRP_ECUDA. */
 int chirp_plan_status(chirp_plan* plan);
 
+/* Selective searches: as chirpolator_run / chimageator_run but only for the
+ * (DM, dump) cells whose byte in cell_mask (HOST uint8 [n_dm][n_dump]) is
+ * nonzero -- e.g. the cells proposed by the learned proposer.  Only the
+ * overlap-save blocks that own a selected dump are inverse transformed and the
+ * back-end runs only on selected dumps; every other output cell is zero.  The
+ * selected cells hold exactly what the full search computes there.  Errors:
+ * as the full searches. */
+int chirpolator_run_selective(chirp_plan* plan, const void* volt, int volt_loc,
+                              const unsigned char* cell_mask, void* vis_out, int vis_loc);
+int chimageator_run_selective(chirp_plan* plan, const void* volt, int volt_loc,
+                              const unsigned char* cell_mask, float* pow_out, int pow_loc);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* chirp_last_error(void);
 

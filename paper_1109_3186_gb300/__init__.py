@@ -42,7 +42,7 @@ EXPORTED_SYMBOLS = ("chirp_plan_create", "chirp_plan_destroy", "chirp_plan_query
                     "chirp_propnet_set_params", "chirp_propnet_get_params",
                     "chirp_propnet_get_grads", "chirp_propnet_forward", "chirp_propnet_backward",
                     "chirp_propnet_train_step", "chirp_propnet_normalize", "chirp_propose_windows",
-                    "chirp_last_error")
+                    "chirpolator_run_selective", "chimageator_run_selective", "chirp_last_error")
 STAGES = ("forward", "inv_rows", "inv_cols", "correlate", "beamform", "split", "chirp",
           "incoherent")
 
@@ -131,6 +131,10 @@ def load():
         lib.chirp_propnet_normalize.restype = i
         lib.chirp_propose_windows.argtypes = [vp, i, ll, i, ctypes.c_float, vp, vp]
         lib.chirp_propose_windows.restype = i
+        lib.chirpolator_run_selective.argtypes = [vp, vp, i, vp, vp, i]
+        lib.chirpolator_run_selective.restype = i
+        lib.chimageator_run_selective.argtypes = [vp, vp, i, vp, vp, i]
+        lib.chimageator_run_selective.restype = i
         lib.chirp_plan_status.argtypes = [vp]
         lib.chirp_plan_status.restype = i
         lib.chirp_dedisperse_noalloc.argtypes = [vp, i, ll, ctypes.c_double, ctypes.c_double,
@@ -302,6 +306,28 @@ class Plan:
 
     def chimageator(self, volt, pow_out):
         chimageator_run(self._h, volt, pow_out)
+        return pow_out
+
+    def _mask(self, cell_mask):
+        m = np.ascontiguousarray(cell_mask, dtype=np.uint8)
+        if m.shape != (self.n_dm, self.n_dump):
+            raise ValueError("cell_mask must be [n_dm, n_dump]")
+        return m
+
+    def chirpolator_selective(self, volt, cell_mask, vis_out):
+        m = self._mask(cell_mask)
+        vp, vl, _k1 = _buf(volt, np.complex64, "volt")
+        op, ol, _k2 = _buf(vis_out, np.complex64, "vis_out")
+        _check(load().chirpolator_run_selective(self._h, vp, vl, ctypes.c_void_p(m.ctypes.data),
+                                                op, ol))
+        return vis_out
+
+    def chimageator_selective(self, volt, cell_mask, pow_out):
+        m = self._mask(cell_mask)
+        vp, vl, _k1 = _buf(volt, np.complex64, "volt")
+        op, ol, _k2 = _buf(pow_out, np.float32, "pow_out")
+        _check(load().chimageator_run_selective(self._h, vp, vl, ctypes.c_void_p(m.ctypes.data),
+                                                op, ol))
         return pow_out
 
     def status(self):

@@ -29,9 +29,10 @@ constexpr int kCorrWarps = 8;
 
 __global__ void __launch_bounds__(32 * kCorrWarps) k_correlate(const float2* __restrict__ y,
                                                                 long long n_samp, int M, int L,
-                                                                long long first, long long last,
+                                                                long long m_base, long long first,
+                                                                long long last,
                                                                 float2* __restrict__ vis) {
-  const long long m = blockIdx.x;
+  const long long m = m_base + blockIdx.x;
   const int n_pair = M * (M + 1) / 2;
   float2* out = vis + m * n_pair;
   if (m < first || m > last) {
@@ -106,14 +107,14 @@ __global__ void __launch_bounds__(32 * kCorrWarps) k_correlate(const float2* __r
 }
 
 cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int dump_len,
-                             long long n_dump, long long first, long long last, float2* vis,
-                             cudaStream_t st) {
+                             long long m_base, long long n_m, long long first, long long last,
+                             float2* vis, cudaStream_t st) {
   const int nt = (n_ant + kCorrTile - 1) / kCorrTile;
   const int n_tiles = nt * (nt + 1) / 2;
-  if (n_dump <= 0) return cudaSuccess;
+  if (n_m <= 0) return cudaSuccess;
   const int warps = n_tiles < kCorrWarps ? n_tiles : kCorrWarps;
-  dim3 grid((unsigned)n_dump, (n_tiles + warps - 1) / warps);
-  k_correlate<<<grid, 32 * warps, 0, st>>>(y, n_samp, n_ant, dump_len, first, last, vis);
+  dim3 grid((unsigned)n_m, (n_tiles + warps - 1) / warps);
+  k_correlate<<<grid, 32 * warps, 0, st>>>(y, n_samp, n_ant, dump_len, m_base, first, last, vis);
   return cudaGetLastError();
 }
 
@@ -176,13 +177,14 @@ constexpr int kBeamChunk = 128;
 
 __global__ void __launch_bounds__(kBeamPix) k_beamform_simt(const float2* __restrict__ y,
                                                             long long n_samp, int M, int L,
-                                                            long long first, long long last,
+                                                            long long m_base, long long first,
+                                                            long long last,
                                                             const float2* __restrict__ W,
                                                             int n_pix, float* __restrict__ pow) {
   extern __shared__ float2 smem[];
   float2* sw = smem;                   // [M][kBeamPix]
   float2* sy = smem + M * kBeamPix;    // [M][kBeamChunk]
-  const long long m = blockIdx.x;
+  const long long m = m_base + blockIdx.x;
   const int p = blockIdx.y * kBeamPix + threadIdx.x;
   float* out = pow + m * n_pix;
   if (m < first || m > last) {
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(kBeamPix) k_beamform_simt(const float2* __rest
 }
 
 cudaError_t launch_beamform_simt(const float2* y, long long n_samp, int n_ant, int dump_len,
-                                 long long n_dump, long long first, long long last,
+                                 long long m_base, long long n_m, long long first, long long last,
                                  const float2* W, int n_pix, float* pow, cudaStream_t st) {
   size_t smem = (size_t)n_ant * (kBeamPix + kBeamChunk) * sizeof(float2);
   if (smem > 48 * 1024) {
@@ -226,10 +228,10 @@ cudaError_t launch_beamform_simt(const float2* y, long long n_samp, int n_ant, i
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  if (n_dump <= 0 || n_pix <= 0) return cudaSuccess;
-  dim3 grid((unsigned)n_dump, (n_pix + kBeamPix - 1) / kBeamPix);
-  k_beamform_simt<<<grid, kBeamPix, smem, st>>>(y, n_samp, n_ant, dump_len, first, last, W,
-                                                n_pix, pow);
+  if (n_m <= 0 || n_pix <= 0) return cudaSuccess;
+  dim3 grid((unsigned)n_m, (n_pix + kBeamPix - 1) / kBeamPix);
+  k_beamform_simt<<<grid, kBeamPix, smem, st>>>(y, n_samp, n_ant, dump_len, m_base, first, last,
+                                                W, n_pix, pow);
   return cudaGetLastError();
 }
 

@@ -2,6 +2,8 @@
 //
 // Every block of Nfft = n1 * n2 samples is transformed with two passes over
 // HBM (the "four-step" factorisation):
+// Sequences (one transform each) are numbered block-major, q = b n_ant + a,
+// so the sequences of a range of blocks are contiguous for all antennas.
 //   forward:  column FFTs of length n1 (stride n2) on the raw voltages, times
 //             the twiddle W_N^(n2 k1), then row FFTs of length n2; the
 //             spectrum X[k1 + n1 k2] is left at position k1 n2 + k2;
@@ -30,7 +32,7 @@ static __device__ __forceinline__ Twiddles mk_tw(TwiddlePtrs p) { return Twiddle
 template <int L>
 __global__ void __launch_bounds__(256, 4) k_fwd_cols(const float2* __restrict__ x, long long n_samp,
                                                   float2* __restrict__ spec, int n2, int log2n,
-                                                  long long step, long long n_blk,
+                                                  long long step, int n_ant,
                                                   TwiddlePtrs twp) {
   constexpr int C = 4096 / L;
   constexpr int T = L / 16;
@@ -39,8 +41,8 @@ __global__ void __launch_bounds__(256, 4) k_fwd_cols(const float2* __restrict__ 
   const int s = threadIdx.x % C, jt = threadIdx.x / C;
   const int c = blockIdx.x * C + s;
   const bool act = c < n2;
-  const long long q = blockIdx.y;  // a * n_blk + b
-  const long long a = q / n_blk, b = q % n_blk;
+  const long long q = blockIdx.y;  // block-major sequence: b * n_ant + a
+  const long long a = q % n_ant, b = q / n_ant;
   const long long nfft = (long long)L * n2;
   const float2* xa = x + a * n_samp;
   const long long base = b * step;
@@ -149,7 +151,7 @@ template <int L>
 __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ Z,
                                                   float2* __restrict__ y, long long n_samp,
                                                   int n2, long long step, long long n_blk,
-                                                  long long n_hi, long long n_lo,
+                                                  int n_ant, long long n_hi, long long n_lo,
                                                   long long n_hi_max, long long q0,
                                                   TwiddlePtrs twp) {
   constexpr int C = 4096 / L;
@@ -159,8 +161,8 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ 
   const int s = threadIdx.x % C, jt = threadIdx.x / C;
   const int c = blockIdx.x * C + s;
   const bool act = c < n2;
-  const long long q = q0 + blockIdx.y;  // sequence; Z holds the chunk only
-  const long long a = q / n_blk, b = q % n_blk;
+  const long long q = q0 + blockIdx.y;  // block-major sequence; Z holds the chunk only
+  const long long a = q % n_ant, b = q / n_ant;
   const long long nfft = (long long)L * n2;
   const float2* src = Z + (long long)blockIdx.y * nfft;
   float2 v[16];
@@ -193,7 +195,7 @@ cudaError_t launch_forward(const float2* x, long long n_samp, int n_ant, const G
     dim3 grid((g.n2 + C - 1) / C, (unsigned)n_seq);
     switch (g.n1) {
 #define X(L) \
-  case L: k_fwd_cols<L><<<grid, 256, 0, st>>>(x, n_samp, spec, g.n2, g.log2n, g.step, g.n_blk, tw); break;
+  case L: k_fwd_cols<L><<<grid, 256, 0, st>>>(x, n_samp, spec, g.n2, g.log2n, g.step, n_ant, tw); break;
       CHIRP_SIZES(X)
 #undef X
       default: return cudaErrorInvalidValue;
@@ -243,15 +245,15 @@ cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, long long q0,
-                                long long nq, const GroupGeom& g, long long n_hi, long long n_lo,
-                                TwiddlePtrs tw, cudaStream_t st) {
+cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, int n_ant,
+                                long long q0, long long nq, const GroupGeom& g, long long n_hi,
+                                long long n_lo, TwiddlePtrs tw, cudaStream_t st) {
   if (nq > 65535 || nq < 1) return cudaErrorInvalidConfiguration;
   const int C = 4096 / g.n1;
   dim3 grid((g.n2 + C - 1) / C, (unsigned)nq);
   switch (g.n1) {
 #define X(L) \
-  case L: k_inv_cols<L><<<grid, 256, 0, st>>>(Z, y, n_samp, g.n2, g.step, g.n_blk, n_hi, n_lo, g.n_hi_max, q0, tw); break;
+  case L: k_inv_cols<L><<<grid, 256, 0, st>>>(Z, y, n_samp, g.n2, g.step, g.n_blk, n_ant, n_hi, n_lo, g.n_hi_max, q0, tw); break;
     CHIRP_SIZES(X)
 #undef X
     default: return cudaErrorInvalidValue;

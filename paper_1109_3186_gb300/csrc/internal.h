@@ -28,7 +28,7 @@ struct TwiddlePtrs {
 };
 
 // ---- dedispersion kernels (dedisperse.cu) ----
-// spectra of every (antenna, block) of one group; spec [n_ant][n_blk][nfft]
+// spectra of every (antenna, block) of one group; spec [n_blk][n_ant][nfft]
 // holds X[k1 + n1 k2] at position k1 * n2 + k2.
 cudaError_t launch_forward(const float2* x, long long n_samp, int n_ant, const GroupGeom& g,
                            float2* spec, TwiddlePtrs tw, cudaStream_t st);
@@ -53,18 +53,19 @@ cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, 
                                 long long nq, const GroupGeom& g, TwiddlePtrs tw,
                                 cudaStream_t st);
 // y[a][t] = dedispersed voltage for every owned, valid t of sequences q0.. (other t untouched)
-cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, long long q0,
-                                long long nq, const GroupGeom& g, long long n_hi, long long n_lo,
-                                TwiddlePtrs tw, cudaStream_t st);
+cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, int n_ant,
+                                long long q0, long long nq, const GroupGeom& g, long long n_hi,
+                                long long n_lo, TwiddlePtrs tw, cudaStream_t st);
 
 // ---- back-ends (backends.cu) ----
+// dumps m_base .. m_base + n_m - 1 (zeros for those outside [first, last])
 cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int dump_len,
-                             long long n_dump, long long first, long long last, float2* vis,
-                             cudaStream_t st);
+                             long long m_base, long long n_m, long long first, long long last,
+                             float2* vis, cudaStream_t st);
 cudaError_t launch_beam_from_vis(const float2* V, const float2* wpair, int n_ant, int n_pix,
                                  long long first, long long last, float* pow, cudaStream_t st);
 cudaError_t launch_beamform_simt(const float2* y, long long n_samp, int n_ant, int dump_len,
-                                 long long n_dump, long long first, long long last,
+                                 long long m_base, long long n_m, long long first, long long last,
                                  const float2* W, int n_pix, float* pow, cudaStream_t st);
 
 // ---- incoherent filterbank path (incoherent.cu) ----

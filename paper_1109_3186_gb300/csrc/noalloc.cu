@@ -173,7 +173,7 @@ extern "C" int chirp_dedisperse_noalloc(const void* volt, int n_ant, long long n
   const long long n_seq = (long long)n_ant * g.n_blk;
   if (e == cudaSuccess) e = launch_inverse_rows(spec, Z, H, 0, n_seq, g, tw, st);
   if (e == cudaSuccess)
-    e = launch_inverse_cols(Z, (float2*)y_out, n_samp, 0, n_seq, g, n_hi, n_lo, tw, st);
+    e = launch_inverse_cols(Z, (float2*)y_out, n_samp, n_ant, 0, n_seq, g, n_hi, n_lo, tw, st);
   if (e != cudaSuccess) {
     snprintf(g_msg, sizeof g_msg, "chirp_dedisperse_noalloc: launch failed: %s",
              cudaGetErrorString(e));

@@ -65,7 +65,7 @@ struct Group {
   GroupGeom geom;
   std::vector<int> dms;
   double* d_G = nullptr;     // FP64 phase table, spectrum order
-  float2* d_spec = nullptr;  // [n_ant][n_blk][nfft]
+  float2* d_spec = nullptr;  // [n_blk][n_ant][nfft] (block-major sequences)
 };
 
 struct DmInfo {
@@ -603,23 +603,157 @@ int forward_all(chirp_plan* p, const float2* dx) {
   return CHIRP_OK;
 }
 
-int dedisperse_one(chirp_plan* p, int d, float2* y) {
+// Dedisperse DM d over the blocks [b0, b1) of its group (all antennas).
+int dedisperse_blocks(chirp_plan* p, int d, float2* y, long long b0, long long b1) {
   const DmInfo& I = p->dmi[d];
   Group& g = p->groups[I.group];
-  int mk = mark_begin(p);
-  CK(launch_chirp_table(g.d_G, p->d_H, p->dm[d], g.geom, p->stream));
-  mark_end(p, CHIRP_STAGE_CHIRP, mk);
-  const long long n_seq = (long long)p->M * g.geom.n_blk;
-  const long long nq = inverse_chunk_sequences(g.geom, n_seq);
-  for (long long q0 = 0; q0 < n_seq; q0 += nq) {
-    const long long n = std::min(nq, n_seq - q0);
-    mk = mark_begin(p);
+  const long long q_end = b1 * p->M;
+  const long long nq = inverse_chunk_sequences(g.geom, (long long)p->M * g.geom.n_blk);
+  for (long long q0 = b0 * p->M; q0 < q_end; q0 += nq) {
+    const long long n = std::min(nq, q_end - q0);
+    int mk = mark_begin(p);
     CK(launch_inverse_rows(g.d_spec, p->d_Z, p->d_H, q0, n, g.geom, p->tw(), p->stream));
     mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
     mk = mark_begin(p);
-    CK(launch_inverse_cols(p->d_Z, y, p->N, q0, n, g.geom, I.n_hi, I.n_lo, p->tw(), p->stream));
+    CK(launch_inverse_cols(p->d_Z, y, p->N, p->M, q0, n, g.geom, I.n_hi, I.n_lo, p->tw(),
+                           p->stream));
     mark_end(p, CHIRP_STAGE_INV_COLS, mk);
   }
+  return CHIRP_OK;
+}
+
+int chirp_for(chirp_plan* p, int d) {
+  const DmInfo& I = p->dmi[d];
+  int mk = mark_begin(p);
+  CK(launch_chirp_table(p->groups[I.group].d_G, p->d_H, p->dm[d], p->groups[I.group].geom,
+                        p->stream));
+  mark_end(p, CHIRP_STAGE_CHIRP, mk);
+  return CHIRP_OK;
+}
+
+int dedisperse_one(chirp_plan* p, int d, float2* y) {
+  int rc = chirp_for(p, d);
+  if (rc) return rc;
+  return dedisperse_blocks(p, d, y, 0, p->groups[p->dmi[d].group].geom.n_blk);
+}
+
+// Block of DM d's group that owns output sample t (the overlap-save rule).
+long long owner_block(const GroupGeom& G, long long t) {
+  if (G.n_blk <= 1) return 0;
+  long long u = t - G.n_hi_max;
+  long long b = u < 0 ? 0 : u / G.step;
+  return b > G.n_blk - 1 ? G.n_blk - 1 : b;
+}
+
+enum Backend { kCorrelate, kBeams };
+
+// Back-end of DM d over its valid dumps [m0, m1) (inside [first, last]).
+int backend_dumps(chirp_plan* p, int d, Backend be, long long m0, long long m1, void* dout) {
+  if (m1 <= m0) return CHIRP_OK;
+  const long long last = m1 - 1;
+  if (be == kCorrelate) {
+    const size_t per_dm = (size_t)p->n_dump * p->n_pair;
+    int mk = mark_begin(p);
+    CK(launch_correlate(p->d_y, p->N, p->M, p->L, m0, m1 - m0, m0, last,
+                        (float2*)dout + d * per_dm, p->stream));
+    mark_end(p, CHIRP_STAGE_CORRELATE, mk);
+    return CHIRP_OK;
+  }
+  float* out = (float*)dout + (size_t)d * p->n_dump * p->n_pix;
+  if (p->beam_mode == CHIRP_BEAM_VIS) {
+    int mk = mark_begin(p);
+    CK(launch_correlate(p->d_y, p->N, p->M, p->L, m0, m1 - m0, m0, last, p->d_V, p->stream));
+    mark_end(p, CHIRP_STAGE_CORRELATE, mk);
+    mk = mark_begin(p);
+    CK(launch_beam_from_vis(p->d_V, p->d_wpair, p->M, p->n_pix, m0, last, out, p->stream));
+    mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
+  } else if (p->beam_mode == CHIRP_BEAM_TC_3XBF16) {
+    int mk = mark_begin(p);
+    CK(launch_split_bf16(p->d_y, p->N, p->M, p->L, m0 * p->L, m1 * p->L, p->d_bimg, p->stream));
+    mark_end(p, CHIRP_STAGE_SPLIT, mk);
+    mk = mark_begin(p);
+    CK(launch_beam_tc(p->d_bimg, p->d_aimg, p->M, p->n_pix, p->L, m0, last, out, p->d_err,
+                      p->stream));
+    mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
+  } else {
+    int mk = mark_begin(p);
+    CK(launch_beamform_simt(p->d_y, p->N, p->M, p->L, m0, m1 - m0, m0, last, p->d_W, p->n_pix,
+                            out, p->stream));
+    mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
+  }
+  return CHIRP_OK;
+}
+
+// The whole search, or (mask != NULL) only the (DM, dump) cells whose mask
+// byte is nonzero: for each DM the blocks owning a selected dump are inverse
+// transformed (runs of consecutive blocks per launch) and the back-end runs on
+// runs of consecutive selected dumps.  Outputs are zero elsewhere.
+int run_search(chirp_plan* p, const void* volt, int volt_loc, const unsigned char* mask,
+               Backend be, void* out_user, int out_loc) {
+  g_err[0] = 0;
+  if (!p) return fail(CHIRP_EINVAL, "plan is NULL");
+  if (be == kBeams && p->n_pix <= 0) return fail(CHIRP_EUNSUPPORTED, "plan was created without pixels");
+  const float2* dx;
+  int rc = stage_input(p, volt, volt_loc, &dx);
+  if (rc) return rc;
+  const size_t per_dm = be == kCorrelate ? (size_t)p->n_dump * p->n_pair : (size_t)p->n_dump * p->n_pix;
+  const size_t bytes = per_dm * p->dm.size() * (be == kCorrelate ? sizeof(float2) : sizeof(float));
+  void* dout;
+  rc = out_buffer(p, out_user, out_loc, bytes, &dout);
+  if (rc) return rc;
+  rc = forward_all(p, dx);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(dout, 0, bytes, p->stream));  // invalid / unselected cells stay zero
+  std::vector<unsigned char> need;
+  for (int d = 0; d < (int)p->dm.size(); d++) {
+    const DmInfo& I = p->dmi[d];
+    if (I.last < I.first) continue;
+    const GroupGeom& G = p->groups[I.group].geom;
+    const unsigned char* row = mask ? mask + (size_t)d * p->n_dump : nullptr;
+    if (row) {
+      bool any = false;
+      for (long long m = I.first; m <= I.last && !any; m++) any = row[m] != 0;
+      if (!any) continue;
+    }
+    rc = chirp_for(p, d);
+    if (rc) return rc;
+    if (!row) {
+      rc = dedisperse_blocks(p, d, p->d_y, 0, G.n_blk);
+      if (!rc) rc = backend_dumps(p, d, be, I.first, I.last + 1, dout);
+      if (rc) return rc;
+      continue;
+    }
+    need.assign((size_t)G.n_blk, 0);
+    for (long long m = I.first; m <= I.last; m++)
+      if (row[m])
+        for (long long b = owner_block(G, m * p->L); b <= owner_block(G, (m + 1) * p->L - 1); b++)
+          need[(size_t)b] = 1;
+    for (long long b = 0; b < G.n_blk;) {
+      if (!need[(size_t)b]) {
+        b++;
+        continue;
+      }
+      long long e = b;
+      while (e < G.n_blk && need[(size_t)e]) e++;
+      rc = dedisperse_blocks(p, d, p->d_y, b, e);
+      if (rc) return rc;
+      b = e;
+    }
+    for (long long m = I.first; m <= I.last;) {
+      if (!row[m]) {
+        m++;
+        continue;
+      }
+      long long e = m;
+      while (e <= I.last && row[e]) e++;
+      rc = backend_dumps(p, d, be, m, e, dout);
+      if (rc) return rc;
+      m = e;
+    }
+  }
+  rc = finish_out(p, out_user, out_loc, dout, bytes);
+  if (rc) return rc;
+  if (be == kBeams && out_loc == CHIRP_HOST) return chirp_plan_status(p);
   return CHIRP_OK;
 }
 
@@ -649,86 +783,23 @@ int chirp_dedisperse_run(chirp_plan* p, const void* volt, int volt_loc, int d, v
 }
 
 int chirpolator_run(chirp_plan* p, const void* volt, int volt_loc, void* vis_out, int vis_loc) {
-  g_err[0] = 0;
-  if (!p) return fail(CHIRP_EINVAL, "plan is NULL");
-  const float2* dx;
-  int rc = stage_input(p, volt, volt_loc, &dx);
-  if (rc) return rc;
-  const size_t per_dm = (size_t)p->n_dump * p->n_pair;
-  const size_t bytes = per_dm * p->dm.size() * sizeof(float2);
-  void* dv;
-  rc = out_buffer(p, vis_out, vis_loc, bytes, &dv);
-  if (rc) return rc;
-  rc = forward_all(p, dx);
-  if (rc) return rc;
-  for (int d = 0; d < (int)p->dm.size(); d++) {
-    rc = dedisperse_one(p, d, p->d_y);
-    if (rc) return rc;
-    const DmInfo& I = p->dmi[d];
-    int mk = mark_begin(p);
-    CK(launch_correlate(p->d_y, p->N, p->M, p->L, p->n_dump, I.first, I.last,
-                        (float2*)dv + d * per_dm, p->stream));
-    mark_end(p, CHIRP_STAGE_CORRELATE, mk);
-  }
-  return finish_out(p, vis_out, vis_loc, dv, bytes);
+  return run_search(p, volt, volt_loc, nullptr, kCorrelate, vis_out, vis_loc);
 }
 
 int chimageator_run(chirp_plan* p, const void* volt, int volt_loc, float* pow_out, int pow_loc) {
-  g_err[0] = 0;
-  if (!p) return fail(CHIRP_EINVAL, "plan is NULL");
-  if (p->n_pix <= 0) return fail(CHIRP_EUNSUPPORTED, "plan was created without pixels");
-  const float2* dx;
-  int rc = stage_input(p, volt, volt_loc, &dx);
-  if (rc) return rc;
-  const size_t per_dm = (size_t)p->n_dump * p->n_pix;
-  const size_t bytes = per_dm * p->dm.size() * sizeof(float);
-  void* dp;
-  rc = out_buffer(p, pow_out, pow_loc, bytes, &dp);
-  if (rc) return rc;
-  rc = forward_all(p, dx);
-  if (rc) return rc;
-  const bool tcore = p->beam_mode == CHIRP_BEAM_TC_3XBF16;
-  const bool vis = p->beam_mode == CHIRP_BEAM_VIS;
-  // invalid dumps stay zero; these modes write only valid ones
-  if (tcore || vis) CK(cudaMemsetAsync(dp, 0, bytes, p->stream));
-  for (int d = 0; d < (int)p->dm.size(); d++) {
-    rc = dedisperse_one(p, d, p->d_y);
-    if (rc) return rc;
-    const DmInfo& I = p->dmi[d];
-    float* out = (float*)dp + d * per_dm;
-    if (vis) {
-      if (I.last < I.first) continue;
-      int mk = mark_begin(p);
-      CK(launch_correlate(p->d_y, p->N, p->M, p->L, p->n_dump, I.first, I.last, p->d_V,
-                          p->stream));
-      mark_end(p, CHIRP_STAGE_CORRELATE, mk);
-      mk = mark_begin(p);
-      CK(launch_beam_from_vis(p->d_V, p->d_wpair, p->M, p->n_pix, I.first, I.last, out,
-                              p->stream));
-      mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
-    } else if (tcore) {
-      if (I.last < I.first) continue;
-      int mk = mark_begin(p);
-      CK(launch_split_bf16(p->d_y, p->N, p->M, p->L, I.first * p->L, (I.last + 1) * p->L,
-                           p->d_bimg, p->stream));
-      mark_end(p, CHIRP_STAGE_SPLIT, mk);
-      mk = mark_begin(p);
-      CK(launch_beam_tc(p->d_bimg, p->d_aimg, p->M, p->n_pix, p->L, I.first, I.last, out,
-                        p->d_err, p->stream));
-      mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
-    } else {
-      int mk = mark_begin(p);
-      CK(launch_beamform_simt(p->d_y, p->N, p->M, p->L, p->n_dump, I.first, I.last, p->d_W,
-                              p->n_pix, out, p->stream));
-      mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
-    }
-  }
-  if (pow_loc == CHIRP_HOST) {
-    rc = finish_out(p, pow_out, pow_loc, dp, bytes);
-    if (rc) return rc;
-    return chirp_plan_status(p);
-  }
-  return CHIRP_OK;
+  return run_search(p, volt, volt_loc, nullptr, kBeams, pow_out, pow_loc);
+}
+
+int chirpolator_run_selective(chirp_plan* p, const void* volt, int volt_loc,
+                              const unsigned char* cell_mask, void* vis_out, int vis_loc) {
+  if (!cell_mask) return fail(CHIRP_EINVAL, "cell_mask is NULL");
+  return run_search(p, volt, volt_loc, cell_mask, kCorrelate, vis_out, vis_loc);
+}
+
+int chimageator_run_selective(chirp_plan* p, const void* volt, int volt_loc,
+                              const unsigned char* cell_mask, float* pow_out, int pow_loc) {
+  if (!cell_mask) return fail(CHIRP_EINVAL, "cell_mask is NULL");
+  return run_search(p, volt, volt_loc, cell_mask, kBeams, pow_out, pow_loc);
 }
 
 int chirp_incoherent_run(chirp_plan* p, const void* volt, int volt_loc, float* S_out,

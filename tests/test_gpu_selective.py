@@ -1,0 +1,53 @@
+"""The selective coherent search computes, in the selected (DM, dump) cells,
+what the full search computes there, and zeros elsewhere."""
+import numpy as np
+import pytest
+
+import paper_1109_3186_gb300 as chirp
+from paper_1109_3186_gb300 import skymodel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.mark.parametrize("mode", [chirp.BEAM_VIS, chirp.BEAM_TC_3XBF16, chirp.BEAM_FP32_SIMT])
+def test_selective_beams_equal_full_on_selected_cells(mode):
+    sc = skymodel.chimageator_medium(n_samp=1 << 18, n_dm=6, n_ant=12, dm_max=150.0,
+                                     nfft_min=1 << 15, dump_len=2048, n_side=8, n_pulse=1)
+    x = sc.voltages()
+    plan = chirp.Plan.from_scenario(sc, beam_mode=mode)
+    xd = torch.from_numpy(x).cuda()
+    full = torch.empty((6, plan.n_dump, plan.n_pix), dtype=torch.float32, device="cuda")
+    plan.chimageator(xd, full)
+    rng = np.random.default_rng(3)
+    mask = (rng.random((6, plan.n_dump)) < 0.15).astype(np.uint8)
+    mask[2] = 0
+    mask[4, 40:60] = 1
+    sel = torch.empty_like(full)
+    plan.chimageator_selective(xd, mask, sel)
+    F, S = full.cpu().numpy(), sel.cpu().numpy()
+    first, last = plan.dump_range()
+    valid = np.zeros_like(mask, bool)
+    for d in range(6):
+        valid[d, first[d]:last[d] + 1] = True
+    pick = (mask.astype(bool) & valid)
+    assert np.all(S[~pick] == 0)
+    assert pick.sum() > 20
+    assert np.abs(S[pick] - F[pick]).max() <= 1e-6 * np.abs(F[pick]).max()
+
+
+def test_selective_visibilities_equal_full():
+    sc = skymodel.chirpolator_small(n_samp=1 << 18, n_dm=5, dm_max=100.0, nfft_min=1 << 15)
+    x = sc.voltages()
+    plan = chirp.Plan.from_scenario(sc)
+    full = np.empty((5, plan.n_dump, plan.n_pair), np.complex64)
+    plan.chirpolator(x, full)
+    mask = np.zeros((5, plan.n_dump), np.uint8)
+    mask[1, 10:12] = 1
+    mask[3, 100:180] = 1
+    mask[3, 240] = 1
+    sel = np.empty_like(full)
+    plan.chirpolator_selective(x, mask, sel)
+    pick = mask.astype(bool)
+    assert np.array_equal(sel[pick], full[pick])
+    assert np.all(sel[~pick] == 0)
