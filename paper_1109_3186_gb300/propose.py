@@ -180,9 +180,10 @@ class Proposer:
         self.net.propose(z.contiguous(), self.s.win, thr, m)
         return m.cpu().numpy().astype(np.uint8)
 
-    def cells(self, mask: np.ndarray) -> np.ndarray:
-        """Coherent (DM, dump) cell mask [n_dm, n_dump] of a proposal mask, one
-        window of margin on each side."""
+    def cells(self, mask: np.ndarray, dm_margin: int = 1) -> np.ndarray:
+        """Coherent (DM, dump) cell mask [n_dm, n_dump] of a proposal mask, with
+        one window of margin in time and dm_margin trial DMs on each side (a
+        burst between two trial DMs is detected on either)."""
         s = self.s
         n_dump = s.n_samp // s.dump_len
         cells = np.zeros((s.n_dm, n_dump), np.uint8)
@@ -190,7 +191,8 @@ class Proposer:
         for d, w in zip(*np.nonzero(mask)):
             t_lo = max(0, (int(w) - 1) * span)
             t_hi = min(s.n_samp, (int(w) + 2) * span)
-            cells[d, t_lo // s.dump_len:(t_hi + s.dump_len - 1) // s.dump_len] = 1
+            d0, d1 = max(0, int(d) - dm_margin), min(s.n_dm, int(d) + dm_margin + 1)
+            cells[d0:d1, t_lo // s.dump_len:(t_hi + s.dump_len - 1) // s.dump_len] = 1
         return cells
 
 
