@@ -31,8 +31,9 @@ __global__ void __launch_bounds__(32 * kCorrWarps) k_correlate(const float2* __r
                                                                 long long n_samp, int M, int L,
                                                                 long long m_base, long long first,
                                                                 long long last,
-                                                                float2* __restrict__ vis) {
-  const long long m = m_base + blockIdx.x;
+                                                                float2* __restrict__ vis,
+                                                                const int* __restrict__ dump_list) {
+  const long long m = dump_list ? (long long)dump_list[blockIdx.x] : m_base + blockIdx.x;
   const int n_pair = M * (M + 1) / 2;
   float2* out = vis + m * n_pair;
   if (m < first || m > last) {
@@ -108,13 +109,14 @@ __global__ void __launch_bounds__(32 * kCorrWarps) k_correlate(const float2* __r
 
 cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int dump_len,
                              long long m_base, long long n_m, long long first, long long last,
-                             float2* vis, cudaStream_t st) {
+                             float2* vis, cudaStream_t st, const int* dump_list) {
   const int nt = (n_ant + kCorrTile - 1) / kCorrTile;
   const int n_tiles = nt * (nt + 1) / 2;
   if (n_m <= 0) return cudaSuccess;
   const int warps = n_tiles < kCorrWarps ? n_tiles : kCorrWarps;
   dim3 grid((unsigned)n_m, (n_tiles + warps - 1) / warps);
-  k_correlate<<<grid, 32 * warps, 0, st>>>(y, n_samp, n_ant, dump_len, m_base, first, last, vis);
+  k_correlate<<<grid, 32 * warps, 0, st>>>(y, n_samp, n_ant, dump_len, m_base, first, last, vis,
+                                           dump_list);
   return cudaGetLastError();
 }
 
@@ -130,12 +132,20 @@ __global__ void __launch_bounds__(kVisPix) k_beam_from_vis(const float2* __restr
                                                            const float2* __restrict__ wpair,
                                                            int n_pair, int n_pix, long long first,
                                                            long long last,
-                                                           float* __restrict__ pow) {
+                                                           float* __restrict__ pow,
+                                                           const int* __restrict__ dump_list,
+                                                           long long n_list) {
   extern __shared__ float2 sv[];  // [kVisDumps][n_pair]
-  const long long m0 = first + (long long)blockIdx.x * kVisDumps;
-  const int nd = (int)((last + 1 - m0) < kVisDumps ? (last + 1 - m0) : kVisDumps);
+  // dumps of this CTA: first + (x kVisDumps + d), or dump_list[x kVisDumps + d]
+  const long long j0 = (long long)blockIdx.x * kVisDumps;
+  const long long n_all = dump_list ? n_list : last + 1 - first;
+  const int nd = (int)((n_all - j0) < kVisDumps ? (n_all - j0) : kVisDumps);
   const int p = blockIdx.y * kVisPix + threadIdx.x;
-  for (int i = threadIdx.x; i < nd * n_pair; i += blockDim.x) sv[i] = V[m0 * n_pair + i];
+  for (int i = threadIdx.x; i < nd * n_pair; i += blockDim.x) {
+    const long long j = j0 + i / n_pair;
+    const long long m = dump_list ? (long long)dump_list[j] : first + j;
+    sv[i] = V[m * n_pair + i % n_pair];
+  }
   __syncthreads();
   if (p >= n_pix) return;
   float acc[kVisDumps];
@@ -149,12 +159,16 @@ __global__ void __launch_bounds__(kVisPix) k_beam_from_vis(const float2* __restr
       acc[d] = fmaf(w.x, v.x, fmaf(-w.y, v.y, acc[d]));
     }
   }
-  for (int d = 0; d < nd; d++) pow[(m0 + d) * n_pix + p] = acc[d];
+  for (int d = 0; d < nd; d++) {
+    const long long m = dump_list ? (long long)dump_list[j0 + d] : first + j0 + d;
+    pow[m * n_pix + p] = acc[d];
+  }
 }
 
 cudaError_t launch_beam_from_vis(const float2* V, const float2* wpair, int n_ant, int n_pix,
-                                 long long first, long long last, float* pow, cudaStream_t st) {
-  if (last < first || n_pix <= 0) return cudaSuccess;
+                                 long long first, long long last, float* pow, cudaStream_t st,
+                                 const int* dump_list, long long n_list) {
+  if (n_pix <= 0 || (dump_list ? n_list <= 0 : last < first)) return cudaSuccess;
   const int n_pair = n_ant * (n_ant + 1) / 2;
   const size_t smem = (size_t)kVisDumps * n_pair * sizeof(float2);
   if (smem > 48 * 1024) {
@@ -162,9 +176,10 @@ cudaError_t launch_beam_from_vis(const float2* V, const float2* wpair, int n_ant
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  const long long n = last - first + 1;
+  const long long n = dump_list ? n_list : last - first + 1;
   dim3 grid((unsigned)((n + kVisDumps - 1) / kVisDumps), (n_pix + kVisPix - 1) / kVisPix);
-  k_beam_from_vis<<<grid, kVisPix, smem, st>>>(V, wpair, n_pair, n_pix, first, last, pow);
+  k_beam_from_vis<<<grid, kVisPix, smem, st>>>(V, wpair, n_pair, n_pix, first, last, pow,
+                                               dump_list, n_list);
   return cudaGetLastError();
 }
 

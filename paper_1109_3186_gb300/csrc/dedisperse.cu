@@ -120,7 +120,9 @@ template <int L>
 __global__ void __launch_bounds__(256, 4) k_inv_rows(const float2* __restrict__ spec,
                                                   float2* __restrict__ Z,
                                                   const float2* __restrict__ H, int n1,
-                                                  int log2n, long long q0, TwiddlePtrs twp) {
+                                                  int log2n, long long q0,
+                                                  const int* __restrict__ blk_list, int n_ant,
+                                                  TwiddlePtrs twp) {
   constexpr int C = 4096 / L;
   constexpr int T = L / 16;
   __shared__ float2 sm[FftTile<L, C>::SLOTS];
@@ -129,7 +131,9 @@ __global__ void __launch_bounds__(256, 4) k_inv_rows(const float2* __restrict__ 
   const int k1 = blockIdx.x * C + s;
   const bool act = k1 < n1;
   const long long nfft = (long long)L * n1;
-  const long long q = q0 + blockIdx.y;  // sequence; Z holds the chunk only
+  // sequence: q0 + y, or (listed block) * n_ant + antenna; Z holds the launch only
+  const long long q = blk_list ? (long long)blk_list[blockIdx.y / n_ant] * n_ant + blockIdx.y % n_ant
+                               : q0 + blockIdx.y;
   const float2* src = spec + q * nfft + (long long)k1 * L;
   const float2* h = H + (long long)k1 * L;
   float2 v[16];
@@ -153,6 +157,7 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ 
                                                   int n2, long long step, long long n_blk,
                                                   int n_ant, long long n_hi, long long n_lo,
                                                   long long n_hi_max, long long q0,
+                                                  const int* __restrict__ blk_list,
                                                   TwiddlePtrs twp) {
   constexpr int C = 4096 / L;
   constexpr int T = L / 16;
@@ -161,7 +166,8 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ 
   const int s = threadIdx.x % C, jt = threadIdx.x / C;
   const int c = blockIdx.x * C + s;
   const bool act = c < n2;
-  const long long q = q0 + blockIdx.y;  // block-major sequence; Z holds the chunk only
+  const long long q = blk_list ? (long long)blk_list[blockIdx.y / n_ant] * n_ant + blockIdx.y % n_ant
+                               : q0 + blockIdx.y;  // block-major sequence; Z holds the launch
   const long long a = q % n_ant, b = q / n_ant;
   const long long nfft = (long long)L * n2;
   const float2* src = Z + (long long)blockIdx.y * nfft;
@@ -231,13 +237,13 @@ cudaError_t launch_chirp_table(const double* G, float2* H, double dm, const Grou
 
 cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, long long q0,
                                 long long nq, const GroupGeom& g, TwiddlePtrs tw,
-                                cudaStream_t st) {
+                                cudaStream_t st, const int* blk_list, int n_ant) {
   if (nq > 65535 || nq < 1) return cudaErrorInvalidConfiguration;
   const int C = 4096 / g.n2;
   dim3 grid((g.n1 + C - 1) / C, (unsigned)nq);
   switch (g.n2) {
 #define X(L) \
-  case L: k_inv_rows<L><<<grid, 256, 0, st>>>(spec, Z, H, g.n1, g.log2n, q0, tw); break;
+  case L: k_inv_rows<L><<<grid, 256, 0, st>>>(spec, Z, H, g.n1, g.log2n, q0, blk_list, n_ant, tw); break;
     CHIRP_SIZES(X)
 #undef X
     default: return cudaErrorInvalidValue;
@@ -247,13 +253,14 @@ cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, 
 
 cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, int n_ant,
                                 long long q0, long long nq, const GroupGeom& g, long long n_hi,
-                                long long n_lo, TwiddlePtrs tw, cudaStream_t st) {
+                                long long n_lo, TwiddlePtrs tw, cudaStream_t st,
+                                const int* blk_list) {
   if (nq > 65535 || nq < 1) return cudaErrorInvalidConfiguration;
   const int C = 4096 / g.n1;
   dim3 grid((g.n2 + C - 1) / C, (unsigned)nq);
   switch (g.n1) {
 #define X(L) \
-  case L: k_inv_cols<L><<<grid, 256, 0, st>>>(Z, y, n_samp, g.n2, g.step, g.n_blk, n_ant, n_hi, n_lo, g.n_hi_max, q0, tw); break;
+  case L: k_inv_cols<L><<<grid, 256, 0, st>>>(Z, y, n_samp, g.n2, g.step, g.n_blk, n_ant, n_hi, n_lo, g.n_hi_max, q0, blk_list, tw); break;
     CHIRP_SIZES(X)
 #undef X
     default: return cudaErrorInvalidValue;

@@ -49,21 +49,27 @@ cudaError_t launch_chirp_table(const double* G, float2* H, double dm, const Grou
 constexpr long long kInverseChunkBytes = CHIRP_INVERSE_CHUNK_BYTES;
 long long inverse_chunk_sequences(const GroupGeom& g, long long n_seq);
 // Z[0 .. nq) = rows of IFFT of sequences q0.. after the chirp multiply and twiddle
+// With blk_list (device int array), the launch covers nq = n_listed * n_ant
+// sequences: listed block b, antenna a -> sequence b * n_ant + a.
 cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, long long q0,
                                 long long nq, const GroupGeom& g, TwiddlePtrs tw,
-                                cudaStream_t st);
+                                cudaStream_t st, const int* blk_list = nullptr, int n_ant = 1);
 // y[a][t] = dedispersed voltage for every owned, valid t of sequences q0.. (other t untouched)
 cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, int n_ant,
                                 long long q0, long long nq, const GroupGeom& g, long long n_hi,
-                                long long n_lo, TwiddlePtrs tw, cudaStream_t st);
+                                long long n_lo, TwiddlePtrs tw, cudaStream_t st,
+                                const int* blk_list = nullptr);
 
 // ---- back-ends (backends.cu) ----
-// dumps m_base .. m_base + n_m - 1 (zeros for those outside [first, last])
+// dumps m_base .. m_base + n_m - 1, or dump_list[0 .. n_m) when dump_list is a
+// device array (zeros for dumps outside [first, last])
 cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int dump_len,
                              long long m_base, long long n_m, long long first, long long last,
-                             float2* vis, cudaStream_t st);
+                             float2* vis, cudaStream_t st, const int* dump_list = nullptr);
+// dumps first..last, or the n_list dumps of dump_list (device) when given
 cudaError_t launch_beam_from_vis(const float2* V, const float2* wpair, int n_ant, int n_pix,
-                                 long long first, long long last, float* pow, cudaStream_t st);
+                                 long long first, long long last, float* pow, cudaStream_t st,
+                                 const int* dump_list = nullptr, long long n_list = 0);
 cudaError_t launch_beamform_simt(const float2* y, long long n_samp, int n_ant, int dump_len,
                                  long long m_base, long long n_m, long long first, long long last,
                                  const float2* W, int n_pix, float* pow, cudaStream_t st);

@@ -111,6 +111,8 @@ struct chirp_plan {
   int* d_fb_shift = nullptr;   // [fb_n_dm][fb_chan]
   float* d_fb_S = nullptr;     // [fb_chan][T_fb]
   float* d_fb_D = nullptr;     // staging for host outputs
+  int* d_lists = nullptr;      // selective searches: block and dump index lists
+  size_t lists_cap = 0;
   void* d_out = nullptr;     // staging for host outputs
   size_t out_bytes = 0;
   size_t ws_bytes = 0;
@@ -162,6 +164,7 @@ void release(chirp_plan* p) {
   cudaFree(p->d_fb_shift);
   cudaFree(p->d_fb_S);
   cudaFree(p->d_fb_D);
+  cudaFree(p->d_lists);
   cudaFree(p->d_out);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
 }
@@ -704,41 +707,87 @@ int run_search(chirp_plan* p, const void* volt, int volt_loc, const unsigned cha
   rc = forward_all(p, dx);
   if (rc) return rc;
   CK(cudaMemsetAsync(dout, 0, bytes, p->stream));  // invalid / unselected cells stay zero
-  std::vector<unsigned char> need;
+  // Selective: per DM, the list of blocks owning a selected dump and the list
+  // of selected valid dumps, uploaded together; each DM then costs one
+  // inverse launch pair over its listed blocks and (visibility path) one
+  // back-end launch pair over its listed dumps.
+  std::vector<int> lists;
+  std::vector<long long> blk_off(p->dm.size(), 0), blk_n(p->dm.size(), 0);
+  std::vector<long long> dmp_off(p->dm.size(), 0), dmp_n(p->dm.size(), 0);
+  if (mask) {
+    std::vector<unsigned char> need;
+    for (int d = 0; d < (int)p->dm.size(); d++) {
+      const DmInfo& I = p->dmi[d];
+      const GroupGeom& G = p->groups[I.group].geom;
+      const unsigned char* row = mask + (size_t)d * p->n_dump;
+      need.assign((size_t)G.n_blk, 0);
+      dmp_off[d] = (long long)lists.size();
+      for (long long m = I.first; m <= I.last; m++)
+        if (row[m]) {
+          lists.push_back((int)m);
+          for (long long b = owner_block(G, m * p->L); b <= owner_block(G, (m + 1) * p->L - 1); b++)
+            need[(size_t)b] = 1;
+        }
+      dmp_n[d] = (long long)lists.size() - dmp_off[d];
+      blk_off[d] = (long long)lists.size();
+      for (long long b = 0; b < G.n_blk; b++)
+        if (need[(size_t)b]) lists.push_back((int)b);
+      blk_n[d] = (long long)lists.size() - blk_off[d];
+    }
+    if (!lists.empty()) {
+      if (p->lists_cap < lists.size()) {
+        cudaFree(p->d_lists);
+        p->d_lists = nullptr;
+        p->lists_cap = 0;
+        rc = dev_alloc(p, (void**)&p->d_lists, lists.size() * sizeof(int), "index lists");
+        if (rc) return rc;
+        p->lists_cap = lists.size();
+      }
+      CK(cudaMemcpyAsync(p->d_lists, lists.data(), lists.size() * sizeof(int),
+                         cudaMemcpyHostToDevice, p->stream));
+    }
+  }
   for (int d = 0; d < (int)p->dm.size(); d++) {
     const DmInfo& I = p->dmi[d];
     if (I.last < I.first) continue;
     const GroupGeom& G = p->groups[I.group].geom;
-    const unsigned char* row = mask ? mask + (size_t)d * p->n_dump : nullptr;
-    if (row) {
-      bool any = false;
-      for (long long m = I.first; m <= I.last && !any; m++) any = row[m] != 0;
-      if (!any) continue;
-    }
+    if (mask && dmp_n[d] == 0) continue;
     rc = chirp_for(p, d);
     if (rc) return rc;
-    if (!row) {
+    if (!mask) {
       rc = dedisperse_blocks(p, d, p->d_y, 0, G.n_blk);
       if (!rc) rc = backend_dumps(p, d, be, I.first, I.last + 1, dout);
       if (rc) return rc;
       continue;
     }
-    need.assign((size_t)G.n_blk, 0);
-    for (long long m = I.first; m <= I.last; m++)
-      if (row[m])
-        for (long long b = owner_block(G, m * p->L); b <= owner_block(G, (m + 1) * p->L - 1); b++)
-          need[(size_t)b] = 1;
-    for (long long b = 0; b < G.n_blk;) {
-      if (!need[(size_t)b]) {
-        b++;
-        continue;
+    Group& g = p->groups[I.group];
+    const int* blist = p->d_lists + blk_off[d];
+    const int* dlist = p->d_lists + dmp_off[d];
+    int mk = mark_begin(p);
+    CK(launch_inverse_rows(g.d_spec, p->d_Z, p->d_H, 0, blk_n[d] * p->M, G, p->tw(), p->stream,
+                           blist, p->M));
+    mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
+    mk = mark_begin(p);
+    CK(launch_inverse_cols(p->d_Z, p->d_y, p->N, p->M, 0, blk_n[d] * p->M, G, I.n_hi, I.n_lo,
+                           p->tw(), p->stream, blist));
+    mark_end(p, CHIRP_STAGE_INV_COLS, mk);
+    if (be == kCorrelate || p->beam_mode == CHIRP_BEAM_VIS) {
+      float2* vout = be == kCorrelate ? (float2*)dout + (size_t)d * p->n_dump * p->n_pair : p->d_V;
+      mk = mark_begin(p);
+      CK(launch_correlate(p->d_y, p->N, p->M, p->L, 0, dmp_n[d], I.first, I.last, vout, p->stream,
+                          dlist));
+      mark_end(p, CHIRP_STAGE_CORRELATE, mk);
+      if (be == kBeams) {
+        mk = mark_begin(p);
+        CK(launch_beam_from_vis(p->d_V, p->d_wpair, p->M, p->n_pix, I.first, I.last,
+                                (float*)dout + (size_t)d * p->n_dump * p->n_pix, p->stream, dlist,
+                                dmp_n[d]));
+        mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
       }
-      long long e = b;
-      while (e < G.n_blk && need[(size_t)e]) e++;
-      rc = dedisperse_blocks(p, d, p->d_y, b, e);
-      if (rc) return rc;
-      b = e;
+      continue;
     }
+    // tensor-core and CUDA-core beam modes: runs of consecutive selected dumps
+    const unsigned char* row = mask + (size_t)d * p->n_dump;
     for (long long m = I.first; m <= I.last;) {
       if (!row[m]) {
         m++;
