@@ -93,7 +93,26 @@ typedef struct {
   int fb_int;              /* spectra integrated per filterbank sample, >= 1    */
   const double* fb_dm;     /* [fb_n_dm] trial DMs of the incoherent search      */
   int fb_n_dm;
+  int flags;               /* CHIRP_FLAG_* bits                                 */
+  int fft_row;             /* 0: row length of the two-pass FFT chosen by the
+                              library (or the autotuner); else a power of two
+                              in 256..4096 forced for every FFT-length group
+                              whose column length Nfft/fft_row lies in
+                              16..4096 (other groups keep the default)        */
 } chirp_config;
+
+/* chirp_config.flags */
+#define CHIRP_FLAG_GRAPHS 1   /* replay full device-buffer searches as CUDA graphs:
+                                 the first call with a given (input, output,
+                                 back-end) runs eagerly, the second captures the
+                                 launch sequence, later calls launch the graph.
+                                 Needs a non-default plan stream.  Stage timing
+                                 does not see inside graph launches.          */
+#define CHIRP_FLAG_AUTOTUNE 2 /* time the candidate FFT factorisations (row
+                                 length 512..4096) of every FFT-length group on
+                                 the device at plan creation and keep the
+                                 fastest; results differ from the default split
+                                 only by rounding.  Cached per process.       */
 
 typedef struct {
   long long n_dump;        /* floor(n_samp / dump_len)                          */
@@ -118,6 +137,11 @@ void chirp_plan_destroy(chirp_plan* plan);
 
 /* Sizes derived at creation.  Errors: CHIRP_EINVAL on NULL. */
 int chirp_plan_query(const chirp_plan* plan, chirp_plan_info* info);
+
+/* FFT length and two-pass split of every FFT-length group: nfft[g] =
+ * n_col[g] * n_row[g] (arrays of chirp_plan_info.n_group entries, caller
+ * owned).  Errors: CHIRP_EINVAL on NULL arguments. */
+int chirp_plan_fft_split(const chirp_plan* plan, long long* nfft, int* n_col, int* n_row);
 
 /* Block grid of DM number d: out7 = {Nfft, n_hi, n_lo, max n_hi of the group,
  * max n_lo of the group, step S, number of blocks}.  Errors: CHIRP_EINVAL. */
@@ -271,6 +295,15 @@ int chirpolator_run_selective(chirp_plan* plan, const void* volt, int volt_loc,
                               const unsigned char* cell_mask, void* vis_out, int vis_loc);
 int chimageator_run_selective(chirp_plan* plan, const void* volt, int volt_loc,
                               const unsigned char* cell_mask, float* pow_out, int pow_loc);
+
+/* Several searches (observations of any shapes) queued together: search i
+ * runs plans[i] (backend 0 = chirpolator_run, 1 = chimageator_run) on volts[i]
+ * into outs[i] with the given buffer locations.  Plans created on distinct
+ * streams overlap on the device; calls with host outputs synchronise their
+ * own stream.  Errors: as the single searches (the first failure stops the
+ * batch). */
+int chirp_batch_run(chirp_plan* const* plans, const void* const* volts, const int* volt_locs,
+                    void* const* outs, const int* out_locs, const int* backends, int n);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* chirp_last_error(void);

@@ -32,6 +32,7 @@ __all__ = ["Plan", "PropNet", "load", "build", "CHIRP_HOST", "CHIRP_DEVICE", "BE
 
 CHIRP_HOST, CHIRP_DEVICE = 0, 1
 BEAM_AUTO, BEAM_FP32_SIMT, BEAM_TC_3XBF16, BEAM_VIS = 0, 1, 2, 3
+FLAG_GRAPHS, FLAG_AUTOTUNE = 1, 2
 K_DM_DEFAULT = 4.148808e15
 
 EXPORTED_SYMBOLS = ("chirp_plan_create", "chirp_plan_destroy", "chirp_plan_query",
@@ -42,7 +43,8 @@ EXPORTED_SYMBOLS = ("chirp_plan_create", "chirp_plan_destroy", "chirp_plan_query
                     "chirp_propnet_set_params", "chirp_propnet_get_params",
                     "chirp_propnet_get_grads", "chirp_propnet_forward", "chirp_propnet_backward",
                     "chirp_propnet_train_step", "chirp_propnet_normalize", "chirp_propose_windows",
-                    "chirpolator_run_selective", "chimageator_run_selective", "chirp_last_error")
+                    "chirpolator_run_selective", "chimageator_run_selective", "chirp_batch_run", "chirp_plan_fft_split",
+                    "chirp_last_error")
 STAGES = ("forward", "inv_rows", "inv_cols", "correlate", "beamform", "split", "chirp",
           "incoherent")
 
@@ -61,7 +63,8 @@ class _Config(ctypes.Structure):
                 ("dump_len", ctypes.c_int), ("nfft_min", ctypes.c_longlong),
                 ("pix_lm", ctypes.POINTER(ctypes.c_double)), ("n_pix", ctypes.c_int),
                 ("beam_mode", ctypes.c_int), ("fb_chan", ctypes.c_int), ("fb_int", ctypes.c_int),
-                ("fb_dm", ctypes.POINTER(ctypes.c_double)), ("fb_n_dm", ctypes.c_int)]
+                ("fb_dm", ctypes.POINTER(ctypes.c_double)), ("fb_n_dm", ctypes.c_int),
+                ("flags", ctypes.c_int), ("fft_row", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -135,6 +138,12 @@ def load():
         lib.chirpolator_run_selective.restype = i
         lib.chimageator_run_selective.argtypes = [vp, vp, i, vp, vp, i]
         lib.chimageator_run_selective.restype = i
+        lib.chirp_batch_run.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i),
+                                        ctypes.POINTER(vp), ctypes.POINTER(i), ctypes.POINTER(i), i]
+        lib.chirp_batch_run.restype = i
+        lib.chirp_plan_fft_split.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
+                                             ctypes.POINTER(i), ctypes.POINTER(i)]
+        lib.chirp_plan_fft_split.restype = i
         lib.chirp_plan_status.argtypes = [vp]
         lib.chirp_plan_status.restype = i
         lib.chirp_dedisperse_noalloc.argtypes = [vp, i, ll, ctypes.c_double, ctypes.c_double,
@@ -223,6 +232,27 @@ def chirp_dedisperse_noalloc(volt, f0: float, bw: float, k_dm: float, dm: float,
                                            _stream_handle(stream)))
 
 
+def chirp_batch_run(plans, volts, outs, backends) -> None:
+    """Queue several searches (chirp_batch_run); backends: 0 Chirpolator, 1 Chimageator."""
+    n = len(plans)
+    keep = []
+    vp = (ctypes.c_void_p * n)()
+    vl = (ctypes.c_int * n)()
+    op = (ctypes.c_void_p * n)()
+    ol = (ctypes.c_int * n)()
+    be = (ctypes.c_int * n)(*[int(b) for b in backends])
+    hp = (ctypes.c_void_p * n)(*[pl._h.value for pl in plans])
+    for k in range(n):
+        a, loc, kk = _buf(volts[k], np.complex64, "volt")
+        vp[k], vl[k] = a, loc
+        keep.append(kk)
+        dt = np.complex64 if int(backends[k]) == 0 else np.float32
+        b, loc2, kk2 = _buf(outs[k], dt, "out")
+        op[k], ol[k] = b, loc2
+        keep.append(kk2)
+    _check(load().chirp_batch_run(hp, vp, vl, op, ol, be, n))
+
+
 def chirp_last_error() -> str:
     return load().chirp_last_error().decode(errors="replace")
 
@@ -234,7 +264,7 @@ class Plan:
     def __init__(self, xyz, f0: float, bw: float, n_samp: int, dms, dump_len: int,
                  nfft_min: int, pix_lm=None, k_dm: float = K_DM_DEFAULT,
                  beam_mode: int = BEAM_AUTO, n_ant: int | None = None, stream=None,
-                 fb_chan: int = 0, fb_int: int = 1, fb_dm=None):
+                 fb_chan: int = 0, fb_int: int = 1, fb_dm=None, flags: int = 0, fft_row: int = 0):
         self._xyz = None if xyz is None else np.ascontiguousarray(xyz, dtype=np.float64)
         self._dms = np.ascontiguousarray(np.atleast_1d(dms), dtype=np.float64)
         self._pix = None if pix_lm is None else np.ascontiguousarray(pix_lm, dtype=np.float64)
@@ -259,6 +289,8 @@ class Plan:
         cfg.fb_int = int(fb_int)
         cfg.fb_dm = self._fb_dm.ctypes.data_as(dp) if self._fb_dm is not None else None
         cfg.fb_n_dm = 0 if self._fb_dm is None else int(self._fb_dm.size)
+        cfg.flags = int(flags)
+        cfg.fft_row = int(fft_row)
         self.n_ant, self.n_samp, self.n_dm = cfg.n_ant, cfg.n_samp, cfg.n_dm
         self.n_pix = cfg.n_pix
         self._h = chirp_plan_create(cfg, stream)
@@ -283,6 +315,15 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def fft_split(self):
+        """[(nfft, n_col, n_row)] of every FFT-length group (chirp_plan_fft_split)."""
+        n = self.info["n_group"]
+        nf = (ctypes.c_longlong * n)()
+        nc = (ctypes.c_int * n)()
+        nr = (ctypes.c_int * n)()
+        _check(load().chirp_plan_fft_split(self._h, nf, nc, nr))
+        return [(int(nf[g]), int(nc[g]), int(nr[g])) for g in range(n)]
 
     def dm_layout(self, d: int) -> dict:
         out = (ctypes.c_longlong * 7)()

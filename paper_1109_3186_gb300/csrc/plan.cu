@@ -8,6 +8,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <vector>
 
@@ -113,6 +116,15 @@ struct chirp_plan {
   float* d_fb_D = nullptr;     // staging for host outputs
   int* d_lists = nullptr;      // selective searches: block and dump index lists
   size_t lists_cap = 0;
+  // CUDA-graph replay of full device-buffer searches (chirp_config.flags)
+  bool use_graphs = false;
+  struct GraphEntry {
+    const void* in;
+    void* out;
+    int be;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
   void* d_out = nullptr;     // staging for host outputs
   size_t out_bytes = 0;
   size_t ws_bytes = 0;
@@ -165,8 +177,90 @@ void release(chirp_plan* p) {
   cudaFree(p->d_fb_S);
   cudaFree(p->d_fb_D);
   cudaFree(p->d_lists);
+  for (auto& g : p->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   cudaFree(p->d_out);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+}
+
+// Two-pass FFT split autotuner.  Every split Nfft = n1 * n2 with the row
+// length n2 in 256..4096 and the column length n1 in 16..4096 gives the same
+// transform up to rounding; the kernels' memory behaviour differs (row tiles
+// of 4096 points hold 4096 / n2 rows, column tiles 4096 / n1 columns).  The
+// forward pass and one DM's inverse passes over the group's blocks are timed
+// with CUDA events for each candidate (one warm-up, best of three) on the
+// plan's own workspace, and the fastest split is kept for the (device, Nfft,
+// antennas, blocks) key for the rest of the process.
+cudaError_t autotune_split(chirp_plan* p, Group& g) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, long long, int, long long>, int> cache;
+  GroupGeom& G = g.geom;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const auto key = std::make_tuple(dev, G.nfft, p->M, G.n_blk);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      G.n2 = it->second;
+      G.n1 = (int)(G.nfft / G.n2);
+      return cudaSuccess;
+    }
+  }
+  std::vector<int> cand;
+  for (int n2 = 256; n2 <= 4096; n2 *= 2)
+    if (G.nfft / n2 >= 16 && G.nfft / n2 <= 4096) cand.push_back(n2);
+  const int n2_default = G.n2;
+  if (cand.size() > 1) {
+    const size_t ybytes = (size_t)p->M * p->N * sizeof(float2);
+    e = cudaMemsetAsync(p->d_y, 0, ybytes, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_H, 0, (size_t)G.nfft * sizeof(float2), p->stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const long long n_seq = (long long)p->M * G.n_blk;
+    const long long nq = inverse_chunk_sequences(G, n_seq);
+    float best = 1e30f;
+    int best_n2 = n2_default;
+    for (int n2 : cand) {
+      if (e != cudaSuccess) break;
+      G.n2 = n2;
+      G.n1 = (int)(G.nfft / n2);
+      auto pass = [&]() -> cudaError_t {
+        cudaError_t r = launch_forward(p->d_y, p->N, p->M, G, g.d_spec, p->tw(), p->stream);
+        for (long long q0 = 0; r == cudaSuccess && q0 < n_seq; q0 += nq) {
+          const long long n = std::min(nq, n_seq - q0);
+          r = launch_inverse_rows(g.d_spec, p->d_Z, p->d_H, q0, n, G, p->tw(), p->stream);
+          if (r == cudaSuccess)
+            r = launch_inverse_cols(p->d_Z, p->d_y, p->N, p->M, q0, n, G, G.n_hi_max, G.n_lo_max,
+                                    p->tw(), p->stream);
+        }
+        return r;
+      };
+      e = pass();
+      for (int rep = 0; e == cudaSuccess && rep < 3; rep++) {
+        e = cudaEventRecord(e0, p->stream);
+        if (e == cudaSuccess) e = pass();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) {
+          best = ms;
+          best_n2 = n2;
+        }
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    G.n2 = best_n2;
+    G.n1 = (int)(G.nfft / G.n2);
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = G.n2;
+  return cudaSuccess;
 }
 
 // events bracketing one kernel launch of a stage (no-op unless timing is on)
@@ -219,6 +313,10 @@ int validate(const chirp_config* c) {
     return fail(CHIRP_EINVAL, "dump_len must be in 1..n_samp");
   if (!is_pow2(c->nfft_min) || c->nfft_min < 256 || c->nfft_min > (1LL << 24))
     return fail(CHIRP_EINVAL, "nfft_min must be a power of two in 256..2^24");
+  if (c->fft_row != 0 && (!is_pow2(c->fft_row) || c->fft_row < 256 || c->fft_row > 4096))
+    return fail(CHIRP_EINVAL, "fft_row must be 0 or a power of two in 256..4096");
+  if (c->flags & ~(CHIRP_FLAG_GRAPHS | CHIRP_FLAG_AUTOTUNE))
+    return fail(CHIRP_EINVAL, "unknown flag bits 0x%x", c->flags);
   if (c->n_pix < 0) return fail(CHIRP_EINVAL, "n_pix must be >= 0");
   if (c->n_pix > 0 && (!c->pix_lm || !c->xyz_m))
     return fail(CHIRP_EINVAL, "beams need pix_lm and xyz_m");
@@ -284,6 +382,11 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   // AUTO: tensor cores (split BF16, FP32 accumulate) for the beam GEMM
   p->beam_mode = cfg->beam_mode == CHIRP_BEAM_AUTO ? CHIRP_BEAM_TC_3XBF16 : cfg->beam_mode;
   p->stream = (cudaStream_t)stream;
+  p->use_graphs = (cfg->flags & CHIRP_FLAG_GRAPHS) != 0;
+  if (p->use_graphs && p->stream == nullptr) {
+    delete p;
+    return fail(CHIRP_EINVAL, "CUDA graphs need a plan stream other than the legacy default stream");
+  }
   p->n_dump = p->N / p->L;
   p->n_pair = p->M * (p->M + 1) / 2;
 
@@ -323,6 +426,10 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
     G.log2n = ilog2ll(G.nfft);
     G.n1 = (int)std::max<long long>(16, G.nfft / 4096);
     G.n2 = (int)(G.nfft / G.n1);
+    if (cfg->fft_row > 0 && G.nfft / cfg->fft_row >= 16 && G.nfft / cfg->fft_row <= 4096) {
+      G.n2 = cfg->fft_row;
+      G.n1 = (int)(G.nfft / G.n2);
+    }
     G.n_hi_max = 0;
     G.n_lo_max = 0;
     for (int d : g.dms) {
@@ -494,6 +601,9 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   if (e == cudaSuccess && !fb_shift.empty())
     e = cudaMemcpyAsync(p->d_fb_shift, fb_shift.data(), fb_shift.size() * sizeof(int),
                         cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess && (cfg->flags & CHIRP_FLAG_AUTOTUNE) && cfg->fft_row == 0)
+    for (auto& g : p->groups)
+      if (e == cudaSuccess) e = autotune_split(p, g);
   for (auto& g : p->groups)
     if (e == cudaSuccess)
       e = launch_build_phase_table(g.d_G, g.geom, p->f0, p->bw, p->kdm, p->stream);
@@ -691,20 +801,9 @@ int backend_dumps(chirp_plan* p, int d, Backend be, long long m0, long long m1, 
 // byte is nonzero: for each DM the blocks owning a selected dump are inverse
 // transformed (runs of consecutive blocks per launch) and the back-end runs on
 // runs of consecutive selected dumps.  Outputs are zero elsewhere.
-int run_search(chirp_plan* p, const void* volt, int volt_loc, const unsigned char* mask,
-               Backend be, void* out_user, int out_loc) {
-  g_err[0] = 0;
-  if (!p) return fail(CHIRP_EINVAL, "plan is NULL");
-  if (be == kBeams && p->n_pix <= 0) return fail(CHIRP_EUNSUPPORTED, "plan was created without pixels");
-  const float2* dx;
-  int rc = stage_input(p, volt, volt_loc, &dx);
-  if (rc) return rc;
-  const size_t per_dm = be == kCorrelate ? (size_t)p->n_dump * p->n_pair : (size_t)p->n_dump * p->n_pix;
-  const size_t bytes = per_dm * p->dm.size() * (be == kCorrelate ? sizeof(float2) : sizeof(float));
-  void* dout;
-  rc = out_buffer(p, out_user, out_loc, bytes, &dout);
-  if (rc) return rc;
-  rc = forward_all(p, dx);
+int enqueue_search(chirp_plan* p, const float2* dx, const unsigned char* mask, Backend be,
+                   void* dout, size_t bytes) {
+  int rc = forward_all(p, dx);
   if (rc) return rc;
   CK(cudaMemsetAsync(dout, 0, bytes, p->stream));  // invalid / unselected cells stay zero
   // Selective: per DM, the list of blocks owning a selected dump and the list
@@ -800,6 +899,67 @@ int run_search(chirp_plan* p, const void* volt, int volt_loc, const unsigned cha
       m = e;
     }
   }
+  return CHIRP_OK;
+}
+
+// Full searches on device buffers replay a CUDA graph: the first call with a
+// given (input, output, back-end) runs eagerly (lazy allocations and kernel
+// attributes happen there), the second captures and instantiates the launch
+// sequence, later calls launch the graph.
+int graph_search(chirp_plan* p, const float2* dx, Backend be, void* dout, size_t bytes) {
+  for (auto& g : p->graphs) {
+    if (g.in != dx || g.out != dout || g.be != (int)be) continue;
+    if (g.exec) {
+      CK(cudaGraphLaunch(g.exec, p->stream));
+      return CHIRP_OK;
+    }
+    const bool timing = p->timing;
+    p->timing = false;  // no event marks inside a capture
+    CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_search(p, dx, nullptr, be, dout, bytes);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->stream, &graph);
+    p->timing = timing;
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(CHIRP_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      g.exec = nullptr;
+      return fail(CHIRP_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    CK(cudaGraphLaunch(g.exec, p->stream));
+    return CHIRP_OK;
+  }
+  if (p->graphs.size() >= 8) {
+    if (p->graphs.front().exec) cudaGraphExecDestroy(p->graphs.front().exec);
+    p->graphs.erase(p->graphs.begin());
+  }
+  p->graphs.push_back({dx, dout, (int)be, nullptr});
+  return enqueue_search(p, dx, nullptr, be, dout, bytes);
+}
+
+int run_search(chirp_plan* p, const void* volt, int volt_loc, const unsigned char* mask,
+               Backend be, void* out_user, int out_loc) {
+  g_err[0] = 0;
+  if (!p) return fail(CHIRP_EINVAL, "plan is NULL");
+  if (be == kBeams && p->n_pix <= 0) return fail(CHIRP_EUNSUPPORTED, "plan was created without pixels");
+  const float2* dx;
+  int rc = stage_input(p, volt, volt_loc, &dx);
+  if (rc) return rc;
+  const size_t per_dm = be == kCorrelate ? (size_t)p->n_dump * p->n_pair : (size_t)p->n_dump * p->n_pix;
+  const size_t bytes = per_dm * p->dm.size() * (be == kCorrelate ? sizeof(float2) : sizeof(float));
+  void* dout;
+  rc = out_buffer(p, out_user, out_loc, bytes, &dout);
+  if (rc) return rc;
+  if (p->use_graphs && !mask && volt_loc == CHIRP_DEVICE && out_loc == CHIRP_DEVICE)
+    rc = graph_search(p, dx, be, dout, bytes);
+  else
+    rc = enqueue_search(p, dx, mask, be, dout, bytes);
+  if (rc) return rc;
   rc = finish_out(p, out_user, out_loc, dout, bytes);
   if (rc) return rc;
   if (be == kBeams && out_loc == CHIRP_HOST) return chirp_plan_status(p);
@@ -884,6 +1044,31 @@ int chirp_incoherent_run(chirp_plan* p, const void* volt, int volt_loc, float* S
     CK(cudaMemcpyAsync(D_out, dD, dbytes, cudaMemcpyDeviceToHost, p->stream));
     if (S_out) CK(cudaMemcpyAsync(S_out, dS, sbytes, cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
+  }
+  return CHIRP_OK;
+}
+
+int chirp_plan_fft_split(const chirp_plan* p, long long* nfft, int* n_col, int* n_row) {
+  g_err[0] = 0;
+  if (!p || !nfft || !n_col || !n_row) return fail(CHIRP_EINVAL, "NULL argument");
+  for (size_t g = 0; g < p->groups.size(); g++) {
+    nfft[g] = p->groups[g].geom.nfft;
+    n_col[g] = p->groups[g].geom.n1;
+    n_row[g] = p->groups[g].geom.n2;
+  }
+  return CHIRP_OK;
+}
+
+int chirp_batch_run(chirp_plan* const* plans, const void* const* volts, const int* volt_locs,
+                    void* const* outs, const int* out_locs, const int* backends, int n) {
+  g_err[0] = 0;
+  if (n < 0 || (n > 0 && (!plans || !volts || !volt_locs || !outs || !out_locs || !backends)))
+    return fail(CHIRP_EINVAL, "bad batch arguments");
+  for (int i = 0; i < n; i++) {
+    if (backends[i] != 0 && backends[i] != 1) return fail(CHIRP_EINVAL, "backend %d must be 0 or 1", i);
+    int rc = run_search(plans[i], volts[i], volt_locs[i], nullptr,
+                        backends[i] == 0 ? kCorrelate : kBeams, outs[i], out_locs[i]);
+    if (rc) return rc;
   }
   return CHIRP_OK;
 }
