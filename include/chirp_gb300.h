@@ -59,13 +59,26 @@ extern "C" {
 #define CHIRP_DEVICE 1
 
 /* contraction used by the Chimageator back-end */
-#define CHIRP_BEAM_AUTO 0      /* tensor-core split-bf16 when available      */
+#define CHIRP_BEAM_AUTO 0      /* CHIRP_BEAM_TC_3XBF16 where its tiles fit in
+                                  shared memory (up to 60 antennas), else
+                                  CHIRP_BEAM_VIS                              */
 #define CHIRP_BEAM_FP32_SIMT 1 /* plain FP32 FMA on the CUDA cores           */
-#define CHIRP_BEAM_TC_3XBF16 2 /* tcgen05, 3-term bf16 split, FP32 accumulate */
+#define CHIRP_BEAM_TC_3XBF16 2 /* tcgen05, 3-term bf16 split, FP32 accumulate;
+                                  CHIRP_EUNSUPPORTED above 60 antennas       */
 #define CHIRP_BEAM_VIS 3       /* exact identity sum_t |w.y|^2 = w^H V w: the
                                   per-dump visibilities V (Chirpolator output)
                                   are formed first, then a quadratic form per
                                   pixel; FP32 CUDA cores                      */
+#define CHIRP_BEAM_TC_BF16 4   /* reduced-precision form: tcgen05, operands
+                                  rounded once to BF16 (one product), FP32
+                                  accumulate; relative error of a beam power
+                                  ~1e-3 (held to 1e-2)                        */
+
+/* element type of the voltage input (chirp_config.in_type) */
+#define CHIRP_IN_C64 0         /* complex64: interleaved FP32 (re, im)        */
+#define CHIRP_IN_CI8 1         /* complex int8: interleaved (re, im) bytes,
+                                  value = in_scale[a] * (re + j im); converted
+                                  to FP32 inside the first FFT pass           */
 
 typedef struct chirp_plan chirp_plan;
 
@@ -94,6 +107,9 @@ typedef struct {
   const double* fb_dm;     /* [fb_n_dm] trial DMs of the incoherent search      */
   int fb_n_dm;
   int flags;               /* CHIRP_FLAG_* bits                                 */
+  int in_type;             /* CHIRP_IN_*: element type of every voltage input
+                              of this plan's runs ([n_ant][n_samp] elements) */
+  const float* in_scale;   /* [n_ant] scale of CHIRP_IN_CI8 input; NULL = 1   */
   int fft_row;             /* 0: row length of the two-pass FFT chosen by the
                               library (or the autotuner); else a power of two
                               in 256..4096 forced for every FFT-length group
@@ -152,7 +168,8 @@ int chirp_dm_layout(const chirp_plan* plan, int d, long long* out7);
 int chirp_dump_range(const chirp_plan* plan, long long* first, long long* last);
 
 /* Coherent dedispersion of one trial DM (Sec. 2.3.2), the shared first stage
- * of both searches.  volt: complex64 [n_ant][n_samp] at volt_loc; y_out:
+ * of both searches.  volt: [n_ant][n_samp] elements of the plan's in_type
+ * (complex64 or complex int8, the same for every run below) at volt_loc; y_out:
  * complex64 [n_ant][n_samp] at y_loc; samples outside the DM's valid range
  * are zero.  Errors: CHIRP_EINVAL, CHIRP_ECUDA. */
 int chirp_dedisperse_run(chirp_plan* plan, const void* volt, int volt_loc, int d, void* y_out,
@@ -187,7 +204,7 @@ int chimageator_run(chirp_plan* plan, const void* volt, int volt_loc, float* pow
  * Then D[d][t] = sum_c S[c][t + s_c(d)] with the Eq. dmdelay lag relative to
  * f0 in filterbank samples, s_c = floor(k DM (f_c^-2 - f0^-2) / t_fb + 1/2),
  * t_fb = fb_chan fb_int / B; D is zero outside [-min s, T_fb - max s).
- *  volt: complex64 [n_ant][n_samp] at volt_loc (not modified);
+ *  volt: [n_ant][n_samp] of the plan's in_type at volt_loc (not modified);
  *  S_out: float32 [fb_chan][T_fb] or NULL;  D_out: float32 [fb_n_dm][T_fb];
  *  both at out_loc.  Needs fb_chan > 0 at plan creation.
  * Errors: CHIRP_EINVAL, CHIRP_EUNSUPPORTED, CHIRP_ECUDA. */

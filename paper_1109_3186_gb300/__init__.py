@@ -31,7 +31,8 @@ __all__ = ["Plan", "PropNet", "load", "build", "CHIRP_HOST", "CHIRP_DEVICE", "BE
            "EXPORTED_SYMBOLS"]
 
 CHIRP_HOST, CHIRP_DEVICE = 0, 1
-BEAM_AUTO, BEAM_FP32_SIMT, BEAM_TC_3XBF16, BEAM_VIS = 0, 1, 2, 3
+BEAM_AUTO, BEAM_FP32_SIMT, BEAM_TC_3XBF16, BEAM_VIS, BEAM_TC_BF16 = 0, 1, 2, 3, 4
+IN_C64, IN_CI8 = 0, 1
 FLAG_GRAPHS, FLAG_AUTOTUNE = 1, 2
 K_DM_DEFAULT = 4.148808e15
 
@@ -64,7 +65,8 @@ class _Config(ctypes.Structure):
                 ("pix_lm", ctypes.POINTER(ctypes.c_double)), ("n_pix", ctypes.c_int),
                 ("beam_mode", ctypes.c_int), ("fb_chan", ctypes.c_int), ("fb_int", ctypes.c_int),
                 ("fb_dm", ctypes.POINTER(ctypes.c_double)), ("fb_n_dm", ctypes.c_int),
-                ("flags", ctypes.c_int), ("fft_row", ctypes.c_int)]
+                ("flags", ctypes.c_int), ("in_type", ctypes.c_int),
+                ("in_scale", ctypes.POINTER(ctypes.c_float)), ("fft_row", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -177,6 +179,32 @@ def _buf(a, dtype_np, what: str):
     return ctypes.c_void_p(arr.ctypes.data), CHIRP_HOST, arr
 
 
+def _vbuf(a, in_type=None):
+    """_buf of a voltage input: complex64 [M, N], or complex int8 as int8
+    [M, N, 2] (in_type None accepts either)."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        is_i8 = a.dtype == torch.int8
+    else:
+        is_i8 = np.asarray(a).dtype == np.int8
+    if in_type is not None and is_i8 != (in_type == IN_CI8):
+        raise TypeError("volt must be %s for this plan"
+                        % ("int8 [n_ant, n_samp, 2]" if in_type == IN_CI8 else "complex64"))
+    if not is_i8:
+        return _buf(a, np.complex64, "volt")
+    if torch is not None and isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            raise TypeError("volt must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), (CHIRP_DEVICE if a.is_cuda else CHIRP_HOST), a
+    arr = np.asarray(a)
+    if not arr.flags["C_CONTIGUOUS"]:
+        raise TypeError("volt must be C-contiguous")
+    return ctypes.c_void_p(arr.ctypes.data), CHIRP_HOST, arr
+
+
 def _stream_handle(stream):
     if stream is not None:
         return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
@@ -200,20 +228,20 @@ def chirp_plan_destroy(h) -> None:
     load().chirp_plan_destroy(h)
 
 
-def chirp_dedisperse_run(h, volt, d: int, y_out) -> None:
-    vp, vl, _k1 = _buf(volt, np.complex64, "volt")
+def chirp_dedisperse_run(h, volt, d: int, y_out, in_type=None) -> None:
+    vp, vl, _k1 = _vbuf(volt, in_type)
     yp, yl, _k2 = _buf(y_out, np.complex64, "y_out")
     _check(load().chirp_dedisperse_run(h, vp, vl, int(d), yp, yl))
 
 
-def chirpolator_run(h, volt, vis_out) -> None:
-    vp, vl, _k1 = _buf(volt, np.complex64, "volt")
+def chirpolator_run(h, volt, vis_out, in_type=None) -> None:
+    vp, vl, _k1 = _vbuf(volt, in_type)
     op, ol, _k2 = _buf(vis_out, np.complex64, "vis_out")
     _check(load().chirpolator_run(h, vp, vl, op, ol))
 
 
-def chimageator_run(h, volt, pow_out) -> None:
-    vp, vl, _k1 = _buf(volt, np.complex64, "volt")
+def chimageator_run(h, volt, pow_out, in_type=None) -> None:
+    vp, vl, _k1 = _vbuf(volt, in_type)
     op, ol, _k2 = _buf(pow_out, np.float32, "pow_out")
     _check(load().chimageator_run(h, vp, vl, op, ol))
 
@@ -243,7 +271,7 @@ def chirp_batch_run(plans, volts, outs, backends) -> None:
     be = (ctypes.c_int * n)(*[int(b) for b in backends])
     hp = (ctypes.c_void_p * n)(*[pl._h.value for pl in plans])
     for k in range(n):
-        a, loc, kk = _buf(volts[k], np.complex64, "volt")
+        a, loc, kk = _vbuf(volts[k], getattr(plans[k], "in_type", None))
         vp[k], vl[k] = a, loc
         keep.append(kk)
         dt = np.complex64 if int(backends[k]) == 0 else np.float32
@@ -264,7 +292,8 @@ class Plan:
     def __init__(self, xyz, f0: float, bw: float, n_samp: int, dms, dump_len: int,
                  nfft_min: int, pix_lm=None, k_dm: float = K_DM_DEFAULT,
                  beam_mode: int = BEAM_AUTO, n_ant: int | None = None, stream=None,
-                 fb_chan: int = 0, fb_int: int = 1, fb_dm=None, flags: int = 0, fft_row: int = 0):
+                 fb_chan: int = 0, fb_int: int = 1, fb_dm=None, flags: int = 0, fft_row: int = 0,
+                 in_type: int = IN_C64, in_scale=None):
         self._xyz = None if xyz is None else np.ascontiguousarray(xyz, dtype=np.float64)
         self._dms = np.ascontiguousarray(np.atleast_1d(dms), dtype=np.float64)
         self._pix = None if pix_lm is None else np.ascontiguousarray(pix_lm, dtype=np.float64)
@@ -291,6 +320,12 @@ class Plan:
         cfg.fb_n_dm = 0 if self._fb_dm is None else int(self._fb_dm.size)
         cfg.flags = int(flags)
         cfg.fft_row = int(fft_row)
+        cfg.in_type = int(in_type)
+        self.in_type = int(in_type)
+        self._scale = (None if in_scale is None
+                       else np.ascontiguousarray(np.atleast_1d(in_scale), dtype=np.float32))
+        cfg.in_scale = (self._scale.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+                        if self._scale is not None else None)
         self.n_ant, self.n_samp, self.n_dm = cfg.n_ant, cfg.n_samp, cfg.n_dm
         self.n_pix = cfg.n_pix
         self._h = chirp_plan_create(cfg, stream)
@@ -338,15 +373,15 @@ class Plan:
         return np.array(first[:], dtype=np.int64), np.array(last[:], dtype=np.int64)
 
     def dedisperse(self, volt, d: int, y_out):
-        chirp_dedisperse_run(self._h, volt, d, y_out)
+        chirp_dedisperse_run(self._h, volt, d, y_out, self.in_type)
         return y_out
 
     def chirpolator(self, volt, vis_out):
-        chirpolator_run(self._h, volt, vis_out)
+        chirpolator_run(self._h, volt, vis_out, self.in_type)
         return vis_out
 
     def chimageator(self, volt, pow_out):
-        chimageator_run(self._h, volt, pow_out)
+        chimageator_run(self._h, volt, pow_out, self.in_type)
         return pow_out
 
     def _mask(self, cell_mask):
@@ -357,7 +392,7 @@ class Plan:
 
     def chirpolator_selective(self, volt, cell_mask, vis_out):
         m = self._mask(cell_mask)
-        vp, vl, _k1 = _buf(volt, np.complex64, "volt")
+        vp, vl, _k1 = _vbuf(volt, self.in_type)
         op, ol, _k2 = _buf(vis_out, np.complex64, "vis_out")
         _check(load().chirpolator_run_selective(self._h, vp, vl, ctypes.c_void_p(m.ctypes.data),
                                                 op, ol))
@@ -365,7 +400,7 @@ class Plan:
 
     def chimageator_selective(self, volt, cell_mask, pow_out):
         m = self._mask(cell_mask)
-        vp, vl, _k1 = _buf(volt, np.complex64, "volt")
+        vp, vl, _k1 = _vbuf(volt, self.in_type)
         op, ol, _k2 = _buf(pow_out, np.float32, "pow_out")
         _check(load().chimageator_run_selective(self._h, vp, vl, ctypes.c_void_p(m.ctypes.data),
                                                 op, ol))
@@ -378,7 +413,7 @@ class Plan:
     def incoherent(self, volt, D_out, S_out=None):
         """Filterbank S [fb_chan, T_fb] (optional) and incoherent dedispersion
         D [fb_n_dm, T_fb] of the voltages (chirp_incoherent_run)."""
-        vp, vl, _k1 = _buf(volt, np.complex64, "volt")
+        vp, vl, _k1 = _vbuf(volt, self.in_type)
         dp_, dl, _k2 = _buf(D_out, np.float32, "D_out")
         sp_ = ctypes.c_void_p(0)
         if S_out is not None:

@@ -18,10 +18,17 @@
 // adjacent 8-wide core-matrix columns.  For 12 antennas (24 real K) that is
 // 72 useful of 80 MMA K (5 steps).
 //
+// Reduced-precision form (one term): the K axis holds only [B_h] against
+// [A_h] (B tile padded to an even number of 8-wide k-groups with zeros), so
+// 12 antennas take 3 MMA K steps instead of 5, with BF16 rounding of both
+// operands (relative error ~2^-9 per product, FP32 accumulation).
+//
 // Layouts (no swizzle, K-major, 8-row x 16-byte core matrices):
 //   A image per 128-row tile: [m-group 16][k-slot 2*ksteps][8 rows][8 bf16]
-//   B tile of NT = 128 samples: [n-group 16][k-group 2G][8 samples][8 bf16]
-//     k-group g < G: heads of real K 8g..8g+7; g >= G: tails of 8(g-G)...
+//   B tile of NT samples: [n-group NT/8][k-group GB][8 samples][8 bf16]
+//     three terms: GB = 2G, k-group g < G: heads of real K 8g..8g+7,
+//     g >= G: tails of 8(g-G)...;  one term: GB = G rounded up to even, heads
+//     only, the padding group zero.
 //     real K index k = 2a + c (antenna a, c = 0 real / 1 imaginary).
 // Both images are written in global memory in exactly this order so that one
 // cp.async.bulk moves a whole tile.
@@ -60,7 +67,7 @@ constexpr int RMAX = 8;        // row tiles per CTA (weights resident in smem)
 template <int NT>
 struct BeamCfg {
   static constexpr int NACC = 512 / NT;           // TMEM accumulators
-  static constexpr int NSTAGE = NT == 256 ? 3 : 4;
+  static constexpr int NSTAGE = NT == 256 ? 3 : 4;  // B ring depth (fewer when smem is short)
   static constexpr int EPI_WARPS = NT == 256 ? 16 : 8;
   static constexpr int THREADS = 64 + 32 * EPI_WARPS;
   static constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, NT);
@@ -72,11 +79,11 @@ struct BeamSmemPlan {
 };
 
 template <int NT>
-__host__ __device__ inline BeamSmemPlan beam_smem_plan(int R, int ksteps, int G) {
+__host__ __device__ inline BeamSmemPlan beam_smem_plan(int R, int ksteps, int G, int nstage) {
   BeamSmemPlan s;
   s.a_bytes = (uint32_t)R * ksteps * 4096u;
-  s.b_stage_bytes = (uint32_t)NT * 2u * G * 16u;
-  s.red_off = s.a_bytes + BeamCfg<NT>::NSTAGE * s.b_stage_bytes;
+  s.b_stage_bytes = (uint32_t)NT * (uint32_t)G * 16u;  // G here = k-groups per B tile
+  s.red_off = s.a_bytes + (uint32_t)nstage * s.b_stage_bytes;
   s.bar_off = s.red_off + BeamCfg<NT>::RED_BYTES;
   s.total = s.bar_off + 256;
   return s;
@@ -91,16 +98,18 @@ struct BeamArgs {
   long long first;     // first valid dump
   long long n_dumps;   // valid dumps of this DM
   long long dumps_per_cta;
-  int L, n_pix, n_rowtiles, R, G, ksteps;
+  int L, n_pix, n_rowtiles, R, GB, bwrap, ksteps;  // GB: k-groups per B tile
+  int nstage;          // B ring depth, 2 .. BeamCfg<NT>::NSTAGE
 };
 
 template <int NT>
 __global__ void __launch_bounds__(BeamCfg<NT>::THREADS, 1) k_beam_tc(BeamArgs args) {
   constexpr int NACC = BeamCfg<NT>::NACC;
-  constexpr int NSTAGE = BeamCfg<NT>::NSTAGE;
+  constexpr int NSTAGE = BeamCfg<NT>::NSTAGE;  // barrier slots; the ring uses nst of them
+  const int nst = args.nstage;
   constexpr uint32_t IDESC = BeamCfg<NT>::IDESC;
   extern __shared__ __align__(1024) uint8_t smem[];
-  const BeamSmemPlan sp = beam_smem_plan<NT>(args.R, args.ksteps, args.G);
+  const BeamSmemPlan sp = beam_smem_plan<NT>(args.R, args.ksteps, args.GB, nst);
   float* red = (float*)(smem + sp.red_off);  // NT = 256: [4 slices][RMAX][128 rows]
   uint8_t* smA = smem;
   uint8_t* smB = smem + sp.a_bytes;
@@ -136,7 +145,7 @@ __global__ void __launch_bounds__(BeamCfg<NT>::THREADS, 1) k_beam_tc(BeamArgs ar
   const uint32_t a_tile_bytes = (uint32_t)args.ksteps * 4096u;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NSTAGE; s++) {
+    for (int s = 0; s < nst; s++) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
@@ -169,8 +178,8 @@ __global__ void __launch_bounds__(BeamCfg<NT>::THREADS, 1) k_beam_tc(BeamArgs ar
                      a_tile_bytes, abar);
       long long issued = 0;
       for (long long i = 0; i < n_tiles; i++) {
-        const int s = (int)(i % NSTAGE);
-        const uint32_t ph = (uint32_t)((i / NSTAGE) & 1);
+        const int s = (int)(i % nst);
+        const uint32_t ph = (uint32_t)((i / nst) & 1);
         if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
           raise();
           break;
@@ -184,19 +193,19 @@ __global__ void __launch_bounds__(BeamCfg<NT>::THREADS, 1) k_beam_tc(BeamArgs ar
       if (*abort_flag) {
         // let every copy this thread issued land before the CTA goes away
         tc::mbar_wait(abar, 0, nullptr, 1u << 22);
-        for (long long i = issued > NSTAGE ? issued - NSTAGE : 0; i < issued; i++)
-          tc::mbar_wait(&full[i % NSTAGE], (uint32_t)((i / NSTAGE) & 1), nullptr, 1u << 22);
+        for (long long i = issued > nst ? issued - nst : 0; i < issued; i++)
+          tc::mbar_wait(&full[i % nst], (uint32_t)((i / nst) & 1), nullptr, 1u << 22);
       }
     } else if (warp == 1 && lane == 0) {
       // ------------------------------------------------------ MMA issuer
       const uint32_t a_base = tc::smem_u32(smA), b_base = tc::smem_u32(smB);
-      const uint32_t a_sbo = 2u * args.ksteps * 128u, b_sbo = 2u * args.G * 128u;
+      const uint32_t a_sbo = 2u * args.ksteps * 128u, b_sbo = (uint32_t)args.GB * 128u;
       bool ok = tc::mbar_wait(abar, 0, abort_flag);
       if (!ok) raise();
       long long u = 0;
       for (long long i = 0; ok && i < n_tiles; i++) {
-        const int s = (int)(i % NSTAGE);
-        const uint32_t ph = (uint32_t)((i / NSTAGE) & 1);
+        const int s = (int)(i % nst);
+        const uint32_t ph = (uint32_t)((i / nst) & 1);
         if (!tc::mbar_wait(&full[s], ph, abort_flag)) {
           raise();
           break;
@@ -214,7 +223,7 @@ __global__ void __launch_bounds__(BeamCfg<NT>::THREADS, 1) k_beam_tc(BeamArgs ar
           const uint32_t d = tmem + (uint32_t)(acc * NT);
           for (int ks = 0; r < R_eff && ks < args.ksteps; ks++) {
             const int p0 = 2 * ks;
-            const int bg = p0 < 2 * args.G ? p0 : p0 - 2 * args.G;
+            const int bg = p0 < args.bwrap ? p0 : p0 - args.bwrap;
             const uint64_t ad = tc::sdesc(a_base + r * a_tile_bytes + ks * 256u, 128u, a_sbo);
             const uint64_t bd =
                 tc::sdesc(b_base + s * sp.b_stage_bytes + bg * 128u, 128u, b_sbo);
@@ -422,14 +431,15 @@ __global__ void __launch_bounds__(BeamCfg<NT>::THREADS, 1) k_beam_tc(BeamArgs ar
   }
 }
 
-// y [n_ant][n_samp] complex64 -> B image tiles (BF16 heads and tails).
+// y [n_ant][n_samp] complex64 -> B image tiles: BF16 heads and (three
+// terms) tails, or (one term) heads and a zero padding group when G is odd.
 // Thread (u, j): sample t = t_begin + u, real-K group j (antennas 4j..4j+3).
-__global__ void k_split_bf16(const float2* __restrict__ y, long long n_samp, int M, int G,
-                             long long t_begin, long long t_end, long long n_tiles, int NT,
-                             uint8_t* __restrict__ b_img) {
+__global__ void k_split_bf16(const float2* __restrict__ y, long long n_samp, int M, int G, int GB,
+                             int terms, long long t_begin, long long t_end, long long n_tiles,
+                             int NT, uint8_t* __restrict__ b_img) {
   const long long U = n_tiles * NT;
   const long long total = U * G;
-  const size_t tile_bytes = (size_t)NT * 2 * G * 16;
+  const size_t tile_bytes = (size_t)NT * GB * 16;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(idx / U);
@@ -455,10 +465,14 @@ __global__ void k_split_bf16(const float2* __restrict__ y, long long n_samp, int
     }
     const long long tile = u / NT;
     const int n = (int)(u % NT);
-    uint8_t* base = b_img + (size_t)tile * tile_bytes + (size_t)(n / 8) * (2 * G * 128) +
+    uint8_t* base = b_img + (size_t)tile * tile_bytes + (size_t)(n / 8) * (GB * 128) +
                     (size_t)(n % 8) * 16;
     *reinterpret_cast<uint4*>(base + (size_t)j * 128) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-    *reinterpret_cast<uint4*>(base + (size_t)(G + j) * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    if (terms == 3)
+      *reinterpret_cast<uint4*>(base + (size_t)(G + j) * 128) =
+          make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    else if (j == G - 1 && GB > G)
+      *reinterpret_cast<uint4*>(base + (size_t)G * 128) = make_uint4(0u, 0u, 0u, 0u);
   }
 }
 
@@ -479,9 +493,10 @@ float bf16_to_float(uint16_t h) {
 
 // A image (see the layout notes at the top) from FP64 weights W [n_pix][n_ant]
 // given as interleaved (re, im).  Rows past 2 n_pix and antennas past n_ant
-// are zero, as is the padding k-slot.
-std::vector<uint8_t> build_beam_a_image(const double* W, int n_ant, int n_pix) {
-  const int G = beam_tc_groups(n_ant), ks = beam_tc_ksteps(n_ant);
+// are zero, as are the padding k-slots.  Slots: three terms [h h l 0],
+// one term [h 0].
+std::vector<uint8_t> build_beam_a_image(const double* W, int n_ant, int n_pix, int terms) {
+  const int G = beam_tc_groups(n_ant), ks = beam_tc_ksteps(n_ant, terms);
   const int n_rowtiles = (2 * n_pix + 127) / 128;
   const size_t tile_bytes = (size_t)ks * 4096;
   std::vector<uint8_t> img((size_t)n_rowtiles * tile_bytes, 0);
@@ -490,6 +505,7 @@ std::vector<uint8_t> build_beam_a_image(const double* W, int n_ant, int n_pix) {
       for (int slot = 0; slot < 2 * ks; slot++) {
         int part, j;  // part 0 head, 1 tail, 2 zero
         if (slot < G) { part = 0; j = slot; }
+        else if (terms == 1) { part = 2; j = 0; }
         else if (slot < 2 * G) { part = 0; j = slot - G; }
         else if (slot < 3 * G) { part = 1; j = slot - 2 * G; }
         else { part = 2; j = 0; }
@@ -515,38 +531,74 @@ std::vector<uint8_t> build_beam_a_image(const double* W, int n_ant, int n_pix) {
 }
 
 int beam_tc_groups(int n_ant) { return (n_ant + 3) / 4; }
-int beam_tc_ksteps(int n_ant) { return (3 * beam_tc_groups(n_ant) + 1) / 2; }
-int beam_tc_tile_samples(int dump_len) { return dump_len % 256 == 0 ? 256 : 128; }
-long long beam_tc_tile_bytes(int n_ant, int dump_len) {
-  return (long long)beam_tc_tile_samples(dump_len) * 2 * beam_tc_groups(n_ant) * 16;
+int beam_tc_bgroups(int n_ant, int terms) {
+  const int G = beam_tc_groups(n_ant);
+  return terms == 3 ? 2 * G : (G + 1) & ~1;
+}
+int beam_tc_ksteps(int n_ant, int terms) {
+  const int G = beam_tc_groups(n_ant);
+  return terms == 3 ? (3 * G + 1) / 2 : (G + 1) / 2;
+}
+// Row tiles per CTA and B ring depth for a tile shape: the deepest ring
+// (down to 2 stages) with at least one row tile, then as many row tiles as
+// fit in 220 KB of shared memory.  False when not even that fits.
+template <int NT>
+static bool beam_tc_shape(int ks, int GB, int n_rowtiles, int* R_out, int* nst_out) {
+  for (int nst = BeamCfg<NT>::NSTAGE; nst >= 2; nst--) {
+    if (beam_smem_plan<NT>(1, ks, GB, nst).total > 220 * 1024) continue;
+    int R = RMAX < n_rowtiles ? RMAX : n_rowtiles;
+    while (R > 1 && beam_smem_plan<NT>(R, ks, GB, nst).total > 220 * 1024) R--;
+    *R_out = R;
+    *nst_out = nst;
+    return true;
+  }
+  return false;
 }
 
-cudaError_t launch_split_bf16(const float2* y, long long n_samp, int n_ant, int dump_len,
-                              long long t_begin, long long t_end, uint8_t* b_img,
-                              cudaStream_t st) {
+// Tile width for a shape: 256 samples when the dump length allows and the
+// shape fits, else 128; 0 when neither fits.
+static int beam_tc_pick_nt(int n_ant, int n_pix, int dump_len, int terms) {
+  const int ks = beam_tc_ksteps(n_ant, terms), GB = beam_tc_bgroups(n_ant, terms);
+  const int n_rowtiles = (2 * n_pix + 127) / 128;
+  int R, nst;
+  if (dump_len % 256 == 0 && beam_tc_shape<256>(ks, GB, n_rowtiles, &R, &nst)) return 256;
+  if (beam_tc_shape<128>(ks, GB, n_rowtiles, &R, &nst)) return 128;
+  return 0;
+}
+
+int beam_tc_tile_samples(int n_ant, int n_pix, int dump_len, int terms) {
+  return beam_tc_pick_nt(n_ant, n_pix, dump_len, terms);
+}
+long long beam_tc_tile_bytes(int n_ant, int n_pix, int dump_len, int terms) {
+  return (long long)beam_tc_tile_samples(n_ant, n_pix, dump_len, terms) *
+         beam_tc_bgroups(n_ant, terms) * 16;
+}
+
+cudaError_t launch_split_bf16(const float2* y, long long n_samp, int n_ant, int n_pix,
+                              int dump_len, long long t_begin, long long t_end, uint8_t* b_img,
+                              int terms, cudaStream_t st) {
   if (t_end <= t_begin) return cudaSuccess;
-  const int G = beam_tc_groups(n_ant);
-  const int NT = beam_tc_tile_samples(dump_len);
+  const int G = beam_tc_groups(n_ant), GB = beam_tc_bgroups(n_ant, terms);
+  const int NT = beam_tc_tile_samples(n_ant, n_pix, dump_len, terms);
+  if (NT == 0) return cudaErrorInvalidConfiguration;
   const long long n_tiles = (t_end - t_begin + NT - 1) / NT;
   const long long total = n_tiles * NT * G;
   long long blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_split_bf16<<<(unsigned)blocks, 256, 0, st>>>(y, n_samp, n_ant, G, t_begin, t_end, n_tiles,
-                                                 NT, b_img);
+  k_split_bf16<<<(unsigned)blocks, 256, 0, st>>>(y, n_samp, n_ant, G, GB, terms, t_begin, t_end,
+                                                 n_tiles, NT, b_img);
   return cudaGetLastError();
 }
 
 template <int NT>
 static cudaError_t launch_beam_tc_nt(const uint8_t* b_img, const uint8_t* a_img, int n_ant,
                                      int n_pix, int dump_len, long long first, long long last,
-                                     float* pow, int* err, cudaStream_t st) {
-  const int G = beam_tc_groups(n_ant), ks = beam_tc_ksteps(n_ant);
+                                     float* pow, int* err, int terms, cudaStream_t st) {
+  const int ks = beam_tc_ksteps(n_ant, terms), G = beam_tc_bgroups(n_ant, terms);
   const int n_rowtiles = (2 * n_pix + 127) / 128;
-  int R = RMAX;
-  if (R > n_rowtiles) R = n_rowtiles;
-  while (R > 1 && beam_smem_plan<NT>(R, ks, G).total > 220 * 1024) R--;
-  const BeamSmemPlan sp = beam_smem_plan<NT>(R, ks, G);
-  if (sp.total > 227 * 1024) return cudaErrorInvalidConfiguration;
+  int R, nst;
+  if (!beam_tc_shape<NT>(ks, G, n_rowtiles, &R, &nst)) return cudaErrorInvalidConfiguration;
+  const BeamSmemPlan sp = beam_smem_plan<NT>(R, ks, G, nst);
   // at least 116 KB so that a second CTA never shares the SM (and its TMEM)
   const uint32_t smem_bytes = sp.total > 116 * 1024 ? sp.total : 116 * 1024;
   cudaError_t e = cudaFuncSetAttribute(k_beam_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -571,19 +623,26 @@ static cudaError_t launch_beam_tc_nt(const uint8_t* b_img, const uint8_t* a_img,
   a.n_pix = n_pix;
   a.n_rowtiles = n_rowtiles;
   a.R = R;
-  a.G = G;
+  a.GB = G;
+  a.bwrap = terms == 3 ? 2 * beam_tc_groups(n_ant) : G;
   a.ksteps = ks;
+  a.nstage = nst;
   k_beam_tc<NT><<<dim3(gx, (unsigned)gy), BeamCfg<NT>::THREADS, smem_bytes, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_beam_tc(const uint8_t* b_img, const uint8_t* a_img, int n_ant, int n_pix,
                            int dump_len, long long first, long long last, float* pow, int* err,
-                           cudaStream_t st) {
+                           int terms, cudaStream_t st) {
   if (last < first) return cudaSuccess;
-  if (dump_len % 256 == 0)
-    return launch_beam_tc_nt<256>(b_img, a_img, n_ant, n_pix, dump_len, first, last, pow, err, st);
-  return launch_beam_tc_nt<128>(b_img, a_img, n_ant, n_pix, dump_len, first, last, pow, err, st);
+  const int nt = beam_tc_pick_nt(n_ant, n_pix, dump_len, terms);
+  if (nt == 256)
+    return launch_beam_tc_nt<256>(b_img, a_img, n_ant, n_pix, dump_len, first, last, pow, err,
+                                  terms, st);
+  if (nt == 128)
+    return launch_beam_tc_nt<128>(b_img, a_img, n_ant, n_pix, dump_len, first, last, pow, err,
+                                  terms, st);
+  return cudaErrorInvalidConfiguration;
 }
 
 }  // namespace chirp

@@ -29,10 +29,13 @@ static __device__ __forceinline__ Twiddles mk_tw(TwiddlePtrs p) { return Twiddle
 
 // ------------------------------------------------------------------ forward
 // Column pass: L = n1, C = 4096 / n1 columns per CTA (interleaved tile).
-template <int L>
-__global__ void __launch_bounds__(256, 4) k_fwd_cols(const float2* __restrict__ x, long long n_samp,
+// CI8: the voltages are complex int8 (re, im) times a per-antenna scale,
+// converted to FP32 on load (the only read of the raw input).
+template <int L, bool CI8>
+__global__ void __launch_bounds__(256, 4) k_fwd_cols(const void* __restrict__ x, long long n_samp,
                                                   float2* __restrict__ spec, int n2, int log2n,
                                                   long long step, int n_ant,
+                                                  const float* __restrict__ scale,
                                                   TwiddlePtrs twp) {
   constexpr int C = 4096 / L;
   constexpr int T = L / 16;
@@ -44,13 +47,26 @@ __global__ void __launch_bounds__(256, 4) k_fwd_cols(const float2* __restrict__ 
   const long long q = blockIdx.y;  // block-major sequence: b * n_ant + a
   const long long a = q % n_ant, b = q / n_ant;
   const long long nfft = (long long)L * n2;
-  const float2* xa = x + a * n_samp;
   const long long base = b * step;
   float2 v[16];
+  if constexpr (CI8) {
+    const char2* xa = (const char2*)x + a * n_samp;
+    const float sc = scale ? scale[a] : 1.0f;
 #pragma unroll
-  for (int k = 0; k < 16; k++) {
-    long long n = base + (long long)(jt + k * T) * n2 + c;
-    v[k] = (act && n < n_samp) ? xa[n] : make_float2(0.f, 0.f);
+    for (int k = 0; k < 16; k++) {
+      long long n = base + (long long)(jt + k * T) * n2 + c;
+      const char2 z = (act && n < n_samp) ? xa[n] : make_char2(0, 0);
+      // rounded products, never fused into the first butterfly: the spectrum
+      // equals that of the FP32 voltages scale * code
+      v[k] = make_float2(__fmul_rn((float)z.x, sc), __fmul_rn((float)z.y, sc));
+    }
+  } else {
+    const float2* xa = (const float2*)x + a * n_samp;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      long long n = base + (long long)(jt + k * T) * n2 + c;
+      v[k] = (act && n < n_samp) ? xa[n] : make_float2(0.f, 0.f);
+    }
   }
   fft_core<L, C, false, false>(v, sm, s, jt, tw);
   if (!act) return;
@@ -192,16 +208,24 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ 
 // ------------------------------------------------------------------ launchers
 #define CHIRP_SIZES(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
 
-cudaError_t launch_forward(const float2* x, long long n_samp, int n_ant, const GroupGeom& g,
-                           float2* spec, TwiddlePtrs tw, cudaStream_t st) {
+cudaError_t launch_forward(const void* x, long long n_samp, int n_ant, const GroupGeom& g,
+                           float2* spec, TwiddlePtrs tw, cudaStream_t st, int in_type,
+                           const float* scale) {
   const long long n_seq = (long long)n_ant * g.n_blk;
   if (n_seq > 65535) return cudaErrorInvalidConfiguration;
   {
     const int C = 4096 / g.n1;
     dim3 grid((g.n2 + C - 1) / C, (unsigned)n_seq);
     switch (g.n1) {
-#define X(L) \
-  case L: k_fwd_cols<L><<<grid, 256, 0, st>>>(x, n_samp, spec, g.n2, g.log2n, g.step, n_ant, tw); break;
+#define X(L)                                                                                   \
+  case L:                                                                                      \
+    if (in_type == 1)                                                                          \
+      k_fwd_cols<L, true><<<grid, 256, 0, st>>>(x, n_samp, spec, g.n2, g.log2n, g.step, n_ant,  \
+                                                scale, tw);                                    \
+    else                                                                                       \
+      k_fwd_cols<L, false><<<grid, 256, 0, st>>>(x, n_samp, spec, g.n2, g.log2n, g.step, n_ant, \
+                                                 scale, tw);                                   \
+    break;
       CHIRP_SIZES(X)
 #undef X
       default: return cudaErrorInvalidValue;

@@ -79,6 +79,26 @@ __global__ void k_incoherent(const float* __restrict__ S, int n_chan, long long 
   }
 }
 
+__global__ void k_unpack_ci8(const char2* __restrict__ x, const float* __restrict__ scale,
+                             long long n_samp, long long total, float2* __restrict__ y) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float sc = scale ? scale[i / n_samp] : 1.0f;
+    const char2 z = x[i];
+    y[i] = make_float2(__fmul_rn((float)z.x, sc), __fmul_rn((float)z.y, sc));
+  }
+}
+
+cudaError_t launch_unpack_ci8(const void* x, const float* scale, int n_ant, long long n_samp,
+                              float2* y, cudaStream_t st) {
+  const long long total = (long long)n_ant * n_samp;
+  if (total <= 0) return cudaSuccess;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_unpack_ci8<<<(unsigned)blocks, 256, 0, st>>>((const char2*)x, scale, n_samp, total, y);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_incoherent(float2* scratch, long long seq_stride, int n_ant, int n_chan,
                               int n_int, long long T_fb, const int* shift, int n_dm, float* S,
                               float* D, TwiddlePtrs tw, cudaStream_t st) {

@@ -30,8 +30,11 @@ struct TwiddlePtrs {
 // ---- dedispersion kernels (dedisperse.cu) ----
 // spectra of every (antenna, block) of one group; spec [n_blk][n_ant][nfft]
 // holds X[k1 + n1 k2] at position k1 * n2 + k2.
-cudaError_t launch_forward(const float2* x, long long n_samp, int n_ant, const GroupGeom& g,
-                           float2* spec, TwiddlePtrs tw, cudaStream_t st);
+// x: complex64 [n_ant][n_samp] (in_type 0) or complex int8 pairs times
+// scale[a] (in_type 1, scale NULL = 1)
+cudaError_t launch_forward(const void* x, long long n_samp, int n_ant, const GroupGeom& g,
+                           float2* spec, TwiddlePtrs tw, cudaStream_t st, int in_type = 0,
+                           const float* scale = nullptr);
 // G[pos] = k_dm f^2/(f0^2 (f0 + f)) in the spectrum's (transposed) order, FP64
 cudaError_t launch_build_phase_table(double* G, const GroupGeom& g, double f0, double bw,
                                      double k_dm, cudaStream_t st);
@@ -77,21 +80,28 @@ cudaError_t launch_beamform_simt(const float2* y, long long n_samp, int n_ant, i
 // ---- incoherent filterbank path (incoherent.cu) ----
 // scratch holds a copy of the voltages ([n_ant] rows of seq_stride samples) and
 // is transformed in place; S [n_chan][T_fb], D [n_dm][T_fb]; shift [n_dm][n_chan]
+// y[a][t] = scale[a] * complex int8 x[a][t] as complex64 (scale NULL = 1)
+cudaError_t launch_unpack_ci8(const void* x, const float* scale, int n_ant, long long n_samp,
+                              float2* y, cudaStream_t st);
 cudaError_t launch_incoherent(float2* scratch, long long seq_stride, int n_ant, int n_chan,
                               int n_int, long long T_fb, const int* shift, int n_dm, float* S,
                               float* D, TwiddlePtrs tw, cudaStream_t st);
 
 // ---- tensor-core beamformer (beamform_tc.cu) ----
-int beam_tc_groups(int n_ant);           // 8-wide real-K groups per head/tail part
-int beam_tc_ksteps(int n_ant);           // 16-wide MMA K steps
-int beam_tc_tile_samples(int dump_len);  // 256 when dump_len % 256 == 0, else 128
-long long beam_tc_tile_bytes(int n_ant, int dump_len);  // bytes of one B tile
-std::vector<uint8_t> build_beam_a_image(const double* W, int n_ant, int n_pix);
-cudaError_t launch_split_bf16(const float2* y, long long n_samp, int n_ant, int dump_len,
-                              long long t_begin, long long t_end, uint8_t* b_img,
-                              cudaStream_t st);
+// terms = 3: split-BF16 (A_h B_h + A_h B_l + A_l B_h); terms = 1: plain BF16
+int beam_tc_groups(int n_ant);                // 8-wide real-K groups per head/tail part
+int beam_tc_bgroups(int n_ant, int terms);    // 8-wide k-groups of one B tile
+int beam_tc_ksteps(int n_ant, int terms);     // 16-wide MMA K steps
+// samples per B tile: 256 when dump_len % 256 == 0 and the shape fits in
+// shared memory, else 128; 0 when the shape does not fit at all
+int beam_tc_tile_samples(int n_ant, int n_pix, int dump_len, int terms);
+long long beam_tc_tile_bytes(int n_ant, int n_pix, int dump_len, int terms);  // one B tile
+std::vector<uint8_t> build_beam_a_image(const double* W, int n_ant, int n_pix, int terms);
+cudaError_t launch_split_bf16(const float2* y, long long n_samp, int n_ant, int n_pix,
+                              int dump_len, long long t_begin, long long t_end, uint8_t* b_img,
+                              int terms, cudaStream_t st);
 cudaError_t launch_beam_tc(const uint8_t* b_img, const uint8_t* a_img, int n_ant, int n_pix,
                            int dump_len, long long first, long long last, float* pow, int* err,
-                           cudaStream_t st);
+                           int terms, cudaStream_t st);
 
 }  // namespace chirp

@@ -91,6 +91,9 @@ struct chirp_plan {
   std::vector<double> pix;
   int n_pix = 0;
   int beam_mode = 0;
+  int beam_terms = 3;         // tensor-core modes: 3 (split BF16) or 1 (BF16)
+  int in_type = CHIRP_IN_C64;
+  float* d_scale = nullptr;   // [M] CHIRP_IN_CI8 scales
   cudaStream_t stream = nullptr;
   std::vector<Group> groups;
   std::vector<DmInfo> dmi;
@@ -142,6 +145,10 @@ struct chirp_plan {
 
 namespace {
 
+bool tc_beams(const chirp_plan* p) {
+  return p->beam_mode == CHIRP_BEAM_TC_3XBF16 || p->beam_mode == CHIRP_BEAM_TC_BF16;
+}
+
 int dev_alloc(chirp_plan* p, void** ptr, size_t bytes, const char* what) {
   if (bytes == 0) bytes = 16;
   cudaError_t e = cudaMalloc(ptr, bytes);
@@ -177,6 +184,7 @@ void release(chirp_plan* p) {
   cudaFree(p->d_fb_S);
   cudaFree(p->d_fb_D);
   cudaFree(p->d_lists);
+  cudaFree(p->d_scale);
   for (auto& g : p->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   cudaFree(p->d_out);
@@ -325,8 +333,13 @@ int validate(const chirp_config* c) {
       double l = c->pix_lm[2 * p], m = c->pix_lm[2 * p + 1];
       if (!(l * l + m * m <= 1.0)) return fail(CHIRP_EINVAL, "pixel %d has l^2 + m^2 > 1", p);
     }
-  if (c->beam_mode < 0 || c->beam_mode > CHIRP_BEAM_VIS)
+  if (c->beam_mode < 0 || c->beam_mode > CHIRP_BEAM_TC_BF16)
     return fail(CHIRP_EINVAL, "unknown beam_mode");
+  if (c->in_type != CHIRP_IN_C64 && c->in_type != CHIRP_IN_CI8)
+    return fail(CHIRP_EINVAL, "unknown in_type");
+  if (c->in_type == CHIRP_IN_CI8 && c->in_scale)
+    for (int a = 0; a < c->n_ant; a++)
+      if (!std::isfinite(c->in_scale[a])) return fail(CHIRP_EINVAL, "in_scale must be finite");
   if (c->fb_chan != 0) {
     if (!is_pow2(c->fb_chan) || c->fb_chan < 16 || c->fb_chan > 4096)
       return fail(CHIRP_EINVAL, "fb_chan must be 0 or a power of two in 16..4096");
@@ -380,7 +393,20 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   if (cfg->n_pix > 0) p->pix.assign(cfg->pix_lm, cfg->pix_lm + 2 * cfg->n_pix);
   p->n_pix = cfg->n_pix;
   // AUTO: tensor cores (split BF16, FP32 accumulate) for the beam GEMM
-  p->beam_mode = cfg->beam_mode == CHIRP_BEAM_AUTO ? CHIRP_BEAM_TC_3XBF16 : cfg->beam_mode;
+  p->beam_mode = cfg->beam_mode;
+  if (p->beam_mode == CHIRP_BEAM_AUTO)  // split-BF16 tensor cores where the shape fits
+    p->beam_mode = cfg->n_pix > 0 && beam_tc_tile_samples(cfg->n_ant, cfg->n_pix, cfg->dump_len, 3) == 0
+                       ? CHIRP_BEAM_VIS
+                       : CHIRP_BEAM_TC_3XBF16;
+  p->beam_terms = p->beam_mode == CHIRP_BEAM_TC_BF16 ? 1 : 3;
+  if (cfg->n_pix > 0 && tc_beams(p) &&
+      beam_tc_tile_samples(p->M, cfg->n_pix, cfg->dump_len, p->beam_terms) == 0) {
+    delete p;
+    return fail(CHIRP_EUNSUPPORTED,
+                "tensor-core beam tiles for %d antennas do not fit in shared memory; use "
+                "CHIRP_BEAM_VIS or CHIRP_BEAM_FP32_SIMT", cfg->n_ant);
+  }
+  p->in_type = cfg->in_type;
   p->stream = (cudaStream_t)stream;
   p->use_graphs = (cfg->flags & CHIRP_FLAG_GRAPHS) != 0;
   if (p->use_graphs && p->stream == nullptr) {
@@ -483,6 +509,12 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   if (!rc && p->n_pix > 0)
     rc = dev_alloc(p, (void**)&p->d_W, (size_t)p->n_pix * p->M * sizeof(float2), "weights");
   if (!rc) rc = dev_alloc(p, (void**)&p->d_err, sizeof(int), "status word");
+  std::vector<float> scale;
+  if (!rc && p->in_type == CHIRP_IN_CI8) {
+    scale.assign((size_t)p->M, 1.0f);
+    if (cfg->in_scale) std::copy(cfg->in_scale, cfg->in_scale + p->M, scale.begin());
+    rc = dev_alloc(p, (void**)&p->d_scale, scale.size() * sizeof(float), "input scales");
+  }
   std::vector<int> fb_shift;
   if (!rc && cfg->fb_chan > 0) {
     p->fb_chan = cfg->fb_chan;
@@ -534,16 +566,18 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
       }
     }
   }
-  if (!rc && p->n_pix > 0 && p->beam_mode == CHIRP_BEAM_TC_3XBF16) {
+  if (!rc && p->n_pix > 0 && tc_beams(p)) {
     long long max_tiles = 0;
     for (const DmInfo& I : p->dmi)
       if (I.last >= I.first) {
         long long span = (I.last - I.first + 1) * p->L;
-        long long nt = (span + beam_tc_tile_samples(p->L) - 1) / beam_tc_tile_samples(p->L);
+        const int ts = beam_tc_tile_samples(p->M, p->n_pix, p->L, p->beam_terms);
+        long long nt = (span + ts - 1) / ts;
         max_tiles = std::max(max_tiles, nt);
       }
     rc = dev_alloc(p, (void**)&p->d_bimg, (size_t)std::max(1LL, max_tiles) *
-                                              (size_t)beam_tc_tile_bytes(p->M, p->L), "beam B image");
+                                              (size_t)beam_tc_tile_bytes(p->M, p->n_pix, p->L, p->beam_terms),
+                   "beam B image");
     if (!rc) {
       std::vector<double> Wd((size_t)p->n_pix * p->M * 2);
       for (int q = 0; q < p->n_pix; q++) {
@@ -557,7 +591,7 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
           Wd[2 * ((size_t)q * p->M + a) + 1] = std::sin(ph);
         }
       }
-      aimg = build_beam_a_image(Wd.data(), p->M, p->n_pix);
+      aimg = build_beam_a_image(Wd.data(), p->M, p->n_pix, p->beam_terms);
       rc = dev_alloc(p, (void**)&p->d_aimg, aimg.size(), "beam A image");
     }
   }
@@ -598,6 +632,9 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   if (e == cudaSuccess && !aimg.empty())
     e = cudaMemcpyAsync(p->d_aimg, aimg.data(), aimg.size(), cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
+  if (e == cudaSuccess && !scale.empty())
+    e = cudaMemcpyAsync(p->d_scale, scale.data(), scale.size() * sizeof(float),
+                        cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess && !fb_shift.empty())
     e = cudaMemcpyAsync(p->d_fb_shift, fb_shift.data(), fb_shift.size() * sizeof(int),
                         cudaMemcpyHostToDevice, p->stream);
@@ -663,19 +700,23 @@ int chirp_dump_range(const chirp_plan* p, long long* first, long long* last) {
 namespace {
 
 // voltages on the device, copying host input into the plan's staging buffer
-int stage_input(chirp_plan* p, const void* volt, int loc, const float2** dx) {
+size_t in_elem_bytes(const chirp_plan* p) {
+  return p->in_type == CHIRP_IN_CI8 ? 2 : sizeof(float2);
+}
+
+int stage_input(chirp_plan* p, const void* volt, int loc, const void** dx) {
   if (!volt) return fail(CHIRP_EINVAL, "voltage pointer is NULL");
   if (loc == CHIRP_DEVICE) {
-    *dx = (const float2*)volt;
+    *dx = volt;
     return CHIRP_OK;
   }
   if (loc != CHIRP_HOST) return fail(CHIRP_EINVAL, "bad buffer location");
+  const size_t bytes = (size_t)p->M * p->N * in_elem_bytes(p);
   if (!p->d_x) {
-    int rc = dev_alloc(p, (void**)&p->d_x, (size_t)p->M * p->N * sizeof(float2), "input staging");
+    int rc = dev_alloc(p, (void**)&p->d_x, bytes, "input staging");
     if (rc) return rc;
   }
-  CK(cudaMemcpyAsync(p->d_x, volt, (size_t)p->M * p->N * sizeof(float2), cudaMemcpyHostToDevice,
-                     p->stream));
+  CK(cudaMemcpyAsync(p->d_x, volt, bytes, cudaMemcpyHostToDevice, p->stream));
   *dx = p->d_x;
   return CHIRP_OK;
 }
@@ -707,10 +748,11 @@ int finish_out(chirp_plan* p, void* user, int loc, const void* dev, size_t bytes
   return CHIRP_OK;
 }
 
-int forward_all(chirp_plan* p, const float2* dx) {
+int forward_all(chirp_plan* p, const void* dx) {
   for (auto& g : p->groups) {
     int mk = mark_begin(p);
-    CK(launch_forward(dx, p->N, p->M, g.geom, g.d_spec, p->tw(), p->stream));
+    CK(launch_forward(dx, p->N, p->M, g.geom, g.d_spec, p->tw(), p->stream, p->in_type,
+                      p->d_scale));
     mark_end(p, CHIRP_STAGE_FORWARD, mk);
   }
   return CHIRP_OK;
@@ -780,13 +822,14 @@ int backend_dumps(chirp_plan* p, int d, Backend be, long long m0, long long m1, 
     mk = mark_begin(p);
     CK(launch_beam_from_vis(p->d_V, p->d_wpair, p->M, p->n_pix, m0, last, out, p->stream));
     mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
-  } else if (p->beam_mode == CHIRP_BEAM_TC_3XBF16) {
+  } else if (tc_beams(p)) {
     int mk = mark_begin(p);
-    CK(launch_split_bf16(p->d_y, p->N, p->M, p->L, m0 * p->L, m1 * p->L, p->d_bimg, p->stream));
+    CK(launch_split_bf16(p->d_y, p->N, p->M, p->n_pix, p->L, m0 * p->L, m1 * p->L, p->d_bimg,
+                         p->beam_terms, p->stream));
     mark_end(p, CHIRP_STAGE_SPLIT, mk);
     mk = mark_begin(p);
     CK(launch_beam_tc(p->d_bimg, p->d_aimg, p->M, p->n_pix, p->L, m0, last, out, p->d_err,
-                      p->stream));
+                      p->beam_terms, p->stream));
     mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
   } else {
     int mk = mark_begin(p);
@@ -801,7 +844,7 @@ int backend_dumps(chirp_plan* p, int d, Backend be, long long m0, long long m1, 
 // byte is nonzero: for each DM the blocks owning a selected dump are inverse
 // transformed (runs of consecutive blocks per launch) and the back-end runs on
 // runs of consecutive selected dumps.  Outputs are zero elsewhere.
-int enqueue_search(chirp_plan* p, const float2* dx, const unsigned char* mask, Backend be,
+int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Backend be,
                    void* dout, size_t bytes) {
   int rc = forward_all(p, dx);
   if (rc) return rc;
@@ -906,7 +949,7 @@ int enqueue_search(chirp_plan* p, const float2* dx, const unsigned char* mask, B
 // given (input, output, back-end) runs eagerly (lazy allocations and kernel
 // attributes happen there), the second captures and instantiates the launch
 // sequence, later calls launch the graph.
-int graph_search(chirp_plan* p, const float2* dx, Backend be, void* dout, size_t bytes) {
+int graph_search(chirp_plan* p, const void* dx, Backend be, void* dout, size_t bytes) {
   for (auto& g : p->graphs) {
     if (g.in != dx || g.out != dout || g.be != (int)be) continue;
     if (g.exec) {
@@ -947,7 +990,7 @@ int run_search(chirp_plan* p, const void* volt, int volt_loc, const unsigned cha
   g_err[0] = 0;
   if (!p) return fail(CHIRP_EINVAL, "plan is NULL");
   if (be == kBeams && p->n_pix <= 0) return fail(CHIRP_EUNSUPPORTED, "plan was created without pixels");
-  const float2* dx;
+  const void* dx;
   int rc = stage_input(p, volt, volt_loc, &dx);
   if (rc) return rc;
   const size_t per_dm = be == kCorrelate ? (size_t)p->n_dump * p->n_pair : (size_t)p->n_dump * p->n_pix;
@@ -975,7 +1018,7 @@ int chirp_dedisperse_run(chirp_plan* p, const void* volt, int volt_loc, int d, v
   g_err[0] = 0;
   if (!p) return fail(CHIRP_EINVAL, "plan is NULL");
   if (d < 0 || d >= (int)p->dm.size()) return fail(CHIRP_EINVAL, "DM index out of range");
-  const float2* dx;
+  const void* dx;
   int rc = stage_input(p, volt, volt_loc, &dx);
   if (rc) return rc;
   size_t bytes = (size_t)p->M * p->N * sizeof(float2);
@@ -984,7 +1027,8 @@ int chirp_dedisperse_run(chirp_plan* p, const void* volt, int volt_loc, int d, v
   if (rc) return rc;
   const DmInfo& I = p->dmi[d];
   Group& g = p->groups[I.group];
-  CK(launch_forward(dx, p->N, p->M, g.geom, g.d_spec, p->tw(), p->stream));
+  CK(launch_forward(dx, p->N, p->M, g.geom, g.d_spec, p->tw(), p->stream, p->in_type,
+                    p->d_scale));
   CK(cudaMemsetAsync(dy, 0, bytes, p->stream));
   rc = dedisperse_one(p, d, (float2*)dy);
   if (rc) return rc;
@@ -1019,7 +1063,7 @@ int chirp_incoherent_run(chirp_plan* p, const void* volt, int volt_loc, float* S
   if (!D_out) return fail(CHIRP_EINVAL, "D_out is NULL");
   if (out_loc != CHIRP_HOST && out_loc != CHIRP_DEVICE)
     return fail(CHIRP_EINVAL, "bad buffer location");
-  const float2* dx;
+  const void* dx;
   int rc = stage_input(p, volt, volt_loc, &dx);
   if (rc) return rc;
   const size_t vbytes = (size_t)p->M * p->N * sizeof(float2);
@@ -1036,7 +1080,10 @@ int chirp_incoherent_run(chirp_plan* p, const void* volt, int volt_loc, float* S
   float* dS = (out_loc == CHIRP_DEVICE && S_out) ? S_out : p->d_fb_S;
   int mk = mark_begin(p);
   // the filterbank transforms a copy of the voltages in the dedispersion scratch
-  CK(cudaMemcpyAsync(p->d_y, dx, vbytes, cudaMemcpyDeviceToDevice, p->stream));
+  if (p->in_type == CHIRP_IN_CI8)
+    CK(launch_unpack_ci8(dx, p->d_scale, p->M, p->N, p->d_y, p->stream));
+  else
+    CK(cudaMemcpyAsync(p->d_y, dx, vbytes, cudaMemcpyDeviceToDevice, p->stream));
   CK(launch_incoherent(p->d_y, p->N, p->M, p->fb_chan, p->fb_int, p->T_fb, p->d_fb_shift,
                        p->fb_n_dm, dS, dD, p->tw(), p->stream));
   mark_end(p, CHIRP_STAGE_INCOHERENT, mk);

@@ -250,3 +250,68 @@ def chimageator_medium(n_samp: int = 1 << 22, n_dm: int = 64, seed: int = 1002,
     return Scenario("chimageator 12 ant, 32 MHz, 2^%d samples, %d DMs, %d beams"
                     % (int(math.log2(n_samp)), n_dm, pix.shape[0]),
                     xyz, f0, bw, n_samp, dms, dump_len, nfft_min, pix, pulses, seed)
+
+
+# --------------------------------------------------------------------------
+# int8 voltages (the precision form's ingest format)
+# --------------------------------------------------------------------------
+def quantize_ci8(x: np.ndarray, counts_rms: float = 16.0):
+    """Complex int8 voltages as a digitiser would record them.
+
+    Per antenna the gain puts the per-component RMS at ``counts_rms`` counts;
+    each component is rounded half to even and clamped to +-127.  Returns
+    (q int8 [M, N, 2] interleaved (re, im), scale float32 [M]) with
+    x ~= scale[a] * (q[a, :, 0] + j q[a, :, 1]).
+    """
+    M = x.shape[0]
+    q = np.empty((M, x.shape[1], 2), np.int8)
+    scale = np.empty(M, np.float32)
+    for a in range(M):
+        rms = math.sqrt(float(np.mean(np.abs(x[a].astype(np.complex128)) ** 2)) / 2.0)
+        g = counts_rms / rms if rms > 0 else 1.0
+        scale[a] = np.float32(1.0 / g)
+        q[a, :, 0] = np.clip(np.rint(x[a].real * g), -127, 127)
+        q[a, :, 1] = np.clip(np.rint(x[a].imag * g), -127, 127)
+    return q, scale
+
+
+def dequantize_ci8(q: np.ndarray, scale: np.ndarray) -> np.ndarray:
+    """complex64 [M, N]: scale[a] * (re + j im), each product rounded to FP32
+    (what the int8 ingest computes before the first FFT pass)."""
+    s = scale.astype(np.float32)[:, None]
+    re = q[..., 0].astype(np.float32) * s
+    im = q[..., 1].astype(np.float32) * s
+    return (re + 1j * im).astype(np.complex64)
+
+
+def precision_form(channel: int = 0, n_chan: int = 8, n_samp: int = 1 << 24, n_dm: int = 256,
+                   dm_min: float = 1.0, dm_max: float = 2000.0, seed: int = 1003,
+                   n_ant: int = 36, n_side: int = 64, field_deg: float = 1.0,
+                   dump_len: int = 4096, nfft_min: int = 1 << 16, chan_bw: float = 42e6,
+                   f_centre: float = 1.4e9, n_pulse: int = 1) -> Scenario:
+    """One coarse channel of the sparse 36-antenna array (6 km maximum
+    baseline): 8 x 42 MHz channels around 1.4 GHz, channel c centred at
+    f_centre + (c - (n_chan - 1) / 2) chan_bw; trial DMs log-spaced from
+    dm_min to dm_max; 64 x 64 beams.  Voltages are meant to be quantised with
+    quantize_ci8 before the search."""
+    f0 = f_centre + (channel - 0.5 * (n_chan - 1)) * chan_bw
+    rng = np.random.Generator(np.random.PCG64(seed + 7 + 1000 * channel))
+    xyz = antenna_positions(n_ant, 6000.0, seed)
+    dms = np.geomspace(dm_min, dm_max, n_dm)
+    pix = pixel_grid(n_side, field_deg)
+    pulses = []
+    fw = 50e-6
+    for i in range(n_pulse):
+        dm_p = float(np.exp(rng.uniform(math.log(dm_min), math.log(dm_max))))
+        guard = 8 * fw * chan_bw + 64
+        t0 = _place_pulse(rng, dm_p, f0, chan_bw, n_samp, dump_len, K_DM, guard)
+        if t0 is None:
+            continue
+        pidx = int(rng.integers(0, pix.shape[0]))
+        amp = burst_amplitude(20.0, n_ant, dump_len, fw * chan_bw, dump_len / 2)
+        pulses.append(Pulse(dm_p, t0, fw, amp, float(pix[pidx, 0]), float(pix[pidx, 1]),
+                            seed + 100 + i + 1000 * channel))
+    return Scenario("precision form: 36 ant, channel %d of %d x %.0f MHz, 2^%d samples, %d DMs"
+                    % (channel, n_chan, chan_bw / 1e6, int(math.log2(n_samp)), n_dm),
+                    xyz, f0, chan_bw, n_samp, dms, dump_len, nfft_min, pix, pulses,
+                    seed + 1000 * channel)

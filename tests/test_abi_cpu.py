@@ -49,9 +49,28 @@ def _cfg(**over):
     (dict(bw=-1.0), "bw"),
     (dict(n_samp=0), "n_samp"),
     (dict(pix_lm=np.array([[0.9, 0.9]])), "l^2"),
+    (dict(in_type=3), "in_type"),
+    (dict(beam_mode=9), "beam_mode"),
+    (dict(fft_row=300), "fft_row"),
+    (dict(flags=8), "flag"),
+    (dict(in_type=1, in_scale=np.array([np.inf, 1.0])), "in_scale"),
 ])
 def test_plan_validation_rejects_bad_shapes(over, msg):
     with pytest.raises(chirp.ChirpError) as ei:
         chirp.Plan(**_cfg(**over))
     assert ei.value.code == -1
     assert msg in str(ei.value)
+
+
+def test_graphs_flag_needs_a_stream():
+    with pytest.raises(chirp.ChirpError) as ei:
+        chirp.Plan(**_cfg(flags=chirp.FLAG_GRAPHS), stream=0)
+    assert ei.value.code == -1 and "stream" in str(ei.value)
+
+
+def test_split_bf16_beams_reject_shapes_beyond_shared_memory():
+    xyz = np.zeros((64, 3))
+    xyz[:, 0] = np.arange(64.0)
+    with pytest.raises(chirp.ChirpError) as ei:
+        chirp.Plan(**_cfg(xyz=xyz, pix_lm=np.zeros((4, 2)), beam_mode=chirp.BEAM_TC_3XBF16))
+    assert ei.value.code == -5 and "shared memory" in str(ei.value)
