@@ -78,6 +78,11 @@ def _load():
             lib.orc_filterbank.argtypes = [_dp, _i, _ll, _i, _i, _dp]
             lib.orc_channel_shift.argtypes = [_d, _d, _d, _d, _i, _i, _i]
             lib.orc_channel_shift.restype = _ll
+            _fp = ctypes.POINTER(ctypes.c_float)
+            lib.orc_series_stats.argtypes = [_fp, _i, _ll, _i, _llp, _llp, _fp]
+            lib.orc_detect.argtypes = [_fp, _i, _ll, _i, _llp, _llp, ctypes.c_float, _fp, _ip,
+                                       _llp, _ip, _fp, _ll]
+            lib.orc_detect.restype = _ll
             lib.orc_incoherent.argtypes = [_dp, _i, _ll, _d, _d, _d, _i, _dp, _i, _dp]
             _lib = lib
     return _lib
@@ -246,3 +251,47 @@ def incoherent(S, f0, bw, k_dm, n_int, dms) -> np.ndarray:
     D = np.empty((dd.size, T), dtype=np.float64)
     _load().orc_incoherent(_ptr(SS), n_chan, T, f0, bw, k_dm, n_int, _ptr(dd), dd.size, _ptr(D))
     return D
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def series_stats(P, first, last) -> np.ndarray:
+    """(median, 1.4826 MAD) [n_dm, n_pix, 2] of every (DM, pixel) series of
+    dump powers P [n_dm, n_dump, n_pix] over the valid dumps, in FP32."""
+    PP = _f32(P)
+    n_dm, n_dump, n_pix = PP.shape
+    f = np.ascontiguousarray(first, dtype=np.int64)
+    l = np.ascontiguousarray(last, dtype=np.int64)
+    st = np.empty((n_dm, n_pix, 2), np.float32)
+    _load().orc_series_stats(_fptr(PP), n_dm, n_dump, n_pix, f.ctypes.data_as(_llp),
+                             l.ctypes.data_as(_llp), _fptr(st))
+    return st
+
+
+def detect(P, first, last, snr_min):
+    """Candidates (local S/N maxima >= snr_min) of P [n_dm, n_dump, n_pix]:
+    (d int32 [n], m int64 [n], p int32 [n], snr float32 [n]) in (d, m, p) order."""
+    PP = _f32(P)
+    n_dm, n_dump, n_pix = PP.shape
+    f = np.ascontiguousarray(first, dtype=np.int64)
+    l = np.ascontiguousarray(last, dtype=np.int64)
+    st = series_stats(PP, f, l)
+    cap = 1 << 16
+    while True:
+        cd = np.empty(cap, np.int32)
+        cm = np.empty(cap, np.int64)
+        cp = np.empty(cap, np.int32)
+        cs = np.empty(cap, np.float32)
+        n = _load().orc_detect(_fptr(PP), n_dm, n_dump, n_pix, f.ctypes.data_as(_llp),
+                               l.ctypes.data_as(_llp), float(snr_min), _fptr(st),
+                               cd.ctypes.data_as(_ip), cm.ctypes.data_as(_llp),
+                               cp.ctypes.data_as(_ip), _fptr(cs), cap)
+        if n <= cap:
+            return cd[:n], cm[:n], cp[:n], cs[:n]
+        cap = int(n)

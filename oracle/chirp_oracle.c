@@ -31,6 +31,11 @@
  *     antennas b(t) = sum_a W_pa y_a(t), W_pa = exp(+2 pi j f0 tau_a(l_p,m_p))
  *     with tau from Eq. tau3D (App. A.1) and c = 299792458 m/s, detected as
  *     |b|^2 and summed over the dump (direct beamforming, Sec. 2.4.2).
+ *  5. Candidates: per (DM, pixel) series of dump powers, median and
+ *     1.4826 x MAD give an S/N per cell; cells at or above a threshold that
+ *     are local maxima over (DM, dump, pixel) +- 1 are the detections
+ *     (thresholding of the detection metric, Sec. 3.3; best of a bank of
+ *     trial filters, App. A.3).
  *
  * Readings where the paper is silent (each listed in the design notes):
  *  - FFT length per DM: Nfft(DM) = max(nfft_min, min(pow2ceil(2 n_d),
@@ -499,4 +504,102 @@ void orc_incoherent(const double* S, int n_chan, long long T_fb, double f0, doub
     }
     free(s);
   }
+}
+
+/* ---------------------------------------------------------------------------
+ * Candidate detection on the beam powers (thresholding of the detection
+ * metric, Sec. 3.3 after Eq. eth; the unknown DM, arrival time and direction
+ * are searched by taking the best of a bank of trial filters, App. A.3).
+ *
+ * Per (DM d, pixel p) the series x_m = P[d][m][p] over the DM's valid dumps
+ * m = first[d] .. last[d] (n values) gives
+ *    med   = median(x)                (even n: mean of the two middle values)
+ *    sigma = 1.4826 * median(|x - med|)
+ * and every valid cell gets S/N = (x - med) / sigma (0 when sigma == 0).  A
+ * candidate is a valid cell with S/N >= snr_min that no valid cell among its
+ * 26 neighbours (d +- 1, m +- 1, p +- 1 in the pixel list) exceeds.
+ * The statistics are computed in FP32, the precision of the powers, one
+ * IEEE-rounded operation at a time:  med = (a + b) * 0.5,  |x - med|,
+ * sigma = 1.4826f * mad,  S/N = (x - med) / sigma.
+ * -------------------------------------------------------------------------*/
+static int orc_cmp_float(const void* a, const void* b) {
+  float x = *(const float*)a, y = *(const float*)b;
+  return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* median of v[0..n) (v is sorted in place) */
+static float orc_median_f(float* v, long long n) {
+  qsort(v, (size_t)n, sizeof(float), orc_cmp_float);
+  if (n % 2) return v[n / 2];
+  volatile float s = v[n / 2 - 1] + v[n / 2];
+  return s * 0.5f;
+}
+
+/* stats [n_dm][n_pix][2] = (med, sigma) */
+void orc_series_stats(const float* P, int n_dm, long long n_dump, int n_pix,
+                      const long long* first, const long long* last, float* stats) {
+  for (int d = 0; d < n_dm; d++) {
+    long long n = last[d] - first[d] + 1;
+    for (int p = 0; p < n_pix; p++) {
+      float med = 0.f, sigma = 0.f;
+      if (n > 0) {
+        float* v = (float*)malloc((size_t)n * sizeof(float));
+        for (long long m = 0; m < n; m++) v[m] = P[((size_t)d * n_dump + first[d] + m) * n_pix + p];
+        med = orc_median_f(v, n);
+        for (long long m = 0; m < n; m++) {
+          volatile float dv = v[m] - med;
+          v[m] = fabsf(dv);
+        }
+        volatile float mad = orc_median_f(v, n);
+        sigma = 1.4826f * mad;
+        free(v);
+      }
+      stats[2 * ((size_t)d * n_pix + p)] = med;
+      stats[2 * ((size_t)d * n_pix + p) + 1] = sigma;
+    }
+  }
+}
+
+static float orc_snr_at(const float* P, long long n_dump, int n_pix, const float* stats, int d,
+                        long long m, int p) {
+  const float med = stats[2 * ((size_t)d * n_pix + p)];
+  const float sigma = stats[2 * ((size_t)d * n_pix + p) + 1];
+  if (!(sigma > 0.f)) return 0.f;
+  volatile float num = P[((size_t)d * n_dump + m) * n_pix + p] - med;
+  return num / sigma;
+}
+
+/* Candidates in (d, m, p) order; returns their number (only the first
+ * max_out are stored). */
+long long orc_detect(const float* P, int n_dm, long long n_dump, int n_pix,
+                     const long long* first, const long long* last, float snr_min,
+                     const float* stats, int* cd, long long* cm, int* cp, float* csnr,
+                     long long max_out) {
+  long long n = 0;
+  for (int d = 0; d < n_dm; d++)
+    for (long long m = first[d]; m <= last[d]; m++)
+      for (int p = 0; p < n_pix; p++) {
+        const float s = orc_snr_at(P, n_dump, n_pix, stats, d, m, p);
+        if (!(s >= snr_min)) continue;
+        int peak = 1;
+        for (int dd = -1; dd <= 1 && peak; dd++)
+          for (long long dm = -1; dm <= 1 && peak; dm++)
+            for (int dp = -1; dp <= 1 && peak; dp++) {
+              if (!dd && !dm && !dp) continue;
+              const int d2 = d + dd, p2 = p + dp;
+              const long long m2 = m + dm;
+              if (d2 < 0 || d2 >= n_dm || p2 < 0 || p2 >= n_pix) continue;
+              if (m2 < first[d2] || m2 > last[d2]) continue;
+              if (orc_snr_at(P, n_dump, n_pix, stats, d2, m2, p2) > s) peak = 0;
+            }
+        if (!peak) continue;
+        if (n < max_out) {
+          cd[n] = d;
+          cm[n] = m;
+          cp[n] = p;
+          csnr[n] = s;
+        }
+        n++;
+      }
+  return n;
 }
