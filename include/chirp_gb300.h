@@ -259,7 +259,8 @@ int chirp_propose_windows(const float* logits, int n_dm, long long n_time, int w
 #define CHIRP_STAGE_SPLIT 5     /* BF16 head/tail split of the voltages, per DM */
 #define CHIRP_STAGE_CHIRP 6     /* FP64-phase chirp table H_DM, per DM           */
 #define CHIRP_STAGE_INCOHERENT 7 /* filterbank + incoherent dedispersion        */
-#define CHIRP_N_STAGES 8
+#define CHIRP_STAGE_DETECT 8    /* candidate detection (chirp_detect)            */
+#define CHIRP_N_STAGES 9
 /* Returns the milliseconds and launch counts accumulated per stage since the
  * previous call (ms, launches: host arrays of CHIRP_N_STAGES, either may be
  * NULL), resets them, and switches event timing on (enable != 0) or off for
@@ -321,6 +322,34 @@ int chimageator_run_selective(chirp_plan* plan, const void* volt, int volt_loc,
  * batch). */
 int chirp_batch_run(chirp_plan* const* plans, const void* const* volts, const int* volt_locs,
                     void* const* outs, const int* out_locs, const int* backends, int n);
+
+/* One detection: trial DM index, dump, pixel, its S/N and dump power. */
+typedef struct {
+  long long dump;
+  int dm;
+  int pix;
+  float snr;
+  float power;
+} chirp_candidate;
+
+/* Candidate detection on Chimageator dump powers (thresholding of the
+ * detection metric, Sec. 3.3 after Eq. eth; the best of a bank of trial
+ * filters over DM, time and direction, App. A.3).  Per (DM, pixel) series
+ * over the DM's valid dumps: med = median (even count: mean of the two
+ * middle values), sigma = 1.4826 * median(|x - med|), S/N = (x - med) / sigma
+ * (0 where sigma == 0), each an IEEE-rounded FP32 operation.  A candidate is
+ * a valid cell with S/N >= snr_min that no valid cell among its 26 neighbours
+ * (DM +- 1, dump +- 1, pixel index +- 1) exceeds.
+ *  pow:   float32 [n_dm][n_dump][n_pix] at pow_loc (chimageator_run's layout);
+ *  cand:  [max_cand] at cand_loc, filled in (DM, dump, pixel) order with the
+ *         first min(*n_cand, max_cand) candidates;
+ *  n_cand: HOST, receives the total number of candidates;
+ *  stats_out: NULL or float32 [n_dm][n_pix][2] (med, sigma) at cand_loc.
+ * Synchronises the plan's stream.  Errors: CHIRP_EINVAL, CHIRP_EUNSUPPORTED
+ * (plan without pixels), CHIRP_ENOMEM, CHIRP_ECUDA. */
+int chirp_detect(chirp_plan* plan, const float* pow, int pow_loc, float snr_min,
+                 chirp_candidate* cand, long long max_cand, int cand_loc, long long* n_cand,
+                 float* stats_out);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* chirp_last_error(void);

@@ -44,10 +44,10 @@ EXPORTED_SYMBOLS = ("chirp_plan_create", "chirp_plan_destroy", "chirp_plan_query
                     "chirp_propnet_set_params", "chirp_propnet_get_params",
                     "chirp_propnet_get_grads", "chirp_propnet_forward", "chirp_propnet_backward",
                     "chirp_propnet_train_step", "chirp_propnet_normalize", "chirp_propose_windows",
-                    "chirpolator_run_selective", "chimageator_run_selective", "chirp_batch_run", "chirp_plan_fft_split",
+                    "chirpolator_run_selective", "chimageator_run_selective", "chirp_batch_run", "chirp_plan_fft_split", "chirp_detect",
                     "chirp_last_error")
 STAGES = ("forward", "inv_rows", "inv_cols", "correlate", "beamform", "split", "chirp",
-          "incoherent")
+          "incoherent", "detect")
 
 
 class ChirpError(RuntimeError):
@@ -146,6 +146,9 @@ def load():
         lib.chirp_plan_fft_split.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
                                              ctypes.POINTER(i), ctypes.POINTER(i)]
         lib.chirp_plan_fft_split.restype = i
+        lib.chirp_detect.argtypes = [vp, vp, i, ctypes.c_float, vp, ctypes.c_longlong, i,
+                                     ctypes.POINTER(ctypes.c_longlong), vp]
+        lib.chirp_detect.restype = i
         lib.chirp_plan_status.argtypes = [vp]
         lib.chirp_plan_status.restype = i
         lib.chirp_dedisperse_noalloc.argtypes = [vp, i, ll, ctypes.c_double, ctypes.c_double,
@@ -177,6 +180,16 @@ def _buf(a, dtype_np, what: str):
     if arr.dtype != dtype_np or not arr.flags["C_CONTIGUOUS"]:
         raise TypeError("%s must be a C-contiguous %s array" % (what, np.dtype(dtype_np).name))
     return ctypes.c_void_p(arr.ctypes.data), CHIRP_HOST, arr
+
+
+class Candidate(ctypes.Structure):
+    """chirp_candidate: one detection (trial DM index, dump, pixel, S/N, power)."""
+    _fields_ = [("dump", ctypes.c_longlong), ("dm", ctypes.c_int), ("pix", ctypes.c_int),
+                ("snr", ctypes.c_float), ("power", ctypes.c_float)]
+
+
+CANDIDATE_DTYPE = np.dtype([("dump", np.int64), ("dm", np.int32), ("pix", np.int32),
+                            ("snr", np.float32), ("power", np.float32)])
 
 
 def _vbuf(a, in_type=None):
@@ -405,6 +418,23 @@ class Plan:
         _check(load().chimageator_run_selective(self._h, vp, vl, ctypes.c_void_p(m.ctypes.data),
                                                 op, ol))
         return pow_out
+
+    def detect(self, pow_in, snr_min: float, max_cand: int = 1 << 16, with_stats: bool = False):
+        """Candidates of dump powers [n_dm, n_dump, n_pix] (chirp_detect) as a
+        numpy structured array (CANDIDATE_DTYPE) in (DM, dump, pixel) order;
+        with_stats also returns the (median, sigma) array [n_dm, n_pix, 2]."""
+        pp, pl, _k = _buf(pow_in, np.float32, "pow")
+        out = np.zeros(max(int(max_cand), 0), dtype=CANDIDATE_DTYPE)
+        st = np.zeros((self.n_dm, self.n_pix, 2), np.float32) if with_stats else None
+        n = ctypes.c_longlong(0)
+        _check(load().chirp_detect(self._h, pp, pl, float(snr_min),
+                                   ctypes.c_void_p(out.ctypes.data) if out.size else None,
+                                   int(out.size), CHIRP_HOST, ctypes.byref(n),
+                                   ctypes.c_void_p(st.ctypes.data) if st is not None else None))
+        if n.value > out.size:
+            raise ChirpError(-2, "%d candidates exceed max_cand = %d" % (n.value, out.size))
+        cands = out[:n.value].copy()
+        return (cands, st) if with_stats else cands
 
     def status(self):
         """Raise ChirpError if a bounded device wait of an earlier run gave up."""

@@ -7,6 +7,8 @@
 #include <cstdint>
 #include <vector>
 
+#include "../../include/chirp_gb300.h"
+
 // Records msg as the calling thread's chirp_last_error() and returns code.
 int chirp_report_error(int code, const char* msg);
 
@@ -103,5 +105,12 @@ cudaError_t launch_split_bf16(const float2* y, long long n_samp, int n_ant, int 
 cudaError_t launch_beam_tc(const uint8_t* b_img, const uint8_t* a_img, int n_ant, int n_pix,
                            int dump_len, long long first, long long last, float* pow, int* err,
                            int terms, cudaStream_t st);
+
+// ---- candidate detection (detect.cu) ----
+long long detect_chunks(int n_dm, long long n_dump, int n_pix);  // entries of counts / offsets
+cudaError_t launch_detect(const float* P, int n_dm, long long n_dump, int n_pix,
+                          const long long* first, const long long* last, float snr_min,
+                          float2* stats, int* counts, long long* offsets, long long* n_total,
+                          chirp_candidate* out, long long max_out, cudaStream_t st);
 
 }  // namespace chirp

@@ -117,6 +117,14 @@ struct chirp_plan {
   int* d_fb_shift = nullptr;   // [fb_n_dm][fb_chan]
   float* d_fb_S = nullptr;     // [fb_chan][T_fb]
   float* d_fb_D = nullptr;     // staging for host outputs
+  // candidate detection (chirp_detect), allocated on first use
+  long long* d_first_last = nullptr;  // [2][n_dm] valid dump range (set up at creation)
+  float* d_det_P = nullptr;           // staging of host powers
+  float2* d_det_stats = nullptr;      // [n_dm][n_pix] (med, sigma)
+  int* d_det_counts = nullptr;        // per chunk
+  long long* d_det_offsets = nullptr; // per chunk + 1 (total)
+  chirp_candidate* d_det_cand = nullptr;  // staging of host candidate lists
+  long long det_cand_cap = 0;
   int* d_lists = nullptr;      // selective searches: block and dump index lists
   size_t lists_cap = 0;
   // CUDA-graph replay of full device-buffer searches (chirp_config.flags)
@@ -185,6 +193,12 @@ void release(chirp_plan* p) {
   cudaFree(p->d_fb_D);
   cudaFree(p->d_lists);
   cudaFree(p->d_scale);
+  cudaFree(p->d_first_last);
+  cudaFree(p->d_det_P);
+  cudaFree(p->d_det_stats);
+  cudaFree(p->d_det_counts);
+  cudaFree(p->d_det_offsets);
+  cudaFree(p->d_det_cand);
   for (auto& g : p->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   cudaFree(p->d_out);
@@ -509,6 +523,13 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   if (!rc && p->n_pix > 0)
     rc = dev_alloc(p, (void**)&p->d_W, (size_t)p->n_pix * p->M * sizeof(float2), "weights");
   if (!rc) rc = dev_alloc(p, (void**)&p->d_err, sizeof(int), "status word");
+  std::vector<long long> first_last(2 * p->dmi.size());
+  for (size_t d = 0; d < p->dmi.size(); d++) {
+    first_last[d] = p->dmi[d].first;
+    first_last[p->dmi.size() + d] = p->dmi[d].last;
+  }
+  if (!rc) rc = dev_alloc(p, (void**)&p->d_first_last, first_last.size() * sizeof(long long),
+                          "dump ranges");
   std::vector<float> scale;
   if (!rc && p->in_type == CHIRP_IN_CI8) {
     scale.assign((size_t)p->M, 1.0f);
@@ -632,6 +653,9 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   if (e == cudaSuccess && !aimg.empty())
     e = cudaMemcpyAsync(p->d_aimg, aimg.data(), aimg.size(), cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->d_first_last, first_last.data(), first_last.size() * sizeof(long long),
+                        cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess && !scale.empty())
     e = cudaMemcpyAsync(p->d_scale, scale.data(), scale.size() * sizeof(float),
                         cudaMemcpyHostToDevice, p->stream);
@@ -1117,6 +1141,75 @@ int chirp_batch_run(chirp_plan* const* plans, const void* const* volts, const in
                         backends[i] == 0 ? kCorrelate : kBeams, outs[i], out_locs[i]);
     if (rc) return rc;
   }
+  return CHIRP_OK;
+}
+
+int chirp_detect(chirp_plan* p, const float* pow, int pow_loc, float snr_min,
+                 chirp_candidate* cand, long long max_cand, int cand_loc, long long* n_cand,
+                 float* stats_out) {
+  g_err[0] = 0;
+  if (!p || !pow || !n_cand || max_cand < 0 || (max_cand > 0 && !cand))
+    return fail(CHIRP_EINVAL, "NULL argument or negative max_cand");
+  if (p->n_pix <= 0) return fail(CHIRP_EUNSUPPORTED, "plan was created without pixels");
+  if (std::isnan(snr_min)) return fail(CHIRP_EINVAL, "snr_min is NaN");
+  if ((pow_loc != CHIRP_HOST && pow_loc != CHIRP_DEVICE) ||
+      (cand_loc != CHIRP_HOST && cand_loc != CHIRP_DEVICE))
+    return fail(CHIRP_EINVAL, "bad buffer location");
+  const int n_dm = (int)p->dm.size();
+  const size_t pbytes = (size_t)n_dm * p->n_dump * p->n_pix * sizeof(float);
+  const long long nc = detect_chunks(n_dm, p->n_dump, p->n_pix);
+  int rc = CHIRP_OK;
+  if (!p->d_det_stats) {
+    rc = dev_alloc(p, (void**)&p->d_det_stats, (size_t)n_dm * p->n_pix * sizeof(float2),
+                   "detection statistics");
+    if (!rc) rc = dev_alloc(p, (void**)&p->d_det_counts, (size_t)std::max(1LL, nc) * sizeof(int),
+                            "detection counts");
+    if (!rc) rc = dev_alloc(p, (void**)&p->d_det_offsets,
+                            (size_t)(std::max(1LL, nc) + 1) * sizeof(long long), "detection offsets");
+    if (rc) return rc;
+  }
+  const float* dP = pow;
+  if (pow_loc == CHIRP_HOST) {
+    if (!p->d_det_P) {
+      rc = dev_alloc(p, (void**)&p->d_det_P, pbytes, "power staging");
+      if (rc) return rc;
+    }
+    CK(cudaMemcpyAsync(p->d_det_P, pow, pbytes, cudaMemcpyHostToDevice, p->stream));
+    dP = p->d_det_P;
+  }
+  chirp_candidate* dc = cand;
+  if (cand_loc == CHIRP_HOST && max_cand > 0) {
+    if (p->det_cand_cap < max_cand) {
+      cudaFree(p->d_det_cand);
+      p->d_det_cand = nullptr;
+      p->det_cand_cap = 0;
+      rc = dev_alloc(p, (void**)&p->d_det_cand, (size_t)max_cand * sizeof(chirp_candidate),
+                     "candidate staging");
+      if (rc) return rc;
+      p->det_cand_cap = max_cand;
+    }
+    dc = p->d_det_cand;
+  }
+  const long long* dfirst = p->d_first_last;
+  const long long* dlast = p->d_first_last + n_dm;
+  long long* d_total = p->d_det_offsets + std::max(1LL, nc);
+  int mk = mark_begin(p);
+  CK(launch_detect(dP, n_dm, p->n_dump, p->n_pix, dfirst, dlast, snr_min, p->d_det_stats,
+                   p->d_det_counts, p->d_det_offsets, d_total, dc, max_cand, p->stream));
+  mark_end(p, CHIRP_STAGE_DETECT, mk);
+  long long total = 0;
+  CK(cudaMemcpyAsync(&total, d_total, sizeof(long long), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  const long long n_copy = std::min(total, max_cand);
+  const cudaMemcpyKind sk = cand_loc == CHIRP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (cand_loc == CHIRP_HOST && n_copy > 0)
+    CK(cudaMemcpyAsync(cand, dc, (size_t)n_copy * sizeof(chirp_candidate), cudaMemcpyDeviceToHost,
+                       p->stream));
+  if (stats_out)
+    CK(cudaMemcpyAsync(stats_out, p->d_det_stats, (size_t)n_dm * p->n_pix * sizeof(float2), sk,
+                       p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  *n_cand = total;
   return CHIRP_OK;
 }
 

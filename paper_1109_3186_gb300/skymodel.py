@@ -315,3 +315,29 @@ def precision_form(channel: int = 0, n_chan: int = 8, n_samp: int = 1 << 24, n_d
                     % (channel, n_chan, chan_bw / 1e6, int(math.log2(n_samp)), n_dm),
                     xyz, f0, chan_bw, n_samp, dms, dump_len, nfft_min, pix, pulses,
                     seed + 1000 * channel)
+
+
+# --------------------------------------------------------------------------
+# dump-power fields (inputs of the candidate detection alone)
+# --------------------------------------------------------------------------
+def power_field(n_dm: int, n_dump: int, n_pix: int, first, last, seed: int,
+                mean: float = 1.0, n_peaks: int = 0, peak_scale: float = 30.0) -> np.ndarray:
+    """float32 [n_dm, n_dump, n_pix] of exponentially distributed dump powers
+    (the chi-squared noise of a detected beam) inside each DM's valid dumps
+    [first[d], last[d]], zero outside, plus n_peaks seeded bright cells of
+    mean * (1 + peak_scale * U(0.5, 1))."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    P = np.zeros((n_dm, n_dump, n_pix), np.float32)
+    for d in range(n_dm):
+        f, l = int(first[d]), int(last[d])
+        if l >= f:
+            P[d, f:l + 1] = (mean * rng.exponential(size=(l - f + 1, n_pix))).astype(np.float32)
+    for _ in range(n_peaks):
+        d = int(rng.integers(0, n_dm))
+        f, l = int(first[d]), int(last[d])
+        if l < f:
+            continue
+        m = int(rng.integers(f, l + 1))
+        p = int(rng.integers(0, n_pix))
+        P[d, m, p] = np.float32(mean * (1.0 + peak_scale * rng.uniform(0.5, 1.0)))
+    return P
