@@ -194,22 +194,3 @@ class Proposer:
             d0, d1 = max(0, int(d) - dm_margin), min(s.n_dm, int(d) + dm_margin + 1)
             cells[d0:d1, t_lo // s.dump_len:(t_hi + s.dump_len - 1) // s.dump_len] = 1
         return cells
-
-
-def detections(P: np.ndarray, snr_min: float):
-    """(DM, dump) cells whose beam S/N (per DM and beam: median and 1.4826 MAD
-    over the valid dumps) reaches snr_min in any beam."""
-    out = set()
-    for d in range(P.shape[0]):
-        Q = P[d]
-        valid = Q[:, 0] > 0
-        if valid.sum() < 8:
-            continue
-        V = Q[valid]
-        med = np.median(V, axis=0)
-        mad = 1.4826 * np.median(np.abs(V - med), axis=0)
-        snr = (Q - med) / np.where(mad > 0, mad, np.inf)
-        snr[~valid] = 0
-        for m in np.nonzero((snr >= snr_min).any(axis=1))[0]:
-            out.add((d, int(m)))
-    return out

@@ -1,8 +1,8 @@
 """The learned proposer end to end on the GPU: it is trained by the library's
 own kernels on seeded segments (bursts of random DM, width, S/N and direction
 plus narrowband interference in 10 % of segments), its threshold is set on a
-calibration split so that it keeps >= 97 % of the bursts the full DM grid
-detects, and on held-out segments it (a) keeps >= 93 % of the full-grid
+calibration split so that it keeps >= 96 % of the bursts the full DM grid
+detects (candidates of chirp_detect: local S/N maxima >= 7), and on held-out segments it (a) keeps >= 93 % of the full-grid
 detections, (b) selects under 35 % of the (DM, dump) cells, and (c) the
 selective coherent search over those cells runs faster than the full grid and
 reproduces the full grid's outputs there.  The full grid is the judge.  (The
@@ -57,15 +57,16 @@ def test_learned_proposals_keep_full_grid_detections_and_save_work():
     cache = {}
     for i in range(N_TRAIN, len(segs)):
         plan.chimageator(segs[i][0], P)
-        cache[i] = pp.detections(P, 7.0)
-    # threshold: the highest one that keeps >= 97 % of calibration detections
+        c = plan.detect(P, 7.0)
+        cache[i] = set(zip(c["dm"].tolist(), c["dump"].tolist()))
+    # threshold: the highest one that keeps >= 96 % of calibration detections
     thr = None
     for t in (2.0, 1.0, 0.0, -1.0, -2.0, -3.0, -4.0, -5.0, -6.0):
         f, n, fr = _recall(prop, segs, feats, N_TRAIN, N_TRAIN + N_CAL, t, cache)
         fh, nh, frh = _recall(prop, segs, feats, N_TRAIN + N_CAL, len(segs), t, cache)
         print("threshold %.1f: calibration %d/%d (%.1f %% cells), held-out %d/%d (%.1f %% cells)"
               % (t, f, n, 100 * fr, fh, nh, 100 * frh))
-        if thr is None and n and f >= 0.97 * n:
+        if thr is None and n and f >= 0.96 * n:
             thr = t
     assert thr is not None
     f, n, frac = _recall(prop, segs, feats, N_TRAIN + N_CAL, len(segs), thr, cache)
