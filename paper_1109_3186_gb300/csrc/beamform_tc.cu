@@ -34,7 +34,7 @@
 // cp.async.bulk moves a whole tile.
 //
 // Kernel roles (320 threads): warp 0 lane 0 streams B tiles (bulk copies into
-// a 4-stage ring); warp 1 owns TMEM (512 columns = 4 accumulators of 128) and
+// a ring of 2-4 stages, as deep as shared memory allows); warp 1 owns TMEM (512 columns = 4 accumulators of 128) and
 // its lane 0 issues the MMAs; warps 2-9 form two warpgroups that drain the
 // accumulators of even / odd row tiles (one 128-column tcgen05.ld each), square
 // and integrate per dump, and write whole-dump powers.  Every wait is bounded;
@@ -55,6 +55,15 @@ namespace chirp {
 namespace {
 
 constexpr int RMAX = 8;        // row tiles per CTA (weights resident in smem)
+
+// Bytes of one 128-row A tile with ks K-steps (16 row groups of 2 ks core
+// matrices) and of one B tile of NT samples with GB k-groups.
+__host__ __device__ constexpr uint32_t a_tile_bytes_of(int ks) {
+  return 16u * 2u * (uint32_t)ks * 128u;
+}
+__host__ __device__ constexpr uint32_t b_tile_bytes_of(int NT, int GB) {
+  return (uint32_t)(NT / 8) * (uint32_t)GB * 128u;
+}
 
 // Two shapes of the same kernel:
 //  NT = 128 (any dump length): 4 accumulators of 128 columns, two warpgroups
@@ -81,8 +90,8 @@ struct BeamSmemPlan {
 template <int NT>
 __host__ __device__ inline BeamSmemPlan beam_smem_plan(int R, int ksteps, int G, int nstage) {
   BeamSmemPlan s;
-  s.a_bytes = (uint32_t)R * ksteps * 4096u;
-  s.b_stage_bytes = (uint32_t)NT * (uint32_t)G * 16u;  // G here = k-groups per B tile
+  s.a_bytes = (uint32_t)R * a_tile_bytes_of(ksteps);
+  s.b_stage_bytes = b_tile_bytes_of(NT, G);  // G here = k-groups per B tile
   s.red_off = s.a_bytes + (uint32_t)nstage * s.b_stage_bytes;
   s.bar_off = s.red_off + BeamCfg<NT>::RED_BYTES;
   s.total = s.bar_off + 256;
@@ -142,7 +151,7 @@ __global__ void __launch_bounds__(BeamCfg<NT>::THREADS, 1) k_beam_tc(BeamArgs ar
   const long long j_a = (ta - args.t_begin) / NT;
   const long long j_b = (tb - args.t_begin + NT - 1) / NT;
   const long long n_tiles = (m_b > m_a && R_eff > 0) ? j_b - j_a : 0;
-  const uint32_t a_tile_bytes = (uint32_t)args.ksteps * 4096u;
+  const uint32_t a_tile_bytes = a_tile_bytes_of(args.ksteps);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < nst; s++) {
@@ -439,7 +448,7 @@ __global__ void k_split_bf16(const float2* __restrict__ y, long long n_samp, int
                              int NT, uint8_t* __restrict__ b_img) {
   const long long U = n_tiles * NT;
   const long long total = U * G;
-  const size_t tile_bytes = (size_t)NT * GB * 16;
+  const size_t tile_bytes = b_tile_bytes_of(NT, GB);
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(idx / U);
@@ -498,7 +507,7 @@ float bf16_to_float(uint16_t h) {
 std::vector<uint8_t> build_beam_a_image(const double* W, int n_ant, int n_pix, int terms) {
   const int G = beam_tc_groups(n_ant), ks = beam_tc_ksteps(n_ant, terms);
   const int n_rowtiles = (2 * n_pix + 127) / 128;
-  const size_t tile_bytes = (size_t)ks * 4096;
+  const size_t tile_bytes = a_tile_bytes_of(ks);
   std::vector<uint8_t> img((size_t)n_rowtiles * tile_bytes, 0);
   for (int rt = 0; rt < n_rowtiles; rt++)
     for (int mg = 0; mg < 16; mg++)
@@ -539,20 +548,32 @@ int beam_tc_ksteps(int n_ant, int terms) {
   const int G = beam_tc_groups(n_ant);
   return terms == 3 ? (3 * G + 1) / 2 : (G + 1) / 2;
 }
-// Row tiles per CTA and B ring depth for a tile shape: the deepest ring
-// (down to 2 stages) with at least one row tile, then as many row tiles as
-// fit in 220 KB of shared memory.  False when not even that fits.
+// Row tiles per CTA and B ring depth for a tile shape.  All CTA columns of
+// a launch walk the same B tiles, so the column with the most row tiles sets
+// the time: take the fewest columns that the largest fitting R allows (R
+// fitting in 220 KB of shared memory with a 2-stage ring), spread the row
+// tiles evenly over them, then use the deepest ring that still fits.  False
+// when not even one row tile fits.
 template <int NT>
 static bool beam_tc_shape(int ks, int GB, int n_rowtiles, int* R_out, int* nst_out) {
-  for (int nst = BeamCfg<NT>::NSTAGE; nst >= 2; nst--) {
-    if (beam_smem_plan<NT>(1, ks, GB, nst).total > 220 * 1024) continue;
-    int R = RMAX < n_rowtiles ? RMAX : n_rowtiles;
-    while (R > 1 && beam_smem_plan<NT>(R, ks, GB, nst).total > 220 * 1024) R--;
-    *R_out = R;
-    *nst_out = nst;
-    return true;
-  }
-  return false;
+  auto fits = [&](int R, int nst) {
+    return beam_smem_plan<NT>(R, ks, GB, nst).total <= 220u * 1024u;
+  };
+  int rmax = 0;
+  for (int R = RMAX < n_rowtiles ? RMAX : n_rowtiles; R >= 1 && !rmax; R--)
+    if (fits(R, 2)) rmax = R;
+  if (!rmax) return false;
+  const int gx = (n_rowtiles + rmax - 1) / rmax;
+  const int R = (n_rowtiles + gx - 1) / gx;
+  int nst = 2;
+  for (int s = BeamCfg<NT>::NSTAGE; s > 2; s--)
+    if (fits(R, s)) {
+      nst = s;
+      break;
+    }
+  *R_out = R;
+  *nst_out = nst;
+  return true;
 }
 
 // Tile width for a shape: 256 samples when the dump length allows and the
@@ -570,8 +591,8 @@ int beam_tc_tile_samples(int n_ant, int n_pix, int dump_len, int terms) {
   return beam_tc_pick_nt(n_ant, n_pix, dump_len, terms);
 }
 long long beam_tc_tile_bytes(int n_ant, int n_pix, int dump_len, int terms) {
-  return (long long)beam_tc_tile_samples(n_ant, n_pix, dump_len, terms) *
-         beam_tc_bgroups(n_ant, terms) * 16;
+  const int nt = beam_tc_tile_samples(n_ant, n_pix, dump_len, terms);
+  return nt ? (long long)b_tile_bytes_of(nt, beam_tc_bgroups(n_ant, terms)) : 0;
 }
 
 cudaError_t launch_split_bf16(const float2* y, long long n_samp, int n_ant, int n_pix,
