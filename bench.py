@@ -40,6 +40,10 @@ WORKLOAD = ("chimageator: 12 ant within 6 km, 32 MHz @ 1.4 GHz, 2^22 samples/ant
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                   "sm_max_mhz": 2070.0}
 N_SM = 152
+DTYPE_LABEL = {1: "f32", 2: "f32 (beams: split-bf16 x3 on tensor cores, f32 acc)",
+               3: "f32 (beams: visibility quadratic form)",
+               4: "f32 dedispersion, bf16 beams (tensor cores, f32 acc)"}
+MODE_NAME = {1: "fp32_simt", 2: "tc_3xbf16", 3: "vis", 4: "tc_bf16"}
 FP32_LANES_PER_SM = 128
 
 
@@ -49,8 +53,12 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--beam-mode", type=int, default=0, help="0 auto, 1 FP32 SIMT, 2 tcgen05 3xbf16")
-    ap.add_argument("--cpu-dumps", type=int, default=128,
+    ap.add_argument("--beam-mode", type=int, default=0,
+                    help="0 auto (= 2), 1 FP32 CUDA cores, 2 tcgen05 split-BF16, "
+                         "3 visibility quadratic form, 4 tcgen05 BF16 (reduced precision)")
+    ap.add_argument("--no-alt", action="store_true",
+                    help="skip the extra timings of the other beam modes and of detection")
+    ap.add_argument("--cpu-dumps", type=int, default=640,
                     help="dumps per selected DM in the oracle's bounded CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -267,6 +275,8 @@ def stage_roofline(sc, plan, stage_ms, peaks, peak_kind, beam_mode, steps):
     n_pair = M * (M + 1) // 2
     # correlate: read the dedispersed voltages of every valid dump, write V
     stages["correlate"] = ("hbm", float(n_dump_valid) * (L * 8 * M + 8 * n_pair), hbm, "GB/s")
+    if beam_mode == 4:
+        beam_flops = float(n_dump_valid) * L * n_pix * (8 * M + 3)
     if beam_mode == 3:
         # beams from visibilities: 2 FMA per (pair, pixel, dump)
         stages["beamform"] = ("alu", 4.0 * n_pair * n_pix * n_dump_valid, fp32_tflops, "TFLOP/s")
@@ -371,21 +381,51 @@ def run_ours(args):
 
     roof = stage_roofline(sc, plan, stage, peaks, peak_kind, plan.info["beam_mode"], args.steps)
     dom = max(roof, key=lambda k: roof[k]["ms_per_step"]) if roof else None
-    n_groups = plan.info["n_group"]
-    per_dm = 5 if plan.info["beam_mode"] == 2 else 4
-    launches = args.steps * (2 * n_groups + per_dm * n_dm)
+    # kernels launched in the timed steps: one per timed stage launch, plus the
+    # second kernel (row pass) of every forward launch
+    launches = int(sum(n for _, n in stage.values())) + int(stage.get("forward", (0, 0))[1])
+
+    # the other beam modes and candidate detection, timed the same way (rank 0)
+    alt = {}
+    if not args.no_alt and rank == 0:
+        for mode in (3, 4, 1):
+            if mode == plan.info["beam_mode"]:
+                continue
+            pl2 = chirp.Plan.from_scenario(sc, beam_mode=mode, stream=stream)
+            k = 2 if mode == 1 else max(2, args.steps // 2)
+            pl2.chimageator(xd, Pd)
+            torch.cuda.synchronize()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(k):
+                pl2.chimageator(xd, Pd)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ms2 = a0.elapsed_time(a1) / k
+            alt[MODE_NAME[mode]] = {"value": units / (ms2 * 1e-3), "ms_per_step": ms2,
+                                    "steps": k, "dtype": DTYPE_LABEL[mode]}
+            pl2.close()
+        plan.chimageator(xd, Pd)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cands = plan.detect(Pd, 6.0, max_cand=1 << 20)
+        alt["detect"] = {"ms": 1e3 * (time.perf_counter() - t0), "candidates": int(len(cands)),
+                         "snr_min": 6.0, "note": "chirp_detect on one step's powers, host-timed"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if plan.info["beam_mode"] == 1 else "f32 (beams: 3xbf16 tensor, f32 acc)",
+                "dtype": DTYPE_LABEL[plan.info["beam_mode"]],
                 "data": "synthetic (seeded sky model: noise + dispersed bursts)",
                 "config": config_block(sc, world),
                 "beam_dm_dumps_per_s": world * beam_dumps / (ms * 1e-3),
                 "gpu_launches": launches, "clocks": clk}
         if e2e:
             line["e2e"] = e2e
+        if alt:
+            line["other_modes"] = alt
         if dom:
             r = roof[dom]
             traffic = None
