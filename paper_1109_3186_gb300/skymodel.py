@@ -291,13 +291,13 @@ def precision_form(channel: int = 0, n_chan: int = 8, n_samp: int = 1 << 24, n_d
                    f_centre: float = 1.4e9, n_pulse: int = 1) -> Scenario:
     """One coarse channel of the sparse 36-antenna array (6 km maximum
     baseline): 8 x 42 MHz channels around 1.4 GHz, channel c centred at
-    f_centre + (c - (n_chan - 1) / 2) chan_bw; trial DMs log-spaced from
-    dm_min to dm_max; 64 x 64 beams.  Voltages are meant to be quantised with
+    f_centre + (c - (n_chan - 1) / 2) chan_bw; trial DMs 0 and then n_dm - 1
+    log-spaced from dm_min to dm_max; 64 x 64 beams.  Voltages are meant to be quantised with
     quantize_ci8 before the search."""
     f0 = f_centre + (channel - 0.5 * (n_chan - 1)) * chan_bw
     rng = np.random.Generator(np.random.PCG64(seed + 7 + 1000 * channel))
     xyz = antenna_positions(n_ant, 6000.0, seed)
-    dms = np.geomspace(dm_min, dm_max, n_dm)
+    dms = np.concatenate([[0.0], np.geomspace(dm_min, dm_max, n_dm - 1)])
     pix = pixel_grid(n_side, field_deg)
     pulses = []
     fw = 50e-6
