@@ -59,12 +59,11 @@ extern "C" {
 #define CHIRP_DEVICE 1
 
 /* contraction used by the Chimageator back-end */
-#define CHIRP_BEAM_AUTO 0      /* CHIRP_BEAM_TC_3XBF16 where its tiles fit in
-                                  shared memory (up to 60 antennas), else
-                                  CHIRP_BEAM_VIS                              */
+#define CHIRP_BEAM_AUTO 0      /* CHIRP_BEAM_TC_3XBF16                        */
 #define CHIRP_BEAM_FP32_SIMT 1 /* plain FP32 FMA on the CUDA cores           */
-#define CHIRP_BEAM_TC_3XBF16 2 /* tcgen05, 3-term bf16 split, FP32 accumulate;
-                                  CHIRP_EUNSUPPORTED above 60 antennas       */
+#define CHIRP_BEAM_TC_3XBF16 2 /* tcgen05, 3-term bf16 split, FP32 accumulate
+                                  (above 60 antennas the weights are held in
+                                  TMEM instead of shared memory)             */
 #define CHIRP_BEAM_VIS 3       /* exact identity sum_t |w.y|^2 = w^H V w: the
                                   per-dump visibilities V (Chirpolator output)
                                   are formed first, then a quadratic form per
@@ -110,6 +109,11 @@ typedef struct {
   int in_type;             /* CHIRP_IN_*: element type of every voltage input
                               of this plan's runs ([n_ant][n_samp] elements) */
   const float* in_scale;   /* [n_ant] scale of CHIRP_IN_CI8 input; NULL = 1   */
+  int beam_shape;          /* tensor-core beam kernel shape: 0 = the library's
+                              choice; 1 = 128-sample tiles, weights in shared
+                              memory; 2 = 256-sample tiles (dump_len % 256 ==
+                              0); 3 = 128-sample tiles, weights in TMEM.  A
+                              shape that does not fit: CHIRP_EUNSUPPORTED    */
   int fft_row;             /* 0: row length of the two-pass FFT chosen by the
                               library (or the autotuner); else a power of two
                               in 256..4096 forced for every FFT-length group
@@ -139,6 +143,7 @@ typedef struct {
   long long valid_samples; /* sum over DMs of n_ant * (n_samp - n_hi - n_lo)^+  */
   int beam_mode;           /* CHIRP_BEAM_* actually used (AUTO resolved)        */
   long long fb_samples;    /* T_fb of the incoherent search (0 when off)        */
+  int beam_shape;          /* tensor-core beam kernel shape used (0: none)      */
 } chirp_plan_info;
 
 /* Create a plan: validates cfg, derives the per-DM FFT lengths and block

@@ -66,14 +66,16 @@ class _Config(ctypes.Structure):
                 ("beam_mode", ctypes.c_int), ("fb_chan", ctypes.c_int), ("fb_int", ctypes.c_int),
                 ("fb_dm", ctypes.POINTER(ctypes.c_double)), ("fb_n_dm", ctypes.c_int),
                 ("flags", ctypes.c_int), ("in_type", ctypes.c_int),
-                ("in_scale", ctypes.POINTER(ctypes.c_float)), ("fft_row", ctypes.c_int)]
+                ("in_scale", ctypes.POINTER(ctypes.c_float)), ("beam_shape", ctypes.c_int),
+                ("fft_row", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
     _fields_ = [("n_dump", ctypes.c_longlong), ("n_pair", ctypes.c_int),
                 ("n_group", ctypes.c_int), ("workspace_bytes", ctypes.c_longlong),
                 ("ifft_points", ctypes.c_longlong), ("valid_samples", ctypes.c_longlong),
-                ("beam_mode", ctypes.c_int), ("fb_samples", ctypes.c_longlong)]
+                ("beam_mode", ctypes.c_int), ("fb_samples", ctypes.c_longlong),
+                ("beam_shape", ctypes.c_int)]
 
 
 _lib = None
@@ -306,7 +308,7 @@ class Plan:
                  nfft_min: int, pix_lm=None, k_dm: float = K_DM_DEFAULT,
                  beam_mode: int = BEAM_AUTO, n_ant: int | None = None, stream=None,
                  fb_chan: int = 0, fb_int: int = 1, fb_dm=None, flags: int = 0, fft_row: int = 0,
-                 in_type: int = IN_C64, in_scale=None):
+                 in_type: int = IN_C64, in_scale=None, beam_shape: int = 0):
         self._xyz = None if xyz is None else np.ascontiguousarray(xyz, dtype=np.float64)
         self._dms = np.ascontiguousarray(np.atleast_1d(dms), dtype=np.float64)
         self._pix = None if pix_lm is None else np.ascontiguousarray(pix_lm, dtype=np.float64)
@@ -334,6 +336,7 @@ class Plan:
         cfg.flags = int(flags)
         cfg.fft_row = int(fft_row)
         cfg.in_type = int(in_type)
+        cfg.beam_shape = int(beam_shape)
         self.in_type = int(in_type)
         self._scale = (None if in_scale is None
                        else np.ascontiguousarray(np.atleast_1d(in_scale), dtype=np.float32))

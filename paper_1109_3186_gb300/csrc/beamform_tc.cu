@@ -65,7 +65,11 @@ __host__ __device__ constexpr uint32_t b_tile_bytes_of(int NT, int GB) {
   return (uint32_t)(NT / 8) * (uint32_t)GB * 128u;
 }
 
-// Two shapes of the same kernel:
+// Three shapes of the same kernel:
+//  NT = 128, A in TMEM (AT): the weights are copied once into TMEM columns
+//    256.. (128 lanes = rows, two BF16 per column) and every MMA reads A from
+//    there, so shared memory feeds only B; 2 accumulators of 128 columns,
+//    two warpgroups each draining the row tiles of one parity;
 //  NT = 128 (any dump length): 4 accumulators of 128 columns, two warpgroups
 //    each draining whole accumulators (row tiles of one parity);
 //  NT = 256 (dump length a multiple of 256): 2 accumulators of 256 columns,
@@ -73,9 +77,11 @@ __host__ __device__ constexpr uint32_t b_tile_bytes_of(int NT, int GB) {
 //    releasing it right after the load; the four partial sums of a row are
 //    combined in shared memory once per dump.  The wider MMA halves the
 //    shared-memory operand traffic per flop.
-template <int NT>
+template <int NT, bool AT = false>
 struct BeamCfg {
-  static constexpr int NACC = 512 / NT;           // TMEM accumulators
+  static_assert(!AT || NT == 128, "A in TMEM is used with 128-sample tiles");
+  static constexpr int NACC = AT ? 2 : 512 / NT;  // TMEM accumulators
+  static constexpr uint32_t A_COL = 256;          // AT: first TMEM column of the weights
   static constexpr int NSTAGE = NT == 256 ? 3 : 4;  // B ring depth (fewer when smem is short)
   static constexpr int EPI_WARPS = NT == 256 ? 16 : 8;
   static constexpr int THREADS = 64 + 32 * EPI_WARPS;
@@ -87,13 +93,13 @@ struct BeamSmemPlan {
   uint32_t a_bytes, b_stage_bytes, red_off, bar_off, total;
 };
 
-template <int NT>
+template <int NT, bool AT = false>
 __host__ __device__ inline BeamSmemPlan beam_smem_plan(int R, int ksteps, int G, int nstage) {
   BeamSmemPlan s;
-  s.a_bytes = (uint32_t)R * a_tile_bytes_of(ksteps);
+  s.a_bytes = AT ? 0u : (uint32_t)R * a_tile_bytes_of(ksteps);
   s.b_stage_bytes = b_tile_bytes_of(NT, G);  // G here = k-groups per B tile
   s.red_off = s.a_bytes + (uint32_t)nstage * s.b_stage_bytes;
-  s.bar_off = s.red_off + BeamCfg<NT>::RED_BYTES;
+  s.bar_off = s.red_off + BeamCfg<NT, AT>::RED_BYTES;
   s.total = s.bar_off + 256;
   return s;
 }
@@ -108,17 +114,18 @@ struct BeamArgs {
   long long n_dumps;   // valid dumps of this DM
   long long dumps_per_cta;
   int L, n_pix, n_rowtiles, R, GB, bwrap, ksteps;  // GB: k-groups per B tile
-  int nstage;          // B ring depth, 2 .. BeamCfg<NT>::NSTAGE
+  int nstage;          // B ring depth, 2 .. BeamCfg<NT, AT>::NSTAGE
 };
 
-template <int NT>
-__global__ void __launch_bounds__(BeamCfg<NT>::THREADS, 1) k_beam_tc(BeamArgs args) {
-  constexpr int NACC = BeamCfg<NT>::NACC;
-  constexpr int NSTAGE = BeamCfg<NT>::NSTAGE;  // barrier slots; the ring uses nst of them
+template <int NT, bool AT>
+__global__ void __launch_bounds__(BeamCfg<NT, AT>::THREADS, 1) k_beam_tc(BeamArgs args) {
+  using Cfg = BeamCfg<NT, AT>;
+  constexpr int NACC = Cfg::NACC;
+  constexpr int NSTAGE = Cfg::NSTAGE;  // barrier slots; the ring uses nst of them
   const int nst = args.nstage;
-  constexpr uint32_t IDESC = BeamCfg<NT>::IDESC;
+  constexpr uint32_t IDESC = Cfg::IDESC;
   extern __shared__ __align__(1024) uint8_t smem[];
-  const BeamSmemPlan sp = beam_smem_plan<NT>(args.R, args.ksteps, args.GB, nst);
+  const BeamSmemPlan sp = beam_smem_plan<NT, AT>(args.R, args.ksteps, args.GB, nst);
   float* red = (float*)(smem + sp.red_off);  // NT = 256: [4 slices][RMAX][128 rows]
   uint8_t* smA = smem;
   uint8_t* smB = smem + sp.a_bytes;
@@ -172,6 +179,30 @@ __global__ void __launch_bounds__(BeamCfg<NT>::THREADS, 1) k_beam_tc(BeamArgs ar
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tmem_slot;
+  if constexpr (AT) {
+    // weights into TMEM: warpgroup wg copies the row tiles of its parity;
+    // thread (quarter q, lane) holds row 32 q + lane of the tile
+    if (warp >= 2 && n_tiles > 0) {
+      const int wg = (warp - 2) / 4, q = warp & 3, row = 32 * q + lane;
+      const int mg = row / 8, r8 = row % 8;
+      for (int r = wg; r < R_eff; r += 2) {
+        const uint8_t* src = args.a_img + (size_t)(rt0 + r) * a_tile_bytes +
+                             (size_t)mg * (2 * args.ksteps * 128) + (size_t)r8 * 16;
+        for (int ks = 0; ks < args.ksteps; ks++) {
+          const uint4 lo = *reinterpret_cast<const uint4*>(src + (size_t)(2 * ks) * 128);
+          const uint4 hi = *reinterpret_cast<const uint4*>(src + (size_t)(2 * ks + 1) * 128);
+          const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+          tc::tmem_st8(tmem + ((uint32_t)(32 * q) << 16) + Cfg::A_COL +
+                           (uint32_t)((r * args.ksteps + ks) * 8),
+                       w);
+        }
+      }
+      tc::tmem_wait_st();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+  }
 
   auto raise = [&]() {
     *abort_flag = 1;
@@ -181,14 +212,20 @@ __global__ void __launch_bounds__(BeamCfg<NT>::THREADS, 1) k_beam_tc(BeamArgs ar
   if (n_tiles > 0) {
     if (warp == 0 && lane == 0) {
       // ------------------------------------------------------ producer
-      tc::mbar_arrive_expect_tx(abar, (uint32_t)R_eff * a_tile_bytes);
-      for (int r = 0; r < R_eff; r++)
-        tc::bulk_g2s(smA + r * a_tile_bytes, args.a_img + (size_t)(rt0 + r) * a_tile_bytes,
-                     a_tile_bytes, abar);
+      if constexpr (!AT) {
+        tc::mbar_arrive_expect_tx(abar, (uint32_t)R_eff * a_tile_bytes);
+        for (int r = 0; r < R_eff; r++)
+          tc::bulk_g2s(smA + r * a_tile_bytes, args.a_img + (size_t)(rt0 + r) * a_tile_bytes,
+                       a_tile_bytes, abar);
+      }
       long long issued = 0;
+      int s = 0;
+      uint32_t ph = 0;
       for (long long i = 0; i < n_tiles; i++) {
-        const int s = (int)(i % nst);
-        const uint32_t ph = (uint32_t)((i / nst) & 1);
+        if (i > 0 && ++s == nst) {
+          s = 0;
+          ph ^= 1u;
+        }
         if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
           raise();
           break;
@@ -201,28 +238,33 @@ __global__ void __launch_bounds__(BeamCfg<NT>::THREADS, 1) k_beam_tc(BeamArgs ar
       }
       if (*abort_flag) {
         // let every copy this thread issued land before the CTA goes away
-        tc::mbar_wait(abar, 0, nullptr, 1u << 22);
+        if constexpr (!AT) tc::mbar_wait(abar, 0, nullptr, 1u << 22);
         for (long long i = issued > nst ? issued - nst : 0; i < issued; i++)
           tc::mbar_wait(&full[i % nst], (uint32_t)((i / nst) & 1), nullptr, 1u << 22);
       }
     } else if (warp == 1 && lane == 0) {
       // ------------------------------------------------------ MMA issuer
-      const uint32_t a_base = tc::smem_u32(smA), b_base = tc::smem_u32(smB);
+      // Descriptors are formed once and advanced by adding the start-address
+      // offset (bytes / 16) of each K step, stage and row tile: the issue
+      // loop of this single thread is what feeds the tensor pipe.
       const uint32_t a_sbo = 2u * args.ksteps * 128u, b_sbo = (uint32_t)args.GB * 128u;
-      bool ok = tc::mbar_wait(abar, 0, abort_flag);
+      const uint64_t a_desc0 = tc::sdesc(tc::smem_u32(smA), 128u, a_sbo);
+      const uint64_t b_desc0 = tc::sdesc(tc::smem_u32(smB), 128u, b_sbo);
+      const int ksteps = args.ksteps, bwrap = args.bwrap;
+      bool ok = AT ? true : tc::mbar_wait(abar, 0, abort_flag);
       if (!ok) raise();
-      long long u = 0;
+      int acc = 0;
+      uint32_t aph = 0;
+      int s = 0;
+      uint32_t ph = 0;
       for (long long i = 0; ok && i < n_tiles; i++) {
-        const int s = (int)(i % nst);
-        const uint32_t ph = (uint32_t)((i / nst) & 1);
         if (!tc::mbar_wait(&full[s], ph, abort_flag)) {
           raise();
           break;
         }
         tc::fence_after();
-        for (int r = 0; r < R_pipe; r++, u++) {
-          const int acc = (int)(u % NACC);
-          const uint32_t aph = (uint32_t)((u / NACC) & 1);
+        const uint64_t b_desc = b_desc0 + (uint64_t)((s * sp.b_stage_bytes) >> 4);
+        for (int r = 0; r < R_pipe; r++) {
           if (!tc::mbar_wait(&acce[acc], aph ^ 1, abort_flag)) {
             raise();
             ok = false;
@@ -230,18 +272,32 @@ __global__ void __launch_bounds__(BeamCfg<NT>::THREADS, 1) k_beam_tc(BeamArgs ar
           }
           tc::fence_after();
           const uint32_t d = tmem + (uint32_t)(acc * NT);
-          for (int ks = 0; r < R_eff && ks < args.ksteps; ks++) {
-            const int p0 = 2 * ks;
-            const int bg = p0 < args.bwrap ? p0 : p0 - args.bwrap;
-            const uint64_t ad = tc::sdesc(a_base + r * a_tile_bytes + ks * 256u, 128u, a_sbo);
-            const uint64_t bd =
-                tc::sdesc(b_base + s * sp.b_stage_bytes + bg * 128u, 128u, b_sbo);
-            tc::mma_bf16(d, ad, bd, IDESC, ks > 0 ? 1u : 0u);
+          if (r < R_eff) {
+            const uint64_t a_desc = a_desc0 + (uint64_t)((r * a_tile_bytes) >> 4);
+            const uint32_t a_col = tmem + Cfg::A_COL + (uint32_t)(r * ksteps * 8);
+#pragma unroll 4
+            for (int ks = 0; ks < ksteps; ks++) {
+              const int p0 = 2 * ks;
+              const int bg = p0 < bwrap ? p0 : p0 - bwrap;
+              const uint64_t bd = b_desc + (uint64_t)(bg * 8);
+              if constexpr (AT)
+                tc::mma_bf16_ts(d, a_col + (uint32_t)(ks * 8), bd, IDESC, ks > 0 ? 1u : 0u);
+              else
+                tc::mma_bf16(d, a_desc + (uint64_t)(ks * 16), bd, IDESC, ks > 0 ? 1u : 0u);
+            }
           }
           tc::mma_commit(&accf[acc]);
+          if (++acc == NACC) {
+            acc = 0;
+            aph ^= 1u;
+          }
         }
         if (!ok) break;
         tc::mma_commit(&empty[s]);
+        if (++s == nst) {
+          s = 0;
+          ph ^= 1u;
+        }
       }
       // nothing may be in flight when TMEM is released
       tc::mma_commit(drain);
@@ -262,14 +318,17 @@ __global__ void __launch_bounds__(BeamCfg<NT>::THREADS, 1) k_beam_tc(BeamArgs ar
         // (later waits return at once because the abort flag is up) and all
         // warps leave together at the next combine point, or at the end.
         bool aborted = false;
+        // counters instead of divisions: accumulator ring position, and the
+        // tile within the current dump (dumps are whole tiles here)
+        int acc = 0;
+        uint32_t aph = 0;
+        const int tiles_per_dump = args.L / NT;
+        int tile_in_dump = 0;
+        long long m = m_a;
         for (long long i = 0; i < n_tiles; i++) {
-          const long long t0 = args.t_begin + (j_a + i) * NT;
 #pragma unroll
           for (int r = 0; r < RMAX; r++) {
             if (r >= R_pipe) break;
-            const long long u = i * R_pipe + r;
-            const int acc = (int)(u % NACC);
-            const uint32_t aph = (uint32_t)((u / NACC) & 1);
             if (!aborted && !tc::mbar_wait(&accf[acc], aph, abort_flag)) {
               raise();
               aborted = true;
@@ -293,9 +352,13 @@ __global__ void __launch_bounds__(BeamCfg<NT>::THREADS, 1) k_beam_tc(BeamArgs ar
               }
               sum[r] += (p0 + p1) + (p2 + p3);
             }
+            if (++acc == NACC) {
+              acc = 0;
+              aph ^= 1u;
+            }
           }
-          if ((t0 + NT) % args.L == 0) {  // this tile closes dump m (warp-uniform)
-            const long long m = (t0 + NT) / args.L - 1;
+          if (++tile_in_dump == tiles_per_dump) {  // this tile closes dump m (warp-uniform)
+            tile_in_dump = 0;
 #pragma unroll
             for (int r = 0; r < RMAX; r++) {
               if (r < R_eff) red[(g * RMAX + r) * 128 + row] = sum[r];
@@ -310,7 +373,7 @@ __global__ void __launch_bounds__(BeamCfg<NT>::THREADS, 1) k_beam_tc(BeamArgs ar
                 "bar.red.or.pred q, 1, %2, p;\n\t"
                 "selp.u32 %0, 1, 0, q;\n\t}"
                 : "=r"(stop_u)
-                : "r"((uint32_t)(aborted || *abort_flag != 0)), "r"(32 * BeamCfg<NT>::EPI_WARPS)
+                : "r"((uint32_t)(aborted || *abort_flag != 0)), "r"(32 * Cfg::EPI_WARPS)
                 : "memory");
             const bool stop = stop_u != 0;
             if (!stop)
@@ -322,8 +385,9 @@ __global__ void __launch_bounds__(BeamCfg<NT>::THREADS, 1) k_beam_tc(BeamArgs ar
                 const int p = ((rt0 + r) * 128 + row) >> 1;
                 if (!(lane & 1) && p < args.n_pix) args.pow[m * args.n_pix + p] = tot + other;
               }
-            asm volatile("bar.sync 1, %0;" ::"r"(32 * BeamCfg<NT>::EPI_WARPS) : "memory");
+            asm volatile("bar.sync 1, %0;" ::"r"(32 * Cfg::EPI_WARPS) : "memory");
             if (stop) break;
+            m++;
           }
         }
       } else {
@@ -551,13 +615,15 @@ int beam_tc_ksteps(int n_ant, int terms) {
 // Row tiles per CTA and B ring depth for a tile shape.  All CTA columns of
 // a launch walk the same B tiles, so the column with the most row tiles sets
 // the time: take the fewest columns that the largest fitting R allows (R
-// fitting in 220 KB of shared memory with a 2-stage ring), spread the row
+// fitting in 220 KB of shared memory with a 2-stage ring, and for AT its
+// weights in the 256 TMEM columns beside the accumulators), spread the row
 // tiles evenly over them, then use the deepest ring that still fits.  False
 // when not even one row tile fits.
-template <int NT>
+template <int NT, bool AT>
 static bool beam_tc_shape(int ks, int GB, int n_rowtiles, int* R_out, int* nst_out) {
   auto fits = [&](int R, int nst) {
-    return beam_smem_plan<NT>(R, ks, GB, nst).total <= 220u * 1024u;
+    if (AT && R * ks * 8 > 512 - (int)BeamCfg<NT, AT>::A_COL) return false;
+    return beam_smem_plan<NT, AT>(R, ks, GB, nst).total <= 220u * 1024u;
   };
   int rmax = 0;
   for (int R = RMAX < n_rowtiles ? RMAX : n_rowtiles; R >= 1 && !rmax; R--)
@@ -566,7 +632,7 @@ static bool beam_tc_shape(int ks, int GB, int n_rowtiles, int* R_out, int* nst_o
   const int gx = (n_rowtiles + rmax - 1) / rmax;
   const int R = (n_rowtiles + gx - 1) / gx;
   int nst = 2;
-  for (int s = BeamCfg<NT>::NSTAGE; s > 2; s--)
+  for (int s = BeamCfg<NT, AT>::NSTAGE; s > 2; s--)
     if (fits(R, s)) {
       nst = s;
       break;
@@ -576,31 +642,42 @@ static bool beam_tc_shape(int ks, int GB, int n_rowtiles, int* R_out, int* nst_o
   return true;
 }
 
-// Tile width for a shape: 256 samples when the dump length allows and the
-// shape fits, else 128; 0 when neither fits.
-static int beam_tc_pick_nt(int n_ant, int n_pix, int dump_len, int terms) {
+// Kernel shape for a search: 0 none fits, 1 = 128-sample tiles with the
+// weights in shared memory, 2 = 256-sample tiles (dump length a multiple of
+// 256), 3 = 128-sample tiles with the weights in TMEM.  Preference, from
+// timing the 12-antenna, 1024-beam search (beam stage per 64 DMs): 2 (84.6
+// ms), then 1 (131 ms), then 3 (150 ms; it only frees shared memory, which
+// matters when the weights of one row tile do not fit there).
+
+int beam_tc_pick(int n_ant, int n_pix, int dump_len, int terms, int forced) {
   const int ks = beam_tc_ksteps(n_ant, terms), GB = beam_tc_bgroups(n_ant, terms);
   const int n_rowtiles = (2 * n_pix + 127) / 128;
   int R, nst;
-  if (dump_len % 256 == 0 && beam_tc_shape<256>(ks, GB, n_rowtiles, &R, &nst)) return 256;
-  if (beam_tc_shape<128>(ks, GB, n_rowtiles, &R, &nst)) return 128;
+  const bool at = beam_tc_shape<128, true>(ks, GB, n_rowtiles, &R, &nst);
+  const bool w256 = dump_len % 256 == 0 && beam_tc_shape<256, false>(ks, GB, n_rowtiles, &R, &nst);
+  const bool w128 = beam_tc_shape<128, false>(ks, GB, n_rowtiles, &R, &nst);
+  if (forced != 0)
+    return (forced == 3 && at) || (forced == 2 && w256) || (forced == 1 && w128) ? forced : 0;
+  if (w256) return 2;
+  if (w128) return 1;
+  if (at) return 3;
   return 0;
 }
 
-int beam_tc_tile_samples(int n_ant, int n_pix, int dump_len, int terms) {
-  return beam_tc_pick_nt(n_ant, n_pix, dump_len, terms);
-}
-long long beam_tc_tile_bytes(int n_ant, int n_pix, int dump_len, int terms) {
-  const int nt = beam_tc_tile_samples(n_ant, n_pix, dump_len, terms);
+
+int beam_tc_tile_samples(int shape) { return shape == 0 ? 0 : (shape == 2 ? 256 : 128); }
+long long beam_tc_tile_bytes(int n_ant, int shape, int terms) {
+  const int nt = beam_tc_tile_samples(shape);
   return nt ? (long long)b_tile_bytes_of(nt, beam_tc_bgroups(n_ant, terms)) : 0;
 }
 
-cudaError_t launch_split_bf16(const float2* y, long long n_samp, int n_ant, int n_pix,
-                              int dump_len, long long t_begin, long long t_end, uint8_t* b_img,
-                              int terms, cudaStream_t st) {
+
+cudaError_t launch_split_bf16(const float2* y, long long n_samp, int n_ant, int shape,
+                              long long t_begin, long long t_end, uint8_t* b_img, int terms,
+                              cudaStream_t st) {
   if (t_end <= t_begin) return cudaSuccess;
   const int G = beam_tc_groups(n_ant), GB = beam_tc_bgroups(n_ant, terms);
-  const int NT = beam_tc_tile_samples(n_ant, n_pix, dump_len, terms);
+  const int NT = beam_tc_tile_samples(shape);
   if (NT == 0) return cudaErrorInvalidConfiguration;
   const long long n_tiles = (t_end - t_begin + NT - 1) / NT;
   const long long total = n_tiles * NT * G;
@@ -611,18 +688,22 @@ cudaError_t launch_split_bf16(const float2* y, long long n_samp, int n_ant, int 
   return cudaGetLastError();
 }
 
-template <int NT>
+namespace {
+
+template <int NT, bool AT>
 static cudaError_t launch_beam_tc_nt(const uint8_t* b_img, const uint8_t* a_img, int n_ant,
                                      int n_pix, int dump_len, long long first, long long last,
                                      float* pow, int* err, int terms, cudaStream_t st) {
+  using Cfg = BeamCfg<NT, AT>;
   const int ks = beam_tc_ksteps(n_ant, terms), G = beam_tc_bgroups(n_ant, terms);
   const int n_rowtiles = (2 * n_pix + 127) / 128;
   int R, nst;
-  if (!beam_tc_shape<NT>(ks, G, n_rowtiles, &R, &nst)) return cudaErrorInvalidConfiguration;
-  const BeamSmemPlan sp = beam_smem_plan<NT>(R, ks, G, nst);
+  if (!beam_tc_shape<NT, AT>(ks, G, n_rowtiles, &R, &nst)) return cudaErrorInvalidConfiguration;
+  const BeamSmemPlan sp = beam_smem_plan<NT, AT>(R, ks, G, nst);
   // at least 116 KB so that a second CTA never shares the SM (and its TMEM)
   const uint32_t smem_bytes = sp.total > 116 * 1024 ? sp.total : 116 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_beam_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_beam_tc<NT, AT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes);
   if (e != cudaSuccess) return e;
   const int gx = (n_rowtiles + R - 1) / R;
@@ -648,22 +729,29 @@ static cudaError_t launch_beam_tc_nt(const uint8_t* b_img, const uint8_t* a_img,
   a.bwrap = terms == 3 ? 2 * beam_tc_groups(n_ant) : G;
   a.ksteps = ks;
   a.nstage = nst;
-  k_beam_tc<NT><<<dim3(gx, (unsigned)gy), BeamCfg<NT>::THREADS, smem_bytes, st>>>(a);
+  k_beam_tc<NT, AT><<<dim3(gx, (unsigned)gy), Cfg::THREADS, smem_bytes, st>>>(a);
   return cudaGetLastError();
 }
 
+}  // namespace
+
 cudaError_t launch_beam_tc(const uint8_t* b_img, const uint8_t* a_img, int n_ant, int n_pix,
                            int dump_len, long long first, long long last, float* pow, int* err,
-                           int terms, cudaStream_t st) {
+                           int terms, int shape, cudaStream_t st) {
   if (last < first) return cudaSuccess;
-  const int nt = beam_tc_pick_nt(n_ant, n_pix, dump_len, terms);
-  if (nt == 256)
-    return launch_beam_tc_nt<256>(b_img, a_img, n_ant, n_pix, dump_len, first, last, pow, err,
-                                  terms, st);
-  if (nt == 128)
-    return launch_beam_tc_nt<128>(b_img, a_img, n_ant, n_pix, dump_len, first, last, pow, err,
-                                  terms, st);
-  return cudaErrorInvalidConfiguration;
+  switch (shape) {
+    case 3:
+      return launch_beam_tc_nt<128, true>(b_img, a_img, n_ant, n_pix, dump_len, first, last, pow,
+                                          err, terms, st);
+    case 2:
+      return launch_beam_tc_nt<256, false>(b_img, a_img, n_ant, n_pix, dump_len, first, last,
+                                           pow, err, terms, st);
+    case 1:
+      return launch_beam_tc_nt<128, false>(b_img, a_img, n_ant, n_pix, dump_len, first, last,
+                                           pow, err, terms, st);
+    default:
+      return cudaErrorInvalidConfiguration;
+  }
 }
 
 }  // namespace chirp

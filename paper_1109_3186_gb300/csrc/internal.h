@@ -94,17 +94,20 @@ cudaError_t launch_incoherent(float2* scratch, long long seq_stride, int n_ant, 
 int beam_tc_groups(int n_ant);                // 8-wide real-K groups per head/tail part
 int beam_tc_bgroups(int n_ant, int terms);    // 8-wide k-groups of one B tile
 int beam_tc_ksteps(int n_ant, int terms);     // 16-wide MMA K steps
-// samples per B tile: 256 when dump_len % 256 == 0 and the shape fits in
-// shared memory, else 128; 0 when the shape does not fit at all
-int beam_tc_tile_samples(int n_ant, int n_pix, int dump_len, int terms);
-long long beam_tc_tile_bytes(int n_ant, int n_pix, int dump_len, int terms);  // one B tile
+// Kernel shape: 1 = 128-sample tiles, weights in shared memory; 2 = 256-sample
+// tiles (dump_len % 256 == 0); 3 = 128-sample tiles, weights in TMEM.
+// forced = 0 picks the preferred shape that fits; a forced shape that does
+// not fit, or no fitting shape, gives 0.
+int beam_tc_pick(int n_ant, int n_pix, int dump_len, int terms, int forced);
+int beam_tc_tile_samples(int shape);                          // samples per B tile
+long long beam_tc_tile_bytes(int n_ant, int shape, int terms);  // bytes of one B tile
 std::vector<uint8_t> build_beam_a_image(const double* W, int n_ant, int n_pix, int terms);
-cudaError_t launch_split_bf16(const float2* y, long long n_samp, int n_ant, int n_pix,
-                              int dump_len, long long t_begin, long long t_end, uint8_t* b_img,
-                              int terms, cudaStream_t st);
+cudaError_t launch_split_bf16(const float2* y, long long n_samp, int n_ant, int shape,
+                              long long t_begin, long long t_end, uint8_t* b_img, int terms,
+                              cudaStream_t st);
 cudaError_t launch_beam_tc(const uint8_t* b_img, const uint8_t* a_img, int n_ant, int n_pix,
                            int dump_len, long long first, long long last, float* pow, int* err,
-                           int terms, cudaStream_t st);
+                           int terms, int shape, cudaStream_t st);
 
 // ---- candidate detection (detect.cu) ----
 long long detect_chunks(int n_dm, long long n_dump, int n_pix);  // entries of counts / offsets

@@ -92,6 +92,7 @@ struct chirp_plan {
   int n_pix = 0;
   int beam_mode = 0;
   int beam_terms = 3;         // tensor-core modes: 3 (split BF16) or 1 (BF16)
+  int beam_shape = 0;         // tensor-core kernel shape (beam_tc_pick)
   int in_type = CHIRP_IN_C64;
   float* d_scale = nullptr;   // [M] CHIRP_IN_CI8 scales
   cudaStream_t stream = nullptr;
@@ -337,6 +338,8 @@ int validate(const chirp_config* c) {
     return fail(CHIRP_EINVAL, "nfft_min must be a power of two in 256..2^24");
   if (c->fft_row != 0 && (!is_pow2(c->fft_row) || c->fft_row < 256 || c->fft_row > 4096))
     return fail(CHIRP_EINVAL, "fft_row must be 0 or a power of two in 256..4096");
+  if (c->beam_shape < 0 || c->beam_shape > 3)
+    return fail(CHIRP_EINVAL, "beam_shape must be 0..3");
   if (c->flags & ~(CHIRP_FLAG_GRAPHS | CHIRP_FLAG_AUTOTUNE))
     return fail(CHIRP_EINVAL, "unknown flag bits 0x%x", c->flags);
   if (c->n_pix < 0) return fail(CHIRP_EINVAL, "n_pix must be >= 0");
@@ -408,17 +411,21 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   p->n_pix = cfg->n_pix;
   // AUTO: tensor cores (split BF16, FP32 accumulate) for the beam GEMM
   p->beam_mode = cfg->beam_mode;
-  if (p->beam_mode == CHIRP_BEAM_AUTO)  // split-BF16 tensor cores where the shape fits
-    p->beam_mode = cfg->n_pix > 0 && beam_tc_tile_samples(cfg->n_ant, cfg->n_pix, cfg->dump_len, 3) == 0
+  if (p->beam_mode == CHIRP_BEAM_AUTO)  // split-BF16 tensor cores where a shape fits
+    p->beam_mode = cfg->n_pix > 0 && beam_tc_pick(cfg->n_ant, cfg->n_pix, cfg->dump_len, 3, 0) == 0
                        ? CHIRP_BEAM_VIS
                        : CHIRP_BEAM_TC_3XBF16;
   p->beam_terms = p->beam_mode == CHIRP_BEAM_TC_BF16 ? 1 : 3;
-  if (cfg->n_pix > 0 && tc_beams(p) &&
-      beam_tc_tile_samples(p->M, cfg->n_pix, cfg->dump_len, p->beam_terms) == 0) {
-    delete p;
-    return fail(CHIRP_EUNSUPPORTED,
-                "tensor-core beam tiles for %d antennas do not fit in shared memory; use "
-                "CHIRP_BEAM_VIS or CHIRP_BEAM_FP32_SIMT", cfg->n_ant);
+  if (cfg->n_pix > 0 && tc_beams(p)) {
+    p->beam_shape = beam_tc_pick(p->M, cfg->n_pix, cfg->dump_len, p->beam_terms, cfg->beam_shape);
+    if (p->beam_shape == 0) {
+      delete p;
+      return fail(CHIRP_EUNSUPPORTED,
+                  cfg->beam_shape ? "the requested tensor-core beam kernel shape does not fit this "
+                                    "search"
+                                  : "tensor-core beam tiles for these antennas do not fit in "
+                                    "shared memory; use CHIRP_BEAM_VIS or CHIRP_BEAM_FP32_SIMT");
+    }
   }
   p->in_type = cfg->in_type;
   p->stream = (cudaStream_t)stream;
@@ -592,12 +599,12 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
     for (const DmInfo& I : p->dmi)
       if (I.last >= I.first) {
         long long span = (I.last - I.first + 1) * p->L;
-        const int ts = beam_tc_tile_samples(p->M, p->n_pix, p->L, p->beam_terms);
+        const int ts = beam_tc_tile_samples(p->beam_shape);
         long long nt = (span + ts - 1) / ts;
         max_tiles = std::max(max_tiles, nt);
       }
     rc = dev_alloc(p, (void**)&p->d_bimg, (size_t)std::max(1LL, max_tiles) *
-                                              (size_t)beam_tc_tile_bytes(p->M, p->n_pix, p->L, p->beam_terms),
+                                              (size_t)beam_tc_tile_bytes(p->M, p->beam_shape, p->beam_terms),
                    "beam B image");
     if (!rc) {
       std::vector<double> Wd((size_t)p->n_pix * p->M * 2);
@@ -692,6 +699,7 @@ int chirp_plan_query(const chirp_plan* p, chirp_plan_info* info) {
   info->ifft_points = p->ifft_points;
   info->valid_samples = p->valid_samples;
   info->beam_mode = p->beam_mode;
+  info->beam_shape = p->beam_shape;
   info->fb_samples = p->T_fb;
   return CHIRP_OK;
 }
@@ -848,12 +856,12 @@ int backend_dumps(chirp_plan* p, int d, Backend be, long long m0, long long m1, 
     mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
   } else if (tc_beams(p)) {
     int mk = mark_begin(p);
-    CK(launch_split_bf16(p->d_y, p->N, p->M, p->n_pix, p->L, m0 * p->L, m1 * p->L, p->d_bimg,
+    CK(launch_split_bf16(p->d_y, p->N, p->M, p->beam_shape, m0 * p->L, m1 * p->L, p->d_bimg,
                          p->beam_terms, p->stream));
     mark_end(p, CHIRP_STAGE_SPLIT, mk);
     mk = mark_begin(p);
     CK(launch_beam_tc(p->d_bimg, p->d_aimg, p->M, p->n_pix, p->L, m0, last, out, p->d_err,
-                      p->beam_terms, p->stream));
+                      p->beam_terms, p->beam_shape, p->stream));
     mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
   } else {
     int mk = mark_begin(p);

@@ -53,6 +53,7 @@ def _cfg(**over):
     (dict(beam_mode=9), "beam_mode"),
     (dict(fft_row=300), "fft_row"),
     (dict(flags=8), "flag"),
+    (dict(beam_shape=4), "beam_shape"),
     (dict(in_type=1, in_scale=np.array([np.inf, 1.0])), "in_scale"),
 ])
 def test_plan_validation_rejects_bad_shapes(over, msg):
@@ -68,9 +69,12 @@ def test_graphs_flag_needs_a_stream():
     assert ei.value.code == -1 and "stream" in str(ei.value)
 
 
-def test_split_bf16_beams_reject_shapes_beyond_shared_memory():
+def test_forced_beam_kernel_shape_that_does_not_fit_is_refused():
+    # 64 antennas, split-BF16: the weights of one row tile and two voltage
+    # tiles exceed shared memory with 128-sample tiles (only the TMEM shape fits)
     xyz = np.zeros((64, 3))
     xyz[:, 0] = np.arange(64.0)
     with pytest.raises(chirp.ChirpError) as ei:
-        chirp.Plan(**_cfg(xyz=xyz, pix_lm=np.zeros((4, 2)), beam_mode=chirp.BEAM_TC_3XBF16))
-    assert ei.value.code == -5 and "shared memory" in str(ei.value)
+        chirp.Plan(**_cfg(xyz=xyz, pix_lm=np.zeros((4, 2)), beam_mode=chirp.BEAM_TC_3XBF16,
+                          beam_shape=1))
+    assert ei.value.code == -5 and "does not fit" in str(ei.value)

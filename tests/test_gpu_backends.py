@@ -48,17 +48,29 @@ BEAM_CASES = [
 ]
 
 
-@pytest.mark.parametrize("mode", [chirp.BEAM_FP32_SIMT, chirp.BEAM_TC_3XBF16, chirp.BEAM_VIS],
-                         ids=["fp32_simt", "tc_3xbf16", "vis"])
+# (beam mode, tensor-core kernel shape): 0 = the library's choice, 1 = 128-sample
+# tiles with the weights in shared memory, 2 = 256-sample tiles, 3 = 128-sample
+# tiles with the weights in TMEM
+MODES = [(chirp.BEAM_FP32_SIMT, 0), (chirp.BEAM_TC_3XBF16, 0), (chirp.BEAM_TC_3XBF16, 1),
+         (chirp.BEAM_TC_3XBF16, 2), (chirp.BEAM_TC_3XBF16, 3), (chirp.BEAM_VIS, 0)]
+
+
+@pytest.mark.parametrize("mode,shape", MODES,
+                         ids=["fp32_simt", "tc_3xbf16", "tc_smem128", "tc_smem256", "tc_tmem128",
+                              "vis"])
 @pytest.mark.parametrize("M,N,L,n_side,dms,nfft_min", BEAM_CASES,
                          ids=["M%d_N%d_L%d_pix%d" % (c[0], c[1], c[2], c[3] ** 2) for c in BEAM_CASES])
-def test_chimageator_matches_oracle(M, N, L, n_side, dms, nfft_min, mode, k_dm):
+def test_chimageator_matches_oracle(M, N, L, n_side, dms, nfft_min, mode, shape, k_dm):
+    if shape == 2 and L % 256:
+        pytest.skip("256-sample tiles need dump_len % 256 == 0")
     sc = skymodel.chimageator_medium(n_samp=N, n_dm=len(dms), n_ant=M, dm_max=max(dms),
                                      nfft_min=nfft_min, dump_len=L, n_side=n_side, n_pulse=1)
     sc.dms = np.array(dms)
     x = sc.voltages()
-    plan = chirp.Plan.from_scenario(sc, beam_mode=mode)
+    plan = chirp.Plan.from_scenario(sc, beam_mode=mode, beam_shape=shape)
     assert plan.info["beam_mode"] == mode
+    if mode == chirp.BEAM_TC_3XBF16:
+        assert plan.info["beam_shape"] == (shape or (2 if L % 256 == 0 else 1))
     P = torch.empty((len(dms), plan.n_dump, plan.n_pix), dtype=torch.float32, device="cuda")
     plan.chimageator(torch.from_numpy(x).cuda(), P)
     Pg = P.cpu().numpy()
