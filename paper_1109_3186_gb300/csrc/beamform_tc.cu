@@ -275,8 +275,7 @@ __global__ void __launch_bounds__(BeamCfg<NT, AT>::THREADS, 1) k_beam_tc(BeamArg
           if (r < R_eff) {
             const uint64_t a_desc = a_desc0 + (uint64_t)((r * a_tile_bytes) >> 4);
             const uint32_t a_col = tmem + Cfg::A_COL + (uint32_t)(r * ksteps * 8);
-#pragma unroll 4
-            for (int ks = 0; ks < ksteps; ks++) {
+            auto issue = [&](int ks) {
               const int p0 = 2 * ks;
               const int bg = p0 < bwrap ? p0 : p0 - bwrap;
               const uint64_t bd = b_desc + (uint64_t)(bg * 8);
@@ -284,6 +283,16 @@ __global__ void __launch_bounds__(BeamCfg<NT, AT>::THREADS, 1) k_beam_tc(BeamArg
                 tc::mma_bf16_ts(d, a_col + (uint32_t)(ks * 8), bd, IDESC, ks > 0 ? 1u : 0u);
               else
                 tc::mma_bf16(d, a_desc + (uint64_t)(ks * 16), bd, IDESC, ks > 0 ? 1u : 0u);
+            };
+            // straight-line issue for the common K-step counts (12 antennas:
+            // 5 split-BF16, 2 plain BF16 ... ), a loop otherwise
+            switch (ksteps) {
+              case 2: issue(0); issue(1); break;
+              case 3: issue(0); issue(1); issue(2); break;
+              case 5: issue(0); issue(1); issue(2); issue(3); issue(4); break;
+              case 6: issue(0); issue(1); issue(2); issue(3); issue(4); issue(5); break;
+              default:
+                for (int ks = 0; ks < ksteps; ks++) issue(ks);
             }
           }
           tc::mma_commit(&accf[acc]);
