@@ -258,10 +258,14 @@ def stage_roofline(sc, plan, stage_ms, peaks, peak_kind, beam_mode, steps):
         g_bytes += 8 * lay["nfft"]
         y_bytes += 8 * M * max(0, N - lay["n_hi"] - lay["n_lo"])
     fwd_pts = sum(groups.values())
-    n_dump_valid = int(np.sum(np.maximum(0, last - first + 1)))
     hbm = peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
     sm_max = peaks.get("sm_max_mhz", FALLBACK_PEAKS["sm_max_mhz"])
     fp32_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    n_dump_valid = int(np.sum(np.maximum(0, last - first + 1)))
+    if beam_mode in (2, 4):
+        # the inverse column pass writes the BF16 image of the valid dumps
+        # (head + tail, or head only: 8 or 4 B per antenna-sample) instead of y
+        y_bytes = float(n_dump_valid) * L * M * (8 if beam_mode == 2 else 4)
     stages = {
         "forward": ("hbm", 32.0 * fwd_pts, hbm, "GB/s"),
         "chirp": ("hbm", 2.0 * g_bytes, hbm, "GB/s"),
@@ -269,9 +273,6 @@ def stage_roofline(sc, plan, stage_ms, peaks, peak_kind, beam_mode, steps):
         "inv_cols": ("hbm", 8.0 * inv_pts + y_bytes, hbm, "GB/s"),
     }
     beam_flops = float(n_dump_valid) * L * n_pix * (8 * M + 3)
-    # split: read M complex64 + write the BF16 head/tail image (4 antennas per 16 B row pair)
-    split_bytes = float(n_dump_valid) * L * (8 * M + 32 * ((M + 3) // 4))
-    stages["split"] = ("hbm", split_bytes, hbm, "GB/s")
     n_pair = M * (M + 1) // 2
     # correlate: read the dedispersed voltages of every valid dump, write V
     stages["correlate"] = ("hbm", float(n_dump_valid) * (L * 8 * M + 8 * n_pair), hbm, "GB/s")

@@ -261,7 +261,8 @@ int chirp_propose_windows(const float* logits, int n_dm, long long n_time, int w
 #define CHIRP_STAGE_INV_COLS 2  /* inverse column pass + discard, per DM        */
 #define CHIRP_STAGE_CORRELATE 3 /* Chirpolator back-end, per DM                 */
 #define CHIRP_STAGE_BEAMFORM 4  /* Chimageator back-end, per DM                 */
-#define CHIRP_STAGE_SPLIT 5     /* BF16 head/tail split of the voltages, per DM */
+#define CHIRP_STAGE_SPLIT 5     /* not timed: the BF16 image of the voltages is
+                                   written by the inverse column pass        */
 #define CHIRP_STAGE_CHIRP 6     /* FP64-phase chirp table H_DM, per DM           */
 #define CHIRP_STAGE_INCOHERENT 7 /* filterbank + incoherent dedispersion        */
 #define CHIRP_STAGE_DETECT 8    /* candidate detection (chirp_detect)            */

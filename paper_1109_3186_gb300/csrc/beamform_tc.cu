@@ -513,51 +513,6 @@ __global__ void __launch_bounds__(BeamCfg<NT, AT>::THREADS, 1) k_beam_tc(BeamArg
   }
 }
 
-// y [n_ant][n_samp] complex64 -> B image tiles: BF16 heads and (three
-// terms) tails, or (one term) heads and a zero padding group when G is odd.
-// Thread (u, j): sample t = t_begin + u, real-K group j (antennas 4j..4j+3).
-__global__ void k_split_bf16(const float2* __restrict__ y, long long n_samp, int M, int G, int GB,
-                             int terms, long long t_begin, long long t_end, long long n_tiles,
-                             int NT, uint8_t* __restrict__ b_img) {
-  const long long U = n_tiles * NT;
-  const long long total = U * G;
-  const size_t tile_bytes = b_tile_bytes_of(NT, GB);
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(idx / U);
-    const long long u = idx % U;
-    const long long t = t_begin + u;
-    float v[8];
-#pragma unroll
-    for (int e = 0; e < 4; e++) {
-      const int a = 4 * j + e;
-      float2 s = make_float2(0.f, 0.f);
-      if (a < M && t < t_end) s = y[(long long)a * n_samp + t];
-      v[2 * e] = s.x;
-      v[2 * e + 1] = s.y;
-    }
-    uint32_t hi[4], lo[4];
-#pragma unroll
-    for (int e = 0; e < 4; e++) {
-      __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-      float2 hf = __bfloat1622float2(h);
-      __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
-      hi[e] = *reinterpret_cast<uint32_t*>(&h);
-      lo[e] = *reinterpret_cast<uint32_t*>(&l);
-    }
-    const long long tile = u / NT;
-    const int n = (int)(u % NT);
-    uint8_t* base = b_img + (size_t)tile * tile_bytes + (size_t)(n / 8) * (GB * 128) +
-                    (size_t)(n % 8) * 16;
-    *reinterpret_cast<uint4*>(base + (size_t)j * 128) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-    if (terms == 3)
-      *reinterpret_cast<uint4*>(base + (size_t)(G + j) * 128) =
-          make_uint4(lo[0], lo[1], lo[2], lo[3]);
-    else if (j == G - 1 && GB > G)
-      *reinterpret_cast<uint4*>(base + (size_t)G * 128) = make_uint4(0u, 0u, 0u, 0u);
-  }
-}
-
 uint16_t bf16_bits_rn(float f) {
   uint32_t u;
   memcpy(&u, &f, 4);
@@ -681,28 +636,13 @@ long long beam_tc_tile_bytes(int n_ant, int shape, int terms) {
 }
 
 
-cudaError_t launch_split_bf16(const float2* y, long long n_samp, int n_ant, int shape,
-                              long long t_begin, long long t_end, uint8_t* b_img, int terms,
-                              cudaStream_t st) {
-  if (t_end <= t_begin) return cudaSuccess;
-  const int G = beam_tc_groups(n_ant), GB = beam_tc_bgroups(n_ant, terms);
-  const int NT = beam_tc_tile_samples(shape);
-  if (NT == 0) return cudaErrorInvalidConfiguration;
-  const long long n_tiles = (t_end - t_begin + NT - 1) / NT;
-  const long long total = n_tiles * NT * G;
-  long long blocks = (total + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  k_split_bf16<<<(unsigned)blocks, 256, 0, st>>>(y, n_samp, n_ant, G, GB, terms, t_begin, t_end,
-                                                 n_tiles, NT, b_img);
-  return cudaGetLastError();
-}
-
 namespace {
 
 template <int NT, bool AT>
 static cudaError_t launch_beam_tc_nt(const uint8_t* b_img, const uint8_t* a_img, int n_ant,
                                      int n_pix, int dump_len, long long first, long long last,
-                                     float* pow, int* err, int terms, cudaStream_t st) {
+                                     long long t_origin, float* pow, int* err, int terms,
+                                     cudaStream_t st) {
   using Cfg = BeamCfg<NT, AT>;
   const int ks = beam_tc_ksteps(n_ant, terms), G = beam_tc_bgroups(n_ant, terms);
   const int n_rowtiles = (2 * n_pix + 127) / 128;
@@ -725,7 +665,7 @@ static cudaError_t launch_beam_tc_nt(const uint8_t* b_img, const uint8_t* a_img,
   a.a_img = a_img;
   a.pow = pow;
   a.err = err;
-  a.t_begin = first * dump_len;
+  a.t_begin = t_origin;
   a.first = first;
   a.n_dumps = n_dumps;
   a.dumps_per_cta = (n_dumps + gy - 1) / gy;
@@ -745,19 +685,21 @@ static cudaError_t launch_beam_tc_nt(const uint8_t* b_img, const uint8_t* a_img,
 }  // namespace
 
 cudaError_t launch_beam_tc(const uint8_t* b_img, const uint8_t* a_img, int n_ant, int n_pix,
-                           int dump_len, long long first, long long last, float* pow, int* err,
-                           int terms, int shape, cudaStream_t st) {
+                           int dump_len, long long first, long long last, long long t_origin,
+                           float* pow, int* err, int terms, int shape, cudaStream_t st) {
   if (last < first) return cudaSuccess;
+  if (t_origin > first * dump_len) return cudaErrorInvalidValue;
+  if (shape == 2 && (first * dump_len - t_origin) % 256) return cudaErrorInvalidValue;
   switch (shape) {
     case 3:
-      return launch_beam_tc_nt<128, true>(b_img, a_img, n_ant, n_pix, dump_len, first, last, pow,
-                                          err, terms, st);
+      return launch_beam_tc_nt<128, true>(b_img, a_img, n_ant, n_pix, dump_len, first, last,
+                                          t_origin, pow, err, terms, st);
     case 2:
       return launch_beam_tc_nt<256, false>(b_img, a_img, n_ant, n_pix, dump_len, first, last,
-                                           pow, err, terms, st);
+                                           t_origin, pow, err, terms, st);
     case 1:
       return launch_beam_tc_nt<128, false>(b_img, a_img, n_ant, n_pix, dump_len, first, last,
-                                           pow, err, terms, st);
+                                           t_origin, pow, err, terms, st);
     default:
       return cudaErrorInvalidConfiguration;
   }

@@ -18,6 +18,7 @@
 // the DM-independent table G = k_dm f^2/(f0^2 (f0+f)) is built in FP64, the
 // per-DM phase c = DM G is formed and range-reduced (c - rint c) in FP64, and
 // only the reduced fraction is converted to FP32 for sincospif.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "fft.cuh"
@@ -167,14 +168,18 @@ __global__ void __launch_bounds__(256, 4) k_inv_rows(const float2* __restrict__ 
 
 // Column pass of the inverse: natural-order output, 1/Nfft, overlap-save
 // discard and ownership.  Block b owns block positions [lo_b, hi_b).
-template <int L>
+// IMG: instead of y, the owned samples inside [img.t0, img.t1) are written
+// as the beamformer's BF16 head (and tail) image: one 4-byte (re, im) pair
+// per antenna and sample and term, the head rounded to nearest BF16 and the
+// tail the rounded remainder.
+template <int L, bool IMG>
 __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ Z,
                                                   float2* __restrict__ y, long long n_samp,
                                                   int n2, long long step, long long n_blk,
                                                   int n_ant, long long n_hi, long long n_lo,
                                                   long long n_hi_max, long long q0,
                                                   const int* __restrict__ blk_list,
-                                                  TwiddlePtrs twp) {
+                                                  TwiddlePtrs twp, BeamImageOut img) {
   constexpr int C = 4096 / L;
   constexpr int T = L / 16;
   __shared__ float2 sm[FftTile<L, C>::SLOTS];
@@ -197,11 +202,37 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ 
   const long long lo_b = (b == 0) ? n_hi : n_hi_max;
   const long long hi_b = (b == n_blk - 1) ? (n_samp - n_lo - base) : (n_hi_max + step);
   const float scale = 1.0f / (float)nfft;  // exact: power of two
-  float2* ya = y + a * n_samp;
+  if constexpr (IMG) {
+    const long long nt_mask = (1LL << img.log2_nt) - 1;
+    const size_t grp_bytes = (size_t)img.GB * 128;
+    const size_t tile_bytes = ((size_t)1 << img.log2_nt) / 8 * grp_bytes;
+    uint8_t* img_a = img.img + (size_t)(a >> 2) * 128 + (size_t)(a & 3) * 4;
 #pragma unroll
-  for (int k = 0; k < 16; k++) {
-    long long n = (long long)(jt + k * T) * n2 + c;
-    if (n >= lo_b && n < hi_b) ya[base + n] = cscale(v[k], scale);
+    for (int k = 0; k < 16; k++) {
+      const long long n = (long long)(jt + k * T) * n2 + c;
+      const long long t = base + n;
+      if (n >= lo_b && n < hi_b && t >= img.t0 && t < img.t1) {
+        const long long u = t - img.t0;
+        const long long nn = u & nt_mask;
+        const float2 val = cscale(v[k], scale);
+        const __nv_bfloat162 h = __floats2bfloat162_rn(val.x, val.y);
+        uint8_t* dst = img_a + (size_t)(u >> img.log2_nt) * tile_bytes +
+                       (size_t)(nn >> 3) * grp_bytes + (size_t)(nn & 7) * 16;
+        *reinterpret_cast<__nv_bfloat162*>(dst) = h;
+        if (img.terms == 3) {
+          const float2 hf = __bfloat1622float2(h);
+          *reinterpret_cast<__nv_bfloat162*>(dst + (size_t)img.G * 128) =
+              __floats2bfloat162_rn(val.x - hf.x, val.y - hf.y);
+        }
+      }
+    }
+  } else {
+    float2* ya = y + a * n_samp;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      long long n = (long long)(jt + k * T) * n2 + c;
+      if (n >= lo_b && n < hi_b) ya[base + n] = cscale(v[k], scale);
+    }
   }
 }
 
@@ -278,13 +309,21 @@ cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, 
 cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, int n_ant,
                                 long long q0, long long nq, const GroupGeom& g, long long n_hi,
                                 long long n_lo, TwiddlePtrs tw, cudaStream_t st,
-                                const int* blk_list) {
+                                const int* blk_list, const BeamImageOut* img) {
   if (nq > 65535 || nq < 1) return cudaErrorInvalidConfiguration;
   const int C = 4096 / g.n1;
   dim3 grid((g.n2 + C - 1) / C, (unsigned)nq);
+  const BeamImageOut io = img ? *img : BeamImageOut{nullptr, 0, 0, 0, 0, 0, 0};
   switch (g.n1) {
-#define X(L) \
-  case L: k_inv_cols<L><<<grid, 256, 0, st>>>(Z, y, n_samp, g.n2, g.step, g.n_blk, n_ant, n_hi, n_lo, g.n_hi_max, q0, blk_list, tw); break;
+#define X(L)                                                                                    \
+  case L:                                                                                       \
+    if (img)                                                                                    \
+      k_inv_cols<L, true><<<grid, 256, 0, st>>>(Z, y, n_samp, g.n2, g.step, g.n_blk, n_ant,     \
+                                                n_hi, n_lo, g.n_hi_max, q0, blk_list, tw, io);  \
+    else                                                                                        \
+      k_inv_cols<L, false><<<grid, 256, 0, st>>>(Z, y, n_samp, g.n2, g.step, g.n_blk, n_ant,    \
+                                                 n_hi, n_lo, g.n_hi_max, q0, blk_list, tw, io); \
+    break;
     CHIRP_SIZES(X)
 #undef X
     default: return cudaErrorInvalidValue;

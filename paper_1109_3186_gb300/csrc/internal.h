@@ -59,11 +59,21 @@ long long inverse_chunk_sequences(const GroupGeom& g, long long n_seq);
 cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, long long q0,
                                 long long nq, const GroupGeom& g, TwiddlePtrs tw,
                                 cudaStream_t st, const int* blk_list = nullptr, int n_ant = 1);
+// The tensor-core beamformer's B image, written directly by the inverse
+// column pass (instead of y) when a Chimageator search runs in a tensor-core
+// mode: sample t in [t0, t1) of antenna a goes to tile (t - t0) >> log2_nt,
+// as BF16 head (and, for three terms, tail) in the layout of beamform_tc.cu.
+struct BeamImageOut {
+  uint8_t* img;
+  long long t0, t1;
+  int log2_nt;
+  int G, GB, terms;
+};
 // y[a][t] = dedispersed voltage for every owned, valid t of sequences q0.. (other t untouched)
 cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, int n_ant,
                                 long long q0, long long nq, const GroupGeom& g, long long n_hi,
                                 long long n_lo, TwiddlePtrs tw, cudaStream_t st,
-                                const int* blk_list = nullptr);
+                                const int* blk_list = nullptr, const BeamImageOut* img = nullptr);
 
 // ---- back-ends (backends.cu) ----
 // dumps m_base .. m_base + n_m - 1, or dump_list[0 .. n_m) when dump_list is a
@@ -102,12 +112,10 @@ int beam_tc_pick(int n_ant, int n_pix, int dump_len, int terms, int forced);
 int beam_tc_tile_samples(int shape);                          // samples per B tile
 long long beam_tc_tile_bytes(int n_ant, int shape, int terms);  // bytes of one B tile
 std::vector<uint8_t> build_beam_a_image(const double* W, int n_ant, int n_pix, int terms);
-cudaError_t launch_split_bf16(const float2* y, long long n_samp, int n_ant, int shape,
-                              long long t_begin, long long t_end, uint8_t* b_img, int terms,
-                              cudaStream_t st);
+// t_origin: sample of column 0 of B tile 0 (dump-aligned for 256-sample tiles)
 cudaError_t launch_beam_tc(const uint8_t* b_img, const uint8_t* a_img, int n_ant, int n_pix,
-                           int dump_len, long long first, long long last, float* pow, int* err,
-                           int terms, int shape, cudaStream_t st);
+                           int dump_len, long long first, long long last, long long t_origin,
+                           float* pow, int* err, int terms, int shape, cudaStream_t st);
 
 // ---- candidate detection (detect.cu) ----
 long long detect_chunks(int n_dm, long long n_dump, int n_pix);  // entries of counts / offsets

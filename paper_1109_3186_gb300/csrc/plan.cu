@@ -109,6 +109,7 @@ struct chirp_plan {
   float2* d_W = nullptr;     // beam weights [n_pix][M]
   uint8_t* d_aimg = nullptr; // tensor-core A image (split-BF16 weights)
   uint8_t* d_bimg = nullptr; // tensor-core B image of one DM (split-BF16 voltages)
+  size_t bimg_bytes = 0;
   int* d_err = nullptr;      // device status word (bounded waits that timed out)
   float2* d_V = nullptr;     // visibilities of one DM [n_dump][n_pair] (beam mode VIS)
   float2* d_wpair = nullptr; // pair weights [n_pair][n_pix] (beam mode VIS)
@@ -603,9 +604,9 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
         long long nt = (span + ts - 1) / ts;
         max_tiles = std::max(max_tiles, nt);
       }
-    rc = dev_alloc(p, (void**)&p->d_bimg, (size_t)std::max(1LL, max_tiles) *
-                                              (size_t)beam_tc_tile_bytes(p->M, p->beam_shape, p->beam_terms),
-                   "beam B image");
+    p->bimg_bytes = (size_t)std::max(1LL, max_tiles) *
+                    (size_t)beam_tc_tile_bytes(p->M, p->beam_shape, p->beam_terms);
+    rc = dev_alloc(p, (void**)&p->d_bimg, p->bimg_bytes, "beam B image");
     if (!rc) {
       std::vector<double> Wd((size_t)p->n_pix * p->M * 2);
       for (int q = 0; q < p->n_pix; q++) {
@@ -660,6 +661,9 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   if (e == cudaSuccess && !aimg.empty())
     e = cudaMemcpyAsync(p->d_aimg, aimg.data(), aimg.size(), cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
+  // the B image slots of absent antennas (n_ant % 4) and of the padding
+  // k-group are never written and must read as zeros
+  if (e == cudaSuccess && p->d_bimg) e = cudaMemsetAsync(p->d_bimg, 0, p->bimg_bytes, p->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(p->d_first_last, first_last.data(), first_last.size() * sizeof(long long),
                         cudaMemcpyHostToDevice, p->stream);
@@ -791,7 +795,8 @@ int forward_all(chirp_plan* p, const void* dx) {
 }
 
 // Dedisperse DM d over the blocks [b0, b1) of its group (all antennas).
-int dedisperse_blocks(chirp_plan* p, int d, float2* y, long long b0, long long b1) {
+int dedisperse_blocks(chirp_plan* p, int d, float2* y, long long b0, long long b1,
+                      const BeamImageOut* img = nullptr) {
   const DmInfo& I = p->dmi[d];
   Group& g = p->groups[I.group];
   const long long q_end = b1 * p->M;
@@ -803,7 +808,7 @@ int dedisperse_blocks(chirp_plan* p, int d, float2* y, long long b0, long long b
     mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
     mk = mark_begin(p);
     CK(launch_inverse_cols(p->d_Z, y, p->N, p->M, q0, n, g.geom, I.n_hi, I.n_lo, p->tw(),
-                           p->stream));
+                           p->stream, nullptr, img));
     mark_end(p, CHIRP_STAGE_INV_COLS, mk);
   }
   return CHIRP_OK;
@@ -834,7 +839,29 @@ long long owner_block(const GroupGeom& G, long long t) {
 
 enum Backend { kCorrelate, kBeams };
 
+// A Chimageator search in a tensor-core mode has the inverse column pass
+// write the beamformer's BF16 image of DM d's valid dumps directly.
+bool fused_image(const chirp_plan* p, Backend be) { return be == kBeams && tc_beams(p); }
+
+BeamImageOut beam_image_for(const chirp_plan* p, int d) {
+  const DmInfo& I = p->dmi[d];
+  const int nt = beam_tc_tile_samples(p->beam_shape);
+  int log2_nt = 0;
+  while ((1 << log2_nt) < nt) log2_nt++;
+  BeamImageOut o;
+  o.img = p->d_bimg;
+  o.t0 = I.first * p->L;
+  o.t1 = (I.last + 1) * p->L;
+  o.log2_nt = log2_nt;
+  o.G = beam_tc_groups(p->M);
+  o.GB = beam_tc_bgroups(p->M, p->beam_terms);
+  o.terms = p->beam_terms;
+  return o;
+}
+
 // Back-end of DM d over its valid dumps [m0, m1) (inside [first, last]).
+// The tensor-core modes read the image the inverse column pass wrote, whose
+// tiles count from the DM's first valid dump.
 int backend_dumps(chirp_plan* p, int d, Backend be, long long m0, long long m1, void* dout) {
   if (m1 <= m0) return CHIRP_OK;
   const long long last = m1 - 1;
@@ -855,13 +882,10 @@ int backend_dumps(chirp_plan* p, int d, Backend be, long long m0, long long m1, 
     CK(launch_beam_from_vis(p->d_V, p->d_wpair, p->M, p->n_pix, m0, last, out, p->stream));
     mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
   } else if (tc_beams(p)) {
+    const long long origin = p->dmi[d].first * p->L;
     int mk = mark_begin(p);
-    CK(launch_split_bf16(p->d_y, p->N, p->M, p->beam_shape, m0 * p->L, m1 * p->L, p->d_bimg,
-                         p->beam_terms, p->stream));
-    mark_end(p, CHIRP_STAGE_SPLIT, mk);
-    mk = mark_begin(p);
-    CK(launch_beam_tc(p->d_bimg, p->d_aimg, p->M, p->n_pix, p->L, m0, last, out, p->d_err,
-                      p->beam_terms, p->beam_shape, p->stream));
+    CK(launch_beam_tc(p->d_bimg, p->d_aimg, p->M, p->n_pix, p->L, m0, last, origin, out,
+                      p->d_err, p->beam_terms, p->beam_shape, p->stream));
     mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
   } else {
     int mk = mark_begin(p);
@@ -929,7 +953,8 @@ int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Bac
     rc = chirp_for(p, d);
     if (rc) return rc;
     if (!mask) {
-      rc = dedisperse_blocks(p, d, p->d_y, 0, G.n_blk);
+      const BeamImageOut img = fused_image(p, be) ? beam_image_for(p, d) : BeamImageOut{};
+      rc = dedisperse_blocks(p, d, p->d_y, 0, G.n_blk, fused_image(p, be) ? &img : nullptr);
       if (!rc) rc = backend_dumps(p, d, be, I.first, I.last + 1, dout);
       if (rc) return rc;
       continue;
@@ -942,8 +967,9 @@ int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Bac
                            blist, p->M));
     mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
     mk = mark_begin(p);
+    const BeamImageOut img = fused_image(p, be) ? beam_image_for(p, d) : BeamImageOut{};
     CK(launch_inverse_cols(p->d_Z, p->d_y, p->N, p->M, 0, blk_n[d] * p->M, G, I.n_hi, I.n_lo,
-                           p->tw(), p->stream, blist));
+                           p->tw(), p->stream, blist, fused_image(p, be) ? &img : nullptr));
     mark_end(p, CHIRP_STAGE_INV_COLS, mk);
     if (be == kCorrelate || p->beam_mode == CHIRP_BEAM_VIS) {
       float2* vout = be == kCorrelate ? (float2*)dout + (size_t)d * p->n_dump * p->n_pair : p->d_V;
