@@ -576,10 +576,13 @@ int beam_tc_ksteps(int n_ant, int terms) {
   const int G = beam_tc_groups(n_ant);
   return terms == 3 ? (3 * G + 1) / 2 : (G + 1) / 2;
 }
+// Largest dynamic shared memory one CTA may request on sm_103 (227 KB).
+constexpr uint32_t kSmemLimit = 227u * 1024u;
+
 // Row tiles per CTA and B ring depth for a tile shape.  All CTA columns of
 // a launch walk the same B tiles, so the column with the most row tiles sets
 // the time: take the fewest columns that the largest fitting R allows (R
-// fitting in 220 KB of shared memory with a 2-stage ring, and for AT its
+// fitting in 227 KB of shared memory with a 2-stage ring, and for AT its
 // weights in the 256 TMEM columns beside the accumulators), spread the row
 // tiles evenly over them, then use the deepest ring that still fits.  False
 // when not even one row tile fits.
@@ -587,7 +590,7 @@ template <int NT, bool AT>
 static bool beam_tc_shape(int ks, int GB, int n_rowtiles, int* R_out, int* nst_out) {
   auto fits = [&](int R, int nst) {
     if (AT && R * ks * 8 > 512 - (int)BeamCfg<NT, AT>::A_COL) return false;
-    return beam_smem_plan<NT, AT>(R, ks, GB, nst).total <= 220u * 1024u;
+    return beam_smem_plan<NT, AT>(R, ks, GB, nst).total <= kSmemLimit;
   };
   int rmax = 0;
   for (int R = RMAX < n_rowtiles ? RMAX : n_rowtiles; R >= 1 && !rmax; R--)
