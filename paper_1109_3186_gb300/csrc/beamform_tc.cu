@@ -77,6 +77,14 @@ __host__ __device__ constexpr uint32_t b_tile_bytes_of(int NT, int GB) {
 //    releasing it right after the load; the four partial sums of a row are
 //    combined in shared memory once per dump.  The wider MMA halves the
 //    shared-memory operand traffic per flop.
+// MMA-issuing warps.  One thread can only issue so fast (each tcgen05.mma
+// of a 128 x 256 x 16 tile, its descriptors, the per-row-tile barrier wait
+// and commit); two warps, each owning the accumulators of one row-tile
+// parity, keep the tensor pipe fed.
+#ifndef CHIRP_BEAM_ISSUERS
+#define CHIRP_BEAM_ISSUERS 2
+#endif
+
 template <int NT, bool AT = false>
 struct BeamCfg {
   static_assert(!AT || NT == 128, "A in TMEM is used with 128-sample tiles");
@@ -84,10 +92,33 @@ struct BeamCfg {
   static constexpr uint32_t A_COL = 256;          // AT: first TMEM column of the weights
   static constexpr int NSTAGE = NT == 256 ? 3 : 4;  // B ring depth (fewer when smem is short)
   static constexpr int EPI_WARPS = NT == 256 ? 16 : 8;
-  static constexpr int THREADS = 64 + 32 * EPI_WARPS;
+  static constexpr int ISSUERS = CHIRP_BEAM_ISSUERS;     // MMA-issuing warps
+  static constexpr int EPI0 = 1 + ISSUERS;               // first epilogue warp
+  static constexpr int THREADS = 32 * (EPI0 + EPI_WARPS);
   static constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, NT);
   static constexpr uint32_t RED_BYTES = NT == 256 ? 4u * RMAX * 128u * 4u : 0u;
 };
+
+// Sum of squares of 64 values with paired FP32 FMAs (fma.rn.f32x2: two
+// lanes per instruction), halving the epilogue's instruction count; four
+// independent pair accumulators.
+__device__ __forceinline__ float sumsq64(const float (&v)[64]) {
+  unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};
+#pragma unroll
+  for (int e = 0; e < 32; e++) {
+    unsigned long long x;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(v[2 * e]), "f"(v[2 * e + 1]));
+    asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(acc[e & 3]) : "l"(x));
+  }
+  float t = 0.f;
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(acc[j]));
+    t += lo + hi;
+  }
+  return t;
+}
 
 struct BeamSmemPlan {
   uint32_t a_bytes, b_stage_bytes, red_off, bar_off, total;
@@ -163,14 +194,14 @@ __global__ void __launch_bounds__(BeamCfg<NT, AT>::THREADS, 1) k_beam_tc(BeamArg
   if (threadIdx.x == 0) {
     for (int s = 0; s < nst; s++) {
       tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], 1);
+      tc::mbar_init(&empty[s], Cfg::ISSUERS);  // every issuer commits once per tile
     }
     for (int a = 0; a < NACC; a++) {
       tc::mbar_init(&accf[a], 1);
       tc::mbar_init(&acce[a], NT == 256 ? 16 : 4);  // every draining warp arrives once
     }
     tc::mbar_init(abar, 1);
-    tc::mbar_init(drain, 1);
+    tc::mbar_init(drain, Cfg::ISSUERS);
     *abort_flag = 0;
     tc::fence_mbar_init();
   }
@@ -182,8 +213,8 @@ __global__ void __launch_bounds__(BeamCfg<NT, AT>::THREADS, 1) k_beam_tc(BeamArg
   if constexpr (AT) {
     // weights into TMEM: warpgroup wg copies the row tiles of its parity;
     // thread (quarter q, lane) holds row 32 q + lane of the tile
-    if (warp >= 2 && n_tiles > 0) {
-      const int wg = (warp - 2) / 4, q = warp & 3, row = 32 * q + lane;
+    if (warp >= Cfg::EPI0 && n_tiles > 0) {
+      const int wg = (warp - Cfg::EPI0) / 4, q = warp & 3, row = 32 * q + lane;
       const int mg = row / 8, r8 = row % 8;
       for (int r = wg; r < R_eff; r += 2) {
         const uint8_t* src = args.a_img + (size_t)(rt0 + r) * a_tile_bytes +
@@ -242,19 +273,19 @@ __global__ void __launch_bounds__(BeamCfg<NT, AT>::THREADS, 1) k_beam_tc(BeamArg
         for (long long i = issued > nst ? issued - nst : 0; i < issued; i++)
           tc::mbar_wait(&full[i % nst], (uint32_t)((i / nst) & 1), nullptr, 1u << 22);
       }
-    } else if (warp == 1 && lane == 0) {
-      // ------------------------------------------------------ MMA issuer
-      // Descriptors are formed once and advanced by adding the start-address
-      // offset (bytes / 16) of each K step, stage and row tile: the issue
-      // loop of this single thread is what feeds the tensor pipe.
+    } else if (warp >= 1 && warp <= Cfg::ISSUERS && lane == 0) {
+      // ------------------------------------------------------ MMA issuers
+      // Issuer `me` takes the row tiles r = me, me + ISSUERS, ... (and with
+      // them the accumulators of that parity).  Descriptors are formed once
+      // and advanced by adding the start-address offset (bytes / 16) of each
+      // K step, stage and row tile.
+      const int me = warp - 1;
       const uint32_t a_sbo = 2u * args.ksteps * 128u, b_sbo = (uint32_t)args.GB * 128u;
       const uint64_t a_desc0 = tc::sdesc(tc::smem_u32(smA), 128u, a_sbo);
       const uint64_t b_desc0 = tc::sdesc(tc::smem_u32(smB), 128u, b_sbo);
       const int ksteps = args.ksteps, bwrap = args.bwrap;
       bool ok = AT ? true : tc::mbar_wait(abar, 0, abort_flag);
       if (!ok) raise();
-      int acc = 0;
-      uint32_t aph = 0;
       int s = 0;
       uint32_t ph = 0;
       for (long long i = 0; ok && i < n_tiles; i++) {
@@ -264,7 +295,10 @@ __global__ void __launch_bounds__(BeamCfg<NT, AT>::THREADS, 1) k_beam_tc(BeamArg
         }
         tc::fence_after();
         const uint64_t b_desc = b_desc0 + (uint64_t)((s * sp.b_stage_bytes) >> 4);
-        for (int r = 0; r < R_pipe; r++) {
+        for (int r = me; r < R_pipe; r += Cfg::ISSUERS) {
+          const unsigned long long u = (unsigned long long)(i * R_pipe + r);
+          const int acc = (int)(u % NACC);
+          const uint32_t aph = (uint32_t)((u / NACC) & 1);
           if (!tc::mbar_wait(&acce[acc], aph ^ 1, abort_flag)) {
             raise();
             ok = false;
@@ -296,10 +330,6 @@ __global__ void __launch_bounds__(BeamCfg<NT, AT>::THREADS, 1) k_beam_tc(BeamArg
             }
           }
           tc::mma_commit(&accf[acc]);
-          if (++acc == NACC) {
-            acc = 0;
-            aph ^= 1u;
-          }
         }
         if (!ok) break;
         tc::mma_commit(&empty[s]);
@@ -311,12 +341,12 @@ __global__ void __launch_bounds__(BeamCfg<NT, AT>::THREADS, 1) k_beam_tc(BeamArg
       // nothing may be in flight when TMEM is released
       tc::mma_commit(drain);
       tc::mbar_wait(drain, 0, nullptr, 1u << 22);
-    } else if (warp >= 2) {
+    } else if (warp >= Cfg::EPI0) {
       if constexpr (NT == 256) {
         // ---------------------------------------------------- epilogue, 4 slices
         // Dumps start on tile boundaries (L % 256 == 0 and the CTA's range is
         // dump-aligned), so a dump ends only at the end of a tile.
-        const int g = (warp - 2) / 4;        // column slice [64 g, 64 g + 64)
+        const int g = (warp - Cfg::EPI0) / 4;  // column slice [64 g, 64 g + 64)
         const int q = warp & 3;              // TMEM lane quarter of this warp
         const int row = 32 * q + lane;
         float sum[RMAX];
@@ -351,15 +381,7 @@ __global__ void __launch_bounds__(BeamCfg<NT, AT>::THREADS, 1) k_beam_tc(BeamArg
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&acce[acc]);
             if (use) {
-              float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-#pragma unroll
-              for (int e = 0; e < 16; e++) {
-                p0 = fmaf(v[e], v[e], p0);
-                p1 = fmaf(v[16 + e], v[16 + e], p1);
-                p2 = fmaf(v[32 + e], v[32 + e], p2);
-                p3 = fmaf(v[48 + e], v[48 + e], p3);
-              }
-              sum[r] += (p0 + p1) + (p2 + p3);
+              sum[r] += sumsq64(v);
             }
             if (++acc == NACC) {
               acc = 0;
@@ -404,7 +426,7 @@ __global__ void __launch_bounds__(BeamCfg<NT, AT>::THREADS, 1) k_beam_tc(BeamArg
       // warpgroup wg drains row tiles r = wg, wg + 2, ...; rr = r / 2 indexes
       // its per-row running dump sums.  All row tiles of a B tile cover the
       // same samples, so the dump boundary state (next_b) is per warpgroup.
-      const int wg = (warp - 2) / 4;
+      const int wg = (warp - Cfg::EPI0) / 4;
       const int q = warp & 3;              // TMEM lane quarter of this warp
       const int row = 32 * q + lane;       // row inside a 128-row tile
       constexpr int RH = RMAX / 2;
@@ -451,15 +473,7 @@ __global__ void __launch_bounds__(BeamCfg<NT, AT>::THREADS, 1) k_beam_tc(BeamArg
             for (int h = 0; h < NT / 64; h++) {
               float v[64];
               tc::tmem_ld64(tbase + 64 * h, v);
-              float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-#pragma unroll
-              for (int e = 0; e < 16; e++) {
-                p0 = fmaf(v[e], v[e], p0);
-                p1 = fmaf(v[16 + e], v[16 + e], p1);
-                p2 = fmaf(v[32 + e], v[32 + e], p2);
-                p3 = fmaf(v[48 + e], v[48 + e], p3);
-              }
-              part += (p0 + p1) + (p2 + p3);
+              part += sumsq64(v);
             }
             tc::fence_before();
             __syncwarp();
