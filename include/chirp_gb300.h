@@ -73,6 +73,20 @@ extern "C" {
                                   accumulate; relative error of a beam power
                                   ~1e-3 (held to 1e-2)                        */
 
+/* contraction used by the Chirpolator back-end (and by CHIRP_BEAM_VIS) */
+#define CHIRP_CORR_AUTO 0      /* CHIRP_CORR_TC_3XBF16 from 12 antennas up where
+                                  supported (dump length a multiple of 128, or
+                                  a divisor of 256 that is a multiple of 16; up
+                                  to 48 antennas),
+                                  else CHIRP_CORR_FP32_SIMT; the visibility
+                                  beam mode then keeps FP32 products (its sum
+                                  over M^2 pairs amplifies the ~1e-6 relative
+                                  error of split-BF16 visibilities by up to M) */
+#define CHIRP_CORR_FP32_SIMT 1 /* FP32 FMA on the CUDA cores                  */
+#define CHIRP_CORR_TC_3XBF16 2 /* tcgen05, [H; L] H^T split-BF16, FP32 acc    */
+#define CHIRP_CORR_TC_BF16 3   /* reduced precision: tcgen05, H H^T in BF16,
+                                  FP32 accumulate (relative error ~1e-3)      */
+
 /* element type of the voltage input (chirp_config.in_type) */
 #define CHIRP_IN_C64 0         /* complex64: interleaved FP32 (re, im)        */
 #define CHIRP_IN_CI8 1         /* complex int8: interleaved (re, im) bytes,
@@ -109,6 +123,8 @@ typedef struct {
   int in_type;             /* CHIRP_IN_*: element type of every voltage input
                               of this plan's runs ([n_ant][n_samp] elements) */
   const float* in_scale;   /* [n_ant] scale of CHIRP_IN_CI8 input; NULL = 1   */
+  int corr_mode;           /* CHIRP_CORR_*; a tensor-core mode the shape does not
+                              allow gives CHIRP_EUNSUPPORTED                  */
   int beam_shape;          /* tensor-core beam kernel shape: 0 = the library's
                               choice; 1 = 128-sample tiles, weights in shared
                               memory; 2 = 256-sample tiles (dump_len % 256 ==
@@ -144,6 +160,7 @@ typedef struct {
   int beam_mode;           /* CHIRP_BEAM_* actually used (AUTO resolved)        */
   long long fb_samples;    /* T_fb of the incoherent search (0 when off)        */
   int beam_shape;          /* tensor-core beam kernel shape used (0: none)      */
+  int corr_mode;           /* CHIRP_CORR_* actually used (AUTO resolved)        */
 } chirp_plan_info;
 
 /* Create a plan: validates cfg, derives the per-DM FFT lengths and block

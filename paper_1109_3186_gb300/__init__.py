@@ -33,6 +33,7 @@ __all__ = ["Plan", "PropNet", "load", "build", "CHIRP_HOST", "CHIRP_DEVICE", "BE
 CHIRP_HOST, CHIRP_DEVICE = 0, 1
 BEAM_AUTO, BEAM_FP32_SIMT, BEAM_TC_3XBF16, BEAM_VIS, BEAM_TC_BF16 = 0, 1, 2, 3, 4
 IN_C64, IN_CI8 = 0, 1
+CORR_AUTO, CORR_FP32_SIMT, CORR_TC_3XBF16, CORR_TC_BF16 = 0, 1, 2, 3
 FLAG_GRAPHS, FLAG_AUTOTUNE = 1, 2
 K_DM_DEFAULT = 4.148808e15
 
@@ -66,7 +67,8 @@ class _Config(ctypes.Structure):
                 ("beam_mode", ctypes.c_int), ("fb_chan", ctypes.c_int), ("fb_int", ctypes.c_int),
                 ("fb_dm", ctypes.POINTER(ctypes.c_double)), ("fb_n_dm", ctypes.c_int),
                 ("flags", ctypes.c_int), ("in_type", ctypes.c_int),
-                ("in_scale", ctypes.POINTER(ctypes.c_float)), ("beam_shape", ctypes.c_int),
+                ("in_scale", ctypes.POINTER(ctypes.c_float)), ("corr_mode", ctypes.c_int),
+                ("beam_shape", ctypes.c_int),
                 ("fft_row", ctypes.c_int)]
 
 
@@ -75,7 +77,7 @@ class _Info(ctypes.Structure):
                 ("n_group", ctypes.c_int), ("workspace_bytes", ctypes.c_longlong),
                 ("ifft_points", ctypes.c_longlong), ("valid_samples", ctypes.c_longlong),
                 ("beam_mode", ctypes.c_int), ("fb_samples", ctypes.c_longlong),
-                ("beam_shape", ctypes.c_int)]
+                ("beam_shape", ctypes.c_int), ("corr_mode", ctypes.c_int)]
 
 
 _lib = None
@@ -308,7 +310,8 @@ class Plan:
                  nfft_min: int, pix_lm=None, k_dm: float = K_DM_DEFAULT,
                  beam_mode: int = BEAM_AUTO, n_ant: int | None = None, stream=None,
                  fb_chan: int = 0, fb_int: int = 1, fb_dm=None, flags: int = 0, fft_row: int = 0,
-                 in_type: int = IN_C64, in_scale=None, beam_shape: int = 0):
+                 in_type: int = IN_C64, in_scale=None, beam_shape: int = 0,
+                 corr_mode: int = CORR_AUTO):
         self._xyz = None if xyz is None else np.ascontiguousarray(xyz, dtype=np.float64)
         self._dms = np.ascontiguousarray(np.atleast_1d(dms), dtype=np.float64)
         self._pix = None if pix_lm is None else np.ascontiguousarray(pix_lm, dtype=np.float64)
@@ -337,6 +340,7 @@ class Plan:
         cfg.fft_row = int(fft_row)
         cfg.in_type = int(in_type)
         cfg.beam_shape = int(beam_shape)
+        cfg.corr_mode = int(corr_mode)
         self.in_type = int(in_type)
         self._scale = (None if in_scale is None
                        else np.ascontiguousarray(np.atleast_1d(in_scale), dtype=np.float32))

@@ -117,6 +117,14 @@ cudaError_t launch_beam_tc(const uint8_t* b_img, const uint8_t* a_img, int n_ant
                            int dump_len, long long first, long long last, long long t_origin,
                            float* pow, int* err, int terms, int shape, cudaStream_t st);
 
+// ---- tensor-core correlator (corr_tc.cu) ----
+// terms = 3: split-BF16 ([H; L] H^T), terms = 1: plain BF16 (H H^T)
+bool corr_tc_supported(int n_ant, int dump_len, int terms);
+// vis[m][pair] for the dumps first..last of one DM (FP32 accumulation)
+cudaError_t launch_correlate_tc(const float2* y, long long n_samp, int n_ant, int dump_len,
+                                long long first, long long last, float2* vis, int* err, int terms,
+                                cudaStream_t st);
+
 // ---- candidate detection (detect.cu) ----
 long long detect_chunks(int n_dm, long long n_dump, int n_pix);  // entries of counts / offsets
 cudaError_t launch_detect(const float* P, int n_dm, long long n_dump, int n_pix,

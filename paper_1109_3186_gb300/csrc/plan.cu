@@ -93,6 +93,8 @@ struct chirp_plan {
   int beam_mode = 0;
   int beam_terms = 3;         // tensor-core modes: 3 (split BF16) or 1 (BF16)
   int beam_shape = 0;         // tensor-core kernel shape (beam_tc_pick)
+  int corr_mode = CHIRP_CORR_FP32_SIMT;  // resolved CHIRP_CORR_*
+  bool corr_forced = false;              // set explicitly (else AUTO)
   int in_type = CHIRP_IN_C64;
   float* d_scale = nullptr;   // [M] CHIRP_IN_CI8 scales
   cudaStream_t stream = nullptr;
@@ -341,6 +343,8 @@ int validate(const chirp_config* c) {
     return fail(CHIRP_EINVAL, "fft_row must be 0 or a power of two in 256..4096");
   if (c->beam_shape < 0 || c->beam_shape > 3)
     return fail(CHIRP_EINVAL, "beam_shape must be 0..3");
+  if (c->corr_mode < 0 || c->corr_mode > CHIRP_CORR_TC_BF16)
+    return fail(CHIRP_EINVAL, "unknown corr_mode");
   if (c->flags & ~(CHIRP_FLAG_GRAPHS | CHIRP_FLAG_AUTOTUNE))
     return fail(CHIRP_EINVAL, "unknown flag bits 0x%x", c->flags);
   if (c->n_pix < 0) return fail(CHIRP_EINVAL, "n_pix must be >= 0");
@@ -417,6 +421,23 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
                        ? CHIRP_BEAM_VIS
                        : CHIRP_BEAM_TC_3XBF16;
   p->beam_terms = p->beam_mode == CHIRP_BEAM_TC_BF16 ? 1 : 3;
+  p->corr_mode = cfg->corr_mode;
+  p->corr_forced = cfg->corr_mode != CHIRP_CORR_AUTO;
+  // AUTO: the tensor cores from 12 antennas up (measured: 12 antennas on par
+  // with the CUDA cores, 36 antennas 1.6x faster; 6 antennas 1.7x slower,
+  // where 128-row MMA tiles carry 12 useful rows)
+  if (p->corr_mode == CHIRP_CORR_AUTO)
+    p->corr_mode = cfg->n_ant >= 12 && corr_tc_supported(cfg->n_ant, cfg->dump_len, 3)
+                       ? CHIRP_CORR_TC_3XBF16
+                       : CHIRP_CORR_FP32_SIMT;
+  if (p->corr_mode != CHIRP_CORR_FP32_SIMT &&
+      !corr_tc_supported(cfg->n_ant, cfg->dump_len, p->corr_mode == CHIRP_CORR_TC_BF16 ? 1 : 3)) {
+    delete p;
+    return fail(CHIRP_EUNSUPPORTED,
+                "tensor-core correlation needs a dump length that lines up with its 128- or "
+                "256-sample chunks and an antenna count whose operands fit (48 for split-BF16, "
+                "84 for BF16)");
+  }
   if (cfg->n_pix > 0 && tc_beams(p)) {
     p->beam_shape = beam_tc_pick(p->M, cfg->n_pix, cfg->dump_len, p->beam_terms, cfg->beam_shape);
     if (p->beam_shape == 0) {
@@ -704,6 +725,7 @@ int chirp_plan_query(const chirp_plan* p, chirp_plan_info* info) {
   info->valid_samples = p->valid_samples;
   info->beam_mode = p->beam_mode;
   info->beam_shape = p->beam_shape;
+  info->corr_mode = p->corr_mode;
   info->fb_samples = p->T_fb;
   return CHIRP_OK;
 }
@@ -865,19 +887,27 @@ BeamImageOut beam_image_for(const chirp_plan* p, int d) {
 int backend_dumps(chirp_plan* p, int d, Backend be, long long m0, long long m1, void* dout) {
   if (m1 <= m0) return CHIRP_OK;
   const long long last = m1 - 1;
-  if (be == kCorrelate) {
-    const size_t per_dm = (size_t)p->n_dump * p->n_pair;
+  // visibilities of dumps [m0, m1) into vis[m][pair] (absolute dump index m).
+  // The visibility beam identity sums M^2 pair terms per pixel, which
+  // multiplies a visibility's relative error by up to M, so unless a
+  // tensor-core correlation was asked for explicitly it uses FP32 products.
+  auto correlate = [&](float2* vis, bool for_beams) -> int {
     int mk = mark_begin(p);
-    CK(launch_correlate(p->d_y, p->N, p->M, p->L, m0, m1 - m0, m0, last,
-                        (float2*)dout + d * per_dm, p->stream));
+    if (p->corr_mode == CHIRP_CORR_FP32_SIMT || (for_beams && !p->corr_forced))
+      CK(launch_correlate(p->d_y, p->N, p->M, p->L, m0, m1 - m0, m0, last, vis, p->stream));
+    else
+      CK(launch_correlate_tc(p->d_y, p->N, p->M, p->L, m0, last, vis, p->d_err,
+                             p->corr_mode == CHIRP_CORR_TC_BF16 ? 1 : 3, p->stream));
     mark_end(p, CHIRP_STAGE_CORRELATE, mk);
     return CHIRP_OK;
-  }
+  };
+  if (be == kCorrelate)
+    return correlate((float2*)dout + d * (size_t)p->n_dump * p->n_pair, false);
   float* out = (float*)dout + (size_t)d * p->n_dump * p->n_pix;
   if (p->beam_mode == CHIRP_BEAM_VIS) {
-    int mk = mark_begin(p);
-    CK(launch_correlate(p->d_y, p->N, p->M, p->L, m0, m1 - m0, m0, last, p->d_V, p->stream));
-    mark_end(p, CHIRP_STAGE_CORRELATE, mk);
+    int rc = correlate(p->d_V, true);
+    if (rc) return rc;
+    int mk;
     mk = mark_begin(p);
     CK(launch_beam_from_vis(p->d_V, p->d_wpair, p->M, p->n_pix, m0, last, out, p->stream));
     mark_end(p, CHIRP_STAGE_BEAMFORM, mk);

@@ -54,6 +54,7 @@ def _cfg(**over):
     (dict(fft_row=300), "fft_row"),
     (dict(flags=8), "flag"),
     (dict(beam_shape=4), "beam_shape"),
+    (dict(corr_mode=7), "corr_mode"),
     (dict(in_type=1, in_scale=np.array([np.inf, 1.0])), "in_scale"),
 ])
 def test_plan_validation_rejects_bad_shapes(over, msg):
@@ -70,10 +71,10 @@ def test_graphs_flag_needs_a_stream():
 
 
 def test_forced_beam_kernel_shape_that_does_not_fit_is_refused():
-    # 64 antennas, split-BF16: the weights of one row tile and two voltage
+    # 84 antennas, split-BF16: the weights of one row tile and two voltage
     # tiles exceed shared memory with 128-sample tiles (only the TMEM shape fits)
-    xyz = np.zeros((64, 3))
-    xyz[:, 0] = np.arange(64.0)
+    xyz = np.zeros((84, 3))
+    xyz[:, 0] = np.arange(84.0)
     with pytest.raises(chirp.ChirpError) as ei:
         chirp.Plan(**_cfg(xyz=xyz, pix_lm=np.zeros((4, 2)), beam_mode=chirp.BEAM_TC_3XBF16,
                           beam_shape=1))

@@ -14,19 +14,29 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.mark.parametrize("M,N,L,dms,nfft_min", [
+CORR_CASES = [
     (6, 1 << 17, 1024, [0.0, 20.0, 40.0, 75.0], 1 << 14),
     (4, 100003, 777, [0.0, 33.0], 1 << 13),     # ragged N and dump length
     (1, 1 << 15, 512, [5.0], 1 << 12),          # one antenna: autos only
     (13, 1 << 15, 256, [0.0, 9.0], 1 << 12),    # 91 pairs
-    (36, 1 << 14, 1024, [0.0, 5.0], 1 << 12),   # 666 pairs, 45 tiles of 4 x 4
-])
-def test_chirpolator_matches_oracle(M, N, L, dms, nfft_min, k_dm):
+    (36, 1 << 14, 1024, [0.0, 5.0], 1 << 12),   # 666 pairs; tensor cores: two row tiles
+    (48, 1 << 14, 2048, [0.0, 3.0], 1 << 12),   # largest split-BF16 tensor-core shape
+]
+
+
+@pytest.mark.parametrize("corr", [chirp.CORR_FP32_SIMT, chirp.CORR_TC_3XBF16],
+                         ids=["fp32_simt", "tc_3xbf16"])
+@pytest.mark.parametrize("M,N,L,dms,nfft_min", CORR_CASES,
+                         ids=["M%d_N%d_L%d" % (c[0], c[1], c[2]) for c in CORR_CASES])
+def test_chirpolator_matches_oracle(M, N, L, dms, nfft_min, corr, k_dm):
+    if corr == chirp.CORR_TC_3XBF16 and L % 128 and 256 % L:
+        pytest.skip("tensor-core correlation needs dump chunks that line up")
     sc = skymodel.chirpolator_small(n_samp=N, n_dm=len(dms), n_ant=M, dm_max=max(dms),
                                     nfft_min=nfft_min, dump_len=L)
     sc.dms = np.array(dms)
     x = sc.voltages()
-    plan = chirp.Plan.from_scenario(sc)
+    plan = chirp.Plan.from_scenario(sc, corr_mode=corr)
+    assert plan.info["corr_mode"] == corr
     V = torch.empty((len(dms), plan.n_dump, plan.n_pair), dtype=torch.complex64, device="cuda")
     plan.chirpolator(torch.from_numpy(x).cuda(), V)
     Vg = V.cpu().numpy()
@@ -94,3 +104,14 @@ def test_host_buffers_round_trip(k_dm):
     Vd = torch.empty(Vh.shape, dtype=torch.complex64, device="cuda")
     plan.chirpolator(torch.from_numpy(x).cuda(), Vd)
     assert np.array_equal(Vh, Vd.cpu().numpy())
+
+
+def test_auto_correlation_mode_and_refusals():
+    sc = skymodel.chirpolator_small(n_samp=1 << 15, n_dm=2, n_ant=12, dm_max=10.0,
+                                    nfft_min=1 << 12, dump_len=777)
+    assert chirp.Plan.from_scenario(sc).info["corr_mode"] == chirp.CORR_FP32_SIMT
+    with pytest.raises(chirp.ChirpError) as ei:
+        chirp.Plan.from_scenario(sc, corr_mode=chirp.CORR_TC_3XBF16)
+    assert ei.value.code == -5
+    sc.dump_len = 1024
+    assert chirp.Plan.from_scenario(sc).info["corr_mode"] == chirp.CORR_TC_3XBF16

@@ -23,6 +23,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 TOL_POW_BF16 = 1e-2
+TOL_VIS_BF16 = 1e-2
 
 
 def _int8(sc):
@@ -104,6 +105,20 @@ def test_bf16_beams_match_oracle(M, N, L, n_side, dms, nfft_min, k_dm):
     assert err < TOL_POW_BF16, err
 
 
+@pytest.mark.parametrize("M,L", [(12, 1024), (36, 2048), (84, 512)])
+def test_bf16_correlation_matches_oracle(M, L, k_dm):
+    sc = skymodel.chirpolator_small(n_samp=1 << 15, n_dm=2, n_ant=M, dm_max=10.0,
+                                    nfft_min=1 << 12, dump_len=L)
+    x = sc.voltages()
+    plan = chirp.Plan.from_scenario(sc, corr_mode=chirp.CORR_TC_BF16)
+    V = np.empty((2, plan.n_dump, plan.n_pair), np.complex64)
+    plan.chirpolator(x, V)
+    plan.status()
+    Vo = orc.chirpolator(x, sc.f0, sc.bw, k_dm, sc.dms, sc.nfft_min, sc.dump_len)
+    err = vis_error(V, Vo, M)
+    assert err < TOL_VIS_BF16, err
+
+
 def test_precision_form_channel(k_dm):
     """One coarse channel of the 36-antenna int8 array (reduced length and DM
     range): int8 ingest, FP32 Chirpolator, BF16 Chimageator."""
@@ -117,6 +132,13 @@ def test_precision_form_channel(k_dm):
     pv.chirpolator(qd, V)
     Vo = orc.chirpolator(xo, sc.f0, sc.bw, k_dm, sc.dms, sc.nfft_min, sc.dump_len)
     assert vis_error(V.cpu().numpy(), Vo, sc.n_ant) < TOL_VIS
+    # the precision form's correlation: BF16 on the tensor cores
+    pb16 = chirp.Plan.from_scenario(sc, in_type=chirp.IN_CI8, in_scale=s,
+                                    corr_mode=chirp.CORR_TC_BF16)
+    V16 = torch.empty_like(V)
+    pb16.chirpolator(qd, V16)
+    pb16.status()
+    assert vis_error(V16.cpu().numpy(), Vo, sc.n_ant) < TOL_VIS_BF16
     pb = chirp.Plan.from_scenario(sc, in_type=chirp.IN_CI8, in_scale=s,
                                   beam_mode=chirp.BEAM_TC_BF16)
     P = torch.empty((len(sc.dms), pb.n_dump, pb.n_pix), dtype=torch.float32, device="cuda")
