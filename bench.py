@@ -417,6 +417,25 @@ def run_ours(args):
             alt[MODE_NAME[mode]] = {"value": units / (ms2 * 1e-3), "ms_per_step": ms2,
                                     "steps": k, "dtype": DTYPE_LABEL[mode]}
             pl2.close()
+        # the Chirpolator back-end on the same voltages and DMs
+        Vd = torch.empty((n_dm, n_dump, plan.n_pair), dtype=torch.complex64, device="cuda")
+        plan.chirpolator(xd, Vd)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        k = max(2, args.steps // 2)
+        a0.record(stream)
+        for _ in range(k):
+            plan.chirpolator(xd, Vd)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms2 = a0.elapsed_time(a1) / k
+        n_valid_dumps = int(np.sum(np.maximum(0, last - first + 1)))
+        alt["chirpolator"] = {"value": units / (ms2 * 1e-3), "ms_per_step": ms2, "steps": k,
+                              "baseline_dm_dumps_per_s": n_valid_dumps * plan.n_pair / (ms2 * 1e-3),
+                              "corr_mode": {1: "fp32_simt", 2: "tc_3xbf16", 3: "tc_bf16"}[
+                                  plan.info["corr_mode"]]}
+        del Vd
         plan.chimageator(xd, Pd)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
