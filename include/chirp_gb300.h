@@ -24,7 +24,8 @@
  *            n_lo = ceil(k DM ((f0-B/2)^-2 - f0^-2) B);
  *    Nfft = max(nfft_min, min(pow2ceil(2 (n_hi + n_lo)), pow2ceil(n_samp)));
  *    DMs with equal Nfft share one block grid of step
- *    S = Nfft - max n_hi - max n_lo.  Output sample t refers to the arrival
+ *    S = Nfft - max n_hi - max n_lo, rounded down to a multiple of 8 when at
+ *    least 8.  Output sample t refers to the arrival
  *    at f0 and is valid for t in [n_hi, n_samp - n_lo).
  *  - Dumps are the absolute grid [m L, (m+1) L), m < floor(n_samp / L).  A
  *    dump is valid for a DM only if it lies inside that DM's valid range;

@@ -41,8 +41,10 @@
  *  - FFT length per DM: Nfft(DM) = max(nfft_min, min(pow2ceil(2 n_d),
  *    pow2ceil(N))), n_d = n_hi + n_lo.  DMs with equal Nfft form a group that
  *    shares one block grid with step S = Nfft - max(n_hi) - max(n_lo) over
- *    the group; n_blk = 1 if N <= Nfft else ceil((N - Nfft)/S) + 1; block b
- *    reads x[b S, b S + Nfft) (zero past N).
+ *    the group, rounded down to a multiple of 8 when it is at least 8 (any
+ *    step up to that difference keeps every kept output clear of the
+ *    circular wrap); n_blk = 1 if N <= Nfft else ceil((N - Nfft)/S) + 1;
+ *    block b reads x[b S, b S + Nfft) (zero past N).
  *  - Output time t refers to the arrival at f0.  Valid outputs of a DM are
  *    t in [n_hi, N - n_lo).  Block b owns t in [b S + max n_hi, (b+1) S +
  *    max n_hi); block 0 also owns everything below, the last block
@@ -196,6 +198,7 @@ int orc_layout(const double* dms, int n_dm, int d, double f0, double bw, double 
     if (lo > L.n_lo_max) L.n_lo_max = lo;
   }
   L.step = L.nfft - L.n_hi_max - L.n_lo_max;
+  if (L.step >= 8) L.step -= L.step % 8;  /* block starts on multiples of 8 samples */
   if (n_samp <= L.nfft) {
     L.n_blk = 1;
   } else {

@@ -130,6 +130,7 @@ extern "C" int chirp_dedisperse_noalloc(const void* volt, int n_ant, long long n
   g.n_hi_max = n_hi;
   g.n_lo_max = n_lo;
   g.step = nfft - n_hi - n_lo;
+  if (g.step >= 8) g.step -= g.step % 8;  // blocks start on multiples of 8 samples
   if (n_samp <= nfft) {
     g.n_blk = 1;
   } else {

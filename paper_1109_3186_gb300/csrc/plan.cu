@@ -506,6 +506,7 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
       G.n_lo_max = std::max(G.n_lo_max, lo[d]);
     }
     G.step = G.nfft - G.n_hi_max - G.n_lo_max;
+    if (G.step >= 8) G.step -= G.step % 8;  // blocks start on multiples of 8 samples
     if (p->N <= G.nfft) {
       G.n_blk = 1;
     } else {

@@ -172,7 +172,7 @@ def test_layout_groups_follow_the_fft_length_rule(k_dm):
     dms = np.linspace(0, 150, 16)
     lay = orc.layout(dms, 15, 1.4e9, 8e6, k_dm, 1 << 20, 1 << 16)
     assert lay["nfft"] == 1 << 16
-    assert lay["step"] == (1 << 16) - lay["n_hi"] - lay["n_lo"]
+    assert lay["step"] == ((1 << 16) - lay["n_hi"] - lay["n_lo"]) // 8 * 8
     assert lay["n_blk"] == 28
     # 12 antennas, 32 MHz, 2^22 samples, 64 DMs in 0-300, FFT >= 2^18
     dms = np.linspace(0, 300, 64)
