@@ -25,7 +25,10 @@
 //
 // Layouts (no swizzle, K-major, 8-row x 16-byte core matrices):
 //   A image per 128-row tile: [m-group 16][k-slot 2*ksteps][8 rows][8 bf16]
-//   B tile of NT samples: [n-group NT/8][k-group GB][8 samples][8 bf16]
+//     (K-major: a 16-byte row holds 8 K-values of one output row)
+//   B tile of NT samples: [n-group NT/8][k-group GB][8 K-rows][8 samples bf16]
+//     (MN-major: a 16-byte row holds 8 consecutive samples of one K-value,
+//     which lets the inverse column pass write whole rows of one antenna)
 //     three terms: GB = 2G, k-group g < G: heads of real K 8g..8g+7,
 //     g >= G: tails of 8(g-G)...;  one term: GB = G rounded up to even, heads
 //     only, the padding group zero.
@@ -95,7 +98,7 @@ struct BeamCfg {
   static constexpr int ISSUERS = CHIRP_BEAM_ISSUERS;     // MMA-issuing warps
   static constexpr int EPI0 = 1 + ISSUERS;               // first epilogue warp
   static constexpr int THREADS = 32 * (EPI0 + EPI_WARPS);
-  static constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, NT);
+  static constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, NT, true);  // B MN-major
   static constexpr uint32_t RED_BYTES = NT == 256 ? 4u * RMAX * 128u * 4u : 0u;
 };
 

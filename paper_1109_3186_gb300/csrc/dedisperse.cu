@@ -168,10 +168,13 @@ __global__ void __launch_bounds__(256, 4) k_inv_rows(const float2* __restrict__ 
 
 // Column pass of the inverse: natural-order output, 1/Nfft, overlap-save
 // discard and ownership.  Block b owns block positions [lo_b, hi_b).
-// IMG: instead of y, the owned samples inside [img.t0, img.t1) are written
-// as the beamformer's BF16 head (and tail) image: one 4-byte (re, im) pair
-// per antenna and sample and term, the head rounded to nearest BF16 and the
-// tail the rounded remainder.
+// IMG: instead of y, the owned samples inside [img.t0, img.t1) go to the
+// beamformer's BF16 image (MN-major core matrices: a 16-byte row holds 8
+// consecutive samples of one real component; head rounded to nearest BF16,
+// tail the rounded remainder).  The values are staged in shared memory per
+// component and written as whole rows where 8 consecutive samples are all
+// owned and aligned (block starts are multiples of 8 samples), one real and
+// one imaginary row together (32 bytes); elsewhere sample by sample.
 template <int L, bool IMG>
 __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ Z,
                                                   float2* __restrict__ y, long long n_samp,
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ 
                                                   TwiddlePtrs twp, BeamImageOut img) {
   constexpr int C = 4096 / L;
   constexpr int T = L / 16;
-  __shared__ float2 sm[FftTile<L, C>::SLOTS];
+  __shared__ __align__(16) float2 sm[FftTile<L, C>::SLOTS];
   const Twiddles tw = mk_tw(twp);
   const int s = threadIdx.x % C, jt = threadIdx.x / C;
   const int c = blockIdx.x * C + s;
@@ -197,36 +200,86 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ 
   for (int k = 0; k < 16; k++)
     v[k] = act ? src[(long long)(jt + k * T) * n2 + c] : make_float2(0.f, 0.f);
   fft_core<L, C, false, true>(v, sm, s, jt, tw);
-  if (!act) return;
   const long long base = b * step;
   const long long lo_b = (b == 0) ? n_hi : n_hi_max;
   const long long hi_b = (b == n_blk - 1) ? (n_samp - n_lo - base) : (n_hi_max + step);
   const float scale = 1.0f / (float)nfft;  // exact: power of two
   if constexpr (IMG) {
+    // staging [component][row][column] of BF16: components re_h, im_h (, re_l, im_l)
+    __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(sm);
+    const int ncomp = img.terms == 3 ? 4 : 2;
+    __syncthreads();  // every thread is done with the transform's exchanges
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      const int row = jt + k * T;
+      const float2 val = cscale(v[k], scale);
+      const __nv_bfloat162 h = __floats2bfloat162_rn(val.x, val.y);
+      stg[(0 * L + row) * C + s] = h.x;
+      stg[(1 * L + row) * C + s] = h.y;
+      if (ncomp == 4) {
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(val.x - hf.x, val.y - hf.y);
+        stg[(2 * L + row) * C + s] = l.x;
+        stg[(3 * L + row) * C + s] = l.y;
+      }
+    }
+    __syncthreads();
     const long long nt_mask = (1LL << img.log2_nt) - 1;
     const size_t grp_bytes = (size_t)img.GB * 128;
     const size_t tile_bytes = ((size_t)1 << img.log2_nt) / 8 * grp_bytes;
-    uint8_t* img_a = img.img + (size_t)(a >> 2) * 128 + (size_t)(a & 3) * 4;
-#pragma unroll
-    for (int k = 0; k < 16; k++) {
-      const long long n = (long long)(jt + k * T) * n2 + c;
-      const long long t = base + n;
-      if (n >= lo_b && n < hi_b && t >= img.t0 && t < img.t1) {
-        const long long u = t - img.t0;
-        const long long nn = u & nt_mask;
-        const float2 val = cscale(v[k], scale);
-        const __nv_bfloat162 h = __floats2bfloat162_rn(val.x, val.y);
-        uint8_t* dst = img_a + (size_t)(u >> img.log2_nt) * tile_bytes +
-                       (size_t)(nn >> 3) * grp_bytes + (size_t)(nn & 7) * 16;
-        *reinterpret_cast<__nv_bfloat162*>(dst) = h;
-        if (img.terms == 3) {
-          const float2 hf = __bfloat1622float2(h);
-          *reinterpret_cast<__nv_bfloat162*>(dst + (size_t)img.G * 128) =
-              __floats2bfloat162_rn(val.x - hf.x, val.y - hf.y);
+    // byte offset of antenna a's real row in a core-matrix column (imaginary: +16)
+    const size_t a_ofs = (size_t)(a >> 2) * 128 + (size_t)(a & 3) * 32;
+    const size_t tail_ofs = (size_t)img.G * 128;
+    auto owned = [&](long long n, long long t, int col) {
+      return col < n2 && n >= lo_b && n < hi_b && t >= img.t0 && t < img.t1;
+    };
+    if constexpr (C >= 8) {
+      constexpr int CPR = C / 8;  // 8-sample chunks per row
+      const int n_work = (ncomp / 2) * L * CPR;
+      for (int w = threadIdx.x; w < n_work; w += 256) {
+        const int j = w % CPR, rp = w / CPR;
+        const int row = rp % L, pair = rp / L;  // pair 0: head, 1: tail
+        const int col0 = blockIdx.x * C + 8 * j;
+        const long long n0 = (long long)row * n2 + col0;
+        const long long t0 = base + n0, u0 = t0 - img.t0;
+        const __nv_bfloat16* s_re = stg + ((size_t)(2 * pair) * L + row) * C + 8 * j;
+        const __nv_bfloat16* s_im = stg + ((size_t)(2 * pair + 1) * L + row) * C + 8 * j;
+        const size_t ofs = a_ofs + (pair ? tail_ofs : 0);
+        if ((u0 & 7) == 0 && owned(n0, t0, col0) && owned(n0 + 7, t0 + 7, col0 + 7)) {
+          uint8_t* dst = img.img + (size_t)(u0 >> img.log2_nt) * tile_bytes +
+                         (size_t)((u0 & nt_mask) >> 3) * grp_bytes + ofs;
+          *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(s_re);
+          *reinterpret_cast<uint4*>(dst + 16) = *reinterpret_cast<const uint4*>(s_im);
+        } else {
+          for (int e = 0; e < 8; e++) {
+            if (!owned(n0 + e, t0 + e, col0 + e)) continue;
+            const long long u = u0 + e;
+            uint8_t* dst = img.img + (size_t)(u >> img.log2_nt) * tile_bytes +
+                           (size_t)((u & nt_mask) >> 3) * grp_bytes + ofs + (size_t)(u & 7) * 2;
+            *reinterpret_cast<__nv_bfloat16*>(dst) = s_re[e];
+            *reinterpret_cast<__nv_bfloat16*>(dst + 16) = s_im[e];
+          }
         }
+      }
+    } else {
+      // rows shorter than 8 samples: sample by sample from the staging
+      const int n_work = (ncomp / 2) * L * C;
+      for (int w = threadIdx.x; w < n_work; w += 256) {
+        const int col = w % C, rp = w / C;
+        const int row = rp % L, pair = rp / L;
+        const int cc = blockIdx.x * C + col;
+        const long long n = (long long)row * n2 + cc, t = base + n;
+        if (!owned(n, t, cc)) continue;
+        const long long u = t - img.t0;
+        uint8_t* dst = img.img + (size_t)(u >> img.log2_nt) * tile_bytes +
+                       (size_t)((u & nt_mask) >> 3) * grp_bytes + a_ofs + (pair ? tail_ofs : 0) +
+                       (size_t)(u & 7) * 2;
+        *reinterpret_cast<__nv_bfloat16*>(dst) = stg[((size_t)(2 * pair) * L + row) * C + col];
+        *reinterpret_cast<__nv_bfloat16*>(dst + 16) = stg[((size_t)(2 * pair + 1) * L + row) * C + col];
       }
     }
   } else {
+    if (!act) return;
     float2* ya = y + a * n_samp;
 #pragma unroll
     for (int k = 0; k < 16; k++) {

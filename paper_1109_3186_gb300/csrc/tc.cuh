@@ -101,11 +101,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
 }
 
 // Instruction descriptor of kind::f16 with BF16 A/B, FP32 accumulator,
-// both operands K-major, shape M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+// A K-major, B K-major or (b_mn) MN-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N, bool b_mn = false) {
   return (1u << 4)                      // D format: F32
          | (1u << 7)                    // A format: BF16
          | (1u << 10)                   // B format: BF16
+         | ((b_mn ? 1u : 0u) << 16)     // B major-ness: MN
          | ((uint32_t)(N >> 3) << 17)   // N / 8
          | ((uint32_t)(M >> 4) << 24);  // M / 16
 }
