@@ -311,6 +311,121 @@ def stage_roofline(sc, plan, stage_ms, peaks, peak_kind, beam_mode, steps):
     return out
 
 
+def extra_forms(sc, plan, xd, stream, args):
+    """Timings of the forms beside the headline search (rank 0): the
+    incoherent filterbank search, the learned proposer's inference, the
+    selective coherent search over a proposal-like cell mask, and a batch of
+    uneven observations under CUDA graphs."""
+    import torch
+    import paper_1109_3186_gb300 as chirp
+    from paper_1109_3186_gb300 import skymodel
+    out = {}
+
+    def timed(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    n_dm = len(sc.dms)
+    # incoherent search (filterbank of 32 channels, 16 spectra per sample, the same DM grid)
+    pfb = chirp.Plan.from_scenario(sc, beam_mode=chirp.BEAM_VIS, stream=stream, fb_chan=32,
+                                   fb_int=16, fb_dm=sc.dms)
+    T_fb = pfb.info["fb_samples"]
+    D = torch.empty((n_dm, T_fb), dtype=torch.float32, device="cuda")
+    ms = timed(lambda: pfb.incoherent(xd, D), 5)
+    out["incoherent"] = {"ms": ms, "input_antenna_samples_per_s": sc.n_ant * sc.n_samp / (ms * 1e-3),
+                         "fb_chan": 32, "fb_int": 16, "n_dm": n_dm}
+    # learned proposer inference (z-score, conv net, window mask); weights seeded
+    net = chirp.PropNet(n_dm, 64, 9, 5, 1, T_fb, stream=stream)
+    rng = np.random.default_rng(7)
+    net.set_params((0.05 * rng.standard_normal(net.n_params)).astype(np.float32))
+    xz = torch.empty_like(D)
+    z = torch.empty((1, n_dm, T_fb), dtype=torch.float32, device="cuda")
+    win = 8
+    mask = torch.empty((n_dm, (T_fb + win - 1) // win), dtype=torch.int32, device="cuda")
+
+    def infer():
+        net.normalize(D, xz)
+        net.forward(xz[None], z)
+        net.propose(z[0], win, 0.0, mask)
+    ms = timed(infer, 5)
+    out["proposer_inference"] = {"ms": ms, "params": int(net.n_params), "precision": "f32"}
+    pfb.close()
+    # selective coherent search: per DM, seeded runs of dumps covering ~1/3 of the cells
+    first, last = plan.dump_range()
+    cells = np.zeros((n_dm, plan.n_dump), np.uint8)
+    for d in range(n_dm):
+        n_valid = max(0, last[d] - first[d] + 1)
+        for _ in range(6):
+            if n_valid <= 0:
+                break
+            run = max(1, n_valid // 18)
+            m0 = first[d] + int(rng.integers(0, max(1, n_valid - run)))
+            cells[d, m0:m0 + run] = 1
+    frac = float(cells[:, :].sum()) / max(1, int(np.sum(np.maximum(0, last - first + 1))))
+    P = torch.empty((n_dm, plan.n_dump, plan.n_pix), dtype=torch.float32, device="cuda")
+    ms_sel = timed(lambda: plan.chimageator_selective(xd, cells, P), 3)
+    ms_full = timed(lambda: plan.chimageator(xd, P), 3)
+    # the same selection with the reduced-precision (one-term BF16) beams
+    p16 = chirp.Plan.from_scenario(sc, beam_mode=chirp.BEAM_TC_BF16, stream=stream)
+    ms_sel16 = timed(lambda: p16.chimageator_selective(xd, cells, P), 3)
+    p16.close()
+    pipeline = out["incoherent"]["ms"] + out["proposer_inference"]["ms"] + ms_sel16
+    out["selective"] = {"ms": ms_sel, "full_grid_ms": ms_full, "cell_fraction": frac,
+                        "speedup": ms_full / ms_sel, "bf16_beams_ms": ms_sel16,
+                        "incoherent_proposer_selective_bf16_ms": pipeline,
+                        "pipeline_speedup_vs_full_grid": ms_full / pipeline,
+                        "mask": "seeded runs of dumps per DM (6 runs of 1/18 of the valid dumps), "
+                                "not a trained proposer's output"}
+    del P
+    # batch of uneven observations (noise generated on the device), CUDA graphs
+    g = np.random.default_rng(1004)
+    plans, xs, outs = [], [], []
+    units = 0
+    for i in range(8):
+        M = int(g.integers(8, 33))
+        N = int(2 ** g.integers(19, 22))
+        nd = int(g.integers(16, 65))
+        bw = float(g.uniform(16e6, 64e6))
+        L = int(2 ** g.integers(9, 13))
+        scb = skymodel.chimageator_medium(n_samp=N, n_dm=nd, n_ant=M, dm_max=100.0,
+                                                nfft_min=1 << 16, dump_len=L, n_side=16,
+                                                n_pulse=0, seed=3000 + i, bw=bw)
+        st = torch.cuda.Stream()
+        pl = chirp.Plan.from_scenario(scb, stream=st, flags=chirp.FLAG_GRAPHS)
+        plans.append(pl)
+        xs.append(torch.complex(torch.randn(M, N, device="cuda"),
+                                torch.randn(M, N, device="cuda")) * (0.5 ** 0.5))
+        outs.append(torch.empty((nd, pl.n_dump, pl.n_pix), dtype=torch.float32, device="cuda"))
+        units += pl.info["valid_samples"]
+    bes = [1] * len(plans)
+    torch.cuda.synchronize()
+    for _ in range(2):  # eager, then captured
+        chirp.chirp_batch_run(plans, xs, outs, bes)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    k = 3
+    for _ in range(k):
+        chirp.chirp_batch_run(plans, xs, outs, bes)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / k
+    for pl in plans:
+        pl.status()
+        pl.close()
+    out["batch"] = {"value": units / dt, "unit": UNIT, "ms_per_batch": dt * 1e3,
+                    "observations": len(plans),
+                    "shapes": "seeded: 8-32 antennas, 2^19-2^21 samples, 16-64 DMs, 16-64 MHz, "
+                              "dumps 512-4096, 256 beams; one stream each, CUDA graphs"}
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_1109_3186_gb300 as chirp
@@ -436,6 +551,7 @@ def run_ours(args):
                               "corr_mode": {1: "fp32_simt", 2: "tc_3xbf16", 3: "tc_bf16"}[
                                   plan.info["corr_mode"]]}
         del Vd
+        alt.update(extra_forms(sc, plan, xd, stream, args))
         plan.chimageator(xd, Pd)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
