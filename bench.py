@@ -311,6 +311,24 @@ def stage_roofline(sc, plan, stage_ms, peaks, peak_kind, beam_mode, steps):
     return out
 
 
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """The largest value of x over all ranks (the job's time is its slowest
+    rank's); x itself without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: every rank searches its own observation of the
+    same size (weak scaling), so the job covers world x units in the slowest
+    rank's time."""
+    return world * units_per_rank / seconds
+
+
 def extra_forms(sc, plan, xd, stream, args):
     """Timings of the forms beside the headline search (rank 0): the
     incoherent filterbank search, the learned proposer's inference, the
@@ -478,11 +496,8 @@ def run_ours(args):
     clk = clocks.stop()
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * units / (ms * 1e-3)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = job_value(units, world, ms * 1e-3)
 
     # end to end through the same call: pinned host input, host output
     e2e = None
@@ -497,11 +512,8 @@ def run_ours(args):
             plan.chimageator(xh, Ph)
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / args.steps
-        if dist is not None:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * units / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+        dt = max_over_ranks(dt, dist, "cuda")
+        e2e = {"value": job_value(units, world, dt), "unit": UNIT, "ms_per_step": dt * 1e3,
                "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(Ph.numel() * 4)}
 
     roof = stage_roofline(sc, plan, stage, peaks, peak_kind, plan.info["beam_mode"], args.steps)
