@@ -26,7 +26,9 @@
 
 namespace chirp {
 
-static __device__ __forceinline__ Twiddles mk_tw(TwiddlePtrs p) { return Twiddles{p.coarse, p.fine}; }
+static __device__ __forceinline__ Twiddles mk_tw(TwiddlePtrs p) {
+  return Twiddles{p.coarse, p.fine, p.stage};
+}
 
 // ------------------------------------------------------------------ forward
 // Column pass: L = n1, C = 4096 / n1 columns per CTA (interleaved tile).
@@ -130,16 +132,49 @@ __global__ void k_chirp_table(const double* __restrict__ G, float2* __restrict__
   H[pos] = make_float2(cs, sn);
 }
 
+// ------------------------------------------------------------------ twiddles
+// exp(-2 pi j e / n) from the exact fraction e / n (n a power of two), FP64
+// with the argument reduced by sincospi, rounded once to FP32.
+static __device__ __forceinline__ float2 unit_root(long long e, long long n) {
+  double s, c;
+  sincospi(-2.0 * (double)e / (double)n, &s, &c);
+  return make_float2((float)c, (float)s);
+}
+
+__global__ void k_twiddles(float2* __restrict__ tw) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < 4096) {
+    tw[m] = unit_root(m, 4096);
+    tw[4096 + m] = unit_root(m, 1 << 24);
+  }
+  // stage pairs: span 16 at entries [0, 16), span 256 at [16, 272)
+  if (m < kStageTwiddles) {
+    const int ns = m < 16 ? 16 : 256, j = m < 16 ? m : m - 16;
+    float4* st = reinterpret_cast<float4*>(tw + 8192);
+    const float2 w1 = unit_root(j, 16LL * ns), w4 = unit_root(4LL * j, 16LL * ns);
+    st[m] = make_float4(w1.x, w1.y, w4.x, w4.y);
+  }
+}
+
+__global__ void k_row_twiddles(float2* __restrict__ rtw, int n1, int T, int log2n) {
+  const long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= (long long)n1 * T) return;
+  const long long k1 = pos / T, j = pos % T, n = 1LL << log2n;
+  rtw[pos] = unit_root((k1 * j) & (n - 1), n);
+}
+
 // ------------------------------------------------------------------ inverse
 // Row pass: X * H on load, IFFT of length L = n2, twiddle W_N^(-n2 k1) on
-// store.  One CTA per (C rows, sequence); H comes from the per-DM table.
+// store.  One CTA per (C rows, sequence); H comes from the per-DM table, the
+// per-thread twiddle factor W_N^(k1 jt) from the group's row table.
 template <int L>
 __global__ void __launch_bounds__(256, 4) k_inv_rows(const float2* __restrict__ spec,
                                                   float2* __restrict__ Z,
                                                   const float2* __restrict__ H, int n1,
                                                   int log2n, long long q0,
                                                   const int* __restrict__ blk_list, int n_ant,
-                                                  TwiddlePtrs twp) {
+                                                  TwiddlePtrs twp,
+                                                  const float2* __restrict__ rtw) {
   constexpr int C = 4096 / L;
   constexpr int T = L / 16;
   __shared__ float2 sm[FftTile<L, C>::SLOTS];
@@ -161,9 +196,52 @@ __global__ void __launch_bounds__(256, 4) k_inv_rows(const float2* __restrict__ 
   if (!act) return;
   float2* dst = Z + (long long)blockIdx.y * nfft + (long long)k1 * L;
   // twiddle W_N^(-k1 n2), n2 = jt + k T
-  twiddle_run<true>(v, (unsigned)k1, (unsigned)jt, (unsigned)T, log2n, tw);
+  twiddle_run_base<true>(v, __ldg(rtw + (long long)k1 * T + jt), (unsigned)k1, (unsigned)T, log2n,
+                         tw);
 #pragma unroll
   for (int k = 0; k < 16; k++) dst[jt + k * T] = v[k];
+}
+
+// Row pass for n_dm trial DMs of one FFT-length group at once: the spectrum
+// row is read from DRAM once (later DMs find it in L2) and multiplied by each
+// DM's chirp in turn; DM d's rows go to Z + d * z_stride.  Saves up to half
+// of the row pass's DRAM traffic (the spectrum read) for all but one DM.
+// The sequence is the fast grid index, so the blocks that share the n_dm
+// chirp rows of one row index run together and find them in L2 (with the
+// sequence slow, n_dm whole chirp tables would have to stay in L2 beside the
+// streamed spectra and outputs).
+template <int L>
+__global__ void __launch_bounds__(256, 4) k_inv_rows_multi(const float2* __restrict__ spec,
+                                                        float2* __restrict__ Z, long long z_stride,
+                                                        const float2* __restrict__ H,
+                                                        long long h_stride, int n_dm, int n1,
+                                                        int log2n, TwiddlePtrs twp,
+                                                        const float2* __restrict__ rtw) {
+  constexpr int C = 4096 / L;
+  constexpr int T = L / 16;
+  __shared__ float2 sm[FftTile<L, C>::SLOTS];
+  const Twiddles tw = mk_tw(twp);
+  const int jt = threadIdx.x % T, s = threadIdx.x / T;
+  const int k1 = blockIdx.y * C + s;
+  const bool act = k1 < n1;
+  const long long nfft = (long long)L * n1;
+  const float2* src = spec + (long long)blockIdx.x * nfft + (long long)k1 * L;
+  const float2 rbase = act ? __ldg(rtw + (long long)k1 * T + jt) : make_float2(1.f, 0.f);
+  for (int d = 0; d < n_dm; d++) {
+    const float2* h = H + d * h_stride + (long long)k1 * L;
+    float2 v[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++)
+      v[k] = act ? cmul(src[jt + k * T], __ldg(h + jt + k * T)) : make_float2(0.f, 0.f);
+    fft_core<L, C, true, true>(v, sm, s, jt, tw);
+    if (act) {
+      float2* dst = Z + d * z_stride + (long long)blockIdx.x * nfft + (long long)k1 * L;
+      twiddle_run_base<true>(v, rbase, (unsigned)k1, (unsigned)T, log2n, tw);
+#pragma unroll
+      for (int k = 0; k < 16; k++) dst[jt + k * T] = v[k];
+    }
+    __syncthreads();  // sm is reused by the next DM's transform
+  }
 }
 
 // Column pass of the inverse: natural-order output, 1/Nfft, overlap-save
@@ -336,6 +414,17 @@ cudaError_t launch_build_phase_table(double* G, const GroupGeom& g, double f0, d
   return cudaGetLastError();
 }
 
+cudaError_t launch_build_twiddles(float2* buf, cudaStream_t st) {
+  k_twiddles<<<16, 256, 0, st>>>(buf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_row_twiddles(float2* rtw, const GroupGeom& g, cudaStream_t st) {
+  const long long n = (long long)g.n1 * (g.n2 / 16);
+  k_row_twiddles<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rtw, g.n1, g.n2 / 16, g.log2n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_chirp_table(const double* G, float2* H, double dm, const GroupGeom& g,
                                cudaStream_t st) {
   long long blocks = (g.nfft + 255) / 256;
@@ -345,13 +434,31 @@ cudaError_t launch_chirp_table(const double* G, float2* H, double dm, const Grou
 
 cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, long long q0,
                                 long long nq, const GroupGeom& g, TwiddlePtrs tw,
-                                cudaStream_t st, const int* blk_list, int n_ant) {
+                                const float2* rtw, cudaStream_t st, const int* blk_list,
+                                int n_ant) {
   if (nq > 65535 || nq < 1) return cudaErrorInvalidConfiguration;
   const int C = 4096 / g.n2;
   dim3 grid((g.n1 + C - 1) / C, (unsigned)nq);
   switch (g.n2) {
 #define X(L) \
-  case L: k_inv_rows<L><<<grid, 256, 0, st>>>(spec, Z, H, g.n1, g.log2n, q0, blk_list, n_ant, tw); break;
+  case L: k_inv_rows<L><<<grid, 256, 0, st>>>(spec, Z, H, g.n1, g.log2n, q0, blk_list, n_ant, tw, rtw); break;
+    CHIRP_SIZES(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inverse_rows_multi(const float2* spec, float2* Z, long long z_stride,
+                                      const float2* H, long long h_stride, int n_dm,
+                                      long long nq, const GroupGeom& g, TwiddlePtrs tw,
+                                      const float2* rtw, cudaStream_t st) {
+  if (nq > 65535 || nq < 1 || n_dm < 1) return cudaErrorInvalidConfiguration;
+  const int C = 4096 / g.n2;
+  dim3 grid((unsigned)nq, (g.n1 + C - 1) / C);
+  switch (g.n2) {
+#define X(L) \
+  case L: k_inv_rows_multi<L><<<grid, 256, 0, st>>>(spec, Z, z_stride, H, h_stride, n_dm, g.n1, g.log2n, tw, rtw); break;
     CHIRP_SIZES(X)
 #undef X
     default: return cudaErrorInvalidValue;

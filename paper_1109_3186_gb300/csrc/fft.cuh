@@ -37,13 +37,20 @@ __device__ __forceinline__ float2 mul_mj(float2 a) {
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
-// twiddle tables in global memory (filled once per plan, FP64 on the host):
+// twiddle tables in global memory (filled once, FP64 rounded once to FP32):
 //   tw_coarse[m] = exp(-2 pi j m / 4096)      m < 4096
 //   tw_fine[m]   = exp(-2 pi j m / 2^24)      m < 4096
+//   stage[o(Ns) + m] = (w, w^4), w = exp(-2 pi j m / (16 Ns)), m < Ns, for
+//                  the radix-16 stages of span Ns = 16 (o = 0) and 256 (o = 16):
+//                  the butterflies of a warp read consecutive 16-byte entries
+//                  (the same factors taken from tw_coarse sit 128 bytes or more
+//                  apart, one L1 wavefront per lane)
 struct Twiddles {
   const float2* coarse;
   const float2* fine;
+  const float4* stage;
 };
+constexpr int kStageTwiddles = 16 + 256;
 
 // exp(-+2 pi j m / 4096), m in [0, 4096)
 template <bool INV>
@@ -207,9 +214,15 @@ __device__ __forceinline__ void stage_twiddle(float2* v, int j, int Ns, const Tw
   int jm = j & (Ns - 1);
   int scale = 4096 / (Ns * R);
   if constexpr (R == 16) {
+    // radix-16 stages have Ns = 16 or 256 (L <= 4096)
     float2 (&vv)[16] = *reinterpret_cast<float2(*)[16]>(v);
-    apply_pow16(vv, make_float2(1.f, 0.f), tw4096<INV>(tw, jm * scale),
-                tw4096<INV>(tw, 4 * jm * scale));
+    const float4 t = __ldg(tw.stage + (Ns == 16 ? 0 : 16) + jm);
+    float2 w1 = make_float2(t.x, t.y), w4 = make_float2(t.z, t.w);
+    if (INV) {
+      w1 = cconj(w1);
+      w4 = cconj(w4);
+    }
+    apply_pow16(vv, make_float2(1.f, 0.f), w1, w4);
   } else {
 #pragma unroll
     for (int q = 1; q < R; q++) v[q] = cmul(v[q], tw4096<INV>(tw, (q * jm * scale) & 4095));
@@ -223,6 +236,17 @@ __device__ __forceinline__ void twiddle_run(float2 (&v)[16], unsigned m, unsigne
                                             int log2n, const Twiddles& tw) {
   const unsigned mask = (1u << log2n) - 1u;
   apply_pow16(v, tw_big<INV>(tw, (m * j0) & mask, log2n), tw_big<INV>(tw, (m * T) & mask, log2n),
+              tw_big<INV>(tw, (4u * m * T) & mask, log2n));
+}
+
+// The same with the per-thread factor W_N^(m j0) given as base (forward
+// sign, e.g. from a per-row table read with consecutive addresses): the two
+// remaining look-ups are uniform across the threads of a row.
+template <bool INV>
+__device__ __forceinline__ void twiddle_run_base(float2 (&v)[16], float2 base, unsigned m,
+                                                 unsigned T, int log2n, const Twiddles& tw) {
+  const unsigned mask = (1u << log2n) - 1u;
+  apply_pow16(v, INV ? cconj(base) : base, tw_big<INV>(tw, (m * T) & mask, log2n),
               tw_big<INV>(tw, (4u * m * T) & mask, log2n));
 }
 

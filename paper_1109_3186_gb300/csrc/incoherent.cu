@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(256) k_fb_fft(float2* __restrict__ data, long 
   constexpr int C = 4096 / L;
   constexpr int T = L / 16;
   __shared__ float2 sm[FftTile<L, C>::SLOTS];
-  const Twiddles tw{twp.coarse, twp.fine};
+  const Twiddles tw{twp.coarse, twp.fine, twp.stage};
   const int jt = threadIdx.x % T, s = threadIdx.x / T;
   const long long r = (long long)blockIdx.x * C + s;
   const bool act = r < n_rows;

@@ -27,7 +27,18 @@ struct GroupGeom {
 struct TwiddlePtrs {
   const float2* coarse;  // exp(-2 pi j m / 4096), m < 4096
   const float2* fine;    // exp(-2 pi j m / 2^24), m < 4096
+  const float4* stage;   // radix-16 stage pairs (w, w^4), spans 16 and 256
 };
+// One buffer of kTwiddleElems float2 holds coarse | fine | stage.
+constexpr int kTwiddleElems = 8192 + 2 * (16 + 256);
+inline TwiddlePtrs twiddle_ptrs(const float2* buf) {
+  return TwiddlePtrs{buf, buf + 4096, reinterpret_cast<const float4*>(buf + 8192)};
+}
+// Fills such a buffer (FP64, rounded once).
+cudaError_t launch_build_twiddles(float2* buf, cudaStream_t st);
+// Row-pass twiddles of one group: rtw[k1 * (n2/16) + j] = exp(-2 pi j' (k1 j mod
+// nfft) / nfft) for k1 < n1, j < n2/16 (FP64, rounded once); nfft/16 entries.
+cudaError_t launch_build_row_twiddles(float2* rtw, const GroupGeom& g, cudaStream_t st);
 
 // ---- dedispersion kernels (dedisperse.cu) ----
 // spectra of every (antenna, block) of one group; spec [n_blk][n_ant][nfft]
@@ -56,9 +67,17 @@ long long inverse_chunk_sequences(const GroupGeom& g, long long n_seq);
 // Z[0 .. nq) = rows of IFFT of sequences q0.. after the chirp multiply and twiddle
 // With blk_list (device int array), the launch covers nq = n_listed * n_ant
 // sequences: listed block b, antenna a -> sequence b * n_ant + a.
+// rtw: the group's row-pass twiddles (launch_build_row_twiddles).
 cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, long long q0,
                                 long long nq, const GroupGeom& g, TwiddlePtrs tw,
-                                cudaStream_t st, const int* blk_list = nullptr, int n_ant = 1);
+                                const float2* rtw, cudaStream_t st,
+                                const int* blk_list = nullptr, int n_ant = 1);
+// The row pass of all (antenna, block) sequences of a group for n_dm DMs at
+// once: DM d multiplies by H + d h_stride and writes Z + d z_stride.
+cudaError_t launch_inverse_rows_multi(const float2* spec, float2* Z, long long z_stride,
+                                      const float2* H, long long h_stride, int n_dm,
+                                      long long nq, const GroupGeom& g, TwiddlePtrs tw,
+                                      const float2* rtw, cudaStream_t st);
 // The tensor-core beamformer's B image, written directly by the inverse
 // column pass (instead of y) when a Chimageator search runs in a tensor-core
 // mode: sample t in [t0, t1) of antenna a goes to tile (t - t0) >> log2_nt,

@@ -28,7 +28,7 @@ using namespace chirp;
 namespace {
 
 constexpr size_t kScratchBytes = (size_t)CHIRP_NOALLOC_SCRATCH_BYTES;
-constexpr size_t kTwiddleBytes = 8192 * sizeof(float2);
+constexpr size_t kTwiddleBytes = kTwiddleElems * sizeof(float2);
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -43,18 +43,6 @@ std::mutex g_dev_mu;
 thread_local char g_msg[256];
 
 size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
-
-// tw[m] = exp(-2 pi j m / 4096), tw[4096 + m] = exp(-2 pi j m / 2^24), m < 4096
-__global__ void k_noalloc_twiddles(float2* tw) {
-  int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= 4096) return;
-  const double two_pi = 6.283185307179586476925286766559;
-  double s, c;
-  sincos(-two_pi * (double)m / 4096.0, &s, &c);
-  tw[m] = make_float2((float)c, (float)s);
-  sincos(-two_pi * (double)m / 16777216.0, &s, &c);
-  tw[4096 + m] = make_float2((float)c, (float)s);
-}
 
 int bad(int code, const char* msg) {
   snprintf(g_msg, sizeof g_msg, "%s", msg);
@@ -77,8 +65,7 @@ int setup_device(cudaStream_t st, unsigned char** base) {
                cudaGetErrorString(e));
       return chirp_report_error(CHIRP_ECUDA, g_msg);
     }
-    k_noalloc_twiddles<<<16, 256, 0, st>>>((float2*)p);
-    e = cudaGetLastError();
+    e = launch_build_twiddles((float2*)p, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
       snprintf(g_msg, sizeof g_msg, "chirp_dedisperse_noalloc: set-up failed: %s",
@@ -140,9 +127,11 @@ extern "C" int chirp_dedisperse_noalloc(const void* volt, int n_ant, long long n
   if ((long long)n_ant * g.n_blk > 65535)
     return bad(CHIRP_EUNSUPPORTED, "chirp_dedisperse_noalloc: n_ant * blocks exceeds 65535");
 
-  // scratch layout: twiddles | FP64 phase table | FP32 chirp | spectra | inverse intermediate
+  // scratch layout: twiddles | row twiddles | FP64 phase table | FP32 chirp | spectra |
+  // inverse intermediate
   const size_t points = (size_t)n_ant * (size_t)g.n_blk * (size_t)nfft;
-  const size_t off_G = kTwiddleBytes;
+  const size_t off_R = align256(kTwiddleBytes);
+  const size_t off_G = align256(off_R + (size_t)nfft / 16 * sizeof(float2));
   const size_t off_H = align256(off_G + (size_t)nfft * sizeof(double));
   const size_t off_spec = align256(off_H + (size_t)nfft * sizeof(float2));
   const size_t off_Z = align256(off_spec + points * sizeof(float2));
@@ -158,7 +147,8 @@ extern "C" int chirp_dedisperse_noalloc(const void* volt, int n_ant, long long n
   unsigned char* base = nullptr;
   int rc = setup_device(st, &base);
   if (rc) return rc;
-  const TwiddlePtrs tw{(const float2*)base, (const float2*)base + 4096};
+  const TwiddlePtrs tw = twiddle_ptrs((const float2*)base);
+  float2* rtw = (float2*)(base + off_R);
   double* G = (double*)(base + off_G);
   float2* H = (float2*)(base + off_H);
   float2* spec = (float2*)(base + off_spec);
@@ -167,12 +157,13 @@ extern "C" int chirp_dedisperse_noalloc(const void* volt, int n_ant, long long n
   // nothing in the scratch has to start at zero: every region read below is
   // fully written first by this call; only the caller's output is cleared
   cudaError_t e = launch_build_phase_table(G, g, f0_hz, bw_hz, k_dm, st);
+  if (e == cudaSuccess) e = launch_build_row_twiddles(rtw, g, st);
   if (e == cudaSuccess) e = launch_forward((const float2*)volt, n_samp, n_ant, g, spec, tw, st);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(y_out, 0, (size_t)n_ant * (size_t)n_samp * sizeof(float2), st);
   if (e == cudaSuccess) e = launch_chirp_table(G, H, dm, g, st);
   const long long n_seq = (long long)n_ant * g.n_blk;
-  if (e == cudaSuccess) e = launch_inverse_rows(spec, Z, H, 0, n_seq, g, tw, st);
+  if (e == cudaSuccess) e = launch_inverse_rows(spec, Z, H, 0, n_seq, g, tw, rtw, st);
   if (e == cudaSuccess)
     e = launch_inverse_cols(Z, (float2*)y_out, n_samp, n_ant, 0, n_seq, g, n_hi, n_lo, tw, st);
   if (e != cudaSuccess) {

@@ -69,6 +69,7 @@ struct Group {
   std::vector<int> dms;
   double* d_G = nullptr;     // FP64 phase table, spectrum order
   float2* d_spec = nullptr;  // [n_blk][n_ant][nfft] (block-major sequences)
+  float2* d_rtw = nullptr;   // row-pass twiddles [n1][n2/16]
 };
 
 struct DmInfo {
@@ -103,10 +104,13 @@ struct chirp_plan {
   long long n_dump = 0;
   int n_pair = 0;
   // device workspace
-  float2* d_tw = nullptr;    // [8192]: coarse then fine
+  float2* d_tw = nullptr;    // [kTwiddleElems]: coarse, fine, stage pairs
   float2* d_x = nullptr;     // staging copy of host voltages [M][N]
   float2* d_Z = nullptr;     // inverse-row intermediate, largest group
-  float2* d_H = nullptr;     // FP32 chirp of the current DM, largest group
+  float2* d_H = nullptr;     // FP32 chirps of the current DMs [dm_chunk][h_stride]
+  int dm_chunk = 1;          // DMs of one group whose row passes run together
+  long long h_stride = 0;    // elements between chirp tables
+  size_t z_stride = 0;       // elements between the DMs' inverse workspaces
   float2* d_y = nullptr;     // dedispersed voltages of one DM [M][N]
   float2* d_W = nullptr;     // beam weights [n_pix][M]
   uint8_t* d_aimg = nullptr; // tensor-core A image (split-BF16 weights)
@@ -152,7 +156,7 @@ struct chirp_plan {
   double stage_ms[CHIRP_N_STAGES] = {0};
   long long stage_launches[CHIRP_N_STAGES] = {0};
 
-  TwiddlePtrs tw() const { return TwiddlePtrs{d_tw, d_tw + 4096}; }
+  TwiddlePtrs tw() const { return twiddle_ptrs(d_tw); }
 };
 
 namespace {
@@ -179,6 +183,7 @@ void release(chirp_plan* p) {
   if (p->stream) cudaStreamSynchronize(p->stream);
   for (auto& g : p->groups) {
     cudaFree(g.d_G);
+    cudaFree(g.d_rtw);
     cudaFree(g.d_spec);
   }
   cudaFree(p->d_tw);
@@ -253,11 +258,14 @@ cudaError_t autotune_split(chirp_plan* p, Group& g) {
       if (e != cudaSuccess) break;
       G.n2 = n2;
       G.n1 = (int)(G.nfft / n2);
+      e = launch_build_row_twiddles(g.d_rtw, G, p->stream);
+      if (e != cudaSuccess) break;
       auto pass = [&]() -> cudaError_t {
         cudaError_t r = launch_forward(p->d_y, p->N, p->M, G, g.d_spec, p->tw(), p->stream);
         for (long long q0 = 0; r == cudaSuccess && q0 < n_seq; q0 += nq) {
           const long long n = std::min(nq, n_seq - q0);
-          r = launch_inverse_rows(g.d_spec, p->d_Z, p->d_H, q0, n, G, p->tw(), p->stream);
+          r = launch_inverse_rows(g.d_spec, p->d_Z, p->d_H, q0, n, G, p->tw(), g.d_rtw,
+                                  p->stream);
           if (r == cudaSuccess)
             r = launch_inverse_cols(p->d_Z, p->d_y, p->N, p->M, q0, n, G, G.n_hi_max, G.n_lo_max,
                                     p->tw(), p->stream);
@@ -536,7 +544,7 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   }
 
   // ---- device workspace
-  rc = dev_alloc(p, (void**)&p->d_tw, 8192 * sizeof(float2), "twiddles");
+  rc = dev_alloc(p, (void**)&p->d_tw, kTwiddleElems * sizeof(float2), "twiddles");
   size_t z_elems = 0;
   for (auto& g : p->groups) {
     size_t elems = (size_t)p->M * g.geom.n_blk * g.geom.nfft;
@@ -544,11 +552,30 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
                                     (size_t)g.geom.nfft);
     if (!rc) rc = dev_alloc(p, (void**)&g.d_spec, elems * sizeof(float2), "spectra");
     if (!rc) rc = dev_alloc(p, (void**)&g.d_G, g.geom.nfft * sizeof(double), "phase table");
+    if (!rc)
+      rc = dev_alloc(p, (void**)&g.d_rtw, g.geom.nfft / 16 * sizeof(float2), "row twiddles");
   }
-  if (!rc) rc = dev_alloc(p, (void**)&p->d_Z, z_elems * sizeof(float2), "inverse workspace");
+  // Full searches run the row pass of up to 4 DMs of a group together (the
+  // spectrum is read once for them), each with its own workspace, as long
+  // as those workspaces stay within 4 GB and no group is chunked.
+  bool chunked = false;
+  for (auto& g : p->groups)
+    chunked |= inverse_chunk_sequences(g.geom, (long long)p->M * g.geom.n_blk) <
+               (long long)p->M * g.geom.n_blk;
+  p->dm_chunk = 1;
+  if (!chunked)
+    while (p->dm_chunk < 4 && (size_t)(p->dm_chunk + 1) * z_elems * sizeof(float2) <= (4ull << 30))
+      p->dm_chunk++;
+  p->z_stride = z_elems;
+  if (!rc)
+    rc = dev_alloc(p, (void**)&p->d_Z, (size_t)p->dm_chunk * z_elems * sizeof(float2),
+                   "inverse workspace");
   long long max_nfft = 0;
   for (auto& g : p->groups) max_nfft = std::max(max_nfft, g.geom.nfft);
-  if (!rc) rc = dev_alloc(p, (void**)&p->d_H, (size_t)max_nfft * sizeof(float2), "chirp table");
+  p->h_stride = max_nfft;
+  if (!rc)
+    rc = dev_alloc(p, (void**)&p->d_H, (size_t)p->dm_chunk * max_nfft * sizeof(float2),
+                   "chirp tables");
   if (!rc) rc = dev_alloc(p, (void**)&p->d_y, (size_t)p->M * p->N * sizeof(float2), "voltages");
   if (!rc && p->n_pix > 0)
     rc = dev_alloc(p, (void**)&p->d_W, (size_t)p->n_pix * p->M * sizeof(float2), "weights");
@@ -652,14 +679,6 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
     return rc;
   }
 
-  // ---- twiddles (FP64 on the host, rounded once)
-  std::vector<float2> tw(8192);
-  for (int m = 0; m < 4096; m++) {
-    double a = -2.0 * kPi * m / 4096.0;
-    tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
-    double b = -2.0 * kPi * m / 16777216.0;
-    tw[4096 + m] = make_float2((float)std::cos(b), (float)std::sin(b));
-  }
   // ---- beam weights W_pa = exp(+2 pi j f0 tau_a(l_p, m_p)), Eq. tau3D
   std::vector<float2> W((size_t)p->n_pix * p->M);
   for (int q = 0; q < p->n_pix; q++) {
@@ -672,8 +691,7 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
       W[(size_t)q * p->M + a] = make_float2((float)std::cos(ph), (float)std::sin(ph));
     }
   }
-  cudaError_t e = cudaMemcpyAsync(p->d_tw, tw.data(), tw.size() * sizeof(float2),
-                                  cudaMemcpyHostToDevice, p->stream);
+  cudaError_t e = launch_build_twiddles(p->d_tw, p->stream);
   if (e == cudaSuccess && p->n_pix > 0)
     e = cudaMemcpyAsync(p->d_W, W.data(), W.size() * sizeof(float2), cudaMemcpyHostToDevice,
                         p->stream);
@@ -698,9 +716,11 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   if (e == cudaSuccess && (cfg->flags & CHIRP_FLAG_AUTOTUNE) && cfg->fft_row == 0)
     for (auto& g : p->groups)
       if (e == cudaSuccess) e = autotune_split(p, g);
-  for (auto& g : p->groups)
+  for (auto& g : p->groups) {
     if (e == cudaSuccess)
       e = launch_build_phase_table(g.d_G, g.geom, p->f0, p->bw, p->kdm, p->stream);
+    if (e == cudaSuccess) e = launch_build_row_twiddles(g.d_rtw, g.geom, p->stream);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) {
     release(p);
@@ -827,7 +847,8 @@ int dedisperse_blocks(chirp_plan* p, int d, float2* y, long long b0, long long b
   for (long long q0 = b0 * p->M; q0 < q_end; q0 += nq) {
     const long long n = std::min(nq, q_end - q0);
     int mk = mark_begin(p);
-    CK(launch_inverse_rows(g.d_spec, p->d_Z, p->d_H, q0, n, g.geom, p->tw(), p->stream));
+    CK(launch_inverse_rows(g.d_spec, p->d_Z, p->d_H, q0, n, g.geom, p->tw(), g.d_rtw,
+                           p->stream));
     mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
     mk = mark_begin(p);
     CK(launch_inverse_cols(p->d_Z, y, p->N, p->M, q0, n, g.geom, I.n_hi, I.n_lo, p->tw(),
@@ -837,11 +858,11 @@ int dedisperse_blocks(chirp_plan* p, int d, float2* y, long long b0, long long b
   return CHIRP_OK;
 }
 
-int chirp_for(chirp_plan* p, int d) {
+int chirp_for(chirp_plan* p, int d, int slot = 0) {
   const DmInfo& I = p->dmi[d];
   int mk = mark_begin(p);
-  CK(launch_chirp_table(p->groups[I.group].d_G, p->d_H, p->dm[d], p->groups[I.group].geom,
-                        p->stream));
+  CK(launch_chirp_table(p->groups[I.group].d_G, p->d_H + (size_t)slot * p->h_stride, p->dm[d],
+                        p->groups[I.group].geom, p->stream));
   mark_end(p, CHIRP_STAGE_CHIRP, mk);
   return CHIRP_OK;
 }
@@ -927,6 +948,43 @@ int backend_dumps(chirp_plan* p, int d, Backend be, long long m0, long long m1, 
   return CHIRP_OK;
 }
 
+// The whole search with the row passes of up to dm_chunk DMs of a group in
+// one launch: per chunk the chirp tables, one multi-DM row pass, then per
+// DM the column pass (voltages or the beam image) and the back-end.
+int full_search_chunked(chirp_plan* p, Backend be, void* dout) {
+  for (auto& grp : p->groups) {
+    std::vector<int> dms;
+    for (int d : grp.dms)
+      if (p->dmi[d].last >= p->dmi[d].first) dms.push_back(d);
+    const GroupGeom& G = grp.geom;
+    const long long nq = (long long)p->M * G.n_blk;
+    for (size_t c0 = 0; c0 < dms.size(); c0 += (size_t)p->dm_chunk) {
+      const int n = (int)std::min((size_t)p->dm_chunk, dms.size() - c0);
+      for (int j = 0; j < n; j++) {
+        int rc = chirp_for(p, dms[c0 + j], j);
+        if (rc) return rc;
+      }
+      int mk = mark_begin(p);
+      CK(launch_inverse_rows_multi(grp.d_spec, p->d_Z, (long long)p->z_stride, p->d_H,
+                                   p->h_stride, n, nq, G, p->tw(), grp.d_rtw, p->stream));
+      mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
+      for (int j = 0; j < n; j++) {
+        const int d = dms[c0 + j];
+        const DmInfo& I = p->dmi[d];
+        const BeamImageOut img = fused_image(p, be) ? beam_image_for(p, d) : BeamImageOut{};
+        mk = mark_begin(p);
+        CK(launch_inverse_cols(p->d_Z + (size_t)j * p->z_stride, p->d_y, p->N, p->M, 0, nq, G,
+                               I.n_hi, I.n_lo, p->tw(), p->stream, nullptr,
+                               fused_image(p, be) ? &img : nullptr));
+        mark_end(p, CHIRP_STAGE_INV_COLS, mk);
+        int rc = backend_dumps(p, d, be, I.first, I.last + 1, dout);
+        if (rc) return rc;
+      }
+    }
+  }
+  return CHIRP_OK;
+}
+
 // The whole search, or (mask != NULL) only the (DM, dump) cells whose mask
 // byte is nonzero: for each DM the blocks owning a selected dump are inverse
 // transformed (runs of consecutive blocks per launch) and the back-end runs on
@@ -976,6 +1034,7 @@ int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Bac
                          cudaMemcpyHostToDevice, p->stream));
     }
   }
+  if (!mask && p->dm_chunk > 1) return full_search_chunked(p, be, dout);
   for (int d = 0; d < (int)p->dm.size(); d++) {
     const DmInfo& I = p->dmi[d];
     if (I.last < I.first) continue;
@@ -994,8 +1053,8 @@ int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Bac
     const int* blist = p->d_lists + blk_off[d];
     const int* dlist = p->d_lists + dmp_off[d];
     int mk = mark_begin(p);
-    CK(launch_inverse_rows(g.d_spec, p->d_Z, p->d_H, 0, blk_n[d] * p->M, G, p->tw(), p->stream,
-                           blist, p->M));
+    CK(launch_inverse_rows(g.d_spec, p->d_Z, p->d_H, 0, blk_n[d] * p->M, G, p->tw(), g.d_rtw,
+                           p->stream, blist, p->M));
     mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
     mk = mark_begin(p);
     const BeamImageOut img = fused_image(p, be) ? beam_image_for(p, d) : BeamImageOut{};
