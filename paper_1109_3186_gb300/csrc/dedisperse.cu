@@ -226,7 +226,6 @@ __global__ void __launch_bounds__(256, 4) k_inv_rows_multi(const float2* __restr
   const bool act = k1 < n1;
   const long long nfft = (long long)L * n1;
   const float2* src = spec + (long long)blockIdx.x * nfft + (long long)k1 * L;
-  const float2 rbase = act ? __ldg(rtw + (long long)k1 * T + jt) : make_float2(1.f, 0.f);
   for (int d = 0; d < n_dm; d++) {
     const float2* h = H + d * h_stride + (long long)k1 * L;
     float2 v[16];
@@ -236,7 +235,8 @@ __global__ void __launch_bounds__(256, 4) k_inv_rows_multi(const float2* __restr
     fft_core<L, C, true, true>(v, sm, s, jt, tw);
     if (act) {
       float2* dst = Z + d * z_stride + (long long)blockIdx.x * nfft + (long long)k1 * L;
-      twiddle_run_base<true>(v, rbase, (unsigned)k1, (unsigned)T, log2n, tw);
+      twiddle_run_base<true>(v, __ldg(rtw + (long long)k1 * T + jt), (unsigned)k1, (unsigned)T,
+                             log2n, tw);
 #pragma unroll
       for (int k = 0; k < 16; k++) dst[jt + k * T] = v[k];
     }
@@ -302,38 +302,39 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ 
       }
     }
     __syncthreads();
-    const long long nt_mask = (1LL << img.log2_nt) - 1;
+    // Owned positions inside the image's sample range: n in [nlo, nhi), at
+    // image sample u = u_blk + n.  The image is [8-sample chunk][k-group]
+    // [128 B] across its tiles, so chunk u >> 3 starts at (u >> 3) * grp_bytes.
+    const long long nlo = lo_b > img.t0 - base ? lo_b : img.t0 - base;
+    const long long nhi = hi_b < img.t1 - base ? hi_b : img.t1 - base;
+    const long long u_blk = base - img.t0;
     const size_t grp_bytes = (size_t)img.GB * 128;
-    const size_t tile_bytes = ((size_t)1 << img.log2_nt) / 8 * grp_bytes;
     // byte offset of antenna a's real row in a core-matrix column (imaginary: +16)
     const size_t a_ofs = (size_t)(a >> 2) * 128 + (size_t)(a & 3) * 32;
     const size_t tail_ofs = (size_t)img.G * 128;
-    auto owned = [&](long long n, long long t, int col) {
-      return col < n2 && n >= lo_b && n < hi_b && t >= img.t0 && t < img.t1;
-    };
+    const int col_blk = blockIdx.x * C;
     if constexpr (C >= 8) {
       constexpr int CPR = C / 8;  // 8-sample chunks per row
       const int n_work = (ncomp / 2) * L * CPR;
       for (int w = threadIdx.x; w < n_work; w += 256) {
         const int j = w % CPR, rp = w / CPR;
         const int row = rp % L, pair = rp / L;  // pair 0: head, 1: tail
-        const int col0 = blockIdx.x * C + 8 * j;
-        const long long n0 = (long long)row * n2 + col0;
-        const long long t0 = base + n0, u0 = t0 - img.t0;
+        const int col0 = col_blk + 8 * j;
+        const long long n0 = (long long)(row * n2 + col0);  // < nfft <= 2^24
+        const long long u0 = u_blk + n0;
         const __nv_bfloat16* s_re = stg + ((size_t)(2 * pair) * L + row) * C + 8 * j;
         const __nv_bfloat16* s_im = stg + ((size_t)(2 * pair + 1) * L + row) * C + 8 * j;
-        const size_t ofs = a_ofs + (pair ? tail_ofs : 0);
-        if ((u0 & 7) == 0 && owned(n0, t0, col0) && owned(n0 + 7, t0 + 7, col0 + 7)) {
-          uint8_t* dst = img.img + (size_t)(u0 >> img.log2_nt) * tile_bytes +
-                         (size_t)((u0 & nt_mask) >> 3) * grp_bytes + ofs;
+        uint8_t* dst0 = img.img + a_ofs + (pair ? tail_ofs : 0);
+        if ((u0 & 7) == 0 && n0 >= nlo && n0 + 8 <= nhi && col0 + 8 <= n2) {
+          uint8_t* dst = dst0 + (size_t)(u0 >> 3) * grp_bytes;
           *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(s_re);
           *reinterpret_cast<uint4*>(dst + 16) = *reinterpret_cast<const uint4*>(s_im);
         } else {
           for (int e = 0; e < 8; e++) {
-            if (!owned(n0 + e, t0 + e, col0 + e)) continue;
+            const long long n = n0 + e;
+            if (col0 + e >= n2 || n < nlo || n >= nhi) continue;
             const long long u = u0 + e;
-            uint8_t* dst = img.img + (size_t)(u >> img.log2_nt) * tile_bytes +
-                           (size_t)((u & nt_mask) >> 3) * grp_bytes + ofs + (size_t)(u & 7) * 2;
+            uint8_t* dst = dst0 + (size_t)(u >> 3) * grp_bytes + (size_t)(u & 7) * 2;
             *reinterpret_cast<__nv_bfloat16*>(dst) = s_re[e];
             *reinterpret_cast<__nv_bfloat16*>(dst + 16) = s_im[e];
           }
@@ -345,12 +346,11 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ 
       for (int w = threadIdx.x; w < n_work; w += 256) {
         const int col = w % C, rp = w / C;
         const int row = rp % L, pair = rp / L;
-        const int cc = blockIdx.x * C + col;
-        const long long n = (long long)row * n2 + cc, t = base + n;
-        if (!owned(n, t, cc)) continue;
-        const long long u = t - img.t0;
-        uint8_t* dst = img.img + (size_t)(u >> img.log2_nt) * tile_bytes +
-                       (size_t)((u & nt_mask) >> 3) * grp_bytes + a_ofs + (pair ? tail_ofs : 0) +
+        const int cc = col_blk + col;
+        const long long n = (long long)(row * n2 + cc);
+        if (cc >= n2 || n < nlo || n >= nhi) continue;
+        const long long u = u_blk + n;
+        uint8_t* dst = img.img + (size_t)(u >> 3) * grp_bytes + a_ofs + (pair ? tail_ofs : 0) +
                        (size_t)(u & 7) * 2;
         *reinterpret_cast<__nv_bfloat16*>(dst) = stg[((size_t)(2 * pair) * L + row) * C + col];
         *reinterpret_cast<__nv_bfloat16*>(dst + 16) = stg[((size_t)(2 * pair + 1) * L + row) * C + col];
