@@ -249,6 +249,7 @@ def stage_roofline(sc, plan, stage_ms, peaks, peak_kind, beam_mode, steps):
     n_pix = sc.pix_lm.shape[0]
     first, last = plan.dump_range()
     groups = {}
+    n_searched = {}
     fwd_pts = inv_pts = g_bytes = y_bytes = 0
     for d in range(len(sc.dms)):
         lay = plan.dm_layout(d)
@@ -257,7 +258,13 @@ def stage_roofline(sc, plan, stage_ms, peaks, peak_kind, beam_mode, steps):
         inv_pts += pts
         g_bytes += 8 * lay["nfft"]
         y_bytes += 8 * M * max(0, N - lay["n_hi"] - lay["n_lo"])
+        if last[d] >= first[d]:
+            n_searched[lay["nfft"]] = n_searched.get(lay["nfft"], 0) + 1
     fwd_pts = sum(groups.values())
+    # row pass: a group's spectra are read once per chunk of dm_chunk DMs; each
+    # DM reads its chirp table and writes its transformed rows
+    chunk = max(1, plan.info.get("dm_chunk", 1))
+    spec_reads = sum(8.0 * groups[g] * -(-n // chunk) for g, n in n_searched.items())
     hbm = peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
     sm_max = peaks.get("sm_max_mhz", FALLBACK_PEAKS["sm_max_mhz"])
     fp32_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
@@ -269,7 +276,7 @@ def stage_roofline(sc, plan, stage_ms, peaks, peak_kind, beam_mode, steps):
     stages = {
         "forward": ("hbm", 32.0 * fwd_pts, hbm, "GB/s"),
         "chirp": ("hbm", 2.0 * g_bytes, hbm, "GB/s"),
-        "inv_rows": ("hbm", 16.0 * inv_pts + g_bytes, hbm, "GB/s"),
+        "inv_rows": ("hbm", spec_reads + 8.0 * inv_pts + g_bytes, hbm, "GB/s"),
         "inv_cols": ("hbm", 8.0 * inv_pts + y_bytes, hbm, "GB/s"),
     }
     beam_flops = float(n_dump_valid) * L * n_pix * (8 * M + 3)
@@ -592,7 +599,7 @@ def run_ours(args):
                 if per is not None:  # bytes per valid-dump DM*sample x samples per launch
                     traffic = per * beam_dumps / n_pix * sc.dump_len / n_dm
             elif dom == "inv_rows":
-                per = committed_traffic(["dedisperse.cu", "fft.cuh"], "k_inv_rows<4096>")
+                per = committed_traffic(["dedisperse.cu", "fft.cuh"], "k_inv_rows_multi<4096>")
                 if per is not None:
                     traffic = per * plan.info["ifft_points"] / n_dm
             line["roofline"] = {"kernel": dom, "bound": r["bound"], "achieved": r["achieved"],

@@ -162,6 +162,9 @@ typedef struct {
   long long fb_samples;    /* T_fb of the incoherent search (0 when off)        */
   int beam_shape;          /* tensor-core beam kernel shape used (0: none)      */
   int corr_mode;           /* CHIRP_CORR_* actually used (AUTO resolved)        */
+  int dm_chunk;            /* trial DMs of one FFT-length group whose inverse
+                              row passes a full search runs in one launch (the
+                              group's spectra are read once for them)           */
 } chirp_plan_info;
 
 /* Create a plan: validates cfg, derives the per-DM FFT lengths and block

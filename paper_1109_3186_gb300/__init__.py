@@ -77,7 +77,8 @@ class _Info(ctypes.Structure):
                 ("n_group", ctypes.c_int), ("workspace_bytes", ctypes.c_longlong),
                 ("ifft_points", ctypes.c_longlong), ("valid_samples", ctypes.c_longlong),
                 ("beam_mode", ctypes.c_int), ("fb_samples", ctypes.c_longlong),
-                ("beam_shape", ctypes.c_int), ("corr_mode", ctypes.c_int)]
+                ("beam_shape", ctypes.c_int), ("corr_mode", ctypes.c_int),
+                ("dm_chunk", ctypes.c_int)]
 
 
 _lib = None

@@ -233,6 +233,25 @@ __device__ __forceinline__ void apply_pow16(float2 (&v)[16], float2 a, float2 w1
   }
 }
 
+// The same for a = 1: v[0] is left alone and the first row of powers is
+// w1, w2, w3 themselves (the products with an exact 1 are skipped).
+__device__ __forceinline__ void apply_pow16_unit(float2 (&v)[16], float2 w1, float2 w4) {
+  const float2 w2 = cmul(w1, w1);
+  const float2 w3 = cmul(w2, w1);
+  v[1] = cmul(v[1], w1);
+  v[2] = cmul(v[2], w2);
+  v[3] = cmul(v[3], w3);
+  float2 base = w4;
+#pragma unroll
+  for (int b = 1; b < 4; b++) {
+    v[4 * b] = cmul(v[4 * b], base);
+    v[4 * b + 1] = cmul(v[4 * b + 1], cmul(base, w1));
+    v[4 * b + 2] = cmul(v[4 * b + 2], cmul(base, w2));
+    v[4 * b + 3] = cmul(v[4 * b + 3], cmul(base, w3));
+    if (b < 3) base = cmul(base, w4);
+  }
+}
+
 // Stockham stage helpers -------------------------------------------------
 // One radix-R stage of span Ns over L points for butterfly j:
 //   in:  a[j + q L/R],  twiddle W_{Ns R}^{q (j mod Ns)},  DFT_R,
@@ -251,7 +270,7 @@ __device__ __forceinline__ void stage_twiddle(float2* v, int j, int Ns, const Tw
       w1 = cconj(w1);
       w4 = cconj(w4);
     }
-    apply_pow16(vv, make_float2(1.f, 0.f), w1, w4);
+    apply_pow16_unit(vv, w1, w4);
   } else {
 #pragma unroll
     for (int q = 1; q < R; q++) v[q] = cmul(v[q], tw4096<INV>(tw, (q * jm * scale) & 4095));

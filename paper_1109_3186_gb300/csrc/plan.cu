@@ -747,6 +747,7 @@ int chirp_plan_query(const chirp_plan* p, chirp_plan_info* info) {
   info->beam_mode = p->beam_mode;
   info->beam_shape = p->beam_shape;
   info->corr_mode = p->corr_mode;
+  info->dm_chunk = p->dm_chunk;
   info->fb_samples = p->T_fb;
   return CHIRP_OK;
 }

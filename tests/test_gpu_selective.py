@@ -1,5 +1,8 @@
 """The selective coherent search computes, in the selected (DM, dump) cells,
-what the full search computes there, and zeros elsewhere."""
+what the full search computes there, and zeros elsewhere.  The full search
+runs the inverse row pass of several DMs of a group in one launch, the
+selective search one DM at a time, so the bit-for-bit equality of the
+visibilities also pins the multi-DM row pass to the single-DM one."""
 import numpy as np
 import pytest
 
@@ -40,6 +43,9 @@ def test_selective_visibilities_equal_full():
     sc = skymodel.chirpolator_small(n_samp=1 << 18, n_dm=5, dm_max=100.0, nfft_min=1 << 15)
     x = sc.voltages()
     plan = chirp.Plan.from_scenario(sc)
+    assert plan.info["dm_chunk"] >= 2
+    first, last = plan.dump_range()
+    assert len(set(plan.dm_layout(d)["nfft"] for d in range(5))) < 5  # a group holds 2+ DMs
     full = np.empty((5, plan.n_dump, plan.n_pair), np.complex64)
     plan.chirpolator(x, full)
     mask = np.zeros((5, plan.n_dump), np.uint8)
