@@ -44,7 +44,6 @@ def test_selective_visibilities_equal_full():
     x = sc.voltages()
     plan = chirp.Plan.from_scenario(sc)
     assert plan.info["dm_chunk"] >= 2
-    first, last = plan.dump_range()
     assert len(set(plan.dm_layout(d)["nfft"] for d in range(5))) < 5  # a group holds 2+ DMs
     full = np.empty((5, plan.n_dump, plan.n_pair), np.complex64)
     plan.chirpolator(x, full)
