@@ -153,3 +153,61 @@ def test_precision_form_channel(k_dm):
     P3 = torch.empty_like(P)
     p3.chimageator(qd, P3)
     assert pow_error(P3.cpu().numpy(), Po) < TOL_POW
+
+
+def test_precision_form_slice_of_the_36_antenna_array(k_dm):
+    """The measurement slice of the 36-antenna precision form: one coarse
+    channel, 2^20 int8 samples, 8 trial DMs spanning its 0-2000 grid (FFT
+    groups 2^16 ... 2^20; the last group is one block holding four DMs, three
+    of which have no valid dump), 64 x 64 beams.  Sampled dumps of every DM
+    with valid output (its first, middle and last dumps, and the burst's dump)
+    against the oracle on the dequantised voltages: BF16 beams and BF16
+    correlation within 1e-2, split-BF16 beams and correlation within 1e-5;
+    DMs without valid dumps are all zero."""
+    sc = skymodel.precision_form(channel=3, n_samp=1 << 20, n_dm=256)
+    sc.dms = sc.dms[np.unique(np.linspace(0, 255, 8).round().astype(int))]
+    q, s, xf = _int8(sc)
+    qd = torch.from_numpy(q).cuda()
+    n_dm = len(sc.dms)
+    out = {}
+    for name, kw in (("p16", dict(beam_mode=chirp.BEAM_TC_BF16)),
+                     ("p3", dict(beam_mode=chirp.BEAM_TC_3XBF16)),
+                     ("v16", dict(corr_mode=chirp.CORR_TC_BF16)),
+                     ("v3", dict(corr_mode=chirp.CORR_TC_3XBF16))):
+        plan = chirp.Plan.from_scenario(sc, in_type=chirp.IN_CI8, in_scale=s, **kw)
+        if name.startswith("p"):
+            o = torch.empty((n_dm, plan.n_dump, plan.n_pix), dtype=torch.float32, device="cuda")
+            plan.chimageator(qd, o)
+        else:
+            o = torch.empty((n_dm, plan.n_dump, plan.n_pair), dtype=torch.complex64, device="cuda")
+            plan.chirpolator(qd, o)
+        plan.status()
+        out[name] = o.cpu().numpy()
+        first, last = plan.dump_range()
+        plan.close()
+    lay = [orc.layout(sc.dms, d, sc.f0, sc.bw, k_dm, sc.n_samp, sc.nfft_min) for d in range(n_dm)]
+    assert len({l["nfft"] for l in lay}) == 4 and lay[-1]["n_blk"] == 1
+    valid = [d for d in range(n_dm) if last[d] >= first[d]]
+    assert len(valid) == 5 and valid == list(range(5))
+    for d in range(5, n_dm):
+        for o in out.values():
+            assert np.all(o[d] == 0)
+    L = sc.dump_len
+    W = orc.beam_weights(sc.xyz, sc.pix_lm, sc.f0)
+    x128 = xf.astype(np.complex128)
+    p = sc.pulses[0]
+    d_p = int(np.argmin(np.abs(sc.dms - p.dm)))
+    for d in valid:
+        y = orc.dedisperse(x128, sc.f0, sc.bw, k_dm, sc.dms, d, sc.nfft_min)
+        f, l = int(first[d]), int(last[d])
+        spans = [(f, f + 1), ((f + l) // 2, (f + l) // 2 + 1), (l, l + 1)]
+        if d == d_p:
+            spans.append((int(p.t0 // L), int(p.t0 // L) + 1))
+        for m0, m1 in spans:
+            ys = y[:, m0 * L:m1 * L]
+            Po = orc.beamform(ys, W, L, m0, m1, f, l)
+            Vo = orc.correlate(ys, L, m0, m1, f, l)
+            assert pow_error(out["p16"][d, m0:m1], Po) < TOL_POW_BF16, (d, m0)
+            assert pow_error(out["p3"][d, m0:m1], Po) < TOL_POW, (d, m0)
+            assert vis_error(out["v16"][d, m0:m1], Vo, sc.n_ant) < TOL_VIS_BF16, (d, m0)
+            assert vis_error(out["v3"][d, m0:m1], Vo, sc.n_ant) < TOL_VIS, (d, m0)
