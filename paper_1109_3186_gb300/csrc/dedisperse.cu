@@ -8,9 +8,9 @@
 //             the twiddle W_N^(n2 k1), then row FFTs of length n2; the
 //             spectrum X[k1 + n1 k2] is left at position k1 n2 + k2;
 //   inverse:  row IFFTs of length n2 on that transposed spectrum with the
-//             chirp H_DM multiplied in on load and W_N^(-n2 k1) on store,
-//             then column IFFTs of length n1 that produce natural time order,
-//             scaled by 1/Nfft and scattered to the owned, valid samples.
+//             chirp H_DM / Nfft multiplied in on load and W_N^(-n2 k1) on
+//             store, then column IFFTs of length n1 that produce natural
+//             time order, scattered to the owned, valid samples.
 // The forward spectra do not depend on the DM and are computed once per
 // FFT-length group; the inverse pair runs once per trial DM.
 //
@@ -117,19 +117,22 @@ __global__ void k_phase_table(double* __restrict__ G, long long nfft, int n1, in
 }
 
 // ------------------------------------------------------------------ chirp
-// H[pos] = exp(-2 pi j frac(DM G[pos])) for one trial DM, in the spectrum's
-// order.  The product DM G and its reduction c - rint(c) are FP64 (the phase
-// reaches ~1e6 cycles at high DM); only the reduced fraction |r| <= 1/2 is
-// rounded to FP32, and the chirp is stored as FP32 complex.
+// H[pos] = exp(-2 pi j frac(DM G[pos])) / Nfft for one trial DM, in the
+// spectrum's order.  The product DM G and its reduction c - rint(c) are FP64
+// (the phase reaches ~1e6 cycles at high DM); only the reduced fraction
+// |r| <= 1/2 is rounded to FP32, and the chirp is stored as FP32 complex.
+// The inverse transform's 1/Nfft rides on the chirp: Nfft is a power of two,
+// so the scaling is exact and commutes with every rounding of the inverse
+// FFT (the outputs equal those of scaling at the end, bit for bit).
 __global__ void k_chirp_table(const double* __restrict__ G, float2* __restrict__ H, double dm,
-                              long long nfft) {
+                              long long nfft, float inv_nfft) {
   long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pos >= nfft) return;
   double c = __dmul_rn(dm, G[pos]);
   double r = __dsub_rn(c, rint(c));  // exact
   float sn, cs;
   sincospif(-2.0f * (float)r, &sn, &cs);
-  H[pos] = make_float2(cs, sn);
+  H[pos] = make_float2(cs * inv_nfft, sn * inv_nfft);
 }
 
 // ------------------------------------------------------------------ twiddles
@@ -244,8 +247,8 @@ __global__ void __launch_bounds__(256, 4) k_inv_rows_multi(const float2* __restr
   }
 }
 
-// Column pass of the inverse: natural-order output, 1/Nfft, overlap-save
-// discard and ownership.  Block b owns block positions [lo_b, hi_b).
+// Column pass of the inverse: natural-order output, overlap-save discard and
+// ownership.  Block b owns block positions [lo_b, hi_b).
 // IMG: instead of y, the owned samples inside [img.t0, img.t1) go to the
 // beamformer's BF16 image (MN-major core matrices: a 16-byte row holds 8
 // consecutive samples of one real component; head rounded to nearest BF16,
@@ -281,7 +284,7 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ 
   const long long base = b * step;
   const long long lo_b = (b == 0) ? n_hi : n_hi_max;
   const long long hi_b = (b == n_blk - 1) ? (n_samp - n_lo - base) : (n_hi_max + step);
-  const float scale = 1.0f / (float)nfft;  // exact: power of two
+  // (1/Nfft was applied with the chirp)
   if constexpr (IMG) {
     // staging [component][row][column] of BF16: components re_h, im_h (, re_l, im_l)
     __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(sm);
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ 
 #pragma unroll
     for (int k = 0; k < 16; k++) {
       const int row = jt + k * T;
-      const float2 val = cscale(v[k], scale);
+      const float2 val = v[k];
       const __nv_bfloat162 h = __floats2bfloat162_rn(val.x, val.y);
       stg[(0 * L + row) * C + s] = h.x;
       stg[(1 * L + row) * C + s] = h.y;
@@ -316,24 +319,39 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ 
     if constexpr (C >= 8) {
       constexpr int CPR = C / 8;  // 8-sample chunks per row
       const int n_work = (ncomp / 2) * L * CPR;
+      // Block positions n0 = row * n2 + col0 are multiples of 8, so a chunk
+      // starts on an image chunk boundary when u_blk does; the owned range
+      // clamped to [0, Nfft] fits 32 bits, and chunk addresses are offsets
+      // from the block's first chunk.
+      const bool aligned = (u_blk & 7) == 0;
+      const int nlo32 = (int)(nlo < 0 ? 0 : (nlo > nfft ? nfft : nlo));
+      const int nhi32 = (int)(nhi < 0 ? 0 : (nhi > nfft ? nfft : nhi));
+      uint8_t* const dst_blk = img.img + a_ofs + (aligned ? (u_blk >> 3) * (long long)grp_bytes : 0);
       for (int w = threadIdx.x; w < n_work; w += 256) {
         const int j = w % CPR, rp = w / CPR;
         const int row = rp % L, pair = rp / L;  // pair 0: head, 1: tail
         const int col0 = col_blk + 8 * j;
-        const long long n0 = (long long)(row * n2 + col0);  // < nfft <= 2^24
-        const long long u0 = u_blk + n0;
-        const __nv_bfloat16* s_re = stg + ((size_t)(2 * pair) * L + row) * C + 8 * j;
-        const __nv_bfloat16* s_im = stg + ((size_t)(2 * pair + 1) * L + row) * C + 8 * j;
-        uint8_t* dst0 = img.img + a_ofs + (pair ? tail_ofs : 0);
-        if ((u0 & 7) == 0 && n0 >= nlo && n0 + 8 <= nhi && col0 + 8 <= n2) {
-          uint8_t* dst = dst0 + (size_t)(u0 >> 3) * grp_bytes;
-          *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(s_re);
-          *reinterpret_cast<uint4*>(dst + 16) = *reinterpret_cast<const uint4*>(s_im);
-        } else {
+        const int n0 = row * n2 + col0;  // < nfft <= 2^24
+        const __nv_bfloat16* s_re = stg + ((2 * pair) * L + row) * C + 8 * j;
+        const __nv_bfloat16* s_im = s_re + L * C;
+        const size_t pofs = pair ? tail_ofs : 0;
+        if (aligned && n0 >= nlo32 && n0 + 8 <= nhi32 && col0 + 8 <= n2) {
+          // the real and imaginary rows are one 32-byte sector (32-byte
+          // aligned: allocation base, 32-byte antenna rows, 128-byte groups):
+          // one 256-bit store
+          uint8_t* dst = dst_blk + pofs + (size_t)(n0 >> 3) * grp_bytes;
+          const uint4 re = *reinterpret_cast<const uint4*>(s_re);
+          const uint4 im = *reinterpret_cast<const uint4*>(s_im);
+          asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                       :: "l"(dst), "r"(re.x), "r"(re.y), "r"(re.z), "r"(re.w), "r"(im.x),
+                          "r"(im.y), "r"(im.z), "r"(im.w)
+                       : "memory");
+        } else if (n0 + 8 > nlo32 && n0 < nhi32) {
+          uint8_t* dst0 = img.img + a_ofs + pofs;
           for (int e = 0; e < 8; e++) {
-            const long long n = n0 + e;
-            if (col0 + e >= n2 || n < nlo || n >= nhi) continue;
-            const long long u = u0 + e;
+            const int n = n0 + e;
+            if (col0 + e >= n2 || n < nlo32 || n >= nhi32) continue;
+            const long long u = u_blk + n;
             uint8_t* dst = dst0 + (size_t)(u >> 3) * grp_bytes + (size_t)(u & 7) * 2;
             *reinterpret_cast<__nv_bfloat16*>(dst) = s_re[e];
             *reinterpret_cast<__nv_bfloat16*>(dst + 16) = s_im[e];
@@ -362,7 +380,7 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ 
 #pragma unroll
     for (int k = 0; k < 16; k++) {
       long long n = (long long)(jt + k * T) * n2 + c;
-      if (n >= lo_b && n < hi_b) ya[base + n] = cscale(v[k], scale);
+      if (n >= lo_b && n < hi_b) ya[base + n] = v[k];
     }
   }
 }
@@ -428,7 +446,7 @@ cudaError_t launch_build_row_twiddles(float2* rtw, const GroupGeom& g, cudaStrea
 cudaError_t launch_chirp_table(const double* G, float2* H, double dm, const GroupGeom& g,
                                cudaStream_t st) {
   long long blocks = (g.nfft + 255) / 256;
-  k_chirp_table<<<(unsigned)blocks, 256, 0, st>>>(G, H, dm, g.nfft);
+  k_chirp_table<<<(unsigned)blocks, 256, 0, st>>>(G, H, dm, g.nfft, ldexpf(1.0f, -g.log2n));
   return cudaGetLastError();
 }
 

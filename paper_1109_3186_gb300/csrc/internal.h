@@ -51,7 +51,8 @@ cudaError_t launch_forward(const void* x, long long n_samp, int n_ant, const Gro
 // G[pos] = k_dm f^2/(f0^2 (f0 + f)) in the spectrum's (transposed) order, FP64
 cudaError_t launch_build_phase_table(double* G, const GroupGeom& g, double f0, double bw,
                                      double k_dm, cudaStream_t st);
-// H[pos] = exp(-2 pi j frac(dm G[pos])), FP64 phase, FP32 complex result
+// H[pos] = exp(-2 pi j frac(dm G[pos])) / nfft, FP64 phase, FP32 complex result
+// (the inverse FFT's normalisation, exact: nfft is a power of two)
 cudaError_t launch_chirp_table(const double* G, float2* H, double dm, const GroupGeom& g,
                                cudaStream_t st);
 // The inverse can run over chunks of (antenna, block) sequences [q0, q0 + nq)
