@@ -115,3 +115,49 @@ def test_auto_correlation_mode_and_refusals():
     assert ei.value.code == -5
     sc.dump_len = 1024
     assert chirp.Plan.from_scenario(sc).info["corr_mode"] == chirp.CORR_TC_3XBF16
+
+
+_LONG = {}
+
+
+def _long_case(M, N, dms, nfft_min, n_side, k_dm):
+    """Scenario, voltages and oracle powers of a case whose FFT groups have
+    column lengths of 1024 or more (the column pass writes the beam image
+    sample by sample there), computed once per module."""
+    key = (M, N, tuple(dms), nfft_min, n_side)
+    if key not in _LONG:
+        sc = skymodel.chimageator_medium(n_samp=N, n_dm=len(dms), n_ant=M, dm_max=max(dms),
+                                         nfft_min=nfft_min, dump_len=4096, n_side=n_side,
+                                         n_pulse=1)
+        sc.dms = np.array(dms)
+        x = sc.voltages()
+        Po = orc.chimageator(x, sc.f0, sc.bw, k_dm, sc.dms, nfft_min, 4096, sc.xyz, sc.pix_lm)
+        _LONG[key] = (sc, x, Po)
+    return _LONG[key]
+
+
+LONG_CASES = [
+    (4, 1 << 23, [0.0, 300.0, 700.0], 1 << 22, 2),   # columns of 1024 (3 blocks) and 2048
+    (2, 1 << 24, [0.0, 900.0], 1 << 24, 1),          # columns of 4096: one 2^24 block
+]
+
+
+@pytest.mark.parametrize("mode", [chirp.BEAM_TC_3XBF16, chirp.BEAM_TC_BF16],
+                         ids=["tc_3xbf16", "tc_bf16"])
+@pytest.mark.parametrize("M,N,dms,nfft_min,n_side", LONG_CASES,
+                         ids=["M%d_N%d" % (c[0], c[1]) for c in LONG_CASES])
+def test_chimageator_long_transforms(M, N, dms, nfft_min, n_side, mode, k_dm):
+    sc, x, Po = _long_case(M, N, dms, nfft_min, n_side, k_dm)
+    plan = chirp.Plan.from_scenario(sc, beam_mode=mode)
+    assert plan.info["beam_mode"] == mode
+    assert max(plan.dm_layout(d)["nfft"] for d in range(len(dms))) >= 1 << 23
+    P = torch.empty((len(dms), plan.n_dump, plan.n_pix), dtype=torch.float32, device="cuda")
+    plan.chimageator(torch.from_numpy(x).cuda(), P)
+    plan.status()
+    Pg = P.cpu().numpy()
+    first, last = plan.dump_range()
+    for d in range(len(dms)):
+        assert np.all(Pg[d, :first[d]] == 0) and np.all(Pg[d, last[d] + 1:] == 0)
+    tol = TOL_POW if mode == chirp.BEAM_TC_3XBF16 else 1e-2
+    assert pow_error(Pg, Po) < tol
+    plan.close()

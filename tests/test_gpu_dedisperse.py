@@ -29,6 +29,8 @@ CASES = [
     (1.4e9, 32e6, 2, 1 << 19, [0.0, 10.0, 30.0], 1 << 17), # 32 x 4096
     (1.4e9, 32e6, 1, 1 << 20, [0.0, 60.0], 1 << 18),       # 64 x 4096 and 2^19
     (1.4e9, 32e6, 1, 1 << 20, [150.0], 1 << 18),           # 2^20 = 256 x 4096 single block
+    (1.4e9, 32e6, 1, 1 << 23, [0.0, 300.0, 700.0], 1 << 22),  # 1024 x 4096 (3 blocks), 2048 x 4096
+    (1.4e9, 32e6, 1, 1 << 24, [0.0, 900.0], 1 << 24),      # 4096 x 4096: the largest transform
 ]
 
 
