@@ -14,7 +14,7 @@
 // The forward spectra do not depend on the DM and are computed once per
 // FFT-length group; the inverse pair runs once per trial DM.
 //
-// Chirp phase (Eq. 1 integrated over frequency; the benchmark spec precision rule):
+// Chirp phase (Eq. 1 integrated over frequency; FP64 only for the phase):
 // the DM-independent table G = k_dm f^2/(f0^2 (f0+f)) is built in FP64, the
 // per-DM phase c = DM G is formed and range-reduced (c - rint c) in FP64, and
 // only the reduced fraction is converted to FP32 for sincospif.

@@ -5,7 +5,8 @@ calibration split so that it keeps >= 96 % of the bursts the full DM grid
 detects (candidates of chirp_detect: local S/N maxima >= 7), and on held-out segments it (a) keeps >= 93 % of the full-grid
 detections, (b) selects under 35 % of the (DM, dump) cells, and (c) the
 selective coherent search over those cells runs faster than the full grid and
-reproduces the full grid's outputs there.  The full grid is the judge.  (The
+reproduces the full grid's outputs there.  Recall is measured against the
+full grid's detections.  (The
 bursts it still misses sit at the coherent detection limit, where the
 antenna-incoherent power the proposer reads is sqrt(M) times weaker.)"""
 import time
