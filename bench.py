@@ -58,6 +58,9 @@ def parse_args():
                          "3 visibility quadratic form, 4 tcgen05 BF16 (reduced precision)")
     ap.add_argument("--no-alt", action="store_true",
                     help="skip the extra timings of the other beam modes and of detection")
+    ap.add_argument("--chirpolator-only", action="store_true",
+                    help="time only the Chirpolator search on the same workload (for profiling "
+                         "its kernels); prints one line with its per-step and per-stage times")
     ap.add_argument("--cpu-dumps", type=int, default=640,
                     help="dumps per selected DM in the oracle's bounded CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -474,6 +477,38 @@ def extra_forms(sc, plan, xd, stream, args):
     return out
 
 
+def chirpolator_only(sc, x, stream, args):
+    """The Chirpolator search alone on the benchmark's observation: W warm-up
+    and K timed steps, CUDA events on the plan's stream; one JSON line."""
+    import torch
+    import paper_1109_3186_gb300 as chirp
+    plan = chirp.Plan.from_scenario(sc, stream=stream)
+    xd = torch.from_numpy(x).cuda()
+    V = torch.empty((len(sc.dms), plan.n_dump, plan.n_pair), dtype=torch.complex64, device="cuda")
+    for _ in range(args.warmup):
+        plan.chirpolator(xd, V)
+    torch.cuda.synchronize()
+    plan.stage_timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.chirpolator(xd, V)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    stage = plan.stage_timing(False)
+    plan.status()
+    ms = e0.elapsed_time(e1) / args.steps
+    line = {"mode": "chirpolator", "ms_per_step": ms, "steps": args.steps,
+            "value": plan.info["valid_samples"] / (ms * 1e-3), "unit": UNIT,
+            "corr_mode": {1: "fp32_simt", 2: "tc_3xbf16", 3: "tc_bf16"}[plan.info["corr_mode"]],
+            "stages_ms": {k: v[0] / args.steps for k, v in stage.items() if v[1]},
+            "config": config_block(sc, 1)}
+    print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
 def run_ours(args):
     import torch
     import paper_1109_3186_gb300 as chirp
@@ -496,6 +531,8 @@ def run_ours(args):
     sc = scenario(rank, args)
     x = sc.voltages()
     stream = torch.cuda.current_stream()
+    if args.chirpolator_only:
+        return chirpolator_only(sc, x, stream, args)
     plan = chirp.Plan.from_scenario(sc, beam_mode=args.beam_mode, stream=stream)
     n_dm, n_dump, n_pix = len(sc.dms), plan.n_dump, plan.n_pix
     xd = torch.from_numpy(x).cuda()

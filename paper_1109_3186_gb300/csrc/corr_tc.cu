@@ -16,7 +16,11 @@
 // Rows are grouped 8 per 4 antennas (G = ceil(M / 4) groups): head rows
 // 0 .. 8G-1 (rows of absent antennas zero), tail rows 8G .. 16G-1.
 //
-// The kernel reads the FP32 voltages y [M][N] once.  Two groups of 4
+// The kernel reads the FP32 voltages y [M][N] once: a loader warp streams
+// each chunk's antenna rows into a ring of raw FP32 stages with bulk copies
+// (several chunks ahead, so that enough bytes are in flight to stream HBM);
+// where the rows are not 16-byte aligned (odd N) or the ring does not fit,
+// the producers load y themselves.  Two groups of 4
 // producer warps convert alternate chunks of kc samples into the BF16
 // operand (K-major, no swizzle: core matrices of 8 rows x 8 samples; the
 // k-groups of a row group 144 B apart, row groups SBO apart) in a ring of
@@ -47,9 +51,11 @@ namespace {
 constexpr int kProdWarps = 8;                 // two groups of 4
 constexpr int kIssuerWarp = kProdWarps;       // also allocates TMEM
 constexpr int kEpiWarp0 = kProdWarps + 1;     // 4 epilogue warps
-constexpr int kCorrThreads = 32 * (kEpiWarp0 + 4);
+constexpr int kLoaderWarp = kEpiWarp0 + 4;    // bulk copies of the raw voltages
+constexpr int kCorrThreads = 32 * (kLoaderWarp + 1);
 constexpr int kMaxStages = 4;
 constexpr int kMaxAcc = 4;
+constexpr int kMaxRaw = 4;
 constexpr uint32_t kCorrSmemLimit = 227u * 1024u;
 // Stride between the K-adjacent core matrices of a row group: 128 B plus a
 // 16-byte gap, so that the producer lanes writing consecutive 8-sample
@@ -58,13 +64,39 @@ constexpr uint32_t kLbo = 144;
 constexpr int kBatch = 4;                     // producer items loaded together
 
 struct CorrGeom {
-  int G, KR, n_rt, NC, Npad, nacc, kc, nst;
-  uint32_t sbo, stage_stride, stage_region, dsm_off, bar_off, total;
+  int G, KR, n_rt, NC, Npad, nacc, kc, nst, nraw;
+  uint32_t sbo, stage_stride, stage_region, dsm_off, bar_off, total, raw_off, raw_stride;
 };
+
+// Stage plan for chunks of kc samples and nst stages; nraw raw FP32 stages
+// (M rows of kc float2 each) after the barriers, or none.  Returns the bytes.
+__host__ __device__ inline uint32_t corr_plan(CorrGeom* g, int M, int kc, int nst, int nraw) {
+  g->kc = kc;
+  g->nst = nst;
+  g->sbo = (uint32_t)(kc / 8) * kLbo;
+  const uint32_t groups = (uint32_t)(g->KR + 7) / 8;
+  g->stage_stride = groups * g->sbo;
+  // the MMA windows of the last stage may run into the staging, the
+  // barriers and the raw ring (only accumulator rows that are never read
+  // come from there): they only have to stay inside the allocation
+  const uint32_t window = (uint32_t)g->n_rt * 16u * g->sbo;
+  g->stage_region = (uint32_t)nst * g->stage_stride;
+  g->dsm_off = g->stage_region;
+  g->bar_off = (g->dsm_off + (uint32_t)g->KR * (g->NC + 1) * 4u + 15u) & ~15u;
+  g->nraw = nraw;
+  g->raw_stride = ((uint32_t)M * (uint32_t)kc * 8u + 127u) & ~127u;
+  g->raw_off = (g->bar_off + 256u + 127u) & ~127u;
+  const uint32_t end = nraw > 0 ? g->raw_off + (uint32_t)nraw * g->raw_stride : g->bar_off + 256;
+  const uint32_t last_window_end = (uint32_t)(nst - 1) * g->stage_stride + window;
+  g->total = end > last_window_end ? end : last_window_end;
+  return g->total;
+}
 
 // Shared-memory plan: the stages (each KR rows of kc samples), the staging
 // of one accumulator (KR x (NC + 1) floats) and the barriers, with the
-// allocation long enough for the 128-row windows the MMAs read.
+// allocation long enough for the 128-row windows the MMAs read; then, with
+// the same chunk length, as deep a raw ring as fits (giving up stages down
+// to two for it), else none.
 __host__ __device__ inline bool corr_geom(int M, int terms, int L, CorrGeom* g) {
   if (L % 16 != 0) return false;
   g->G = (M + 3) / 4;
@@ -79,21 +111,12 @@ __host__ __device__ inline bool corr_geom(int M, int terms, int L, CorrGeom* g) 
   for (int kc = 256; kc >= 128; kc -= 128) {
     if (L % kc != 0 && kc % L != 0) continue;  // chunks and dumps must line up
     for (int nst = kMaxStages; nst >= 2; nst--) {
-      g->kc = kc;
-      g->nst = nst;
-      g->sbo = (uint32_t)(kc / 8) * kLbo;
-      const uint32_t groups = (uint32_t)(g->KR + 7) / 8;
-      g->stage_stride = groups * g->sbo;
-      // the MMA windows of the last stage may run into the staging and the
-      // barriers (only accumulator rows that are never read come from there):
-      // they only have to stay inside the allocation
-      const uint32_t window = (uint32_t)g->n_rt * 16u * g->sbo;
-      g->stage_region = (uint32_t)nst * g->stage_stride;
-      g->dsm_off = g->stage_region;
-      g->bar_off = (g->dsm_off + (uint32_t)g->KR * (g->NC + 1) * 4u + 15u) & ~15u;
-      const uint32_t last_window_end = (uint32_t)(nst - 1) * g->stage_stride + window;
-      g->total = g->bar_off + 256 > last_window_end ? g->bar_off + 256 : last_window_end;
-      if (g->total <= kCorrSmemLimit) return true;
+      if (corr_plan(g, M, kc, nst, 0) > kCorrSmemLimit) continue;
+      for (int ns = nst; ns >= 2; ns--)
+        for (int nraw = kMaxRaw; nraw >= 2; nraw--)
+          if (corr_plan(g, M, kc, ns, nraw) <= kCorrSmemLimit) return true;
+      corr_plan(g, M, kc, nst, 0);
+      return true;
     }
   }
   return false;
@@ -108,6 +131,7 @@ struct CorrArgs {
   long long n_dumps;
   long long dumps_per_cta;
   int M, L, terms;
+  int raw_path;         // the loader streams y into the raw ring (rows 16-byte aligned)
   CorrGeom g;
 };
 
@@ -121,7 +145,9 @@ __global__ void __launch_bounds__(kCorrThreads, 1) k_corr_tc(CorrArgs args) {
   uint64_t* accf = empty + kMaxStages;              // [kMaxAcc]
   uint64_t* acce = accf + kMaxAcc;                  // [kMaxAcc]
   uint64_t* drain = acce + kMaxAcc;
-  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  uint64_t* raw_full = drain + 1;                   // [kMaxRaw]
+  uint64_t* raw_empty = raw_full + kMaxRaw;         // [kMaxRaw]
+  uint32_t* tmem_slot = (uint32_t*)(raw_empty + kMaxRaw);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -145,6 +171,10 @@ __global__ void __launch_bounds__(kCorrThreads, 1) k_corr_tc(CorrArgs args) {
       tc::mbar_init(&acce[a], 4);  // every epilogue warp arrives once
     }
     tc::mbar_init(drain, 1);
+    for (int r = 0; r < kMaxRaw; r++) {
+      tc::mbar_init(&raw_full[r], 1);      // the loader's expect-tx arrival
+      tc::mbar_init(&raw_empty[r], 4 * 32);  // the threads of one producer group
+    }
     *abort_flag = 0;
     tc::fence_mbar_init();
   }
@@ -166,6 +196,7 @@ __global__ void __launch_bounds__(kCorrThreads, 1) k_corr_tc(CorrArgs args) {
       // group e) -> 4 rows (head re/im, tail re/im) of 16 bytes each
       const int pg = warp / 4, ptid = threadIdx.x % 128;
       const int groups_per_chunk = kc / 8;
+      const uint8_t* raw = smem + g.raw_off;
       for (long long i = pg; i < n_chunks; i += 2) {
         const int s = (int)(i % nst);
         const uint32_t ph = (uint32_t)((i / nst) & 1);
@@ -176,60 +207,85 @@ __global__ void __launch_bounds__(kCorrThreads, 1) k_corr_tc(CorrArgs args) {
         const long long tc0 = ta + i * kc;
         const int n_groups = (int)min((long long)groups_per_chunk, (tb - tc0) / 8);
         uint8_t* st = stages + (size_t)s * g.stage_stride;
-        // items are handled in batches of kBatch per thread whose loads are all
-        // issued before any is used (16-byte loads where the row is aligned),
-        // so that enough bytes are in flight to stream y at full bandwidth
         const int n_items = M * n_groups;
-        for (int it0 = 0; it0 < n_items; it0 += 128 * kBatch) {
-          float4 raw[kBatch][4];
+        // samples 8e .. 8e + 7 of antenna a (as 4 float4: re, im of two
+        // samples each) -> the 4 rows of the item
+        auto convert = [&](int a, int e, const float4 (&v4)[4]) {
+          uint32_t hr[4], hi[4], lr[4], li[4];
 #pragma unroll
-          for (int b = 0; b < kBatch; b++) {
-            const int it = it0 + b * 128 + ptid;
-            if (it < n_items) {
-              const int a = it / n_groups, e = it % n_groups;
-              const long long off = (long long)a * args.n_samp + tc0 + 8 * e;
-              if ((off & 1) == 0) {
-                const float4* src = reinterpret_cast<const float4*>(args.y + off);
+          for (int j = 0; j < 4; j++) {  // samples 2j, 2j + 1 of the group
+            const float4 v = v4[j];
+            const __nv_bfloat162 h_r = __floats2bfloat162_rn(v.x, v.z);
+            const __nv_bfloat162 h_i = __floats2bfloat162_rn(v.y, v.w);
+            const float2 fr = __bfloat1622float2(h_r), fi = __bfloat1622float2(h_i);
+            const __nv_bfloat162 l_r = __floats2bfloat162_rn(v.x - fr.x, v.z - fr.y);
+            const __nv_bfloat162 l_i = __floats2bfloat162_rn(v.y - fi.x, v.w - fi.y);
+            hr[j] = *reinterpret_cast<const uint32_t*>(&h_r);
+            hi[j] = *reinterpret_cast<const uint32_t*>(&h_i);
+            lr[j] = *reinterpret_cast<const uint32_t*>(&l_r);
+            li[j] = *reinterpret_cast<const uint32_t*>(&l_i);
+          }
+          auto put = [&](int row, const uint32_t (&w)[4]) {
+            *reinterpret_cast<uint4*>(st + (size_t)(row / 8) * g.sbo + (size_t)e * kLbo +
+                                      (size_t)(row % 8) * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+          };
+          put(2 * a, hr);
+          put(2 * a + 1, hi);
+          if (args.terms == 3) {
+            put(g.NC + 2 * a, lr);
+            put(g.NC + 2 * a + 1, li);
+          }
+        };
+        if (args.raw_path) {
+          // the chunk's rows arrive in raw stage r by bulk copy (a ring in
+          // chunk order; each phase of a slot has one consumer group)
+          const int r = (int)(i % g.nraw);
+          const uint32_t rph = (uint32_t)((i / g.nraw) & 1);
+          if (!tc::mbar_wait(&raw_full[r], rph, abort_flag)) {
+            raise();
+            break;
+          }
+          const uint8_t* rs = raw + (size_t)r * g.raw_stride;
+          for (int it = ptid; it < n_items; it += 128) {
+            const int a = it / n_groups, e = it % n_groups;
+            const float4* src = reinterpret_cast<const float4*>(rs + ((size_t)a * kc + 8 * e) * 8);
+            float4 v4[4];
 #pragma unroll
-                for (int j = 0; j < 4; j++) raw[b][j] = src[j];
-              } else {
-                const float2* src = args.y + off;
+            for (int j = 0; j < 4; j++) v4[j] = src[j];
+            convert(a, e, v4);
+          }
+          tc::mbar_arrive(&raw_empty[r]);
+        } else {
+          // items are handled in batches of kBatch per thread whose loads are all
+          // issued before any is used (16-byte loads where the row is aligned),
+          // so that more bytes are in flight
+          for (int it0 = 0; it0 < n_items; it0 += 128 * kBatch) {
+            float4 rawv[kBatch][4];
 #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                  const float2 u = src[2 * j], w = src[2 * j + 1];
-                  raw[b][j] = make_float4(u.x, u.y, w.x, w.y);
+            for (int b = 0; b < kBatch; b++) {
+              const int it = it0 + b * 128 + ptid;
+              if (it < n_items) {
+                const int a = it / n_groups, e = it % n_groups;
+                const long long off = (long long)a * args.n_samp + tc0 + 8 * e;
+                if ((off & 1) == 0) {
+                  const float4* src = reinterpret_cast<const float4*>(args.y + off);
+#pragma unroll
+                  for (int j = 0; j < 4; j++) rawv[b][j] = src[j];
+                } else {
+                  const float2* src = args.y + off;
+#pragma unroll
+                  for (int j = 0; j < 4; j++) {
+                    const float2 u = src[2 * j], w = src[2 * j + 1];
+                    rawv[b][j] = make_float4(u.x, u.y, w.x, w.y);
+                  }
                 }
               }
             }
-          }
 #pragma unroll
-          for (int b = 0; b < kBatch; b++) {
-            const int it = it0 + b * 128 + ptid;
-            if (it >= n_items) continue;
-            const int a = it / n_groups, e = it % n_groups;
-            uint32_t hr[4], hi[4], lr[4], li[4];
-#pragma unroll
-            for (int j = 0; j < 4; j++) {  // samples 2j, 2j + 1 of the group
-              const float4 v = raw[b][j];
-              const __nv_bfloat162 h_r = __floats2bfloat162_rn(v.x, v.z);
-              const __nv_bfloat162 h_i = __floats2bfloat162_rn(v.y, v.w);
-              const float2 fr = __bfloat1622float2(h_r), fi = __bfloat1622float2(h_i);
-              const __nv_bfloat162 l_r = __floats2bfloat162_rn(v.x - fr.x, v.z - fr.y);
-              const __nv_bfloat162 l_i = __floats2bfloat162_rn(v.y - fi.x, v.w - fi.y);
-              hr[j] = *reinterpret_cast<const uint32_t*>(&h_r);
-              hi[j] = *reinterpret_cast<const uint32_t*>(&h_i);
-              lr[j] = *reinterpret_cast<const uint32_t*>(&l_r);
-              li[j] = *reinterpret_cast<const uint32_t*>(&l_i);
-            }
-            auto put = [&](int row, const uint32_t (&w)[4]) {
-              *reinterpret_cast<uint4*>(st + (size_t)(row / 8) * g.sbo + (size_t)e * kLbo +
-                                        (size_t)(row % 8) * 16) = make_uint4(w[0], w[1], w[2], w[3]);
-            };
-            put(2 * a, hr);
-            put(2 * a + 1, hi);
-            if (args.terms == 3) {
-              put(g.NC + 2 * a, lr);
-              put(g.NC + 2 * a + 1, li);
+            for (int b = 0; b < kBatch; b++) {
+              const int it = it0 + b * 128 + ptid;
+              if (it >= n_items) continue;
+              convert(it / n_groups, it % n_groups, rawv[b]);
             }
           }
         }
@@ -290,6 +346,34 @@ __global__ void __launch_bounds__(kCorrThreads, 1) k_corr_tc(CorrArgs args) {
       }
       tc::mma_commit(drain);
       tc::mbar_wait(drain, 0, nullptr, 1u << 22);
+    } else if (warp == kLoaderWarp) {
+      // ------------------------------------------------------ loader
+      // chunk i's antenna rows -> raw stage i % nraw, in chunk order, as far
+      // ahead as the ring allows; before leaving, wait (bounded) for every
+      // copy still in flight into this CTA's shared memory
+      if (args.raw_path && lane == 0) {
+        uint8_t* raw = smem + g.raw_off;
+        long long issued = 0;
+        for (long long i = 0; i < n_chunks; i++) {
+          const int r = (int)(i % g.nraw);
+          const uint32_t rph = (uint32_t)((i / g.nraw) & 1);
+          if (!tc::mbar_wait(&raw_empty[r], rph ^ 1, abort_flag)) {
+            raise();
+            break;
+          }
+          const long long tc0 = ta + i * kc;
+          const long long n_smp = min((long long)kc, tb - tc0);  // a multiple of 16
+          const uint32_t bytes = (uint32_t)n_smp * 8u;
+          tc::mbar_arrive_expect_tx(&raw_full[r], bytes * (uint32_t)M);
+          for (int a = 0; a < M; a++)
+            tc::bulk_g2s(raw + (size_t)r * g.raw_stride + (size_t)a * kc * 8,
+                         args.y + (long long)a * args.n_samp + tc0, bytes, &raw_full[r]);
+          issued = i + 1;
+        }
+        for (long long k = issued > g.nraw ? issued - g.nraw : 0; k < issued; k++)
+          tc::mbar_wait(&raw_full[(int)(k % g.nraw)], (uint32_t)((k / g.nraw) & 1), nullptr,
+                        1u << 22);
+      }
     } else if (warp >= kEpiWarp0) {
       // ------------------------------------------------------ epilogue
       const int q = warp & 3;  // TMEM lane quarter of this warp
@@ -301,6 +385,11 @@ __global__ void __launch_bounds__(kCorrThreads, 1) k_corr_tc(CorrArgs args) {
       uint32_t aph = 0;
       bool aborted = false;
       const int n_seg = L > kc ? L / kc : 1;  // accumulation segments per dump
+      // up to 32 columns and one row tile: running sums in registers, stored
+      // once per dump; lane quarters without used rows load nothing
+      const bool reg_acc = g.n_rt == 1 && g.NC <= 32;
+      const bool rows_used = 32 * q < g.KR;
+      float racc[32];
       for (long long m = m_a; m < m_b; m++) {
         // each lane sums its own rows over the dump's segments
         for (int sg = 0; sg < n_seg; sg++) {
@@ -309,7 +398,20 @@ __global__ void __launch_bounds__(kCorrThreads, 1) k_corr_tc(CorrArgs args) {
             aborted = true;
           }
           tc::fence_after();
-          if (!aborted) {
+          if (!aborted && reg_acc) {
+            if (rows_used) {
+#pragma unroll
+              for (int c0 = 0; c0 < 32; c0 += 16) {
+                if (c0 >= g.NC) break;
+                float v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)acc * acc_cols +
+                                  (uint32_t)c0,
+                              v);
+#pragma unroll
+                for (int c = 0; c < 16; c++) racc[c0 + c] = sg == 0 ? v[c] : racc[c0 + c] + v[c];
+              }
+            }
+          } else if (!aborted) {
             for (int rt = 0; rt < g.n_rt; rt++) {
               const int row = rt * 128 + 32 * q + lane;
               for (int c0 = 0; c0 < g.NC; c0 += 16) {
@@ -334,6 +436,13 @@ __global__ void __launch_bounds__(kCorrThreads, 1) k_corr_tc(CorrArgs args) {
             acc = 0;
             aph ^= 1u;
           }
+        }
+        if (reg_acc && !aborted && rows_used) {
+          const int row = 32 * q + lane;
+          if (row < g.KR)
+#pragma unroll
+            for (int c = 0; c < 32; c++)
+              if (c < g.NC) dsm[row * ld + c] = racc[c];
         }
         // all four warps take the same stop decision
         uint32_t stop_u;
@@ -406,6 +515,8 @@ cudaError_t launch_correlate_tc(const float2* y, long long n_samp, int n_ant, in
   a.M = n_ant;
   a.L = dump_len;
   a.terms = terms;
+  // bulk copies need 16-byte aligned rows: an even row length and base
+  a.raw_path = a.g.nraw > 0 && (n_samp % 2) == 0 && ((uintptr_t)y % 16) == 0;
   k_corr_tc<<<(unsigned)grid, kCorrThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
