@@ -378,6 +378,17 @@ int chirp_detect(chirp_plan* plan, const float* pow, int pow_loc, float snr_min,
                  chirp_candidate* cand, long long max_cand, int cand_loc, long long* n_cand,
                  float* stats_out);
 
+/* Self-test of the device watchdog (no GPU fault, trap or endless loop): a
+ * one-CTA kernel runs the bounded mbarrier wait of the tensor-core kernels'
+ * roles on a barrier that nothing arrives at, with a limit of `polls` polls
+ * (1 .. 2^24; each poll after the 32nd sleeps ~64 ns).  The wait must give up
+ * and raise the device error word the host reads.  Returns CHIRP_ETIMEOUT --
+ * the code a run whose wait gave up reports through chirp_plan_status -- and
+ * the kernel's duration in *waited_ms (HOST, may be NULL), with the context
+ * still usable; CHIRP_ECUDA if the wait wrongly succeeded or a CUDA call
+ * failed; CHIRP_EINVAL for a poll count out of range.  Synchronises stream. */
+int chirp_watchdog_selftest(unsigned int polls, double* waited_ms, void* stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* chirp_last_error(void);
 

@@ -35,6 +35,7 @@ BEAM_AUTO, BEAM_FP32_SIMT, BEAM_TC_3XBF16, BEAM_VIS, BEAM_TC_BF16 = 0, 1, 2, 3, 
 IN_C64, IN_CI8 = 0, 1
 CORR_AUTO, CORR_FP32_SIMT, CORR_TC_3XBF16, CORR_TC_BF16 = 0, 1, 2, 3
 FLAG_GRAPHS, FLAG_AUTOTUNE = 1, 2
+CHIRP_OK, CHIRP_EINVAL, CHIRP_ENOMEM, CHIRP_ECUDA, CHIRP_ETIMEOUT, CHIRP_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 K_DM_DEFAULT = 4.148808e15
 
 EXPORTED_SYMBOLS = ("chirp_plan_create", "chirp_plan_destroy", "chirp_plan_query",
@@ -46,7 +47,7 @@ EXPORTED_SYMBOLS = ("chirp_plan_create", "chirp_plan_destroy", "chirp_plan_query
                     "chirp_propnet_get_grads", "chirp_propnet_forward", "chirp_propnet_backward",
                     "chirp_propnet_train_step", "chirp_propnet_normalize", "chirp_propose_windows",
                     "chirpolator_run_selective", "chimageator_run_selective", "chirp_batch_run", "chirp_plan_fft_split", "chirp_detect",
-                    "chirp_last_error")
+                    "chirp_dedisperse_noalloc", "chirp_watchdog_selftest", "chirp_last_error")
 STAGES = ("forward", "inv_rows", "inv_cols", "correlate", "beamform", "split", "chirp",
           "incoherent", "detect")
 
@@ -159,6 +160,8 @@ def load():
         lib.chirp_dedisperse_noalloc.argtypes = [vp, i, ll, ctypes.c_double, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_double, ll, vp, vp]
         lib.chirp_dedisperse_noalloc.restype = i
+        lib.chirp_watchdog_selftest.argtypes = [ctypes.c_uint, ctypes.POINTER(ctypes.c_double), vp]
+        lib.chirp_watchdog_selftest.restype = i
         lib.chirp_last_error.argtypes = []
         lib.chirp_last_error.restype = ctypes.c_char_p
         _lib = lib
@@ -276,6 +279,15 @@ def chirp_dedisperse_noalloc(volt, f0: float, bw: float, k_dm: float, dm: float,
     _check(load().chirp_dedisperse_noalloc(vp, int(n_ant), int(n_samp), float(f0), float(bw),
                                            float(k_dm), float(dm), int(nfft_min), yp,
                                            _stream_handle(stream)))
+
+
+def chirp_watchdog_selftest(polls: int = 1 << 16, stream=None):
+    """Run the device watchdog's self-test (a bounded wait on a barrier that
+    nothing arrives at); returns (status code, kernel milliseconds).  The
+    expected code is CHIRP_ETIMEOUT."""
+    ms = ctypes.c_double(0.0)
+    rc = load().chirp_watchdog_selftest(int(polls), ctypes.byref(ms), _stream_handle(stream))
+    return int(rc), float(ms.value)
 
 
 def chirp_batch_run(plans, volts, outs, backends) -> None:

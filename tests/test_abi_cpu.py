@@ -79,3 +79,10 @@ def test_forced_beam_kernel_shape_that_does_not_fit_is_refused():
         chirp.Plan(**_cfg(xyz=xyz, pix_lm=np.zeros((4, 2)), beam_mode=chirp.BEAM_TC_3XBF16,
                           beam_shape=1))
     assert ei.value.code == -5 and "does not fit" in str(ei.value)
+
+
+def test_watchdog_selftest_rejects_a_poll_count_out_of_range():
+    rc, ms = chirp.chirp_watchdog_selftest(0)
+    assert rc == chirp.CHIRP_EINVAL
+    rc, ms = chirp.chirp_watchdog_selftest((1 << 24) + 1)
+    assert rc == chirp.CHIRP_EINVAL
