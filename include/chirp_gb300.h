@@ -258,6 +258,15 @@ long long chirp_propnet_param_count(const chirp_propnet* net);
 /* host float32 [param_count]; set_params also resets the Adam state */
 int chirp_propnet_set_params(chirp_propnet* net, const float* params);
 int chirp_propnet_get_params(const chirp_propnet* net, float* params);
+/* The trainer's whole state, for checkpoint and resume: parameters, Adam's
+ * first and second moments (host float32 [param_count] each) and the Adam
+ * step count (the bias corrections of the next step use step + 1).  After
+ * set_state the next train_step continues exactly as the saved trainer
+ * would have.  Errors: CHIRP_EINVAL (NULL buffer, negative step), CHIRP_ECUDA. */
+int chirp_propnet_get_state(const chirp_propnet* net, float* params, float* m, float* v,
+                            long long* step);
+int chirp_propnet_set_state(chirp_propnet* net, const float* params, const float* m,
+                            const float* v, long long step);
 /* gradients of the last backward / train step, host float32 [param_count] */
 int chirp_propnet_get_grads(const chirp_propnet* net, float* grads);
 int chirp_propnet_forward(chirp_propnet* net, const float* x, int batch, float* logits);

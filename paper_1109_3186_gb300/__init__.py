@@ -47,7 +47,8 @@ EXPORTED_SYMBOLS = ("chirp_plan_create", "chirp_plan_destroy", "chirp_plan_query
                     "chirp_propnet_get_grads", "chirp_propnet_forward", "chirp_propnet_backward",
                     "chirp_propnet_train_step", "chirp_propnet_normalize", "chirp_propose_windows",
                     "chirpolator_run_selective", "chimageator_run_selective", "chirp_batch_run", "chirp_plan_fft_split", "chirp_detect",
-                    "chirp_dedisperse_noalloc", "chirp_watchdog_selftest", "chirp_last_error")
+                    "chirp_dedisperse_noalloc", "chirp_watchdog_selftest", "chirp_propnet_get_state",
+                    "chirp_propnet_set_state", "chirp_last_error")
 STAGES = ("forward", "inv_rows", "inv_cols", "correlate", "beamform", "split", "chirp",
           "incoherent", "detect")
 
@@ -132,6 +133,10 @@ def load():
         for nm in ("chirp_propnet_set_params", "chirp_propnet_get_params", "chirp_propnet_get_grads"):
             getattr(lib, nm).argtypes = [vp, fp]
             getattr(lib, nm).restype = i
+        lib.chirp_propnet_get_state.argtypes = [vp, fp, fp, fp, ctypes.POINTER(ll)]
+        lib.chirp_propnet_get_state.restype = i
+        lib.chirp_propnet_set_state.argtypes = [vp, fp, fp, fp, ll]
+        lib.chirp_propnet_set_state.restype = i
         lib.chirp_propnet_forward.argtypes = [vp, vp, i, vp]
         lib.chirp_propnet_forward.restype = i
         lib.chirp_propnet_backward.argtypes = [vp, vp, vp, i, ctypes.c_float, fp]
@@ -525,6 +530,22 @@ class PropNet:
         a = np.empty(self.n_params, np.float32)
         _check(load().chirp_propnet_get_params(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
         return a
+
+    def get_state(self) -> dict:
+        """Parameters, Adam moments and Adam step (checkpoint of the trainer)."""
+        arrs = [np.empty(self.n_params, np.float32) for _ in range(3)]
+        step = ctypes.c_longlong(0)
+        fpp = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) for a in arrs]
+        _check(load().chirp_propnet_get_state(self._h, *fpp, ctypes.byref(step)))
+        return {"params": arrs[0], "m": arrs[1], "v": arrs[2], "step": int(step.value)}
+
+    def set_state(self, state: dict) -> None:
+        arrs = [np.ascontiguousarray(state[k], dtype=np.float32) for k in ("params", "m", "v")]
+        for a in arrs:
+            if a.size != self.n_params:
+                raise ValueError("state arrays must hold %d values" % self.n_params)
+        fpp = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) for a in arrs]
+        _check(load().chirp_propnet_set_state(self._h, *fpp, int(state["step"])))
 
     def grads(self) -> np.ndarray:
         a = np.empty(self.n_params, np.float32)

@@ -444,6 +444,31 @@ int chirp_propnet_get_params(const chirp_propnet* n, float* params) {
   return CHIRP_OK;
 }
 
+int chirp_propnet_get_state(const chirp_propnet* n, float* params, float* m, float* v,
+                            long long* step) {
+  if (!n || !params || !m || !v || !step) return perr(CHIRP_EINVAL, "NULL argument");
+  const size_t bytes = (size_t)n->n_par * sizeof(float);
+  PK(cudaMemcpyAsync(params, n->theta, bytes, cudaMemcpyDeviceToHost, n->st));
+  PK(cudaMemcpyAsync(m, n->m, bytes, cudaMemcpyDeviceToHost, n->st));
+  PK(cudaMemcpyAsync(v, n->v, bytes, cudaMemcpyDeviceToHost, n->st));
+  PK(cudaStreamSynchronize(n->st));
+  *step = n->step;
+  return CHIRP_OK;
+}
+
+int chirp_propnet_set_state(chirp_propnet* n, const float* params, const float* m,
+                            const float* v, long long step) {
+  if (!n || !params || !m || !v) return perr(CHIRP_EINVAL, "NULL argument");
+  if (step < 0) return perr(CHIRP_EINVAL, "negative Adam step");
+  const size_t bytes = (size_t)n->n_par * sizeof(float);
+  PK(cudaMemcpyAsync(n->theta, params, bytes, cudaMemcpyHostToDevice, n->st));
+  PK(cudaMemcpyAsync(n->m, m, bytes, cudaMemcpyHostToDevice, n->st));
+  PK(cudaMemcpyAsync(n->v, v, bytes, cudaMemcpyHostToDevice, n->st));
+  PK(cudaStreamSynchronize(n->st));
+  n->step = step;
+  return CHIRP_OK;
+}
+
 int chirp_propnet_get_grads(const chirp_propnet* n, float* grads) {
   if (!n || !grads) return perr(CHIRP_EINVAL, "NULL argument");
   PK(cudaMemcpyAsync(grads, n->grad, (size_t)n->n_par * sizeof(float), cudaMemcpyDeviceToHost,

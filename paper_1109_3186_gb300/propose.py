@@ -23,7 +23,7 @@ import math
 
 import numpy as np
 
-from . import Plan, PropNet, skymodel
+from . import Plan, PropNet, checkpoint, skymodel
 
 
 @dataclasses.dataclass
@@ -155,17 +155,31 @@ class Proposer:
         return out
 
     def train(self, feats, ys, steps: int, batch: int, lr: float = 2e-3, pos_weight: float = 20.0,
-              seed: int = 0):
+              seed: int = 0, start_step: int = 0):
+        """steps Adam steps on batches drawn from a generator seeded with seed;
+        start_step > 0 resumes a trainer restored from a checkpoint taken
+        after start_step steps (the batches it already drew are skipped, so
+        the run continues exactly as the uninterrupted one)."""
         torch = self.torch
         X = torch.stack(feats)
         Y = torch.stack([torch.from_numpy(y) for y in ys]).cuda()
         g = np.random.default_rng(seed)
+        for _ in range(start_step):
+            g.choice(len(feats), size=batch, replace=False)
         losses = []
         for _ in range(steps):
             idx = torch.from_numpy(g.choice(len(feats), size=batch, replace=False)).cuda()
             losses.append(self.net.train_step(X[idx].contiguous(), Y[idx].contiguous(),
                                               pos_weight, lr))
         return losses
+
+    def save(self, path: str) -> None:
+        """Checkpoint of the trainer (network parameters, Adam state and step)."""
+        checkpoint.save(self.net, path)
+
+    def load(self, path: str) -> int:
+        """Restore a checkpoint; returns the step to pass as start_step."""
+        return checkpoint.load(self.net, path)
 
     def logits(self, feat) -> "torch.Tensor":
         z = self.torch.empty((1,) + tuple(feat.shape), dtype=self.torch.float32, device="cuda")

@@ -78,3 +78,44 @@ def test_normalize_and_windows():
     net.propose(torch.from_numpy(z).cuda(), 45, 1.5, mask)
     ref = np.array([[z[d, w * 45:(w + 1) * 45].max() > 1.5 for w in range(7)] for d in range(5)])
     assert np.array_equal(mask.cpu().numpy().astype(bool), ref)
+
+
+def test_checkpoint_resume_continues_bit_for_bit(tmp_path):
+    """Six Adam steps in one go equal three steps, a checkpoint written to a
+    file, a fresh network restored from it and three more steps -- the
+    parameters and both Adam moments bit for bit; restoring the parameters
+    alone (Adam state lost) gives a different trainer."""
+    from paper_1109_3186_gb300 import checkpoint
+    C, H, K1, K2, B, T = 12, 16, 5, 3, 2, 90
+    rng = np.random.default_rng(11)
+    theta = pn.init(C, H, K1, K2, 4).astype(np.float32)
+    batches = [(torch.from_numpy(rng.standard_normal((B, C, T)).astype(np.float32)).cuda(),
+                torch.from_numpy((rng.random((B, C, T)) < 0.05).astype(np.float32)).cuda())
+               for _ in range(6)]
+
+    def fresh():
+        net = chirp.PropNet(C, H, K1, K2, B, T)
+        net.set_params(theta)
+        return net
+
+    whole = fresh()
+    for xb, yb in batches:
+        whole.train_step(xb, yb, 5.0, 1e-3)
+    first = fresh()
+    for xb, yb in batches[:3]:
+        first.train_step(xb, yb, 5.0, 1e-3)
+    path = str(tmp_path / "trainer.ck")
+    checkpoint.save(first, path)
+    resumed = chirp.PropNet(C, H, K1, K2, B, T)
+    assert checkpoint.load(resumed, path) == 3
+    for xb, yb in batches[3:]:
+        resumed.train_step(xb, yb, 5.0, 1e-3)
+    a, b = whole.get_state(), resumed.get_state()
+    assert a["step"] == b["step"] == 6
+    for k in ("params", "m", "v"):
+        assert np.array_equal(a[k], b[k]), k
+    params_only = fresh()
+    params_only.set_params(first.params())
+    for xb, yb in batches[3:]:
+        params_only.train_step(xb, yb, 5.0, 1e-3)
+    assert not np.array_equal(params_only.params(), a["params"])
