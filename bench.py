@@ -268,6 +268,8 @@ def stage_roofline(sc, plan, stage_ms, peaks, peak_kind, beam_mode, steps):
     # DM reads its chirp table and writes its transformed rows
     chunk = max(1, plan.info.get("dm_chunk", 1))
     spec_reads = sum(8.0 * groups[g] * -(-n // chunk) for g, n in n_searched.items())
+    # chirp tables: the group's FP64 phase table read once per chunk, each DM's table written
+    g_reads = sum(8.0 * g * -(-n // chunk) for g, n in n_searched.items())
     hbm = peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
     sm_max = peaks.get("sm_max_mhz", FALLBACK_PEAKS["sm_max_mhz"])
     fp32_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
@@ -278,7 +280,7 @@ def stage_roofline(sc, plan, stage_ms, peaks, peak_kind, beam_mode, steps):
         y_bytes = float(n_dump_valid) * L * M * (8 if beam_mode == 2 else 4)
     stages = {
         "forward": ("hbm", 32.0 * fwd_pts, hbm, "GB/s"),
-        "chirp": ("hbm", 2.0 * g_bytes, hbm, "GB/s"),
+        "chirp": ("hbm", g_reads + g_bytes, hbm, "GB/s"),
         "inv_rows": ("hbm", spec_reads + 8.0 * inv_pts + g_bytes, hbm, "GB/s"),
         "inv_cols": ("hbm", 8.0 * inv_pts + y_bytes, hbm, "GB/s"),
     }

@@ -135,6 +135,27 @@ __global__ void k_chirp_table(const double* __restrict__ G, float2* __restrict__
   H[pos] = make_float2(cs * inv_nfft, sn * inv_nfft);
 }
 
+// The chirps of up to kMaxChirps DMs of one group in one pass over G (each
+// element of G is read once); DM i's table goes to H + i h_stride.  Every
+// value equals k_chirp_table's for the same DM.
+struct ChirpDms {
+  double dm[kMaxChirps];
+};
+__global__ void k_chirp_tables(const double* __restrict__ G, float2* __restrict__ H,
+                               long long h_stride, ChirpDms dms, int n_dm, long long nfft,
+                               float inv_nfft) {
+  long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= nfft) return;
+  const double gv = G[pos];
+  for (int i = 0; i < n_dm; i++) {
+    double c = __dmul_rn(dms.dm[i], gv);
+    double r = __dsub_rn(c, rint(c));  // exact
+    float sn, cs;
+    sincospif(-2.0f * (float)r, &sn, &cs);
+    H[i * h_stride + pos] = make_float2(cs * inv_nfft, sn * inv_nfft);
+  }
+}
+
 // ------------------------------------------------------------------ twiddles
 // exp(-2 pi j e / n) from the exact fraction e / n (n a power of two), FP64
 // with the argument reduced by sincospi, rounded once to FP32.
@@ -429,6 +450,17 @@ cudaError_t launch_build_phase_table(double* G, const GroupGeom& g, double f0, d
                                      double k_dm, cudaStream_t st) {
   long long blocks = (g.nfft + 255) / 256;
   k_phase_table<<<(unsigned)blocks, 256, 0, st>>>(G, g.nfft, g.n1, g.n2, f0, bw, k_dm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chirp_tables(const double* G, float2* H, long long h_stride, const double* dms,
+                                int n_dm, const GroupGeom& g, cudaStream_t st) {
+  if (n_dm < 1 || n_dm > kMaxChirps) return cudaErrorInvalidValue;
+  ChirpDms d{};
+  for (int i = 0; i < n_dm; i++) d.dm[i] = dms[i];
+  long long blocks = (g.nfft + 255) / 256;
+  k_chirp_tables<<<(unsigned)blocks, 256, 0, st>>>(G, H, h_stride, d, n_dm, g.nfft,
+                                                   ldexpf(1.0f, -g.log2n));
   return cudaGetLastError();
 }
 

@@ -564,7 +564,7 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
                (long long)p->M * g.geom.n_blk;
   p->dm_chunk = 1;
   if (!chunked)
-    while (p->dm_chunk < 4 && (size_t)(p->dm_chunk + 1) * z_elems * sizeof(float2) <= (4ull << 30))
+    while (p->dm_chunk < kMaxChirps && (size_t)(p->dm_chunk + 1) * z_elems * sizeof(float2) <= (4ull << 30))
       p->dm_chunk++;
   p->z_stride = z_elems;
   if (!rc)
@@ -961,11 +961,12 @@ int full_search_chunked(chirp_plan* p, Backend be, void* dout) {
     const long long nq = (long long)p->M * G.n_blk;
     for (size_t c0 = 0; c0 < dms.size(); c0 += (size_t)p->dm_chunk) {
       const int n = (int)std::min((size_t)p->dm_chunk, dms.size() - c0);
-      for (int j = 0; j < n; j++) {
-        int rc = chirp_for(p, dms[c0 + j], j);
-        if (rc) return rc;
-      }
+      double dmv[kMaxChirps];
+      for (int j = 0; j < n; j++) dmv[j] = p->dm[dms[c0 + j]];
       int mk = mark_begin(p);
+      CK(launch_chirp_tables(grp.d_G, p->d_H, p->h_stride, dmv, n, G, p->stream));
+      mark_end(p, CHIRP_STAGE_CHIRP, mk);
+      mk = mark_begin(p);
       CK(launch_inverse_rows_multi(grp.d_spec, p->d_Z, (long long)p->z_stride, p->d_H,
                                    p->h_stride, n, nq, G, p->tw(), grp.d_rtw, p->stream));
       mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
