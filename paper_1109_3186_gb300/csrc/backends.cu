@@ -109,13 +109,7 @@ __global__ void __launch_bounds__(32 * kCorrWarps) k_correlate(const float2* __r
 
 cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int dump_len,
                              long long m_base, long long n_m, long long first, long long last,
-                             float2* vis, int* err, cudaStream_t st, const int* dump_list) {
-  if (err != nullptr && n_m > 0 && correlate_staged_supported(n_ant, dump_len, n_samp, y)) {
-    if (dump_list != nullptr)
-      return launch_correlate_staged(y, n_samp, n_ant, dump_len, 0, n_m, vis, err, st, dump_list);
-    if (m_base >= first && m_base + n_m - 1 <= last)
-      return launch_correlate_staged(y, n_samp, n_ant, dump_len, m_base, n_m, vis, err, st);
-  }
+                             float2* vis, cudaStream_t st, const int* dump_list) {
   const int nt = (n_ant + kCorrTile - 1) / kCorrTile;
   const int n_tiles = nt * (nt + 1) / 2;
   if (n_m <= 0) return cudaSuccess;

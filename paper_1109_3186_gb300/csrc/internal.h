@@ -102,21 +102,9 @@ cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, in
 // ---- back-ends (backends.cu) ----
 // dumps m_base .. m_base + n_m - 1, or dump_list[0 .. n_m) when dump_list is a
 // device array (zeros for dumps outside [first, last])
-// err: the plan's device error word (raised when a bounded wait of the
-// staged kernel gives up).  With up to 16 antennas, even dump length and N
-// and a 16-byte aligned y, contiguous ranges of valid dumps and dump lists
-// (which hold valid dumps only) run the staged kernel (corr_simt.cu); the
-// rest the plain one.  Both sum each dump in an order that does not depend
-// on the launch, so a dump's visibilities are the same in full and
-// selective searches.
 cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int dump_len,
                              long long m_base, long long n_m, long long first, long long last,
-                             float2* vis, int* err, cudaStream_t st,
-                             const int* dump_list = nullptr);
-bool correlate_staged_supported(int n_ant, int dump_len, long long n_samp, const void* y);
-cudaError_t launch_correlate_staged(const float2* y, long long n_samp, int n_ant, int dump_len,
-                                    long long first, long long n_dumps, float2* vis, int* err,
-                                    cudaStream_t st, const int* dump_list = nullptr);
+                             float2* vis, cudaStream_t st, const int* dump_list = nullptr);
 // dumps first..last, or the n_list dumps of dump_list (device) when given
 cudaError_t launch_beam_from_vis(const float2* V, const float2* wpair, int n_ant, int n_pix,
                                  long long first, long long last, float* pow, cudaStream_t st,

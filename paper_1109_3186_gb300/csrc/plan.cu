@@ -917,8 +917,7 @@ int backend_dumps(chirp_plan* p, int d, Backend be, long long m0, long long m1, 
   auto correlate = [&](float2* vis, bool for_beams) -> int {
     int mk = mark_begin(p);
     if (p->corr_mode == CHIRP_CORR_FP32_SIMT || (for_beams && !p->corr_forced))
-      CK(launch_correlate(p->d_y, p->N, p->M, p->L, m0, m1 - m0, m0, last, vis, p->d_err,
-                          p->stream));
+      CK(launch_correlate(p->d_y, p->N, p->M, p->L, m0, m1 - m0, m0, last, vis, p->stream));
     else
       CK(launch_correlate_tc(p->d_y, p->N, p->M, p->L, m0, last, vis, p->d_err,
                              p->corr_mode == CHIRP_CORR_TC_BF16 ? 1 : 3, p->stream));
@@ -1067,8 +1066,8 @@ int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Bac
     if (be == kCorrelate || p->beam_mode == CHIRP_BEAM_VIS) {
       float2* vout = be == kCorrelate ? (float2*)dout + (size_t)d * p->n_dump * p->n_pair : p->d_V;
       mk = mark_begin(p);
-      CK(launch_correlate(p->d_y, p->N, p->M, p->L, 0, dmp_n[d], I.first, I.last, vout, p->d_err,
-                          p->stream, dlist));
+      CK(launch_correlate(p->d_y, p->N, p->M, p->L, 0, dmp_n[d], I.first, I.last, vout, p->stream,
+                          dlist));
       mark_end(p, CHIRP_STAGE_CORRELATE, mk);
       if (be == kBeams) {
         mk = mark_begin(p);

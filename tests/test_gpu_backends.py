@@ -17,7 +17,7 @@ torch = pytest.importorskip("torch")
 CORR_CASES = [
     (6, 1 << 17, 1024, [0.0, 20.0, 40.0, 75.0], 1 << 14),
     (4, 100003, 777, [0.0, 33.0], 1 << 13),     # ragged N and dump length
-    (8, 50000, 1000, [0.0, 12.0], 1 << 13),     # dumps of 3 full chunks and a partial one
+    (8, 50000, 1000, [0.0, 12.0], 1 << 13),     # even dump length, not a multiple of 256
     (1, 1 << 15, 512, [5.0], 1 << 12),          # one antenna: autos only
     (13, 1 << 15, 256, [0.0, 9.0], 1 << 12),    # 91 pairs
     (36, 1 << 14, 1024, [0.0, 5.0], 1 << 12),   # 666 pairs; tensor cores: two row tiles
