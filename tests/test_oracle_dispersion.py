@@ -182,3 +182,23 @@ def test_layout_groups_follow_the_fft_length_rule(k_dm):
     for d in range(64):
         lay = orc.layout(dms, d, 1.4e9, 32e6, k_dm, 1 << 22, 1 << 18)
         assert lay["nfft"] >= 2 * (lay["n_hi_max"] + lay["n_lo_max"])   # >= 50 % kept
+
+
+@pytest.mark.parametrize("dm", [0.0, 3.7, 48.0, 150.0])
+def test_whole_block_products_do_not_depend_on_dm(k_dm, dm):
+    """Unitarity: over one whole circular block, dedispersion (forward FFT,
+    chirp multiply, inverse FFT with 1/N) leaves every antenna-pair product
+    sum unchanged, sum_t y_p y_q^* = sum_t x_p x_q^* for any DM, because
+    |H| = 1 (Parseval on both sides).  A chirp with the wrong modulus, a
+    missing or doubled 1/N, or a chirp applied to one antenna only fails."""
+    nfft = 1 << 12
+    rng = np.random.default_rng(5)
+    x = (rng.standard_normal((3, nfft)) + 1j * rng.standard_normal((3, nfft))) / math.sqrt(2)
+    H = orc.chirp(1.4e9, 8e6, k_dm, dm, nfft)
+    y = np.array([orc.fft(orc.fft(x[a]) * H, +1) / nfft for a in range(3)])
+    G_x = x @ x.conj().T
+    G_y = y @ y.conj().T
+    assert np.abs(G_y - G_x).max() <= 1e-9 * np.abs(G_x).max()
+    if dm > 0:
+        # the voltages themselves do change (the products would not pin anything otherwise)
+        assert np.abs(y - x).max() > 0.1
