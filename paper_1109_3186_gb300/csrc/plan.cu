@@ -1003,7 +1003,28 @@ int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Bac
   std::vector<int> lists;
   std::vector<long long> blk_off(p->dm.size(), 0), blk_n(p->dm.size(), 0);
   std::vector<long long> dmp_off(p->dm.size(), 0), dmp_n(p->dm.size(), 0);
-  if (mask) {
+  // A selection covering at least 80 % of the valid cells runs the full
+  // search (its multi-DM row passes beat per-DM block lists there) and then
+  // clears the unselected valid cells, listed as d n_dump + m.
+  bool dense = false;
+  if (mask && p->dm_chunk > 1 && (long long)p->dm.size() * p->n_dump < (1LL << 31)) {
+    long long n_valid = 0, n_sel = 0;
+    for (int d = 0; d < (int)p->dm.size(); d++) {
+      const DmInfo& I = p->dmi[d];
+      const unsigned char* row = mask + (size_t)d * p->n_dump;
+      for (long long m = I.first; m <= I.last; m++) n_sel += row[m] != 0;
+      if (I.last >= I.first) n_valid += I.last - I.first + 1;
+    }
+    dense = n_valid > 0 && n_sel * 5 >= n_valid * 4;
+    if (dense)
+      for (int d = 0; d < (int)p->dm.size(); d++) {
+        const DmInfo& I = p->dmi[d];
+        const unsigned char* row = mask + (size_t)d * p->n_dump;
+        for (long long m = I.first; m <= I.last; m++)
+          if (!row[m]) lists.push_back((int)((long long)d * p->n_dump + m));
+      }
+  }
+  if (mask && !dense) {
     std::vector<unsigned char> need;
     for (int d = 0; d < (int)p->dm.size(); d++) {
       const DmInfo& I = p->dmi[d];
@@ -1023,18 +1044,25 @@ int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Bac
         if (need[(size_t)b]) lists.push_back((int)b);
       blk_n[d] = (long long)lists.size() - blk_off[d];
     }
-    if (!lists.empty()) {
-      if (p->lists_cap < lists.size()) {
-        cudaFree(p->d_lists);
-        p->d_lists = nullptr;
-        p->lists_cap = 0;
-        rc = dev_alloc(p, (void**)&p->d_lists, lists.size() * sizeof(int), "index lists");
-        if (rc) return rc;
-        p->lists_cap = lists.size();
-      }
-      CK(cudaMemcpyAsync(p->d_lists, lists.data(), lists.size() * sizeof(int),
-                         cudaMemcpyHostToDevice, p->stream));
+  }
+  if (!lists.empty()) {
+    if (p->lists_cap < lists.size()) {
+      cudaFree(p->d_lists);
+      p->d_lists = nullptr;
+      p->lists_cap = 0;
+      rc = dev_alloc(p, (void**)&p->d_lists, lists.size() * sizeof(int), "index lists");
+      if (rc) return rc;
+      p->lists_cap = lists.size();
     }
+    CK(cudaMemcpyAsync(p->d_lists, lists.data(), lists.size() * sizeof(int),
+                       cudaMemcpyHostToDevice, p->stream));
+  }
+  if (dense) {
+    rc = full_search_chunked(p, be, dout);
+    if (rc) return rc;
+    const int row_floats = be == kCorrelate ? 2 * p->n_pair : p->n_pix;
+    CK(launch_zero_cells((float*)dout, p->d_lists, (long long)lists.size(), row_floats, p->stream));
+    return CHIRP_OK;
   }
   if (!mask && p->dm_chunk > 1) return full_search_chunked(p, be, dout);
   for (int d = 0; d < (int)p->dm.size(); d++) {

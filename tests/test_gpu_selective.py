@@ -56,3 +56,29 @@ def test_selective_visibilities_equal_full():
     pick = mask.astype(bool)
     assert np.array_equal(sel[pick], full[pick])
     assert np.all(sel[~pick] == 0)
+
+
+@pytest.mark.parametrize("frac", [0.7, 0.9, 1.0])
+def test_dense_selections_equal_full(frac):
+    """Selections either side of the 80 % switch to the full multi-DM search
+    (which then clears the unselected cells): both give the full search's
+    values bit for bit and zeros elsewhere."""
+    sc = skymodel.chirpolator_small(n_samp=1 << 18, n_dm=5, dm_max=100.0, nfft_min=1 << 15)
+    x = sc.voltages()
+    plan = chirp.Plan.from_scenario(sc)
+    full = np.empty((5, plan.n_dump, plan.n_pair), np.complex64)
+    plan.chirpolator(x, full)
+    first, last = plan.dump_range()
+    valid = np.zeros((5, plan.n_dump), bool)
+    for d in range(5):
+        valid[d, first[d]:last[d] + 1] = True
+    rng = np.random.default_rng(11)
+    mask = (rng.random(valid.shape) < frac).astype(np.uint8)
+    mask[0, first[0]:first[0] + 10] = 0
+    share = (mask.astype(bool) & valid).sum() / valid.sum()
+    assert (share >= 0.8) == (frac >= 0.9)
+    sel = np.full_like(full, np.complex64(7 + 7j))
+    plan.chirpolator_selective(x, mask, sel)
+    pick = mask.astype(bool) & valid
+    assert np.array_equal(sel[pick], full[pick])
+    assert np.all(sel[~pick] == 0)
