@@ -61,6 +61,9 @@ def parse_args():
     ap.add_argument("--chirpolator-only", action="store_true",
                     help="time only the Chirpolator search on the same workload (for profiling "
                          "its kernels); prints one line with its per-step and per-stage times")
+    ap.add_argument("--cpi-only", action="store_true",
+                    help="time only the paper's Chirpolator pre-integrator on the same workload "
+                         "(for profiling its kernels); prints one line")
     ap.add_argument("--cpu-dumps", type=int, default=640,
                     help="dumps per selected DM in the oracle's bounded CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -479,6 +482,69 @@ def extra_forms(sc, plan, xd, stream, args):
     return out
 
 
+def cpi_search(sc, xd, stream, args, peaks):
+    """The paper's own Chirpolator pre-integrator (pair mixing, block-based
+    sliding DFTs, moving sums, matched-filter image; chirp_cpi_run) on the
+    same observation: the trial DMs above 0 (the linear-chirp model needs a
+    sweep), blocks of 2048 samples, F = 2.  Device buffers, CUDA events on the
+    plan's stream; per-pass times from a separate loop of single runs."""
+    import torch
+    from paper_1109_3186_gb300.cpi import CPI_STAGES, CpiPlan
+    dms = sc.dms[sc.dms > 0]
+    L, F = 2048, 2
+    plan = CpiPlan(sc.xyz, sc.f0, sc.bw, sc.n_samp, dms, L, sc.pix_lm, F, k_dm=sc.k_dm,
+                   stream=stream)
+    E = torch.empty((len(dms), plan.n_blk, plan.n_pix), dtype=torch.float32, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        plan.run(xd, E)
+    torch.cuda.synchronize()
+    k = max(3, args.steps)
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(k):
+        plan.run(xd, E)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms = a0.elapsed_time(a1) / k
+    st = dict.fromkeys(CPI_STAGES, 0.0)
+    for _ in range(3):
+        plan.run(xd, E)
+        for name, v in plan.timing().items():
+            st[name] += v / 3
+    nws = [plan.layout(d)["n_win"] for d in range(len(dms))]
+    windows = sum(max(0, plan.n_blk - nw + 1) for nw in nws)
+    units = sc.n_ant * len(dms) * plan.n_blk * L
+    sm_max = peaks.get("sm_max_mhz", FALLBACK_PEAKS["sm_max_mhz"])
+    alu = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    hbm = peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
+    nk = 2 * plan.max_bin + 1
+    # image: one complex multiply-add (8 flops) per (window, pixel, pair, filter bin), + |P|^2
+    img_flops = 8.0 * windows * plan.n_pix * plan.n_pair * (2 * F + 1) + 3.0 * windows * plan.n_pix
+    # moving sums: each (DM, block, bin, pair) reads V twice and writes X (8 B each)
+    cic_bytes = 24.0 * len(dms) * plan.n_blk * nk * plan.n_pair
+    # moments: read the voltages once, write J moments per (sub-block, pair)
+    mom_bytes = 8.0 * sc.n_ant * plan.n_blk * L + 8.0 * plan.n_blk * (L // plan.info["sub_len"]) \
+        * plan.info["n_terms"] * plan.n_pair
+    roof = {
+        "moments": ("hbm", mom_bytes / (st["moments"] * 1e-3) / 1e9, hbm, "GB/s"),
+        "cic": ("hbm", cic_bytes / (st["cic"] * 1e-3) / 1e9, hbm, "GB/s"),
+        "image": ("alu", img_flops / (st["image"] * 1e-3) / 1e12, alu, "TFLOP/s"),
+    }
+    out = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": k,
+           "beam_dm_windows_per_s": windows * plan.n_pix / (ms * 1e-3),
+           "n_dm": len(dms), "blk_len": L, "half_width": F, "max_bin": plan.max_bin,
+           "n_freq": plan.info["n_freq"], "sub_len": plan.info["sub_len"],
+           "n_terms": plan.info["n_terms"], "gpu_launches_per_step": 4,
+           "stages_ms": st,
+           "roofline": {n: {"bound": b, "achieved": a, "peak": pk, "unit": u, "frac": a / pk}
+                        for n, (b, a, pk, u) in roof.items()},
+           "dtype": "f32 (moving sums f64)",
+           "note": "paper's own pre-integrator on the raw voltages: DMs > 0 of the 64"}
+    plan.close()
+    return out
+
+
 def chirpolator_only(sc, x, stream, args):
     """The Chirpolator search alone on the benchmark's observation: W warm-up
     and K timed steps, CUDA events on the plan's stream; one JSON line."""
@@ -535,6 +601,13 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     if args.chirpolator_only:
         return chirpolator_only(sc, x, stream, args)
+    if args.cpi_only:
+        import torch as _t
+        line = cpi_search(sc, _t.from_numpy(x).cuda(), stream, args, load_peaks()[0])
+        line["mode"] = "cpi"
+        line["config"] = config_block(sc, 1)
+        print(json.dumps(line), flush=True)
+        return 0
     plan = chirp.Plan.from_scenario(sc, beam_mode=args.beam_mode, stream=stream)
     n_dm, n_dump, n_pix = len(sc.dms), plan.n_dump, plan.n_pix
     xd = torch.from_numpy(x).cuda()
@@ -632,6 +705,7 @@ def run_ours(args):
                               "corr_mode": {1: "fp32_simt", 2: "tc_3xbf16", 3: "tc_bf16"}[
                                   plan.info["corr_mode"]]}
         del Vd
+        alt["cpi"] = cpi_search(sc, xd, stream, args, peaks)
         alt.update(extra_forms(sc, plan, xd, stream, args))
         plan.chimageator(xd, Pd)
         torch.cuda.synchronize()

@@ -400,6 +400,91 @@ int chirp_detect(chirp_plan* plan, const float* pow, int pow_loc, float snr_min,
  * failed; CHIRP_EINVAL for a poll count out of range.  Synchronises stream. */
 int chirp_watchdog_selftest(unsigned int polls, double* waited_ms, void* stream);
 
+/* ------------------------------------------------------------------------
+ * The paper's own Chirpolator pre-integrator (Sec. 3, App. A.3) on the RAW
+ * voltages, for every trial DM:
+ *   mixing       x_pq[n] = y_p[n] y_q[n]^*, p < q (Eq. xpq)
+ *   partial DFTs V_k[m] = sum_{n<L} exp(-2 pi j (n + mL) k / N) x_pq[n + mL]
+ *                (Sec. A.3.2), k in [-K, K], blocks m < n_blk = floor(n_samp / L)
+ *   moving sum   S_k[m] = S_k[m-1] + V_k[m] - V_k[m - n_win] (Eq. block_cic)
+ *   window DFT   X_k[m] = exp(2 pi j (m + 1 - n_win) k / n_win) S_k[m], the
+ *                DFT of samples [(m + 1 - n_win) L, (m + 1) L) in their own
+ *                time; zero while m < n_win - 1
+ *   image        P = sum_{p<q} sum_{k = k0'-F}^{k0'+F} w_pq,k X_pq,k (Eq. pth
+ *                with the 2F+1-bin matched filter of Sec. 3.4), E = |P|^2
+ *                (Eq. eth)
+ * A trial DM is a linear chirp (Sec. 2.1, Eq. freqvst2, about the sweep's
+ * temporal midpoint): T = k_dm DM ((f0 - B/2)^-2 - (f0 + B/2)^-2),
+ * alpha = ((f0 - B/2)^-2 + (f0 + B/2)^-2) / 2, a0 = alpha^-1/2 (Hz),
+ * fdot = a1 = -alpha^-3/2 / (2 k_dm DM) (Hz/s), window
+ * n_win = max(1, floor(B T / L + 1/2)) blocks, N = n_win L.  For direction
+ * (l, m) with delays tau from Eq. tau3D: kappa = -fdot (tau_p - tau_q) N / B
+ * (Eq. f0Bt), k0' = rint(kappa), and the filter is the conjugate response of
+ * a unit chirp whose midpoint is at the window centre,
+ *   w_pq,k = conj(phi exp(-pi j kappa) exp(-pi j (k - kappa)(N-1)/N))
+ *            D_N(k - kappa) / N,
+ *   phi = exp(pi j fdot (tau_p^2 - tau_q^2) - 2 pi j a0 (tau_p - tau_q)),
+ * D_N the Dirichlet kernel (Eq. dn).  Pair pq needs bins |k| <= K_pq =
+ * max over DMs and pixels of |k0'| + F (Sec. A.3.1); bins beyond it are not
+ * computed and read as zero.
+ * All arithmetic is FP32 on the CUDA cores except the moving sums (FP64) and
+ * the filter table (FP64, rounded once).  The partial DFTs are evaluated by a
+ * Taylor expansion inside sub-blocks whose truncation is below 1e-9 of the
+ * sub-block's sum of |x_pq| (chirp_cpi_info.sub_len, .n_terms).
+ * ---------------------------------------------------------------------- */
+typedef struct chirp_cpi_plan chirp_cpi_plan;
+
+/* All pointers are HOST memory, copied at plan creation. */
+typedef struct {
+  int n_ant;             /* M, 2..84                                          */
+  const double* xyz_m;   /* [n_ant][3] positions, metres ((u,v,w), Eq. tau3D)  */
+  double f0_hz;          /* band centre                                        */
+  double bw_hz;          /* bandwidth = complex sample rate                    */
+  double k_dm;           /* <= 0 selects 4.148808e15 s Hz^2 / (pc cm^-3)       */
+  long long n_samp;      /* samples per antenna, >= blk_len                    */
+  const double* dm;      /* [n_dm] trial DMs, each > 0                          */
+  int n_dm;              /* >= 1                                               */
+  int blk_len;           /* L, power of two 16..65536                          */
+  const double* pix_lm;  /* [n_pix][2] direction cosines                       */
+  int n_pix;             /* >= 1                                               */
+  int half_width;        /* F, 0..8                                            */
+  int max_bin;           /* K (0: the smallest that holds every pixel's bins);
+                            at most 64                                         */
+} chirp_cpi_config;
+
+typedef struct {
+  int n_pair;            /* M (M - 1) / 2, order (0,1), (0,2), ..., (M-2,M-1)   */
+  long long n_blk;       /* floor(n_samp / L)                                  */
+  int max_bin;           /* K in use                                           */
+  int n_freq;            /* distinct frequencies k / N over (DM, |k| <= K),
+                            f = 0 included (the factorised partial DFTs)       */
+  int sub_len, n_terms;  /* Taylor evaluation: sub-block length, terms         */
+  long long work_bytes;  /* device workspace                                   */
+} chirp_cpi_info;
+
+/* Creates a plan (device workspace, FP64 filter table) whose work is queued
+ * on `stream` (a cudaStream_t, NULL = legacy default stream).  Errors:
+ * CHIRP_EINVAL (bad size, DM <= 0, max_bin below what the pixels need),
+ * CHIRP_EUNSUPPORTED (more than 1024 sub-blocks per block would be needed),
+ * CHIRP_ENOMEM, CHIRP_ECUDA.  *out is NULL on failure. */
+int chirp_cpi_create(chirp_cpi_plan** out, const chirp_cpi_config* cfg, void* stream);
+int chirp_cpi_query(const chirp_cpi_plan* plan, chirp_cpi_info* info);
+/* Per DM d: n_win and fdot (Hz/s); pair_bins (may be NULL): [n_pair] K_pq. */
+int chirp_cpi_layout(const chirp_cpi_plan* plan, int d, int* n_win, double* fdot, int* pair_bins);
+/* E [n_dm][n_blk][n_pix] float (|P|^2; zero for incomplete windows) from
+ * complex64 voltages [n_ant][n_samp].  volt_loc / out_loc: CHIRP_HOST or
+ * CHIRP_DEVICE.  A host output synchronises the plan's stream. */
+int chirp_cpi_run(chirp_cpi_plan* plan, const void* volt, int volt_loc, float* energy, int out_loc);
+/* The intermediate spectra of the same search, both complex64
+ * [n_dm][n_blk][2K+1][n_pair] (bin k at index k + K): V the partial DFTs,
+ * X the window DFTs; bins beyond K_pq are zero.  Either may be NULL. */
+int chirp_cpi_spectra(chirp_cpi_plan* plan, const void* volt, int volt_loc, void* V, void* X,
+                      int out_loc);
+/* Milliseconds of the last run's four passes (moments, partial DFTs, moving
+ * sums, image), CUDA events on the plan's stream; synchronises it. */
+int chirp_cpi_timing(chirp_cpi_plan* plan, double ms[4]);
+void chirp_cpi_destroy(chirp_cpi_plan* plan);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* chirp_last_error(void);
 

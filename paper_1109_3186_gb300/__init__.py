@@ -48,7 +48,9 @@ EXPORTED_SYMBOLS = ("chirp_plan_create", "chirp_plan_destroy", "chirp_plan_query
                     "chirp_propnet_train_step", "chirp_propnet_normalize", "chirp_propose_windows",
                     "chirpolator_run_selective", "chimageator_run_selective", "chirp_batch_run", "chirp_plan_fft_split", "chirp_detect",
                     "chirp_dedisperse_noalloc", "chirp_watchdog_selftest", "chirp_propnet_get_state",
-                    "chirp_propnet_set_state", "chirp_last_error")
+                    "chirp_propnet_set_state", "chirp_last_error", "chirp_cpi_create",
+                    "chirp_cpi_query", "chirp_cpi_layout", "chirp_cpi_run", "chirp_cpi_spectra",
+                    "chirp_cpi_timing", "chirp_cpi_destroy")
 STAGES = ("forward", "inv_rows", "inv_cols", "correlate", "beamform", "split", "chirp",
           "incoherent", "detect")
 

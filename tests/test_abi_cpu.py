@@ -86,3 +86,31 @@ def test_watchdog_selftest_rejects_a_poll_count_out_of_range():
     assert rc == chirp.CHIRP_EINVAL
     rc, ms = chirp.chirp_watchdog_selftest((1 << 24) + 1)
     assert rc == chirp.CHIRP_EINVAL
+
+
+def _cpi(**over):
+    from paper_1109_3186_gb300.cpi import CpiPlan
+    base = dict(xyz=np.array([[0.0, 0, 0], [1000.0, 0, 0], [0, 800.0, 0]]), f0=1.4e9, bw=8e6,
+                n_samp=1 << 14, dms=np.array([5.0, 10.0]), blk_len=256,
+                pix_lm=np.array([[0.0, 0.0], [0.005, 0.0]]), half_width=2, max_bin=0)
+    base.update(over)
+    return CpiPlan(**base)
+
+
+@pytest.mark.parametrize("over,msg", [
+    (dict(xyz=np.zeros((1, 3))), "n_ant"),
+    (dict(blk_len=100), "blk_len"),
+    (dict(blk_len=8), "blk_len"),
+    (dict(n_samp=100), "n_samp"),
+    (dict(dms=np.array([0.0])), "DM"),
+    (dict(dms=np.array([5000.0])), "longer than the data"),
+    (dict(half_width=9), "half_width"),
+    (dict(max_bin=65), "max_bin"),
+    (dict(max_bin=1), "below"),
+    (dict(bw=0.0), "bw_hz"),
+])
+def test_cpi_plan_validation_rejects_bad_shapes(over, msg):
+    with pytest.raises(chirp.ChirpError) as ei:
+        _cpi(**over)
+    assert ei.value.code == -1
+    assert msg in str(ei.value)
