@@ -50,7 +50,7 @@ constexpr int kChunk = 64;        // samples staged per step of the moment pass
 constexpr int kMaxSubPerBlk = 1024;
 constexpr int kFreqPerThread = 8; // frequencies evaluated per thread (partial pass)
 constexpr int kCicSeg = 256;      // blocks per thread of the moving sum
-constexpr int kImgBlocks = 8;     // blocks per CTA of the imaging pass
+constexpr int kImgBlocks = 16;    // blocks per CTA of the imaging pass (even)
 constexpr int kImgSmemBytes = 96 * 1024;
 constexpr double kPi = 3.14159265358979323846264338327950288;
 constexpr double kCLight = 299792458.0;
@@ -60,11 +60,21 @@ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {  // c + a
   return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
 }
 
+// hi + lo += x with the rounding error of hi + x carried in lo (TwoSum)
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float t = __fadd_rn(hi, x);
+  const float bp = __fsub_rn(t, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+  hi = t;
+  lo = __fadd_rn(lo, e);
+}
+
 // ---------------------------------------------------------------- moments
-// One CTA per sub-block s: the antennas' samples [s Ls, (s+1) Ls) are staged
-// kChunk at a time; item (pair, r) sums the samples i = r (mod R) of its pair's
-// mixed series x_p x_q^* into J moments, the R partial sums of a pair are
-// adjacent lanes and meet by shuffles.
+// One CTA per sub-block s (R * n_pair threads rounded up to whole warps, at
+// most 256): the antennas' samples [s Ls, (s+1) Ls) are staged kChunk at a
+// time; item (pair, r) sums the samples i = r (mod R) of its pair's mixed
+// series x_p x_q^* into J moments, the R partial sums of a pair are adjacent
+// lanes and meet by shuffles.
 __global__ void __launch_bounds__(256) k_cpi_moments(const float2* __restrict__ x, long long n_samp,
                                                      int n_ant, const short2* __restrict__ pairs,
                                                      int n_pair, int Ls, int J, int R,
@@ -72,7 +82,7 @@ __global__ void __launch_bounds__(256) k_cpi_moments(const float2* __restrict__ 
   __shared__ float2 xs[kMaxAnt * (kChunk + 1)];
   const long long s = blockIdx.x;
   const long long base = s * Ls;
-  const int per = 256 / R;  // pairs per pass
+  const int per = blockDim.x / R;  // pairs per pass (blockDim: a multiple of 32, <= 256)
   const float inv_ls = 1.0f / (float)Ls;  // a power of two: u below is exact
   for (int p0 = 0; p0 < n_pair; p0 += per) {
     const int item = threadIdx.x / R, r = threadIdx.x % R;
@@ -85,16 +95,41 @@ __global__ void __launch_bounds__(256) k_cpi_moments(const float2* __restrict__ 
     for (int c0 = 0; c0 < Ls; c0 += kChunk) {
       const int cn = min(kChunk, Ls - c0);
       __syncthreads();
-      for (int e = threadIdx.x; e < n_ant * cn; e += 256) {
+      for (int e = threadIdx.x; e < n_ant * cn; e += blockDim.x) {
         const int a = e / cn, i = e % cn;
         const long long t = base + c0 + i;
         xs[a * (kChunk + 1) + i] = t < n_samp ? x[(long long)a * n_samp + t] : make_float2(0.f, 0.f);
       }
       __syncthreads();
       if (act) {
-        for (int i = r; i < cn; i += R) {
+        // four samples per step: their power chains u^j run side by side
+        int i = r;
+        for (; i + 3 * R < cn; i += 4 * R) {
+          float2 mx[4];
+          float u[4], pw[4];
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            const int ii = i + q * R;
+            const float2 yp = xs[pq.x * (kChunk + 1) + ii], yq = xs[pq.y * (kChunk + 1) + ii];
+            // x_pq = y_p conj(y_q) (Eq. xpq)
+            mx[q] = make_float2(fmaf(yp.x, yq.x, yp.y * yq.y), fmaf(yp.y, yq.x, -yp.x * yq.y));
+            u[q] = (float)(2 * (c0 + ii) - Ls + 1) * inv_ls;
+            pw[q] = 1.f;
+          }
+#pragma unroll
+          for (int j = 0; j < kMaxTerms; j++) {
+            if (j < J) {
+#pragma unroll
+              for (int q = 0; q < 4; q++) {
+                acc[j].x = fmaf(pw[q], mx[q].x, acc[j].x);
+                acc[j].y = fmaf(pw[q], mx[q].y, acc[j].y);
+                pw[q] *= u[q];
+              }
+            }
+          }
+        }
+        for (; i < cn; i += R) {
           const float2 yp = xs[pq.x * (kChunk + 1) + i], yq = xs[pq.y * (kChunk + 1) + i];
-          // x_pq = y_p conj(y_q) (Eq. xpq)
           const float2 m = make_float2(fmaf(yp.x, yq.x, yp.y * yq.y), fmaf(yp.y, yq.x, -yp.x * yq.y));
           const float u = (float)(2 * (c0 + i) - Ls + 1) * inv_ls;
           float pw = 1.f;
@@ -253,7 +288,8 @@ __global__ void __launch_bounds__(256) k_cpi_partial(const float2* __restrict__ 
 // Item (d, segment, bin, pair), pair fastest: the window DFTs of kCicSeg
 // consecutive blocks.  The sum is started directly over the window that ends
 // just before the segment and then advanced by Eq. block_cic, S[m] = S[m-1] + V[m] - V[m - n_win],
-// in FP64; the result is moved to the window's own time,
+// in compensated FP32 (two floats per component); the result is moved to the
+// window's own time,
 // X[m] = exp(2 pi j (m + 1 - n_win) k / n_win) S[m] (a root of unity of order
 // n_win, reduced exactly in integers).  Incomplete windows and bins beyond
 // the pair's K_pq are zero.
@@ -282,48 +318,67 @@ __global__ void __launch_bounds__(256) k_cpi_cic(const float2* __restrict__ V,
   }
   const int nw = n_win[d];
   const float2* v = V + (long long)vrow[d * nk + kidx] * n_blk * n_pair + pair;
-  // S[m0 - 1] = sum of V over blocks [m0 - n_win, m0 - 1]
-  double sr = 0.0, si = 0.0;
+  // S[m0 - 1] = sum of V over blocks [m0 - n_win, m0 - 1], kept as an
+  // unevaluated sum hi + lo of two floats per component (TwoSum, Knuth):
+  // the running sum loses nothing to rounding over thousands of blocks
+  // while staying on the FP32 pipes.
+  float2 hi = make_float2(0.f, 0.f), lo = make_float2(0.f, 0.f);
   for (int mm = max(0, m0 - nw); mm < m0; mm++) {
     const float2 a = v[(long long)mm * n_pair];
-    sr += a.x;
-    si += a.y;
+    two_sum_acc(hi.x, lo.x, a.x);
+    two_sum_acc(hi.y, lo.y, a.y);
   }
-  const long long kk = ((k % nw) + nw) % nw;
-  for (int m = m0; m < m1; m++) {
-    const float2 a = v[(long long)m * n_pair];
-    sr += a.x;
-    si += a.y;
-    if (m - nw >= 0) {
-      const float2 b = v[(long long)(m - nw) * n_pair];
-      sr -= b.x;
-      si -= b.y;
+  // phase index r = ((m + 1) k) mod n_win, advanced by k each block
+  const int kk = ((k % nw) + nw) % nw;
+  int r = (int)(((long long)((m0 + 1) % nw) * kk) % nw);
+  constexpr int U = 4;  // blocks per step: their loads are issued together
+  for (int mu = m0; mu < m1; mu += U) {
+    float2 add[U], sub[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int m = mu + u;
+      add[u] = m < m1 ? v[(long long)m * n_pair] : make_float2(0.f, 0.f);
+      sub[u] = (m < m1 && m - nw >= 0) ? v[(long long)(m - nw) * n_pair] : make_float2(0.f, 0.f);
     }
-    float2 o = make_float2(0.f, 0.f);
-    if (m >= nw - 1) {
-      long long r2 = 2 * (((long long)(m + 1) % nw) * kk % nw);  // phase pi r2 / nw
-      if (r2 >= nw) r2 -= 2LL * nw;
-      float sn, cs;
-      sincospif((float)((double)r2 / (double)nw), &sn, &cs);
-      const float fr = (float)sr, fi = (float)si;
-      o = make_float2(fr * cs - fi * sn, fr * sn + fi * cs);
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int m = mu + u;
+      if (m >= m1) break;
+      two_sum_acc(hi.x, lo.x, add[u].x);
+      two_sum_acc(hi.y, lo.y, add[u].y);
+      two_sum_acc(hi.x, lo.x, -sub[u].x);
+      two_sum_acc(hi.y, lo.y, -sub[u].y);
+      float2 o = make_float2(0.f, 0.f);
+      if (m >= nw - 1) {
+        const int r2 = 2 * r >= nw ? 2 * r - 2 * nw : 2 * r;  // phase pi r2 / nw in [-pi, pi)
+        float sn, cs;
+        sincospif((float)r2 / (float)nw, &sn, &cs);
+        const float fr = hi.x + lo.x, fi = hi.y + lo.y;
+        o = make_float2(fr * cs - fi * sn, fr * sn + fi * cs);
+      }
+      out[m * ostride] = o;
+      r += kk;
+      if (r >= nw) r -= nw;
     }
-    out[m * ostride] = o;
   }
 }
 
 // ---------------------------------------------------------------- imaging
 // grid (pixel tiles of 256, block tiles of kImgBlocks, DM).  The window DFTs
-// of the tile's blocks are staged pc pairs at a time; each thread is one
-// pixel and accumulates P for the tile's blocks (Eq. pth with the 2F+1-bin
-// matched filter of Sec. 3.4), then writes E = |P|^2 (Eq. eth).
+// of the tile's blocks are staged pc pairs at a time as [pair][bin][block]
+// rows of kImgBlocks + 2 float2 (144 bytes: lanes whose pixels sit at
+// different bins read different 16-byte bank groups); each thread is one
+// pixel, reads a bin's kImgBlocks values with 128-bit loads and accumulates
+// P for the tile's blocks (Eq. pth with the 2F+1-bin matched filter of
+// Sec. 3.4), then writes E = |P|^2 (Eq. eth).
+constexpr int kImgRow = kImgBlocks + 2;  // float2 per staged bin row
 __global__ void __launch_bounds__(256) k_cpi_image(const float2* __restrict__ X,
                                                    const float2* __restrict__ W,
                                                    const short* __restrict__ K0,
                                                    const int* __restrict__ n_win, int n_pair,
                                                    int K, int F, int n_pix, int n_blk, int pc,
                                                    float* __restrict__ E) {
-  extern __shared__ float2 xs[];  // [block][bin][pc]
+  extern __shared__ __align__(16) float2 xs[];  // [pair][bin][kImgRow]
   const int nk = 2 * K + 1, nj = 2 * F + 1;
   const long long d = blockIdx.z;
   const int m0 = blockIdx.y * kImgBlocks;
@@ -342,10 +397,11 @@ __global__ void __launch_bounds__(256) k_cpi_image(const float2* __restrict__ X,
   for (int p0 = 0; p0 < n_pair; p0 += pc) {
     const int pn = min(pc, n_pair - p0);
     __syncthreads();
-    for (int e = threadIdx.x; e < mb * nk * pn; e += 256) {
-      const int b = e / (nk * pn), rem = e % (nk * pn);
-      const int kidx = rem / pn, pl = rem % pn;
-      xs[(b * nk + kidx) * pc + pl] = X[((d * n_blk + m0 + b) * nk + kidx) * n_pair + p0 + pl];
+    for (int e = threadIdx.x; e < kImgBlocks * nk * pn; e += 256) {
+      const int pl = e % pn, rest = e / pn;
+      const int kidx = rest % nk, b = rest / nk;
+      xs[(pl * nk + kidx) * kImgRow + b] =
+          b < mb ? X[((d * n_blk + m0 + b) * nk + kidx) * n_pair + p0 + pl] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     if (pix < n_pix) {
@@ -354,17 +410,23 @@ __global__ void __launch_bounds__(256) k_cpi_image(const float2* __restrict__ X,
         const int k0 = K0[dp * n_pix + pix];
         for (int j = 0; j < nj; j++) {
           const float2 w = W[(dp * nj + j) * n_pix + pix];
-          const float2* xr = xs + (k0 + j) * pc + pl;
+          const float4* row = reinterpret_cast<const float4*>(xs + (pl * nk + k0 + j) * kImgRow);
 #pragma unroll
-          for (int b = 0; b < kImgBlocks; b++)
-            if (b < mb) P[b] = cfma(w, xr[b * nk * pc], P[b]);
+          for (int q = 0; q < kImgBlocks / 2; q++) {
+            const float4 v = row[q];
+            P[2 * q] = cfma(w, make_float2(v.x, v.y), P[2 * q]);
+            P[2 * q + 1] = cfma(w, make_float2(v.z, v.w), P[2 * q + 1]);
+          }
         }
       }
     }
   }
-  if (pix < n_pix)
-    for (int b = 0; b < mb; b++)
-      e_out[(long long)b * n_pix] = (m0 + b >= nw - 1) ? P[b].x * P[b].x + P[b].y * P[b].y : 0.f;
+  if (pix < n_pix) {
+#pragma unroll
+    for (int b = 0; b < kImgBlocks; b++)  // static indices keep P in registers
+      if (b < mb)
+        e_out[(long long)b * n_pix] = (m0 + b >= nw - 1) ? P[b].x * P[b].x + P[b].y * P[b].y : 0.f;
+  }
 }
 
 // ---------------------------------------------------------- filter table
@@ -525,7 +587,7 @@ int plan_host(chirp_cpi_plan* p, const chirp_cpi_config* c, std::vector<double>&
   p->N = c->n_samp;
   p->L = c->blk_len;
   p->n_blk = c->n_samp / c->blk_len;
-  if (p->n_blk > 65535LL * kImgBlocks) return cfail(CHIRP_EINVAL, "more than 524280 blocks");
+  if (p->n_blk > 65535LL * kImgBlocks) return cfail(CHIRP_EINVAL, "more than 1048560 blocks");
   p->n_dm = c->n_dm;
   p->n_pix = c->n_pix;
   p->F = c->half_width;
@@ -618,7 +680,7 @@ int plan_host(chirp_cpi_plan* p, const chirp_cpi_config* c, std::vector<double>&
   while (p->R < 8 && 2 * p->R * p->n_pair <= 256) p->R *= 2;
   p->G = p->n_pair <= 256 ? std::min(32, 256 / p->n_pair) : 1;
   p->n_chunk = (p->n_freq + p->G * kFreqPerThread - 1) / (p->G * kFreqPerThread);
-  p->pc = std::max(1, std::min(p->n_pair, kImgSmemBytes / (kImgBlocks * nk * (int)sizeof(float2))));
+  p->pc = std::max(1, std::min(p->n_pair, kImgSmemBytes / ((kImgBlocks + 2) * nk * (int)sizeof(float2))));
   p->n_seg = (int)((p->n_blk + kCicSeg - 1) / kCicSeg);
   const long long cic_ctas = ((long long)p->n_dm * p->n_seg * nk * p->n_pair + 255) / 256;
   if (p->n_sub >= (1LL << 31) || (long long)p->n_chunk * p->n_blk >= (1LL << 31) ||
@@ -646,8 +708,9 @@ int cpi_enqueue(chirp_cpi_plan* p, const void* volt, int volt_loc, float* E) {
   }
   const int nk = 2 * p->K + 1;
   CKC(cudaEventRecord(p->ev[0], p->st));
-  k_cpi_moments<<<(unsigned)p->n_sub, 256, 0, p->st>>>(x, p->N, p->M, p->d_pairs, p->n_pair, p->Ls,
-                                                       p->J, p->R, p->d_T);
+  const int mom_threads = std::min(256, (p->R * p->n_pair + 31) / 32 * 32);
+  k_cpi_moments<<<(unsigned)p->n_sub, mom_threads, 0, p->st>>>(x, p->N, p->M, p->d_pairs, p->n_pair,
+                                                               p->Ls, p->J, p->R, p->d_T);
   CKC(cudaGetLastError());
   CKC(cudaEventRecord(p->ev[1], p->st));
   k_cpi_partial<<<(unsigned)((long long)p->n_chunk * p->n_blk), 256, 0, p->st>>>(
