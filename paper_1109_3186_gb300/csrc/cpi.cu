@@ -364,13 +364,15 @@ __global__ void __launch_bounds__(256) k_cpi_cic(const float2* __restrict__ V,
 }
 
 // ---------------------------------------------------------------- imaging
-// grid (pixel tiles of 256, block tiles of kImgBlocks, DM).  The window DFTs
+// grid (pixel tiles of 512, block tiles of kImgBlocks, DM).  The window DFTs
 // of the tile's blocks are staged pc pairs at a time as [pair][bin][block]
-// rows of kImgBlocks + 2 float2 (144 bytes: lanes whose pixels sit at
-// different bins read different 16-byte bank groups); each thread is one
-// pixel, reads a bin's kImgBlocks values with 128-bit loads and accumulates
-// P for the tile's blocks (Eq. pth with the 2F+1-bin matched filter of
-// Sec. 3.4), then writes E = |P|^2 (Eq. eth).
+// rows of kImgBlocks + 2 float2 (144 bytes: lanes at different bins read
+// different 16-byte bank groups).  Each thread is two adjacent pixels, whose
+// filters cover nearly the same bins: per pair it walks the union of their
+// 2F+1-bin ranges, reads each staged row once (128-bit loads, 8 blocks at a
+// time) and adds it, times each pixel's weight for that bin (zero outside the
+// pixel's range), to P of the tile's blocks (Eq. pth with the matched filter
+// of Sec. 3.4); then E = |P|^2 (Eq. eth).
 constexpr int kImgRow = kImgBlocks + 2;  // float2 per staged bin row
 __global__ void __launch_bounds__(256) k_cpi_image(const float2* __restrict__ X,
                                                    const float2* __restrict__ W,
@@ -383,17 +385,20 @@ __global__ void __launch_bounds__(256) k_cpi_image(const float2* __restrict__ X,
   const long long d = blockIdx.z;
   const int m0 = blockIdx.y * kImgBlocks;
   const int mb = min(kImgBlocks, n_blk - m0);
-  const int pix = blockIdx.x * 256 + threadIdx.x;
+  const int pa = blockIdx.x * 512 + 2 * threadIdx.x, pb = pa + 1;
+  const bool va = pa < n_pix, vb = pb < n_pix;
   const int nw = n_win[d];
-  float* e_out = E + (d * n_blk + m0) * n_pix + pix;
+  float* e_out = E + (d * n_blk + m0) * n_pix;
   if (m0 + mb - 1 < nw - 1) {  // every window of the tile is incomplete
-    if (pix < n_pix)
-      for (int b = 0; b < mb; b++) e_out[(long long)b * n_pix] = 0.f;
+    for (int b = 0; b < mb; b++) {
+      if (va) e_out[(long long)b * n_pix + pa] = 0.f;
+      if (vb) e_out[(long long)b * n_pix + pb] = 0.f;
+    }
     return;
   }
-  float2 P[kImgBlocks];
+  float2 Pa[kImgBlocks], Pb[kImgBlocks];
 #pragma unroll
-  for (int b = 0; b < kImgBlocks; b++) P[b] = make_float2(0.f, 0.f);
+  for (int b = 0; b < kImgBlocks; b++) Pa[b] = Pb[b] = make_float2(0.f, 0.f);
   for (int p0 = 0; p0 < n_pair; p0 += pc) {
     const int pn = min(pc, n_pair - p0);
     __syncthreads();
@@ -404,28 +409,38 @@ __global__ void __launch_bounds__(256) k_cpi_image(const float2* __restrict__ X,
           b < mb ? X[((d * n_blk + m0 + b) * nk + kidx) * n_pair + p0 + pl] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    if (pix < n_pix) {
+    if (va) {
       for (int pl = 0; pl < pn; pl++) {
         const long long dp = d * n_pair + p0 + pl;
-        const int k0 = K0[dp * n_pix + pix];
-        for (int j = 0; j < nj; j++) {
-          const float2 w = W[(dp * nj + j) * n_pix + pix];
-          const float4* row = reinterpret_cast<const float4*>(xs + (pl * nk + k0 + j) * kImgRow);
+        const int ka = K0[dp * n_pix + pa];
+        const int kb = vb ? K0[dp * n_pix + pb] : ka;
+        const int lo = min(ka, kb), hi = max(ka, kb) + nj;  // rows [lo, hi), within [0, nk)
+        for (int r = lo; r < hi; r++) {
+          const int ja = r - ka, jb = r - kb;
+          const float2 wa = (ja >= 0 && ja < nj) ? W[(dp * nj + ja) * n_pix + pa] : make_float2(0.f, 0.f);
+          const float2 wb = (vb && jb >= 0 && jb < nj) ? W[(dp * nj + jb) * n_pix + pb]
+                                                       : make_float2(0.f, 0.f);
+          const float4* row = reinterpret_cast<const float4*>(xs + (pl * nk + r) * kImgRow);
 #pragma unroll
           for (int q = 0; q < kImgBlocks / 2; q++) {
             const float4 v = row[q];
-            P[2 * q] = cfma(w, make_float2(v.x, v.y), P[2 * q]);
-            P[2 * q + 1] = cfma(w, make_float2(v.z, v.w), P[2 * q + 1]);
+            const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
+            Pa[2 * q] = cfma(wa, v0, Pa[2 * q]);
+            Pa[2 * q + 1] = cfma(wa, v1, Pa[2 * q + 1]);
+            Pb[2 * q] = cfma(wb, v0, Pb[2 * q]);
+            Pb[2 * q + 1] = cfma(wb, v1, Pb[2 * q + 1]);
           }
         }
       }
     }
   }
-  if (pix < n_pix) {
 #pragma unroll
-    for (int b = 0; b < kImgBlocks; b++)  // static indices keep P in registers
-      if (b < mb)
-        e_out[(long long)b * n_pix] = (m0 + b >= nw - 1) ? P[b].x * P[b].x + P[b].y * P[b].y : 0.f;
+  for (int b = 0; b < kImgBlocks; b++) {  // static indices keep P in registers
+    if (b < mb) {
+      const bool ok = m0 + b >= nw - 1;
+      if (va) e_out[(long long)b * n_pix + pa] = ok ? Pa[b].x * Pa[b].x + Pa[b].y * Pa[b].y : 0.f;
+      if (vb) e_out[(long long)b * n_pix + pb] = ok ? Pb[b].x * Pb[b].x + Pb[b].y * Pb[b].y : 0.f;
+    }
   }
 }
 
@@ -725,7 +740,7 @@ int cpi_enqueue(chirp_cpi_plan* p, const void* volt, int volt_loc, float* E) {
   CKC(cudaGetLastError());
   CKC(cudaEventRecord(p->ev[3], p->st));
   if (E) {
-    const dim3 grid((unsigned)((p->n_pix + 255) / 256), (unsigned)((p->n_blk + kImgBlocks - 1) / kImgBlocks),
+    const dim3 grid((unsigned)((p->n_pix + 511) / 512), (unsigned)((p->n_blk + kImgBlocks - 1) / kImgBlocks),
                     (unsigned)p->n_dm);
     k_cpi_image<<<grid, 256, kImgSmemBytes, p->st>>>(p->d_X, p->d_W, p->d_K0, p->d_nwin, p->n_pair,
                                                      p->K, p->F, p->n_pix, (int)p->n_blk, p->pc, E);
