@@ -539,7 +539,7 @@ def cpi_search(sc, xd, stream, args, peaks):
            "stages_ms": st,
            "roofline": {n: {"bound": b, "achieved": a, "peak": pk, "unit": u, "frac": a / pk}
                         for n, (b, a, pk, u) in roof.items()},
-           "dtype": "f32 (moving sums f64)",
+           "dtype": "f32 (moving sums compensated, two floats)",
            "note": "paper's own pre-integrator on the raw voltages: DMs > 0 of the 64"}
     plan.close()
     return out

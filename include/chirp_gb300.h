@@ -427,8 +427,9 @@ int chirp_watchdog_selftest(unsigned int polls, double* waited_ms, void* stream)
  * D_N the Dirichlet kernel (Eq. dn).  Pair pq needs bins |k| <= K_pq =
  * max over DMs and pixels of |k0'| + F (Sec. A.3.1); bins beyond it are not
  * computed and read as zero.
- * All arithmetic is FP32 on the CUDA cores except the moving sums (FP64) and
- * the filter table (FP64, rounded once).  The partial DFTs are evaluated by a
+ * All arithmetic is FP32 on the CUDA cores; the moving sums carry each sum as
+ * two floats (compensated, TwoSum) and the filter table is built in FP64 and
+ * rounded once.  The partial DFTs are evaluated by a
  * Taylor expansion inside sub-blocks whose truncation is below 1e-9 of the
  * sub-block's sum of |x_pq| (chirp_cpi_info.sub_len, .n_terms).
  * ---------------------------------------------------------------------- */

@@ -8,7 +8,8 @@ windows of the 12-antenna, 2^22-sample, 63-DM workload.
 Tolerances (FP32 arithmetic, unit roundoff u = 6e-8): a partial DFT sums L
 mixed products, so its error is at most ~sqrt(L) u of the block's scale
 (1e-6 at L = 256) plus the Taylor truncation (1e-9) and FP32 phases
-(~3e-7 rad); the window DFTs add the blocks in FP64.  V and X are held to
+(~3e-7 rad); the window DFTs add the blocks in compensated FP32 (two
+floats per sum).  V and X are held to
 2e-5 of their largest magnitude per DM, E = |P|^2 to 1e-4 of its largest
 value per DM."""
 import math
