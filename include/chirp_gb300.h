@@ -486,6 +486,53 @@ int chirp_cpi_spectra(chirp_cpi_plan* plan, const void* volt, int volt_loc, void
 int chirp_cpi_timing(chirp_cpi_plan* plan, double ms[4]);
 void chirp_cpi_destroy(chirp_cpi_plan* plan);
 
+/* ------------------------------------------------------------------------
+ * The paper's own Chimageator pre-integrator (Sec. 4.2, App. B.2) on a
+ * uniform linear array: antennas p = 0..M-1 at p * spacing_m along u, for
+ * every trial DM:
+ *   mixing       x_{p,p+l}[n] = y_p[n] y_{p+l}[n]^* (Eq. xpq_chimg)
+ *   gridding     x'_l[n] = sum_{p<M-l} w_l x_{p,p+l}[n], l = 1..M-1, with
+ *                w_l = 1/(M-l) (weights = 0, the paper's "natural") or 1
+ *   spatial DFT  X_k[n] = sum_l exp(-2 pi j k l / Ns) x'_l[n], k < Ns
+ *   integrate    Y_k[m] = sum_{i<L} X_k[i + mL], m < n_dump = floor(n_samp / L)
+ *   trajectory   P = sum_{r<n_win} sum_{k = k0'(r)-F}^{k0'(r)+F} w Y_k[m-n_win+1+r]
+ *                (Eq. chimg_pth, App. B.2.3), E = |P|^2 (Eq. eth)
+ * The trial chirp and its window follow the Chirpolator pre-integrator's
+ * conventions (rate a1, centre a0, n_win = max(1, floor(B T / L + 1/2))
+ * dumps, the chirp's temporal midpoint at the window centre).  For direction
+ * cosine l_dir (tau = spacing_m l_dir / c) the spatial tone is
+ * nu(t) = tau (a0 + a1 (t - t_c)) cycles per spacing, k0'(r) = rint(Ns nu) mod Ns
+ * at dump r's centre, and w = conj(Yhat) / ((M - 1) L), Yhat the expected Y
+ * of a unit chirp (closed form in FP64).  Gridding, DFT and integration
+ * commute: the GPU sums each dump first (FP32).
+ * ---------------------------------------------------------------------- */
+typedef struct chirp_chimg_plan chirp_chimg_plan;
+typedef struct {
+  int n_ant;             /* M, 2..32                                           */
+  double spacing_m;      /* element spacing D, metres                          */
+  double f0_hz, bw_hz;   /* band centre; bandwidth = complex sample rate        */
+  double k_dm;           /* <= 0 selects 4.148808e15                           */
+  long long n_samp;      /* samples per antenna, >= dump_len                   */
+  const double* dm;      /* [n_dm] trial DMs, each > 0 (HOST)                  */
+  int n_dm;
+  int dump_len;          /* L                                                  */
+  const double* l_dir;   /* [n_pix] direction cosines along the array (HOST)   */
+  int n_pix;
+  int n_spatial;         /* Ns, n_ant..1024                                    */
+  int half_width;        /* F, 0..8, 2F+1 <= Ns                                */
+  int weights;           /* 0: 1/(M-l), 1: 1                                   */
+} chirp_chimg_config;
+/* Errors: CHIRP_EINVAL (bad size, DM <= 0, a sweep longer than the data),
+ * CHIRP_ENOMEM, CHIRP_ECUDA; *out is NULL on failure. */
+int chirp_chimg_create(chirp_chimg_plan** out, const chirp_chimg_config* cfg, void* stream);
+/* n_dump, and n_win of every DM ([n_dm], may be NULL). */
+int chirp_chimg_query(const chirp_chimg_plan* plan, long long* n_dump, int* n_win);
+/* Y [n_dump][Ns] complex64 from complex64 voltages [n_ant][n_samp]. */
+int chirp_chimg_grid(chirp_chimg_plan* plan, const void* volt, int volt_loc, void* Y, int out_loc);
+/* E [n_dm][n_dump][n_pix] float; zero for incomplete windows. */
+int chirp_chimg_run(chirp_chimg_plan* plan, const void* volt, int volt_loc, float* energy, int out_loc);
+void chirp_chimg_destroy(chirp_chimg_plan* plan);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* chirp_last_error(void);
 

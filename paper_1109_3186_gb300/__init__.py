@@ -50,7 +50,9 @@ EXPORTED_SYMBOLS = ("chirp_plan_create", "chirp_plan_destroy", "chirp_plan_query
                     "chirp_dedisperse_noalloc", "chirp_watchdog_selftest", "chirp_propnet_get_state",
                     "chirp_propnet_set_state", "chirp_last_error", "chirp_cpi_create",
                     "chirp_cpi_query", "chirp_cpi_layout", "chirp_cpi_run", "chirp_cpi_spectra",
-                    "chirp_cpi_timing", "chirp_cpi_destroy")
+                    "chirp_cpi_timing", "chirp_cpi_destroy", "chirp_chimg_create",
+                    "chirp_chimg_query", "chirp_chimg_grid", "chirp_chimg_run",
+                    "chirp_chimg_destroy")
 STAGES = ("forward", "inv_rows", "inv_cols", "correlate", "beamform", "split", "chirp",
           "incoherent", "detect")
 

@@ -1,0 +1,99 @@
+"""ctypes binding of the Chimageator pre-integrator on a uniform linear array
+(the chirp_chimg_* entry points of include/chirp_gb300.h): argument
+marshalling only, every step runs in the CUDA library.
+
+The search (Sec. 4.2, App. B.2 of the paper) mixes every antenna pair, grids
+equal spacings, takes a spatial DFT, integrates and dumps, and sums 2F+1
+bins per dump along each trial chirp's trajectory (Eq. chimg_pth, Eq. eth).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _buf, _check, _stream_handle, load
+
+__all__ = ["ChimgPlan"]
+
+
+class _ChimgConfig(ctypes.Structure):
+    _fields_ = [("n_ant", ctypes.c_int), ("spacing_m", ctypes.c_double), ("f0_hz", ctypes.c_double),
+                ("bw_hz", ctypes.c_double), ("k_dm", ctypes.c_double), ("n_samp", ctypes.c_longlong),
+                ("dm", ctypes.POINTER(ctypes.c_double)), ("n_dm", ctypes.c_int),
+                ("dump_len", ctypes.c_int), ("l_dir", ctypes.POINTER(ctypes.c_double)),
+                ("n_pix", ctypes.c_int), ("n_spatial", ctypes.c_int), ("half_width", ctypes.c_int),
+                ("weights", ctypes.c_int)]
+
+
+def _lib():
+    lib = load()
+    if not getattr(lib, "_chimg_ready", False):
+        vp, i = ctypes.c_void_p, ctypes.c_int
+        lib.chirp_chimg_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_ChimgConfig), vp]
+        lib.chirp_chimg_create.restype = i
+        lib.chirp_chimg_query.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), vp]
+        lib.chirp_chimg_query.restype = i
+        lib.chirp_chimg_grid.argtypes = [vp, vp, i, vp, i]
+        lib.chirp_chimg_grid.restype = i
+        lib.chirp_chimg_run.argtypes = [vp, vp, i, vp, i]
+        lib.chirp_chimg_run.restype = i
+        lib.chirp_chimg_destroy.argtypes = [vp]
+        lib.chirp_chimg_destroy.restype = None
+        lib._chimg_ready = True
+    return lib
+
+
+class ChimgPlan:
+    """A Chimageator pre-integrator plan (chirp_chimg_create) for n_ant antennas
+    at spacing_m along u.  grid() fills Y [n_dump, Ns] complex64; run() fills
+    E [n_dm, n_dump, n_pix] float32."""
+
+    def __init__(self, n_ant, spacing_m, f0, bw, n_samp, dms, dump_len, l_dir, n_spatial,
+                 half_width=1, weights="natural", k_dm=0.0, stream=None):
+        self._dms = np.ascontiguousarray(np.asarray(dms, np.float64).ravel())
+        self._ld = np.ascontiguousarray(np.asarray(l_dir, np.float64).ravel())
+        c = _ChimgConfig()
+        c.n_ant, c.spacing_m = int(n_ant), float(spacing_m)
+        c.f0_hz, c.bw_hz, c.k_dm = float(f0), float(bw), float(k_dm)
+        c.n_samp = int(n_samp)
+        c.dm = self._dms.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        c.n_dm = len(self._dms)
+        c.dump_len = int(dump_len)
+        c.l_dir = self._ld.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        c.n_pix = len(self._ld)
+        c.n_spatial, c.half_width = int(n_spatial), int(half_width)
+        c.weights = {"natural": 0, "uniform": 1}[weights]
+        self._h = ctypes.c_void_p()
+        _check(_lib().chirp_chimg_create(ctypes.byref(self._h), ctypes.byref(c), _stream_handle(stream)))
+        nd = ctypes.c_longlong()
+        self.n_win = np.zeros(c.n_dm, np.int32)
+        _check(_lib().chirp_chimg_query(self._h, ctypes.byref(nd), ctypes.c_void_p(self.n_win.ctypes.data)))
+        self.n_dump, self.n_dm, self.n_pix, self.n_spatial = nd.value, c.n_dm, c.n_pix, c.n_spatial
+
+    def grid(self, volt, Y) -> None:
+        vp, vl, _k1 = _buf(volt, np.complex64, "volt")
+        yp, yl, _k2 = _buf(Y, np.complex64, "Y")
+        _check(_lib().chirp_chimg_grid(self._h, vp, vl, yp, yl))
+
+    def run(self, volt, energy) -> None:
+        vp, vl, _k1 = _buf(volt, np.complex64, "volt")
+        ep, el, _k2 = _buf(energy, np.float32, "energy")
+        _check(_lib().chirp_chimg_run(self._h, vp, vl, ep, el))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            _lib().chirp_chimg_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

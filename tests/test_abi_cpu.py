@@ -114,3 +114,24 @@ def test_cpi_plan_validation_rejects_bad_shapes(over, msg):
         _cpi(**over)
     assert ei.value.code == -1
     assert msg in str(ei.value)
+
+
+@pytest.mark.parametrize("over,msg", [
+    (dict(n_ant=1), "n_ant"),
+    (dict(n_ant=40), "n_ant"),
+    (dict(spacing_m=0.0), "spacing_m"),
+    (dict(n_spatial=4), "n_spatial"),
+    (dict(half_width=5, n_spatial=8), "half_width"),
+    (dict(dms=[0.0]), "DM"),
+    (dict(dms=[5000.0]), "longer than the data"),
+    (dict(dump_len=0), "dump_len"),
+])
+def test_chimg_plan_validation_rejects_bad_shapes(over, msg):
+    from paper_1109_3186_gb300.chimg import ChimgPlan
+    base = dict(n_ant=6, spacing_m=50.0, f0=1.4e9, bw=8e6, n_samp=1 << 14, dms=[5.0], dump_len=256,
+                l_dir=[0.0, 0.01], n_spatial=16, half_width=1)
+    base.update(over)
+    with pytest.raises(chirp.ChirpError) as ei:
+        ChimgPlan(**base)
+    assert ei.value.code == -1
+    assert msg in str(ei.value)

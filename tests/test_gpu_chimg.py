@@ -1,0 +1,70 @@
+"""Parity of the CUDA Chimageator pre-integrator on a uniform linear array
+(chirp_chimg_*) with the FP64 oracle (oracle/chimg.py): the integrated
+spatial spectra Y and the trajectory images E element by element, for 5 to
+32 antennas, both weightings, F = 0..2 and a ragged tail; and a perfect
+chirp found at its direction.
+
+Tolerances: the GPU sums each dump's L products per spacing in FP32 before
+the spatial DFT (the oracle transforms every sample), so Y agrees to a few
+FP32 roundings of the dump's sum: 1e-5 of its largest magnitude.  E = |P|^2
+sums (2F+1) n_win filter taps: 1e-4 of its largest value per DM."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import chimg as ochimg
+from oracle import cpi as ocpi
+from paper_1109_3186_gb300 import skymodel
+from paper_1109_3186_gb300.chimg import ChimgPlan
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+K_DM = skymodel.K_DM
+F0, BW = 1.4e9, 8e6
+
+
+def _voltages(M, D, n_samp, dm, L, seed, l_dir, amp):
+    y = skymodel.noise(M, n_samp, seed).astype(np.complex128)
+    if amp:
+        _, a0, a1 = ocpi.chirp_model(F0, BW, K_DM, dm)
+        nw = ocpi.window_blocks(F0, BW, K_DM, dm, L)
+        tc = (2 * L + nw * L / 2.0) / BW
+        t = np.arange(n_samp) / BW
+        for p in range(M):
+            tau = p * D * l_dir / 299792458.0
+            u = t - tc - tau
+            y[p] += amp * np.exp(2j * math.pi * ((a0 - F0) * u + 0.5 * a1 * u * u)) \
+                * np.exp(-2j * math.pi * F0 * tau)
+    return y.astype(np.complex64)
+
+
+CASES = {
+    "8ant_natural": (8, 40.0, 1 << 14, [5.0, 20.0], 256, 16, 1, "natural", 31, 12, 0.5),
+    "5ant_uniform_ragged_F0": (5, 80.0, 64 * 50 + 7, [2.0, 6.0], 64, 8, 0, "uniform", 32, 7, 0.0),
+    "32ant_F2": (32, 20.0, 1 << 13, [3.0], 128, 64, 2, "natural", 33, 9, 0.3),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_grid_and_image_match_the_oracle(name):
+    M, D, n, dms, L, Ns, F, w, seed, n_pix, amp = CASES[name]
+    l_dirs = np.linspace(-0.01, 0.01, n_pix)
+    y = _voltages(M, D, n, dms[-1], L, seed, l_dirs[n_pix // 3], amp)
+    Yo = ochimg.integrate(ochimg.spatial_dft(ochimg.mix_grid(y, w), Ns), L)      # [Ns][n_dump]
+    Eo = ochimg.image(Yo, M, D, l_dirs, F0, BW, K_DM, dms, L, Ns, F, w)
+    with ChimgPlan(M, D, F0, BW, n, dms, L, l_dirs, Ns, F, weights=w, k_dm=K_DM) as plan:
+        assert plan.n_dump == Yo.shape[1]
+        assert list(plan.n_win) == [ocpi.window_blocks(F0, BW, K_DM, dm, L) for dm in dms]
+        Y = np.empty((plan.n_dump, Ns), np.complex64)
+        plan.grid(y, Y)
+        assert np.abs(Y - Yo.T).max() <= 1e-5 * np.abs(Yo).max()
+        E = np.empty((len(dms), plan.n_dump, n_pix), np.float32)
+        plan.run(y, E)
+        Ed = torch.empty(E.shape, dtype=torch.float32, device="cuda")
+        plan.run(torch.from_numpy(y).cuda(), Ed)
+        assert np.array_equal(E, Ed.cpu().numpy())
+        for d in range(len(dms)):
+            assert np.all(E[d][Eo[d] == 0] == 0)
+            assert np.abs(E[d] - Eo[d]).max() <= 1e-4 * Eo[d].max(), d
