@@ -465,7 +465,8 @@ typedef struct {
 
 /* Creates a plan (device workspace, FP64 filter table) whose work is queued
  * on `stream` (a cudaStream_t, NULL = legacy default stream).  Errors:
- * CHIRP_EINVAL (bad size, DM <= 0, max_bin below what the pixels need),
+ * CHIRP_EINVAL (bad size, DM <= 0, a pixel with l^2 + m^2 > 1, max_bin below
+ * what the pixels need),
  * CHIRP_EUNSUPPORTED (more than 1024 sub-blocks per block would be needed),
  * CHIRP_ENOMEM, CHIRP_ECUDA.  *out is NULL on failure. */
 int chirp_cpi_create(chirp_cpi_plan** out, const chirp_cpi_config* cfg, void* stream);
@@ -522,7 +523,8 @@ typedef struct {
   int half_width;        /* F, 0..8, 2F+1 <= Ns                                */
   int weights;           /* 0: 1/(M-l), 1: 1                                   */
 } chirp_chimg_config;
-/* Errors: CHIRP_EINVAL (bad size, DM <= 0, a sweep longer than the data),
+/* Errors: CHIRP_EINVAL (bad size, DM <= 0, |l_dir| > 1, a sweep longer than
+ * the data), CHIRP_EUNSUPPORTED (2^31 or more dumps x directions),
  * CHIRP_ENOMEM, CHIRP_ECUDA; *out is NULL on failure. */
 int chirp_chimg_create(chirp_chimg_plan** out, const chirp_chimg_config* cfg, void* stream);
 /* n_dump, and n_win of every DM ([n_dm], may be NULL). */

@@ -267,6 +267,11 @@ int chirp_chimg_create(chirp_chimg_plan** out, const chirp_chimg_config* c, void
     return gfail(CHIRP_EINVAL, "half_width must be in 0..8 with 2F+1 <= n_spatial");
   if (c->n_dm < 1 || c->n_dm > 65535 || c->n_pix < 1) return gfail(CHIRP_EINVAL, "n_dm in 1..65535, n_pix >= 1");
   if (c->weights != 0 && c->weights != 1) return gfail(CHIRP_EINVAL, "weights must be 0 or 1");
+  for (int i = 0; i < c->n_pix; i++)
+    if (!(std::fabs(c->l_dir[i]) <= 1.0)) return gfail(CHIRP_EINVAL, "direction %d has |l_dir| > 1", i);
+  if (c->n_samp / c->dump_len >= (1LL << 31) ||
+      (c->n_samp / c->dump_len) * (long long)c->n_pix / 256 >= (1LL << 31))
+    return gfail(CHIRP_EUNSUPPORTED, "too many dumps x directions for one launch");
   chirp_chimg_plan* p = new (std::nothrow) chirp_chimg_plan();
   if (!p) return gfail(CHIRP_ENOMEM, "host allocation failed");
   p->M = c->n_ant;

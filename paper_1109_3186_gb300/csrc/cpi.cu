@@ -630,6 +630,7 @@ int plan_host(chirp_cpi_plan* p, const chirp_cpi_config* c, std::vector<double>&
   tau.resize((size_t)p->n_pix * p->M);
   for (int i = 0; i < p->n_pix; i++) {
     const double l = c->pix_lm[2 * i], m = c->pix_lm[2 * i + 1];
+    if (!(l * l + m * m <= 1.0)) return cfail(CHIRP_EINVAL, "pixel %d has l^2 + m^2 > 1", i);
     const double n = std::sqrt(std::max(0.0, 1.0 - l * l - m * m));
     for (int a = 0; a < p->M; a++) {
       const double* r = c->xyz_m + 3 * a;

@@ -108,6 +108,7 @@ def _cpi(**over):
     (dict(max_bin=65), "max_bin"),
     (dict(max_bin=1), "below"),
     (dict(bw=0.0), "bw_hz"),
+    (dict(pix_lm=np.array([[0.9, 0.9]])), "l^2"),
 ])
 def test_cpi_plan_validation_rejects_bad_shapes(over, msg):
     with pytest.raises(chirp.ChirpError) as ei:
@@ -125,6 +126,7 @@ def test_cpi_plan_validation_rejects_bad_shapes(over, msg):
     (dict(dms=[0.0]), "DM"),
     (dict(dms=[5000.0]), "longer than the data"),
     (dict(dump_len=0), "dump_len"),
+    (dict(l_dir=[0.0, 1.5]), "l_dir"),
 ])
 def test_chimg_plan_validation_rejects_bad_shapes(over, msg):
     from paper_1109_3186_gb300.chimg import ChimgPlan
