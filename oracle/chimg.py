@@ -121,3 +121,104 @@ def search(y, D, l_dirs, f0, bw, k_dm, dms, L, Ns, F, weights="natural"):
     M = np.asarray(y).shape[0]
     Y = integrate(spatial_dft(mix_grid(y, weights), Ns), L)
     return image(Y, M, D, l_dirs, f0, bw, k_dm, dms, L, Ns, F, weights)
+
+
+# ------------------------------------------------ uniform rectangular array
+# Antenna a = iy * Mx + ix at (ix Dx, iy Dy, 0).  Spacings (lx, ly) of the
+# half plane ly > 0, or ly = 0 and lx > 0, each gridded as the weighted sum of
+# its pairs (p, q = p + (lx, ly)); the spatial DFT is 2-D over that grid:
+#   X[kx][ky][n] = sum_{lx,ly} exp(-2 pi j (kx lx / Nx + ky ly / Ny)) x'_{lx,ly}[n].
+# A unit chirp from (l, m) puts the tone nu = (Dx l, Dy m)(a_0 + fdot (t - t_c))/c
+# cycles per spacing on the grid; the trajectory sums take (2Fx+1)(2Fy+1) bins
+# per dump around (rint(Nx nu_x), rint(Ny nu_y)) (mod Nx, Ny) with the conjugate
+# expected Y divided by (number of spacings) L.  With My = 1, Ny = 1 and
+# Fy = 0 every step is the uniform linear array's.
+
+def spacings_2d(Mx: int, My: int):
+    """Half-plane spacings (lx, ly) and, for each, its pairs (p, q)."""
+    out = {}
+    for iy in range(My):
+        for ix in range(Mx):
+            for jy in range(My):
+                for jx in range(Mx):
+                    lx, ly = jx - ix, jy - iy
+                    if ly > 0 or (ly == 0 and lx > 0):
+                        out.setdefault((lx, ly), []).append((iy * Mx + ix, jy * Mx + jx))
+    keys = sorted(out, key=lambda s: (s[1], s[0]))
+    return keys, [out[k] for k in keys]
+
+
+def mix_grid_2d(y, Mx: int, My: int, weights: str = "natural"):
+    """x'[s][n] for the half-plane spacings s (steps 1 and 2)."""
+    y = np.asarray(y, np.complex128)
+    keys, prs = spacings_2d(Mx, My)
+    out = np.zeros((len(keys), y.shape[1]), np.complex128)
+    for s, pl in enumerate(prs):
+        w = 1.0 / len(pl) if weights == "natural" else 1.0
+        for p, q in pl:
+            out[s] += w * y[p] * np.conj(y[q])
+    return out
+
+
+def spatial_dft_2d(xg, Mx: int, My: int, Nx: int, Ny: int):
+    """X[kx][ky][n] over the half-plane grid (step 3)."""
+    keys, _ = spacings_2d(Mx, My)
+    kx = np.arange(Nx)[:, None, None]
+    ky = np.arange(Ny)[None, :, None]
+    lx = np.array([k[0] for k in keys])[None, None, :]
+    ly = np.array([k[1] for k in keys])[None, None, :]
+    basis = np.exp(-2j * math.pi * (kx * lx / Nx + ky * ly / Ny))          # [Nx][Ny][S]
+    return np.einsum("abs,sn->abn", basis, xg)
+
+
+def expected_y_2d(Mx, My, Dx, Dy, l, m, f0, bw, k_dm, dm, L, Nx, Ny, m_rel, weights="natural"):
+    """Expected Y[kx][ky] of a unit linear chirp from (l, m) in dump m_rel of the window."""
+    _, a0, a1 = cpi.chirp_model(f0, bw, k_dm, dm)
+    n_win = cpi.window_blocks(f0, bw, k_dm, dm, L)
+    t = (m_rel * L + np.arange(L) - n_win * L / 2.0) / bw
+    pos = [(ix * Dx, iy * Dy) for iy in range(My) for ix in range(Mx)]
+    tau = np.array([(px * l + py * m) / C_LIGHT for px, py in pos])
+    keys, prs = spacings_2d(Mx, My)
+    xg = np.zeros((len(keys), L), np.complex128)
+    for s, pl in enumerate(prs):
+        w = 1.0 / len(pl) if weights == "natural" else 1.0
+        for p, q in pl:
+            dt = tau[p] - tau[q]
+            xg[s] += w * np.exp(-2j * math.pi * dt * (a0 + a1 * t)) \
+                * np.exp(1j * math.pi * a1 * (tau[p] ** 2 - tau[q] ** 2))
+    return spatial_dft_2d(xg, Mx, My, Nx, Ny).sum(axis=2)
+
+
+def trajectory_bins_2d(Dx, Dy, l, m, f0, bw, k_dm, dm, L, Nx, Ny, m_rel):
+    _, a0, a1 = cpi.chirp_model(f0, bw, k_dm, dm)
+    n_win = cpi.window_blocks(f0, bw, k_dm, dm, L)
+    tm = (m_rel * L + (L - 1) / 2.0 - n_win * L / 2.0) / bw
+    fr = a0 + a1 * tm
+    return (int(np.rint(Nx * Dx * l * fr / C_LIGHT)) % Nx, int(np.rint(Ny * Dy * m * fr / C_LIGHT)) % Ny)
+
+
+def search_2d(y, Mx, My, Dx, Dy, pix_lm, f0, bw, k_dm, dms, L, Nx, Ny, F, weights="natural"):
+    """E[d][m][pix] for a uniform rectangular array (steps 1-5); F is the
+    half width (Fx, Fy) of the bin neighbourhood, or one value for both."""
+    Fx, Fy = (F, F) if np.isscalar(F) else F
+    keys, _ = spacings_2d(Mx, My)
+    Xs = spatial_dft_2d(mix_grid_2d(y, Mx, My, weights), Mx, My, Nx, Ny)
+    n_dump = Xs.shape[2] // L
+    Y = Xs[:, :, :n_dump * L].reshape(Nx, Ny, n_dump, L).sum(axis=3)
+    E = np.zeros((len(dms), n_dump, len(pix_lm)))
+    for d, dm in enumerate(dms):
+        n_win = cpi.window_blocks(f0, bw, k_dm, dm, L)
+        for i, (l, m) in enumerate(np.asarray(pix_lm, np.float64)):
+            taps = []
+            for r in range(n_win):
+                yh = expected_y_2d(Mx, My, Dx, Dy, l, m, f0, bw, k_dm, dm, L, Nx, Ny, r, weights)
+                cx, cy = trajectory_bins_2d(Dx, Dy, l, m, f0, bw, k_dm, dm, L, Nx, Ny, r)
+                kk = [((cx + jx) % Nx, (cy + jy) % Ny) for jx in range(-Fx, Fx + 1) for jy in range(-Fy, Fy + 1)]
+                taps.append((kk, np.array([np.conj(yh[a, b]) for a, b in kk]) / (len(keys) * L)))
+            for mm in range(n_win - 1, n_dump):
+                P = 0j
+                for r, (kk, w) in enumerate(taps):
+                    col = mm - n_win + 1 + r
+                    P += np.sum(w * np.array([Y[a, b, col] for a, b in kk]))
+                E[d, mm, i] = abs(P) ** 2
+    return E

@@ -129,3 +129,51 @@ def test_spatial_dft_is_linear(Ns):
     a = rng.standard_normal((5, 4)) + 1j * rng.standard_normal((5, 4))
     b = rng.standard_normal((5, 4)) + 1j * rng.standard_normal((5, 4))
     assert np.abs(chimg.spatial_dft(2 * a - 1j * b, Ns) - (2 * chimg.spatial_dft(a, Ns) - 1j * chimg.spatial_dft(b, Ns))).max() < 1e-12
+
+
+def test_rectangular_array_with_one_row_is_the_linear_array():
+    M, D, f0, bw, L, Ns, F = 6, 60.0, 1.4e9, 8e6, 64, 16, 1
+    dms = [8.0, 16.0]
+    l_dirs = [-0.004, 0.003]
+    y, _, _ = _chirp_ula(M, D, 0.003, f0, bw, 16.0, L, 3, 30 * L)
+    y = y + 0.3 * (np.random.default_rng(1).standard_normal(y.shape))
+    E1 = chimg.search(y, D, l_dirs, f0, bw, K_DM, dms, L, Ns, F)
+    E2 = chimg.search_2d(y, M, 1, D, 1.0, [(l, 0.0) for l in l_dirs], f0, bw, K_DM, dms, L, Ns, 1,
+                         (F, 0))
+    assert np.abs(E1 - E2).max() <= 1e-10 * E1.max()
+
+
+def _chirp_ura(Mx, My, Dx, Dy, l, m, f0, bw, dm, L, m_first, n_samp):
+    _, a0, a1 = cpi.chirp_model(f0, bw, K_DM, dm)
+    n_win = cpi.window_blocks(f0, bw, K_DM, dm, L)
+    tc = (m_first * L + n_win * L / 2.0) / bw
+    t = np.arange(n_samp) / bw
+    y = np.empty((Mx * My, n_samp), np.complex128)
+    for iy in range(My):
+        for ix in range(Mx):
+            tau = (ix * Dx * l + iy * Dy * m) / C
+            u = t - tc - tau
+            y[iy * Mx + ix] = np.exp(2j * math.pi * ((a0 - f0) * u + 0.5 * a1 * u * u)) \
+                * np.exp(-2j * math.pi * f0 * tau)
+    return y, n_win
+
+
+def test_rectangular_array_image_of_a_perfect_chirp_is_exact_and_peaks_at_its_pixel():
+    Mx, My, Dx, Dy, f0, bw, L, Nx, Ny, F, dm = 3, 3, 70.0, 50.0, 1.4e9, 8e6, 64, 8, 8, 1, 16.0
+    ang = np.linspace(-0.004, 0.004, 3)
+    pix = [(a, b) for b in ang for a in ang]
+    true = 5
+    n_win = cpi.window_blocks(f0, bw, K_DM, dm, L)
+    y, _ = _chirp_ura(Mx, My, Dx, Dy, *pix[true], f0, bw, dm, L, 2, (n_win + 4) * L)
+    E = chimg.search_2d(y, Mx, My, Dx, Dy, pix, f0, bw, K_DM, [dm], L, Nx, Ny, F)
+    keys, _ = chimg.spacings_2d(Mx, My)
+    P = 0.0
+    for r in range(n_win):
+        yh = chimg.expected_y_2d(Mx, My, Dx, Dy, *pix[true], f0, bw, K_DM, dm, L, Nx, Ny, r)
+        cx, cy = chimg.trajectory_bins_2d(Dx, Dy, *pix[true], f0, bw, K_DM, dm, L, Nx, Ny, r)
+        for jx in range(-F, F + 1):
+            for jy in range(-F, F + 1):
+                P += abs(yh[(cx + jx) % Nx, (cy + jy) % Ny]) ** 2 / (len(keys) * L)
+    m_end = 2 + n_win - 1
+    assert abs(E[0, m_end, true] - P * P) < 1e-9 * P * P
+    assert int(np.argmax(E[0, m_end])) == true
