@@ -54,7 +54,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--beam-mode", type=int, default=0,
-                    help="0 auto (= 2), 1 FP32 CUDA cores, 2 tcgen05 split-BF16, "
+                    help="0 auto (the faster exact form: 3 on this workload), 1 FP32 CUDA "
+                         "cores, 2 tcgen05 split-BF16, "
                          "3 visibility quadratic form, 4 tcgen05 BF16 (reduced precision)")
     ap.add_argument("--no-alt", action="store_true",
                     help="skip the extra timings of the other beam modes and of detection")
@@ -70,6 +71,8 @@ def parse_args():
     ap.add_argument("--cpu-dumps", type=int, default=640,
                     help="dumps per selected DM in the oracle's bounded CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the 36-antenna int8 channel leg (~100 GB of device memory)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dms", type=int, default=0,
                     help="profiling only: keep this many evenly spaced DMs of the 64")
@@ -255,7 +258,7 @@ def run_reference(args):
 def stage_roofline(sc, plan, stage_ms, peaks, peak_kind, beam_mode, steps):
     """Algorithmic bytes / flops per stage for one step, and achieved rates."""
     M, N, L = sc.n_ant, sc.n_samp, sc.dump_len
-    n_pix = sc.pix_lm.shape[0]
+    n_pix = 0 if sc.pix_lm is None else sc.pix_lm.shape[0]
     first, last = plan.dump_range()
     groups = {}
     n_searched = {}
@@ -285,7 +288,8 @@ def stage_roofline(sc, plan, stage_ms, peaks, peak_kind, beam_mode, steps):
         # (head + tail, or head only: 8 or 4 B per antenna-sample) instead of y
         y_bytes = float(n_dump_valid) * L * M * (8 if beam_mode == 2 else 4)
     stages = {
-        "forward": ("hbm", 32.0 * fwd_pts, hbm, "GB/s"),
+        # read x (8 B complex64 or 2 B complex int8), write, read, write the spectrum
+        "forward": ("hbm", (24.0 + (2.0 if plan.in_type == 1 else 8.0)) * fwd_pts, hbm, "GB/s"),
         "chirp": ("hbm", g_reads + g_bytes, hbm, "GB/s"),
         "inv_rows": ("hbm", spec_reads + 8.0 * inv_pts + g_bytes, hbm, "GB/s"),
         "inv_cols": ("hbm", 8.0 * inv_pts + y_bytes, hbm, "GB/s"),
@@ -621,6 +625,137 @@ def chirpolator_only(sc, x, stream, args):
     return 0
 
 
+def _roof_entry(r):
+    return {k: r[k] for k in ("bound", "achieved", "peak", "unit", "frac", "peak_source")}
+
+
+def timed_steps(plan, fn, k, stream):
+    """Mean ms of k calls of fn on the plan's stream (CUDA events), with the
+    plan's per-stage event timing on; returns (ms, per-stage totals)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    plan.stage_timing(True)
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(k):
+        fn()
+    a1.record(stream)
+    torch.cuda.synchronize()
+    stage = plan.stage_timing(False)
+    plan.status()
+    return a0.elapsed_time(a1) / k, stage
+
+
+def beam_mode_leg(sc, xd, Pd, stream, mode, k, peaks, peak_kind, units):
+    """One other Chimageator form on the headline workload: throughput, every
+    stage's time and roofline, and (tensor-core forms) the beam GEMM's rate
+    of algorithmic and of executed tensor flops."""
+    import paper_1109_3186_gb300 as chirp
+    pl = chirp.Plan.from_scenario(sc, beam_mode=mode, stream=stream)
+    ms, stage = timed_steps(pl, lambda: pl.chimageator(xd, Pd), k, stream)
+    roof = stage_roofline(sc, pl, stage, peaks, peak_kind, mode, k)
+    tex = roof.pop("_tensor_executed_tflops", None)
+    out = {"value": units / (ms * 1e-3), "ms_per_step": ms, "steps": k,
+           "dtype": DTYPE_LABEL[mode],
+           "stages_ms": {n: r["ms_per_step"] for n, r in roof.items()}}
+    if "beamform" in roof:
+        out["roofline"] = dict(_roof_entry(roof["beamform"]), kernel="beamform")
+        if tex is not None:
+            out["roofline"]["tensor_executed_tflops"] = tex
+            out["roofline"]["tensor_executed_frac"] = tex / roof["beamform"]["peak"]
+    pl.close()
+    return out
+
+
+def chirpolator_6ant_leg(stream, peaks, peak_kind, args):
+    """The plain-FP32 Chirpolator workload at its stated shape: 6 antennas
+    within 2 km, 8 MHz at 1.4 GHz, 2^20 samples, 16 DMs in 0-150, FFT 2^16,
+    dumps of 1024, one burst (seed 1001); device buffers."""
+    import torch
+    import paper_1109_3186_gb300 as chirp
+    from paper_1109_3186_gb300 import skymodel
+    sc = skymodel.chirpolator_small()
+    xd = torch.from_numpy(sc.voltages()).cuda()
+    plan = chirp.Plan.from_scenario(sc, stream=stream)
+    V = torch.empty((len(sc.dms), plan.n_dump, plan.n_pair), dtype=torch.complex64, device="cuda")
+    k = max(20, 4 * args.steps)
+    ms, stage = timed_steps(plan, lambda: plan.chirpolator(xd, V), k, stream)
+    roof = stage_roofline(sc, plan, stage, peaks, peak_kind, None, k)
+    roof.pop("_tensor_executed_tflops", None)
+    first, last = plan.dump_range()
+    n_valid = int(np.sum(np.maximum(0, last - first + 1)))
+    dom = max(roof, key=lambda n: roof[n]["ms_per_step"])
+    out = {"value": plan.info["valid_samples"] / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+           "steps": k, "baseline_dm_dumps_per_s": n_valid * plan.n_pair / (ms * 1e-3),
+           "corr_mode": {1: "fp32_simt", 2: "tc_3xbf16", 3: "tc_bf16"}[plan.info["corr_mode"]],
+           "dtype": "f32",
+           "workload": "chirpolator: 6 ant within 2 km, 8 MHz @ 1.4 GHz, 2^20 samples/antenna, "
+                       "16 DMs 0-150, FFT 2^16, dump 1024",
+           "l2": "voltages 50 MB, spectra 86 MB: may stay resident in L2 (129 MB)",
+           "roofline": dict(_roof_entry(roof[dom]), kernel=dom),
+           "stages_ms": {n: r["ms_per_step"] for n, r in roof.items()}}
+    plan.close()
+    return out
+
+
+def precision_channel_leg(stream, peaks, peak_kind, args):
+    """One coarse channel of the precision form at its stated shape: 36
+    antennas within 6 km, 42 MHz at 1.253 GHz (channel 0 of 8 x 42 MHz about
+    1.4 GHz), complex int8 voltages (noise drawn on the device, 16 counts
+    rms per component), 2^24 samples, 256 DMs (0, then log-spaced 1-2000),
+    64 x 64 beams over 1 deg, dumps of 4096.  Three forms: the library's
+    choice (exact visibility identity), the visibility identity with a BF16
+    tensor-core correlator, and the one-term BF16 beam GEMM on the tensor
+    cores.  About 100 GB of device memory per plan."""
+    import torch
+    import paper_1109_3186_gb300 as chirp
+    from paper_1109_3186_gb300 import skymodel
+    sc = skymodel.precision_form(channel=0, n_pulse=0)
+    M, N = sc.n_ant, sc.n_samp
+    g = torch.Generator(device="cuda").manual_seed(1003)
+    q = torch.randn((M, N, 2), generator=g, device="cuda").mul_(16.0).round_().clamp_(-127, 127)
+    q = q.to(torch.int8)
+    scale = np.full(M, (0.5 ** 0.5) / 16.0, np.float32)
+    out = {"workload": "precision form, one channel: 36 ant within 6 km, 42 MHz @ 1.253 GHz, "
+                       "int8, 2^24 samples/antenna, 256 DMs (0 + log 1-2000), 64x64 beams, "
+                       "dump 4096 (noise drawn on the device)"}
+    forms = (("auto", dict()),
+             ("vis_corr_tc_bf16", dict(beam_mode=chirp.BEAM_VIS, corr_mode=chirp.CORR_TC_BF16)),
+             ("tc_bf16", dict(beam_mode=chirp.BEAM_TC_BF16)))
+    P = None
+    for name, kw in forms:
+        plan = chirp.Plan.from_scenario(sc, stream=stream, in_type=chirp.IN_CI8, in_scale=scale,
+                                        **kw)
+        if P is None:
+            P = torch.empty((len(sc.dms), plan.n_dump, plan.n_pix), dtype=torch.float32,
+                            device="cuda")
+        ms, stage = timed_steps(plan, lambda: plan.chimageator(q, P), 2, stream)
+        mode = plan.info["beam_mode"]
+        roof = stage_roofline(sc, plan, stage, peaks, peak_kind, mode, 2)
+        tex = roof.pop("_tensor_executed_tflops", None)
+        dom = max(roof, key=lambda n: roof[n]["ms_per_step"])
+        first, last = plan.dump_range()
+        beam_dumps = int(np.sum(np.maximum(0, last - first + 1))) * plan.n_pix
+        ent = {"value": plan.info["valid_samples"] / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+               "steps": 2, "beam_mode": MODE_NAME[mode],
+               "corr_mode": {1: "fp32_simt", 2: "tc_3xbf16", 3: "tc_bf16"}[plan.info["corr_mode"]],
+               "beam_dm_dumps_per_s": beam_dumps / (ms * 1e-3),
+               "workspace_gb": plan.info["workspace_bytes"] / 1e9,
+               "roofline": dict(_roof_entry(roof[dom]), kernel=dom),
+               "stages_ms": {n: r["ms_per_step"] for n, r in roof.items()}}
+        if "beamform" in roof and roof["beamform"]["bound"] == "tensor":
+            ent["beamform_roofline"] = _roof_entry(roof["beamform"])
+            if tex is not None:
+                ent["beamform_roofline"]["tensor_executed_tflops"] = tex
+        out[name] = ent
+        plan.close()
+        torch.cuda.empty_cache()
+    del P, q
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_1109_3186_gb300 as chirp
@@ -717,24 +852,12 @@ def run_ours(args):
     # the other beam modes and candidate detection, timed the same way (rank 0)
     alt = {}
     if not args.no_alt and rank == 0:
-        for mode in (3, 4, 1):
+        for mode in (2, 4, 3, 1):
             if mode == plan.info["beam_mode"]:
                 continue
-            pl2 = chirp.Plan.from_scenario(sc, beam_mode=mode, stream=stream)
             k = 2 if mode == 1 else max(2, args.steps // 2)
-            pl2.chimageator(xd, Pd)
-            torch.cuda.synchronize()
-            a0 = torch.cuda.Event(enable_timing=True)
-            a1 = torch.cuda.Event(enable_timing=True)
-            a0.record(stream)
-            for _ in range(k):
-                pl2.chimageator(xd, Pd)
-            a1.record(stream)
-            torch.cuda.synchronize()
-            ms2 = a0.elapsed_time(a1) / k
-            alt[MODE_NAME[mode]] = {"value": units / (ms2 * 1e-3), "ms_per_step": ms2,
-                                    "steps": k, "dtype": DTYPE_LABEL[mode]}
-            pl2.close()
+            alt[MODE_NAME[mode]] = beam_mode_leg(sc, xd, Pd, stream, mode, k, peaks, peak_kind,
+                                                 units)
         # the Chirpolator back-end on the same voltages and DMs
         Vd = torch.empty((n_dm, n_dump, plan.n_pair), dtype=torch.complex64, device="cuda")
         plan.chirpolator(xd, Vd)
@@ -760,6 +883,14 @@ def run_ours(args):
         except Exception as exc:  # an auxiliary leg: record, do not lose the line
             alt["chimg_ula"] = {"error": str(exc)}
         alt.update(extra_forms(sc, plan, xd, stream, args))
+        alt["chirpolator_6ant"] = chirpolator_6ant_leg(stream, peaks, peak_kind, args)
+        if not args.no_precision:
+            try:
+                alt["precision_36ant_channel"] = precision_channel_leg(stream, peaks, peak_kind,
+                                                                       args)
+            except Exception as exc:  # an auxiliary leg: record, do not lose the line
+                alt["precision_36ant_channel"] = {"error": str(exc)}
+            torch.cuda.empty_cache()
         plan.chimageator(xd, Pd)
         torch.cuda.synchronize()
         t0 = time.perf_counter()

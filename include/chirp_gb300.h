@@ -60,7 +60,12 @@ extern "C" {
 #define CHIRP_DEVICE 1
 
 /* contraction used by the Chimageator back-end */
-#define CHIRP_BEAM_AUTO 0      /* CHIRP_BEAM_TC_3XBF16                        */
+#define CHIRP_BEAM_AUTO 0      /* the faster exact form for the shape, by a
+                                  cost model of both: CHIRP_BEAM_VIS when its
+                                  correlation + quadratic form is estimated
+                                  cheaper than the split-BF16 GEMM (e.g. 12
+                                  antennas, 1024 pixels), or when no tensor-core
+                                  shape fits; else CHIRP_BEAM_TC_3XBF16       */
 #define CHIRP_BEAM_FP32_SIMT 1 /* plain FP32 FMA on the CUDA cores           */
 #define CHIRP_BEAM_TC_3XBF16 2 /* tcgen05, 3-term bf16 split, FP32 accumulate
                                   (above 60 antennas the weights are held in
@@ -315,7 +320,8 @@ int chirp_stage_timing(chirp_plan* plan, int enable, double* ms, long long* laun
  * fixed array of CHIRP_NOALLOC_SCRATCH_BYTES that the library holds on every
  * GPU that loads it, until the process exits.
  *  volt:  DEVICE complex64 [n_ant][n_samp];  y_out: DEVICE complex64
- *         [n_ant][n_samp], zero outside the DM's valid range;
+ *         [n_ant][n_samp], zero outside the DM's valid range; both must be
+ *         device or managed memory (a host pointer gives CHIRP_EINVAL);
  *  stream: cudaStream_t (NULL = legacy default stream); work is queued on it.
  * It calls no cudaMalloc, cudaFree or allocating library routine.  The first
  * call on a device looks up the array's device address and fills its twiddle

@@ -160,8 +160,20 @@ def mix_grid_2d(y, Mx: int, My: int, weights: str = "natural"):
     return out
 
 
+def check_grid_2d(Mx: int, My: int, Nx: int, Ny: int):
+    """The half-plane spacings run lx = -(Mx-1)..(Mx-1) and ly = 0..(My-1): a
+    grid with Nx < 2 Mx - 1 or Ny < My would fold distinct spacings onto one
+    DFT bin (aliasing), so it is refused.  One row (My = 1) has lx = 1..Mx-1
+    only and needs Nx >= Mx (the linear array's rule) and Ny >= 1."""
+    nx_min = Mx if My == 1 else 2 * Mx - 1
+    if Nx < nx_min or Ny < My or Ny < 1:
+        raise ValueError("spatial grid %dx%d aliases the spacings of a %dx%d array "
+                         "(need Nx >= %d, Ny >= %d)" % (Nx, Ny, Mx, My, nx_min, My))
+
+
 def spatial_dft_2d(xg, Mx: int, My: int, Nx: int, Ny: int):
     """X[kx][ky][n] over the half-plane grid (step 3)."""
+    check_grid_2d(Mx, My, Nx, Ny)
     keys, _ = spacings_2d(Mx, My)
     kx = np.arange(Nx)[:, None, None]
     ky = np.arange(Ny)[None, :, None]
@@ -201,6 +213,7 @@ def search_2d(y, Mx, My, Dx, Dy, pix_lm, f0, bw, k_dm, dms, L, Nx, Ny, F, weight
     """E[d][m][pix] for a uniform rectangular array (steps 1-5); F is the
     half width (Fx, Fy) of the bin neighbourhood, or one value for both."""
     Fx, Fy = (F, F) if np.isscalar(F) else F
+    check_grid_2d(Mx, My, Nx, Ny)
     keys, _ = spacings_2d(Mx, My)
     Xs = spatial_dft_2d(mix_grid_2d(y, Mx, My, weights), Mx, My, Nx, Ny)
     n_dump = Xs.shape[2] // L

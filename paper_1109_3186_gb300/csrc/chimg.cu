@@ -24,13 +24,14 @@
 #include "../../include/chirp_gb300.h"
 #include "internal.h"
 
+using chirp::kCLight;
+using chirp::kDefaultKdm;
+
 namespace {
 
 constexpr int kMaxAntUla = 32;
 constexpr int kMaxNs = 1024;
 constexpr int kStage = 64;  // samples staged per step of the gridding pass
-constexpr double kCLight = 299792458.0;
-constexpr double kDefaultKdm = 4.148808e15;
 
 __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {  // c + a b
   return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));

@@ -41,6 +41,10 @@
 #include "../../include/chirp_gb300.h"
 #include "internal.h"
 
+using chirp::kCLight;
+using chirp::kDefaultKdm;
+using chirp::kPi;
+
 namespace {
 
 constexpr int kMaxTerms = 12;     // J
@@ -52,9 +56,6 @@ constexpr int kFreqPerThread = 8; // frequencies evaluated per thread (partial p
 constexpr int kCicSeg = 256;      // blocks per thread of the moving sum
 constexpr int kImgBlocks = 16;    // blocks per CTA of the imaging pass (even)
 constexpr int kImgSmemBytes = 96 * 1024;
-constexpr double kPi = 3.14159265358979323846264338327950288;
-constexpr double kCLight = 299792458.0;
-constexpr double kDefaultKdm = 4.148808e15;
 
 __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {  // c + a b
   return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));

@@ -11,8 +11,15 @@
 
 // Records msg as the calling thread's chirp_last_error() and returns code.
 int chirp_report_error(int code, const char* msg);
+// Clears the calling thread's chirp_last_error() text (entry of every ABI call).
+void chirp_clear_error();
 
 namespace chirp {
+
+// Physical constants shared by every plan type.
+constexpr double kDefaultKdm = 4.148808e15;  // dispersion constant k, s Hz^2 / (pc cm^-3), Eq. 1
+constexpr double kCLight = 299792458.0;      // m/s, the delays of Eq. tau3D
+constexpr double kPi = 3.14159265358979323846264338327950288;
 
 // One FFT-length group: DMs that share Nfft and therefore one block grid.
 struct GroupGeom {

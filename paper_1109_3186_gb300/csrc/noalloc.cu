@@ -79,12 +79,27 @@ int setup_device(cudaStream_t st, unsigned char** base) {
   return CHIRP_OK;
 }
 
+// Both buffers must be memory the kernels can address: device or managed.  A
+// host pointer handed to the kernels would fault the GPU, so it is refused.
+bool device_reachable(const void* ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();  // an unregistered host pointer leaves no sticky error
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
 }  // namespace
 
 extern "C" int chirp_dedisperse_noalloc(const void* volt, int n_ant, long long n_samp,
                                         double f0_hz, double bw_hz, double k_dm, double dm,
                                         long long nfft_min, void* y_out, void* stream) {
+  chirp_clear_error();
   if (!volt || !y_out) return bad(CHIRP_EINVAL, "chirp_dedisperse_noalloc: NULL buffer");
+  if (!device_reachable(volt) || !device_reachable(y_out))
+    return bad(CHIRP_EINVAL,
+               "chirp_dedisperse_noalloc: volt and y_out must be device (or managed) memory");
   if (n_ant < 1 || n_samp < 1) return bad(CHIRP_EINVAL, "chirp_dedisperse_noalloc: empty input");
   if (!(f0_hz > 0) || !(bw_hz > 0) || !(bw_hz < 2 * f0_hz))
     return bad(CHIRP_EINVAL, "chirp_dedisperse_noalloc: need f0 > 0 and 0 < bw < 2 f0");
@@ -92,7 +107,7 @@ extern "C" int chirp_dedisperse_noalloc(const void* volt, int n_ant, long long n
     return bad(CHIRP_EINVAL, "chirp_dedisperse_noalloc: DM must be finite and >= 0");
   if (nfft_min < 256 || nfft_min > (1LL << 24) || (nfft_min & (nfft_min - 1)))
     return bad(CHIRP_EINVAL, "chirp_dedisperse_noalloc: nfft_min must be a power of two in 256..2^24");
-  if (!(k_dm > 0)) k_dm = 4.148808e15;
+  if (!(k_dm > 0)) k_dm = kDefaultKdm;
   cudaStream_t st = (cudaStream_t)stream;
 
   // block grid of a one-DM search (same rules as a plan holding only this DM)

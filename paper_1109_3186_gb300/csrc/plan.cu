@@ -39,9 +39,6 @@ int fail(int code, const char* fmt, ...) {
                   __FILE__, __LINE__);                                                    \
   } while (0)
 
-constexpr double kDefaultKdm = 4.148808e15;  // s Hz^2 / (pc cm^-3)
-constexpr double kCLight = 299792458.0;      // m/s
-constexpr double kPi = 3.14159265358979323846264338327950288;
 
 long long pow2ceil(long long n) {
   long long p = 1;
@@ -79,7 +76,25 @@ struct DmInfo {
 
 }  // namespace
 
+// Cost model of the two exact Chimageator forms, seconds per DM-sample (both
+// read the dedispersed voltages once; the column pass writes the same bytes
+// for either).  Phased-sum GEMM: 8 n_pix M flops, executed ~3.3x over in the
+// split-BF16 form, at the tensor pipe's measured ~1.85 PFLOP/s, or its read of
+// the 8 M-byte BF16 image at ~5 TB/s when that is slower.  Visibility
+// identity sum_t |w.y|^2 = w^H V w: the correlator's 8 M(M+1)/2 flops, bound
+// by its ~1.5e13 flop/s or by reading 8 M bytes at ~2.5 TB/s (both measured on
+// GB300 at 12 antennas), plus the quadratic form's 4 M(M+1)/2 n_pix flops per
+// dump of L samples at ~2e13 flop/s.
+bool vis_beats_gemm(int M, int n_pix, int L) {
+  const double pairs = 0.5 * M * (M + 1.0);
+  const double t_gemm = std::max(8.0 * n_pix * M * 3.33 / 1.85e15, 8.0 * M / 5e12);
+  const double t_corr = std::max(8.0 * pairs / 1.5e13, 8.0 * M / 2.5e12);
+  const double t_vis = t_corr + 4.0 * pairs * n_pix / L / 2e13;
+  return t_vis < t_gemm;
+}
+
 int chirp_report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+void chirp_clear_error() { g_err[0] = 0; }
 
 struct chirp_plan {
   int M = 0;
@@ -422,10 +437,13 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   p->nfft_min = cfg->nfft_min;
   if (cfg->n_pix > 0) p->pix.assign(cfg->pix_lm, cfg->pix_lm + 2 * cfg->n_pix);
   p->n_pix = cfg->n_pix;
-  // AUTO: tensor cores (split BF16, FP32 accumulate) for the beam GEMM
+  // AUTO: the faster of the two exact (FP32-accurate) forms, by the cost model
+  // of vis_beats_gemm; the visibility identity also where no tensor-core
+  // shape fits
   p->beam_mode = cfg->beam_mode;
-  if (p->beam_mode == CHIRP_BEAM_AUTO)  // split-BF16 tensor cores where a shape fits
-    p->beam_mode = cfg->n_pix > 0 && beam_tc_pick(cfg->n_ant, cfg->n_pix, cfg->dump_len, 3, 0) == 0
+  if (p->beam_mode == CHIRP_BEAM_AUTO)
+    p->beam_mode = cfg->n_pix > 0 && (beam_tc_pick(cfg->n_ant, cfg->n_pix, cfg->dump_len, 3, 0) == 0 ||
+                                      vis_beats_gemm(cfg->n_ant, cfg->n_pix, cfg->dump_len))
                        ? CHIRP_BEAM_VIS
                        : CHIRP_BEAM_TC_3XBF16;
   p->beam_terms = p->beam_mode == CHIRP_BEAM_TC_BF16 ? 1 : 3;

@@ -4,7 +4,8 @@ options, the current torch stream, device-resident input).  The GPU computes
 the whole search; the FP64 oracle recomputes sampled cells one by one, and
 properties that hold at any size are checked on the whole output.
 
-- Chimageator: 12 antennas within 6 km, 32 MHz at 1.4 GHz, 2^22 samples,
+- Chimageator (the library's AUTO choice and the split-BF16 tensor-core
+  form): 12 antennas within 6 km, 32 MHz at 1.4 GHz, 2^22 samples,
   64 DMs in 0-300, FFT >= 2^18 (four FFT-length groups), 32 x 32 beams over
   1 deg, dumps of 4096.  Sampled: DM 0 and the first and last DM of every
   group, each at its first valid dumps, a middle dump and its last valid
@@ -30,12 +31,15 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def test_chimageator_full_size_sampled_cells():
+@pytest.mark.parametrize("mode,resolved", [(chirp.BEAM_AUTO, chirp.BEAM_VIS),
+                                           (chirp.BEAM_TC_3XBF16, chirp.BEAM_TC_3XBF16)])
+def test_chimageator_full_size_sampled_cells(mode, resolved):
+    """The benchmark's headline form (AUTO: the visibility identity, the
+    faster exact form here) and the split-BF16 tensor-core GEMM."""
     sc = skymodel.chimageator_medium(seed=1002)      # the benchmark's observation
     x = sc.voltages()
-    plan = chirp.Plan.from_scenario(sc, beam_mode=chirp.BEAM_AUTO,
-                                    stream=torch.cuda.current_stream())
-    assert plan.info["beam_mode"] == chirp.BEAM_TC_3XBF16
+    plan = chirp.Plan.from_scenario(sc, beam_mode=mode, stream=torch.cuda.current_stream())
+    assert plan.info["beam_mode"] == resolved
     xd = torch.from_numpy(x).cuda()
     P = torch.empty((len(sc.dms), plan.n_dump, plan.n_pix), dtype=torch.float32, device="cuda")
     plan.chimageator(xd, P)

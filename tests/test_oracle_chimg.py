@@ -177,3 +177,19 @@ def test_rectangular_array_image_of_a_perfect_chirp_is_exact_and_peaks_at_its_pi
     m_end = 2 + n_win - 1
     assert abs(E[0, m_end, true] - P * P) < 1e-9 * P * P
     assert int(np.argmax(E[0, m_end])) == true
+
+
+def test_rectangular_grids_that_alias_spacings_are_refused():
+    """Spacings lx = -(Mx-1)..(Mx-1), ly = 0..(My-1) need Nx >= 2 Mx - 1 and
+    Ny >= My to land on distinct bins; one row needs only Nx >= Mx."""
+    y = np.ones((9, 64), np.complex128)
+    xg = chimg.mix_grid_2d(y, 3, 3)
+    chimg.spatial_dft_2d(xg, 3, 3, 5, 3)
+    for nx, ny in ((4, 3), (5, 2)):
+        with pytest.raises(ValueError):
+            chimg.spatial_dft_2d(xg, 3, 3, nx, ny)
+    with pytest.raises(ValueError):
+        chimg.search_2d(y, 3, 3, 50.0, 50.0, [(0.0, 0.0)], 1.4e9, 8e6, K_DM, [8.0], 16, 4, 3, 0)
+    chimg.spatial_dft_2d(chimg.mix_grid_2d(y[:4], 4, 1), 4, 1, 4, 1)
+    with pytest.raises(ValueError):
+        chimg.spatial_dft_2d(chimg.mix_grid_2d(y[:4], 4, 1), 4, 1, 3, 1)
