@@ -226,6 +226,28 @@ int chirpolator_run(chirp_plan* plan, const void* volt, int volt_loc, void* vis_
  * chirp_plan_status). */
 int chimageator_run(chirp_plan* plan, const void* volt, int volt_loc, float* pow_out, int pow_loc);
 
+/* True-delay (wideband) beams of the dedispersed voltages (Sec. 2.4.2
+ * direct beamforming with each antenna's geometric delay of Eq. tau3D applied
+ * at every frequency rather than as one phase at f0).  In overlap-save block
+ * b of DM d, with X_ab the block's spectrum and H the DM's chirp,
+ *   Y_pb(f) = H(f) sum_a exp(+2 pi j (f0 + f) tau_a(l_p, m_p)) X_ab(f),
+ * f = i B / Nfft for bin i < Nfft/2, (i - Nfft) B / Nfft from there; the beam
+ * is the inverse transform (1/Nfft included) over the samples block b owns,
+ * and P[d][m][p] = sum over dump m of |beam|^2 for the DM's valid dumps, zero
+ * elsewhere.  Block grid, chirp, ownership and valid dumps are those of the
+ * phased beams; the geometric delays (at most B max|tau| samples) wrap inside
+ * a block like the chirp's tail does.  The weights' phases are formed in
+ * 64-bit fixed point from FP64 (exact modulo one cycle), the sums in FP32
+ * (dump sums by atomic adds, so the last bits may differ between runs).
+ * Costs n_pix / n_ant times the phased beams' inverse-FFT work.
+ *  pow_out: float32 [n_dm][n_dump][n_pix] at pow_loc (chimageator_run's
+ *  layout).  Needs pixels and antenna positions at plan creation.  The first
+ *  call allocates two chunk buffers of at most 1 GB each and the per-group
+ *  phase tables.  Errors: CHIRP_EINVAL, CHIRP_EUNSUPPORTED, CHIRP_ENOMEM,
+ *  CHIRP_ECUDA. */
+int chirp_truedelay_run(chirp_plan* plan, const void* volt, int volt_loc, float* pow_out,
+                        int pow_loc);
+
 /* Antenna-incoherent search (Sec. 2.3.1 incoherent dedispersion of the power
  * beam of Sec. 2.4.1), the cheap stage that proposes where the coherent path
  * should look.  Each antenna's series is cut into blocks of fb_chan samples
@@ -301,7 +323,8 @@ int chirp_propose_windows(const float* logits, int n_dm, long long n_time, int w
 #define CHIRP_STAGE_CHIRP 6     /* FP64-phase chirp table H_DM, per DM           */
 #define CHIRP_STAGE_INCOHERENT 7 /* filterbank + incoherent dedispersion        */
 #define CHIRP_STAGE_DETECT 8    /* candidate detection (chirp_detect)            */
-#define CHIRP_N_STAGES 9
+#define CHIRP_STAGE_TD_SPECTRA 9 /* true-delay beam spectra (chirp_truedelay_run) */
+#define CHIRP_N_STAGES 10
 /* Returns the milliseconds and launch counts accumulated per stage since the
  * previous call (ms, launches: host arrays of CHIRP_N_STAGES, either may be
  * NULL), resets them, and switches event timing on (enable != 0) or off for
@@ -540,6 +563,86 @@ int chirp_chimg_grid(chirp_chimg_plan* plan, const void* volt, int volt_loc, voi
 /* E [n_dm][n_dump][n_pix] float; zero for incomplete windows. */
 int chirp_chimg_run(chirp_chimg_plan* plan, const void* volt, int volt_loc, float* energy, int out_loc);
 void chirp_chimg_destroy(chirp_chimg_plan* plan);
+
+/* ------------------------------------------------------------------------
+ * The same pre-integrator on a uniform RECTANGULAR array (Sec. 4.2 in two
+ * dimensions, App. B.2): antenna a = iy n_x + ix at (ix dx_m, iy dy_m, 0).
+ *   mixing + gridding  x'_s[n] = w_s sum_{(p,q) in s} y_p[n] y_q[n]^* over the
+ *                half-plane spacings s = (lx, ly) = pos(q) - pos(p) with
+ *                ly > 0, or ly = 0 and lx > 0 (ordered by ly, then lx);
+ *                w_s = 1 / (pairs of s) (weights 0, "natural") or 1
+ *   spatial DFT  X[kx][ky][n] = sum_s exp(-2 pi j (kx lx / Nx + ky ly / Ny)) x'_s[n]
+ *   integrate    Y[m][kx][ky] = sum_{i<L} X[kx][ky][i + mL]
+ *   trajectory   P = sum_{r<n_win} sum_{|jx|<=Fx, |jy|<=Fy} w Y[m-n_win+1+r][kx0+jx][ky0+jy]
+ *                (indices mod Nx, Ny), (kx0, ky0) = (rint(Nx dx_m l nu / c),
+ *                rint(Ny dy_m m nu / c)) at dump r's centre, nu = a0 + a1 (t - t_c),
+ *                w = conj(Yhat) / (S L), Yhat the expected Y of a unit chirp
+ *                from (l, m), S the number of spacings;  E = |P|^2 (Eq. eth).
+ * Trial chirps and windows as in chirp_chimg_*.  The GPU forms the per-dump
+ * products of every pair on the raw voltages first (FP32; the DM-independent
+ * visibilities), then grids and transforms each dump.  With n_y = 1 and
+ * Ny = 1 every step is the uniform linear array's.
+ * ---------------------------------------------------------------------- */
+typedef struct chirp_chimg2d_plan chirp_chimg2d_plan;
+typedef struct {
+  int n_x, n_y;          /* antennas along u and v; 2 <= n_x n_y <= 84          */
+  double dx_m, dy_m;     /* element spacings, metres                           */
+  double f0_hz, bw_hz;   /* band centre; bandwidth = complex sample rate        */
+  double k_dm;           /* <= 0 selects 4.148808e15                           */
+  long long n_samp;      /* samples per antenna, >= dump_len                   */
+  const double* dm;      /* [n_dm] trial DMs, each > 0 (HOST)                  */
+  int n_dm;
+  int dump_len;          /* L                                                  */
+  const double* pix_lm;  /* [n_pix][2] direction cosines (l, m) (HOST)         */
+  int n_pix;
+  int n_spatial_x;       /* Nx >= 2 n_x - 1 (n_x when n_y = 1): no two spacings
+                            share a bin                                         */
+  int n_spatial_y;       /* Ny >= n_y; Nx Ny <= 16384                          */
+  int half_width_x;      /* Fx, 0..8, 2 Fx + 1 <= Nx                           */
+  int half_width_y;      /* Fy, 0..8, 2 Fy + 1 <= Ny                           */
+  int weights;           /* 0: 1 / (pairs of the spacing), 1: 1                */
+} chirp_chimg2d_config;
+/* Errors: CHIRP_EINVAL (bad size, a grid that aliases spacings, DM <= 0,
+ * l^2 + m^2 > 1, a sweep longer than the data), CHIRP_EUNSUPPORTED,
+ * CHIRP_ENOMEM, CHIRP_ECUDA; *out is NULL on failure.  Work is queued on
+ * stream (a cudaStream_t, NULL = legacy default stream). */
+int chirp_chimg2d_create(chirp_chimg2d_plan** out, const chirp_chimg2d_config* cfg, void* stream);
+/* n_dump; n_win of every DM ([n_dm], may be NULL); the number of spacings S. */
+int chirp_chimg2d_query(const chirp_chimg2d_plan* plan, long long* n_dump, int* n_win,
+                        int* n_spacing);
+/* Y complex64 [n_dump][Nx][Ny] from complex64 voltages [n_ant][n_samp]; a
+ * host output synchronises the stream. */
+int chirp_chimg2d_grid(chirp_chimg2d_plan* plan, const void* volt, int volt_loc, void* Y,
+                       int out_loc);
+/* E [n_dm][n_dump][n_pix] float; zero for incomplete windows. */
+int chirp_chimg2d_run(chirp_chimg2d_plan* plan, const void* volt, int volt_loc, float* energy,
+                      int out_loc);
+void chirp_chimg2d_destroy(chirp_chimg2d_plan* plan);
+
+/* ------------------------------------------------------------------------
+ * Combination of coarse channels (post-integration, Sec. 2.1 Eq. 1 applied
+ * between channel centres): a wide band searched as n_chan coarse channels
+ * of equal bandwidth bw_hz and dump length (one Chimageator plan per channel,
+ * each dedispersing about its own centre f_c), aligned to the top channel
+ * (f_ref = max f_c) and added incoherently:
+ *   E[d][m][pix] = sum_c P_c[d][m + s_c(d)][pix],
+ *   s_c(d) = rint(k_dm DM_d (f_c^-2 - f_ref^-2) bw_hz / dump_len)  (FP64),
+ * where every channel's dump m + s_c(d) is below n_dump and inside that
+ * channel's valid dumps [first_c[d], last_c[d]]; E = 0 elsewhere.
+ *  P:     HOST array of n_chan DEVICE pointers, each float32
+ *         [n_dm][n_dump][n_pix] (chimageator_run's layout);
+ *  first, last: HOST int64 [n_chan][n_dm] (chirp_dump_range of each plan);
+ *  f_c:   HOST [n_chan] channel centres, Hz;  dm: HOST [n_dm], pc cm^-3;
+ *  k_dm <= 0 selects 4.148808e15;  E: DEVICE float32 [n_dm][n_dump][n_pix].
+ * Sums are FP32 in channel order.  Work is queued on stream (a cudaStream_t,
+ * NULL = legacy default stream); a small stream-ordered workspace holds the
+ * shifts.  Errors: CHIRP_EINVAL (NULL or bad size; n_chan above
+ * CHIRP_MAX_CHANNELS), CHIRP_ENOMEM, CHIRP_ECUDA. */
+#define CHIRP_MAX_CHANNELS 64
+int chirp_combine_channels(const float* const* P, int n_chan, int n_dm, long long n_dump,
+                           int n_pix, const long long* first, const long long* last,
+                           const double* f_c, double bw_hz, int dump_len, double k_dm,
+                           const double* dm, float* E, void* stream);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* chirp_last_error(void);

@@ -27,6 +27,7 @@ from . import _build
 
 __all__ = ["Plan", "PropNet", "load", "build", "CHIRP_HOST", "CHIRP_DEVICE", "BEAM_AUTO", "BEAM_FP32_SIMT",
            "BEAM_TC_3XBF16", "BEAM_VIS", "ChirpError", "chirp_plan_create", "chirp_plan_destroy",
+           "chirp_combine_channels",
            "chirpolator_run", "chimageator_run", "chirp_dedisperse_run", "chirp_last_error",
            "EXPORTED_SYMBOLS"]
 
@@ -52,9 +53,11 @@ EXPORTED_SYMBOLS = ("chirp_plan_create", "chirp_plan_destroy", "chirp_plan_query
                     "chirp_cpi_query", "chirp_cpi_layout", "chirp_cpi_run", "chirp_cpi_spectra",
                     "chirp_cpi_timing", "chirp_cpi_destroy", "chirp_chimg_create",
                     "chirp_chimg_query", "chirp_chimg_grid", "chirp_chimg_run",
-                    "chirp_chimg_destroy")
+                    "chirp_chimg_destroy", "chirp_combine_channels", "chirp_chimg2d_create",
+                    "chirp_chimg2d_query", "chirp_chimg2d_grid", "chirp_chimg2d_run",
+                    "chirp_chimg2d_destroy", "chirp_truedelay_run")
 STAGES = ("forward", "inv_rows", "inv_cols", "correlate", "beamform", "split", "chirp",
-          "incoherent", "detect")
+          "incoherent", "detect", "td_spectra")
 
 
 class ChirpError(RuntimeError):
@@ -122,6 +125,8 @@ def load():
         lib.chirpolator_run.restype = i
         lib.chimageator_run.argtypes = [vp, vp, i, vp, i]
         lib.chimageator_run.restype = i
+        lib.chirp_truedelay_run.argtypes = [vp, vp, i, vp, i]
+        lib.chirp_truedelay_run.restype = i
         lib.chirp_stage_timing.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ll)]
         lib.chirp_stage_timing.restype = i
@@ -171,6 +176,11 @@ def load():
         lib.chirp_dedisperse_noalloc.restype = i
         lib.chirp_watchdog_selftest.argtypes = [ctypes.c_uint, ctypes.POINTER(ctypes.c_double), vp]
         lib.chirp_watchdog_selftest.restype = i
+        dp = ctypes.POINTER(ctypes.c_double)
+        llp = ctypes.POINTER(ll)
+        lib.chirp_combine_channels.argtypes = [ctypes.POINTER(vp), i, i, ll, i, llp, llp, dp,
+                                               ctypes.c_double, i, ctypes.c_double, dp, vp, vp]
+        lib.chirp_combine_channels.restype = i
         lib.chirp_last_error.argtypes = []
         lib.chirp_last_error.restype = ctypes.c_char_p
         _lib = lib
@@ -320,6 +330,35 @@ def chirp_batch_run(plans, volts, outs, backends) -> None:
     _check(load().chirp_batch_run(hp, vp, vl, op, ol, be, n))
 
 
+def chirp_combine_channels(P, first, last, f_c, bw: float, dump_len: int, dms, E,
+                           k_dm: float = 0.0, stream=None) -> None:
+    """Coarse channels aligned to the top channel and added (chirp_combine_channels).
+    P: list of C contiguous float32 CUDA tensors [n_dm, n_dump, n_pix]; first,
+    last: [C, n_dm] valid-dump bounds per channel; f_c: [C] centres (Hz);
+    E: float32 CUDA tensor of P's shape."""
+    import torch
+    C = len(P)
+    for t in list(P) + [E]:
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+                and t.is_contiguous() and t.shape == P[0].shape):
+            raise TypeError("P and E must be contiguous float32 CUDA tensors of one shape")
+    n_dm, n_dump, n_pix = P[0].shape
+    fl = np.ascontiguousarray(np.asarray(first, np.int64).reshape(C, n_dm))
+    la = np.ascontiguousarray(np.asarray(last, np.int64).reshape(C, n_dm))
+    fc = np.ascontiguousarray(np.asarray(f_c, np.float64).ravel())
+    dd = np.ascontiguousarray(np.asarray(dms, np.float64).ravel())
+    if fc.size != C or dd.size != n_dm:
+        raise ValueError("f_c must have one entry per channel and dms one per DM")
+    ptrs = (ctypes.c_void_p * C)(*[t.data_ptr() for t in P])
+    llp = ctypes.POINTER(ctypes.c_longlong)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(load().chirp_combine_channels(ptrs, C, int(n_dm), int(n_dump), int(n_pix),
+                                         fl.ctypes.data_as(llp), la.ctypes.data_as(llp),
+                                         fc.ctypes.data_as(dp), float(bw), int(dump_len),
+                                         float(k_dm), dd.ctypes.data_as(dp),
+                                         ctypes.c_void_p(E.data_ptr()), _stream_handle(stream)))
+
+
 def chirp_last_error() -> str:
     return load().chirp_last_error().decode(errors="replace")
 
@@ -424,6 +463,13 @@ class Plan:
 
     def chimageator(self, volt, pow_out):
         chimageator_run(self._h, volt, pow_out, self.in_type)
+        return pow_out
+
+    def truedelay(self, volt, pow_out):
+        """True-delay (wideband) beam powers [n_dm, n_dump, n_pix] (chirp_truedelay_run)."""
+        vp, vl, _k1 = _vbuf(volt, self.in_type)
+        op, ol, _k2 = _buf(pow_out, np.float32, "pow_out")
+        _check(load().chirp_truedelay_run(self._h, vp, vl, op, ol))
         return pow_out
 
     def _mask(self, cell_mask):

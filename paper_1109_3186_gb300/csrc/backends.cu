@@ -142,62 +142,112 @@ cudaError_t launch_zero_cells(float* out, const int* cells, long long n_cells, i
 // Exact identity: sum_t |sum_a W_pa y_a(t)|^2 = sum_{a,b} W_pa W_pb^* V_ab with
 // V_ab = sum_t y_a y_b^* (the correlator's output), i.e. for the packed upper
 // triangle  P_p = sum_{a<=b} Re(w_p,ab V_ab),  w_p,ab = c_ab W_pa W_pb^*,
-// c = 1 on the diagonal, 2 above it.  wpair is [n_pair][n_pix] (pixel-fastest).
-constexpr int kVisPix = 128;
-constexpr int kVisDumps = 16;
+// c = 1 on the diagonal, 2 above it.  In real form this is one FP32 GEMM per
+// DM:  P[m][p] = sum_{k < 2 n_pair} V[m][k] B[k][p]  with V read as floats
+// (re, im interleaved) and B[2 i][p] = Re w_p,i, B[2 i + 1][p] = -Im w_p,i
+// (plan-time layout, rows padded to kVisBK, columns to kVisBN, zero-filled).
+// Register-tiled SGEMM: a CTA computes 64 dumps x 128 pixels, each thread
+// 4 dumps x 8 pixels, K in steps of 16 staged through double-buffered shared
+// memory; FP32 products accumulated in k order.
+constexpr int kVisBM = 64;
+constexpr int kVisBN = 128;
+constexpr int kVisBK = 16;
 
-__global__ void __launch_bounds__(kVisPix) k_beam_from_vis(const float2* __restrict__ V,
-                                                           const float2* __restrict__ wpair,
-                                                           int n_pair, int n_pix, long long first,
-                                                           long long last,
-                                                           float* __restrict__ pow,
-                                                           const int* __restrict__ dump_list,
-                                                           long long n_list) {
-  extern __shared__ float2 sv[];  // [kVisDumps][n_pair]
-  // dumps of this CTA: first + (x kVisDumps + d), or dump_list[x kVisDumps + d]
-  const long long j0 = (long long)blockIdx.x * kVisDumps;
-  const long long n_all = dump_list ? n_list : last + 1 - first;
-  const int nd = (int)((n_all - j0) < kVisDumps ? (n_all - j0) : kVisDumps);
-  const int p = blockIdx.y * kVisPix + threadIdx.x;
-  for (int i = threadIdx.x; i < nd * n_pair; i += blockDim.x) {
-    const long long j = j0 + i / n_pair;
-    const long long m = dump_list ? (long long)dump_list[j] : first + j;
-    sv[i] = V[m * n_pair + i % n_pair];
+__global__ void __launch_bounds__(256) k_beam_from_vis(const float* __restrict__ V, int K,
+                                                       const float* __restrict__ B, int ldb,
+                                                       int n_pix, long long first, long long n_rows,
+                                                       const int* __restrict__ dump_list,
+                                                       float* __restrict__ pow) {
+  __shared__ __align__(16) float As[2][kVisBK][kVisBM];
+  __shared__ __align__(16) float Bs[2][kVisBK][kVisBN];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const long long row0 = (long long)blockIdx.x * kVisBM;
+  const int p0 = blockIdx.y * kVisBN;
+  // loader coordinates: A 64 rows x 16 k (4 k per thread), B 16 k x 128 (8 per thread)
+  const int a_row = tid / 4, a_k = (tid % 4) * 4;
+  const long long ar = row0 + a_row;
+  const float* a_src = nullptr;
+  if (ar < n_rows) {
+    const long long m = dump_list ? (long long)dump_list[ar] : first + ar;
+    a_src = V + m * K;
   }
+  const int b_k = tid / 16, b_c = (tid % 16) * 8;
+  const float* b_src = B + (long long)b_k * ldb + p0 + b_c;
+  const int n_kt = (K + kVisBK - 1) / kVisBK;
+  float ra[4];
+  float4 rb0, rb1;
+  auto load = [&](int kt) {
+    const int k0 = kt * kVisBK;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int k = k0 + a_k + j;
+      ra[j] = (a_src && k < K) ? __ldg(a_src + k) : 0.f;
+    }
+    const float4* bp = reinterpret_cast<const float4*>(b_src + (long long)k0 * ldb);
+    rb0 = __ldg(bp);
+    rb1 = __ldg(bp + 1);
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int j = 0; j < 4; j++) As[buf][a_k + j][a_row] = ra[j];
+    *reinterpret_cast<float4*>(&Bs[buf][b_k][b_c]) = rb0;
+    *reinterpret_cast<float4*>(&Bs[buf][b_k][b_c + 4]) = rb1;
+  };
+  float acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 8; j++) acc[i][j] = 0.f;
+  load(0);
+  store(0);
   __syncthreads();
-  if (p >= n_pix) return;
-  float acc[kVisDumps];
+  for (int kt = 0; kt < n_kt; kt++) {
+    const int cur = kt & 1;
+    if (kt + 1 < n_kt) load(kt + 1);
 #pragma unroll
-  for (int d = 0; d < kVisDumps; d++) acc[d] = 0.f;
-  for (int k = 0; k < n_pair; k++) {
-    const float2 w = wpair[(long long)k * n_pix + p];
+    for (int k = 0; k < kVisBK; k++) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][k][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][k][64 + tx * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-    for (int d = 0; d < kVisDumps; d++) {
-      const float2 v = sv[d * n_pair + k < nd * n_pair ? d * n_pair + k : 0];
-      acc[d] = fmaf(w.x, v.x, fmaf(-w.y, v.y, acc[d]));
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (kt + 1 < n_kt) {
+      store(cur ^ 1);
+      __syncthreads();
     }
   }
-  for (int d = 0; d < nd; d++) {
-    const long long m = dump_list ? (long long)dump_list[j0 + d] : first + j0 + d;
-    pow[m * n_pix + p] = acc[d];
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const long long r = row0 + ty * 4 + i;
+    if (r >= n_rows) continue;
+    const long long m = dump_list ? (long long)dump_list[r] : first + r;
+    float* out = pow + m * n_pix;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      const int p = p0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+      if (p < n_pix) out[p] = acc[i][j];
+    }
   }
 }
 
-cudaError_t launch_beam_from_vis(const float2* V, const float2* wpair, int n_ant, int n_pix,
+int beam_vis_rows(int n_ant) { return ((n_ant * (n_ant + 1) + kVisBK - 1) / kVisBK) * kVisBK; }
+int beam_vis_ld(int n_pix) { return ((n_pix + kVisBN - 1) / kVisBN) * kVisBN; }
+
+cudaError_t launch_beam_from_vis(const float2* V, const float* wvis, int n_ant, int n_pix,
                                  long long first, long long last, float* pow, cudaStream_t st,
                                  const int* dump_list, long long n_list) {
   if (n_pix <= 0 || (dump_list ? n_list <= 0 : last < first)) return cudaSuccess;
-  const int n_pair = n_ant * (n_ant + 1) / 2;
-  const size_t smem = (size_t)kVisDumps * n_pair * sizeof(float2);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_beam_from_vis,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  const int K = n_ant * (n_ant + 1);  // 2 n_pair real columns
   const long long n = dump_list ? n_list : last - first + 1;
-  dim3 grid((unsigned)((n + kVisDumps - 1) / kVisDumps), (n_pix + kVisPix - 1) / kVisPix);
-  k_beam_from_vis<<<grid, kVisPix, smem, st>>>(V, wpair, n_pair, n_pix, first, last, pow,
-                                               dump_list, n_list);
+  dim3 grid((unsigned)((n + kVisBM - 1) / kVisBM), (n_pix + kVisBN - 1) / kVisBN);
+  k_beam_from_vis<<<grid, 256, 0, st>>>(reinterpret_cast<const float*>(V), K, wvis,
+                                        beam_vis_ld(n_pix), n_pix, first, n, dump_list, pow);
   return cudaGetLastError();
 }
 

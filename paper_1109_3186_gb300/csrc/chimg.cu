@@ -403,3 +403,393 @@ void chirp_chimg_destroy(chirp_chimg_plan* p) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Uniform rectangular arrays (Sec. 4.2 in two dimensions, App. B.2).
+// Antenna a = iy Mx + ix sits at (ix Dx, iy Dy, 0).  The per-dump products of
+// every pair p <= q, V_pq[m] = sum_{n in dump m} y_p[n] y_q[n]^*, come from the
+// CUDA-core correlator on the raw voltages (DM-independent, once per search).
+// Spacing s = (lx, ly) = pos(q) - pos(p) of the half plane (ly > 0, or ly = 0
+// and lx > 0; every such pair has p < q) is gridded as G_s[m] = w_s sum over
+// its pairs of V_pq[m], then Y[m][kx][ky] = sum_s exp(-2 pi j (kx lx / Nx +
+// ky ly / Ny)) G_s[m].  The trajectory image reuses k_chimg_image over the
+// flattened bins k = kx Ny + ky.
+// ===========================================================================
+namespace {
+
+constexpr int kMaxAnt2d = 84;
+constexpr int kMaxBins2d = 16384;  // Nx Ny, held by the image's 16-bit bin indices
+
+// One CTA per dump: spacing sums from the dump's visibilities, then the 2-D
+// DFT over the spacings with exactly reduced integer phases.
+// sp[s] = {lx, ly, first pair entry, pair count}; pidx[] = packed pair indices.
+__global__ void __launch_bounds__(256) k_chimg2d_grid(const float2* __restrict__ V, int n_pair,
+                                                      int S, const int4* __restrict__ sp,
+                                                      const int* __restrict__ pidx,
+                                                      const float* __restrict__ ws, int Nx,
+                                                      int Ny, float2* __restrict__ Y) {
+  extern __shared__ float2 G[];  // [S]
+  const long long m = blockIdx.x;
+  const float2* v = V + m * n_pair;
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    const int4 e = sp[s];
+    float2 acc = make_float2(0.f, 0.f);
+    for (int i = 0; i < e.w; i++) {
+      const float2 x = v[pidx[e.z + i]];
+      acc.x += x.x;
+      acc.y += x.y;
+    }
+    G[s] = make_float2(ws[s] * acc.x, ws[s] * acc.y);
+  }
+  __syncthreads();
+  const int NN = Nx * Ny;
+  for (int k = threadIdx.x; k < NN; k += blockDim.x) {
+    const int kx = k / Ny, ky = k % Ny;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int s = 0; s < S; s++) {
+      const int4 e = sp[s];
+      // phase (kx lx / Nx + ky ly / Ny) cycles = q / (Nx Ny), q reduced exactly
+      long long q = ((long long)kx * e.x * Ny + (long long)ky * e.y * Nx) % NN;
+      if (q < 0) q += NN;
+      if (2 * q >= NN) q -= NN;
+      float sn, cs;
+      sincospif(2.0f * (float)q / (float)NN, &sn, &cs);
+      acc = cfma(make_float2(cs, -sn), G[s], acc);
+    }
+    Y[m * NN + k] = acc;
+  }
+}
+
+// Filter taps of one DM, FP64: thread per (pixel, dump r of the window).
+// Yhat[kx][ky] = sum_s exp(-2 pi j (kx lx/Nx + ky ly/Ny)) w_s g_s A_s e^{2 pi j c_s}
+// with, for a unit chirp from (l, m) (delays tau_a = (x_a l + y_a m) / c,
+// dt = tau_p - tau_q = -(lx Dx l + ly Dy m) / c the same for every pair of s):
+//   g_s = sum_{(p,q) in s} exp(pi j fdot (tau_p^2 - tau_q^2)),
+//   sum_{i<L} exp(-2 pi j dt (a0 + fdot t_i)), t_i = (r L + i - N/2) / B
+//       = A_s e^{2 pi j c_s},  phi = -dt fdot / B,  A_s = sin(pi phi L) / sin(pi phi),
+//   c_s = -dt (a0 + fdot (r L - N/2) / B) + phi (L - 1) / 2.
+// Bins (rint(Nx Dx l nu / c), rint(Ny Dy m nu / c)) mod (Nx, Ny) at the dump's
+// centre, nu = a0 + fdot (t_r - t_c); w = conj(Yhat) / (S L).
+__global__ void k_chimg2d_taps(const double* __restrict__ pix, int n_pix, int Mx, double Dx,
+                               double Dy, int L, int Nx, int Ny, int Fx, int Fy, double bw,
+                               double a0, double a1, int nw, int S, const int4* __restrict__ sp,
+                               const int2* __restrict__ pairs, const float* __restrict__ ws,
+                               float2* __restrict__ w, short* __restrict__ bin) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nj = (2 * Fx + 1) * (2 * Fy + 1);
+  if (idx >= (long long)n_pix * nw) return;
+  const int ip = (int)(idx / nw), r = (int)(idx % nw);
+  const double l = pix[2 * ip], mm = pix[2 * ip + 1];
+  const double N = (double)nw * L;
+  const double tr = ((double)r * L + 0.5 * (L - 1) - 0.5 * N) / bw;
+  const double nu = a0 + a1 * tr;
+  const double vx = Nx * Dx * l * nu / kCLight, vy = Ny * Dy * mm * nu / kCLight;
+  const long long cx = (((long long)rint(vx)) % Nx + Nx) % Nx;
+  const long long cy = (((long long)rint(vy)) % Ny + Ny) % Ny;
+  int t = 0;
+  for (int jx = -Fx; jx <= Fx; jx++)
+    for (int jy = -Fy; jy <= Fy; jy++, t++) {
+      const long long kx = ((cx + jx) % Nx + Nx) % Nx, ky = ((cy + jy) % Ny + Ny) % Ny;
+      double yr = 0.0, yi = 0.0;
+      for (int s = 0; s < S; s++) {
+        const int4 e = sp[s];
+        const double dt = -((double)e.x * Dx * l + (double)e.y * Dy * mm) / kCLight;
+        double gr = 0.0, gi = 0.0;
+        for (int i = 0; i < e.w; i++) {
+          const int2 pq = pairs[e.z + i];
+          const double xp = (pq.x % Mx) * Dx * l + (pq.x / Mx) * Dy * mm;
+          const double xq = (pq.y % Mx) * Dx * l + (pq.y / Mx) * Dy * mm;
+          const double tp = xp / kCLight, tq = xq / kCLight;
+          double c = 0.5 * a1 * (tp * tp - tq * tq);  // cycles
+          c -= rint(c);
+          double s_, c_;
+          sincospi(2.0 * c, &s_, &c_);
+          gr += c_;
+          gi += s_;
+        }
+        const double phi = -dt * a1 / bw;
+        const double den = sinpi(phi);
+        const double amp = fabs(den) < 1e-300 ? (double)L : sinpi(phi * L) / den;
+        double cyc = -dt * (a0 + a1 * ((double)r * L - 0.5 * N) / bw) + 0.5 * phi * (L - 1);
+        // the DFT kernel's phase, reduced exactly: (kx lx Ny + ky ly Nx) / (Nx Ny)
+        const long long NN = (long long)Nx * Ny;
+        long long q = (kx * e.x * Ny + ky * e.y * Nx) % NN;
+        if (q < 0) q += NN;
+        cyc -= rint(cyc);
+        cyc -= (double)q / (double)NN;
+        double sr_, si_;
+        sincospi(2.0 * cyc, &si_, &sr_);
+        const double f = ws[s] * amp;
+        yr += f * (gr * sr_ - gi * si_);
+        yi += f * (gr * si_ + gi * sr_);
+      }
+      const double sc = 1.0 / ((double)S * L);
+      w[idx * nj + t] = make_float2((float)(yr * sc), (float)(-yi * sc));
+      bin[idx * nj + t] = (short)(kx * Ny + ky);
+    }
+}
+
+}  // namespace
+
+struct chirp_chimg2d_plan {
+  int Mx = 0, My = 0, M = 0, L = 0, Nx = 0, Ny = 0, Fx = 0, Fy = 0, n_pix = 0, n_dm = 0, S = 0;
+  int n_pair = 0;
+  long long N = 0, n_dump = 0;
+  double Dx = 0, Dy = 0, f0 = 0, bw = 0, kdm = 0;
+  std::vector<int> n_win;
+  std::vector<long long> tap_off;
+  cudaStream_t st = nullptr;
+  float2 *d_x = nullptr, *d_V = nullptr, *d_Y = nullptr, *d_w = nullptr;
+  short* d_bin = nullptr;
+  float *d_E = nullptr, *d_ws = nullptr;
+  int4* d_sp = nullptr;
+  int* d_pidx = nullptr;
+  int* d_nwin = nullptr;
+  long long* d_off = nullptr;
+};
+
+namespace {
+
+void free_chimg2d(chirp_chimg2d_plan* p) {
+  if (!p) return;
+  void* bufs[] = {p->d_x,  p->d_V,  p->d_Y,    p->d_w,    p->d_bin, p->d_E,
+                  p->d_ws, p->d_sp, p->d_pidx, p->d_nwin, p->d_off};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete p;
+}
+
+int chimg2d_grid(chirp_chimg2d_plan* p, const void* volt, int loc) {
+  if (!volt) return gfail(CHIRP_EINVAL, "voltages are NULL");
+  if (loc != CHIRP_HOST && loc != CHIRP_DEVICE) return gfail(CHIRP_EINVAL, "bad volt_loc");
+  const float2* x = static_cast<const float2*>(volt);
+  if (loc == CHIRP_HOST) {
+    if (!p->d_x) {
+      int rc = galloc((void**)&p->d_x, (long long)p->M * p->N * 8, "voltages");
+      if (rc) return rc;
+    }
+    CKG(cudaMemcpyAsync(p->d_x, volt, (size_t)p->M * p->N * 8, cudaMemcpyHostToDevice, p->st));
+    x = p->d_x;
+  }
+  CKG(chirp::launch_correlate(x, p->N, p->M, p->L, 0, p->n_dump, 0, p->n_dump - 1, p->d_V, p->st));
+  k_chimg2d_grid<<<(unsigned)p->n_dump, 256, (size_t)p->S * sizeof(float2), p->st>>>(
+      p->d_V, p->n_pair, p->S, p->d_sp, p->d_pidx, p->d_ws, p->Nx, p->Ny, p->d_Y);
+  CKG(cudaGetLastError());
+  return CHIRP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int chirp_chimg2d_create(chirp_chimg2d_plan** out, const chirp_chimg2d_config* c, void* stream) {
+  chirp_clear_error();
+  if (!out) return gfail(CHIRP_EINVAL, "plan pointer is NULL");
+  *out = nullptr;
+  if (!c || !c->dm || !c->pix_lm) return gfail(CHIRP_EINVAL, "config, dm and pix_lm are required");
+  const int Mx = c->n_x, My = c->n_y;
+  if (Mx < 1 || My < 1 || Mx * My < 2 || Mx * My > kMaxAnt2d)
+    return gfail(CHIRP_EINVAL, "need n_x, n_y >= 1 and 2 <= n_x n_y <= 84");
+  if (!(c->dx_m > 0) || !(c->dy_m > 0)) return gfail(CHIRP_EINVAL, "dx_m and dy_m must be > 0");
+  if (!(c->bw_hz > 0) || !(c->f0_hz > 0.5 * c->bw_hz))
+    return gfail(CHIRP_EINVAL, "need bw_hz > 0 and f0_hz > bw_hz / 2");
+  if (c->dump_len < 1 || c->n_samp < c->dump_len)
+    return gfail(CHIRP_EINVAL, "dump_len must be in 1..n_samp");
+  const int nx_min = My == 1 ? Mx : 2 * Mx - 1;
+  if (c->n_spatial_x < nx_min || c->n_spatial_y < My || c->n_spatial_y < 1 ||
+      (long long)c->n_spatial_x * c->n_spatial_y > kMaxBins2d)
+    return gfail(CHIRP_EINVAL,
+                 "need n_spatial_x >= %d, n_spatial_y >= %d (no aliased spacings) and "
+                 "n_spatial_x n_spatial_y <= 16384", nx_min, My);
+  if (c->half_width_x < 0 || c->half_width_y < 0 || c->half_width_x > 8 || c->half_width_y > 8 ||
+      2 * c->half_width_x + 1 > c->n_spatial_x || 2 * c->half_width_y + 1 > c->n_spatial_y)
+    return gfail(CHIRP_EINVAL, "half widths must be in 0..8 with 2F+1 <= n_spatial");
+  if (c->n_dm < 1 || c->n_dm > 65535 || c->n_pix < 1)
+    return gfail(CHIRP_EINVAL, "n_dm in 1..65535, n_pix >= 1");
+  if (c->weights != 0 && c->weights != 1) return gfail(CHIRP_EINVAL, "weights must be 0 or 1");
+  for (int i = 0; i < c->n_pix; i++) {
+    const double l = c->pix_lm[2 * i], m = c->pix_lm[2 * i + 1];
+    if (!(l * l + m * m <= 1.0)) return gfail(CHIRP_EINVAL, "pixel %d has l^2 + m^2 > 1", i);
+  }
+  const long long n_dump = c->n_samp / c->dump_len;
+  if (n_dump >= (1LL << 31) || n_dump * (long long)c->n_pix / 256 >= (1LL << 31))
+    return gfail(CHIRP_EUNSUPPORTED, "too many dumps x pixels for one launch");
+  chirp_chimg2d_plan* p = new (std::nothrow) chirp_chimg2d_plan();
+  if (!p) return gfail(CHIRP_ENOMEM, "host allocation failed");
+  p->Mx = Mx;
+  p->My = My;
+  p->M = Mx * My;
+  p->Dx = c->dx_m;
+  p->Dy = c->dy_m;
+  p->f0 = c->f0_hz;
+  p->bw = c->bw_hz;
+  p->kdm = c->k_dm > 0 ? c->k_dm : kDefaultKdm;
+  p->N = c->n_samp;
+  p->L = c->dump_len;
+  p->n_dump = n_dump;
+  p->Nx = c->n_spatial_x;
+  p->Ny = c->n_spatial_y;
+  p->Fx = c->half_width_x;
+  p->Fy = c->half_width_y;
+  p->n_pix = c->n_pix;
+  p->n_dm = c->n_dm;
+  p->n_pair = p->M * (p->M + 1) / 2;
+  p->st = (cudaStream_t)stream;
+
+  // half-plane spacings in (ly, lx) order and their pairs (p < q)
+  std::vector<int4> sp;
+  std::vector<int> pidx;
+  std::vector<int2> pairs;
+  std::vector<float> ws;
+  for (int ly = 0; ly < My; ly++)
+    for (int lx = -(Mx - 1); lx <= Mx - 1; lx++) {
+      if (ly == 0 && lx <= 0) continue;
+      const int first = (int)pidx.size();
+      for (int iy = 0; iy + ly < My; iy++)
+        for (int ix = 0; ix < Mx; ix++) {
+          const int jx = ix + lx;
+          if (jx < 0 || jx >= Mx) continue;
+          const int a = iy * Mx + ix, b = (iy + ly) * Mx + jx;  // a < b
+          pidx.push_back(a * p->M - a * (a - 1) / 2 + (b - a));
+          pairs.push_back(make_int2(a, b));
+        }
+      const int n = (int)pidx.size() - first;
+      if (n == 0) continue;
+      sp.push_back(make_int4(lx, ly, first, n));
+      ws.push_back(c->weights == 0 ? 1.0f / (float)n : 1.0f);
+    }
+  p->S = (int)sp.size();
+
+  const double nu_lo = p->f0 - 0.5 * p->bw, nu_hi = p->f0 + 0.5 * p->bw;
+  const int nj = (2 * p->Fx + 1) * (2 * p->Fy + 1);
+  std::vector<double> a0(p->n_dm), a1(p->n_dm);
+  long long taps = 0;
+  for (int d = 0; d < p->n_dm; d++) {
+    const double dm = c->dm[d];
+    if (!(dm > 0) || !std::isfinite(dm)) {
+      free_chimg2d(p);
+      return gfail(CHIRP_EINVAL, "trial DM %d must be > 0", d);
+    }
+    const double T = p->kdm * dm * (1.0 / (nu_lo * nu_lo) - 1.0 / (nu_hi * nu_hi));
+    const double alpha = 0.5 * (1.0 / (nu_lo * nu_lo) + 1.0 / (nu_hi * nu_hi));
+    const double wn = std::floor(p->bw * T / p->L + 0.5);
+    if (wn > (double)p->n_dump) {
+      free_chimg2d(p);
+      return gfail(CHIRP_EINVAL, "the sweep of DM %g (%g dumps) is longer than the data", dm, wn);
+    }
+    a0[d] = 1.0 / std::sqrt(alpha);
+    a1[d] = -0.5 / (alpha * std::sqrt(alpha)) / (p->kdm * dm);
+    p->n_win.push_back(std::max(1, (int)wn));
+    p->tap_off.push_back(taps);
+    taps += (long long)p->n_pix * p->n_win.back() * nj;
+  }
+  double* d_pix = nullptr;
+  int2* d_pairs = nullptr;
+  int rc = galloc((void**)&p->d_V, p->n_dump * p->n_pair * 8LL, "visibilities");
+  if (!rc) rc = galloc((void**)&p->d_Y, p->n_dump * (long long)p->Nx * p->Ny * 8, "gridded spectra");
+  if (!rc) rc = galloc((void**)&p->d_w, taps * 8, "filter taps");
+  if (!rc) rc = galloc((void**)&p->d_bin, taps * 2, "filter bins");
+  if (!rc) rc = galloc((void**)&p->d_ws, p->S * 4LL, "spacing weights");
+  if (!rc) rc = galloc((void**)&p->d_sp, p->S * 16LL, "spacings");
+  if (!rc) rc = galloc((void**)&p->d_pidx, (long long)pidx.size() * 4, "pair indices");
+  if (!rc) rc = galloc((void**)&d_pairs, (long long)pairs.size() * 8, "pairs");
+  if (!rc) rc = galloc((void**)&p->d_nwin, p->n_dm * 4LL, "windows");
+  if (!rc) rc = galloc((void**)&p->d_off, p->n_dm * 8LL, "tap offsets");
+  if (!rc) rc = galloc((void**)&d_pix, p->n_pix * 16LL, "pixels");
+  if (rc) {
+    cudaFree(d_pix);
+    cudaFree(d_pairs);
+    free_chimg2d(p);
+    return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(p->d_ws, ws.data(), ws.size() * 4, cudaMemcpyHostToDevice, p->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->d_sp, sp.data(), sp.size() * 16, cudaMemcpyHostToDevice, p->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->d_pidx, pidx.data(), pidx.size() * 4, cudaMemcpyHostToDevice, p->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_pairs, pairs.data(), pairs.size() * 8, cudaMemcpyHostToDevice, p->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->d_nwin, p->n_win.data(), p->n_dm * 4, cudaMemcpyHostToDevice, p->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->d_off, p->tap_off.data(), p->n_dm * 8, cudaMemcpyHostToDevice, p->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_pix, c->pix_lm, p->n_pix * 16, cudaMemcpyHostToDevice, p->st);
+  for (int d = 0; d < p->n_dm && e == cudaSuccess; d++) {
+    const long long n = (long long)p->n_pix * p->n_win[d];
+    k_chimg2d_taps<<<(unsigned)((n + 127) / 128), 128, 0, p->st>>>(
+        d_pix, p->n_pix, p->Mx, p->Dx, p->Dy, p->L, p->Nx, p->Ny, p->Fx, p->Fy, p->bw, a0[d],
+        a1[d], p->n_win[d], p->S, p->d_sp, d_pairs, p->d_ws, p->d_w + p->tap_off[d],
+        p->d_bin + p->tap_off[d]);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+  cudaFree(d_pix);
+  cudaFree(d_pairs);
+  if (e != cudaSuccess) {
+    free_chimg2d(p);
+    return gfail(CHIRP_ECUDA, "plan setup failed: %s", cudaGetErrorString(e));
+  }
+  *out = p;
+  return CHIRP_OK;
+}
+
+int chirp_chimg2d_query(const chirp_chimg2d_plan* p, long long* n_dump, int* n_win,
+                        int* n_spacing) {
+  if (!p) return gfail(CHIRP_EINVAL, "plan is NULL");
+  if (n_dump) *n_dump = p->n_dump;
+  if (n_win) std::memcpy(n_win, p->n_win.data(), p->n_win.size() * sizeof(int));
+  if (n_spacing) *n_spacing = p->S;
+  return CHIRP_OK;
+}
+
+int chirp_chimg2d_grid(chirp_chimg2d_plan* p, const void* volt, int volt_loc, void* Y,
+                       int out_loc) {
+  chirp_clear_error();
+  if (!p || !Y) return gfail(CHIRP_EINVAL, "NULL argument");
+  if (out_loc != CHIRP_HOST && out_loc != CHIRP_DEVICE) return gfail(CHIRP_EINVAL, "bad out_loc");
+  int rc = chimg2d_grid(p, volt, volt_loc);
+  if (rc) return rc;
+  CKG(cudaMemcpyAsync(Y, p->d_Y, (size_t)p->n_dump * p->Nx * p->Ny * 8,
+                      out_loc == CHIRP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                      p->st));
+  if (out_loc == CHIRP_HOST) CKG(cudaStreamSynchronize(p->st));
+  return CHIRP_OK;
+}
+
+int chirp_chimg2d_run(chirp_chimg2d_plan* p, const void* volt, int volt_loc, float* energy,
+                      int out_loc) {
+  chirp_clear_error();
+  if (!p || !energy) return gfail(CHIRP_EINVAL, "NULL argument");
+  if (out_loc != CHIRP_HOST && out_loc != CHIRP_DEVICE) return gfail(CHIRP_EINVAL, "bad out_loc");
+  const long long n_out = (long long)p->n_dm * p->n_dump * p->n_pix;
+  float* E = energy;
+  if (out_loc == CHIRP_HOST) {
+    if (!p->d_E) {
+      int rc = galloc((void**)&p->d_E, n_out * 4, "image");
+      if (rc) return rc;
+    }
+    E = p->d_E;
+  }
+  int rc = chimg2d_grid(p, volt, volt_loc);
+  if (rc) return rc;
+  const long long per = (long long)p->n_pix * p->n_dump;
+  const dim3 grid((unsigned)((per + 255) / 256), (unsigned)p->n_dm);
+  k_chimg_image<<<grid, 256, 0, p->st>>>(p->d_Y, p->Nx * p->Ny, p->n_dump, p->n_pix, p->d_nwin,
+                                         p->d_off, (2 * p->Fx + 1) * (2 * p->Fy + 1), p->d_w,
+                                         p->d_bin, E);
+  CKG(cudaGetLastError());
+  if (out_loc == CHIRP_HOST) {
+    CKG(cudaMemcpyAsync(energy, E, (size_t)n_out * 4, cudaMemcpyDeviceToHost, p->st));
+    CKG(cudaStreamSynchronize(p->st));
+  }
+  return CHIRP_OK;
+}
+
+void chirp_chimg2d_destroy(chirp_chimg2d_plan* p) {
+  if (!p) return;
+  cudaStreamSynchronize(p->st);
+  free_chimg2d(p);
+}
+
+}  // extern "C"

@@ -106,6 +106,20 @@ cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, in
                                 long long n_lo, TwiddlePtrs tw, cudaStream_t st,
                                 const int* blk_list = nullptr, const BeamImageOut* img = nullptr);
 
+// ---- true-delay beams (dedisperse.cu) ----
+// Y[(b - b0) np + p] = sum_a W_pa(f) X[b][a] for blocks b0 .. b0+nb-1 and
+// pixels p_base .. p_base+np-1 of the group's spectra; ph: [n_pix][n_ant]
+// {frac(f0 tau), frac(B tau / nfft)} as 64-bit fixed-point cycles.
+cudaError_t launch_td_spectra(const float2* spec, float2* Y, long long b0, int nb, int np,
+                              int p_base, int n_ant, const GroupGeom& g, const void* ph,
+                              cudaStream_t st);
+// Column pass of nb x np beam sequences (from the row pass of Y with the DM's
+// chirp), |y|^2 of the owned samples in [t_lo, t_hi) added to P[t / dump_len][p].
+cudaError_t launch_inverse_cols_pow(const float2* Z, float* P, long long n_samp, long long b0,
+                                    int nb, int np, int p_base, int n_pix, const GroupGeom& g,
+                                    long long n_hi, long long n_lo, int dump_len, long long t_lo,
+                                    long long t_hi, TwiddlePtrs tw, cudaStream_t st);
+
 // ---- back-ends (backends.cu) ----
 // Clears the rows (row_floats floats each) of the listed cells (d n_dump + m).
 cudaError_t launch_zero_cells(float* out, const int* cells, long long n_cells, int row_floats,
@@ -115,8 +129,13 @@ cudaError_t launch_zero_cells(float* out, const int* cells, long long n_cells, i
 cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int dump_len,
                              long long m_base, long long n_m, long long first, long long last,
                              float2* vis, cudaStream_t st, const int* dump_list = nullptr);
-// dumps first..last, or the n_list dumps of dump_list (device) when given
-cudaError_t launch_beam_from_vis(const float2* V, const float2* wpair, int n_ant, int n_pix,
+// Beams from the visibility matrix V [n_dump][n_pair] of one DM: dumps
+// first..last, or the n_list dumps of dump_list (device) when given.  wvis is
+// the real pair-weight matrix [beam_vis_rows(n_ant)][beam_vis_ld(n_pix)]:
+// row 2i = Re w_p,i, row 2i+1 = -Im w_p,i, zero padding.
+int beam_vis_rows(int n_ant);
+int beam_vis_ld(int n_pix);
+cudaError_t launch_beam_from_vis(const float2* V, const float* wvis, int n_ant, int n_pix,
                                  long long first, long long last, float* pow, cudaStream_t st,
                                  const int* dump_list = nullptr, long long n_list = 0);
 cudaError_t launch_beamform_simt(const float2* y, long long n_samp, int n_ant, int dump_len,

@@ -67,6 +67,7 @@ struct Group {
   double* d_G = nullptr;     // FP64 phase table, spectrum order
   float2* d_spec = nullptr;  // [n_blk][n_ant][nfft] (block-major sequences)
   float2* d_rtw = nullptr;   // row-pass twiddles [n1][n2/16]
+  void* d_tdph = nullptr;    // true-delay beams: [n_pix][n_ant] 64-bit phase pairs (lazy)
 };
 
 struct DmInfo {
@@ -133,7 +134,11 @@ struct chirp_plan {
   size_t bimg_bytes = 0;
   int* d_err = nullptr;      // device status word (bounded waits that timed out)
   float2* d_V = nullptr;     // visibilities of one DM [n_dump][n_pair] (beam mode VIS)
-  float2* d_wpair = nullptr; // pair weights [n_pair][n_pix] (beam mode VIS)
+  float* d_wpair = nullptr;  // real pair weights, beam_vis_rows x beam_vis_ld (beam mode VIS)
+  // true-delay beams (chirp_truedelay_run), allocated on first use
+  float2* d_tdY = nullptr;   // beam spectra of a chunk of (block, pixel) sequences
+  float2* d_tdZ = nullptr;   // their inverse-row intermediate
+  long long td_cap = 0;      // sequences per chunk
   // incoherent filterbank search
   int fb_chan = 0, fb_int = 0, fb_n_dm = 0;
   long long T_fb = 0;
@@ -200,7 +205,10 @@ void release(chirp_plan* p) {
     cudaFree(g.d_G);
     cudaFree(g.d_rtw);
     cudaFree(g.d_spec);
+    cudaFree(g.d_tdph);
   }
+  cudaFree(p->d_tdY);
+  cudaFree(p->d_tdZ);
   cudaFree(p->d_tw);
   cudaFree(p->d_x);
   cudaFree(p->d_Z);
@@ -632,15 +640,14 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
                      (size_t)std::max(1LL, p->T_fb) * p->fb_chan * sizeof(float), "filterbank");
   }
   std::vector<uint8_t> aimg;
-  std::vector<float2> wpair;
+  std::vector<float> wpair;
   if (!rc && p->n_pix > 0 && p->beam_mode == CHIRP_BEAM_VIS) {
     rc = dev_alloc(p, (void**)&p->d_V, (size_t)std::max(1LL, p->n_dump) * p->n_pair * sizeof(float2),
                    "visibilities");
-    if (!rc)
-      rc = dev_alloc(p, (void**)&p->d_wpair, (size_t)p->n_pair * p->n_pix * sizeof(float2),
-                     "pair weights");
+    const size_t wrows = (size_t)beam_vis_rows(p->M), wld = (size_t)beam_vis_ld(p->n_pix);
+    if (!rc) rc = dev_alloc(p, (void**)&p->d_wpair, wrows * wld * sizeof(float), "pair weights");
     if (!rc) {
-      wpair.resize((size_t)p->n_pair * p->n_pix);
+      wpair.assign(wrows * wld, 0.0f);
       std::vector<double> wr(p->M), wi(p->M);
       for (int q = 0; q < p->n_pix; q++) {
         double l = p->pix[2 * q], m = p->pix[2 * q + 1];
@@ -656,8 +663,9 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
         for (int a = 0; a < p->M; a++)
           for (int b = a; b < p->M; b++, k++) {
             const double c = a == b ? 1.0 : 2.0;  // W_a conj(W_b), doubled above the diagonal
-            wpair[(size_t)k * p->n_pix + q] = make_float2((float)(c * (wr[a] * wr[b] + wi[a] * wi[b])),
-                                                          (float)(c * (wi[a] * wr[b] - wr[a] * wi[b])));
+            // Re P gets Re w Re V - Im w Im V: rows 2k (Re w) and 2k+1 (-Im w)
+            wpair[(2 * (size_t)k) * wld + q] = (float)(c * (wr[a] * wr[b] + wi[a] * wi[b]));
+            wpair[(2 * (size_t)k + 1) * wld + q] = (float)(-c * (wi[a] * wr[b] - wr[a] * wi[b]));
           }
       }
     }
@@ -714,7 +722,7 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
     e = cudaMemcpyAsync(p->d_W, W.data(), W.size() * sizeof(float2), cudaMemcpyHostToDevice,
                         p->stream);
   if (e == cudaSuccess && !wpair.empty())
-    e = cudaMemcpyAsync(p->d_wpair, wpair.data(), wpair.size() * sizeof(float2),
+    e = cudaMemcpyAsync(p->d_wpair, wpair.data(), wpair.size() * sizeof(float),
                         cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess && !aimg.empty())
     e = cudaMemcpyAsync(p->d_aimg, aimg.data(), aimg.size(), cudaMemcpyHostToDevice, p->stream);
@@ -1141,6 +1149,97 @@ int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Bac
   return CHIRP_OK;
 }
 
+// ---- true-delay (wideband) beams
+// x mod 1 as cycles x 2^64 (exact: f * 2^32 splits without rounding).
+unsigned long long frac_u64(double x) {
+  const double f = x - std::floor(x);
+  const double hi = std::floor(f * 4294967296.0);
+  const double lo = std::floor((f * 4294967296.0 - hi) * 4294967296.0);
+  return ((unsigned long long)hi << 32) + (unsigned long long)lo;
+}
+
+constexpr size_t kTdChunkBytes = 1ull << 30;  // per chunk buffer (beam spectra, intermediate)
+
+// First use: per group the phase pairs {frac(f0 tau), frac(B tau / Nfft)} of
+// every (pixel, antenna) in FP64, and the two chunk buffers.
+int truedelay_setup(chirp_plan* p) {
+  if (p->d_tdY) return CHIRP_OK;
+  long long max_nfft = 0, max_seq = 0;
+  for (auto& g : p->groups) {
+    max_nfft = std::max(max_nfft, g.geom.nfft);
+    max_seq = std::max(max_seq, g.geom.n_blk * (long long)p->n_pix);
+  }
+  p->td_cap = std::max(1LL, std::min({(long long)(kTdChunkBytes / (max_nfft * sizeof(float2))),
+                                      max_seq, 65535LL}));
+  std::vector<unsigned long long> ph(2 * (size_t)p->n_pix * p->M);
+  for (auto& g : p->groups) {
+    for (int q = 0; q < p->n_pix; q++) {
+      const double l = p->pix[2 * q], m = p->pix[2 * q + 1];
+      const double n = std::sqrt(std::max(0.0, 1.0 - l * l - m * m));
+      for (int a = 0; a < p->M; a++) {
+        const double tau = (p->xyz[3 * a] * l + p->xyz[3 * a + 1] * m + p->xyz[3 * a + 2] * (n - 1.0)) /
+                           kCLight;
+        const size_t i = 2 * ((size_t)q * p->M + a);
+        ph[i] = frac_u64(p->f0 * tau);
+        ph[i + 1] = frac_u64(p->bw * tau / (double)g.geom.nfft);
+      }
+    }
+    int rc = dev_alloc(p, &g.d_tdph, ph.size() * sizeof(unsigned long long), "true-delay phases");
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(g.d_tdph, ph.data(), ph.size() * sizeof(unsigned long long),
+                       cudaMemcpyHostToDevice, p->stream));
+    CK(cudaStreamSynchronize(p->stream));  // ph is reused for the next group
+  }
+  const size_t bytes = (size_t)p->td_cap * (size_t)max_nfft * sizeof(float2);
+  int rc = dev_alloc(p, (void**)&p->d_tdY, bytes, "true-delay beam spectra");
+  if (!rc) rc = dev_alloc(p, (void**)&p->d_tdZ, bytes, "true-delay intermediate");
+  return rc;
+}
+
+// Per DM: the chirp; per chunk of (block, pixel) sequences (whole blocks of
+// every pixel when they fit, else pixel ranges of one block) the beam spectra,
+// the inverse row pass with the chirp, and the column pass that detects and
+// integrates into dout (cleared first).
+int truedelay_search(chirp_plan* p, const void* dx, float* dout, size_t bytes) {
+  int rc = truedelay_setup(p);
+  if (rc) return rc;
+  rc = forward_all(p, dx);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(dout, 0, bytes, p->stream));
+  for (int d = 0; d < (int)p->dm.size(); d++) {
+    const DmInfo& I = p->dmi[d];
+    if (I.last < I.first) continue;
+    Group& g = p->groups[I.group];
+    const GroupGeom& G = g.geom;
+    rc = chirp_for(p, d);
+    if (rc) return rc;
+    float* out = dout + (size_t)d * p->n_dump * p->n_pix;
+    const long long cap =
+        std::max(1LL, std::min(p->td_cap, (long long)kTdChunkBytes / (G.nfft * 8)));
+    const int np_max = (int)std::min<long long>(p->n_pix, cap);
+    const long long nb_max = np_max == p->n_pix ? std::max(1LL, cap / p->n_pix) : 1;
+    for (long long b0 = 0; b0 < G.n_blk; b0 += nb_max) {
+      const int nb = (int)std::min(nb_max, G.n_blk - b0);
+      for (int p0 = 0; p0 < p->n_pix; p0 += np_max) {
+        const int np = std::min(np_max, p->n_pix - p0);
+        int mk = mark_begin(p);
+        CK(launch_td_spectra(g.d_spec, p->d_tdY, b0, nb, np, p0, p->M, G, g.d_tdph, p->stream));
+        mark_end(p, CHIRP_STAGE_TD_SPECTRA, mk);
+        mk = mark_begin(p);
+        CK(launch_inverse_rows(p->d_tdY, p->d_tdZ, p->d_H, 0, (long long)nb * np, G, p->tw(),
+                               g.d_rtw, p->stream));
+        mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
+        mk = mark_begin(p);
+        CK(launch_inverse_cols_pow(p->d_tdZ, out, p->N, b0, nb, np, p0, p->n_pix, G, I.n_hi,
+                                   I.n_lo, p->L, I.first * p->L, (I.last + 1) * p->L, p->tw(),
+                                   p->stream));
+        mark_end(p, CHIRP_STAGE_INV_COLS, mk);
+      }
+    }
+  }
+  return CHIRP_OK;
+}
+
 // Full searches on device buffers replay a CUDA graph: the first call with a
 // given (input, output, back-end) runs eagerly (lazy allocations and kernel
 // attributes happen there), the second captures and instantiates the launch
@@ -1237,6 +1336,24 @@ int chirpolator_run(chirp_plan* p, const void* volt, int volt_loc, void* vis_out
 
 int chimageator_run(chirp_plan* p, const void* volt, int volt_loc, float* pow_out, int pow_loc) {
   return run_search(p, volt, volt_loc, nullptr, kBeams, pow_out, pow_loc);
+}
+
+int chirp_truedelay_run(chirp_plan* p, const void* volt, int volt_loc, float* pow_out,
+                        int pow_loc) {
+  g_err[0] = 0;
+  if (!p) return fail(CHIRP_EINVAL, "plan is NULL");
+  if (p->n_pix <= 0) return fail(CHIRP_EUNSUPPORTED, "plan was created without pixels");
+  if (p->xyz.empty()) return fail(CHIRP_EINVAL, "plan was created without antenna positions");
+  const void* dx;
+  int rc = stage_input(p, volt, volt_loc, &dx);
+  if (rc) return rc;
+  const size_t bytes = (size_t)p->n_dump * p->n_pix * p->dm.size() * sizeof(float);
+  void* dout;
+  rc = out_buffer(p, pow_out, pow_loc, bytes, &dout);
+  if (rc) return rc;
+  rc = truedelay_search(p, dx, (float*)dout, bytes);
+  if (rc) return rc;
+  return finish_out(p, pow_out, pow_loc, dout, bytes);
 }
 
 int chirpolator_run_selective(chirp_plan* p, const void* volt, int volt_loc,
