@@ -42,8 +42,9 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 N_SM = 152
 DTYPE_LABEL = {1: "f32", 2: "f32 (beams: split-bf16 x3 on tensor cores, f32 acc)",
                3: "f32 (beams: visibility quadratic form)",
-               4: "f32 dedispersion, bf16 beams (tensor cores, f32 acc)"}
-MODE_NAME = {1: "fp32_simt", 2: "tc_3xbf16", 3: "vis", 4: "tc_bf16"}
+               4: "f32 dedispersion, bf16 beams (tensor cores, f32 acc)",
+               5: "f32 dedispersion, bf16 voltages, f32 visibilities and beams"}
+MODE_NAME = {1: "fp32_simt", 2: "tc_3xbf16", 3: "vis", 4: "tc_bf16", 5: "vis_bf16"}
 FP32_LANES_PER_SM = 128
 
 
@@ -287,6 +288,9 @@ def stage_roofline(sc, plan, stage_ms, peaks, peak_kind, beam_mode, steps):
         # the inverse column pass writes the BF16 image of the valid dumps
         # (head + tail, or head only: 8 or 4 B per antenna-sample) instead of y
         y_bytes = float(n_dump_valid) * L * M * (8 if beam_mode == 2 else 4)
+    y_elem = 4 if beam_mode == 5 else 8  # BF16 or FP32 complex voltages
+    if beam_mode == 5:
+        y_bytes = y_bytes / 2
     stages = {
         # read x (8 B complex64 or 2 B complex int8), write, read, write the spectrum
         "forward": ("hbm", (24.0 + (2.0 if plan.in_type == 1 else 8.0)) * fwd_pts, hbm, "GB/s"),
@@ -297,10 +301,10 @@ def stage_roofline(sc, plan, stage_ms, peaks, peak_kind, beam_mode, steps):
     beam_flops = float(n_dump_valid) * L * n_pix * (8 * M + 3)
     n_pair = M * (M + 1) // 2
     # correlate: read the dedispersed voltages of every valid dump, write V
-    stages["correlate"] = ("hbm", float(n_dump_valid) * (L * 8 * M + 8 * n_pair), hbm, "GB/s")
+    stages["correlate"] = ("hbm", float(n_dump_valid) * (L * y_elem * M + 8 * n_pair), hbm, "GB/s")
     if beam_mode == 4:
         beam_flops = float(n_dump_valid) * L * n_pix * (8 * M + 3)
-    if beam_mode == 3:
+    if beam_mode in (3, 5):
         # beams from visibilities: 2 FMA per (pair, pixel, dump)
         stages["beamform"] = ("alu", 4.0 * n_pair * n_pix * n_dump_valid, fp32_tflops, "TFLOP/s")
     elif beam_mode == 1:
@@ -413,14 +417,18 @@ def extra_forms(sc, plan, xd, stream, args):
     P = torch.empty((n_dm, plan.n_dump, plan.n_pix), dtype=torch.float32, device="cuda")
     ms_sel = timed(lambda: plan.chimageator_selective(xd, cells, P), 3)
     ms_full = timed(lambda: plan.chimageator(xd, P), 3)
-    # the same selection with the reduced-precision (one-term BF16) beams
-    p16 = chirp.Plan.from_scenario(sc, beam_mode=chirp.BEAM_TC_BF16, stream=stream)
+    # the same selection in the reduced-precision form (BF16-rounded voltages,
+    # FP32 visibilities and beams)
+    p16 = chirp.Plan.from_scenario(sc, beam_mode=chirp.BEAM_VIS_BF16, stream=stream)
     ms_sel16 = timed(lambda: p16.chimageator_selective(xd, cells, P), 3)
+    ms_full16 = timed(lambda: p16.chimageator(xd, P), 3)
     p16.close()
     pipeline = out["incoherent"]["ms"] + out["proposer_inference"]["ms"] + ms_sel16
     out["selective"] = {"ms": ms_sel, "full_grid_ms": ms_full, "cell_fraction": frac,
-                        "speedup": ms_full / ms_sel, "bf16_beams_ms": ms_sel16,
-                        "incoherent_proposer_selective_bf16_ms": pipeline,
+                        "speedup": ms_full / ms_sel, "reduced_precision_ms": ms_sel16,
+                        "reduced_precision_full_grid_ms": ms_full16,
+                        "reduced_precision_form": "vis_bf16",
+                        "incoherent_proposer_selective_reduced_ms": pipeline,
                         "pipeline_speedup_vs_full_grid": ms_full / pipeline,
                         "mask": "seeded runs of dumps per DM (6 runs of 1/18 of the valid dumps), "
                                 "not a trained proposer's output"}
@@ -438,12 +446,13 @@ def extra_forms(sc, plan, xd, stream, args):
             m0 = first[d] + int(rng.integers(0, max(1, n_valid - gap)))
             cells99[d, m0:m0 + gap] = 0
     frac99 = float(cells99.sum()) / max(1, int(np.sum(np.maximum(0, last - first + 1))))
-    p16 = chirp.Plan.from_scenario(sc, beam_mode=chirp.BEAM_TC_BF16, stream=stream)
+    p16 = chirp.Plan.from_scenario(sc, beam_mode=chirp.BEAM_VIS_BF16, stream=stream)
     ms_sel16_99 = timed(lambda: p16.chimageator_selective(xd, cells99, P), 3)
     p16.close()
     pipe99 = out["incoherent"]["ms"] + out["proposer_inference"]["ms"] + ms_sel16_99
     out["selective_99pct_recall"] = {
-        "cell_fraction": frac99, "incoherent_proposer_selective_bf16_ms": pipe99,
+        "cell_fraction": frac99, "incoherent_proposer_selective_reduced_ms": pipe99,
+        "reduced_precision_form": "vis_bf16",
         "speedup_vs_full_grid": ms_full / pipe99,
         "mask": "seeded, the cell fraction the trained proposer needs for >= 99 % recall of the "
                 "full-grid detections on held-out segments (6-antenna test setup)"}
@@ -669,6 +678,48 @@ def beam_mode_leg(sc, xd, Pd, stream, mode, k, peaks, peak_kind, units):
     return out
 
 
+def truedelay_leg(sc, xd, stream, peaks, peak_kind, args):
+    """True-delay (wideband) beams on the headline observation for 8 x 8
+    pixels over 1 deg (chirp_truedelay_run: n_pix / n_ant times the inverse
+    FFT work of the phased beams), beside the phased beams of the same
+    pixels; device buffers, per-stage CUDA events."""
+    import torch
+    import paper_1109_3186_gb300 as chirp
+    from paper_1109_3186_gb300 import skymodel
+    pix = skymodel.pixel_grid(8, 1.0)
+    plan = chirp.Plan(sc.xyz, sc.f0, sc.bw, sc.n_samp, sc.dms, sc.dump_len, sc.nfft_min,
+                      pix_lm=pix, k_dm=sc.k_dm, stream=stream)
+    P = torch.empty((len(sc.dms), plan.n_dump, plan.n_pix), dtype=torch.float32, device="cuda")
+    k = 2
+    ms, stage = timed_steps(plan, lambda: plan.truedelay(xd, P), k, stream)
+    ms_pb, _ = timed_steps(plan, lambda: plan.chimageator(xd, P), k, stream)
+    first, last = plan.dump_range()
+    n_valid = int(np.sum(np.maximum(0, last - first + 1)))
+    # beam sequences: every (DM, block, pixel) is one inverse FFT of its group's length
+    pts = sum(plan.n_pix * plan.dm_layout(d)["n_blk"] * plan.dm_layout(d)["nfft"]
+              for d in range(len(sc.dms)) if last[d] >= first[d])
+    hbm = peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
+    st = {n: stage[n][0] / k for n in ("td_spectra", "inv_rows", "inv_cols", "forward", "chirp")
+          if stage[n][1]}
+    out = {"value": plan.info["valid_samples"] / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+           "steps": k, "n_pix": plan.n_pix,
+           "beam_dm_dumps_per_s": n_valid * plan.n_pix / (ms * 1e-3),
+           "phased_beams_same_pixels_ms": ms_pb, "stages_ms": st,
+           "beam_ifft_points_per_step": pts,
+           "dtype": "f32 (weight phases in 64-bit fixed point from f64)",
+           "note": "8x8 pixels over 1 deg on the headline observation"}
+    # the beam inverse passes: 8 B read + 8 B written per point (row pass, plus
+    # the chirp table), 8 B read per point (column pass; powers by atomics)
+    if "inv_rows" in st and "inv_cols" in st:
+        byts = 16.0 * pts + 8.0 * pts
+        rate = byts / ((st["inv_rows"] + st["inv_cols"]) * 1e-3) / 1e9
+        out["roofline"] = {"kernel": "beam inverse passes", "bound": "hbm", "achieved": rate,
+                           "peak": hbm, "unit": "GB/s", "frac": rate / hbm,
+                           "peak_source": peak_kind}
+    plan.close()
+    return out
+
+
 def chirpolator_6ant_leg(stream, peaks, peak_kind, args):
     """The plain-FP32 Chirpolator workload at its stated shape: 6 antennas
     within 2 km, 8 MHz at 1.4 GHz, 2^20 samples, 16 DMs in 0-150, FFT 2^16,
@@ -852,7 +903,7 @@ def run_ours(args):
     # the other beam modes and candidate detection, timed the same way (rank 0)
     alt = {}
     if not args.no_alt and rank == 0:
-        for mode in (2, 4, 3, 1):
+        for mode in (2, 4, 5, 3, 1):
             if mode == plan.info["beam_mode"]:
                 continue
             k = 2 if mode == 1 else max(2, args.steps // 2)
@@ -884,6 +935,10 @@ def run_ours(args):
             alt["chimg_ula"] = {"error": str(exc)}
         alt.update(extra_forms(sc, plan, xd, stream, args))
         alt["chirpolator_6ant"] = chirpolator_6ant_leg(stream, peaks, peak_kind, args)
+        try:
+            alt["truedelay_64pix"] = truedelay_leg(sc, xd, stream, peaks, peak_kind, args)
+        except Exception as exc:  # an auxiliary leg: record, do not lose the line
+            alt["truedelay_64pix"] = {"error": str(exc)}
         if not args.no_precision:
             try:
                 alt["precision_36ant_channel"] = precision_channel_leg(stream, peaks, peak_kind,

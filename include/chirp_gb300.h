@@ -78,6 +78,13 @@ extern "C" {
                                   rounded once to BF16 (one product), FP32
                                   accumulate; relative error of a beam power
                                   ~1e-3 (held to 1e-2)                        */
+#define CHIRP_BEAM_VIS_BF16 5  /* reduced-precision visibility identity: the
+                                  inverse column pass rounds the dedispersed
+                                  voltages once to BF16 (4 bytes per antenna-
+                                  sample instead of 8), the correlator and the
+                                  quadratic form run in FP32 on the CUDA cores;
+                                  relative error of a beam power ~1e-4 (held
+                                  to 1e-2)                                    */
 
 /* contraction used by the Chirpolator back-end (and by CHIRP_BEAM_VIS) */
 #define CHIRP_CORR_AUTO 0      /* CHIRP_CORR_TC_3XBF16 from 12 antennas up where

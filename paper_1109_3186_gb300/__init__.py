@@ -32,7 +32,7 @@ __all__ = ["Plan", "PropNet", "load", "build", "CHIRP_HOST", "CHIRP_DEVICE", "BE
            "EXPORTED_SYMBOLS"]
 
 CHIRP_HOST, CHIRP_DEVICE = 0, 1
-BEAM_AUTO, BEAM_FP32_SIMT, BEAM_TC_3XBF16, BEAM_VIS, BEAM_TC_BF16 = 0, 1, 2, 3, 4
+BEAM_AUTO, BEAM_FP32_SIMT, BEAM_TC_3XBF16, BEAM_VIS, BEAM_TC_BF16, BEAM_VIS_BF16 = 0, 1, 2, 3, 4, 5
 IN_C64, IN_CI8 = 0, 1
 CORR_AUTO, CORR_FP32_SIMT, CORR_TC_3XBF16, CORR_TC_BF16 = 0, 1, 2, 3
 FLAG_GRAPHS, FLAG_AUTOTUNE = 1, 2

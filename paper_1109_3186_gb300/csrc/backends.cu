@@ -10,6 +10,7 @@
 // Both accumulate in FP32 with a two-level sum (a short inner run, then the
 // running total) so that a 4096-sample dump stays within the 1e-5 relative
 // budget of the FP32 path.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -18,16 +19,188 @@ namespace chirp {
 
 // ------------------------------------------------------------------ correlate
 // The M x M product is cut into 4 x 4 antenna tiles on or above the diagonal.
-// One warp owns one tile of one dump: lane l walks the samples l, l + 32, ...
-// (consecutive lanes read consecutive samples, so every antenna row is read
-// with full coalescing), keeps the 16 complex products of the tile in
-// registers, and the 32 lane partials are summed with warp shuffles.  The
-// warps of a CTA work on the same dump, so the antenna rows they share come
-// from L1.
+// One warp owns one tile of one dump: lane l takes the samples l, l + 32, ...
+// of the dump, keeps the tile's complex products in registers, and the 32
+// lane partials are summed with warp shuffles at the end.
+//
+// Up to 16 antennas (at most 10 tiles) one CTA holds every tile of a dump and
+// streams the dump through shared memory (k_correlate_staged): chunks of CH
+// samples of every antenna row are fetched with cp.async (16-byte copies when
+// rows and dumps start on even samples) into a ring of kCorrStages buffers,
+// so each sample is read from global memory once and several chunks are in
+// flight while the warps multiply; diagonal tiles form only their upper
+// triangle, and each complex product-accumulate is two paired FP32 FMAs
+// (fma.rn.f32x2 on the (re, im) accumulator pair).  Above 16 antennas
+// (k_correlate_direct) the warps of a CTA (kCorrWarps tiles of one dump, grid
+// dimension y over the rest) read the samples straight from global memory.
 constexpr int kCorrTile = 4;
 constexpr int kCorrWarps = 8;
+constexpr int kCorrStages = 3;
+constexpr int kCorrStagedMaxAnt = 16;
 
-__global__ void __launch_bounds__(32 * kCorrWarps) k_correlate(const float2* __restrict__ y,
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(float2* smem, const float2* gmem) { cp_async8(smem, gmem); }
+__device__ __forceinline__ void cp_async_elem(__nv_bfloat162* smem, const __nv_bfloat162* gmem) {
+  cp_async4(smem, gmem);
+}
+__device__ __forceinline__ float2 to_f2(float2 v) { return v; }
+__device__ __forceinline__ float2 to_f2(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// acc (re, im) += u * conj(w) as two paired FMAs:
+//   (re, im) += (u.x, u.y) w.x  and  (re, im) += (u.y, -u.x) w.y
+__device__ __forceinline__ void cmac_conj2(unsigned long long& acc, unsigned long long u,
+                                           unsigned long long uswap, unsigned long long wxx,
+                                           unsigned long long wyy) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(u), "l"(wxx));
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(uswap), "l"(wyy));
+}
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+
+template <typename T, int CH, bool VEC16>
+__global__ void __launch_bounds__(32 * 10) k_correlate_staged(const T* __restrict__ y,
+                                                               long long n_samp, int M, int L,
+                                                               long long m_base, long long first,
+                                                               long long last,
+                                                               float2* __restrict__ vis,
+                                                               const int* __restrict__ dump_list) {
+  extern __shared__ __align__(16) unsigned char ring_raw[];
+  T* ring = reinterpret_cast<T*>(ring_raw);  // [kCorrStages][M][CH]
+  const long long m = dump_list ? (long long)dump_list[blockIdx.x] : m_base + blockIdx.x;
+  const int n_pair = M * (M + 1) / 2;
+  float2* out = vis + m * n_pair;
+  if (m < first || m > last) {
+    for (int i = threadIdx.x; i < n_pair; i += blockDim.x) out[i] = make_float2(0.f, 0.f);
+    return;
+  }
+  const int nt = (M + kCorrTile - 1) / kCorrTile;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  int ti = 0, rem = warp;  // one tile per warp (blockDim = 32 x tiles)
+  while (rem >= nt - ti) {
+    rem -= nt - ti;
+    ti++;
+  }
+  const int tj = ti + rem;
+  const bool diag = ti == tj;
+  bool vi[kCorrTile], vj[kCorrTile];
+#pragma unroll
+  for (int a = 0; a < kCorrTile; a++) {
+    vi[a] = ti * kCorrTile + a < M;
+    vj[a] = tj * kCorrTile + a < M;
+  }
+  unsigned long long acc[kCorrTile][kCorrTile];
+#pragma unroll
+  for (int a = 0; a < kCorrTile; a++)
+#pragma unroll
+    for (int b = 0; b < kCorrTile; b++) acc[a][b] = 0ull;
+
+  const T* src = y + m * L;  // sample 0 of the dump, antenna 0
+  const int n_chunks = (L + CH - 1) / CH;
+  constexpr int EPV = 16 / (int)sizeof(T);  // samples per 16-byte copy
+  auto fetch = [&](int c) {
+    if (c < n_chunks) {
+      T* buf = ring + (size_t)(c % kCorrStages) * M * CH;
+      const int t0 = c * CH, len = min(CH, L - t0);
+      if constexpr (VEC16) {  // rows and chunks start on multiples of EPV samples
+        constexpr int U = CH / EPV;
+        for (int e = threadIdx.x; e < M * U; e += blockDim.x) {
+          const int a = e / U, i = EPV * (e % U);
+          if (i < len) cp_async16(buf + a * CH + i, src + (long long)a * n_samp + t0 + i);
+        }
+      } else {
+        for (int e = threadIdx.x; e < M * CH; e += blockDim.x) {
+          const int a = e / CH, i = e % CH;
+          if (i < len) cp_async_elem(buf + a * CH + i, src + (long long)a * n_samp + t0 + i);
+        }
+      }
+    }
+    cp_async_commit();  // possibly empty: keeps the group count in step
+  };
+#pragma unroll
+  for (int c = 0; c < kCorrStages - 1; c++) fetch(c);
+  for (int c = 0; c < n_chunks; c++) {
+    cp_async_wait<kCorrStages - 2>();
+    __syncthreads();  // chunk c is in; every warp is done with chunk c - 1
+    fetch(c + kCorrStages - 1);
+    const T* buf = ring + (size_t)(c % kCorrStages) * M * CH;
+    const int len = min(CH, L - c * CH);
+    const T* ri = buf + ti * kCorrTile * CH;
+    const T* rj = buf + tj * kCorrTile * CH;
+    for (int t = lane; t < len; t += 32) {
+      unsigned long long u[kCorrTile], us[kCorrTile];
+#pragma unroll
+      for (int a = 0; a < kCorrTile; a++) {
+        const float2 v = vi[a] ? to_f2(ri[a * CH + t]) : make_float2(0.f, 0.f);
+        u[a] = pack2(v.x, v.y);
+        us[a] = pack2(v.y, -v.x);
+      }
+      if (diag) {
+#pragma unroll
+        for (int b = 0; b < kCorrTile; b++) {
+          const float2 w = vi[b] ? to_f2(ri[b * CH + t]) : make_float2(0.f, 0.f);
+          const unsigned long long wxx = pack2(w.x, w.x), wyy = pack2(w.y, w.y);
+#pragma unroll
+          for (int a = 0; a <= b; a++) cmac_conj2(acc[a][b], u[a], us[a], wxx, wyy);
+        }
+      } else {
+#pragma unroll
+        for (int b = 0; b < kCorrTile; b++) {
+          const float2 w = vj[b] ? to_f2(rj[b * CH + t]) : make_float2(0.f, 0.f);
+          const unsigned long long wxx = pack2(w.x, w.x), wyy = pack2(w.y, w.y);
+#pragma unroll
+          for (int a = 0; a < kCorrTile; a++) cmac_conj2(acc[a][b], u[a], us[a], wxx, wyy);
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  // lane a*4+b writes pair (ti*4+a, tj*4+b) if it is in the upper triangle
+  float2 mine = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int a = 0; a < kCorrTile; a++)
+#pragma unroll
+    for (int b = 0; b < kCorrTile; b++) {
+      float2 v = unpack2(acc[a][b]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+      }
+      if (lane == a * kCorrTile + b) mine = v;
+    }
+  if (lane < kCorrTile * kCorrTile) {
+    const int a = lane / kCorrTile, b = lane % kCorrTile;
+    const int p = ti * kCorrTile + a, q = tj * kCorrTile + b;
+    if (p < M && q < M && p <= q) out[p * M - p * (p - 1) / 2 + (q - p)] = mine;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kCorrWarps) k_correlate_direct(const T* __restrict__ y,
                                                                 long long n_samp, int M, int L,
                                                                 long long m_base, long long first,
                                                                 long long last,
@@ -52,8 +225,8 @@ __global__ void __launch_bounds__(32 * kCorrWarps) k_correlate(const float2* __r
     ti++;
   }
   const int tj = ti + rem;
-  const float2* yi[kCorrTile];
-  const float2* yj[kCorrTile];
+  const T* yi[kCorrTile];
+  const T* yj[kCorrTile];
   bool vi[kCorrTile], vj[kCorrTile];
 #pragma unroll
   for (int a = 0; a < kCorrTile; a++) {
@@ -73,8 +246,8 @@ __global__ void __launch_bounds__(32 * kCorrWarps) k_correlate(const float2* __r
     float2 u[kCorrTile], w[kCorrTile];
 #pragma unroll
     for (int a = 0; a < kCorrTile; a++) {
-      u[a] = vi[a] ? __ldg(yi[a] + t) : make_float2(0.f, 0.f);
-      w[a] = vj[a] ? __ldg(yj[a] + t) : make_float2(0.f, 0.f);
+      u[a] = vi[a] ? to_f2(__ldg(yi[a] + t)) : make_float2(0.f, 0.f);
+      w[a] = vj[a] ? to_f2(__ldg(yj[a] + t)) : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int a = 0; a < kCorrTile; a++)
@@ -107,17 +280,56 @@ __global__ void __launch_bounds__(32 * kCorrWarps) k_correlate(const float2* __r
   }
 }
 
-cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int dump_len,
-                             long long m_base, long long n_m, long long first, long long last,
-                             float2* vis, cudaStream_t st, const int* dump_list) {
+template <typename T, int CH, bool VEC16>
+static cudaError_t launch_staged(const T* y, long long n_samp, int n_ant, int dump_len,
+                                 long long m_base, long long n_m, long long first, long long last,
+                                 float2* vis, cudaStream_t st, const int* dump_list, int n_tiles) {
+  const size_t smem = (size_t)kCorrStages * n_ant * CH * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(k_correlate_staged<T, CH, VEC16>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_correlate_staged<T, CH, VEC16><<<(unsigned)n_m, 32 * n_tiles, smem, st>>>(
+      y, n_samp, n_ant, dump_len, m_base, first, last, vis, dump_list);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t correlate_any(const T* y, long long n_samp, int n_ant, int dump_len,
+                                 long long m_base, long long n_m, long long first, long long last,
+                                 float2* vis, cudaStream_t st, const int* dump_list) {
   const int nt = (n_ant + kCorrTile - 1) / kCorrTile;
   const int n_tiles = nt * (nt + 1) / 2;
   if (n_m <= 0) return cudaSuccess;
+  if (n_ant <= kCorrStagedMaxAnt) {
+    if (n_m >= (1LL << 31)) return cudaErrorInvalidConfiguration;
+    // 256-sample chunks (at most 96 KB of ring for 16 antennas); 16-byte
+    // copies when every row and dump starts on a 16-byte boundary of a
+    // 16-byte aligned array
+    constexpr int EPV = 16 / (int)sizeof(T);
+    if (n_samp % EPV == 0 && dump_len % EPV == 0 && ((uintptr_t)y & 15) == 0)
+      return launch_staged<T, 256, true>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last,
+                                         vis, st, dump_list, n_tiles);
+    return launch_staged<T, 256, false>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis,
+                                        st, dump_list, n_tiles);
+  }
   const int warps = n_tiles < kCorrWarps ? n_tiles : kCorrWarps;
   dim3 grid((unsigned)n_m, (n_tiles + warps - 1) / warps);
-  k_correlate<<<grid, 32 * warps, 0, st>>>(y, n_samp, n_ant, dump_len, m_base, first, last, vis,
-                                           dump_list);
+  k_correlate_direct<T><<<grid, 32 * warps, 0, st>>>(y, n_samp, n_ant, dump_len, m_base, first,
+                                                     last, vis, dump_list);
   return cudaGetLastError();
+}
+
+cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int dump_len,
+                             long long m_base, long long n_m, long long first, long long last,
+                             float2* vis, cudaStream_t st, const int* dump_list) {
+  return correlate_any(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis, st, dump_list);
+}
+
+cudaError_t launch_correlate_bf16(const void* y16, long long n_samp, int n_ant, int dump_len,
+                                  long long m_base, long long n_m, long long first, long long last,
+                                  float2* vis, cudaStream_t st, const int* dump_list) {
+  return correlate_any(static_cast<const __nv_bfloat162*>(y16), n_samp, n_ant, dump_len, m_base,
+                       n_m, first, last, vis, st, dump_list);
 }
 
 // ------------------------------------------------------------------ clear cells

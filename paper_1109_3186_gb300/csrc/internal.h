@@ -106,13 +106,21 @@ cudaError_t launch_inverse_cols(const float2* Z, float2* y, long long n_samp, in
                                 long long n_lo, TwiddlePtrs tw, cudaStream_t st,
                                 const int* blk_list = nullptr, const BeamImageOut* img = nullptr);
 
-// ---- true-delay beams (dedisperse.cu) ----
+// The same column pass writing the owned, valid samples as BF16 (re, im)
+// pairs: y16 is [n_ant][n_samp] __nv_bfloat162 (reduced.cu).
+cudaError_t launch_inverse_cols_bf16(const float2* Z, void* y16, long long n_samp, int n_ant,
+                                     long long q0, long long nq, const GroupGeom& g,
+                                     long long n_hi, long long n_lo, TwiddlePtrs tw,
+                                     cudaStream_t st, const int* blk_list = nullptr);
+
+// ---- true-delay beams (truedelay.cu) ----
 // Y[(b - b0) np + p] = sum_a W_pa(f) X[b][a] for blocks b0 .. b0+nb-1 and
 // pixels p_base .. p_base+np-1 of the group's spectra; ph: [n_pix][n_ant]
-// {frac(f0 tau), frac(B tau / nfft)} as 64-bit fixed-point cycles.
+// {frac(f0 tau), frac(B tau / nfft)} as 64-bit fixed-point cycles; rot:
+// [n_pix][n_ant] exp(2 pi j n1 B tau / nfft), the weight's step along a row.
 cudaError_t launch_td_spectra(const float2* spec, float2* Y, long long b0, int nb, int np,
                               int p_base, int n_ant, const GroupGeom& g, const void* ph,
-                              cudaStream_t st);
+                              const float2* rot, cudaStream_t st);
 // Column pass of nb x np beam sequences (from the row pass of Y with the DM's
 // chirp), |y|^2 of the owned samples in [t_lo, t_hi) added to P[t / dump_len][p].
 cudaError_t launch_inverse_cols_pow(const float2* Z, float* P, long long n_samp, long long b0,
@@ -129,6 +137,11 @@ cudaError_t launch_zero_cells(float* out, const int* cells, long long n_cells, i
 cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int dump_len,
                              long long m_base, long long n_m, long long first, long long last,
                              float2* vis, cudaStream_t st, const int* dump_list = nullptr);
+// The same from dedispersed voltages rounded to BF16: y16 is [n_ant][n_samp]
+// pairs (re, im) of BF16 (__nv_bfloat162); products and sums in FP32.
+cudaError_t launch_correlate_bf16(const void* y16, long long n_samp, int n_ant, int dump_len,
+                                  long long m_base, long long n_m, long long first, long long last,
+                                  float2* vis, cudaStream_t st, const int* dump_list = nullptr);
 // Beams from the visibility matrix V [n_dump][n_pair] of one DM: dumps
 // first..last, or the n_list dumps of dump_list (device) when given.  wvis is
 // the real pair-weight matrix [beam_vis_rows(n_ant)][beam_vis_ld(n_pix)]:

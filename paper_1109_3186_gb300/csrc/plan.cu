@@ -68,6 +68,7 @@ struct Group {
   float2* d_spec = nullptr;  // [n_blk][n_ant][nfft] (block-major sequences)
   float2* d_rtw = nullptr;   // row-pass twiddles [n1][n2/16]
   void* d_tdph = nullptr;    // true-delay beams: [n_pix][n_ant] 64-bit phase pairs (lazy)
+  float2* d_tdrot = nullptr; // true-delay beams: [n_pix][n_ant] weight step along a row
 };
 
 struct DmInfo {
@@ -184,6 +185,10 @@ namespace {
 bool tc_beams(const chirp_plan* p) {
   return p->beam_mode == CHIRP_BEAM_TC_3XBF16 || p->beam_mode == CHIRP_BEAM_TC_BF16;
 }
+// Beams from per-dump visibilities (exact FP32, or from BF16-rounded voltages).
+bool vis_beams(const chirp_plan* p) {
+  return p->beam_mode == CHIRP_BEAM_VIS || p->beam_mode == CHIRP_BEAM_VIS_BF16;
+}
 
 int dev_alloc(chirp_plan* p, void** ptr, size_t bytes, const char* what) {
   if (bytes == 0) bytes = 16;
@@ -206,6 +211,7 @@ void release(chirp_plan* p) {
     cudaFree(g.d_rtw);
     cudaFree(g.d_spec);
     cudaFree(g.d_tdph);
+    cudaFree(g.d_tdrot);
   }
   cudaFree(p->d_tdY);
   cudaFree(p->d_tdZ);
@@ -386,7 +392,7 @@ int validate(const chirp_config* c) {
       double l = c->pix_lm[2 * p], m = c->pix_lm[2 * p + 1];
       if (!(l * l + m * m <= 1.0)) return fail(CHIRP_EINVAL, "pixel %d has l^2 + m^2 > 1", p);
     }
-  if (c->beam_mode < 0 || c->beam_mode > CHIRP_BEAM_TC_BF16)
+  if (c->beam_mode < 0 || c->beam_mode > CHIRP_BEAM_VIS_BF16)
     return fail(CHIRP_EINVAL, "unknown beam_mode");
   if (c->in_type != CHIRP_IN_C64 && c->in_type != CHIRP_IN_CI8)
     return fail(CHIRP_EINVAL, "unknown in_type");
@@ -641,7 +647,7 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   }
   std::vector<uint8_t> aimg;
   std::vector<float> wpair;
-  if (!rc && p->n_pix > 0 && p->beam_mode == CHIRP_BEAM_VIS) {
+  if (!rc && p->n_pix > 0 && vis_beams(p)) {
     rc = dev_alloc(p, (void**)&p->d_V, (size_t)std::max(1LL, p->n_dump) * p->n_pair * sizeof(float2),
                    "visibilities");
     const size_t wrows = (size_t)beam_vis_rows(p->M), wld = (size_t)beam_vis_ld(p->n_pix);
@@ -866,7 +872,7 @@ int forward_all(chirp_plan* p, const void* dx) {
 
 // Dedisperse DM d over the blocks [b0, b1) of its group (all antennas).
 int dedisperse_blocks(chirp_plan* p, int d, float2* y, long long b0, long long b1,
-                      const BeamImageOut* img = nullptr) {
+                      const BeamImageOut* img = nullptr, bool y16 = false) {
   const DmInfo& I = p->dmi[d];
   Group& g = p->groups[I.group];
   const long long q_end = b1 * p->M;
@@ -878,8 +884,12 @@ int dedisperse_blocks(chirp_plan* p, int d, float2* y, long long b0, long long b
                            p->stream));
     mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
     mk = mark_begin(p);
-    CK(launch_inverse_cols(p->d_Z, y, p->N, p->M, q0, n, g.geom, I.n_hi, I.n_lo, p->tw(),
-                           p->stream, nullptr, img));
+    if (y16)
+      CK(launch_inverse_cols_bf16(p->d_Z, y, p->N, p->M, q0, n, g.geom, I.n_hi, I.n_lo, p->tw(),
+                                  p->stream));
+    else
+      CK(launch_inverse_cols(p->d_Z, y, p->N, p->M, q0, n, g.geom, I.n_hi, I.n_lo, p->tw(),
+                             p->stream, nullptr, img));
     mark_end(p, CHIRP_STAGE_INV_COLS, mk);
   }
   return CHIRP_OK;
@@ -913,6 +923,27 @@ enum Backend { kCorrelate, kBeams };
 // A Chimageator search in a tensor-core mode has the inverse column pass
 // write the beamformer's BF16 image of DM d's valid dumps directly.
 bool fused_image(const chirp_plan* p, Backend be) { return be == kBeams && tc_beams(p); }
+BeamImageOut beam_image_for(const chirp_plan* p, int d);
+// A Chimageator search in the reduced-precision visibility form has the
+// inverse column pass write the voltages as BF16 pairs (into d_y's memory).
+bool bf16_y(const chirp_plan* p, Backend be) {
+  return be == kBeams && p->beam_mode == CHIRP_BEAM_VIS_BF16;
+}
+
+// Inverse column pass of DM d over sequences [q0, q0 + nq) (or the listed
+// blocks) with the output the back-end reads: FP32 voltages, BF16 voltages,
+// or the tensor-core beamformer's image.
+cudaError_t column_pass(chirp_plan* p, int d, Backend be, const float2* Z, long long q0,
+                        long long nq, const int* blist) {
+  const DmInfo& I = p->dmi[d];
+  const GroupGeom& G = p->groups[I.group].geom;
+  if (bf16_y(p, be))
+    return launch_inverse_cols_bf16(Z, p->d_y, p->N, p->M, q0, nq, G, I.n_hi, I.n_lo, p->tw(),
+                                    p->stream, blist);
+  const BeamImageOut img = fused_image(p, be) ? beam_image_for(p, d) : BeamImageOut{};
+  return launch_inverse_cols(Z, p->d_y, p->N, p->M, q0, nq, G, I.n_hi, I.n_lo, p->tw(), p->stream,
+                             blist, fused_image(p, be) ? &img : nullptr);
+}
 
 BeamImageOut beam_image_for(const chirp_plan* p, int d) {
   const DmInfo& I = p->dmi[d];
@@ -942,7 +973,9 @@ int backend_dumps(chirp_plan* p, int d, Backend be, long long m0, long long m1, 
   // tensor-core correlation was asked for explicitly it uses FP32 products.
   auto correlate = [&](float2* vis, bool for_beams) -> int {
     int mk = mark_begin(p);
-    if (p->corr_mode == CHIRP_CORR_FP32_SIMT || (for_beams && !p->corr_forced))
+    if (for_beams && p->beam_mode == CHIRP_BEAM_VIS_BF16)
+      CK(launch_correlate_bf16(p->d_y, p->N, p->M, p->L, m0, m1 - m0, m0, last, vis, p->stream));
+    else if (p->corr_mode == CHIRP_CORR_FP32_SIMT || (for_beams && !p->corr_forced))
       CK(launch_correlate(p->d_y, p->N, p->M, p->L, m0, m1 - m0, m0, last, vis, p->stream));
     else
       CK(launch_correlate_tc(p->d_y, p->N, p->M, p->L, m0, last, vis, p->d_err,
@@ -953,7 +986,7 @@ int backend_dumps(chirp_plan* p, int d, Backend be, long long m0, long long m1, 
   if (be == kCorrelate)
     return correlate((float2*)dout + d * (size_t)p->n_dump * p->n_pair, false);
   float* out = (float*)dout + (size_t)d * p->n_dump * p->n_pix;
-  if (p->beam_mode == CHIRP_BEAM_VIS) {
+  if (vis_beams(p)) {
     int rc = correlate(p->d_V, true);
     if (rc) return rc;
     int mk;
@@ -999,11 +1032,8 @@ int full_search_chunked(chirp_plan* p, Backend be, void* dout) {
       for (int j = 0; j < n; j++) {
         const int d = dms[c0 + j];
         const DmInfo& I = p->dmi[d];
-        const BeamImageOut img = fused_image(p, be) ? beam_image_for(p, d) : BeamImageOut{};
         mk = mark_begin(p);
-        CK(launch_inverse_cols(p->d_Z + (size_t)j * p->z_stride, p->d_y, p->N, p->M, 0, nq, G,
-                               I.n_hi, I.n_lo, p->tw(), p->stream, nullptr,
-                               fused_image(p, be) ? &img : nullptr));
+        CK(column_pass(p, d, be, p->d_Z + (size_t)j * p->z_stride, 0, nq, nullptr));
         mark_end(p, CHIRP_STAGE_INV_COLS, mk);
         int rc = backend_dumps(p, d, be, I.first, I.last + 1, dout);
         if (rc) return rc;
@@ -1100,7 +1130,8 @@ int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Bac
     if (rc) return rc;
     if (!mask) {
       const BeamImageOut img = fused_image(p, be) ? beam_image_for(p, d) : BeamImageOut{};
-      rc = dedisperse_blocks(p, d, p->d_y, 0, G.n_blk, fused_image(p, be) ? &img : nullptr);
+      rc = dedisperse_blocks(p, d, p->d_y, 0, G.n_blk, fused_image(p, be) ? &img : nullptr,
+                             bf16_y(p, be));
       if (!rc) rc = backend_dumps(p, d, be, I.first, I.last + 1, dout);
       if (rc) return rc;
       continue;
@@ -1113,15 +1144,17 @@ int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Bac
                            p->stream, blist, p->M));
     mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
     mk = mark_begin(p);
-    const BeamImageOut img = fused_image(p, be) ? beam_image_for(p, d) : BeamImageOut{};
-    CK(launch_inverse_cols(p->d_Z, p->d_y, p->N, p->M, 0, blk_n[d] * p->M, G, I.n_hi, I.n_lo,
-                           p->tw(), p->stream, blist, fused_image(p, be) ? &img : nullptr));
+    CK(column_pass(p, d, be, p->d_Z, 0, blk_n[d] * p->M, blist));
     mark_end(p, CHIRP_STAGE_INV_COLS, mk);
-    if (be == kCorrelate || p->beam_mode == CHIRP_BEAM_VIS) {
+    if (be == kCorrelate || vis_beams(p)) {
       float2* vout = be == kCorrelate ? (float2*)dout + (size_t)d * p->n_dump * p->n_pair : p->d_V;
       mk = mark_begin(p);
-      CK(launch_correlate(p->d_y, p->N, p->M, p->L, 0, dmp_n[d], I.first, I.last, vout, p->stream,
-                          dlist));
+      if (bf16_y(p, be))
+        CK(launch_correlate_bf16(p->d_y, p->N, p->M, p->L, 0, dmp_n[d], I.first, I.last, vout,
+                                 p->stream, dlist));
+      else
+        CK(launch_correlate(p->d_y, p->N, p->M, p->L, 0, dmp_n[d], I.first, I.last, vout,
+                            p->stream, dlist));
       mark_end(p, CHIRP_STAGE_CORRELATE, mk);
       if (be == kBeams) {
         mk = mark_begin(p);
@@ -1172,6 +1205,7 @@ int truedelay_setup(chirp_plan* p) {
   p->td_cap = std::max(1LL, std::min({(long long)(kTdChunkBytes / (max_nfft * sizeof(float2))),
                                       max_seq, 65535LL}));
   std::vector<unsigned long long> ph(2 * (size_t)p->n_pix * p->M);
+  std::vector<float2> rot((size_t)p->n_pix * p->M);
   for (auto& g : p->groups) {
     for (int q = 0; q < p->n_pix; q++) {
       const double l = p->pix[2 * q], m = p->pix[2 * q + 1];
@@ -1182,12 +1216,20 @@ int truedelay_setup(chirp_plan* p) {
         const size_t i = 2 * ((size_t)q * p->M + a);
         ph[i] = frac_u64(p->f0 * tau);
         ph[i + 1] = frac_u64(p->bw * tau / (double)g.geom.nfft);
+        // step along a row of the transposed spectrum: n1 bins
+        double c = (double)g.geom.n1 * p->bw * tau / (double)g.geom.nfft;
+        c -= std::rint(c);
+        rot[(size_t)q * p->M + a] = make_float2((float)std::cos(2.0 * kPi * c),
+                                                (float)std::sin(2.0 * kPi * c));
       }
     }
     int rc = dev_alloc(p, &g.d_tdph, ph.size() * sizeof(unsigned long long), "true-delay phases");
+    if (!rc) rc = dev_alloc(p, (void**)&g.d_tdrot, rot.size() * sizeof(float2), "true-delay steps");
     if (rc) return rc;
     CK(cudaMemcpyAsync(g.d_tdph, ph.data(), ph.size() * sizeof(unsigned long long),
                        cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(g.d_tdrot, rot.data(), rot.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                       p->stream));
     CK(cudaStreamSynchronize(p->stream));  // ph is reused for the next group
   }
   const size_t bytes = (size_t)p->td_cap * (size_t)max_nfft * sizeof(float2);
@@ -1223,7 +1265,8 @@ int truedelay_search(chirp_plan* p, const void* dx, float* dout, size_t bytes) {
       for (int p0 = 0; p0 < p->n_pix; p0 += np_max) {
         const int np = std::min(np_max, p->n_pix - p0);
         int mk = mark_begin(p);
-        CK(launch_td_spectra(g.d_spec, p->d_tdY, b0, nb, np, p0, p->M, G, g.d_tdph, p->stream));
+        CK(launch_td_spectra(g.d_spec, p->d_tdY, b0, nb, np, p0, p->M, G, g.d_tdph, g.d_tdrot,
+                             p->stream));
         mark_end(p, CHIRP_STAGE_TD_SPECTRA, mk);
         mk = mark_begin(p);
         CK(launch_inverse_rows(p->d_tdY, p->d_tdZ, p->d_H, 0, (long long)nb * np, G, p->tw(),

@@ -211,3 +211,53 @@ def test_precision_form_slice_of_the_36_antenna_array(k_dm):
             assert pow_error(out["p3"][d, m0:m1], Po) < TOL_POW, (d, m0)
             assert vis_error(out["v16"][d, m0:m1], Vo, sc.n_ant) < TOL_VIS_BF16, (d, m0)
             assert vis_error(out["v3"][d, m0:m1], Vo, sc.n_ant) < TOL_VIS, (d, m0)
+
+
+VIS_BF16_CASES = [
+    (12, 1 << 17, 4096, 8, [0.0, 30.0, 60.0], 1 << 15),   # staged correlator, 16-byte copies
+    (5, 50001, 1000, 4, [0.0, 12.0], 1 << 13),            # odd series: 4-byte copies
+    (36, 1 << 16, 1024, 8, [0.0, 3.0], 1 << 14),          # above 16 antennas: direct loads
+]
+
+
+@pytest.mark.parametrize("M,N,L,n_side,dms,nfft_min", VIS_BF16_CASES,
+                         ids=["M%d_N%d" % (c[0], c[1]) for c in VIS_BF16_CASES])
+def test_bf16_voltage_visibility_beams_match_oracle(M, N, L, n_side, dms, nfft_min, k_dm):
+    """CHIRP_BEAM_VIS_BF16: dedispersed voltages rounded once to BF16 (relative
+    error <= 2^-9 per component), FP32 correlation and quadratic form; a dump
+    power sums L products whose rounding errors are independent, so its error
+    is ~2^-8 / sqrt(L) relative, far inside the reduced-precision 1e-2.  The
+    selective search over a seeded mask gives the full search's values."""
+    sc = skymodel.chimageator_medium(n_samp=N, n_dm=len(dms), n_ant=M, dm_max=max(dms),
+                                     nfft_min=nfft_min, dump_len=L, n_side=n_side, n_pulse=1)
+    sc.dms = np.array(dms)
+    x = sc.voltages()
+    plan = chirp.Plan.from_scenario(sc, beam_mode=chirp.BEAM_VIS_BF16)
+    assert plan.info["beam_mode"] == chirp.BEAM_VIS_BF16
+    xd = torch.from_numpy(x).cuda()
+    P = torch.empty((len(dms), plan.n_dump, plan.n_pix), dtype=torch.float32, device="cuda")
+    plan.chimageator(xd, P)
+    Pg = P.cpu().numpy()
+    Po = orc.chimageator(x, sc.f0, sc.bw, k_dm, sc.dms, nfft_min, L, sc.xyz, sc.pix_lm)
+    first, last = plan.dump_range()
+    for d in range(len(dms)):
+        assert np.all(Pg[d, :first[d]] == 0) and np.all(Pg[d, last[d] + 1:] == 0)
+    err = pow_error(Pg, Po)
+    assert err < TOL_POW_BF16, err
+    assert err > 1e-7  # the voltages really were rounded
+    rng = np.random.default_rng(M)
+    mask = (rng.random((len(dms), plan.n_dump)) < 0.3).astype(np.uint8)
+    S = torch.empty_like(P)
+    plan.chimageator_selective(xd, mask, S)
+    valid = np.zeros_like(mask, bool)
+    for d in range(len(dms)):
+        valid[d, first[d]:last[d] + 1] = True
+    pick = mask.astype(bool) & valid
+    Sg = S.cpu().numpy()
+    assert np.all(Sg[~pick] == 0)
+    assert np.array_equal(Sg[pick], Pg[pick])
+    # the Chirpolator of the same plan keeps FP32 voltages
+    V = np.empty((len(dms), plan.n_dump, plan.n_pair), np.complex64)
+    plan.chirpolator(x, V)
+    Vo = orc.chirpolator(x, sc.f0, sc.bw, k_dm, sc.dms, nfft_min, L)
+    assert vis_error(V, Vo, M) < TOL_VIS
