@@ -302,14 +302,14 @@ static cudaError_t correlate_any(const T* y, long long n_samp, int n_ant, int du
   if (n_m <= 0) return cudaSuccess;
   if (n_ant <= kCorrStagedMaxAnt) {
     if (n_m >= (1LL << 31)) return cudaErrorInvalidConfiguration;
-    // 256-sample chunks (at most 96 KB of ring for 16 antennas); 16-byte
-    // copies when every row and dump starts on a 16-byte boundary of a
-    // 16-byte aligned array
+    // 128-sample chunks (at most 48 KB of ring for 16 antennas, so that
+    // several CTAs share an SM); 16-byte copies when every row and dump
+    // starts on a 16-byte boundary of a 16-byte aligned array
     constexpr int EPV = 16 / (int)sizeof(T);
     if (n_samp % EPV == 0 && dump_len % EPV == 0 && ((uintptr_t)y & 15) == 0)
-      return launch_staged<T, 256, true>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last,
+      return launch_staged<T, 128, true>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last,
                                          vis, st, dump_list, n_tiles);
-    return launch_staged<T, 256, false>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis,
+    return launch_staged<T, 128, false>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis,
                                         st, dump_list, n_tiles);
   }
   const int warps = n_tiles < kCorrWarps ? n_tiles : kCorrWarps;
