@@ -468,17 +468,18 @@ def batch_leg(args):
     """The batched form at its stated scale: 24 observations drawn with a
     fixed seed -- 2^U{20..24} samples, U{32..512} trial DMs over 0..U(50, 300)
     pc cm^-3, U{8..64} antennas within 6 km, U(16, 64) MHz at 1.4 GHz, dumps
-    of 2^U{9..13} samples, 8 x 8 beams over 1 deg -- each a plan on its own
-    stream under CUDA graphs, all queued by one chirp_batch_run (complex64
+    of 2^U{9..13} samples, 8 x 8 beams over 1 deg -- each a lean plan (one
+    FFT-length group's spectra at a time) on its own stream under CUDA
+    graphs, all queued by one chirp_batch_run (complex64
     noise drawn on the device).  An observation whose plan, output and
-    input would pass 150 GB in all, or not fit the free device memory, is
+    input would pass 200 GB in all, or not fit the free device memory, is
     skipped; the line lists what ran and what was skipped."""
     import torch
     import paper_1109_3186_gb300 as chirp
     from paper_1109_3186_gb300 import skymodel
     g = np.random.default_rng(1004)
     plans, xs, outs, shapes, skipped = [], [], [], [], []
-    units, used, budget = 0, 0, 150e9
+    units, used, budget = 0, 0, 200e9
     try:
         for i in range(24):
             M = int(g.integers(8, 65))
@@ -492,11 +493,15 @@ def batch_leg(args):
                                               n_pulse=0, seed=3000 + i, bw=bw)
             st = torch.cuda.Stream()
             try:
-                pl = chirp.Plan.from_scenario(scb, stream=st, flags=chirp.FLAG_GRAPHS)
+                pl = chirp.Plan.from_scenario(scb, stream=st,
+                                              flags=chirp.FLAG_GRAPHS | chirp.FLAG_LEAN)
             except chirp.ChirpError:  # its workspace does not fit beside the others
                 skipped.append([M, N, nd])
                 continue
-            need = pl.info["workspace_bytes"] + 4 * nd * pl.n_dump * pl.n_pix + 8 * M * N
+            # workspace (one group's spectra: lean plans), the voltage buffer
+            # the visibility form allocates on its first run, output and input
+            need = pl.info["workspace_bytes"] + 4 * nd * pl.n_dump * pl.n_pix + 8 * M * N + \
+                (8 * M * N if pl.info["beam_mode"] in (1, 3, 5) else 0)
             free, _ = torch.cuda.mem_get_info()
             if used + need > budget or need > free - 8e9:
                 pl.close()
@@ -528,8 +533,8 @@ def batch_leg(args):
                 "skipped_M_N_ndm": skipped,
                 "shapes_M_N_ndm_dmmax_MHz_L": shapes,
                 "recipe": "seeded: 2^20-2^24 samples, 32-512 DMs over 0-U(50,300), 8-64 antennas, "
-                          "16-64 MHz, dumps 2^9-2^13, 8x8 beams; one stream each, CUDA graphs, "
-                          "host-timed"}
+                          "16-64 MHz, dumps 2^9-2^13, 8x8 beams; lean plans, one stream each, "
+                          "CUDA graphs, host-timed"}
     finally:
         for pl in plans:
             pl.close()
@@ -568,6 +573,17 @@ def cpi_search(sc, xd, stream, args, peaks):
         for name, v in plan.timing().items():
             st[name] += v / 3
     nws = [plan.layout(d)["n_win"] for d in range(len(dms))]
+    plan_cc = CpiPlan(sc.xyz, sc.f0, sc.bw, sc.n_samp, dms, L, sc.pix_lm, F, k_dm=sc.k_dm,
+                      stream=stream, image_mode=1)
+    for _ in range(2):
+        plan_cc.run(xd, E)
+    a0.record(stream)
+    for _ in range(k):
+        plan_cc.run(xd, E)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms_cc = a0.elapsed_time(a1) / k
+    plan_cc.close()
     windows = sum(max(0, plan.n_blk - nw + 1) for nw in nws)
     units = sc.n_ant * len(dms) * plan.n_blk * L
     sm_max = peaks.get("sm_max_mhz", FALLBACK_PEAKS["sm_max_mhz"])
@@ -581,20 +597,34 @@ def cpi_search(sc, xd, stream, args, peaks):
     # moments: read the voltages once, write J moments per (sub-block, pair)
     mom_bytes = 8.0 * sc.n_ant * plan.n_blk * L + 8.0 * plan.n_blk * (L // plan.info["sub_len"]) \
         * plan.info["n_terms"] * plan.n_pair
+    # image on the tensor cores: the dense-in-bins contraction, 2 x (2 n_pix
+    # rows) x (2 nk n_pair real K) x (complete-window tiles of 256) per DM, one
+    # term; the split-BF16 form executes three such products (K and rows
+    # padded to the 32 / 128 tiles)
+    rows = -(-2 * plan.n_pix // 128) * 128
+    kpad = -(-2 * nk * plan.n_pair // 32) * 32
+    tiles = sum(max(0, -(-plan.n_blk // 256) - (nw - 1) // 256) for nw in nws)
+    dense = 2.0 * (2 * plan.n_pix) * (2 * nk * plan.n_pair) * windows
+    executed = 3 * 2.0 * rows * kpad * 256 * tiles
+    bf16 = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
     roof = {
         "moments": ("hbm", mom_bytes / (st["moments"] * 1e-3) / 1e9, hbm, "GB/s"),
         "cic": ("hbm", cic_bytes / (st["cic"] * 1e-3) / 1e9, hbm, "GB/s"),
-        "image": ("alu", img_flops / (st["image"] * 1e-3) / 1e12, alu, "TFLOP/s"),
+        "image": ("tensor", dense / (st["image"] * 1e-3) / 1e12, bf16, "TFLOP/s"),
     }
     out = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": k,
            "beam_dm_windows_per_s": windows * plan.n_pix / (ms * 1e-3),
            "n_dm": len(dms), "blk_len": L, "half_width": F, "max_bin": plan.max_bin,
            "n_freq": plan.info["n_freq"], "sub_len": plan.info["sub_len"],
-           "n_terms": plan.info["n_terms"], "gpu_launches_per_step": 4,
+           "n_terms": plan.info["n_terms"], "gpu_launches_per_step": 5,
            "stages_ms": st,
            "roofline": {n: {"bound": b, "achieved": a, "peak": pk, "unit": u, "frac": a / pk}
                         for n, (b, a, pk, u) in roof.items()},
-           "dtype": "f32 (moving sums compensated, two floats)",
+           "image_tensor_executed_tflops": executed / (st["image"] * 1e-3) / 1e12,
+           "image_useful_sparse_tflops": img_flops / (st["image"] * 1e-3) / 1e12,
+           "cuda_core_image_ms_per_step": ms_cc,
+           "dtype": "f32 (moving sums compensated, two floats; image: split-bf16 x3 on tensor "
+                    "cores, f32 acc)",
            "note": "paper's own pre-integrator on the raw voltages: DMs > 0 of the 64"}
     plan.close()
     return out

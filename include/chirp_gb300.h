@@ -157,6 +157,13 @@ typedef struct {
                                  launch sequence, later calls launch the graph.
                                  Needs a non-default plan stream.  Stage timing
                                  does not see inside graph launches.          */
+#define CHIRP_FLAG_LEAN 4     /* hold the forward spectra of one FFT-length
+                                 group at a time (one buffer sized for the
+                                 largest group, each group's spectra formed
+                                 right before its DMs) instead of every
+                                 group's: less device memory, the forward
+                                 passes re-run when a search revisits a group
+                                 (same outputs)                               */
 #define CHIRP_FLAG_AUTOTUNE 2 /* time the candidate FFT factorisations (row
                                  length 512..4096) of every FFT-length group on
                                  the device at plan creation and keep the
@@ -167,7 +174,9 @@ typedef struct {
   long long n_dump;        /* floor(n_samp / dump_len)                          */
   int n_pair;              /* n_ant (n_ant + 1) / 2                             */
   int n_group;             /* distinct FFT lengths                              */
-  long long workspace_bytes;/* device memory owned by the plan                  */
+  long long workspace_bytes;/* device memory owned by the plan (grows on the
+                              first run that needs the dedispersed-voltage
+                              buffer or host-buffer staging)                 */
   long long ifft_points;   /* sum over DMs of n_ant * n_blk * Nfft              */
   long long valid_samples; /* sum over DMs of n_ant * (n_samp - n_hi - n_lo)^+  */
   int beam_mode;           /* CHIRP_BEAM_* actually used (AUTO resolved)        */
@@ -487,6 +496,12 @@ typedef struct {
   int half_width;        /* F, 0..8                                            */
   int max_bin;           /* K (0: the smallest that holds every pixel's bins);
                             at most 64                                         */
+  int image_mode;        /* 0: the image as a dense contraction on the tcgen05
+                            tensor cores (the filter densified over all 2K+1
+                            bins, split-BF16 operands: A_h B_h + A_h B_l +
+                            A_l B_h, FP32 accumulate; about 2.4 GB of operand
+                            images on the bench workload); 1: the sparse
+                            2F+1-bin gathers on the CUDA cores               */
 } chirp_cpi_config;
 
 typedef struct {
@@ -511,7 +526,9 @@ int chirp_cpi_query(const chirp_cpi_plan* plan, chirp_cpi_info* info);
 int chirp_cpi_layout(const chirp_cpi_plan* plan, int d, int* n_win, double* fdot, int* pair_bins);
 /* E [n_dm][n_blk][n_pix] float (|P|^2; zero for incomplete windows) from
  * complex64 voltages [n_ant][n_samp].  volt_loc / out_loc: CHIRP_HOST or
- * CHIRP_DEVICE.  A host output synchronises the plan's stream. */
+ * CHIRP_DEVICE.  A host output synchronises the plan's stream and returns
+ * CHIRP_ETIMEOUT if a bounded wait of the tensor-core image pass gave up
+ * (chirp_cpi_timing reports the same). */
 int chirp_cpi_run(chirp_cpi_plan* plan, const void* volt, int volt_loc, float* energy, int out_loc);
 /* The intermediate spectra of the same search, both complex64
  * [n_dm][n_blk][2K+1][n_pair] (bin k at index k + K): V the partial DFTs,

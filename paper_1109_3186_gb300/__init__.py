@@ -35,7 +35,7 @@ CHIRP_HOST, CHIRP_DEVICE = 0, 1
 BEAM_AUTO, BEAM_FP32_SIMT, BEAM_TC_3XBF16, BEAM_VIS, BEAM_TC_BF16, BEAM_VIS_BF16 = 0, 1, 2, 3, 4, 5
 IN_C64, IN_CI8 = 0, 1
 CORR_AUTO, CORR_FP32_SIMT, CORR_TC_3XBF16, CORR_TC_BF16 = 0, 1, 2, 3
-FLAG_GRAPHS, FLAG_AUTOTUNE = 1, 2
+FLAG_GRAPHS, FLAG_AUTOTUNE, FLAG_LEAN = 1, 2, 4
 CHIRP_OK, CHIRP_EINVAL, CHIRP_ENOMEM, CHIRP_ECUDA, CHIRP_ETIMEOUT, CHIRP_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 K_DM_DEFAULT = 4.148808e15
 

@@ -26,7 +26,8 @@ class _CpiConfig(ctypes.Structure):
                 ("k_dm", ctypes.c_double), ("n_samp", ctypes.c_longlong),
                 ("dm", ctypes.POINTER(ctypes.c_double)), ("n_dm", ctypes.c_int),
                 ("blk_len", ctypes.c_int), ("pix_lm", ctypes.POINTER(ctypes.c_double)),
-                ("n_pix", ctypes.c_int), ("half_width", ctypes.c_int), ("max_bin", ctypes.c_int)]
+                ("n_pix", ctypes.c_int), ("half_width", ctypes.c_int), ("max_bin", ctypes.c_int),
+                ("image_mode", ctypes.c_int)]
 
 
 class _CpiInfo(ctypes.Structure):
@@ -73,7 +74,7 @@ class CpiPlan:
     [n_dm, n_blk, 2K+1, n_pair] complex64."""
 
     def __init__(self, xyz, f0, bw, n_samp, dms, blk_len, pix_lm, half_width=2, max_bin=0,
-                 k_dm=0.0, stream=None):
+                 k_dm=0.0, stream=None, image_mode=0):
         self._xyz = _f64(xyz, (3,))
         self._dms = _f64(dms).ravel()
         self._pix = _f64(pix_lm, (2,))
@@ -88,6 +89,7 @@ class CpiPlan:
         c.pix_lm = self._pix.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         c.n_pix = self._pix.shape[0]
         c.half_width, c.max_bin = int(half_width), int(max_bin)
+        c.image_mode = int(image_mode)  # 0: tensor cores (dense filter), 1: CUDA-core gathers
         self._h = ctypes.c_void_p()
         _check(_lib().chirp_cpi_create(ctypes.byref(self._h), ctypes.byref(c), _stream_handle(stream)))
         inf = _CpiInfo()

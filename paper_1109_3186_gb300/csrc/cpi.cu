@@ -550,6 +550,9 @@ struct chirp_cpi_plan {
   float2 *d_x = nullptr, *d_T = nullptr, *d_V = nullptr, *d_X = nullptr, *d_W = nullptr;
   short* d_K0 = nullptr;
   float* d_E = nullptr;
+  int image_mode = 0;              // 0: tensor-core dense image, 1: CUDA-core gathers
+  uint8_t *d_aimg = nullptr, *d_bimg = nullptr;  // tensor-core operand images
+  int* d_err = nullptr;            // device status word of the tensor-core pass
   CpiFreq* d_freq = nullptr;
   int *d_vrow = nullptr, *d_nwin = nullptr, *d_kpq = nullptr;
   short2* d_pairs = nullptr;
@@ -562,8 +565,9 @@ namespace {
 
 void free_plan(chirp_cpi_plan* p) {
   if (!p) return;
-  void* bufs[] = {p->d_x, p->d_T, p->d_V, p->d_X, p->d_W, p->d_K0, p->d_E,
-                  p->d_freq, p->d_vrow, p->d_nwin, p->d_kpq, p->d_pairs};
+  void* bufs[] = {p->d_x,    p->d_T,    p->d_V,    p->d_X,     p->d_W,    p->d_K0,
+                  p->d_E,    p->d_freq, p->d_vrow, p->d_nwin,  p->d_kpq,  p->d_pairs,
+                  p->d_aimg, p->d_bimg, p->d_err};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (auto& e : p->ev)
@@ -596,6 +600,8 @@ int plan_host(chirp_cpi_plan* p, const chirp_cpi_config* c, std::vector<double>&
     return cfail(CHIRP_EINVAL, "n_dm must be in 1..65535 and n_pix >= 1");
   if (c->half_width < 0 || c->half_width > 8) return cfail(CHIRP_EINVAL, "half_width must be in 0..8");
   if (c->max_bin < 0 || c->max_bin > kMaxBin) return cfail(CHIRP_EINVAL, "max_bin must be in 0..64");
+  if (c->image_mode != 0 && c->image_mode != 1) return cfail(CHIRP_EINVAL, "image_mode must be 0 or 1");
+  p->image_mode = c->image_mode;
   p->M = c->n_ant;
   p->f0 = c->f0_hz;
   p->bw = c->bw_hz;
@@ -741,7 +747,10 @@ int cpi_enqueue(chirp_cpi_plan* p, const void* volt, int volt_loc, float* E) {
       p->d_X);
   CKC(cudaGetLastError());
   CKC(cudaEventRecord(p->ev[3], p->st));
-  if (E) {
+  if (E && p->image_mode == 0) {
+    CKC(chirp::launch_cpi_tc_image(p->d_X, p->d_bimg, p->d_aimg, p->d_nwin, p->n_dm, p->n_blk, nk,
+                                   p->n_pair, p->n_pix, E, p->d_err, p->st));
+  } else if (E) {
     const dim3 grid((unsigned)((p->n_pix + 511) / 512), (unsigned)((p->n_blk + kImgBlocks - 1) / kImgBlocks),
                     (unsigned)p->n_dm);
     k_cpi_image<<<grid, 256, kImgSmemBytes, p->st>>>(p->d_X, p->d_W, p->d_K0, p->d_nwin, p->n_pair,
@@ -750,6 +759,16 @@ int cpi_enqueue(chirp_cpi_plan* p, const void* volt, int volt_loc, float* E) {
   }
   CKC(cudaEventRecord(p->ev[4], p->st));
   p->timed = E != nullptr;
+  return CHIRP_OK;
+}
+
+// After a synchronisation: CHIRP_ETIMEOUT when a bounded wait of the
+// tensor-core image pass gave up (its outputs are then invalid).
+int cpi_status(chirp_cpi_plan* p) {
+  if (!p->d_err) return CHIRP_OK;
+  int flag = 0;
+  CKC(cudaMemcpy(&flag, p->d_err, 4, cudaMemcpyDeviceToHost));
+  if (flag) return cfail(CHIRP_ETIMEOUT, "a bounded wait of the tensor-core image pass gave up");
   return CHIRP_OK;
 }
 
@@ -821,6 +840,26 @@ int chirp_cpi_create(chirp_cpi_plan** out, const chirp_cpi_config* cfg, void* st
   }
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cpi_image, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  kImgSmemBytes);
+  if (e == cudaSuccess && p->image_mode == 0) {
+    // the dense split-BF16 filter of every DM, built once from the sparse one
+    const int nk = 2 * p->K + 1;
+    rc = alloc(p, (void**)&p->d_aimg, chirp::cpi_tc_a_bytes(p->n_dm, p->n_pix, nk, p->n_pair),
+               "tensor-core filter image");
+    if (!rc) rc = alloc(p, (void**)&p->d_bimg, chirp::cpi_tc_b_bytes(p->n_dm, p->n_blk, nk, p->n_pair),
+                        "tensor-core window-DFT image");
+    if (!rc) rc = alloc(p, (void**)&p->d_err, 4, "status word");
+    if (rc) {
+      cudaStreamSynchronize(p->st);
+      cudaFree(d_tau);
+      cudaFree(d_dmc);
+      free_plan(p);
+      return rc;
+    }
+    e = cudaMemsetAsync(p->d_err, 0, 4, p->st);
+    if (e == cudaSuccess)
+      e = chirp::launch_cpi_tc_aimg(p->d_W, p->d_K0, p->n_dm, p->n_pair, 2 * p->F + 1, nk, p->n_pix,
+                                    p->d_aimg, p->st);
+  }
   for (auto& ev : p->ev)
     if (e == cudaSuccess) e = cudaEventCreate(&ev);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);  // the host tables above die here
@@ -871,6 +910,7 @@ int chirp_cpi_run(chirp_cpi_plan* p, const void* volt, int volt_loc, float* ener
   if (out_loc == CHIRP_HOST) {
     CKC(cudaMemcpyAsync(energy, E, (size_t)n_out * 4, cudaMemcpyDeviceToHost, p->st));
     CKC(cudaStreamSynchronize(p->st));
+    return cpi_status(p);
   }
   return CHIRP_OK;
 }
@@ -912,7 +952,7 @@ int chirp_cpi_timing(chirp_cpi_plan* p, double ms[4]) {
     if (i < 3 || p->timed) CKC(cudaEventElapsedTime(&t, p->ev[i], p->ev[i + 1]));
     ms[i] = t;
   }
-  return CHIRP_OK;
+  return cpi_status(p);
 }
 
 void chirp_cpi_destroy(chirp_cpi_plan* p) {

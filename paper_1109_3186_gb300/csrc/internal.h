@@ -128,6 +128,20 @@ cudaError_t launch_inverse_cols_pow(const float2* Z, float* P, long long n_samp,
                                     long long n_hi, long long n_lo, int dump_len, long long t_lo,
                                     long long t_hi, TwiddlePtrs tw, cudaStream_t st);
 
+// ---- Chirpolator pre-integrator image on the tensor cores (cpi_tc.cu) ----
+// Bytes of the dense split-BF16 filter image (all DMs) and window-DFT image.
+long long cpi_tc_a_bytes(int n_dm, int n_pix, int nk, int n_pair);
+long long cpi_tc_b_bytes(int n_dm, long long n_blk, int nk, int n_pair);
+// Filter image from the sparse filter W [n_dm][n_pair][nj][n_pix] and its
+// first bins K0 [n_dm][n_pair][n_pix] (clears the image first).
+cudaError_t launch_cpi_tc_aimg(const float2* W, const short* K0, int n_dm, int n_pair, int nj,
+                               int nk, int n_pix, uint8_t* aimg, cudaStream_t st);
+// E [n_dm][n_blk][n_pix] = |A X|^2 from the window DFTs X [n_dm][n_blk][nk][n_pair]
+// (zero while m < n_win[d] - 1); bimg is the plan's window-DFT image buffer.
+cudaError_t launch_cpi_tc_image(const float2* X, uint8_t* bimg, const uint8_t* aimg,
+                                const int* n_win, int n_dm, long long n_blk, int nk, int n_pair,
+                                int n_pix, float* E, int* err, cudaStream_t st);
+
 // ---- back-ends (backends.cu) ----
 // Clears the rows (row_floats floats each) of the listed cells (d n_dump + m).
 cudaError_t launch_zero_cells(float* out, const int* cells, long long n_cells, int row_floats,

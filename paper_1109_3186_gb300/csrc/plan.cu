@@ -128,7 +128,13 @@ struct chirp_plan {
   int dm_chunk = 1;          // DMs of one group whose row passes run together
   long long h_stride = 0;    // elements between chirp tables
   size_t z_stride = 0;       // elements between the DMs' inverse workspaces
-  float2* d_y = nullptr;     // dedispersed voltages of one DM [M][N]
+  float2* d_y = nullptr;     // dedispersed voltages of one DM [M][N] (allocated on first use)
+  // CHIRP_FLAG_LEAN: one spectra buffer shared by the groups, each group's
+  // spectra formed right before its DMs (spec_group: the group it holds)
+  bool lean = false;
+  float2* d_spec_shared = nullptr;
+  int spec_group = -1;
+  const void* spec_src = nullptr;
   float2* d_W = nullptr;     // beam weights [n_pix][M]
   uint8_t* d_aimg = nullptr; // tensor-core A image (split-BF16 weights)
   uint8_t* d_bimg = nullptr; // tensor-core B image of one DM (split-BF16 voltages)
@@ -203,18 +209,26 @@ int dev_alloc(chirp_plan* p, void** ptr, size_t bytes, const char* what) {
   return CHIRP_OK;
 }
 
+// The dedispersed-voltage buffer, allocated on the first call that needs it
+// (the tensor-core beam path writes its own image and never does).
+int ensure_y(chirp_plan* p) {
+  if (p->d_y) return CHIRP_OK;
+  return dev_alloc(p, (void**)&p->d_y, (size_t)p->M * p->N * sizeof(float2), "voltages");
+}
+
 void release(chirp_plan* p) {
   if (!p) return;
   if (p->stream) cudaStreamSynchronize(p->stream);
   for (auto& g : p->groups) {
     cudaFree(g.d_G);
     cudaFree(g.d_rtw);
-    cudaFree(g.d_spec);
+    if (!p->lean) cudaFree(g.d_spec);
     cudaFree(g.d_tdph);
     cudaFree(g.d_tdrot);
   }
   cudaFree(p->d_tdY);
   cudaFree(p->d_tdZ);
+  cudaFree(p->d_spec_shared);
   cudaFree(p->d_tw);
   cudaFree(p->d_x);
   cudaFree(p->d_Z);
@@ -382,7 +396,7 @@ int validate(const chirp_config* c) {
     return fail(CHIRP_EINVAL, "beam_shape must be 0..3");
   if (c->corr_mode < 0 || c->corr_mode > CHIRP_CORR_TC_BF16)
     return fail(CHIRP_EINVAL, "unknown corr_mode");
-  if (c->flags & ~(CHIRP_FLAG_GRAPHS | CHIRP_FLAG_AUTOTUNE))
+  if (c->flags & ~(CHIRP_FLAG_GRAPHS | CHIRP_FLAG_AUTOTUNE | CHIRP_FLAG_LEAN))
     return fail(CHIRP_EINVAL, "unknown flag bits 0x%x", c->flags);
   if (c->n_pix < 0) return fail(CHIRP_EINVAL, "n_pix must be >= 0");
   if (c->n_pix > 0 && (!c->pix_lm || !c->xyz_m))
@@ -492,6 +506,7 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   p->in_type = cfg->in_type;
   p->stream = (cudaStream_t)stream;
   p->use_graphs = (cfg->flags & CHIRP_FLAG_GRAPHS) != 0;
+  p->lean = (cfg->flags & CHIRP_FLAG_LEAN) != 0;
   if (p->use_graphs && p->stream == nullptr) {
     delete p;
     return fail(CHIRP_EINVAL, "CUDA graphs need a plan stream other than the legacy default stream");
@@ -577,12 +592,19 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
 
   // ---- device workspace
   rc = dev_alloc(p, (void**)&p->d_tw, kTwiddleElems * sizeof(float2), "twiddles");
-  size_t z_elems = 0;
+  size_t z_elems = 0, max_spec = 0;
+  for (auto& g : p->groups)
+    max_spec = std::max(max_spec, (size_t)p->M * (size_t)g.geom.n_blk * (size_t)g.geom.nfft);
+  if (!rc && p->lean)
+    rc = dev_alloc(p, (void**)&p->d_spec_shared, max_spec * sizeof(float2), "spectra (shared)");
   for (auto& g : p->groups) {
     size_t elems = (size_t)p->M * g.geom.n_blk * g.geom.nfft;
     z_elems = std::max(z_elems, (size_t)inverse_chunk_sequences(g.geom, (long long)p->M * g.geom.n_blk) *
                                     (size_t)g.geom.nfft);
-    if (!rc) rc = dev_alloc(p, (void**)&g.d_spec, elems * sizeof(float2), "spectra");
+    if (p->lean)
+      g.d_spec = p->d_spec_shared;
+    else if (!rc)
+      rc = dev_alloc(p, (void**)&g.d_spec, elems * sizeof(float2), "spectra");
     if (!rc) rc = dev_alloc(p, (void**)&g.d_G, g.geom.nfft * sizeof(double), "phase table");
     if (!rc)
       rc = dev_alloc(p, (void**)&g.d_rtw, g.geom.nfft / 16 * sizeof(float2), "row twiddles");
@@ -608,7 +630,7 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   if (!rc)
     rc = dev_alloc(p, (void**)&p->d_H, (size_t)p->dm_chunk * max_nfft * sizeof(float2),
                    "chirp tables");
-  if (!rc) rc = dev_alloc(p, (void**)&p->d_y, (size_t)p->M * p->N * sizeof(float2), "voltages");
+  // (the dedispersed-voltage buffer d_y is allocated on first use: ensure_y)
   if (!rc && p->n_pix > 0)
     rc = dev_alloc(p, (void**)&p->d_W, (size_t)p->n_pix * p->M * sizeof(float2), "weights");
   if (!rc) rc = dev_alloc(p, (void**)&p->d_err, sizeof(int), "status word");
@@ -745,9 +767,15 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   if (e == cudaSuccess && !fb_shift.empty())
     e = cudaMemcpyAsync(p->d_fb_shift, fb_shift.data(), fb_shift.size() * sizeof(int),
                         cudaMemcpyHostToDevice, p->stream);
-  if (e == cudaSuccess && (cfg->flags & CHIRP_FLAG_AUTOTUNE) && cfg->fft_row == 0)
+  if (e == cudaSuccess && (cfg->flags & CHIRP_FLAG_AUTOTUNE) && cfg->fft_row == 0) {
+    if (ensure_y(p)) {
+      release(p);
+      delete p;
+      return CHIRP_ENOMEM;
+    }
     for (auto& g : p->groups)
       if (e == cudaSuccess) e = autotune_split(p, g);
+  }
   for (auto& g : p->groups) {
     if (e == cudaSuccess)
       e = launch_build_phase_table(g.d_G, g.geom, p->f0, p->bw, p->kdm, p->stream);
@@ -861,12 +889,30 @@ int finish_out(chirp_plan* p, void* user, int loc, const void* dev, size_t bytes
 }
 
 int forward_all(chirp_plan* p, const void* dx) {
+  if (p->lean) {  // spectra are formed per group, right before its DMs
+    p->spec_group = -1;
+    p->spec_src = dx;
+    return CHIRP_OK;
+  }
   for (auto& g : p->groups) {
     int mk = mark_begin(p);
     CK(launch_forward(dx, p->N, p->M, g.geom, g.d_spec, p->tw(), p->stream, p->in_type,
                       p->d_scale));
     mark_end(p, CHIRP_STAGE_FORWARD, mk);
   }
+  return CHIRP_OK;
+}
+
+// Lean plans: the shared spectra buffer holds group gi's spectra of the
+// current input afterwards (formed now unless it already does).
+int ensure_spec(chirp_plan* p, int gi) {
+  if (!p->lean || p->spec_group == gi) return CHIRP_OK;
+  Group& g = p->groups[gi];
+  int mk = mark_begin(p);
+  CK(launch_forward(p->spec_src, p->N, p->M, g.geom, g.d_spec, p->tw(), p->stream, p->in_type,
+                    p->d_scale));
+  mark_end(p, CHIRP_STAGE_FORWARD, mk);
+  p->spec_group = gi;
   return CHIRP_OK;
 }
 
@@ -1012,10 +1058,14 @@ int backend_dumps(chirp_plan* p, int d, Backend be, long long m0, long long m1, 
 // one launch: per chunk the chirp tables, one multi-DM row pass, then per
 // DM the column pass (voltages or the beam image) and the back-end.
 int full_search_chunked(chirp_plan* p, Backend be, void* dout) {
-  for (auto& grp : p->groups) {
+  for (size_t gi = 0; gi < p->groups.size(); gi++) {
+    Group& grp = p->groups[gi];
     std::vector<int> dms;
     for (int d : grp.dms)
       if (p->dmi[d].last >= p->dmi[d].first) dms.push_back(d);
+    if (dms.empty()) continue;
+    int rc0 = ensure_spec(p, (int)gi);
+    if (rc0) return rc0;
     const GroupGeom& G = grp.geom;
     const long long nq = (long long)p->M * G.n_blk;
     for (size_t c0 = 0; c0 < dms.size(); c0 += (size_t)p->dm_chunk) {
@@ -1126,7 +1176,8 @@ int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Bac
     if (I.last < I.first) continue;
     const GroupGeom& G = p->groups[I.group].geom;
     if (mask && dmp_n[d] == 0) continue;
-    rc = chirp_for(p, d);
+    rc = ensure_spec(p, I.group);
+    if (!rc) rc = chirp_for(p, d);
     if (rc) return rc;
     if (!mask) {
       const BeamImageOut img = fused_image(p, be) ? beam_image_for(p, d) : BeamImageOut{};
@@ -1253,7 +1304,8 @@ int truedelay_search(chirp_plan* p, const void* dx, float* dout, size_t bytes) {
     if (I.last < I.first) continue;
     Group& g = p->groups[I.group];
     const GroupGeom& G = g.geom;
-    rc = chirp_for(p, d);
+    rc = ensure_spec(p, I.group);
+    if (!rc) rc = chirp_for(p, d);
     if (rc) return rc;
     float* out = dout + (size_t)d * p->n_dump * p->n_pix;
     const long long cap =
@@ -1331,6 +1383,10 @@ int run_search(chirp_plan* p, const void* volt, int volt_loc, const unsigned cha
   const void* dx;
   int rc = stage_input(p, volt, volt_loc, &dx);
   if (rc) return rc;
+  if (be == kCorrelate || !tc_beams(p)) {
+    rc = ensure_y(p);
+    if (rc) return rc;
+  }
   const size_t per_dm = be == kCorrelate ? (size_t)p->n_dump * p->n_pair : (size_t)p->n_dump * p->n_pix;
   const size_t bytes = per_dm * p->dm.size() * (be == kCorrelate ? sizeof(float2) : sizeof(float));
   void* dout;
@@ -1367,6 +1423,8 @@ int chirp_dedisperse_run(chirp_plan* p, const void* volt, int volt_loc, int d, v
   Group& g = p->groups[I.group];
   CK(launch_forward(dx, p->N, p->M, g.geom, g.d_spec, p->tw(), p->stream, p->in_type,
                     p->d_scale));
+  p->spec_group = p->lean ? I.group : -1;  // the shared buffer now holds this group
+  p->spec_src = dx;
   CK(cudaMemsetAsync(dy, 0, bytes, p->stream));
   rc = dedisperse_one(p, d, (float2*)dy);
   if (rc) return rc;
@@ -1421,6 +1479,7 @@ int chirp_incoherent_run(chirp_plan* p, const void* volt, int volt_loc, float* S
     return fail(CHIRP_EINVAL, "bad buffer location");
   const void* dx;
   int rc = stage_input(p, volt, volt_loc, &dx);
+  if (!rc) rc = ensure_y(p);  // the filterbank's scratch
   if (rc) return rc;
   const size_t vbytes = (size_t)p->M * p->N * sizeof(float2);
   const size_t sbytes = (size_t)p->fb_chan * p->T_fb * sizeof(float);

@@ -152,3 +152,53 @@ def test_autotuned_split_matches_oracle_and_is_cached(k_dm):
     Po = orc.chimageator(x, sc.f0, sc.bw, k_dm, sc.dms, sc.nfft_min, sc.dump_len, sc.xyz,
                          sc.pix_lm)
     assert pow_error(P, Po) < TOL_POW
+
+
+@pytest.mark.parametrize("mode", [chirp.BEAM_VIS, chirp.BEAM_TC_3XBF16])
+def test_lean_plan_equals_full_plan_bit_for_bit(mode):
+    """CHIRP_FLAG_LEAN holds one FFT-length group's spectra at a time (formed
+    right before the group's DMs) and allocates the dedispersed-voltage buffer
+    only when a search needs it: every entry point gives the default plan's
+    outputs bit for bit, with less device memory.  Four DMs over three
+    FFT-length groups, visited by the full, selective, Chirpolator, one-DM,
+    true-delay and incoherent entry points in turn (so each run re-forms the
+    spectra it needs)."""
+    sc = _beams(N=1 << 17, n_dm=4)
+    sc.dms = np.array([0.0, 40.0, 90.0, 150.0])
+    kw = dict(beam_mode=mode, fb_chan=32, fb_int=8, fb_dm=sc.dms)
+    full = chirp.Plan.from_scenario(sc, **kw)
+    lean = chirp.Plan.from_scenario(sc, flags=chirp.FLAG_LEAN, **kw)
+    assert len({full.dm_layout(d)["nfft"] for d in range(4)}) >= 3
+    xd = torch.from_numpy(sc.voltages()).cuda()
+    shp = (4, full.n_dump, full.n_pix)
+    outs = {}
+    for name, pl in (("full", full), ("lean", lean)):
+        P = torch.empty(shp, dtype=torch.float32, device="cuda")
+        pl.chimageator(xd, P)
+        mask = np.zeros((4, pl.n_dump), np.uint8)
+        mask[1, 20:30] = 1
+        mask[3, 40:45] = 1
+        S = torch.empty_like(P)
+        pl.chimageator_selective(xd, mask, S)
+        V = torch.empty((4, pl.n_dump, pl.n_pair), dtype=torch.complex64, device="cuda")
+        pl.chirpolator(xd, V)
+        y = torch.empty((sc.n_ant, sc.n_samp), dtype=torch.complex64, device="cuda")
+        pl.dedisperse(xd, 2, y)
+        T = torch.empty_like(P)
+        pl.truedelay(xd, T)
+        D = torch.empty((4, pl.info["fb_samples"]), dtype=torch.float32, device="cuda")
+        pl.incoherent(xd, D)
+        P2 = torch.empty_like(P)
+        pl.chimageator(xd, P2)  # after the other entry points changed the spectra buffer
+        torch.cuda.synchronize()
+        outs[name] = [t.cpu().numpy() for t in (P, S, V, y, D, P2)] + [T.cpu().numpy()]
+    for a, b in zip(outs["full"][:6], outs["lean"][:6]):
+        assert np.array_equal(a, b)
+    # true-delay dump sums are atomic adds: equal to the FP32 roundings of their order
+    tf, tl = outs["full"][6], outs["lean"][6]
+    assert np.array_equal(tf == 0, tl == 0)
+    assert np.abs(tf - tl).max() <= 1e-5 * np.abs(tf).max()
+    assert np.array_equal(outs["lean"][0], outs["lean"][5])
+    ql = lean.info["workspace_bytes"]
+    qf = full.info["workspace_bytes"]
+    assert ql < qf, (ql, qf)

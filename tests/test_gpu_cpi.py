@@ -1,7 +1,8 @@
 """Parity of the CUDA Chirpolator pre-integrator (chirp_cpi_*) with the FP64
 oracle (oracle/cpi.py): partial DFTs V, window DFTs X and images E element by
 element on small seeded cases (ragged tails, one to 276 pairs, F = 0 and
-explicit K), device and host buffers, the bins each pair computes, a
+explicit K; the image both as the dense tensor-core contraction and as the
+sparse CUDA-core gathers), device and host buffers, the bins each pair computes, a
 dispersed burst from the sky model found at its pixel and DM, and sampled
 windows of the 12-antenna, 2^22-sample, 63-DM workload.
 
@@ -61,12 +62,16 @@ def _oracle(cfg, x):
                        keep=True)
 
 
+@pytest.mark.parametrize("mode", [0, 1], ids=["tensor_cores", "cuda_cores"])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_spectra_and_image_match_the_oracle(name):
+def test_spectra_and_image_match_the_oracle(name, mode):
+    """image_mode 0: the dense split-BF16 image on the tensor cores (the
+    default); 1: the sparse gathers on the CUDA cores.  Same tolerances."""
     cfg, x = _case(**CASES[name])
     E_o, kept, K_o = _oracle(cfg, x)
     with CpiPlan(cfg["xyz"], cfg["f0"], cfg["bw"], cfg["n_samp"], cfg["dms"], cfg["blk_len"],
-                 cfg["pix_lm"], cfg["half_width"], cfg["max_bin"], k_dm=K_DM) as plan:
+                 cfg["pix_lm"], cfg["half_width"], cfg["max_bin"], k_dm=K_DM,
+                 image_mode=mode) as plan:
         assert plan.max_bin == K_o
         nk = 2 * K_o + 1
         shape = (len(cfg["dms"]), plan.n_blk, nk, plan.n_pair)
