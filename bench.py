@@ -470,76 +470,85 @@ def batch_leg(args):
     pc cm^-3, U{8..64} antennas within 6 km, U(16, 64) MHz at 1.4 GHz, dumps
     of 2^U{9..13} samples, 8 x 8 beams over 1 deg -- each a lean plan (one
     FFT-length group's spectra at a time) on its own stream under CUDA
-    graphs, all queued by one chirp_batch_run (complex64
-    noise drawn on the device).  An observation whose plan, output and
-    input would pass 200 GB in all, or not fit the free device memory, is
-    skipped; the line lists what ran and what was skipped."""
+    graphs (complex64 noise drawn on the device).  The observations go in
+    waves: plans are created in order until their workspaces, outputs and
+    inputs would pass 200 GB or the free device memory, one chirp_batch_run
+    queues the whole wave (run once untimed, then timed: the second call
+    captures and launches the graphs), the wave's plans are destroyed and the
+    next wave starts.  value = all 24 observations' antenna*DM*samples over
+    the sum of the waves' timed calls."""
     import torch
     import paper_1109_3186_gb300 as chirp
     from paper_1109_3186_gb300 import skymodel
     g = np.random.default_rng(1004)
-    plans, xs, outs, shapes, skipped = [], [], [], [], []
-    units, used, budget = 0, 0, 200e9
-    try:
-        for i in range(24):
-            M = int(g.integers(8, 65))
-            N = int(2 ** g.integers(20, 25))
-            nd = int(g.integers(32, 513))
-            dm_max = float(g.uniform(50.0, 300.0))
-            bw = float(g.uniform(16e6, 64e6))
-            L = int(2 ** g.integers(9, 14))
-            scb = skymodel.chimageator_medium(n_samp=N, n_dm=nd, n_ant=M, dm_max=dm_max,
-                                              nfft_min=1 << 16, dump_len=L, n_side=8,
-                                              n_pulse=0, seed=3000 + i, bw=bw)
-            st = torch.cuda.Stream()
-            try:
-                pl = chirp.Plan.from_scenario(scb, stream=st,
-                                              flags=chirp.FLAG_GRAPHS | chirp.FLAG_LEAN)
-            except chirp.ChirpError:  # its workspace does not fit beside the others
-                skipped.append([M, N, nd])
-                continue
-            # workspace (one group's spectra: lean plans), the voltage buffer
-            # the visibility form allocates on its first run, output and input
-            need = pl.info["workspace_bytes"] + 4 * nd * pl.n_dump * pl.n_pix + 8 * M * N + \
-                (8 * M * N if pl.info["beam_mode"] in (1, 3, 5) else 0)
-            free, _ = torch.cuda.mem_get_info()
-            if used + need > budget or need > free - 8e9:
+    shapes = []
+    for i in range(24):
+        M = int(g.integers(8, 65))
+        N = int(2 ** g.integers(20, 25))
+        nd = int(g.integers(32, 513))
+        dm_max = float(g.uniform(50.0, 300.0))
+        bw = float(g.uniform(16e6, 64e6))
+        L = int(2 ** g.integers(9, 14))
+        shapes.append((i, M, N, nd, dm_max, bw, L))
+    units, total_s, waves, budget, peak_used = 0, 0.0, [], 200e9, 0
+    pending = list(shapes)
+    while pending:
+        plans, xs, outs, used, wave = [], [], [], 0, []
+        try:
+            while pending:
+                i, M, N, nd, dm_max, bw, L = pending[0]
+                scb = skymodel.chimageator_medium(n_samp=N, n_dm=nd, n_ant=M, dm_max=dm_max,
+                                                  nfft_min=1 << 16, dump_len=L, n_side=8,
+                                                  n_pulse=0, seed=3000 + i, bw=bw)
+                st = torch.cuda.Stream()
+                try:
+                    pl = chirp.Plan.from_scenario(scb, stream=st,
+                                                  flags=chirp.FLAG_GRAPHS | chirp.FLAG_LEAN)
+                except chirp.ChirpError:  # does not fit beside this wave's plans
+                    if not plans:
+                        raise
+                    break
+                # workspace (one group's spectra), the voltage buffer the
+                # visibility form allocates on its first run, output, input
+                need = pl.info["workspace_bytes"] + 4 * nd * pl.n_dump * pl.n_pix + 8 * M * N + \
+                    (8 * M * N if pl.info["beam_mode"] in (1, 3, 5) else 0)
+                free, _ = torch.cuda.mem_get_info()
+                if plans and (used + need > budget or need > free - 8e9):
+                    pl.close()
+                    break
+                pending.pop(0)
+                used += need
+                plans.append(pl)
+                xs.append(torch.complex(torch.randn(M, N, device="cuda"),
+                                        torch.randn(M, N, device="cuda")) * (0.5 ** 0.5))
+                outs.append(torch.empty((nd, pl.n_dump, pl.n_pix), dtype=torch.float32,
+                                        device="cuda"))
+                units += pl.info["valid_samples"]
+                wave.append([M, N, nd, round(dm_max, 1), round(bw / 1e6, 1), L])
+            bes = [1] * len(plans)
+            torch.cuda.synchronize()
+            chirp.chirp_batch_run(plans, xs, outs, bes)  # eager (lazy allocations)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            chirp.chirp_batch_run(plans, xs, outs, bes)  # captured and launched
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            for pl in plans:
+                pl.status()
+            total_s += dt
+            peak_used = max(peak_used, used)
+            waves.append({"observations": len(plans), "s": dt, "shapes_M_N_ndm_dmmax_MHz_L": wave})
+        finally:
+            for pl in plans:
                 pl.close()
-                skipped.append([M, N, nd])
-                continue
-            used += need
-            plans.append(pl)
-            xs.append(torch.complex(torch.randn(M, N, device="cuda"),
-                                    torch.randn(M, N, device="cuda")) * (0.5 ** 0.5))
-            outs.append(torch.empty((nd, pl.n_dump, pl.n_pix), dtype=torch.float32,
-                                    device="cuda"))
-            units += pl.info["valid_samples"]
-            shapes.append([M, N, nd, round(dm_max, 1), round(bw / 1e6, 1), L])
-        bes = [1] * len(plans)
-        torch.cuda.synchronize()
-        for _ in range(2):  # eager, then captured
-            chirp.chirp_batch_run(plans, xs, outs, bes)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        k = 1
-        for _ in range(k):
-            chirp.chirp_batch_run(plans, xs, outs, bes)
-        torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / k
-        for pl in plans:
-            pl.status()
-        return {"value": units / dt, "unit": UNIT, "ms_per_batch": dt * 1e3,
-                "observations": len(plans), "device_bytes": used,
-                "skipped_M_N_ndm": skipped,
-                "shapes_M_N_ndm_dmmax_MHz_L": shapes,
-                "recipe": "seeded: 2^20-2^24 samples, 32-512 DMs over 0-U(50,300), 8-64 antennas, "
-                          "16-64 MHz, dumps 2^9-2^13, 8x8 beams; lean plans, one stream each, "
-                          "CUDA graphs, host-timed"}
-    finally:
-        for pl in plans:
-            pl.close()
-        del xs, outs
-        torch.cuda.empty_cache()
+            del xs, outs
+            torch.cuda.empty_cache()
+    return {"value": units / total_s, "unit": UNIT, "ms_per_batch": total_s * 1e3,
+            "observations": sum(w["observations"] for w in waves), "waves": waves,
+            "peak_device_bytes": peak_used,
+            "recipe": "seeded: 2^20-2^24 samples, 32-512 DMs over 0-U(50,300), 8-64 antennas, "
+                      "16-64 MHz, dumps 2^9-2^13, 8x8 beams; lean plans, one stream each, CUDA "
+                      "graphs, waves of at most 200 GB, host-timed"}
 
 
 def cpi_search(sc, xd, stream, args, peaks):
