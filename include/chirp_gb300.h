@@ -87,7 +87,7 @@ extern "C" {
                                   to 1e-2)                                    */
 
 /* contraction used by the Chirpolator back-end (and by CHIRP_BEAM_VIS) */
-#define CHIRP_CORR_AUTO 0      /* CHIRP_CORR_TC_3XBF16 from 12 antennas up where
+#define CHIRP_CORR_AUTO 0      /* CHIRP_CORR_TC_3XBF16 from 17 antennas up where
                                   supported (dump length a multiple of 128, or
                                   a divisor of 256 that is a multiple of 16; up
                                   to 48 antennas),

@@ -20,22 +20,28 @@ namespace chirp {
 // ------------------------------------------------------------------ correlate
 // The M x M product is cut into 4 x 4 antenna tiles on or above the diagonal.
 // One warp owns one tile of one dump: lane l takes the samples l, l + 32, ...
-// of the dump, keeps the tile's complex products in registers, and the 32
-// lane partials are summed with warp shuffles at the end.
+// of the dump, keeps the tile's products in registers, and the 32 lane
+// partials are summed with warp shuffles at the end.
 //
-// Up to 16 antennas (at most 10 tiles) one CTA holds every tile of a dump and
-// streams the dump through shared memory (k_correlate_staged): chunks of CH
-// samples of every antenna row are fetched with cp.async (16-byte copies when
-// rows and dumps start on even samples) into a ring of kCorrStages buffers,
-// so each sample is read from global memory once and several chunks are in
-// flight while the warps multiply; diagonal tiles form only their upper
-// triangle, and each complex product-accumulate is two paired FP32 FMAs
-// (fma.rn.f32x2 on the (re, im) accumulator pair).  Above 16 antennas
-// (k_correlate_direct) the warps of a CTA (kCorrWarps tiles of one dump, grid
-// dimension y over the rest) read the samples straight from global memory.
+// Up to 16 antennas (NT = ceil(M/4) <= 4 tile rows, at most 10 tiles) one CTA
+// holds every tile of a dump and streams the dump through shared memory
+// (k_correlate_staged): chunks of kCorrChunk samples of every antenna row are
+// fetched with cp.async (16-byte copies when rows and dumps start on 16-byte
+// boundaries) into two buffers, the next chunk in flight while the warps
+// multiply the current one.  Rows M .. 4 NT - 1 stay zero, and a dump's ragged
+// last chunk is zero-filled, so the inner loop has no bounds or predicates.
+// Each complex product-accumulate u_a conj(w_b) is two paired FP32 FMAs on
+// lane-split accumulators (fma.rn.f32x2):
+//   P += (u.re w.re, u.im w.im),  Q += (u.im w.re, u.re w.im),
+//   Re V = P.lo + P.hi,  Im V = Q.lo - Q.hi,
+// so a sample needs its (re, im) pair and one swapped copy (im, re) per row
+// antenna, and no broadcasts or sign flips.  Diagonal tiles form only their
+// upper triangle.  Above 16 antennas (k_correlate_direct) the warps of a CTA
+// (kCorrWarps tiles of one dump, grid dimension y over the rest) read the
+// samples straight from global memory.
 constexpr int kCorrTile = 4;
 constexpr int kCorrWarps = 8;
-constexpr int kCorrStages = 3;
+constexpr int kCorrChunk = 256;
 constexpr int kCorrStagedMaxAnt = 16;
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
@@ -62,13 +68,9 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// acc (re, im) += u * conj(w) as two paired FMAs:
-//   (re, im) += (u.x, u.y) w.x  and  (re, im) += (u.y, -u.x) w.y
-__device__ __forceinline__ void cmac_conj2(unsigned long long& acc, unsigned long long u,
-                                           unsigned long long uswap, unsigned long long wxx,
-                                           unsigned long long wyy) {
-  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(u), "l"(wxx));
-  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(uswap), "l"(wyy));
+__device__ __forceinline__ void fma2(unsigned long long& acc, unsigned long long a,
+                                     unsigned long long b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
 }
 __device__ __forceinline__ unsigned long long pack2(float a, float b) {
   unsigned long long r;
@@ -80,99 +82,125 @@ __device__ __forceinline__ float2 unpack2(unsigned long long r) {
   asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
   return v;
 }
+// A staged sample as the (re, im) pair and, with SW, also the (im, re) pair.
+template <bool SW>
+__device__ __forceinline__ void sample_pair(const float2* p, unsigned long long& v,
+                                            unsigned long long& vs) {
+  v = *reinterpret_cast<const unsigned long long*>(p);
+  if (SW) {
+    const float2 a = unpack2(v);
+    vs = pack2(a.y, a.x);
+  }
+}
+template <bool SW>
+__device__ __forceinline__ void sample_pair(const __nv_bfloat162* p, unsigned long long& v,
+                                            unsigned long long& vs) {
+  // BF16 -> FP32 is exact: the 16 bits become the top half of the float
+  const unsigned b = *reinterpret_cast<const unsigned*>(p);
+  const float re = __uint_as_float(b << 16), im = __uint_as_float(b & 0xffff0000u);
+  v = pack2(re, im);
+  if (SW) vs = pack2(im, re);
+}
+__device__ __forceinline__ void zero_elem(float2* p) { *p = make_float2(0.f, 0.f); }
+__device__ __forceinline__ void zero_elem(__nv_bfloat162* p) {
+  *reinterpret_cast<unsigned*>(p) = 0u;
+}
 
-template <typename T, int CH, bool VEC16>
-__global__ void __launch_bounds__(32 * 10) k_correlate_staged(const T* __restrict__ y,
-                                                               long long n_samp, int M, int L,
-                                                               long long m_base, long long first,
-                                                               long long last,
-                                                               float2* __restrict__ vis,
-                                                               const int* __restrict__ dump_list) {
+// 96 registers: two CTAs of 10 warps (NT = 4) or three of 6 (NT = 3) per SM
+template <typename T, int NT, bool VEC16>
+__global__ void __maxnreg__(96)
+    k_correlate_staged(const T* __restrict__ y, long long n_samp, int M, int L, long long m_base,
+                       long long first, long long last, float2* __restrict__ vis,
+                       const int* __restrict__ dump_list) {
+  constexpr int MP = kCorrTile * NT;  // antenna rows of a stage, zero-padded
+  constexpr int NTH = 32 * NT * (NT + 1) / 2;
+  constexpr int CH = kCorrChunk;
+  constexpr int STAGE = MP * CH;
   extern __shared__ __align__(16) unsigned char ring_raw[];
-  T* ring = reinterpret_cast<T*>(ring_raw);  // [kCorrStages][M][CH]
+  T* ring = reinterpret_cast<T*>(ring_raw);  // [2][MP][CH]
   const long long m = dump_list ? (long long)dump_list[blockIdx.x] : m_base + blockIdx.x;
   const int n_pair = M * (M + 1) / 2;
   float2* out = vis + m * n_pair;
   if (m < first || m > last) {
-    for (int i = threadIdx.x; i < n_pair; i += blockDim.x) out[i] = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < n_pair; i += NTH) out[i] = make_float2(0.f, 0.f);
     return;
   }
-  const int nt = (M + kCorrTile - 1) / kCorrTile;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  int ti = 0, rem = warp;  // one tile per warp (blockDim = 32 x tiles)
-  while (rem >= nt - ti) {
-    rem -= nt - ti;
+  int ti = 0, rem = warp;  // one tile per warp
+  while (rem >= NT - ti) {
+    rem -= NT - ti;
     ti++;
   }
   const int tj = ti + rem;
   const bool diag = ti == tj;
-  bool vi[kCorrTile], vj[kCorrTile];
-#pragma unroll
-  for (int a = 0; a < kCorrTile; a++) {
-    vi[a] = ti * kCorrTile + a < M;
-    vj[a] = tj * kCorrTile + a < M;
+  for (int i = threadIdx.x; i < 2 * (MP - M) * CH; i += NTH) {
+    const int st = i / ((MP - M) * CH), r = i % ((MP - M) * CH);
+    zero_elem(ring + st * STAGE + M * CH + r);
   }
-  unsigned long long acc[kCorrTile][kCorrTile];
-#pragma unroll
-  for (int a = 0; a < kCorrTile; a++)
-#pragma unroll
-    for (int b = 0; b < kCorrTile; b++) acc[a][b] = 0ull;
-
   const T* src = y + m * L;  // sample 0 of the dump, antenna 0
   const int n_chunks = (L + CH - 1) / CH;
-  constexpr int EPV = 16 / (int)sizeof(T);  // samples per 16-byte copy
   auto fetch = [&](int c) {
     if (c < n_chunks) {
-      T* buf = ring + (size_t)(c % kCorrStages) * M * CH;
+      T* buf = ring + (c & 1) * STAGE;
       const int t0 = c * CH, len = min(CH, L - t0);
-      if constexpr (VEC16) {  // rows and chunks start on multiples of EPV samples
+      if constexpr (VEC16) {  // rows, dumps and len are multiples of EPV samples
+        constexpr int EPV = 16 / (int)sizeof(T);
         constexpr int U = CH / EPV;
-        for (int e = threadIdx.x; e < M * U; e += blockDim.x) {
+        for (int e = threadIdx.x; e < M * U; e += NTH) {
           const int a = e / U, i = EPV * (e % U);
-          if (i < len) cp_async16(buf + a * CH + i, src + (long long)a * n_samp + t0 + i);
+          if (i < len)
+            cp_async16(buf + a * CH + i, src + (long long)a * n_samp + t0 + i);
+          else
+            *reinterpret_cast<uint4*>(buf + a * CH + i) = make_uint4(0u, 0u, 0u, 0u);
         }
       } else {
-        for (int e = threadIdx.x; e < M * CH; e += blockDim.x) {
+        for (int e = threadIdx.x; e < M * CH; e += NTH) {
           const int a = e / CH, i = e % CH;
-          if (i < len) cp_async_elem(buf + a * CH + i, src + (long long)a * n_samp + t0 + i);
+          if (i < len)
+            cp_async_elem(buf + a * CH + i, src + (long long)a * n_samp + t0 + i);
+          else
+            zero_elem(buf + a * CH + i);
         }
       }
     }
     cp_async_commit();  // possibly empty: keeps the group count in step
   };
+  unsigned long long P[kCorrTile][kCorrTile], Q[kCorrTile][kCorrTile];
 #pragma unroll
-  for (int c = 0; c < kCorrStages - 1; c++) fetch(c);
+  for (int a = 0; a < kCorrTile; a++)
+#pragma unroll
+    for (int b = 0; b < kCorrTile; b++) P[a][b] = Q[a][b] = 0ull;
+  fetch(0);
   for (int c = 0; c < n_chunks; c++) {
-    cp_async_wait<kCorrStages - 2>();
+    cp_async_wait<0>();
     __syncthreads();  // chunk c is in; every warp is done with chunk c - 1
-    fetch(c + kCorrStages - 1);
-    const T* buf = ring + (size_t)(c % kCorrStages) * M * CH;
-    const int len = min(CH, L - c * CH);
-    const T* ri = buf + ti * kCorrTile * CH;
-    const T* rj = buf + tj * kCorrTile * CH;
-    for (int t = lane; t < len; t += 32) {
+    fetch(c + 1);
+    const T* buf = ring + (c & 1) * STAGE;
+    const T* ri = buf + ti * kCorrTile * CH + lane;
+    const T* rj = buf + tj * kCorrTile * CH + lane;
+#pragma unroll 1
+    for (int t = 0; t < CH; t += 32) {
       unsigned long long u[kCorrTile], us[kCorrTile];
 #pragma unroll
-      for (int a = 0; a < kCorrTile; a++) {
-        const float2 v = vi[a] ? to_f2(ri[a * CH + t]) : make_float2(0.f, 0.f);
-        u[a] = pack2(v.x, v.y);
-        us[a] = pack2(v.y, -v.x);
-      }
+      for (int a = 0; a < kCorrTile; a++) sample_pair<true>(ri + a * CH + t, u[a], us[a]);
       if (diag) {
 #pragma unroll
-        for (int b = 0; b < kCorrTile; b++) {
-          const float2 w = vi[b] ? to_f2(ri[b * CH + t]) : make_float2(0.f, 0.f);
-          const unsigned long long wxx = pack2(w.x, w.x), wyy = pack2(w.y, w.y);
+        for (int b = 0; b < kCorrTile; b++)
 #pragma unroll
-          for (int a = 0; a <= b; a++) cmac_conj2(acc[a][b], u[a], us[a], wxx, wyy);
-        }
+          for (int a = 0; a <= b; a++) {
+            fma2(P[a][b], u[a], u[b]);
+            fma2(Q[a][b], us[a], u[b]);
+          }
       } else {
 #pragma unroll
         for (int b = 0; b < kCorrTile; b++) {
-          const float2 w = vj[b] ? to_f2(rj[b * CH + t]) : make_float2(0.f, 0.f);
-          const unsigned long long wxx = pack2(w.x, w.x), wyy = pack2(w.y, w.y);
+          unsigned long long w, unused;
+          sample_pair<false>(rj + b * CH + t, w, unused);
 #pragma unroll
-          for (int a = 0; a < kCorrTile; a++) cmac_conj2(acc[a][b], u[a], us[a], wxx, wyy);
+          for (int a = 0; a < kCorrTile; a++) {
+            fma2(P[a][b], u[a], w);
+            fma2(Q[a][b], us[a], w);
+          }
         }
       }
     }
@@ -184,7 +212,8 @@ __global__ void __launch_bounds__(32 * 10) k_correlate_staged(const T* __restric
   for (int a = 0; a < kCorrTile; a++)
 #pragma unroll
     for (int b = 0; b < kCorrTile; b++) {
-      float2 v = unpack2(acc[a][b]);
+      const float2 pp = unpack2(P[a][b]), qq = unpack2(Q[a][b]);
+      float2 v = make_float2(pp.x + pp.y, qq.x - qq.y);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
@@ -280,17 +309,31 @@ __global__ void __launch_bounds__(32 * kCorrWarps) k_correlate_direct(const T* _
   }
 }
 
-template <typename T, int CH, bool VEC16>
+template <typename T, int NT, bool VEC16>
 static cudaError_t launch_staged(const T* y, long long n_samp, int n_ant, int dump_len,
                                  long long m_base, long long n_m, long long first, long long last,
-                                 float2* vis, cudaStream_t st, const int* dump_list, int n_tiles) {
-  const size_t smem = (size_t)kCorrStages * n_ant * CH * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(k_correlate_staged<T, CH, VEC16>,
+                                 float2* vis, cudaStream_t st, const int* dump_list) {
+  const size_t smem = (size_t)2 * kCorrTile * NT * kCorrChunk * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(k_correlate_staged<T, NT, VEC16>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_correlate_staged<T, CH, VEC16><<<(unsigned)n_m, 32 * n_tiles, smem, st>>>(
+  k_correlate_staged<T, NT, VEC16><<<(unsigned)n_m, 32 * NT * (NT + 1) / 2, smem, st>>>(
       y, n_samp, n_ant, dump_len, m_base, first, last, vis, dump_list);
   return cudaGetLastError();
+}
+
+template <typename T, bool VEC16>
+static cudaError_t launch_staged_nt(const T* y, long long n_samp, int n_ant, int dump_len,
+                                    long long m_base, long long n_m, long long first,
+                                    long long last, float2* vis, cudaStream_t st,
+                                    const int* dump_list) {
+  switch ((n_ant + kCorrTile - 1) / kCorrTile) {
+    case 1: return launch_staged<T, 1, VEC16>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis, st, dump_list);
+    case 2: return launch_staged<T, 2, VEC16>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis, st, dump_list);
+    case 3: return launch_staged<T, 3, VEC16>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis, st, dump_list);
+    case 4: return launch_staged<T, 4, VEC16>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis, st, dump_list);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <typename T>
@@ -302,15 +345,14 @@ static cudaError_t correlate_any(const T* y, long long n_samp, int n_ant, int du
   if (n_m <= 0) return cudaSuccess;
   if (n_ant <= kCorrStagedMaxAnt) {
     if (n_m >= (1LL << 31)) return cudaErrorInvalidConfiguration;
-    // 128-sample chunks (at most 48 KB of ring for 16 antennas, so that
-    // several CTAs share an SM); 16-byte copies when every row and dump
-    // starts on a 16-byte boundary of a 16-byte aligned array
+    // 16-byte copies when every row and dump starts on a 16-byte boundary of a
+    // 16-byte aligned array
     constexpr int EPV = 16 / (int)sizeof(T);
     if (n_samp % EPV == 0 && dump_len % EPV == 0 && ((uintptr_t)y & 15) == 0)
-      return launch_staged<T, 128, true>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last,
-                                         vis, st, dump_list, n_tiles);
-    return launch_staged<T, 128, false>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis,
-                                        st, dump_list, n_tiles);
+      return launch_staged_nt<T, true>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis,
+                                       st, dump_list);
+    return launch_staged_nt<T, false>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis,
+                                      st, dump_list);
   }
   const int warps = n_tiles < kCorrWarps ? n_tiles : kCorrWarps;
   dim3 grid((unsigned)n_m, (n_tiles + warps - 1) / warps);

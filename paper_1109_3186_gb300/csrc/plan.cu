@@ -477,11 +477,12 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   p->beam_terms = p->beam_mode == CHIRP_BEAM_TC_BF16 ? 1 : 3;
   p->corr_mode = cfg->corr_mode;
   p->corr_forced = cfg->corr_mode != CHIRP_CORR_AUTO;
-  // AUTO: the tensor cores from 12 antennas up (measured: 12 antennas on par
-  // with the CUDA cores, 36 antennas 1.6x faster; 6 antennas 1.7x slower,
-  // where 128-row MMA tiles carry 12 useful rows)
+  // AUTO: up to 16 antennas the staged FP32 correlator (12 antennas, 2^22
+  // samples, 64 DMs: 6.0 ms against 9.5 ms per search for the tensor cores,
+  // whose 128-row MMA tiles carry 24 useful rows there); above, the tensor
+  // cores (36 antennas: 1.6x faster than the CUDA cores)
   if (p->corr_mode == CHIRP_CORR_AUTO)
-    p->corr_mode = cfg->n_ant >= 12 && corr_tc_supported(cfg->n_ant, cfg->dump_len, 3)
+    p->corr_mode = cfg->n_ant > 16 && corr_tc_supported(cfg->n_ant, cfg->dump_len, 3)
                        ? CHIRP_CORR_TC_3XBF16
                        : CHIRP_CORR_FP32_SIMT;
   if (p->corr_mode != CHIRP_CORR_FP32_SIMT &&

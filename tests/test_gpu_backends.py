@@ -115,7 +115,13 @@ def test_auto_correlation_mode_and_refusals():
         chirp.Plan.from_scenario(sc, corr_mode=chirp.CORR_TC_3XBF16)
     assert ei.value.code == -5
     sc.dump_len = 1024
-    assert chirp.Plan.from_scenario(sc).info["corr_mode"] == chirp.CORR_TC_3XBF16
+    # up to 16 antennas AUTO keeps the (faster) staged FP32 correlator
+    assert chirp.Plan.from_scenario(sc).info["corr_mode"] == chirp.CORR_FP32_SIMT
+    assert chirp.Plan.from_scenario(sc, corr_mode=chirp.CORR_TC_3XBF16).info["corr_mode"] == \
+        chirp.CORR_TC_3XBF16
+    sc20 = skymodel.chirpolator_small(n_samp=1 << 15, n_dm=2, n_ant=20, dm_max=10.0,
+                                      nfft_min=1 << 12, dump_len=1024)
+    assert chirp.Plan.from_scenario(sc20).info["corr_mode"] == chirp.CORR_TC_3XBF16
 
 
 _LONG = {}
