@@ -344,9 +344,13 @@ int chirp_propose_windows(const float* logits, int n_dm, long long n_time, int w
 /* Returns the milliseconds and launch counts accumulated per stage since the
  * previous call (ms, launches: host arrays of CHIRP_N_STAGES, either may be
  * NULL), resets them, and switches event timing on (enable != 0) or off for
- * later runs.  Timing records one CUDA event pair around every launch on the
- * plan's stream; reading the totals synchronises that stream.  Not a paper
- * operation: instrumentation for the roofline report.  Errors: CHIRP_EINVAL. */
+ * later runs: enable = 1 times every stage; CHIRP_TIMING_SELECT | mask times
+ * only the stages whose bit (1 << CHIRP_STAGE_*) is set in mask.  Timing
+ * records one CUDA event pair around every timed launch on the plan's stream
+ * (a few microseconds each); reading the totals synchronises that stream.
+ * Not a paper operation: instrumentation for the roofline report.
+ * Errors: CHIRP_EINVAL. */
+#define CHIRP_TIMING_SELECT 0x40000000
 int chirp_stage_timing(chirp_plan* plan, int enable, double* ms, long long* launches);
 
 /* Allocation-free dedispersion of one trial DM.  No counterpart in the

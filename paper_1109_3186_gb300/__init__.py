@@ -36,6 +36,7 @@ BEAM_AUTO, BEAM_FP32_SIMT, BEAM_TC_3XBF16, BEAM_VIS, BEAM_TC_BF16, BEAM_VIS_BF16
 IN_C64, IN_CI8 = 0, 1
 CORR_AUTO, CORR_FP32_SIMT, CORR_TC_3XBF16, CORR_TC_BF16 = 0, 1, 2, 3
 FLAG_GRAPHS, FLAG_AUTOTUNE, FLAG_LEAN = 1, 2, 4
+TIMING_SELECT = 0x40000000  # chirp_stage_timing: time only the stages in the mask
 CHIRP_OK, CHIRP_EINVAL, CHIRP_ENOMEM, CHIRP_ECUDA, CHIRP_ETIMEOUT, CHIRP_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 K_DM_DEFAULT = 4.148808e15
 
@@ -528,12 +529,18 @@ class Plan:
         _check(load().chirp_incoherent_run(self._h, vp, vl, sp_, dp_, dl))
         return D_out
 
-    def stage_timing(self, enable: bool):
+    def stage_timing(self, enable, stages=None):
         """Per-stage device ms and launch counts since the last call; switches
-        event timing on or off for later runs (synchronises the stream)."""
+        event timing on or off for later runs (synchronises the stream).
+        stages: names from STAGES to time (None: every stage)."""
         ms = (ctypes.c_double * len(STAGES))()
         n = (ctypes.c_longlong * len(STAGES))()
-        _check(load().chirp_stage_timing(self._h, int(bool(enable)), ms, n))
+        arg = int(bool(enable))
+        if enable and stages is not None:
+            arg = TIMING_SELECT
+            for k in stages:
+                arg |= 1 << STAGES.index(k)
+        _check(load().chirp_stage_timing(self._h, arg, ms, n))
         return {k: (float(ms[j]), int(n[j])) for j, k in enumerate(STAGES)}
 
 

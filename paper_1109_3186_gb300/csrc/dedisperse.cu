@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256, 4) k_fwd_cols(const void* __restrict__ x,
                                                   float2* __restrict__ spec, int n2, int log2n,
                                                   long long step, int n_ant,
                                                   const float* __restrict__ scale,
-                                                  TwiddlePtrs twp) {
+                                                  TwiddlePtrs twp, long long q0) {
   constexpr int C = 4096 / L;
   constexpr int T = L / 16;
   __shared__ float2 sm[FftTile<L, C>::SLOTS];
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256, 4) k_fwd_cols(const void* __restrict__ x,
   const int s = threadIdx.x % C, jt = threadIdx.x / C;
   const int c = blockIdx.x * C + s;
   const bool act = c < n2;
-  const long long q = blockIdx.y;  // block-major sequence: b * n_ant + a
+  const long long q = q0 + blockIdx.y;  // block-major sequence: b * n_ant + a
   const long long a = q % n_ant, b = q / n_ant;
   const long long nfft = (long long)L * n2;
   const long long base = b * step;
@@ -411,8 +411,12 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ 
 
 cudaError_t launch_forward(const void* x, long long n_samp, int n_ant, const GroupGeom& g,
                            float2* spec, TwiddlePtrs tw, cudaStream_t st, int in_type,
-                           const float* scale) {
-  const long long n_seq = (long long)n_ant * g.n_blk;
+                           const float* scale, long long b0, long long b1) {
+  if (b1 < 0) b1 = g.n_blk;
+  if (b0 < 0 || b0 > b1 || b1 > g.n_blk) return cudaErrorInvalidValue;
+  if (b0 == b1) return cudaSuccess;
+  const long long q0 = b0 * n_ant;
+  const long long n_seq = (long long)n_ant * (b1 - b0);
   if (n_seq > 65535) return cudaErrorInvalidConfiguration;
   {
     const int C = 4096 / g.n1;
@@ -422,10 +426,10 @@ cudaError_t launch_forward(const void* x, long long n_samp, int n_ant, const Gro
   case L:                                                                                      \
     if (in_type == 1)                                                                          \
       k_fwd_cols<L, true><<<grid, 256, 0, st>>>(x, n_samp, spec, g.n2, g.log2n, g.step, n_ant,  \
-                                                scale, tw);                                    \
+                                                scale, tw, q0);                                \
     else                                                                                       \
       k_fwd_cols<L, false><<<grid, 256, 0, st>>>(x, n_samp, spec, g.n2, g.log2n, g.step, n_ant, \
-                                                 scale, tw);                                   \
+                                                 scale, tw, q0);                               \
     break;
       CHIRP_SIZES(X)
 #undef X
@@ -435,9 +439,10 @@ cudaError_t launch_forward(const void* x, long long n_samp, int n_ant, const Gro
   {
     const int C = 4096 / g.n2;
     dim3 grid((g.n1 + C - 1) / C, (unsigned)n_seq);
+    float2* spec_q = spec + q0 * g.nfft;
     switch (g.n2) {
 #define X(L) \
-  case L: k_fwd_rows<L><<<grid, 256, 0, st>>>(spec, g.n1, tw); break;
+  case L: k_fwd_rows<L><<<grid, 256, 0, st>>>(spec_q, g.n1, tw); break;
       CHIRP_SIZES(X)
 #undef X
       default: return cudaErrorInvalidValue;

@@ -52,9 +52,11 @@ cudaError_t launch_build_row_twiddles(float2* rtw, const GroupGeom& g, cudaStrea
 // holds X[k1 + n1 k2] at position k1 * n2 + k2.
 // x: complex64 [n_ant][n_samp] (in_type 0) or complex int8 pairs times
 // scale[a] (in_type 1, scale NULL = 1)
+// Blocks [b0, b1) only (b1 < 0: through the last block): the sequences
+// [b0 n_ant, b1 n_ant), which read samples [b0 step, (b1 - 1) step + nfft).
 cudaError_t launch_forward(const void* x, long long n_samp, int n_ant, const GroupGeom& g,
                            float2* spec, TwiddlePtrs tw, cudaStream_t st, int in_type = 0,
-                           const float* scale = nullptr);
+                           const float* scale = nullptr, long long b0 = 0, long long b1 = -1);
 // G[pos] = k_dm f^2/(f0^2 (f0 + f)) in the spectrum's (transposed) order, FP64
 cudaError_t launch_build_phase_table(double* G, const GroupGeom& g, double f0, double bw,
                                      double k_dm, cudaStream_t st);

@@ -173,10 +173,23 @@ struct chirp_plan {
   std::vector<GraphEntry> graphs;
   void* d_out = nullptr;     // staging for host outputs
   size_t out_bytes = 0;
+  // Host buffers in page-locked memory: the input is copied in time chunks on
+  // copy_stream and the forward transforms follow chunk by chunk; outputs go
+  // back one DM slab at a time while later DMs are searched.
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t io_ev = nullptr;         // search stream -> copy stream ordering
+  std::vector<cudaEvent_t> in_ev;      // chunk k of the input has landed
+  std::vector<long long> in_t1;        // samples [0, in_t1[k]) of every antenna
+  int in_pending = 0;                  // chunks the forward pass has not consumed
+  char* drain_host = nullptr;          // page-locked host output filled per DM
+  const char* drain_dev = nullptr;
+  size_t drain_per_dm = 0;
+  std::vector<char> drained;
   size_t ws_bytes = 0;
   long long ifft_points = 0, valid_samples = 0;
   // optional per-stage event timing (chirp_stage_timing)
   bool timing = false;
+  unsigned timing_mask = 0;  // stages timed: bit CHIRP_STAGE_*
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<int, int>>> ev_marks;  // stage, (start ev, stop ev)
   size_t ev_next = 0;
@@ -255,6 +268,12 @@ void release(chirp_plan* p) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
   cudaFree(p->d_out);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  if (p->copy_stream) {
+    cudaStreamSynchronize(p->copy_stream);
+    cudaStreamDestroy(p->copy_stream);
+  }
+  if (p->io_ev) cudaEventDestroy(p->io_ev);
+  for (cudaEvent_t e : p->in_ev) cudaEventDestroy(e);
 }
 
 // Two-pass FFT split autotuner.  Every split Nfft = n1 * n2 with the row
@@ -340,9 +359,10 @@ cudaError_t autotune_split(chirp_plan* p, Group& g) {
   return cudaSuccess;
 }
 
-// events bracketing one kernel launch of a stage (no-op unless timing is on)
-int mark_begin(chirp_plan* p) {
-  if (!p->timing) return -1;
+// events bracketing one kernel launch of a stage (no-op unless timing is on
+// for that stage)
+int mark_begin(chirp_plan* p, int stage) {
+  if (!p->timing || !((p->timing_mask >> stage) & 1u)) return -1;
   if (p->ev_next + 2 > p->ev_pool.size()) {
     for (int i = 0; i < 256; i++) {
       cudaEvent_t e;
@@ -443,6 +463,8 @@ int chirp_stage_timing(chirp_plan* p, int enable, double* ms, long long* launche
     p->stage_launches[i] = 0;
   }
   p->timing = enable != 0;
+  p->timing_mask = (enable & CHIRP_TIMING_SELECT) ? (unsigned)enable & ((1u << CHIRP_N_STAGES) - 1u)
+                                                  : (1u << CHIRP_N_STAGES) - 1u;
   return CHIRP_OK;
 }
 
@@ -845,20 +867,99 @@ size_t in_elem_bytes(const chirp_plan* p) {
   return p->in_type == CHIRP_IN_CI8 ? 2 : sizeof(float2);
 }
 
-int stage_input(chirp_plan* p, const void* volt, int loc, const void** dx) {
+bool host_pinned(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+constexpr int kInputChunks = 8;
+
+// The copy stream and its events, created on first use.
+int ensure_copy_stream(chirp_plan* p) {
+  if (p->copy_stream) return CHIRP_OK;
+  CK(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&p->io_ev, cudaEventDisableTiming));
+  p->in_ev.assign(kInputChunks, nullptr);
+  for (auto& e : p->in_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return CHIRP_OK;
+}
+
+// Host voltages go to the staging buffer.  chunked: page-locked input is
+// copied in kInputChunks time chunks (all antennas) on the copy stream, and
+// the forward pass (forward_all) waits for each chunk before transforming the
+// blocks it completes; otherwise the search stream waits for the whole input.
+int stage_input(chirp_plan* p, const void* volt, int loc, const void** dx, bool chunked = false) {
+  p->in_pending = 0;
   if (!volt) return fail(CHIRP_EINVAL, "voltage pointer is NULL");
   if (loc == CHIRP_DEVICE) {
     *dx = volt;
     return CHIRP_OK;
   }
   if (loc != CHIRP_HOST) return fail(CHIRP_EINVAL, "bad buffer location");
-  const size_t bytes = (size_t)p->M * p->N * in_elem_bytes(p);
+  const size_t eb = in_elem_bytes(p);
+  const size_t bytes = (size_t)p->M * p->N * eb;
   if (!p->d_x) {
     int rc = dev_alloc(p, (void**)&p->d_x, bytes, "input staging");
     if (rc) return rc;
   }
-  CK(cudaMemcpyAsync(p->d_x, volt, bytes, cudaMemcpyHostToDevice, p->stream));
   *dx = p->d_x;
+  if (!chunked || p->lean || !host_pinned(volt)) {
+    CK(cudaMemcpyAsync(p->d_x, volt, bytes, cudaMemcpyHostToDevice, p->stream));
+    return CHIRP_OK;
+  }
+  int rc = ensure_copy_stream(p);
+  if (rc) return rc;
+  // the staging buffer is free once the search stream's earlier work is done
+  CK(cudaEventRecord(p->io_ev, p->stream));
+  CK(cudaStreamWaitEvent(p->copy_stream, p->io_ev, 0));
+  const long long per = (p->N + kInputChunks - 1) / kInputChunks;
+  p->in_t1.assign(kInputChunks, p->N);
+  for (int k = 0; k < kInputChunks; k++) {
+    const long long t0 = std::min(p->N, k * per), t1 = std::min(p->N, t0 + per);
+    if (t1 > t0)
+      CK(cudaMemcpy2DAsync((char*)p->d_x + t0 * eb, p->N * eb, (const char*)volt + t0 * eb,
+                           p->N * eb, (t1 - t0) * eb, p->M, cudaMemcpyHostToDevice,
+                           p->copy_stream));
+    CK(cudaEventRecord(p->in_ev[k], p->copy_stream));
+    p->in_t1[k] = t1;
+  }
+  p->in_pending = kInputChunks;
+  return CHIRP_OK;
+}
+
+// The search stream waits for whatever input chunks are still in flight.
+int input_wait_all(chirp_plan* p) {
+  if (p->in_pending > 0) CK(cudaStreamWaitEvent(p->stream, p->in_ev[kInputChunks - 1], 0));
+  p->in_pending = 0;
+  return CHIRP_OK;
+}
+
+// Page-locked host output: slabs of whole DMs are copied back on the copy
+// stream as their back-end finishes (drain_dm), the rest at the end.
+int drain_begin(chirp_plan* p, void* user, const void* dev, size_t bytes) {
+  p->drain_host = nullptr;
+  if (!host_pinned(user) || p->dm.empty()) return CHIRP_OK;
+  int rc = ensure_copy_stream(p);
+  if (rc) return rc;
+  p->drain_host = (char*)user;
+  p->drain_dev = (const char*)dev;
+  p->drain_per_dm = bytes / p->dm.size();
+  p->drained.assign(p->dm.size(), 0);
+  return CHIRP_OK;
+}
+
+int drain_dm(chirp_plan* p, int d) {
+  if (!p->drain_host || p->drained[(size_t)d]) return CHIRP_OK;
+  CK(cudaEventRecord(p->io_ev, p->stream));
+  CK(cudaStreamWaitEvent(p->copy_stream, p->io_ev, 0));
+  const size_t off = (size_t)d * p->drain_per_dm;
+  CK(cudaMemcpyAsync(p->drain_host + off, p->drain_dev + off, p->drain_per_dm,
+                     cudaMemcpyDeviceToHost, p->copy_stream));
+  p->drained[(size_t)d] = 1;
   return CHIRP_OK;
 }
 
@@ -882,21 +983,54 @@ int out_buffer(chirp_plan* p, void* user, int loc, size_t bytes, void** dev) {
 }
 
 int finish_out(chirp_plan* p, void* user, int loc, const void* dev, size_t bytes) {
-  if (loc == CHIRP_HOST) {
+  if (loc != CHIRP_HOST) return CHIRP_OK;
+  if (p->drain_host) {
+    for (int d = 0; d < (int)p->dm.size(); d++) {
+      int rc = drain_dm(p, d);
+      if (rc) return rc;
+    }
+    p->drain_host = nullptr;
+    CK(cudaStreamSynchronize(p->copy_stream));
+  } else {
     CK(cudaMemcpyAsync(user, dev, bytes, cudaMemcpyDeviceToHost, p->stream));
-    CK(cudaStreamSynchronize(p->stream));
   }
+  CK(cudaStreamSynchronize(p->stream));
   return CHIRP_OK;
 }
 
 int forward_all(chirp_plan* p, const void* dx) {
   if (p->lean) {  // spectra are formed per group, right before its DMs
+    int rc = input_wait_all(p);
+    if (rc) return rc;
     p->spec_group = -1;
     p->spec_src = dx;
     return CHIRP_OK;
   }
+  if (p->in_pending > 0) {
+    // chunk by chunk: every group transforms the blocks the chunk completes
+    // (block b reads samples [b step, b step + nfft))
+    std::vector<long long> done(p->groups.size(), 0);
+    for (int k = 0; k < kInputChunks; k++) {
+      CK(cudaStreamWaitEvent(p->stream, p->in_ev[k], 0));
+      const long long t1 = p->in_t1[k];
+      for (size_t gi = 0; gi < p->groups.size(); gi++) {
+        Group& g = p->groups[gi];
+        const GroupGeom& G = g.geom;
+        long long ready = G.n_blk;
+        if (t1 < p->N) ready = t1 >= G.nfft ? std::min(G.n_blk, (t1 - G.nfft) / G.step + 1) : 0;
+        if (ready <= done[gi]) continue;
+        int mk = mark_begin(p, CHIRP_STAGE_FORWARD);
+        CK(launch_forward(dx, p->N, p->M, G, g.d_spec, p->tw(), p->stream, p->in_type, p->d_scale,
+                          done[gi], ready));
+        mark_end(p, CHIRP_STAGE_FORWARD, mk);
+        done[gi] = ready;
+      }
+    }
+    p->in_pending = 0;
+    return CHIRP_OK;
+  }
   for (auto& g : p->groups) {
-    int mk = mark_begin(p);
+    int mk = mark_begin(p, CHIRP_STAGE_FORWARD);
     CK(launch_forward(dx, p->N, p->M, g.geom, g.d_spec, p->tw(), p->stream, p->in_type,
                       p->d_scale));
     mark_end(p, CHIRP_STAGE_FORWARD, mk);
@@ -909,7 +1043,7 @@ int forward_all(chirp_plan* p, const void* dx) {
 int ensure_spec(chirp_plan* p, int gi) {
   if (!p->lean || p->spec_group == gi) return CHIRP_OK;
   Group& g = p->groups[gi];
-  int mk = mark_begin(p);
+  int mk = mark_begin(p, CHIRP_STAGE_FORWARD);
   CK(launch_forward(p->spec_src, p->N, p->M, g.geom, g.d_spec, p->tw(), p->stream, p->in_type,
                     p->d_scale));
   mark_end(p, CHIRP_STAGE_FORWARD, mk);
@@ -926,11 +1060,11 @@ int dedisperse_blocks(chirp_plan* p, int d, float2* y, long long b0, long long b
   const long long nq = inverse_chunk_sequences(g.geom, (long long)p->M * g.geom.n_blk);
   for (long long q0 = b0 * p->M; q0 < q_end; q0 += nq) {
     const long long n = std::min(nq, q_end - q0);
-    int mk = mark_begin(p);
+    int mk = mark_begin(p, CHIRP_STAGE_INV_ROWS);
     CK(launch_inverse_rows(g.d_spec, p->d_Z, p->d_H, q0, n, g.geom, p->tw(), g.d_rtw,
                            p->stream));
     mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
-    mk = mark_begin(p);
+    mk = mark_begin(p, CHIRP_STAGE_INV_COLS);
     if (y16)
       CK(launch_inverse_cols_bf16(p->d_Z, y, p->N, p->M, q0, n, g.geom, I.n_hi, I.n_lo, p->tw(),
                                   p->stream));
@@ -944,7 +1078,7 @@ int dedisperse_blocks(chirp_plan* p, int d, float2* y, long long b0, long long b
 
 int chirp_for(chirp_plan* p, int d, int slot = 0) {
   const DmInfo& I = p->dmi[d];
-  int mk = mark_begin(p);
+  int mk = mark_begin(p, CHIRP_STAGE_CHIRP);
   CK(launch_chirp_table(p->groups[I.group].d_G, p->d_H + (size_t)slot * p->h_stride, p->dm[d],
                         p->groups[I.group].geom, p->stream));
   mark_end(p, CHIRP_STAGE_CHIRP, mk);
@@ -1019,7 +1153,7 @@ int backend_dumps(chirp_plan* p, int d, Backend be, long long m0, long long m1, 
   // multiplies a visibility's relative error by up to M, so unless a
   // tensor-core correlation was asked for explicitly it uses FP32 products.
   auto correlate = [&](float2* vis, bool for_beams) -> int {
-    int mk = mark_begin(p);
+    int mk = mark_begin(p, CHIRP_STAGE_CORRELATE);
     if (for_beams && p->beam_mode == CHIRP_BEAM_VIS_BF16)
       CK(launch_correlate_bf16(p->d_y, p->N, p->M, p->L, m0, m1 - m0, m0, last, vis, p->stream));
     else if (p->corr_mode == CHIRP_CORR_FP32_SIMT || (for_beams && !p->corr_forced))
@@ -1037,17 +1171,17 @@ int backend_dumps(chirp_plan* p, int d, Backend be, long long m0, long long m1, 
     int rc = correlate(p->d_V, true);
     if (rc) return rc;
     int mk;
-    mk = mark_begin(p);
+    mk = mark_begin(p, CHIRP_STAGE_BEAMFORM);
     CK(launch_beam_from_vis(p->d_V, p->d_wpair, p->M, p->n_pix, m0, last, out, p->stream));
     mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
   } else if (tc_beams(p)) {
     const long long origin = p->dmi[d].first * p->L;
-    int mk = mark_begin(p);
+    int mk = mark_begin(p, CHIRP_STAGE_BEAMFORM);
     CK(launch_beam_tc(p->d_bimg, p->d_aimg, p->M, p->n_pix, p->L, m0, last, origin, out,
                       p->d_err, p->beam_terms, p->beam_shape, p->stream));
     mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
   } else {
-    int mk = mark_begin(p);
+    int mk = mark_begin(p, CHIRP_STAGE_BEAMFORM);
     CK(launch_beamform_simt(p->d_y, p->N, p->M, p->L, m0, m1 - m0, m0, last, p->d_W, p->n_pix,
                             out, p->stream));
     mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
@@ -1073,20 +1207,21 @@ int full_search_chunked(chirp_plan* p, Backend be, void* dout) {
       const int n = (int)std::min((size_t)p->dm_chunk, dms.size() - c0);
       double dmv[kMaxChirps];
       for (int j = 0; j < n; j++) dmv[j] = p->dm[dms[c0 + j]];
-      int mk = mark_begin(p);
+      int mk = mark_begin(p, CHIRP_STAGE_CHIRP);
       CK(launch_chirp_tables(grp.d_G, p->d_H, p->h_stride, dmv, n, G, p->stream));
       mark_end(p, CHIRP_STAGE_CHIRP, mk);
-      mk = mark_begin(p);
+      mk = mark_begin(p, CHIRP_STAGE_INV_ROWS);
       CK(launch_inverse_rows_multi(grp.d_spec, p->d_Z, (long long)p->z_stride, p->d_H,
                                    p->h_stride, n, nq, G, p->tw(), grp.d_rtw, p->stream));
       mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
       for (int j = 0; j < n; j++) {
         const int d = dms[c0 + j];
         const DmInfo& I = p->dmi[d];
-        mk = mark_begin(p);
+        mk = mark_begin(p, CHIRP_STAGE_INV_COLS);
         CK(column_pass(p, d, be, p->d_Z + (size_t)j * p->z_stride, 0, nq, nullptr));
         mark_end(p, CHIRP_STAGE_INV_COLS, mk);
         int rc = backend_dumps(p, d, be, I.first, I.last + 1, dout);
+        if (!rc) rc = drain_dm(p, d);
         if (rc) return rc;
       }
     }
@@ -1185,22 +1320,23 @@ int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Bac
       rc = dedisperse_blocks(p, d, p->d_y, 0, G.n_blk, fused_image(p, be) ? &img : nullptr,
                              bf16_y(p, be));
       if (!rc) rc = backend_dumps(p, d, be, I.first, I.last + 1, dout);
+      if (!rc) rc = drain_dm(p, d);
       if (rc) return rc;
       continue;
     }
     Group& g = p->groups[I.group];
     const int* blist = p->d_lists + blk_off[d];
     const int* dlist = p->d_lists + dmp_off[d];
-    int mk = mark_begin(p);
+    int mk = mark_begin(p, CHIRP_STAGE_INV_ROWS);
     CK(launch_inverse_rows(g.d_spec, p->d_Z, p->d_H, 0, blk_n[d] * p->M, G, p->tw(), g.d_rtw,
                            p->stream, blist, p->M));
     mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
-    mk = mark_begin(p);
+    mk = mark_begin(p, CHIRP_STAGE_INV_COLS);
     CK(column_pass(p, d, be, p->d_Z, 0, blk_n[d] * p->M, blist));
     mark_end(p, CHIRP_STAGE_INV_COLS, mk);
     if (be == kCorrelate || vis_beams(p)) {
       float2* vout = be == kCorrelate ? (float2*)dout + (size_t)d * p->n_dump * p->n_pair : p->d_V;
-      mk = mark_begin(p);
+      mk = mark_begin(p, CHIRP_STAGE_CORRELATE);
       if (bf16_y(p, be))
         CK(launch_correlate_bf16(p->d_y, p->N, p->M, p->L, 0, dmp_n[d], I.first, I.last, vout,
                                  p->stream, dlist));
@@ -1209,7 +1345,7 @@ int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Bac
                             p->stream, dlist));
       mark_end(p, CHIRP_STAGE_CORRELATE, mk);
       if (be == kBeams) {
-        mk = mark_begin(p);
+        mk = mark_begin(p, CHIRP_STAGE_BEAMFORM);
         CK(launch_beam_from_vis(p->d_V, p->d_wpair, p->M, p->n_pix, I.first, I.last,
                                 (float*)dout + (size_t)d * p->n_dump * p->n_pix, p->stream, dlist,
                                 dmp_n[d]));
@@ -1317,15 +1453,15 @@ int truedelay_search(chirp_plan* p, const void* dx, float* dout, size_t bytes) {
       const int nb = (int)std::min(nb_max, G.n_blk - b0);
       for (int p0 = 0; p0 < p->n_pix; p0 += np_max) {
         const int np = std::min(np_max, p->n_pix - p0);
-        int mk = mark_begin(p);
+        int mk = mark_begin(p, CHIRP_STAGE_TD_SPECTRA);
         CK(launch_td_spectra(g.d_spec, p->d_tdY, b0, nb, np, p0, p->M, G, g.d_tdph, g.d_tdrot,
                              p->stream));
         mark_end(p, CHIRP_STAGE_TD_SPECTRA, mk);
-        mk = mark_begin(p);
+        mk = mark_begin(p, CHIRP_STAGE_INV_ROWS);
         CK(launch_inverse_rows(p->d_tdY, p->d_tdZ, p->d_H, 0, (long long)nb * np, G, p->tw(),
                                g.d_rtw, p->stream));
         mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
-        mk = mark_begin(p);
+        mk = mark_begin(p, CHIRP_STAGE_INV_COLS);
         CK(launch_inverse_cols_pow(p->d_tdZ, out, p->N, b0, nb, np, p0, p->n_pix, G, I.n_hi,
                                    I.n_lo, p->L, I.first * p->L, (I.last + 1) * p->L, p->tw(),
                                    p->stream));
@@ -1381,22 +1517,28 @@ int run_search(chirp_plan* p, const void* volt, int volt_loc, const unsigned cha
   g_err[0] = 0;
   if (!p) return fail(CHIRP_EINVAL, "plan is NULL");
   if (be == kBeams && p->n_pix <= 0) return fail(CHIRP_EUNSUPPORTED, "plan was created without pixels");
-  const void* dx;
-  int rc = stage_input(p, volt, volt_loc, &dx);
-  if (rc) return rc;
+  p->drain_host = nullptr;
   if (be == kCorrelate || !tc_beams(p)) {
-    rc = ensure_y(p);
+    int rc = ensure_y(p);
     if (rc) return rc;
   }
   const size_t per_dm = be == kCorrelate ? (size_t)p->n_dump * p->n_pair : (size_t)p->n_dump * p->n_pix;
   const size_t bytes = per_dm * p->dm.size() * (be == kCorrelate ? sizeof(float2) : sizeof(float));
   void* dout;
-  rc = out_buffer(p, out_user, out_loc, bytes, &dout);
+  int rc = out_buffer(p, out_user, out_loc, bytes, &dout);
   if (rc) return rc;
+  const void* dx;
+  rc = stage_input(p, volt, volt_loc, &dx, true);
+  if (rc) return rc;
+  if (out_loc == CHIRP_HOST && !mask) {
+    rc = drain_begin(p, out_user, dout, bytes);
+    if (rc) return rc;
+  }
   if (p->use_graphs && !mask && volt_loc == CHIRP_DEVICE && out_loc == CHIRP_DEVICE)
     rc = graph_search(p, dx, be, dout, bytes);
   else
     rc = enqueue_search(p, dx, mask, be, dout, bytes);
+  if (!rc) rc = input_wait_all(p);
   if (rc) return rc;
   rc = finish_out(p, out_user, out_loc, dout, bytes);
   if (rc) return rc;
@@ -1494,7 +1636,7 @@ int chirp_incoherent_run(chirp_plan* p, const void* volt, int volt_loc, float* S
     dD = p->d_fb_D;
   }
   float* dS = (out_loc == CHIRP_DEVICE && S_out) ? S_out : p->d_fb_S;
-  int mk = mark_begin(p);
+  int mk = mark_begin(p, CHIRP_STAGE_INCOHERENT);
   // the filterbank transforms a copy of the voltages in the dedispersion scratch
   if (p->in_type == CHIRP_IN_CI8)
     CK(launch_unpack_ci8(dx, p->d_scale, p->M, p->N, p->d_y, p->stream));
@@ -1585,7 +1727,7 @@ int chirp_detect(chirp_plan* p, const float* pow, int pow_loc, float snr_min,
   const long long* dfirst = p->d_first_last;
   const long long* dlast = p->d_first_last + n_dm;
   long long* d_total = p->d_det_offsets + std::max(1LL, nc);
-  int mk = mark_begin(p);
+  int mk = mark_begin(p, CHIRP_STAGE_DETECT);
   CK(launch_detect(dP, n_dm, p->n_dump, p->n_pix, dfirst, dlast, snr_min, p->d_det_stats,
                    p->d_det_counts, p->d_det_offsets, d_total, dc, max_cand, p->stream));
   mark_end(p, CHIRP_STAGE_DETECT, mk);
