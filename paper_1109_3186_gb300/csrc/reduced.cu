@@ -36,21 +36,23 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols_y16(const float2* __restric
                                : q0 + blockIdx.y;  // block-major sequence; Z holds the launch
   const long long a = q % n_ant, b = q / n_ant;
   const long long nfft = (long long)L * n2;
-  const float2* src = Z + (long long)blockIdx.y * nfft;
+  // positions inside a block, (jt + k T) n2 + c < nfft <= 2^24, are 32-bit
+  const float2* src = Z + (long long)blockIdx.y * nfft + c;
   float2 v[16];
 #pragma unroll
-  for (int k = 0; k < 16; k++)
-    v[k] = act ? src[(long long)(jt + k * T) * n2 + c] : make_float2(0.f, 0.f);
+  for (int k = 0; k < 16; k++) v[k] = act ? src[(jt + k * T) * n2] : make_float2(0.f, 0.f);
   fft_core<L, C, false, true>(v, sm, s, jt, tw);
   if (!act) return;
   const long long base = b * step;
   const long long lo_b = (b == 0) ? n_hi : n_hi_max;
   const long long hi_b = (b == n_blk - 1) ? (n_samp - n_lo - base) : (n_hi_max + step);
-  __nv_bfloat162* ya = y16 + a * n_samp;
+  const int lo32 = (int)(lo_b < 0 ? 0 : (lo_b > nfft ? nfft : lo_b));
+  const int hi32 = (int)(hi_b < 0 ? 0 : (hi_b > nfft ? nfft : hi_b));
+  __nv_bfloat162* yb = y16 + a * n_samp + base;
 #pragma unroll
   for (int k = 0; k < 16; k++) {
-    const long long n = (long long)(jt + k * T) * n2 + c;
-    if (n >= lo_b && n < hi_b) ya[base + n] = __floats2bfloat162_rn(v[k].x, v[k].y);
+    const int n = (jt + k * T) * n2 + c;
+    if (n >= lo32 && n < hi32) yb[n] = __floats2bfloat162_rn(v[k].x, v[k].y);
   }
 }
 
