@@ -432,36 +432,137 @@ def extra_forms(sc, plan, xd, stream, args):
                         "pipeline_speedup_vs_full_grid": ms_full / pipeline,
                         "mask": "seeded runs of dumps per DM (6 runs of 1/18 of the valid dumps), "
                                 "not a trained proposer's output"}
-    # the operating point where the trained proposer keeps >= 99 % of the
-    # full-grid detections (held-out, test setup): ~87 % of the cells; here a
-    # seeded mask of that fraction (two gaps of 6.5 % of the valid dumps per DM)
-    cells99 = np.zeros_like(cells)
-    for d in range(n_dm):
-        n_valid = max(0, last[d] - first[d] + 1)
-        if n_valid <= 0:
-            continue
-        cells99[d, first[d]:last[d] + 1] = 1
-        gap = max(1, int(round(0.065 * n_valid)))
-        for _ in range(2):
-            m0 = first[d] + int(rng.integers(0, max(1, n_valid - gap)))
-            cells99[d, m0:m0 + gap] = 0
-    frac99 = float(cells99.sum()) / max(1, int(np.sum(np.maximum(0, last - first + 1))))
-    p16 = chirp.Plan.from_scenario(sc, beam_mode=chirp.BEAM_VIS_BF16, stream=stream)
-    ms_sel16_99 = timed(lambda: p16.chimageator_selective(xd, cells99, P), 3)
-    p16.close()
-    pipe99 = out["incoherent"]["ms"] + out["proposer_inference"]["ms"] + ms_sel16_99
-    out["selective_99pct_recall"] = {
-        "cell_fraction": frac99, "incoherent_proposer_selective_reduced_ms": pipe99,
-        "reduced_precision_form": "vis_bf16",
-        "speedup_vs_full_grid": ms_full / pipe99,
-        "mask": "seeded, the cell fraction the trained proposer needs for >= 99 % recall of the "
-                "full-grid detections on held-out segments (6-antenna test setup)"}
     del P
+    try:
+        out["learned_99pct_recall"] = learned_leg(sc, plan, xd, stream, ms_full, timed)
+    except Exception as exc:  # an auxiliary leg: record, do not lose the line
+        out["learned_99pct_recall"] = {"error": str(exc)}
+    torch.cuda.empty_cache()
     try:
         out["batch"] = batch_leg(args)
     except Exception as exc:  # an auxiliary leg: record, do not lose the line
         out["batch"] = {"error": str(exc)}
     return out
+
+
+def learned_leg(sc, plan, xd, stream, full_ms, timed):
+    """The learned form on this workload's array class, with the trained
+    network's own proposals.  The proposer (61.6k parameters, FP32, the
+    library's training kernels) is trained on 768 seeded 2^21-sample segments
+    of the same array size, band, DM grid and dump length (0-4 bursts: DM
+    uniform over the grid, width 20 us-1 ms, S/N 6-30, random beam
+    direction; a narrowband tone in 10 %; drawn on the device).  Its
+    threshold is the highest of a sweep that keeps >= 99 % of the bursts the
+    full-grid search detects (candidates >= 7 sigma within one trial DM and
+    two dumps) on 128 calibration segments; recall and cell fraction are then
+    measured on 128 held-out segments.  On this step's voltages the trained
+    network proposes the cells, the reduced-precision selective search runs
+    them, and the pipeline (incoherent search + proposer + selective search)
+    is timed against the full FP32 grid; its recall there is of the bursts
+    the full grid detects in this observation."""
+    import torch
+    import paper_1109_3186_gb300 as chirp
+    from paper_1109_3186_gb300 import propose as pp
+    n_dm = len(sc.dms)
+    setup = pp.ProposalSetup(n_ant=sc.n_ant, max_baseline_m=6000.0, f0=sc.f0, bw=sc.bw,
+                             n_samp=1 << 21, dm_max=float(sc.dms.max()), n_dm=n_dm,
+                             nfft_min=sc.nfft_min, dump_len=sc.dump_len, n_side=4,
+                             fb_chan=32, fb_int=16)
+    n_train, n_cal, n_test = 768, 128, 128
+    t0 = time.perf_counter()
+    prop = pp.Proposer(setup, stream=stream)
+    feats, ys = [], []
+    for seed in range(30000, 30000 + n_train):
+        x, pulses = pp.segment_device(setup, seed)
+        feats.append(prop.features(x))
+        ys.append(pp.labels(setup, pulses))
+    del x
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = prop.train(feats, ys, steps=1500, batch=16, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del feats, ys
+    # calibration and held-out segments: features and full-grid detections
+    P = torch.empty((n_dm, prop.plan.n_dump, prop.plan.n_pix), dtype=torch.float32, device="cuda")
+    ev_feats, ev_truth = [], []
+    for seed in range(40000, 40000 + n_cal + n_test):
+        x, pulses = pp.segment_device(setup, seed)
+        ev_feats.append(prop.features(x))
+        prop.plan.chimageator(x, P)
+        c = prop.plan.detect(P, 7.0)
+        ev_truth.append((pulses, set(zip(c["dm"].tolist(), c["dump"].tolist()))))
+    del x, P
+    ddm = float(setup.dms[1] - setup.dms[0])
+    span = setup.win * setup.t_fb
+
+    def sweep(lo, hi, thr):
+        cl = [pp.cells_of(prop.propose(ev_feats[i], thr), setup.n_samp, setup.dump_len, span)
+              for i in range(lo, hi)]
+        f, n = pp.recall(ev_truth[lo:hi], cl, ddm, setup.dump_len)
+        return f, n, float(np.mean([c.mean() for c in cl]))
+
+    curve, thr99 = [], None
+    for thr in (2.0, 1.0, 0.0, -1.0, -2.0, -3.0, -4.0, -5.0, -6.0, -8.0, -10.0, -14.0):
+        fc, nc, _ = sweep(0, n_cal, thr)
+        fh, nh, frh = sweep(n_cal, n_cal + n_test, thr)
+        curve.append({"threshold": thr, "calibration": "%d/%d" % (fc, nc),
+                      "held_out": "%d/%d" % (fh, nh), "held_out_cell_fraction": frh})
+        if thr99 is None and nc and fc >= 0.99 * nc:
+            thr99 = thr
+    if thr99 is None:
+        thr99 = curve[-1]["threshold"]
+    fh, nh, frh = sweep(n_cal, n_cal + n_test, thr99)
+    # this step's voltages: the trained network's own proposals
+    pfb = chirp.Plan.from_scenario(sc, beam_mode=chirp.BEAM_VIS, stream=stream, fb_chan=32,
+                                   fb_int=16, fb_dm=sc.dms)
+    T_fb = pfb.info["fb_samples"]
+    net = chirp.PropNet(n_dm, 64, 9, 5, 1, T_fb, stream=stream)
+    net.set_params(prop.net.params())
+    D = torch.empty((n_dm, T_fb), dtype=torch.float32, device="cuda")
+    xz = torch.empty_like(D)
+    z = torch.empty((1, n_dm, T_fb), dtype=torch.float32, device="cuda")
+    mask = torch.empty((n_dm, (T_fb + setup.win - 1) // setup.win), dtype=torch.int32,
+                       device="cuda")
+
+    def propose_step():
+        pfb.incoherent(xd, D)
+        net.normalize(D, xz)
+        net.forward(xz[None], z)
+        net.propose(z[0], setup.win, thr99, mask)
+    ms_prop = timed(propose_step, 5)
+    cells = pp.cells_of(mask.cpu().numpy().astype(np.uint8), sc.n_samp, sc.dump_len, span)
+    first, last = plan.dump_range()
+    valid = np.zeros_like(cells, dtype=bool)
+    for d in range(n_dm):
+        valid[d, first[d]:last[d] + 1] = True
+    frac_obs = float(cells[valid].sum()) / max(1, int(valid.sum()))
+    Pf = torch.empty((n_dm, plan.n_dump, plan.n_pix), dtype=torch.float32, device="cuda")
+    plan.chimageator(xd, Pf)
+    c = plan.detect(Pf, 7.0)
+    f_obs, n_obs = pp.recall([(sc.pulses, set(zip(c["dm"].tolist(), c["dump"].tolist())))],
+                             [cells], float(sc.dms[1] - sc.dms[0]), sc.dump_len)
+    p16 = chirp.Plan.from_scenario(sc, beam_mode=chirp.BEAM_VIS_BF16, stream=stream)
+    ms_sel16 = timed(lambda: p16.chimageator_selective(xd, cells, Pf), 3)
+    ms_full16 = timed(lambda: p16.chimageator(xd, Pf), 3)
+    p16.close()
+    pfb.close()
+    del Pf
+    pipe = ms_prop + ms_sel16
+    return {"trained_on": "%d seeded 2^21-sample segments of this array class (12 antennas within "
+                          "6 km, 32 MHz, 64 DMs 0-300, dumps 4096), drawn on the device" % n_train,
+            "params": int(net.n_params), "precision": "f32", "train_steps": 1500,
+            "final_loss": float(np.mean(losses[-50:])), "first_loss": float(losses[0]),
+            "data_s": t_data, "train_s": t_train, "threshold": thr99,
+            "held_out_recall": "%d/%d" % (fh, nh), "held_out_cell_fraction": frh,
+            "curve": curve,
+            "observation_cell_fraction": frac_obs,
+            "observation_recall": "%d/%d" % (f_obs, n_obs),
+            "incoherent_proposer_ms": ms_prop, "selective_reduced_ms": ms_sel16,
+            "incoherent_proposer_selective_reduced_ms": pipe,
+            "full_grid_fp32_ms": full_ms, "full_grid_reduced_ms": ms_full16,
+            "speedup_vs_full_fp32": full_ms / pipe, "speedup_vs_full_reduced": ms_full16 / pipe,
+            "reduced_precision_form": "vis_bf16"}
 
 
 def batch_leg(args):

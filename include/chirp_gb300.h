@@ -389,13 +389,14 @@ int chirp_plan_status(chirp_plan* plan);
 
 /* Selective searches: as chirpolator_run / chimageator_run but only for the
  * (DM, dump) cells whose byte in cell_mask (HOST uint8 [n_dm][n_dump]) is
- * nonzero -- e.g. the cells proposed by the learned proposer.  Only the
- * overlap-save blocks that own a selected dump are inverse transformed and the
- * back-end runs only on selected dumps; every other output cell is zero.  When
- * the selection covers at least 80 % of the valid cells the whole grid is
- * searched (the full search's multi-DM passes are faster there) and the
- * unselected cells are cleared.  The selected cells hold exactly what the
- * full search computes there.  Errors: as the full searches. */
+ * nonzero -- e.g. the cells proposed by the learned proposer.  The back-end
+ * runs only on selected dumps; every other output cell is zero.  Per
+ * FFT-length group, when the selected DMs need at least 85 % of their
+ * (DM, overlap-save block) pairs the group's inverse transforms run in full
+ * with the multi-DM row pass (one spectrum read for up to 4 DMs); otherwise
+ * only the blocks that own a selected dump are inverse transformed, DM by
+ * DM.  The selected cells hold exactly what the full search computes there.
+ * Errors: as the full searches. */
 int chirpolator_run_selective(chirp_plan* plan, const void* volt, int volt_loc,
                               const unsigned char* cell_mask, void* vis_out, int vis_loc);
 int chimageator_run_selective(chirp_plan* plan, const void* volt, int volt_loc,

@@ -374,24 +374,6 @@ cudaError_t launch_correlate_bf16(const void* y16, long long n_samp, int n_ant, 
                        n_m, first, last, vis, st, dump_list);
 }
 
-// ------------------------------------------------------------------ clear cells
-// out[cell][0 .. row_floats) = 0 for the listed cells (index d n_dump + m).
-__global__ void k_zero_cells(float* __restrict__ out, const int* __restrict__ cells,
-                             long long n_cells, int row_floats) {
-  for (long long c = blockIdx.x; c < n_cells; c += gridDim.x) {
-    float* row = out + (long long)cells[c] * row_floats;
-    for (int i = threadIdx.x; i < row_floats; i += blockDim.x) row[i] = 0.f;
-  }
-}
-
-cudaError_t launch_zero_cells(float* out, const int* cells, long long n_cells, int row_floats,
-                              cudaStream_t st) {
-  if (n_cells <= 0) return cudaSuccess;
-  const unsigned grid = (unsigned)(n_cells < 4096 ? n_cells : 4096);
-  k_zero_cells<<<grid, 256, 0, st>>>(out, cells, n_cells, row_floats);
-  return cudaGetLastError();
-}
-
 // ------------------------------------------------------------------ beams from visibilities
 // Exact identity: sum_t |sum_a W_pa y_a(t)|^2 = sum_{a,b} W_pa W_pb^* V_ab with
 // V_ab = sum_t y_a y_b^* (the correlator's output), i.e. for the packed upper

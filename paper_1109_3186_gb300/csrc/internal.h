@@ -145,9 +145,6 @@ cudaError_t launch_cpi_tc_image(const float2* X, uint8_t* bimg, const uint8_t* a
                                 int n_pix, float* E, int* err, cudaStream_t st);
 
 // ---- back-ends (backends.cu) ----
-// Clears the rows (row_floats floats each) of the listed cells (d n_dump + m).
-cudaError_t launch_zero_cells(float* out, const int* cells, long long n_cells, int row_floats,
-                              cudaStream_t st);
 // dumps m_base .. m_base + n_m - 1, or dump_list[0 .. n_m) when dump_list is a
 // device array (zeros for dumps outside [first, last])
 cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int dump_len,

@@ -1189,15 +1189,68 @@ int backend_dumps(chirp_plan* p, int d, Backend be, long long m0, long long m1, 
   return CHIRP_OK;
 }
 
+// A selection of (DM, dump) cells: per DM the device list of its selected
+// valid dumps (dlist + off[d], n[d] entries) and its mask row.
+struct Selection {
+  const unsigned char* mask = nullptr;
+  const int* d_lists = nullptr;
+  const long long* off = nullptr;
+  const long long* n = nullptr;
+  const char* dense_group = nullptr;  // groups searched with the multi-DM inverse
+};
+
+// The back-end of DM d over its selected dumps only: the visibility paths take
+// the dump list, the other beam modes run over runs of consecutive dumps.
+int selected_backend(chirp_plan* p, int d, Backend be, void* dout, const Selection& sel) {
+  const DmInfo& I = p->dmi[d];
+  const int* dlist = sel.d_lists + sel.off[d];
+  const long long n_sel = sel.n[d];
+  if (be == kCorrelate || vis_beams(p)) {
+    float2* vout = be == kCorrelate ? (float2*)dout + (size_t)d * p->n_dump * p->n_pair : p->d_V;
+    int mk = mark_begin(p, CHIRP_STAGE_CORRELATE);
+    if (bf16_y(p, be))
+      CK(launch_correlate_bf16(p->d_y, p->N, p->M, p->L, 0, n_sel, I.first, I.last, vout,
+                               p->stream, dlist));
+    else
+      CK(launch_correlate(p->d_y, p->N, p->M, p->L, 0, n_sel, I.first, I.last, vout, p->stream,
+                          dlist));
+    mark_end(p, CHIRP_STAGE_CORRELATE, mk);
+    if (be == kBeams) {
+      mk = mark_begin(p, CHIRP_STAGE_BEAMFORM);
+      CK(launch_beam_from_vis(p->d_V, p->d_wpair, p->M, p->n_pix, I.first, I.last,
+                              (float*)dout + (size_t)d * p->n_dump * p->n_pix, p->stream, dlist,
+                              n_sel));
+      mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
+    }
+    return CHIRP_OK;
+  }
+  const unsigned char* row = sel.mask + (size_t)d * p->n_dump;
+  for (long long m = I.first; m <= I.last;) {
+    if (!row[m]) {
+      m++;
+      continue;
+    }
+    long long e = m;
+    while (e <= I.last && row[e]) e++;
+    int rc = backend_dumps(p, d, be, m, e, dout);
+    if (rc) return rc;
+    m = e;
+  }
+  return CHIRP_OK;
+}
+
 // The whole search with the row passes of up to dm_chunk DMs of a group in
 // one launch: per chunk the chirp tables, one multi-DM row pass, then per
-// DM the column pass (voltages or the beam image) and the back-end.
-int full_search_chunked(chirp_plan* p, Backend be, void* dout) {
+// DM the column pass (voltages or the beam image) and the back-end.  With a
+// selection: only the groups it marks dense, only their DMs with a selected
+// dump, and the back-end over the selected dumps.
+int full_search_chunked(chirp_plan* p, Backend be, void* dout, const Selection* sel = nullptr) {
   for (size_t gi = 0; gi < p->groups.size(); gi++) {
     Group& grp = p->groups[gi];
+    if (sel && !sel->dense_group[gi]) continue;
     std::vector<int> dms;
     for (int d : grp.dms)
-      if (p->dmi[d].last >= p->dmi[d].first) dms.push_back(d);
+      if (p->dmi[d].last >= p->dmi[d].first && (!sel || sel->n[d] > 0)) dms.push_back(d);
     if (dms.empty()) continue;
     int rc0 = ensure_spec(p, (int)gi);
     if (rc0) return rc0;
@@ -1220,7 +1273,8 @@ int full_search_chunked(chirp_plan* p, Backend be, void* dout) {
         mk = mark_begin(p, CHIRP_STAGE_INV_COLS);
         CK(column_pass(p, d, be, p->d_Z + (size_t)j * p->z_stride, 0, nq, nullptr));
         mark_end(p, CHIRP_STAGE_INV_COLS, mk);
-        int rc = backend_dumps(p, d, be, I.first, I.last + 1, dout);
+        int rc = sel ? selected_backend(p, d, be, dout, *sel)
+                     : backend_dumps(p, d, be, I.first, I.last + 1, dout);
         if (!rc) rc = drain_dm(p, d);
         if (rc) return rc;
       }
@@ -1230,44 +1284,29 @@ int full_search_chunked(chirp_plan* p, Backend be, void* dout) {
 }
 
 // The whole search, or (mask != NULL) only the (DM, dump) cells whose mask
-// byte is nonzero: for each DM the blocks owning a selected dump are inverse
-// transformed (runs of consecutive blocks per launch) and the back-end runs on
-// runs of consecutive selected dumps.  Outputs are zero elsewhere.
+// byte is nonzero; outputs are zero elsewhere.  A selective search lists, per
+// DM, its selected valid dumps and the blocks that own them.  An FFT-length
+// group whose DMs need at least kDenseBlocks of their (DM, block) pairs runs
+// the full multi-DM inverse and restricts only the back-end to the listed
+// dumps; the other groups inverse-transform, per DM, just the listed blocks
+// (runs of block indices per launch).  Per block the per-DM form costs ~1.2x
+// in the row pass and ~2x in the chirp tables (the multi-DM forms read each
+// spectrum and phase table once for up to 4 DMs), so it wins below ~85 %.
+constexpr double kDenseBlocks = 0.85;
+
 int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Backend be,
                    void* dout, size_t bytes) {
   int rc = forward_all(p, dx);
   if (rc) return rc;
   CK(cudaMemsetAsync(dout, 0, bytes, p->stream));  // invalid / unselected cells stay zero
-  // Selective: per DM, the list of blocks owning a selected dump and the list
-  // of selected valid dumps, uploaded together; each DM then costs one
-  // inverse launch pair over its listed blocks and (visibility path) one
-  // back-end launch pair over its listed dumps.
+  if (!mask && p->dm_chunk > 1) return full_search_chunked(p, be, dout);
   std::vector<int> lists;
   std::vector<long long> blk_off(p->dm.size(), 0), blk_n(p->dm.size(), 0);
   std::vector<long long> dmp_off(p->dm.size(), 0), dmp_n(p->dm.size(), 0);
-  // A selection covering at least 80 % of the valid cells runs the full
-  // search (its multi-DM row passes beat per-DM block lists there) and then
-  // clears the unselected valid cells, listed as d n_dump + m.
-  bool dense = false;
-  if (mask && p->dm_chunk > 1 && (long long)p->dm.size() * p->n_dump < (1LL << 31)) {
-    long long n_valid = 0, n_sel = 0;
-    for (int d = 0; d < (int)p->dm.size(); d++) {
-      const DmInfo& I = p->dmi[d];
-      const unsigned char* row = mask + (size_t)d * p->n_dump;
-      for (long long m = I.first; m <= I.last; m++) n_sel += row[m] != 0;
-      if (I.last >= I.first) n_valid += I.last - I.first + 1;
-    }
-    dense = n_valid > 0 && n_sel * 5 >= n_valid * 4;
-    if (dense)
-      for (int d = 0; d < (int)p->dm.size(); d++) {
-        const DmInfo& I = p->dmi[d];
-        const unsigned char* row = mask + (size_t)d * p->n_dump;
-        for (long long m = I.first; m <= I.last; m++)
-          if (!row[m]) lists.push_back((int)((long long)d * p->n_dump + m));
-      }
-  }
-  if (mask && !dense) {
+  std::vector<char> dense(p->groups.size(), 0);
+  if (mask) {
     std::vector<unsigned char> need;
+    std::vector<long long> g_need(p->groups.size(), 0), g_all(p->groups.size(), 0);
     for (int d = 0; d < (int)p->dm.size(); d++) {
       const DmInfo& I = p->dmi[d];
       const GroupGeom& G = p->groups[I.group].geom;
@@ -1285,87 +1324,68 @@ int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Bac
       for (long long b = 0; b < G.n_blk; b++)
         if (need[(size_t)b]) lists.push_back((int)b);
       blk_n[d] = (long long)lists.size() - blk_off[d];
+      if (dmp_n[d] > 0) {
+        g_need[I.group] += blk_n[d];
+        g_all[I.group] += G.n_blk;
+      }
     }
-  }
-  if (!lists.empty()) {
-    if (p->lists_cap < lists.size()) {
-      cudaFree(p->d_lists);
-      p->d_lists = nullptr;
-      p->lists_cap = 0;
-      rc = dev_alloc(p, (void**)&p->d_lists, lists.size() * sizeof(int), "index lists");
-      if (rc) return rc;
-      p->lists_cap = lists.size();
+    if (p->dm_chunk > 1)
+      for (size_t gi = 0; gi < p->groups.size(); gi++)
+        dense[gi] = g_all[gi] > 0 && (double)g_need[gi] >= kDenseBlocks * (double)g_all[gi];
+    if (!lists.empty()) {
+      if (p->lists_cap < lists.size()) {
+        cudaFree(p->d_lists);
+        p->d_lists = nullptr;
+        p->lists_cap = 0;
+        rc = dev_alloc(p, (void**)&p->d_lists, lists.size() * sizeof(int), "index lists");
+        if (rc) return rc;
+        p->lists_cap = lists.size();
+      }
+      CK(cudaMemcpyAsync(p->d_lists, lists.data(), lists.size() * sizeof(int),
+                         cudaMemcpyHostToDevice, p->stream));
     }
-    CK(cudaMemcpyAsync(p->d_lists, lists.data(), lists.size() * sizeof(int),
-                       cudaMemcpyHostToDevice, p->stream));
-  }
-  if (dense) {
-    rc = full_search_chunked(p, be, dout);
+    Selection sel;
+    sel.mask = mask;
+    sel.d_lists = p->d_lists;
+    sel.off = dmp_off.data();
+    sel.n = dmp_n.data();
+    sel.dense_group = dense.data();
+    rc = full_search_chunked(p, be, dout, &sel);
     if (rc) return rc;
-    const int row_floats = be == kCorrelate ? 2 * p->n_pair : p->n_pix;
-    CK(launch_zero_cells((float*)dout, p->d_lists, (long long)lists.size(), row_floats, p->stream));
+    for (int d = 0; d < (int)p->dm.size(); d++) {
+      const DmInfo& I = p->dmi[d];
+      if (I.last < I.first || dense[I.group] || dmp_n[d] == 0) continue;
+      const GroupGeom& G = p->groups[I.group].geom;
+      Group& g = p->groups[I.group];
+      rc = ensure_spec(p, I.group);
+      if (!rc) rc = chirp_for(p, d);
+      if (rc) return rc;
+      const int* blist = p->d_lists + blk_off[d];
+      int mk = mark_begin(p, CHIRP_STAGE_INV_ROWS);
+      CK(launch_inverse_rows(g.d_spec, p->d_Z, p->d_H, 0, blk_n[d] * p->M, G, p->tw(), g.d_rtw,
+                             p->stream, blist, p->M));
+      mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
+      mk = mark_begin(p, CHIRP_STAGE_INV_COLS);
+      CK(column_pass(p, d, be, p->d_Z, 0, blk_n[d] * p->M, blist));
+      mark_end(p, CHIRP_STAGE_INV_COLS, mk);
+      rc = selected_backend(p, d, be, dout, sel);
+      if (rc) return rc;
+    }
     return CHIRP_OK;
   }
-  if (!mask && p->dm_chunk > 1) return full_search_chunked(p, be, dout);
   for (int d = 0; d < (int)p->dm.size(); d++) {
     const DmInfo& I = p->dmi[d];
     if (I.last < I.first) continue;
     const GroupGeom& G = p->groups[I.group].geom;
-    if (mask && dmp_n[d] == 0) continue;
     rc = ensure_spec(p, I.group);
     if (!rc) rc = chirp_for(p, d);
     if (rc) return rc;
-    if (!mask) {
-      const BeamImageOut img = fused_image(p, be) ? beam_image_for(p, d) : BeamImageOut{};
-      rc = dedisperse_blocks(p, d, p->d_y, 0, G.n_blk, fused_image(p, be) ? &img : nullptr,
-                             bf16_y(p, be));
-      if (!rc) rc = backend_dumps(p, d, be, I.first, I.last + 1, dout);
-      if (!rc) rc = drain_dm(p, d);
-      if (rc) return rc;
-      continue;
-    }
-    Group& g = p->groups[I.group];
-    const int* blist = p->d_lists + blk_off[d];
-    const int* dlist = p->d_lists + dmp_off[d];
-    int mk = mark_begin(p, CHIRP_STAGE_INV_ROWS);
-    CK(launch_inverse_rows(g.d_spec, p->d_Z, p->d_H, 0, blk_n[d] * p->M, G, p->tw(), g.d_rtw,
-                           p->stream, blist, p->M));
-    mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
-    mk = mark_begin(p, CHIRP_STAGE_INV_COLS);
-    CK(column_pass(p, d, be, p->d_Z, 0, blk_n[d] * p->M, blist));
-    mark_end(p, CHIRP_STAGE_INV_COLS, mk);
-    if (be == kCorrelate || vis_beams(p)) {
-      float2* vout = be == kCorrelate ? (float2*)dout + (size_t)d * p->n_dump * p->n_pair : p->d_V;
-      mk = mark_begin(p, CHIRP_STAGE_CORRELATE);
-      if (bf16_y(p, be))
-        CK(launch_correlate_bf16(p->d_y, p->N, p->M, p->L, 0, dmp_n[d], I.first, I.last, vout,
-                                 p->stream, dlist));
-      else
-        CK(launch_correlate(p->d_y, p->N, p->M, p->L, 0, dmp_n[d], I.first, I.last, vout,
-                            p->stream, dlist));
-      mark_end(p, CHIRP_STAGE_CORRELATE, mk);
-      if (be == kBeams) {
-        mk = mark_begin(p, CHIRP_STAGE_BEAMFORM);
-        CK(launch_beam_from_vis(p->d_V, p->d_wpair, p->M, p->n_pix, I.first, I.last,
-                                (float*)dout + (size_t)d * p->n_dump * p->n_pix, p->stream, dlist,
-                                dmp_n[d]));
-        mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
-      }
-      continue;
-    }
-    // tensor-core and CUDA-core beam modes: runs of consecutive selected dumps
-    const unsigned char* row = mask + (size_t)d * p->n_dump;
-    for (long long m = I.first; m <= I.last;) {
-      if (!row[m]) {
-        m++;
-        continue;
-      }
-      long long e = m;
-      while (e <= I.last && row[e]) e++;
-      rc = backend_dumps(p, d, be, m, e, dout);
-      if (rc) return rc;
-      m = e;
-    }
+    const BeamImageOut img = fused_image(p, be) ? beam_image_for(p, d) : BeamImageOut{};
+    rc = dedisperse_blocks(p, d, p->d_y, 0, G.n_blk, fused_image(p, be) ? &img : nullptr,
+                           bf16_y(p, be));
+    if (!rc) rc = backend_dumps(p, d, be, I.first, I.last + 1, dout);
+    if (!rc) rc = drain_dm(p, d);
+    if (rc) return rc;
   }
   return CHIRP_OK;
 }

@@ -93,6 +93,44 @@ def segment(setup: ProposalSetup, seed: int):
     return x, pulses
 
 
+def segment_device(setup: ProposalSetup, seed: int):
+    """segment() drawn on the GPU: the same pulses (DM, time, width, S/N,
+    direction, interference) for the same seed, with the noise and the bursts'
+    own noise from torch's generator (skymodel.noise_device / inject_device).
+    Returns (voltages complex64 CUDA tensor [M, N], list of Pulse)."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xyz = skymodel.antenna_positions(setup.n_ant, setup.max_baseline_m, 4242)
+    pix = skymodel.pixel_grid(setup.n_side, setup.field_deg)
+    x = skymodel.noise_device(setup.n_ant, setup.n_samp, seed)
+    pulses = []
+    for i in range(int(rng.integers(0, setup.max_pulses + 1))):
+        dm = float(rng.uniform(0.0, setup.dm_max))
+        w = math.exp(rng.uniform(math.log(setup.width_s[0]), math.log(setup.width_s[1])))
+        hi, lo = skymodel.sweep_samples(setup.f0, setup.bw, dm)
+        guard = 8 * w * setup.bw + 64
+        m_lo = int(math.ceil((hi + guard) / setup.dump_len))
+        m_hi = int(math.floor((setup.n_samp - lo - guard) / setup.dump_len)) - 1
+        if m_hi < m_lo:
+            continue
+        t0 = (int(rng.integers(m_lo, m_hi + 1)) + 0.5) * setup.dump_len
+        snr = float(rng.uniform(*setup.snr))
+        amp = skymodel.burst_amplitude(snr, setup.n_ant, setup.dump_len, w * setup.bw,
+                                       setup.dump_len / 2)
+        p = int(rng.integers(0, pix.shape[0]))
+        pulse = skymodel.Pulse(dm, t0, w, amp, float(pix[p, 0]), float(pix[p, 1]),
+                               seed * 16 + i + 1)
+        skymodel.inject_device(x, xyz, setup.f0, setup.bw, pulse)
+        pulses.append(pulse)
+    if rng.random() < setup.rfi_frac:  # narrowband interference, common to all antennas
+        f = rng.uniform(-0.45, 0.45) * setup.bw
+        a = rng.uniform(0.3, 1.0)
+        n = torch.arange(setup.n_samp, dtype=torch.float64, device=x.device)
+        tone = (a * torch.exp(2j * math.pi * f * n / setup.bw)).to(torch.complex64)
+        x += tone[None, :]
+    return x, pulses
+
+
 def _segment_job(args):
     setup, seed = args
     return segment(setup, seed)
@@ -199,12 +237,35 @@ class Proposer:
         one window of margin in time and dm_margin trial DMs on each side (a
         burst between two trial DMs is detected on either)."""
         s = self.s
-        n_dump = s.n_samp // s.dump_len
-        cells = np.zeros((s.n_dm, n_dump), np.uint8)
-        span = s.win * s.t_fb
-        for d, w in zip(*np.nonzero(mask)):
-            t_lo = max(0, (int(w) - 1) * span)
-            t_hi = min(s.n_samp, (int(w) + 2) * span)
-            d0, d1 = max(0, int(d) - dm_margin), min(s.n_dm, int(d) + dm_margin + 1)
-            cells[d0:d1, t_lo // s.dump_len:(t_hi + s.dump_len - 1) // s.dump_len] = 1
-        return cells
+        return cells_of(mask, s.n_samp, s.dump_len, s.win * s.t_fb, dm_margin)
+
+
+def cells_of(mask: np.ndarray, n_samp: int, dump_len: int, span: int,
+             dm_margin: int = 1) -> np.ndarray:
+    """Proposer.cells for any series length: mask [n_dm, n_win] of windows of
+    span samples -> coherent cells [n_dm, n_samp // dump_len]."""
+    n_dm = mask.shape[0]
+    cells = np.zeros((n_dm, n_samp // dump_len), np.uint8)
+    for d, w in zip(*np.nonzero(mask)):
+        t_lo = max(0, (int(w) - 1) * span)
+        t_hi = min(n_samp, (int(w) + 2) * span)
+        d0, d1 = max(0, int(d) - dm_margin), min(n_dm, int(d) + dm_margin + 1)
+        cells[d0:d1, t_lo // dump_len:(t_hi + dump_len - 1) // dump_len] = 1
+    return cells
+
+
+def recall(pulses_dets, cells_list, ddm: float, dump_len: int):
+    """(found, total): of the injected pulses the full grid detects (a
+    candidate within one trial DM and two dumps of the pulse), those with at
+    least one such candidate inside the selected cells.  pulses_dets: per
+    segment (pulses, set of (dm index, dump) candidates)."""
+    found = tot = 0
+    for (pulses, dets), cells in zip(pulses_dets, cells_list):
+        for p in pulses:
+            d = int(round(p.dm / ddm))
+            m = int(p.t0 // dump_len)
+            near = [(dd, mm) for (dd, mm) in dets if abs(dd - d) <= 1 and abs(mm - m) <= 2]
+            if near:
+                tot += 1
+                found += any(cells[dd, mm] for dd, mm in near)
+    return found, tot

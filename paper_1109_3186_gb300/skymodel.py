@@ -25,7 +25,11 @@ Physical model (all FP64 on the host, numpy only):
   origin; the whole RF phase exp(-2 pi j (f0 + f) tau_a) is applied.
 
 All draws come from numpy's PCG64 with explicit seeds, so every input is
-reproducible bit for bit on any host.
+reproducible bit for bit on any host.  The device variants at the end
+(noise_device, inject_device) apply the same model to a torch tensor on the
+GPU, with torch's seeded generator for the noise draws: they serve bulk
+training data, where moving each segment from host worker processes would
+dominate, and they are not equal sample for sample to the host versions.
 """
 
 from __future__ import annotations
@@ -341,3 +345,58 @@ def power_field(n_dm: int, n_dump: int, n_pix: int, first, last, seed: int,
         p = int(rng.integers(0, n_pix))
         P[d, m, p] = np.float32(mean * (1.0 + peak_scale * rng.uniform(0.5, 1.0)))
     return P
+
+
+# --------------------------------------------------------------------------
+# device variants (bulk training segments)
+# --------------------------------------------------------------------------
+def noise_device(n_ant: int, n_samp: int, seed: int, device="cuda"):
+    """The noise model of noise() drawn on the device: complex64 tensor
+    [n_ant, n_samp] from torch's generator seeded with ``seed``."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    re = torch.randn((n_ant, n_samp), generator=g, device=device, dtype=torch.float32)
+    im = torch.randn((n_ant, n_samp), generator=g, device=device, dtype=torch.float32)
+    return torch.complex(re, im) * (1.0 / math.sqrt(2.0))
+
+
+def inject_device(x, xyz: np.ndarray, f0: float, bw: float, p: Pulse, k_dm: float = K_DM,
+                  burst_noise=None) -> None:
+    """inject() for a torch tensor x [n_ant, n_samp] (complex64), in place: the
+    same window, envelope, dispersion phase and geometric delays in FP64 on
+    x's device.  The burst's unit-variance noise is burst_noise (complex128
+    [nfft], e.g. to reproduce inject() exactly) or drawn from torch's
+    generator seeded with p.seed."""
+    import torch
+    dev = x.device
+    n_ant, n_samp = x.shape
+    w = p.fwhm_s * bw
+    hi, lo = sweep_samples(f0, bw, p.dm, k_dm)
+    tau = geometric_delay(xyz, p.l, p.m)
+    gmax = float(np.max(np.abs(tau))) * bw
+    margin = int(math.ceil(6.0 * w + gmax + 64))
+    start = int(math.floor(p.t0 - hi)) - margin
+    length = int(math.ceil(hi + lo)) + 2 * margin
+    nfft = 1 << int(math.ceil(math.log2(length)))
+    lo_i, hi_i = max(start, 0), min(start + nfft, n_samp)
+    if hi_i <= lo_i:
+        return
+    t = torch.arange(nfft, dtype=torch.float64, device=dev) + float(start - p.t0)
+    env = torch.exp(-2.0 * math.log(2.0) * (t / w) ** 2)
+    env[torch.abs(t) > 8.0 * w] = 0.0
+    if burst_noise is None:
+        g = torch.Generator(device=dev)
+        g.manual_seed(int(p.seed))
+        burst_noise = torch.complex(
+            torch.randn(nfft, generator=g, device=dev, dtype=torch.float64),
+            torch.randn(nfft, generator=g, device=dev, dtype=torch.float64)) / math.sqrt(2.0)
+    burst = p.amp * env * burst_noise.to(dev)
+    spec = torch.fft.fft(burst)
+    f = torch.fft.fftfreq(nfft, d=1.0 / bw, device=dev, dtype=torch.float64)
+    disp = 2.0 * math.pi * k_dm * p.dm * (1.0 / (f0 + f) - 1.0 / f0 + f / f0 ** 2)
+    spec = spec * torch.exp(1j * disp)
+    for a in range(n_ant):
+        sa = spec * torch.exp(-2j * math.pi * (f0 + f) * float(tau[a]))
+        sig = torch.fft.ifft(sa)
+        x[a, lo_i:hi_i] += sig[lo_i - start:hi_i - start].to(torch.complex64)
