@@ -887,10 +887,13 @@ def truedelay_leg(sc, xd, stream, peaks, peak_kind, args):
            "beam_ifft_points_per_step": pts,
            "dtype": "f32 (weight phases in 64-bit fixed point from f64)",
            "note": "8x8 pixels over 1 deg on the headline observation"}
-    # the beam inverse passes: 8 B read + 8 B written per point (row pass, plus
-    # the chirp table), 8 B read per point (column pass; powers by atomics)
+    # the beam inverse passes: per point 8 B written and 8 B / (DMs per launch)
+    # read (the row pass reads a group's beam spectra once for up to dm_chunk
+    # DMs; the chirp tables are negligible), 8 B read (column pass; powers by
+    # one atomic add per row and dump)
     if "inv_rows" in st and "inv_cols" in st:
-        byts = 16.0 * pts + 8.0 * pts
+        chunk = max(1, plan.info.get("dm_chunk", 1))
+        byts = (8.0 + 8.0 / chunk) * pts + 8.0 * pts
         rate = byts / ((st["inv_rows"] + st["inv_cols"]) * 1e-3) / 1e9
         out["roofline"] = {"kernel": "beam inverse passes", "bound": "hbm", "achieved": rate,
                            "peak": hbm, "unit": "GB/s", "frac": rate / hbm,

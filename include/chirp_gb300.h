@@ -255,12 +255,14 @@ int chimageator_run(chirp_plan* plan, const void* volt, int volt_loc, float* pow
  * a block like the chirp's tail does.  The weights' phases are formed in
  * 64-bit fixed point from FP64 (exact modulo one cycle), the sums in FP32
  * (dump sums by atomic adds, so the last bits may differ between runs).
- * Costs n_pix / n_ant times the phased beams' inverse-FFT work.
+ * Costs n_pix / n_ant times the phased beams' inverse-FFT work; the sums
+ * over antennas do not depend on the DM and are formed once per FFT-length
+ * group (and chunk of pixels) for all of the group's DMs.
  *  pow_out: float32 [n_dm][n_dump][n_pix] at pow_loc (chimageator_run's
  *  layout).  Needs pixels and antenna positions at plan creation.  The first
- *  call allocates two chunk buffers of at most 1 GB each and the per-group
- *  phase tables.  Errors: CHIRP_EINVAL, CHIRP_EUNSUPPORTED, CHIRP_ENOMEM,
- *  CHIRP_ECUDA. */
+ *  call allocates the beam spectra of one group's pixel chunk (at most 8 GB),
+ *  a 1 GB chunk buffer of the inverse and the per-group phase tables.
+ *  Errors: CHIRP_EINVAL, CHIRP_EUNSUPPORTED, CHIRP_ENOMEM, CHIRP_ECUDA. */
 int chirp_truedelay_run(chirp_plan* plan, const void* volt, int volt_loc, float* pow_out,
                         int pow_loc);
 

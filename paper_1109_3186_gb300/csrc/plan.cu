@@ -1401,8 +1401,19 @@ unsigned long long frac_u64(double x) {
 
 constexpr size_t kTdChunkBytes = 1ull << 30;  // per chunk buffer (beam spectra, intermediate)
 
+// The beam spectra of a group do not depend on the DM: they are formed once
+// per group and chunk of pixels, for every block, and every DM of the group
+// is searched over them.  Pixels per chunk so that the chunk's spectra stay
+// within kTdBeamBytes (at least one pixel).
+constexpr size_t kTdBeamBytes = 8ull << 30;
+int td_pixel_chunk(const chirp_plan* p, const GroupGeom& G) {
+  const long long per_pix = G.n_blk * G.nfft * (long long)sizeof(float2);
+  return (int)std::max(1LL, std::min((long long)p->n_pix, (long long)kTdBeamBytes / per_pix));
+}
+
 // First use: per group the phase pairs {frac(f0 tau), frac(B tau / Nfft)} of
-// every (pixel, antenna) in FP64, and the two chunk buffers.
+// every (pixel, antenna) in FP64, the beam-spectra buffer and the chunk buffer
+// of the inverse.
 int truedelay_setup(chirp_plan* p) {
   if (p->d_tdY) return CHIRP_OK;
   long long max_nfft = 0, max_seq = 0;
@@ -1440,15 +1451,23 @@ int truedelay_setup(chirp_plan* p) {
                        p->stream));
     CK(cudaStreamSynchronize(p->stream));  // ph is reused for the next group
   }
-  const size_t bytes = (size_t)p->td_cap * (size_t)max_nfft * sizeof(float2);
-  int rc = dev_alloc(p, (void**)&p->d_tdY, bytes, "true-delay beam spectra");
-  if (!rc) rc = dev_alloc(p, (void**)&p->d_tdZ, bytes, "true-delay intermediate");
+  size_t ybytes = 0;
+  for (auto& g : p->groups)
+    ybytes = std::max(ybytes, (size_t)g.geom.n_blk * (size_t)td_pixel_chunk(p, g.geom) *
+                                  (size_t)g.geom.nfft * sizeof(float2));
+  int rc = dev_alloc(p, (void**)&p->d_tdY, ybytes, "true-delay beam spectra");
+  if (!rc)  // one chunk buffer per DM of a multi-DM row pass
+    rc = dev_alloc(p, (void**)&p->d_tdZ,
+                   (size_t)p->dm_chunk * p->td_cap * (size_t)max_nfft * sizeof(float2),
+                   "true-delay intermediate");
   return rc;
 }
 
-// Per DM: the chirp; per chunk of (block, pixel) sequences (whole blocks of
-// every pixel when they fit, else pixel ranges of one block) the beam spectra,
-// the inverse row pass with the chirp, and the column pass that detects and
+// Per group and chunk of pixels: the beam spectra of every block once; then
+// per chunk of up to dm_chunk DMs of the group their chirps, and per chunk of
+// (block, pixel) sequences (whole blocks of the chunk's pixels when they fit
+// the inverse's buffer, else pixel ranges of one block) one multi-DM inverse
+// row pass with the chirps and, per DM, the column pass that detects and
 // integrates into dout (cleared first).
 int truedelay_search(chirp_plan* p, const void* dx, float* dout, size_t bytes) {
   int rc = truedelay_setup(p);
@@ -1456,36 +1475,56 @@ int truedelay_search(chirp_plan* p, const void* dx, float* dout, size_t bytes) {
   rc = forward_all(p, dx);
   if (rc) return rc;
   CK(cudaMemsetAsync(dout, 0, bytes, p->stream));
-  for (int d = 0; d < (int)p->dm.size(); d++) {
-    const DmInfo& I = p->dmi[d];
-    if (I.last < I.first) continue;
-    Group& g = p->groups[I.group];
+  for (size_t gi = 0; gi < p->groups.size(); gi++) {
+    Group& g = p->groups[gi];
     const GroupGeom& G = g.geom;
-    rc = ensure_spec(p, I.group);
-    if (!rc) rc = chirp_for(p, d);
+    std::vector<int> dms;
+    for (int d : g.dms)
+      if (p->dmi[d].last >= p->dmi[d].first) dms.push_back(d);
+    if (dms.empty()) continue;
+    rc = ensure_spec(p, (int)gi);
     if (rc) return rc;
-    float* out = dout + (size_t)d * p->n_dump * p->n_pix;
-    const long long cap =
-        std::max(1LL, std::min(p->td_cap, (long long)kTdChunkBytes / (G.nfft * 8)));
-    const int np_max = (int)std::min<long long>(p->n_pix, cap);
-    const long long nb_max = np_max == p->n_pix ? std::max(1LL, cap / p->n_pix) : 1;
-    for (long long b0 = 0; b0 < G.n_blk; b0 += nb_max) {
-      const int nb = (int)std::min(nb_max, G.n_blk - b0);
-      for (int p0 = 0; p0 < p->n_pix; p0 += np_max) {
-        const int np = std::min(np_max, p->n_pix - p0);
-        int mk = mark_begin(p, CHIRP_STAGE_TD_SPECTRA);
-        CK(launch_td_spectra(g.d_spec, p->d_tdY, b0, nb, np, p0, p->M, G, g.d_tdph, g.d_tdrot,
-                             p->stream));
-        mark_end(p, CHIRP_STAGE_TD_SPECTRA, mk);
-        mk = mark_begin(p, CHIRP_STAGE_INV_ROWS);
-        CK(launch_inverse_rows(p->d_tdY, p->d_tdZ, p->d_H, 0, (long long)nb * np, G, p->tw(),
-                               g.d_rtw, p->stream));
-        mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
-        mk = mark_begin(p, CHIRP_STAGE_INV_COLS);
-        CK(launch_inverse_cols_pow(p->d_tdZ, out, p->N, b0, nb, np, p0, p->n_pix, G, I.n_hi,
-                                   I.n_lo, p->L, I.first * p->L, (I.last + 1) * p->L, p->tw(),
-                                   p->stream));
-        mark_end(p, CHIRP_STAGE_INV_COLS, mk);
+    const int np_max = td_pixel_chunk(p, G);
+    for (int p0 = 0; p0 < p->n_pix; p0 += np_max) {
+      const int np = std::min(np_max, p->n_pix - p0);
+      int mk = mark_begin(p, CHIRP_STAGE_TD_SPECTRA);
+      CK(launch_td_spectra(g.d_spec, p->d_tdY, 0, (int)G.n_blk, np, p0, p->M, G, g.d_tdph,
+                           g.d_tdrot, p->stream));
+      mark_end(p, CHIRP_STAGE_TD_SPECTRA, mk);
+      // up to dm_chunk DMs per row pass (the beam spectra read once for all of
+      // them), then each DM's column pass
+      const size_t z_stride = (size_t)p->td_cap * (size_t)G.nfft;
+      for (size_t c0 = 0; c0 < dms.size(); c0 += (size_t)p->dm_chunk) {
+        const int n = (int)std::min((size_t)p->dm_chunk, dms.size() - c0);
+        double dmv[kMaxChirps];
+        for (int j = 0; j < n; j++) dmv[j] = p->dm[dms[c0 + j]];
+        mk = mark_begin(p, CHIRP_STAGE_CHIRP);
+        CK(launch_chirp_tables(g.d_G, p->d_H, p->h_stride, dmv, n, G, p->stream));
+        mark_end(p, CHIRP_STAGE_CHIRP, mk);
+        // (b0, nb blocks) x (pp, npp pixels of the chunk) per inverse launch
+        const long long nb_max = np <= p->td_cap ? std::max(1LL, p->td_cap / np) : 1;
+        const int npp_max = (int)std::min<long long>(np, p->td_cap);
+        for (long long b0 = 0; b0 < G.n_blk; b0 += nb_max) {
+          const int nb = (int)std::min(nb_max, G.n_blk - b0);
+          for (int pp = 0; pp < np; pp += npp_max) {
+            const int npp = std::min(npp_max, np - pp);
+            mk = mark_begin(p, CHIRP_STAGE_INV_ROWS);
+            CK(launch_inverse_rows_multi(p->d_tdY + (size_t)(b0 * np + pp) * G.nfft, p->d_tdZ,
+                                         (long long)z_stride, p->d_H, p->h_stride, n,
+                                         (long long)nb * npp, G, p->tw(), g.d_rtw, p->stream));
+            mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
+            for (int j = 0; j < n; j++) {
+              const DmInfo& I = p->dmi[dms[c0 + j]];
+              float* out = dout + (size_t)dms[c0 + j] * p->n_dump * p->n_pix;
+              mk = mark_begin(p, CHIRP_STAGE_INV_COLS);
+              CK(launch_inverse_cols_pow(p->d_tdZ + (size_t)j * z_stride, out, p->N, b0, nb, npp,
+                                         p0 + pp, p->n_pix, G, I.n_hi, I.n_lo, p->L,
+                                         I.first * p->L, (I.last + 1) * p->L, p->tw(),
+                                         p->stream));
+              mark_end(p, CHIRP_STAGE_INV_COLS, mk);
+            }
+          }
+        }
       }
     }
   }

@@ -100,10 +100,10 @@ __global__ void __launch_bounds__(128) k_td_spectra(const float2* __restrict__ s
 // Column pass of the inverse for beam sequences, detecting and integrating:
 // sequence q of the launch is block b0 + q / np, pixel p_base + q % np; every
 // owned sample t of the block inside [t_lo, t_hi) (the DM's valid dumps) adds
-// |y(t)|^2 to P[t / dump_len][pixel].  Per CTA the squares are summed in
-// shared memory per (row, dump) -- a row's C consecutive samples meet at most
-// two dumps when dump_len >= C, others go straight to global atomics -- and
-// each partial reaches P with one atomic add.
+// |y(t)|^2 to P[t / dump_len][pixel].  The CTA's C consecutive samples of each
+// of its L rows are staged as powers in the transform's shared tile (zero
+// outside the owned, valid range); one thread then sums a row per dump it
+// meets and adds each sum to P with one atomic add.
 template <int L>
 __global__ void __launch_bounds__(256, 4) k_inv_cols_pow(
     const float2* __restrict__ Z, float* __restrict__ P, long long n_samp, int n2, long long step,
@@ -112,7 +112,6 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols_pow(
   constexpr int C = 4096 / L;
   constexpr int T = L / 16;
   __shared__ __align__(16) float2 sm[FftTile<L, C>::SLOTS];
-  static_assert(FftTile<L, C>::SLOTS >= L, "row partial sums reuse the transform's tile");
   const Twiddles tw = mk_tw(twp);
   const int s = threadIdx.x % C, jt = threadIdx.x / C;
   const int c = blockIdx.x * C + s;
@@ -121,42 +120,52 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols_pow(
   const long long b = b0 + q / np;
   const int pix = p_base + (int)(q % np);
   const long long nfft = (long long)L * n2;
-  const float2* src = Z + q * nfft;
+  // positions inside a block, (jt + k T) n2 + c < nfft <= 2^24, are 32-bit
+  const float2* src = Z + q * nfft + c;
   float2 v[16];
 #pragma unroll
-  for (int k = 0; k < 16; k++)
-    v[k] = act ? src[(long long)(jt + k * T) * n2 + c] : make_float2(0.f, 0.f);
+  for (int k = 0; k < 16; k++) v[k] = act ? src[(jt + k * T) * n2] : make_float2(0.f, 0.f);
   fft_core<L, C, false, true>(v, sm, s, jt, tw);
   const long long base = b * step;
   const long long lo_b = (b == 0) ? n_hi : n_hi_max;
   const long long hi_b = (b == n_blk - 1) ? (n_samp - n_lo - base) : (n_hi_max + step);
-  const long long col0 = (long long)blockIdx.x * C;
-  float* part = reinterpret_cast<float*>(sm);  // [L rows][2 dumps]
-  __syncthreads();                             // the transform is done with sm
-  for (int i = threadIdx.x; i < 2 * L; i += blockDim.x) part[i] = 0.f;
-  __syncthreads();
+  // owned and inside the DM's valid dumps: n in [nlo, nhi), clamped to [0, nfft]
+  long long nlo = lo_b > t_lo - base ? lo_b : t_lo - base;
+  long long nhi = hi_b < t_hi - base ? hi_b : t_hi - base;
+  nlo = nlo < 0 ? 0 : (nlo > nfft ? nfft : nlo);
+  nhi = nhi < 0 ? 0 : (nhi > nfft ? nfft : nhi);
+  const int nlo32 = (int)nlo, nhi32 = (int)nhi;
+  // powers [L rows][C columns], rows padded to C + 1 floats so that the row
+  // sums below (one thread per row) read distinct banks
+  float* et = reinterpret_cast<float*>(sm);
+  static_assert(L * (C + 1) <= 2 * FftTile<L, C>::SLOTS, "staging fits the transform's tile");
+  __syncthreads();                           // the transform is done with sm
 #pragma unroll
   for (int k = 0; k < 16; k++) {
     const int row = jt + k * T;
-    const long long n = (long long)row * n2 + c;
-    const long long t = base + n;
-    if (!act || n < lo_b || n >= hi_b || t < t_lo || t >= t_hi) continue;
-    const float e = v[k].x * v[k].x + v[k].y * v[k].y;
-    const long long m = t / dump_len;
-    const long long m0 = (base + (long long)row * n2 + col0) / dump_len;
-    const long long slot = m - m0;
-    if (slot < 2)
-      atomicAdd(&part[2 * row + slot], e);
-    else
-      atomicAdd(&P[m * n_pix + pix], e);
+    const int n = row * n2 + c;
+    et[row * (C + 1) + s] =
+        (act && n >= nlo32 && n < nhi32) ? v[k].x * v[k].x + v[k].y * v[k].y : 0.f;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 2 * L; i += blockDim.x) {
-    const float e = part[i];
-    if (e == 0.f) continue;
-    const int row = i >> 1;
-    const long long m = (base + (long long)row * n2 + col0) / dump_len + (i & 1);
-    atomicAdd(&P[m * n_pix + pix], e);
+  const int col0 = blockIdx.x * C;
+  const int n_col = min(C, n2 - col0);
+  for (int row = threadIdx.x; row < L; row += blockDim.x) {
+    const int n_first = row * n2 + col0;
+    if (n_first + n_col <= nlo32 || n_first >= nhi32) continue;  // nothing owned and valid
+    const long long tr = base + n_first;  // the row's first sample: m dump_len + r
+    long long m = tr / dump_len;
+    int r = (int)(tr - m * dump_len);
+    float acc = 0.f;
+    for (int j = 0; j < n_col; j++) {
+      acc += et[row * (C + 1) + j];
+      if (++r == dump_len || j == n_col - 1) {  // end of a dump, or of the row
+        if (acc != 0.f) atomicAdd(&P[m * n_pix + pix], acc);
+        acc = 0.f;
+        r = 0;
+        m++;
+      }
+    }
   }
 }
 
