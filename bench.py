@@ -69,6 +69,9 @@ def parse_args():
     ap.add_argument("--chimg-only", action="store_true",
                     help="time only the paper's Chimageator pre-integrator on a uniform linear "
                          "array shaped like the workload; prints one line")
+    ap.add_argument("--truedelay-only", action="store_true",
+                    help="time only the true-delay beams (8 x 8 pixels) on the same workload (for "
+                         "profiling their kernels); prints one line")
     ap.add_argument("--cpu-dumps", type=int, default=640,
                     help="dumps per selected DM in the oracle's bounded CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1016,6 +1019,12 @@ def run_ours(args):
     if args.chimg_only:
         line = chimg_ula_search(stream, args)
         line["mode"] = "chimg_ula"
+        print(json.dumps(line), flush=True)
+        return 0
+    if args.truedelay_only:
+        line = truedelay_leg(sc, torch.from_numpy(x).cuda(), stream, *load_peaks(), args)
+        line["mode"] = "truedelay"
+        line["config"] = config_block(sc, 1)
         print(json.dumps(line), flush=True)
         return 0
     if args.cpi_only:

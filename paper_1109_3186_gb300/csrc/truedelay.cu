@@ -42,10 +42,13 @@ __global__ void __launch_bounds__(128) k_td_spectra(const float2* __restrict__ s
                                                     long long nfft,
                                                     const ulonglong2* __restrict__ ph,
                                                     const float2* __restrict__ rot) {
-  const long long pos0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * kTdRun;
+  // grid (pixel chunks, runs / 128, blocks): the pixel chunks that read the
+  // same spectrum runs are the fastest grid index, so they run together and
+  // find them in L2
+  const long long pos0 = ((long long)blockIdx.y * blockDim.x + threadIdx.x) * kTdRun;
   if (pos0 >= nfft) return;
-  const long long b = b0 + blockIdx.y;
-  const int pz = blockIdx.z * kTdPix;  // first pixel of this thread's chunk (launch-local)
+  const long long b = b0 + blockIdx.z;
+  const int pz = blockIdx.x * kTdPix;  // first pixel of this thread's chunk (launch-local)
   const long long k1 = pos0 / n2, k2 = pos0 % n2;
   long long fi = k1 + (long long)n1 * k2;
   if (2 * fi >= nfft) fi -= nfft;
@@ -89,7 +92,7 @@ __global__ void __launch_bounds__(128) k_td_spectra(const float2* __restrict__ s
   for (int j = 0; j < kTdPix; j++) {
     const int p = pz + j;
     if (p >= np) break;
-    float4* yo = reinterpret_cast<float4*>(Y + ((long long)blockIdx.y * np + p) * nfft + pos0);
+    float4* yo = reinterpret_cast<float4*>(Y + ((long long)blockIdx.z * np + p) * nfft + pos0);
 #pragma unroll
     for (int r = 0; r < kTdRun / 2; r++)
       yo[r] = make_float4(acc[j][2 * r].x, acc[j][2 * r].y, acc[j][2 * r + 1].x,
@@ -174,10 +177,10 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols_pow(
 cudaError_t launch_td_spectra(const float2* spec, float2* Y, long long b0, int nb, int np,
                               int p_base, int n_ant, const GroupGeom& g, const void* ph,
                               const float2* rot, cudaStream_t st) {
-  if (nb < 1 || nb > 65535 || np < 1 || (g.n2 / 2) % kTdRun != 0)
-    return cudaErrorInvalidConfiguration;
   const long long runs = g.nfft / kTdRun;
-  dim3 grid((unsigned)((runs + 127) / 128), (unsigned)nb, (unsigned)((np + kTdPix - 1) / kTdPix));
+  if (nb < 1 || nb > 65535 || np < 1 || (g.n2 / 2) % kTdRun != 0 || (runs + 127) / 128 > 65535)
+    return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)((np + kTdPix - 1) / kTdPix), (unsigned)((runs + 127) / 128), (unsigned)nb);
   k_td_spectra<<<grid, 128, 0, st>>>(spec, Y, b0, np, p_base, n_ant, g.n1, g.n2, g.nfft,
                                      static_cast<const ulonglong2*>(ph), rot);
   return cudaGetLastError();
