@@ -36,11 +36,10 @@ namespace chirp {
 //   Re V = P.lo + P.hi,  Im V = Q.lo - Q.hi,
 // so a sample needs its (re, im) pair and one swapped copy (im, re) per row
 // antenna, and no broadcasts or sign flips.  Diagonal tiles form only their
-// upper triangle.  Above 16 antennas (k_correlate_direct) the warps of a CTA
-// (kCorrWarps tiles of one dump, grid dimension y over the rest) read the
-// samples straight from global memory.
+// upper triangle.  Above 16 antennas the antennas form blocks of 12: one
+// launch takes each block alone (its upper tiles), a second each pair of
+// blocks, staging both blocks' rows.
 constexpr int kCorrTile = 4;
-constexpr int kCorrWarps = 8;
 constexpr int kCorrChunk = 256;
 constexpr int kCorrStagedMaxAnt = 16;
 
@@ -107,37 +106,71 @@ __device__ __forceinline__ void zero_elem(__nv_bfloat162* p) {
 }
 
 // 96 registers: two CTAs of 10 warps (NT = 4) or three of 6 (NT = 3) per SM
-template <typename T, int NT, bool VEC16>
-__global__ void __maxnreg__(96)
+// (single-warp CTAs, NT = 1, are limited by shared memory instead: 128).
+// Antennas form blocks of BA = 4 NT.  PAIR = false: CTA (dump, I) takes block
+// I = blockIdx.y alone -- its NT (NT + 1) / 2 upper 4 x 4 tiles, one per warp
+// (up to 16 antennas this is the whole product).  PAIR = true: CTA (dump,
+// (I, J)), I < J (blockIdx.y over the strict upper triangle of blocks),
+// stages block I's rows, then block J's, and its NT x NT warps each own one
+// 4 x 4 tile of the pairs (block I antenna, block J antenna).
+template <typename T, int NT, bool VEC16, bool PAIR>
+__global__ void __maxnreg__(NT == 1 ? 128 : 96)
     k_correlate_staged(const T* __restrict__ y, long long n_samp, int M, int L, long long m_base,
                        long long first, long long last, float2* __restrict__ vis,
                        const int* __restrict__ dump_list) {
-  constexpr int MP = kCorrTile * NT;  // antenna rows of a stage, zero-padded
-  constexpr int NTH = 32 * NT * (NT + 1) / 2;
+  constexpr int BA = kCorrTile * NT;  // antennas of a block
+  constexpr int NTH = PAIR ? 32 * NT * NT : 32 * NT * (NT + 1) / 2;
+  constexpr int ROWS = PAIR ? 2 * BA : BA;  // stage rows, zero-padded
   constexpr int CH = kCorrChunk;
-  constexpr int STAGE = MP * CH;
+  constexpr int STAGE = ROWS * CH;
   extern __shared__ __align__(16) unsigned char ring_raw[];
-  T* ring = reinterpret_cast<T*>(ring_raw);  // [2][MP][CH]
+  T* ring = reinterpret_cast<T*>(ring_raw);  // [2][ROWS][CH]
   const long long m = dump_list ? (long long)dump_list[blockIdx.x] : m_base + blockIdx.x;
   const int n_pair = M * (M + 1) / 2;
   float2* out = vis + m * n_pair;
   if (m < first || m > last) {
-    for (int i = threadIdx.x; i < n_pair; i += NTH) out[i] = make_float2(0.f, 0.f);
+    if (!PAIR && blockIdx.y == 0)
+      for (int i = threadIdx.x; i < n_pair; i += NTH) out[i] = make_float2(0.f, 0.f);
     return;
   }
+  int I = blockIdx.y, J = I;
+  if (PAIR) {  // strict upper triangle of SB x SB blocks, row-major
+    const int SB = (M + BA - 1) / BA;
+    int rem = blockIdx.y;
+    I = 0;
+    while (rem >= SB - 1 - I) {
+      rem -= SB - 1 - I;
+      I++;
+    }
+    J = I + 1 + rem;
+  }
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  int ti = 0, rem = warp;  // one tile per warp
-  while (rem >= NT - ti) {
-    rem -= NT - ti;
-    ti++;
+  int ti = 0, tj;
+  if (PAIR) {
+    ti = warp / NT;
+    tj = warp % NT;
+  } else {  // one upper tile of the block per warp
+    int rem = warp;
+    while (rem >= NT - ti) {
+      rem -= NT - ti;
+      ti++;
+    }
+    tj = ti + rem;
   }
-  const int tj = ti + rem;
-  const bool diag = ti == tj;
-  for (int i = threadIdx.x; i < 2 * (MP - M) * CH; i += NTH) {
-    const int st = i / ((MP - M) * CH), r = i % ((MP - M) * CH);
-    zero_elem(ring + st * STAGE + M * CH + r);
+  const bool diag = !PAIR && ti == tj;
+  // stage rows [0, nA): antennas I BA + r; [BA, BA + nB): antennas J BA + r
+  const int nA = min(BA, M - I * BA);
+  const int nB = PAIR ? min(BA, M - J * BA) : 0;
+  const int zA = BA - nA, zB = PAIR ? BA - nB : 0;  // padded rows stay zero
+  for (int i = threadIdx.x; i < 2 * (zA + zB) * CH; i += NTH) {
+    const int st = i / ((zA + zB) * CH), k = i % ((zA + zB) * CH);
+    const int r = k / CH;
+    zero_elem(ring + st * STAGE + (r < zA ? nA + r : BA + nB + (r - zA)) * CH + k % CH);
   }
-  const T* src = y + m * L;  // sample 0 of the dump, antenna 0
+  // sample 0 of the dump: antenna I BA (block I) and antenna J BA (block J)
+  const T* srcA = y + (long long)I * BA * n_samp + m * L;
+  const T* srcB = y + (long long)J * BA * n_samp + m * L;
+  const int n_rows = nA + nB;
   const int n_chunks = (L + CH - 1) / CH;
   auto fetch = [&](int c) {
     if (c < n_chunks) {
@@ -146,20 +179,26 @@ __global__ void __maxnreg__(96)
       if constexpr (VEC16) {  // rows, dumps and len are multiples of EPV samples
         constexpr int EPV = 16 / (int)sizeof(T);
         constexpr int U = CH / EPV;
-        for (int e = threadIdx.x; e < M * U; e += NTH) {
-          const int a = e / U, i = EPV * (e % U);
+        for (int e = threadIdx.x; e < n_rows * U; e += NTH) {
+          const int r = e / U, i = EPV * (e % U);
+          const bool inA = !PAIR || r < nA;
+          const T* s_row = inA ? srcA + (long long)r * n_samp : srcB + (long long)(r - nA) * n_samp;
+          T* dst = buf + (inA ? r : BA + (r - nA)) * CH + i;
           if (i < len)
-            cp_async16(buf + a * CH + i, src + (long long)a * n_samp + t0 + i);
+            cp_async16(dst, s_row + t0 + i);
           else
-            *reinterpret_cast<uint4*>(buf + a * CH + i) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
         }
       } else {
-        for (int e = threadIdx.x; e < M * CH; e += NTH) {
-          const int a = e / CH, i = e % CH;
+        for (int e = threadIdx.x; e < n_rows * CH; e += NTH) {
+          const int r = e / CH, i = e % CH;
+          const bool inA = !PAIR || r < nA;
+          const T* s_row = inA ? srcA + (long long)r * n_samp : srcB + (long long)(r - nA) * n_samp;
+          T* dst = buf + (inA ? r : BA + (r - nA)) * CH + i;
           if (i < len)
-            cp_async_elem(buf + a * CH + i, src + (long long)a * n_samp + t0 + i);
+            cp_async_elem(dst, s_row + t0 + i);
           else
-            zero_elem(buf + a * CH + i);
+            zero_elem(dst);
         }
       }
     }
@@ -177,7 +216,7 @@ __global__ void __maxnreg__(96)
     fetch(c + 1);
     const T* buf = ring + (c & 1) * STAGE;
     const T* ri = buf + ti * kCorrTile * CH + lane;
-    const T* rj = buf + tj * kCorrTile * CH + lane;
+    const T* rj = buf + ((PAIR ? BA : 0) + tj * kCorrTile) * CH + lane;
 #pragma unroll 1
     for (int t = 0; t < CH; t += 32) {
       unsigned long long u[kCorrTile], us[kCorrTile];
@@ -206,7 +245,7 @@ __global__ void __maxnreg__(96)
     }
   }
   cp_async_wait<0>();
-  // lane a*4+b writes pair (ti*4+a, tj*4+b) if it is in the upper triangle
+  // lane a*4+b writes pair (p, q) = (I BA + ti*4+a, J BA + tj*4+b) if p <= q
   float2 mine = make_float2(0.f, 0.f);
 #pragma unroll
   for (int a = 0; a < kCorrTile; a++)
@@ -223,102 +262,28 @@ __global__ void __maxnreg__(96)
     }
   if (lane < kCorrTile * kCorrTile) {
     const int a = lane / kCorrTile, b = lane % kCorrTile;
-    const int p = ti * kCorrTile + a, q = tj * kCorrTile + b;
+    const int p = I * BA + ti * kCorrTile + a, q = J * BA + tj * kCorrTile + b;
     if (p < M && q < M && p <= q) out[p * M - p * (p - 1) / 2 + (q - p)] = mine;
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(32 * kCorrWarps) k_correlate_direct(const T* __restrict__ y,
-                                                                long long n_samp, int M, int L,
-                                                                long long m_base, long long first,
-                                                                long long last,
-                                                                float2* __restrict__ vis,
-                                                                const int* __restrict__ dump_list) {
-  const long long m = dump_list ? (long long)dump_list[blockIdx.x] : m_base + blockIdx.x;
-  const int n_pair = M * (M + 1) / 2;
-  float2* out = vis + m * n_pair;
-  if (m < first || m > last) {
-    if (blockIdx.y == 0)
-      for (int i = threadIdx.x; i < n_pair; i += blockDim.x) out[i] = make_float2(0.f, 0.f);
-    return;
-  }
-  const int nt = (M + kCorrTile - 1) / kCorrTile;
-  const int n_tiles = nt * (nt + 1) / 2;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int tile = blockIdx.y * (blockDim.x / 32) + warp;
-  if (tile >= n_tiles) return;
-  int ti = 0, rem = tile;
-  while (rem >= nt - ti) {
-    rem -= nt - ti;
-    ti++;
-  }
-  const int tj = ti + rem;
-  const T* yi[kCorrTile];
-  const T* yj[kCorrTile];
-  bool vi[kCorrTile], vj[kCorrTile];
-#pragma unroll
-  for (int a = 0; a < kCorrTile; a++) {
-    const int ai = ti * kCorrTile + a, aj = tj * kCorrTile + a;
-    vi[a] = ai < M;
-    vj[a] = aj < M;
-    yi[a] = y + (long long)(vi[a] ? ai : 0) * n_samp + m * L;
-    yj[a] = y + (long long)(vj[a] ? aj : 0) * n_samp + m * L;
-  }
-  float2 acc[kCorrTile][kCorrTile];
-#pragma unroll
-  for (int a = 0; a < kCorrTile; a++)
-#pragma unroll
-    for (int b = 0; b < kCorrTile; b++) acc[a][b] = make_float2(0.f, 0.f);
-#pragma unroll 4
-  for (int t = lane; t < L; t += 32) {
-    float2 u[kCorrTile], w[kCorrTile];
-#pragma unroll
-    for (int a = 0; a < kCorrTile; a++) {
-      u[a] = vi[a] ? to_f2(__ldg(yi[a] + t)) : make_float2(0.f, 0.f);
-      w[a] = vj[a] ? to_f2(__ldg(yj[a] + t)) : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int a = 0; a < kCorrTile; a++)
-#pragma unroll
-      for (int b = 0; b < kCorrTile; b++) {  // u_a * conj(w_b)
-        acc[a][b].x = fmaf(u[a].x, w[b].x, fmaf(u[a].y, w[b].y, acc[a][b].x));
-        acc[a][b].y = fmaf(u[a].y, w[b].x, fmaf(-u[a].x, w[b].y, acc[a][b].y));
-      }
-  }
-#pragma unroll
-  for (int a = 0; a < kCorrTile; a++)
-#pragma unroll
-    for (int b = 0; b < kCorrTile; b++)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        acc[a][b].x += __shfl_xor_sync(0xffffffffu, acc[a][b].x, o);
-        acc[a][b].y += __shfl_xor_sync(0xffffffffu, acc[a][b].y, o);
-      }
-  // lane a*4+b writes pair (ti*4+a, tj*4+b) if it is in the upper triangle
-  if (lane < kCorrTile * kCorrTile) {
-    const int a = lane / kCorrTile, b = lane % kCorrTile;
-    const int p = ti * kCorrTile + a, q = tj * kCorrTile + b;
-    float2 v = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int aa = 0; aa < kCorrTile; aa++)
-#pragma unroll
-      for (int bb = 0; bb < kCorrTile; bb++)
-        if (aa == a && bb == b) v = acc[aa][bb];
-    if (p < M && q < M && p <= q) out[p * M - p * (p - 1) / 2 + (q - p)] = v;
-  }
-}
-
-template <typename T, int NT, bool VEC16>
+template <typename T, int NT, bool VEC16, bool PAIR>
 static cudaError_t launch_staged(const T* y, long long n_samp, int n_ant, int dump_len,
                                  long long m_base, long long n_m, long long first, long long last,
                                  float2* vis, cudaStream_t st, const int* dump_list) {
-  const size_t smem = (size_t)2 * kCorrTile * NT * kCorrChunk * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(k_correlate_staged<T, NT, VEC16>,
+  constexpr int BA = kCorrTile * NT;
+  const size_t smem = (size_t)2 * (PAIR ? 2 : 1) * BA * kCorrChunk * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(k_correlate_staged<T, NT, VEC16, PAIR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_correlate_staged<T, NT, VEC16><<<(unsigned)n_m, 32 * NT * (NT + 1) / 2, smem, st>>>(
-      y, n_samp, n_ant, dump_len, m_base, first, last, vis, dump_list);
+  const long long SB = (n_ant + BA - 1) / BA;
+  const long long n_y = PAIR ? SB * (SB - 1) / 2 : SB;
+  if (n_y < 1) return cudaSuccess;
+  if (n_y > 65535) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)n_m, (unsigned)n_y);
+  k_correlate_staged<T, NT, VEC16, PAIR>
+      <<<grid, PAIR ? 32 * NT * NT : 32 * NT * (NT + 1) / 2, smem, st>>>(
+          y, n_samp, n_ant, dump_len, m_base, first, last, vis, dump_list);
   return cudaGetLastError();
 }
 
@@ -327,38 +292,35 @@ static cudaError_t launch_staged_nt(const T* y, long long n_samp, int n_ant, int
                                     long long m_base, long long n_m, long long first,
                                     long long last, float2* vis, cudaStream_t st,
                                     const int* dump_list) {
-  switch ((n_ant + kCorrTile - 1) / kCorrTile) {
-    case 1: return launch_staged<T, 1, VEC16>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis, st, dump_list);
-    case 2: return launch_staged<T, 2, VEC16>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis, st, dump_list);
-    case 3: return launch_staged<T, 3, VEC16>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis, st, dump_list);
-    case 4: return launch_staged<T, 4, VEC16>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis, st, dump_list);
+#define CHIRP_CORR_ARGS y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis, st, dump_list
+  switch (n_ant > kCorrStagedMaxAnt ? 0 : (n_ant + kCorrTile - 1) / kCorrTile) {
+    case 0: {  // blocks of 12 antennas: the diagonal blocks, then the block pairs
+      cudaError_t e = launch_staged<T, 3, VEC16, false>(CHIRP_CORR_ARGS);
+      return e != cudaSuccess ? e : launch_staged<T, 3, VEC16, true>(CHIRP_CORR_ARGS);
+    }
+    case 1: return launch_staged<T, 1, VEC16, false>(CHIRP_CORR_ARGS);
+    case 2: return launch_staged<T, 2, VEC16, false>(CHIRP_CORR_ARGS);
+    case 3: return launch_staged<T, 3, VEC16, false>(CHIRP_CORR_ARGS);
+    case 4: return launch_staged<T, 4, VEC16, false>(CHIRP_CORR_ARGS);
     default: return cudaErrorInvalidValue;
   }
+#undef CHIRP_CORR_ARGS
 }
 
 template <typename T>
 static cudaError_t correlate_any(const T* y, long long n_samp, int n_ant, int dump_len,
                                  long long m_base, long long n_m, long long first, long long last,
                                  float2* vis, cudaStream_t st, const int* dump_list) {
-  const int nt = (n_ant + kCorrTile - 1) / kCorrTile;
-  const int n_tiles = nt * (nt + 1) / 2;
   if (n_m <= 0) return cudaSuccess;
-  if (n_ant <= kCorrStagedMaxAnt) {
-    if (n_m >= (1LL << 31)) return cudaErrorInvalidConfiguration;
-    // 16-byte copies when every row and dump starts on a 16-byte boundary of a
-    // 16-byte aligned array
-    constexpr int EPV = 16 / (int)sizeof(T);
-    if (n_samp % EPV == 0 && dump_len % EPV == 0 && ((uintptr_t)y & 15) == 0)
-      return launch_staged_nt<T, true>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis,
-                                       st, dump_list);
-    return launch_staged_nt<T, false>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis,
-                                      st, dump_list);
-  }
-  const int warps = n_tiles < kCorrWarps ? n_tiles : kCorrWarps;
-  dim3 grid((unsigned)n_m, (n_tiles + warps - 1) / warps);
-  k_correlate_direct<T><<<grid, 32 * warps, 0, st>>>(y, n_samp, n_ant, dump_len, m_base, first,
-                                                     last, vis, dump_list);
-  return cudaGetLastError();
+  if (n_m >= (1LL << 31)) return cudaErrorInvalidConfiguration;
+  // 16-byte copies when every row and dump starts on a 16-byte boundary of a
+  // 16-byte aligned array
+  constexpr int EPV = 16 / (int)sizeof(T);
+  if (n_samp % EPV == 0 && dump_len % EPV == 0 && ((uintptr_t)y & 15) == 0)
+    return launch_staged_nt<T, true>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis,
+                                     st, dump_list);
+  return launch_staged_nt<T, false>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis, st,
+                                    dump_list);
 }
 
 cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int dump_len,
