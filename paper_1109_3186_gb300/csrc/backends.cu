@@ -13,6 +13,9 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstdint>
+
 #include "internal.h"
 
 namespace chirp {
@@ -113,11 +116,20 @@ __device__ __forceinline__ void zero_elem(__nv_bfloat162* p) {
 // (I, J)), I < J (blockIdx.y over the strict upper triangle of blocks),
 // stages block I's rows, then block J's, and its NT x NT warps each own one
 // 4 x 4 tile of the pairs (block I antenna, block J antenna).
+struct CorrBatch {
+  CorrJob job[kCorrBatchMax];
+};
+
 template <typename T, int NT, bool VEC16, bool PAIR>
 __global__ void __maxnreg__(NT == 1 ? 128 : 96)
-    k_correlate_staged(const T* __restrict__ y, long long n_samp, int M, int L, long long m_base,
-                       long long first, long long last, float2* __restrict__ vis,
-                       const int* __restrict__ dump_list) {
+    k_correlate_staged(const __grid_constant__ CorrBatch batch, long long n_samp, int M, int L) {
+  // this CTA's DM (grid dimension z) and dump
+  const CorrJob& job = batch.job[blockIdx.z];
+  if (blockIdx.x >= job.n_m) return;
+  const T* __restrict__ y = static_cast<const T*>(job.y);
+  float2* __restrict__ vis = job.vis;
+  const int* __restrict__ dump_list = job.dump_list;
+  const long long m_base = job.m_base, first = job.first, last = job.last;
   constexpr int BA = kCorrTile * NT;  // antennas of a block
   constexpr int NTH = PAIR ? 32 * NT * NT : 32 * NT * (NT + 1) / 2;
   constexpr int ROWS = PAIR ? 2 * BA : BA;  // stage rows, zero-padded
@@ -268,9 +280,8 @@ __global__ void __maxnreg__(NT == 1 ? 128 : 96)
 }
 
 template <typename T, int NT, bool VEC16, bool PAIR>
-static cudaError_t launch_staged(const T* y, long long n_samp, int n_ant, int dump_len,
-                                 long long m_base, long long n_m, long long first, long long last,
-                                 float2* vis, cudaStream_t st, const int* dump_list) {
+static cudaError_t launch_staged(const CorrBatch& b, int n_jobs, long long max_m, long long n_samp,
+                                 int n_ant, int dump_len, cudaStream_t st) {
   constexpr int BA = kCorrTile * NT;
   const size_t smem = (size_t)2 * (PAIR ? 2 : 1) * BA * kCorrChunk * sizeof(T);
   cudaError_t e = cudaFuncSetAttribute(k_correlate_staged<T, NT, VEC16, PAIR>,
@@ -280,19 +291,17 @@ static cudaError_t launch_staged(const T* y, long long n_samp, int n_ant, int du
   const long long n_y = PAIR ? SB * (SB - 1) / 2 : SB;
   if (n_y < 1) return cudaSuccess;
   if (n_y > 65535) return cudaErrorInvalidConfiguration;
-  dim3 grid((unsigned)n_m, (unsigned)n_y);
+  dim3 grid((unsigned)max_m, (unsigned)n_y, (unsigned)n_jobs);
   k_correlate_staged<T, NT, VEC16, PAIR>
-      <<<grid, PAIR ? 32 * NT * NT : 32 * NT * (NT + 1) / 2, smem, st>>>(
-          y, n_samp, n_ant, dump_len, m_base, first, last, vis, dump_list);
+      <<<grid, PAIR ? 32 * NT * NT : 32 * NT * (NT + 1) / 2, smem, st>>>(b, n_samp, n_ant,
+                                                                        dump_len);
   return cudaGetLastError();
 }
 
 template <typename T, bool VEC16>
-static cudaError_t launch_staged_nt(const T* y, long long n_samp, int n_ant, int dump_len,
-                                    long long m_base, long long n_m, long long first,
-                                    long long last, float2* vis, cudaStream_t st,
-                                    const int* dump_list) {
-#define CHIRP_CORR_ARGS y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis, st, dump_list
+static cudaError_t launch_staged_nt(const CorrBatch& b, int n_jobs, long long max_m,
+                                    long long n_samp, int n_ant, int dump_len, cudaStream_t st) {
+#define CHIRP_CORR_ARGS b, n_jobs, max_m, n_samp, n_ant, dump_len, st
   switch (n_ant > kCorrStagedMaxAnt ? 0 : (n_ant + kCorrTile - 1) / kCorrTile) {
     case 0: {  // blocks of 12 antennas: the diagonal blocks, then the block pairs
       cudaError_t e = launch_staged<T, 3, VEC16, false>(CHIRP_CORR_ARGS);
@@ -308,32 +317,44 @@ static cudaError_t launch_staged_nt(const T* y, long long n_samp, int n_ant, int
 }
 
 template <typename T>
-static cudaError_t correlate_any(const T* y, long long n_samp, int n_ant, int dump_len,
-                                 long long m_base, long long n_m, long long first, long long last,
-                                 float2* vis, cudaStream_t st, const int* dump_list) {
-  if (n_m <= 0) return cudaSuccess;
-  if (n_m >= (1LL << 31)) return cudaErrorInvalidConfiguration;
-  // 16-byte copies when every row and dump starts on a 16-byte boundary of a
-  // 16-byte aligned array
+static cudaError_t correlate_batch(const CorrJob* jobs, int n_jobs, long long n_samp, int n_ant,
+                                   int dump_len, cudaStream_t st) {
+  if (n_jobs < 1 || n_jobs > kCorrBatchMax) return cudaErrorInvalidValue;
+  CorrBatch b{};
+  long long max_m = 0;
+  // 16-byte copies when every row and dump starts on a 16-byte boundary of
+  // 16-byte aligned arrays
   constexpr int EPV = 16 / (int)sizeof(T);
-  if (n_samp % EPV == 0 && dump_len % EPV == 0 && ((uintptr_t)y & 15) == 0)
-    return launch_staged_nt<T, true>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis,
-                                     st, dump_list);
-  return launch_staged_nt<T, false>(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis, st,
-                                    dump_list);
+  bool vec16 = n_samp % EPV == 0 && dump_len % EPV == 0;
+  for (int i = 0; i < n_jobs; i++) {
+    b.job[i] = jobs[i];
+    if (jobs[i].n_m < 0 || jobs[i].n_m >= (1LL << 31)) return cudaErrorInvalidConfiguration;
+    max_m = std::max(max_m, jobs[i].n_m);
+    vec16 = vec16 && ((uintptr_t)jobs[i].y & 15) == 0;
+  }
+  if (max_m <= 0) return cudaSuccess;
+  if (vec16) return launch_staged_nt<T, true>(b, n_jobs, max_m, n_samp, n_ant, dump_len, st);
+  return launch_staged_nt<T, false>(b, n_jobs, max_m, n_samp, n_ant, dump_len, st);
+}
+
+cudaError_t launch_correlate_batch(const CorrJob* jobs, int n_jobs, bool bf16, long long n_samp,
+                                   int n_ant, int dump_len, cudaStream_t st) {
+  return bf16 ? correlate_batch<__nv_bfloat162>(jobs, n_jobs, n_samp, n_ant, dump_len, st)
+              : correlate_batch<float2>(jobs, n_jobs, n_samp, n_ant, dump_len, st);
 }
 
 cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int dump_len,
                              long long m_base, long long n_m, long long first, long long last,
                              float2* vis, cudaStream_t st, const int* dump_list) {
-  return correlate_any(y, n_samp, n_ant, dump_len, m_base, n_m, first, last, vis, st, dump_list);
+  const CorrJob j{y, vis, m_base, n_m, first, last, dump_list};
+  return correlate_batch<float2>(&j, 1, n_samp, n_ant, dump_len, st);
 }
 
 cudaError_t launch_correlate_bf16(const void* y16, long long n_samp, int n_ant, int dump_len,
                                   long long m_base, long long n_m, long long first, long long last,
                                   float2* vis, cudaStream_t st, const int* dump_list) {
-  return correlate_any(static_cast<const __nv_bfloat162*>(y16), n_samp, n_ant, dump_len, m_base,
-                       n_m, first, last, vis, st, dump_list);
+  const CorrJob j{y16, vis, m_base, n_m, first, last, dump_list};
+  return correlate_batch<__nv_bfloat162>(&j, 1, n_samp, n_ant, dump_len, st);
 }
 
 // ------------------------------------------------------------------ beams from visibilities
@@ -351,16 +372,25 @@ constexpr int kVisBM = 64;
 constexpr int kVisBN = 128;
 constexpr int kVisBK = 16;
 
-__global__ void __launch_bounds__(256) k_beam_from_vis(const float* __restrict__ V, int K,
-                                                       const float* __restrict__ B, int ldb,
-                                                       int n_pix, long long first, long long n_rows,
-                                                       const int* __restrict__ dump_list,
-                                                       float* __restrict__ pow) {
+struct VisBatch {
+  VisJob job[kCorrBatchMax];
+};
+
+__global__ void __launch_bounds__(256) k_beam_from_vis(const __grid_constant__ VisBatch batch,
+                                                       int K, const float* __restrict__ B,
+                                                       int ldb, int n_pix) {
+  // this CTA's DM (grid dimension z)
+  const VisJob& job = batch.job[blockIdx.z];
+  const long long row0 = (long long)blockIdx.x * kVisBM;
+  if (row0 >= job.n_rows) return;
+  const float* __restrict__ V = reinterpret_cast<const float*>(job.V);
+  float* __restrict__ pow = job.pow;
+  const int* __restrict__ dump_list = job.dump_list;
+  const long long first = job.first, n_rows = job.n_rows;
   __shared__ __align__(16) float As[2][kVisBK][kVisBM];
   __shared__ __align__(16) float Bs[2][kVisBK][kVisBN];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
-  const long long row0 = (long long)blockIdx.x * kVisBM;
   const int p0 = blockIdx.y * kVisBN;
   // loader coordinates: A 64 rows x 16 k (4 k per thread), B 16 k x 128 (8 per thread)
   const int a_row = tid / 4, a_k = (tid % 4) * 4;
@@ -437,16 +467,31 @@ __global__ void __launch_bounds__(256) k_beam_from_vis(const float* __restrict__
 int beam_vis_rows(int n_ant) { return ((n_ant * (n_ant + 1) + kVisBK - 1) / kVisBK) * kVisBK; }
 int beam_vis_ld(int n_pix) { return ((n_pix + kVisBN - 1) / kVisBN) * kVisBN; }
 
+cudaError_t launch_beam_from_vis_batch(const VisJob* jobs, int n_jobs, const float* wvis,
+                                       int n_ant, int n_pix, cudaStream_t st) {
+  if (n_jobs < 1 || n_jobs > kCorrBatchMax) return cudaErrorInvalidValue;
+  if (n_pix <= 0) return cudaSuccess;
+  VisBatch b{};
+  long long max_rows = 0;
+  for (int i = 0; i < n_jobs; i++) {
+    b.job[i] = jobs[i];
+    max_rows = std::max(max_rows, jobs[i].n_rows);
+  }
+  if (max_rows <= 0) return cudaSuccess;
+  const long long n_x = (max_rows + kVisBM - 1) / kVisBM;
+  if (n_x >= (1LL << 31)) return cudaErrorInvalidConfiguration;
+  const int K = n_ant * (n_ant + 1);  // 2 n_pair real columns
+  dim3 grid((unsigned)n_x, (n_pix + kVisBN - 1) / kVisBN, (unsigned)n_jobs);
+  k_beam_from_vis<<<grid, 256, 0, st>>>(b, K, wvis, beam_vis_ld(n_pix), n_pix);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_beam_from_vis(const float2* V, const float* wvis, int n_ant, int n_pix,
                                  long long first, long long last, float* pow, cudaStream_t st,
                                  const int* dump_list, long long n_list) {
   if (n_pix <= 0 || (dump_list ? n_list <= 0 : last < first)) return cudaSuccess;
-  const int K = n_ant * (n_ant + 1);  // 2 n_pair real columns
-  const long long n = dump_list ? n_list : last - first + 1;
-  dim3 grid((unsigned)((n + kVisBM - 1) / kVisBM), (n_pix + kVisBN - 1) / kVisBN);
-  k_beam_from_vis<<<grid, 256, 0, st>>>(reinterpret_cast<const float*>(V), K, wvis,
-                                        beam_vis_ld(n_pix), n_pix, first, n, dump_list, pow);
-  return cudaGetLastError();
+  const VisJob j{V, pow, first, dump_list ? n_list : last - first + 1, dump_list};
+  return launch_beam_from_vis_batch(&j, 1, wvis, n_ant, n_pix, st);
 }
 
 // ------------------------------------------------------------------ beamform

@@ -145,6 +145,28 @@ cudaError_t launch_cpi_tc_image(const float2* X, uint8_t* bimg, const uint8_t* a
                                 int n_pix, float* E, int* err, cudaStream_t st);
 
 // ---- back-ends (backends.cu) ----
+// Up to kCorrBatchMax DMs' back-ends in one launch (grid dimension z = DM):
+// the correlator over DM j's voltages y (float2, or BF16 pairs), dumps
+// m_base .. m_base + n_m - 1 or dump_list[0 .. n_m) (device), into vis; and
+// the beams from visibilities V of rows first .. first + n_rows - 1 or
+// dump_list[0 .. n_rows) into pow.
+constexpr int kCorrBatchMax = kMaxChirps;
+struct CorrJob {
+  const void* y;
+  float2* vis;
+  long long m_base, n_m, first, last;
+  const int* dump_list;
+};
+struct VisJob {
+  const float2* V;
+  float* pow;
+  long long first, n_rows;
+  const int* dump_list;
+};
+cudaError_t launch_correlate_batch(const CorrJob* jobs, int n_jobs, bool bf16, long long n_samp,
+                                   int n_ant, int dump_len, cudaStream_t st);
+cudaError_t launch_beam_from_vis_batch(const VisJob* jobs, int n_jobs, const float* wvis,
+                                       int n_ant, int n_pix, cudaStream_t st);
 // dumps m_base .. m_base + n_m - 1, or dump_list[0 .. n_m) when dump_list is a
 // device array (zeros for dumps outside [first, last])
 cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int dump_len,

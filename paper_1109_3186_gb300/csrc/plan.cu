@@ -128,7 +128,8 @@ struct chirp_plan {
   int dm_chunk = 1;          // DMs of one group whose row passes run together
   long long h_stride = 0;    // elements between chirp tables
   size_t z_stride = 0;       // elements between the DMs' inverse workspaces
-  float2* d_y = nullptr;     // dedispersed voltages of one DM [M][N] (allocated on first use)
+  float2* d_y = nullptr;     // dedispersed voltages [y_slots][M][N] (allocated on first use)
+  int y_slots = 1;           // DMs of a chunk whose voltages are held at once
   // CHIRP_FLAG_LEAN: one spectra buffer shared by the groups, each group's
   // spectra formed right before its DMs (spec_group: the group it holds)
   bool lean = false;
@@ -140,7 +141,8 @@ struct chirp_plan {
   uint8_t* d_bimg = nullptr; // tensor-core B image of one DM (split-BF16 voltages)
   size_t bimg_bytes = 0;
   int* d_err = nullptr;      // device status word (bounded waits that timed out)
-  float2* d_V = nullptr;     // visibilities of one DM [n_dump][n_pair] (beam mode VIS)
+  float2* d_V = nullptr;     // visibilities [dm_chunk][n_dump][n_pair] (beam mode VIS)
+  size_t v_stride = 0;       // elements between the DMs' visibilities
   float* d_wpair = nullptr;  // real pair weights, beam_vis_rows x beam_vis_ld (beam mode VIS)
   // true-delay beams (chirp_truedelay_run), allocated on first use
   float2* d_tdY = nullptr;   // beam spectra of a chunk of (block, pixel) sequences
@@ -224,9 +226,14 @@ int dev_alloc(chirp_plan* p, void** ptr, size_t bytes, const char* what) {
 
 // The dedispersed-voltage buffer, allocated on the first call that needs it
 // (the tensor-core beam path writes its own image and never does).
+// Full searches keep one slot per DM of a row-pass chunk (unless the plan is
+// lean or the slots would pass 4 GB), so that the chunk's back-ends run as
+// one batched launch.
 int ensure_y(chirp_plan* p) {
   if (p->d_y) return CHIRP_OK;
-  return dev_alloc(p, (void**)&p->d_y, (size_t)p->M * p->N * sizeof(float2), "voltages");
+  const size_t slot = (size_t)p->M * p->N * sizeof(float2);
+  p->y_slots = !p->lean && p->dm_chunk > 1 && p->dm_chunk * slot <= (4ull << 30) ? p->dm_chunk : 1;
+  return dev_alloc(p, (void**)&p->d_y, p->y_slots * slot, "voltages");
 }
 
 void release(chirp_plan* p) {
@@ -693,7 +700,8 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   std::vector<uint8_t> aimg;
   std::vector<float> wpair;
   if (!rc && p->n_pix > 0 && vis_beams(p)) {
-    rc = dev_alloc(p, (void**)&p->d_V, (size_t)std::max(1LL, p->n_dump) * p->n_pair * sizeof(float2),
+    p->v_stride = (size_t)std::max(1LL, p->n_dump) * p->n_pair;
+    rc = dev_alloc(p, (void**)&p->d_V, (size_t)p->dm_chunk * p->v_stride * sizeof(float2),
                    "visibilities");
     const size_t wrows = (size_t)beam_vis_rows(p->M), wld = (size_t)beam_vis_ld(p->n_pix);
     if (!rc) rc = dev_alloc(p, (void**)&p->d_wpair, wrows * wld * sizeof(float), "pair weights");
@@ -1115,14 +1123,15 @@ bool bf16_y(const chirp_plan* p, Backend be) {
 // blocks) with the output the back-end reads: FP32 voltages, BF16 voltages,
 // or the tensor-core beamformer's image.
 cudaError_t column_pass(chirp_plan* p, int d, Backend be, const float2* Z, long long q0,
-                        long long nq, const int* blist) {
+                        long long nq, const int* blist, float2* y = nullptr) {
   const DmInfo& I = p->dmi[d];
   const GroupGeom& G = p->groups[I.group].geom;
+  if (!y) y = p->d_y;
   if (bf16_y(p, be))
-    return launch_inverse_cols_bf16(Z, p->d_y, p->N, p->M, q0, nq, G, I.n_hi, I.n_lo, p->tw(),
+    return launch_inverse_cols_bf16(Z, y, p->N, p->M, q0, nq, G, I.n_hi, I.n_lo, p->tw(),
                                     p->stream, blist);
   const BeamImageOut img = fused_image(p, be) ? beam_image_for(p, d) : BeamImageOut{};
-  return launch_inverse_cols(Z, p->d_y, p->N, p->M, q0, nq, G, I.n_hi, I.n_lo, p->tw(), p->stream,
+  return launch_inverse_cols(Z, y, p->N, p->M, q0, nq, G, I.n_hi, I.n_lo, p->tw(), p->stream,
                              blist, fused_image(p, be) ? &img : nullptr);
 }
 
@@ -1239,11 +1248,51 @@ int selected_backend(chirp_plan* p, int d, Backend be, void* dout, const Selecti
   return CHIRP_OK;
 }
 
+// The back-ends of a chunk batch into one correlator launch (and one launch
+// of beams from visibilities) when they run on the staged CUDA-core
+// correlator -- the choice backend_dumps makes -- and every DM of the chunk
+// has its own voltage slot.
+bool batched_backend(const chirp_plan* p, Backend be) {
+  if (p->y_slots < p->dm_chunk || p->dm_chunk < 2) return false;
+  if (be == kCorrelate) return p->corr_mode == CHIRP_CORR_FP32_SIMT;
+  return vis_beams(p) && (p->beam_mode == CHIRP_BEAM_VIS_BF16 ||
+                          p->corr_mode == CHIRP_CORR_FP32_SIMT || !p->corr_forced);
+}
+
+// Back-ends of the chunk's DMs ds[0 .. n), DM ds[j]'s voltages in slot j:
+// over their valid dumps, or over their selected dumps.
+int batched_backends(chirp_plan* p, Backend be, void* dout, const int* ds, int n,
+                     const Selection* sel) {
+  CorrJob cj[kCorrBatchMax];
+  VisJob vj[kCorrBatchMax];
+  const size_t slot = (size_t)p->M * p->N;
+  for (int j = 0; j < n; j++) {
+    const int d = ds[j];
+    const DmInfo& I = p->dmi[d];
+    const int* dl = sel ? sel->d_lists + sel->off[d] : nullptr;
+    const long long n_m = sel ? sel->n[d] : I.last - I.first + 1;
+    float2* vis = be == kCorrelate ? (float2*)dout + (size_t)d * p->n_dump * p->n_pair
+                                   : p->d_V + (size_t)j * p->v_stride;
+    cj[j] = CorrJob{p->d_y + (size_t)j * slot, vis, I.first, n_m, I.first, I.last, dl};
+    vj[j] = VisJob{vis, (float*)dout + (size_t)d * p->n_dump * p->n_pix, I.first, n_m, dl};
+  }
+  int mk = mark_begin(p, CHIRP_STAGE_CORRELATE);
+  CK(launch_correlate_batch(cj, n, bf16_y(p, be), p->N, p->M, p->L, p->stream));
+  mark_end(p, CHIRP_STAGE_CORRELATE, mk);
+  if (be == kBeams) {
+    mk = mark_begin(p, CHIRP_STAGE_BEAMFORM);
+    CK(launch_beam_from_vis_batch(vj, n, p->d_wpair, p->M, p->n_pix, p->stream));
+    mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
+  }
+  return CHIRP_OK;
+}
+
 // The whole search with the row passes of up to dm_chunk DMs of a group in
 // one launch: per chunk the chirp tables, one multi-DM row pass, then per
-// DM the column pass (voltages or the beam image) and the back-end.  With a
-// selection: only the groups it marks dense, only their DMs with a selected
-// dump, and the back-end over the selected dumps.
+// DM the column pass (voltages or the beam image) and the back-end, or, when
+// the back-ends batch, the column passes into the DMs' slots and then one
+// batched back-end.  With a selection: only the groups it marks dense, only
+// their DMs with a selected dump, and the back-end over the selected dumps.
 int full_search_chunked(chirp_plan* p, Backend be, void* dout, const Selection* sel = nullptr) {
   for (size_t gi = 0; gi < p->groups.size(); gi++) {
     Group& grp = p->groups[gi];
@@ -1267,15 +1316,23 @@ int full_search_chunked(chirp_plan* p, Backend be, void* dout, const Selection* 
       CK(launch_inverse_rows_multi(grp.d_spec, p->d_Z, (long long)p->z_stride, p->d_H,
                                    p->h_stride, n, nq, G, p->tw(), grp.d_rtw, p->stream));
       mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
+      const bool batch = n > 1 && batched_backend(p, be);
       for (int j = 0; j < n; j++) {
         const int d = dms[c0 + j];
         const DmInfo& I = p->dmi[d];
         mk = mark_begin(p, CHIRP_STAGE_INV_COLS);
-        CK(column_pass(p, d, be, p->d_Z + (size_t)j * p->z_stride, 0, nq, nullptr));
+        CK(column_pass(p, d, be, p->d_Z + (size_t)j * p->z_stride, 0, nq, nullptr,
+                       batch ? p->d_y + (size_t)j * p->M * p->N : nullptr));
         mark_end(p, CHIRP_STAGE_INV_COLS, mk);
+        if (batch) continue;
         int rc = sel ? selected_backend(p, d, be, dout, *sel)
                      : backend_dumps(p, d, be, I.first, I.last + 1, dout);
         if (!rc) rc = drain_dm(p, d);
+        if (rc) return rc;
+      }
+      if (batch) {
+        int rc = batched_backends(p, be, dout, dms.data() + c0, n, sel);
+        for (int j = 0; j < n && !rc; j++) rc = drain_dm(p, dms[c0 + j]);
         if (rc) return rc;
       }
     }
