@@ -21,6 +21,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "fft.cuh"
 #include "internal.h"
 
@@ -191,16 +193,29 @@ __global__ void k_row_twiddles(float2* __restrict__ rtw, int n1, int T, int log2
 // Row pass: X * H on load, IFFT of length L = n2, twiddle W_N^(-n2 k1) on
 // store.  One CTA per (C rows, sequence); H comes from the per-DM table, the
 // per-thread twiddle factor W_N^(k1 jt) from the group's row table.
+// Per-DM block lists of one launch (grid dimension z = DM): DM j's
+// sequences are its listed blocks' (n_seq[j] = listed blocks x antennas), or
+// q0 .. q0 + n_seq[j] - 1 without a list.
+struct RowLists {
+  const int* blk_list[kMaxChirps];
+  long long n_seq[kMaxChirps];
+};
+
 template <int L>
 __global__ void __launch_bounds__(256, 4) k_inv_rows(const float2* __restrict__ spec,
-                                                  float2* __restrict__ Z,
-                                                  const float2* __restrict__ H, int n1,
-                                                  int log2n, long long q0,
-                                                  const int* __restrict__ blk_list, int n_ant,
-                                                  TwiddlePtrs twp,
+                                                  float2* __restrict__ Z, long long z_stride,
+                                                  const float2* __restrict__ H,
+                                                  long long h_stride, int n1, int log2n,
+                                                  long long q0,
+                                                  const __grid_constant__ RowLists lists,
+                                                  int n_ant, TwiddlePtrs twp,
                                                   const float2* __restrict__ rtw) {
   constexpr int C = 4096 / L;
   constexpr int T = L / 16;
+  if (blockIdx.y >= lists.n_seq[blockIdx.z]) return;  // this DM lists fewer blocks
+  const int* __restrict__ blk_list = lists.blk_list[blockIdx.z];
+  Z += blockIdx.z * z_stride;
+  H += blockIdx.z * h_stride;
   __shared__ float2 sm[FftTile<L, C>::SLOTS];
   const Twiddles tw = mk_tw(twp);
   const int jt = threadIdx.x % T, s = threadIdx.x / T;
@@ -490,21 +505,49 @@ cudaError_t launch_chirp_table(const double* G, float2* H, double dm, const Grou
   return cudaGetLastError();
 }
 
-cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, long long q0,
-                                long long nq, const GroupGeom& g, TwiddlePtrs tw,
-                                const float2* rtw, cudaStream_t st, const int* blk_list,
-                                int n_ant) {
+static cudaError_t inverse_rows(const float2* spec, float2* Z, long long z_stride,
+                                const float2* H, long long h_stride, int n_dm, long long q0,
+                                const RowLists& lists, int n_ant, const GroupGeom& g,
+                                TwiddlePtrs tw, const float2* rtw, cudaStream_t st) {
+  if (n_dm < 1 || n_dm > kMaxChirps) return cudaErrorInvalidValue;
+  long long nq = 0;
+  for (int j = 0; j < n_dm; j++) nq = std::max(nq, lists.n_seq[j]);
   if (nq > 65535 || nq < 1) return cudaErrorInvalidConfiguration;
   const int C = 4096 / g.n2;
-  dim3 grid((g.n1 + C - 1) / C, (unsigned)nq);
+  dim3 grid((g.n1 + C - 1) / C, (unsigned)nq, (unsigned)n_dm);
   switch (g.n2) {
 #define X(L) \
-  case L: k_inv_rows<L><<<grid, 256, 0, st>>>(spec, Z, H, g.n1, g.log2n, q0, blk_list, n_ant, tw, rtw); break;
+  case L: k_inv_rows<L><<<grid, 256, 0, st>>>(spec, Z, z_stride, H, h_stride, g.n1, g.log2n, q0, lists, n_ant, tw, rtw); break;
     CHIRP_SIZES(X)
 #undef X
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, long long q0,
+                                long long nq, const GroupGeom& g, TwiddlePtrs tw,
+                                const float2* rtw, cudaStream_t st, const int* blk_list,
+                                int n_ant) {
+  RowLists lists{};
+  lists.blk_list[0] = blk_list;
+  lists.n_seq[0] = nq;
+  return inverse_rows(spec, Z, 0, H, 0, 1, q0, lists, n_ant, g, tw, rtw, st);
+}
+
+cudaError_t launch_inverse_rows_lists(const float2* spec, float2* Z, long long z_stride,
+                                      const float2* H, long long h_stride, int n_dm,
+                                      const int* const* blk_lists, const long long* n_list,
+                                      int n_ant, const GroupGeom& g, TwiddlePtrs tw,
+                                      const float2* rtw, cudaStream_t st) {
+  if (n_dm < 1 || n_dm > kMaxChirps) return cudaErrorInvalidValue;
+  RowLists lists{};
+  for (int j = 0; j < n_dm; j++) {
+    if (!blk_lists[j] || n_list[j] < 0) return cudaErrorInvalidValue;
+    lists.blk_list[j] = blk_lists[j];
+    lists.n_seq[j] = n_list[j] * n_ant;
+  }
+  return inverse_rows(spec, Z, z_stride, H, h_stride, n_dm, 0, lists, n_ant, g, tw, rtw, st);
 }
 
 cudaError_t launch_inverse_rows_multi(const float2* spec, float2* Z, long long z_stride,

@@ -86,6 +86,14 @@ cudaError_t launch_inverse_rows(const float2* spec, float2* Z, const float2* H, 
                                 long long nq, const GroupGeom& g, TwiddlePtrs tw,
                                 const float2* rtw, cudaStream_t st,
                                 const int* blk_list = nullptr, int n_ant = 1);
+// The row pass of n_dm <= kMaxChirps DMs, each over its own listed blocks, in
+// one launch (grid dimension z = DM): DM d multiplies by H + d h_stride, takes
+// the n_list[d] blocks of blk_lists[d] (device) and writes Z + d z_stride.
+cudaError_t launch_inverse_rows_lists(const float2* spec, float2* Z, long long z_stride,
+                                      const float2* H, long long h_stride, int n_dm,
+                                      const int* const* blk_lists, const long long* n_list,
+                                      int n_ant, const GroupGeom& g, TwiddlePtrs tw,
+                                      const float2* rtw, cudaStream_t st);
 // The row pass of all (antenna, block) sequences of a group for n_dm DMs at
 // once: DM d multiplies by H + d h_stride and writes Z + d z_stride.
 cudaError_t launch_inverse_rows_multi(const float2* spec, float2* Z, long long z_stride,

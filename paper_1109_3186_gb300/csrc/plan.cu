@@ -1340,13 +1340,89 @@ int full_search_chunked(chirp_plan* p, Backend be, void* dout, const Selection* 
   return CHIRP_OK;
 }
 
+// The selected DMs of the groups a selection does not mark dense, per chunk
+// of up to dm_chunk DMs of a group: one chirp-table launch, one row pass over
+// each DM's listed blocks (blk_off/blk_n into the device lists), the column
+// passes over the same blocks, then the back-ends over the selected dumps
+// (one batched launch where they batch).  A DM whose listed blocks do not fit
+// a workspace slot runs alone, its list in pieces.
+int sparse_search(chirp_plan* p, Backend be, void* dout, const Selection& sel,
+                  const std::vector<char>& dense, const std::vector<long long>& blk_off,
+                  const std::vector<long long>& blk_n) {
+  std::vector<int> dms;
+  for (size_t gi = 0; gi < p->groups.size(); gi++) {
+    if (dense[gi]) continue;
+    Group& g = p->groups[gi];
+    const GroupGeom& G = g.geom;
+    dms.clear();
+    for (int d : g.dms)
+      if (p->dmi[d].last >= p->dmi[d].first && sel.n[d] > 0) dms.push_back(d);
+    if (dms.empty()) continue;
+    int rc = ensure_spec(p, (int)gi);
+    if (rc) return rc;
+    const long long cap = (long long)(p->z_stride / (size_t)G.nfft) / p->M;  // blocks per slot
+    for (size_t c0 = 0; c0 < dms.size();) {
+      int n = (int)std::min((size_t)std::max(1, p->dm_chunk), dms.size() - c0);
+      for (int j = 0; j < n; j++)
+        if (blk_n[dms[c0 + j]] > cap) n = j == 0 ? 1 : std::min(n, j);
+      const int* bl[kMaxChirps];
+      long long nb[kMaxChirps];
+      double dmv[kMaxChirps];
+      for (int j = 0; j < n; j++) {
+        dmv[j] = p->dm[dms[c0 + j]];
+        bl[j] = p->d_lists + blk_off[dms[c0 + j]];
+        nb[j] = blk_n[dms[c0 + j]];
+      }
+      int mk = mark_begin(p, CHIRP_STAGE_CHIRP);
+      CK(launch_chirp_tables(g.d_G, p->d_H, p->h_stride, dmv, n, G, p->stream));
+      mark_end(p, CHIRP_STAGE_CHIRP, mk);
+      if (n == 1) {  // a lone DM: its list in pieces of at most a slot's blocks
+        const int d = dms[c0];
+        const long long piece = std::max(1LL, cap);
+        for (long long k0 = 0; k0 < nb[0]; k0 += piece) {
+          const int* blp = bl[0] + k0;
+          const long long nbp = std::min(piece, nb[0] - k0);
+          mk = mark_begin(p, CHIRP_STAGE_INV_ROWS);
+          CK(launch_inverse_rows_lists(g.d_spec, p->d_Z, 0, p->d_H, 0, 1, &blp, &nbp, p->M, G,
+                                       p->tw(), g.d_rtw, p->stream));
+          mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
+          mk = mark_begin(p, CHIRP_STAGE_INV_COLS);
+          CK(column_pass(p, d, be, p->d_Z, 0, nbp * p->M, blp));
+          mark_end(p, CHIRP_STAGE_INV_COLS, mk);
+        }
+        rc = selected_backend(p, d, be, dout, sel);
+      } else {
+        mk = mark_begin(p, CHIRP_STAGE_INV_ROWS);
+        CK(launch_inverse_rows_lists(g.d_spec, p->d_Z, (long long)p->z_stride, p->d_H,
+                                     p->h_stride, n, bl, nb, p->M, G, p->tw(), g.d_rtw,
+                                     p->stream));
+        mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
+        // batched: every DM's voltages into its slot, then one back-end launch;
+        // otherwise each DM's column pass right before its own back-end
+        const bool batch = batched_backend(p, be);
+        for (int j = 0; j < n && !rc; j++) {
+          mk = mark_begin(p, CHIRP_STAGE_INV_COLS);
+          CK(column_pass(p, dms[c0 + j], be, p->d_Z + (size_t)j * p->z_stride, 0, nb[j] * p->M,
+                         bl[j], batch ? p->d_y + (size_t)j * p->M * p->N : nullptr));
+          mark_end(p, CHIRP_STAGE_INV_COLS, mk);
+          if (!batch) rc = selected_backend(p, dms[c0 + j], be, dout, sel);
+        }
+        if (batch && !rc) rc = batched_backends(p, be, dout, dms.data() + c0, n, &sel);
+      }
+      if (rc) return rc;
+      c0 += (size_t)n;
+    }
+  }
+  return CHIRP_OK;
+}
+
 // The whole search, or (mask != NULL) only the (DM, dump) cells whose mask
 // byte is nonzero; outputs are zero elsewhere.  A selective search lists, per
 // DM, its selected valid dumps and the blocks that own them.  An FFT-length
 // group whose DMs need at least kDenseBlocks of their (DM, block) pairs runs
 // the full multi-DM inverse and restricts only the back-end to the listed
 // dumps; the other groups inverse-transform, per DM, just the listed blocks
-// (runs of block indices per launch).  Per block the per-DM form costs ~1.2x
+// (up to dm_chunk DMs per launch, sparse_search).  Per block the per-DM form costs ~1.2x
 // in the row pass and ~2x in the chirp tables (the multi-DM forms read each
 // spectrum and phase table once for up to 4 DMs), so it wins below ~85 %.
 constexpr double kDenseBlocks = 0.85;
@@ -1409,26 +1485,7 @@ int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Bac
     sel.dense_group = dense.data();
     rc = full_search_chunked(p, be, dout, &sel);
     if (rc) return rc;
-    for (int d = 0; d < (int)p->dm.size(); d++) {
-      const DmInfo& I = p->dmi[d];
-      if (I.last < I.first || dense[I.group] || dmp_n[d] == 0) continue;
-      const GroupGeom& G = p->groups[I.group].geom;
-      Group& g = p->groups[I.group];
-      rc = ensure_spec(p, I.group);
-      if (!rc) rc = chirp_for(p, d);
-      if (rc) return rc;
-      const int* blist = p->d_lists + blk_off[d];
-      int mk = mark_begin(p, CHIRP_STAGE_INV_ROWS);
-      CK(launch_inverse_rows(g.d_spec, p->d_Z, p->d_H, 0, blk_n[d] * p->M, G, p->tw(), g.d_rtw,
-                             p->stream, blist, p->M));
-      mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
-      mk = mark_begin(p, CHIRP_STAGE_INV_COLS);
-      CK(column_pass(p, d, be, p->d_Z, 0, blk_n[d] * p->M, blist));
-      mark_end(p, CHIRP_STAGE_INV_COLS, mk);
-      rc = selected_backend(p, d, be, dout, sel);
-      if (rc) return rc;
-    }
-    return CHIRP_OK;
+    return sparse_search(p, be, dout, sel, dense, blk_off, blk_n);
   }
   for (int d = 0; d < (int)p->dm.size(); d++) {
     const DmInfo& I = p->dmi[d];

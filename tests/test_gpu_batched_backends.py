@@ -27,14 +27,14 @@ def _scene(M=12, n_dm=9, seed=4100):
                                        n_pulse=1, seed=seed)
 
 
-def _chunks(plan, n_dm):
-    """Row-pass chunks of the full search: per FFT-length group, its DMs with
-    a valid dump taken dm_chunk at a time."""
+def _chunks(plan, n_dm, dms=None):
+    """Row-pass chunks of the full search (or of a search over the DMs dms):
+    per FFT-length group, its DMs with a valid dump taken dm_chunk at a time."""
     first, last = plan.dump_range()
     groups = {}
-    for d in range(n_dm):
+    for d in range(n_dm) if dms is None else dms:
         if last[d] >= first[d]:
-            groups.setdefault(plan.dm_layout(d)["nfft"], []).append(d)
+            groups.setdefault(plan.dm_layout(int(d))["nfft"], []).append(d)
     k = plan.info["dm_chunk"]
     return sum((len(v) + k - 1) // k for v in groups.values()), \
         sum(len(v) for v in groups.values())
@@ -113,4 +113,40 @@ def test_dense_selection_batched_with_dump_lists():
     r = ref.cpu().numpy()
     s = out["full"].numpy()
     assert np.array_equal(s[pick], r[pick])
+    assert np.all(s[~pick] == 0)
+
+
+@pytest.mark.parametrize("mode", [chirp.BEAM_VIS, chirp.BEAM_TC_3XBF16])
+def test_run_selection_chunks_share_row_passes(mode):
+    """Runs of a few dumps per DM: each group's DMs go through one row pass
+    over their own listed blocks per chunk, then the column passes and the
+    back-ends (batched in the visibility form, one DM after another for the
+    tensor-core beams); the full plan, the lean plan and the full search agree
+    bit for bit on the selected cells, all other cells are zero."""
+    sc = _scene(seed=4400)
+    full, lean = _pair(sc, beam_mode=mode)
+    xd = torch.from_numpy(sc.voltages()).cuda()
+    shp = (len(sc.dms), full.n_dump, full.n_pix)
+    ref = torch.empty(shp, dtype=torch.float32, device="cuda")
+    full.chimageator(xd, ref)
+    first, last = full.dump_range()
+    mask = np.zeros((len(sc.dms), full.n_dump), np.uint8)
+    rng = np.random.default_rng(9)
+    for d in range(len(sc.dms)):
+        if last[d] - first[d] > 8:
+            m0 = int(rng.integers(first[d], last[d] - 4))
+            mask[d, m0:m0 + 3] = 1
+    pick = mask.astype(bool)
+    out = {}
+    for name, pl in (("full", full), ("lean", lean)):
+        S = torch.full(shp, 5.0, dtype=torch.float32, device="cuda")
+        pl.stage_timing(True, stages=["inv_rows"])
+        pl.chimageator_selective(xd, mask, S)
+        n_rows = pl.stage_timing(False)["inv_rows"][1]
+        n_chunk, n_sel = _chunks(pl, len(sc.dms), np.nonzero(pick.any(axis=1))[0])
+        assert n_rows == n_chunk < n_sel, (name, n_rows, n_chunk)
+        out[name] = S.cpu()
+    assert torch.equal(out["full"], out["lean"])
+    s = out["full"].numpy()
+    assert np.array_equal(s[pick], ref.cpu().numpy()[pick])
     assert np.all(s[~pick] == 0)

@@ -107,9 +107,10 @@ def test_scattered_selections_equal_full(frac):
 
 
 def test_run_selections_equal_full_with_per_dm_blocks():
-    """Runs of a few dumps need few blocks: per-DM block lists, the full
-    search's values bit for bit there and zeros elsewhere; a search mixing a
-    scattered group and a run-shaped one takes both paths at once."""
+    """Runs of a few dumps need few blocks: per-DM block lists (the DMs of a
+    group share a row-pass launch), the full search's values bit for bit there
+    and zeros elsewhere; a search mixing a scattered group and a run-shaped
+    one takes both paths at once."""
     sc = skymodel.chirpolator_small(n_samp=1 << 18, n_dm=5, dm_max=100.0, nfft_min=1 << 15)
     x = sc.voltages()
     plan = chirp.Plan.from_scenario(sc)
@@ -122,8 +123,15 @@ def test_run_selections_equal_full_with_per_dm_blocks():
     mask = _runs_mask(valid, 5)
     sel = np.full_like(full, np.complex64(7 + 7j))
     n_rows = _row_launches(plan, lambda: plan.chirpolator_selective(x, mask, sel))
-    n_sel_dms = int(np.sum((mask.astype(bool) & valid).any(axis=1)))
-    assert n_sel_dms >= 4 and n_rows == n_sel_dms  # one row pass per DM
+    sel_dms = np.nonzero((mask.astype(bool) & valid).any(axis=1))[0]
+    assert len(sel_dms) >= 4
+    # one row pass per chunk of up to dm_chunk DMs of an FFT-length group,
+    # each DM over its own listed blocks
+    per_group = {}
+    for d in sel_dms:
+        per_group[plan.dm_layout(int(d))["nfft"]] = per_group.get(plan.dm_layout(int(d))["nfft"], 0) + 1
+    k = plan.info["dm_chunk"]
+    assert n_rows == sum((c + k - 1) // k for c in per_group.values())
     pick = mask.astype(bool) & valid
     assert np.array_equal(sel[pick], full[pick])
     assert np.all(sel[~pick] == 0)
