@@ -72,6 +72,10 @@ def parse_args():
     ap.add_argument("--truedelay-only", action="store_true",
                     help="time only the true-delay beams (8 x 8 pixels) on the same workload (for "
                          "profiling their kernels); prints one line")
+    ap.add_argument("--precision-only", action="store_true",
+                    help="time only the 36-antenna int8 channel leg; with --n-samp and --dms "
+                         "(profiling: the lowest DMs of its 256, which stay valid on a shorter "
+                         "series) only the library's choice of form; prints one line")
     ap.add_argument("--cpu-dumps", type=int, default=640,
                     help="dumps per selected DM in the oracle's bounded CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -949,6 +953,12 @@ def precision_channel_leg(stream, peaks, peak_kind, args):
     import paper_1109_3186_gb300 as chirp
     from paper_1109_3186_gb300 import skymodel
     sc = skymodel.precision_form(channel=0, n_pulse=0)
+    reduced = args.precision_only and (args.n_samp or args.dms)
+    if reduced:  # profiling: a shorter series and the lowest DMs
+        if args.n_samp:
+            sc.n_samp = args.n_samp
+        if args.dms:
+            sc.dms = sc.dms[:args.dms]
     M, N = sc.n_ant, sc.n_samp
     g = torch.Generator(device="cuda").manual_seed(1003)
     q = torch.randn((M, N, 2), generator=g, device="cuda").mul_(16.0).round_().clamp_(-127, 127)
@@ -960,6 +970,10 @@ def precision_channel_leg(stream, peaks, peak_kind, args):
     forms = (("auto", dict()),
              ("vis_corr_tc_bf16", dict(beam_mode=chirp.BEAM_VIS, corr_mode=chirp.CORR_TC_BF16)),
              ("tc_bf16", dict(beam_mode=chirp.BEAM_TC_BF16)))
+    if reduced:
+        forms = forms[:1]
+        out["workload"] = "REDUCED (profiling): " + out["workload"] + \
+            ", here %d samples, %d DMs" % (N, len(sc.dms))
     P = None
     for name, kw in forms:
         plan = chirp.Plan.from_scenario(sc, stream=stream, in_type=chirp.IN_CI8, in_scale=scale,
@@ -1011,9 +1025,14 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
+    stream = torch.cuda.current_stream()
+    if args.precision_only:
+        line = precision_channel_leg(stream, *load_peaks(), args)
+        line["mode"] = "precision_36ant_channel"
+        print(json.dumps(line), flush=True)
+        return 0
     sc = scenario(rank, args)
     x = sc.voltages()
-    stream = torch.cuda.current_stream()
     if args.chirpolator_only:
         return chirpolator_only(sc, x, stream, args)
     if args.chimg_only:

@@ -111,21 +111,27 @@ __device__ __forceinline__ void zero_elem(__nv_bfloat162* p) {
 // 96 registers: two CTAs of 10 warps (NT = 4) or three of 6 (NT = 3) per SM
 // (single-warp CTAs, NT = 1, are limited by shared memory instead: 128).
 // Antennas form blocks of BA = 4 NT.  PAIR = false: CTA (dump, I) takes block
-// I = blockIdx.y alone -- its NT (NT + 1) / 2 upper 4 x 4 tiles, one per warp
-// (up to 16 antennas this is the whole product).  PAIR = true: CTA (dump,
-// (I, J)), I < J (blockIdx.y over the strict upper triangle of blocks),
+// I alone -- its NT (NT + 1) / 2 upper 4 x 4 tiles, one per warp (up to 16
+// antennas this is the whole product).  PAIR = true: CTA (dump, (I, J)),
+// I < J (the task index runs over the strict upper triangle of blocks),
 // stages block I's rows, then block J's, and its NT x NT warps each own one
 // 4 x 4 tile of the pairs (block I antenna, block J antenna).
+// task_fast: the task (block or block pair) is grid dimension x and the dump
+// y, so that the CTAs of one dump run together and the block pairs that share
+// a block find its rows in L2; otherwise the dump is x and the task y.
 struct CorrBatch {
   CorrJob job[kCorrBatchMax];
 };
 
 template <typename T, int NT, bool VEC16, bool PAIR>
 __global__ void __maxnreg__(NT == 1 ? 128 : 96)
-    k_correlate_staged(const __grid_constant__ CorrBatch batch, long long n_samp, int M, int L) {
-  // this CTA's DM (grid dimension z) and dump
+    k_correlate_staged(const __grid_constant__ CorrBatch batch, long long n_samp, int M, int L,
+                       int task_fast) {
+  // this CTA's DM (grid dimension z), dump and task
   const CorrJob& job = batch.job[blockIdx.z];
-  if (blockIdx.x >= job.n_m) return;
+  const unsigned dump_i = task_fast ? blockIdx.y : blockIdx.x;
+  const unsigned task = task_fast ? blockIdx.x : blockIdx.y;
+  if (dump_i >= job.n_m) return;
   const T* __restrict__ y = static_cast<const T*>(job.y);
   float2* __restrict__ vis = job.vis;
   const int* __restrict__ dump_list = job.dump_list;
@@ -137,18 +143,18 @@ __global__ void __maxnreg__(NT == 1 ? 128 : 96)
   constexpr int STAGE = ROWS * CH;
   extern __shared__ __align__(16) unsigned char ring_raw[];
   T* ring = reinterpret_cast<T*>(ring_raw);  // [2][ROWS][CH]
-  const long long m = dump_list ? (long long)dump_list[blockIdx.x] : m_base + blockIdx.x;
+  const long long m = dump_list ? (long long)dump_list[dump_i] : m_base + dump_i;
   const int n_pair = M * (M + 1) / 2;
   float2* out = vis + m * n_pair;
   if (m < first || m > last) {
-    if (!PAIR && blockIdx.y == 0)
+    if (!PAIR && task == 0)
       for (int i = threadIdx.x; i < n_pair; i += NTH) out[i] = make_float2(0.f, 0.f);
     return;
   }
-  int I = blockIdx.y, J = I;
+  int I = (int)task, J = I;
   if (PAIR) {  // strict upper triangle of SB x SB blocks, row-major
     const int SB = (M + BA - 1) / BA;
-    int rem = blockIdx.y;
+    int rem = (int)task;
     I = 0;
     while (rem >= SB - 1 - I) {
       rem -= SB - 1 - I;
@@ -291,10 +297,12 @@ static cudaError_t launch_staged(const CorrBatch& b, int n_jobs, long long max_m
   const long long n_y = PAIR ? SB * (SB - 1) / 2 : SB;
   if (n_y < 1) return cudaSuccess;
   if (n_y > 65535) return cudaErrorInvalidConfiguration;
-  dim3 grid((unsigned)max_m, (unsigned)n_y, (unsigned)n_jobs);
+  const int task_fast = n_y > 1 && max_m <= 65535;
+  const dim3 grid = task_fast ? dim3((unsigned)n_y, (unsigned)max_m, (unsigned)n_jobs)
+                              : dim3((unsigned)max_m, (unsigned)n_y, (unsigned)n_jobs);
   k_correlate_staged<T, NT, VEC16, PAIR>
       <<<grid, PAIR ? 32 * NT * NT : 32 * NT * (NT + 1) / 2, smem, st>>>(b, n_samp, n_ant,
-                                                                        dump_len);
+                                                                        dump_len, task_fast);
   return cudaGetLastError();
 }
 
