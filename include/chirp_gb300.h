@@ -176,7 +176,11 @@ typedef struct {
   int n_group;             /* distinct FFT lengths                              */
   long long workspace_bytes;/* device memory owned by the plan (grows on the
                               first run that needs the dedispersed-voltage
-                              buffer or host-buffer staging)                 */
+                              buffer -- one n_ant x n_samp slot per DM of a
+                              row-pass chunk, so that the chunk's back-ends
+                              run as one launch, unless the plan is lean or
+                              the slots would pass 4 GB -- or host-buffer
+                              staging)                                       */
   long long ifft_points;   /* sum over DMs of n_ant * n_blk * Nfft              */
   long long valid_samples; /* sum over DMs of n_ant * (n_samp - n_hi - n_lo)^+  */
   int beam_mode;           /* CHIRP_BEAM_* actually used (AUTO resolved)        */
@@ -185,7 +189,9 @@ typedef struct {
   int corr_mode;           /* CHIRP_CORR_* actually used (AUTO resolved)        */
   int dm_chunk;            /* trial DMs of one FFT-length group whose inverse
                               row passes a full search runs in one launch (the
-                              group's spectra are read once for them)           */
+                              group's spectra are read once for them); the
+                              staged FP32 correlator and the visibility beams
+                              of those DMs also run as one launch each       */
 } chirp_plan_info;
 
 /* Create a plan: validates cfg, derives the per-DM FFT lengths and block
@@ -396,8 +402,9 @@ int chirp_plan_status(chirp_plan* plan);
  * FFT-length group, when the selected DMs need at least 85 % of their
  * (DM, overlap-save block) pairs the group's inverse transforms run in full
  * with the multi-DM row pass (one spectrum read for up to 4 DMs); otherwise
- * only the blocks that own a selected dump are inverse transformed, DM by
- * DM.  The selected cells hold exactly what the full search computes there.
+ * only the blocks that own a selected dump are inverse transformed, each DM
+ * over its own blocks, up to dm_chunk DMs of the group per launch.  The
+ * selected cells hold exactly what the full search computes there.
  * Errors: as the full searches. */
 int chirpolator_run_selective(chirp_plan* plan, const void* volt, int volt_loc,
                               const unsigned char* cell_mask, void* vis_out, int vis_loc);
