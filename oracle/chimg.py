@@ -14,6 +14,9 @@ array, Sec. 4.2):
 5. Trajectory sums (Eq. chimg_pth with the 2F widening of App. B.2.3): for a
    trial DM and direction, P = sum over the window's dumps m' of
    sum_{k = k0'(m') - F}^{k0'(m') + F} w_{k,m'} Y_k[m'], E = |P|^2 (Eq. eth).
+6. The partial-sum recursion of App. B.2.1, in the paper's own model (below
+   image()): trials of one trajectory gradient and intercept read their images
+   from one cumulative sum along the line.
 
 Readings (as for the Chirpolator pre-integrator: a baseband array and a
 window-centred trial arrival):
@@ -121,6 +124,82 @@ def search(y, D, l_dirs, f0, bw, k_dm, dms, L, Ns, F, weights="natural"):
     M = np.asarray(y).shape[0]
     Y = integrate(spatial_dft(mix_grid(y, weights), Ns), L)
     return image(Y, M, D, l_dirs, f0, bw, k_dm, dms, L, Ns, F, weights)
+
+
+# ------------------------------------- App. B.2.1: shared partial sums
+# The paper's own model of Sec. 4.2 (Eq. chimg_xpq with its tau^2 term dropped,
+# natural weights summing to 1 per spacing, a baseband chirp that sweeps 0..B
+# from the window start) puts the spatial tone nu(t) = fdot tau t cycles per
+# spacing on the grid, t counted from the window start: the trajectory
+# k_0(n) = Ns fdot tau n / f_s of Eq. chimgf0 passes through k = 0 at the start
+# with a gradient set by rate = fdot tau alone.  With fdot = B / T a trial of
+# sweep T from direction tau has rate tau B / T, and the trials of one rate --
+# one gradient (Eq. chimg_grad), one intercept -- lie on one line: each one's
+# image over a window starting at dump s is a prefix of one cumulative sum
+# along the line from s (App. B.2.1).
+
+def paper_expected_y(M, rate, bw, L, Ns, m_rel) -> np.ndarray:
+    """Expected Y[k] of a unit chirp in the paper's model, dump m_rel of the
+    window (samples t = (m_rel L + i) / B from the window start)."""
+    t = (m_rel * L + np.arange(L)) / bw
+    xg = np.exp(2j * math.pi * np.outer(np.arange(1, M), rate * t))
+    return spatial_dft(xg, Ns).sum(axis=1)
+
+
+def paper_taps(M, rate, bw, L, Ns, F, n_win):
+    """Per dump r < n_win of the window: the 2F+1 bins around rint(Ns nu) at
+    the dump's centre (mod Ns) and the conjugate expected Y there over
+    (M - 1) L, as in image()."""
+    taps = []
+    for r in range(n_win):
+        yh = paper_expected_y(M, rate, bw, L, Ns, r)
+        kc = int(np.rint(Ns * rate * (r * L + (L - 1) / 2.0) / bw)) % Ns
+        ks = [(kc + j) % Ns for j in range(-F, F + 1)]
+        taps.append((ks, np.conj(yh[ks]) / ((M - 1) * L)))
+    return taps
+
+
+def prefix_sums(Y, taps, start) -> np.ndarray:
+    """S[r] = sum_{r' <= r} sum_j w Y[k][start + r'] along the taps (the
+    cumulative trajectory sum of App. B.2.1), for r < len(taps)."""
+    S = np.zeros(len(taps), np.complex128)
+    acc = 0j
+    for r, (ks, w) in enumerate(taps):
+        acc += np.sum(w * Y[ks, start + r])
+        S[r] = acc
+    return S
+
+
+def paper_image_direct(Y, M, rate, n_wins, bw, L, Ns, F) -> np.ndarray:
+    """E[i][m] of the trials with n_wins[i] dumps on the line `rate`, each from
+    its own taps (Eq. chimg_pth), for windows ending at dump m (zero while
+    m < n_win - 1)."""
+    n_dump = Y.shape[1]
+    E = np.zeros((len(n_wins), n_dump))
+    for i, nw in enumerate(n_wins):
+        taps = paper_taps(M, rate, bw, L, Ns, F, nw)
+        for m in range(nw - 1, n_dump):
+            P = 0j
+            for r, (ks, w) in enumerate(taps):
+                P += np.sum(w * Y[ks, m - nw + 1 + r])
+            E[i, m] = abs(P) ** 2
+    return E
+
+
+def paper_image_shared(Y, M, rate, n_wins, bw, L, Ns, F) -> np.ndarray:
+    """The same images by the recursion of App. B.2.1: one cumulative sum
+    along the line per window start, with the longest trial's taps, read at
+    each trial's length."""
+    n_dump = Y.shape[1]
+    n_max = max(n_wins)
+    taps = paper_taps(M, rate, bw, L, Ns, F, n_max)
+    E = np.zeros((len(n_wins), n_dump))
+    for s in range(n_dump):
+        S = prefix_sums(Y, taps[:min(n_max, n_dump - s)], s)
+        for i, nw in enumerate(n_wins):
+            if nw <= len(S):
+                E[i, s + nw - 1] = abs(S[nw - 1]) ** 2
+    return E
 
 
 # ------------------------------------------------ uniform rectangular array
