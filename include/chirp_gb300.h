@@ -602,6 +602,33 @@ int chirp_chimg_grid(chirp_chimg_plan* plan, const void* volt, int volt_loc, voi
 int chirp_chimg_run(chirp_chimg_plan* plan, const void* volt, int volt_loc, float* energy, int out_loc);
 void chirp_chimg_destroy(chirp_chimg_plan* plan);
 
+/* The partial-sum recursion of the imaging step (App. B.2.1): trajectories
+ * of one gradient (Eq. chimg_grad) and one intercept lie on one line, and
+ * every trial on it is a prefix of one cumulative sum along the line.  This
+ * holds in the paper's own model of Sec. 4.2 -- natural weights, Eq.
+ * chimg_xpq without its tau^2 term, a baseband chirp sweeping 0..B from the
+ * window start -- where a unit chirp puts the tone nu(t) = rate t cycles per
+ * spacing on the grid (rate = fdot tau, t from the window start) and every
+ * trajectory starts at k = 0; it does not hold in the carrier-aware model of
+ * chirp_chimg_run, whose trials of equal gradient differ in intercept.
+ * For line g (rate[g], HOST [n_line]) and dump r of a window the taps are
+ * the 2F+1 bins around rint(Ns rate t_r) mod Ns at the dump's centre t_r,
+ * w = conj(Yhat) / ((M - 1) L) with Yhat the expected Y of the unit chirp
+ * (FP64 closed form).  One cumulative sum per (line, window start s) over
+ * Y (DEVICE complex64 [n_dump][Ns], as chirp_chimg_grid writes it with
+ * natural weights) gives each trial t of the line, of n_t dumps,
+ * energy[t][s + n_t - 1] = |P|^2 (Eq. eth); energy is DEVICE float
+ * [n_trial][n_dump], zero where a window is incomplete.  Trials are given in
+ * CSR form: trial_off (HOST [n_line + 1], trial_off[0] = 0) and trial_len
+ * (HOST [n_trial], >= 1, ascending within a line).  Allocates and frees its
+ * own device scratch and synchronises stream.  CHIRP_EINVAL for a bad shape,
+ * lengths or non-device Y / energy; CHIRP_EUNSUPPORTED past 2^26 taps rows;
+ * CHIRP_ENOMEM, CHIRP_ECUDA. */
+int chirp_chimg_lines_run(const void* Y, long long n_dump, int n_ant, int n_spatial, int dump_len,
+                          double bw_hz, int half_width, const double* rate, int n_line,
+                          const int* trial_off, const int* trial_len, float* energy,
+                          void* stream);
+
 /* ------------------------------------------------------------------------
  * The same pre-integrator on a uniform RECTANGULAR array (Sec. 4.2 in two
  * dimensions, App. B.2): antenna a = iy n_x + ix at (ix dx_m, iy dy_m, 0).

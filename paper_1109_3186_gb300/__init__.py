@@ -54,7 +54,8 @@ EXPORTED_SYMBOLS = ("chirp_plan_create", "chirp_plan_destroy", "chirp_plan_query
                     "chirp_cpi_query", "chirp_cpi_layout", "chirp_cpi_run", "chirp_cpi_spectra",
                     "chirp_cpi_timing", "chirp_cpi_destroy", "chirp_chimg_create",
                     "chirp_chimg_query", "chirp_chimg_grid", "chirp_chimg_run",
-                    "chirp_chimg_destroy", "chirp_combine_channels", "chirp_chimg2d_create",
+                    "chirp_chimg_destroy", "chirp_chimg_lines_run", "chirp_combine_channels",
+                    "chirp_chimg2d_create",
                     "chirp_chimg2d_query", "chirp_chimg2d_grid", "chirp_chimg2d_run",
                     "chirp_chimg2d_destroy", "chirp_truedelay_run")
 STAGES = ("forward", "inv_rows", "inv_cols", "correlate", "beamform", "split", "chirp",

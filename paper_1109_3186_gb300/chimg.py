@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _buf, _check, _stream_handle, load
 
-__all__ = ["ChimgPlan", "Chimg2dPlan"]
+__all__ = ["ChimgPlan", "Chimg2dPlan", "lines_run"]
 
 
 class _ChimgConfig(ctypes.Structure):
@@ -57,6 +57,10 @@ def _lib():
         lib.chirp_chimg2d_query.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), vp,
                                             ctypes.POINTER(i)]
         lib.chirp_chimg2d_query.restype = i
+        lib.chirp_chimg_lines_run.argtypes = [vp, ctypes.c_longlong, i, i, i, ctypes.c_double, i,
+                                              ctypes.POINTER(ctypes.c_double), i,
+                                              ctypes.POINTER(i), ctypes.POINTER(i), vp, vp]
+        lib.chirp_chimg_lines_run.restype = i
         lib.chirp_chimg2d_grid.argtypes = [vp, vp, i, vp, i]
         lib.chirp_chimg2d_grid.restype = i
         lib.chirp_chimg2d_run.argtypes = [vp, vp, i, vp, i]
@@ -181,3 +185,29 @@ class Chimg2dPlan:
             self.close()
         except Exception:
             pass
+
+
+def lines_run(Y, n_ant, n_spatial, dump_len, bw, half_width, rates, trial_lens, stream=None):
+    """The partial-sum recursion of App. B.2.1 on the paper's own model
+    (chirp_chimg_lines_run): Y is the complex64 CUDA tensor [n_dump][Ns] that
+    ChimgPlan.grid writes with natural weights; rates[g] = fdot tau of line g
+    (cycles per spacing per second); trial_lens[g] the window lengths (dumps)
+    of its trials.  Returns E, a float32 CUDA tensor [n_trial][n_dump], trials
+    in line order and, within a line, by ascending length."""
+    import torch
+    if not (isinstance(Y, torch.Tensor) and Y.is_cuda and Y.dtype == torch.complex64
+            and Y.is_contiguous() and Y.dim() == 2 and Y.shape[1] == n_spatial):
+        raise TypeError("Y must be a contiguous complex64 CUDA tensor [n_dump][n_spatial]")
+    lens = [sorted(int(n) for n in tl) for tl in trial_lens]
+    off = np.zeros(len(lens) + 1, np.int32)
+    off[1:] = np.cumsum([len(tl) for tl in lens])
+    flat = np.array([n for tl in lens for n in tl], np.int32)
+    rt = np.ascontiguousarray(rates, np.float64)
+    E = torch.empty((int(off[-1]), Y.shape[0]), dtype=torch.float32, device=Y.device)
+    _check(_lib().chirp_chimg_lines_run(
+        ctypes.c_void_p(Y.data_ptr()), Y.shape[0], int(n_ant), int(n_spatial), int(dump_len),
+        float(bw), int(half_width), rt.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(lens),
+        off.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+        flat.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.c_void_p(E.data_ptr()),
+        _stream_handle(stream)))
+    return E

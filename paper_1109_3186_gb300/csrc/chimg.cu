@@ -18,6 +18,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 #include <vector>
 
@@ -174,6 +175,84 @@ __global__ void k_chimg_taps(const double* __restrict__ ldir, int n_pix, int M, 
     const double sc = 1.0 / ((double)(M - 1) * L);
     w[idx * nj + j] = make_float2((float)(yr * sc), (float)(-yi * sc));
     bin[idx * nj + j] = (short)k;
+  }
+}
+
+// The partial-sum recursion of App. B.2.1 on the paper's own model of
+// Sec. 4.2: natural weights, Eq. chimg_xpq without its tau^2 term, a baseband
+// chirp sweeping 0..B from the window start.  A unit chirp then puts the tone
+// nu(t) = rate t cycles per spacing on the grid (rate = fdot tau, t from the
+// window start), so every trajectory starts at k = 0 and trials of one rate
+// lie on one line.  Taps of row i (a line's rate and a dump r of its window),
+// FP64: bin = (rint(Ns rate t_r) + j - F) mod Ns at the dump's centre t_r,
+// w = conj(Yhat_bin) / ((M - 1) L) with
+//   Yhat_k = sum_{l=1}^{M-1} exp(-2 pi j k l / Ns) sum_{i<L} exp(2 pi j l rate (rL + i) / B).
+__global__ void k_chimg_line_taps(const double* __restrict__ row_rate, const int* __restrict__ row_r,
+                                  long long n_rows, int M, int L, int Ns, int F, double bw,
+                                  float2* __restrict__ w, short* __restrict__ bin) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_rows) return;
+  const int nj = 2 * F + 1;
+  const double rate = row_rate[i];
+  const double tc = (double)row_r[i] * L + 0.5 * (L - 1);  // the dump's centre, samples
+  double nu = Ns * rate * tc / bw;
+  nu -= Ns * floor(nu / Ns);
+  const long long kc = (long long)rint(nu) % Ns;
+  for (int j = 0; j < nj; j++) {
+    const int k = (int)(((kc + j - F) % Ns + Ns) % Ns);
+    double yr = 0.0, yi = 0.0;
+    for (int l = 1; l < M; l++) {
+      const double phi = l * rate / bw;  // cycles per sample
+      // sum_{i<L} exp(2 pi j phi i) = exp(pi j phi (L - 1)) sin(pi phi L) / sin(pi phi)
+      const double den = sinpi(phi);
+      double amp;
+      if (fabs(den) < 1e-12) {
+        const long long n = (long long)rint(phi);
+        amp = ((n * (L - 1)) & 1) ? -(double)L : (double)L;
+      } else {
+        amp = sinpi(phi * L) / den;
+      }
+      double cyc = phi * tc - (double)((long long)k * l % Ns) / Ns;
+      cyc -= rint(cyc);
+      double sn, cs;
+      sincospi(2.0 * cyc, &sn, &cs);
+      yr += amp * cs;
+      yi += amp * sn;
+    }
+    const double sc = 1.0 / ((double)(M - 1) * L);
+    w[i * nj + j] = make_float2((float)(yr * sc), (float)(-yi * sc));
+    bin[i * nj + j] = (short)k;
+  }
+}
+
+// Thread per (line g = blockIdx.y, window start s): the cumulative trajectory
+// sum along line g from dump s, P_r = sum_{r' <= r} sum_j w Y[s + r'][bin];
+// the line's trials, sorted by length n_t, read E[t][s + n_t - 1] = |P_{n_t - 1}|^2.
+__global__ void __launch_bounds__(256) k_chimg_lines(const float2* __restrict__ Y, int Ns,
+                                                     long long n_dump,
+                                                     const long long* __restrict__ row_off,
+                                                     const int* __restrict__ n_max, int nj,
+                                                     const float2* __restrict__ w,
+                                                     const short* __restrict__ bin,
+                                                     const int* __restrict__ trial_off,
+                                                     const int* __restrict__ trial_len,
+                                                     float* __restrict__ E) {
+  const int g = blockIdx.y;
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_dump) return;
+  const long long n = min((long long)n_max[g], n_dump - s);
+  int t = trial_off[g];
+  const int t_end = trial_off[g + 1];
+  const long long base = row_off[g] * nj;
+  float2 P = make_float2(0.f, 0.f);
+  for (long long r = 0; r < n && t < t_end; r++) {
+    const float2* yr = Y + (s + r) * Ns;
+    for (int j = 0; j < nj; j++) {
+      const long long q = base + r * nj + j;
+      P = cfma(w[q], yr[bin[q]], P);
+    }
+    for (; t < t_end && trial_len[t] == r + 1; t++)
+      E[(long long)t * n_dump + s + r] = P.x * P.x + P.y * P.y;
   }
 }
 
@@ -790,6 +869,97 @@ void chirp_chimg2d_destroy(chirp_chimg2d_plan* p) {
   if (!p) return;
   cudaStreamSynchronize(p->st);
   free_chimg2d(p);
+}
+
+// ---- App. B.2.1: trials of one trajectory line from one cumulative sum
+namespace {
+struct DevBufs {  // device scratch of one call, freed on every exit path
+  std::vector<void*> p;
+  ~DevBufs() {
+    for (void* q : p) cudaFree(q);
+  }
+  int get(void** out, long long bytes, const char* what) {
+    int rc = galloc(out, bytes, what);
+    if (!rc) p.push_back(*out);
+    return rc;
+  }
+};
+}  // namespace
+
+int chirp_chimg_lines_run(const void* Y, long long n_dump, int n_ant, int n_spatial, int dump_len,
+                          double bw_hz, int half_width, const double* rate, int n_line,
+                          const int* trial_off, const int* trial_len, float* energy,
+                          void* stream) {
+  chirp_clear_error();
+  if (!Y || !rate || !trial_off || !trial_len || !energy) return gfail(CHIRP_EINVAL, "NULL argument");
+  if (n_ant < 2 || n_ant > kMaxAntUla || n_spatial < n_ant || n_spatial > kMaxNs ||
+      half_width < 0 || 2 * half_width + 1 > n_spatial || dump_len < 1 || !(bw_hz > 0.0) ||
+      n_dump < 1 || n_line < 1 || n_line > 65535)
+    return gfail(CHIRP_EINVAL, "chirp_chimg_lines_run: bad shape");
+  for (const void* ptr : {Y, (const void*)energy}) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess ||
+        (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+      cudaGetLastError();
+      return gfail(CHIRP_EINVAL, "chirp_chimg_lines_run: Y and energy must be device memory");
+    }
+  }
+  if (trial_off[0] != 0) return gfail(CHIRP_EINVAL, "chirp_chimg_lines_run: trial_off[0] != 0");
+  std::vector<int> n_max(n_line);
+  std::vector<long long> row_off(n_line + 1, 0);
+  for (int g = 0; g < n_line; g++) {
+    if (trial_off[g + 1] <= trial_off[g])
+      return gfail(CHIRP_EINVAL, "chirp_chimg_lines_run: line %d has no trial", g);
+    for (int t = trial_off[g]; t < trial_off[g + 1]; t++)
+      if (trial_len[t] < 1 || (t > trial_off[g] && trial_len[t] < trial_len[t - 1]))
+        return gfail(CHIRP_EINVAL, "chirp_chimg_lines_run: trial lengths must be >= 1 and "
+                                   "ascending within a line");
+    n_max[g] = trial_len[trial_off[g + 1] - 1];
+    row_off[g + 1] = row_off[g] + n_max[g];
+  }
+  const long long n_rows = row_off[n_line];
+  const int n_trial = trial_off[n_line];
+  const int nj = 2 * half_width + 1;
+  if (n_rows > (1LL << 26)) return gfail(CHIRP_EUNSUPPORTED, "chirp_chimg_lines_run: too many taps");
+  std::vector<double> row_rate((size_t)n_rows);
+  std::vector<int> row_r((size_t)n_rows);
+  for (int g = 0; g < n_line; g++)
+    for (int r = 0; r < n_max[g]; r++) {
+      row_rate[(size_t)(row_off[g] + r)] = rate[g];
+      row_r[(size_t)(row_off[g] + r)] = r;
+    }
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBufs b;
+  double* d_rate;
+  int *d_r, *d_nmax, *d_toff, *d_tlen;
+  long long* d_roff;
+  float2* d_w;
+  short* d_bin;
+  int rc = b.get((void**)&d_rate, n_rows * 8, "line rates");
+  if (!rc) rc = b.get((void**)&d_r, n_rows * 4, "line rows");
+  if (!rc) rc = b.get((void**)&d_nmax, n_line * 4LL, "line lengths");
+  if (!rc) rc = b.get((void**)&d_roff, (n_line + 1) * 8LL, "line offsets");
+  if (!rc) rc = b.get((void**)&d_toff, (n_line + 1) * 4LL, "trial offsets");
+  if (!rc) rc = b.get((void**)&d_tlen, n_trial * 4LL, "trial lengths");
+  if (!rc) rc = b.get((void**)&d_w, n_rows * nj * 8, "line taps");
+  if (!rc) rc = b.get((void**)&d_bin, n_rows * nj * 2, "line bins");
+  if (rc) return rc;
+  CKG(cudaMemcpyAsync(d_rate, row_rate.data(), n_rows * 8, cudaMemcpyHostToDevice, st));
+  CKG(cudaMemcpyAsync(d_r, row_r.data(), n_rows * 4, cudaMemcpyHostToDevice, st));
+  CKG(cudaMemcpyAsync(d_nmax, n_max.data(), n_line * 4LL, cudaMemcpyHostToDevice, st));
+  CKG(cudaMemcpyAsync(d_roff, row_off.data(), (n_line + 1) * 8LL, cudaMemcpyHostToDevice, st));
+  CKG(cudaMemcpyAsync(d_toff, trial_off, (n_line + 1) * 4LL, cudaMemcpyHostToDevice, st));
+  CKG(cudaMemcpyAsync(d_tlen, trial_len, n_trial * 4LL, cudaMemcpyHostToDevice, st));
+  k_chimg_line_taps<<<(unsigned)((n_rows + 127) / 128), 128, 0, st>>>(
+      d_rate, d_r, n_rows, n_ant, dump_len, n_spatial, half_width, bw_hz, d_w, d_bin);
+  CKG(cudaGetLastError());
+  CKG(cudaMemsetAsync(energy, 0, (size_t)n_trial * n_dump * 4, st));
+  const dim3 grid((unsigned)((n_dump + 255) / 256), (unsigned)n_line);
+  k_chimg_lines<<<grid, 256, 0, st>>>((const float2*)Y, n_spatial, n_dump, d_roff, d_nmax, nj, d_w,
+                                      d_bin, d_toff, d_tlen, energy);
+  CKG(cudaGetLastError());
+  CKG(cudaStreamSynchronize(st));  // the scratch is freed on return
+  return CHIRP_OK;
 }
 
 }  // extern "C"
