@@ -304,7 +304,8 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ 
   constexpr int T = L / 16;
   __shared__ __align__(16) float2 sm[FftTile<L, C>::SLOTS];
   const Twiddles tw = mk_tw(twp);
-  const int s = threadIdx.x % C, jt = threadIdx.x / C;
+  int s, jt;
+  col_thread<L, C>(threadIdx.x, s, jt);
   const int c = blockIdx.x * C + s;
   const bool act = c < n2;
   const long long q = blk_list ? (long long)blk_list[blockIdx.y / n_ant] * n_ant + blockIdx.y % n_ant
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(256, 4) k_inv_cols(const float2* __restrict__ 
   float2 v[16];
 #pragma unroll
   for (int k = 0; k < 16; k++) v[k] = act ? src[(jt + k * T) * n2] : make_float2(0.f, 0.f);
-  fft_core<L, C, false, true>(v, sm, s, jt, tw);
+  fft_core<L, C, false, true, kColShfl<L, C>>(v, sm, s, jt, tw);
   const long long base = b * step;
   const long long lo_b = (b == 0) ? n_hi : n_hi_max;
   const long long hi_b = (b == n_blk - 1) ? (n_samp - n_lo - base) : (n_hi_max + step);

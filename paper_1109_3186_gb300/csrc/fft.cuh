@@ -298,11 +298,34 @@ __device__ __forceinline__ void twiddle_run_base(float2 (&v)[16], float2 base, u
               tw_big<INV>(tw, (4u * m * T) & mask, log2n));
 }
 
+// Thread -> (column s, butterfly jt) of a column pass (ROWMAJOR = false).
+// For the 512-point transform (C = 8 columns of T = 32 threads) lane bit 4
+// carries bit 4 of jt, so that threads jt and jt ^ 16 share a warp: between
+// the last radix-16 stage and the radix-2 stage they are the only threads
+// that trade values, which fft_core<..., XSHFL = true> then does by warp
+// shuffles instead of a shared-memory round trip.  A warp still covers 8
+// consecutive columns of 4 rows, as in the plain order s = tid % C.
+template <int L, int C>
+constexpr bool kColShfl = (L == 512 && C == 8);
+
+template <int L, int C>
+__device__ __forceinline__ void col_thread(int tid, int& s, int& jt) {
+  if constexpr (kColShfl<L, C>) {
+    s = tid & 7;
+    jt = ((tid >> 3) & 1) | (((tid >> 5) & 7) << 1) | (((tid >> 4) & 1) << 4);
+  } else {
+    s = tid % C;
+    jt = tid / C;
+  }
+}
+
 // Forward (INV=false) or inverse (INV=true, unnormalised) FFT of length L.
 // On entry v[k] = element jt + k L/16 of sequence s; on exit the same
 // positions hold the transform.  sm: at least FftTile<L,C>::SLOTS float2.
 // All threads of the block that own (s, jt) pairs must call it together.
-template <int L, int C, bool ROWMAJOR, bool INV>
+// XSHFL (512 points, threads placed by col_thread): the exchange before the
+// radix-2 stage by warp shuffles; every lane of each warp must take part.
+template <int L, int C, bool ROWMAJOR, bool INV, bool XSHFL = false>
 __device__ __forceinline__ void fft_core(float2 (&v)[16], float2* sm, int s, int jt,
                                          const Twiddles& tw) {
   static_assert(L >= 16 && L <= 4096 && (L & (L - 1)) == 0, "L");
@@ -310,6 +333,7 @@ __device__ __forceinline__ void fft_core(float2 (&v)[16], float2* sm, int s, int
   constexpr int N16 = LOG / 4;           // radix-16 stages
   constexpr int RLAST = 1 << (LOG % 4);  // trailing radix (1 = none)
   constexpr int T = L / 16;
+  static_assert(!XSHFL || (L == 512 && C == 8 && !ROWMAJOR), "XSHFL: 512-point column pass");
 
   int Ns = 1;
 #pragma unroll
@@ -317,6 +341,32 @@ __device__ __forceinline__ void fft_core(float2 (&v)[16], float2* sm, int s, int
     // radix-16 stage: butterfly j = jt reads a[jt + q T] (already in v)
     stage_twiddle<L, 16, INV>(v, jt, Ns, tw);
     dft_r<16, INV>(v);
+    if constexpr (XSHFL) {
+      if (st == N16 - 1) {
+        // v[q] is element 256 h + (jt & 15) + 16 q (h = bit 4 of jt); the
+        // radix-2 stage wants elements jt + 32 k, k < 16: the even q of
+        // thread (jt & 15) and then of thread (jt & 15) + 16 for h = 0, their
+        // odd q for h = 1.  Each thread keeps its own half and trades the
+        // other half with its partner jt ^ 16 (lane ^ 16).
+        const bool h = (jt >> 4) & 1;
+        float2 got[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const float2 val = h ? v[2 * i] : v[2 * i + 1];
+          got[i].x = __shfl_xor_sync(0xffffffffu, val.x, 16);
+          got[i].y = __shfl_xor_sync(0xffffffffu, val.y, 16);
+        }
+        float2 nv[16];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          nv[k] = h ? got[k] : v[2 * k];
+          nv[8 + k] = h ? v[2 * k + 1] : got[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 16; k++) v[k] = nv[k];
+        break;  // on to the radix-2 stage
+      }
+    }
     const bool last = (st == N16 - 1) && (RLAST == 1);
     if (last) return;  // outputs b[jt + q T] == positions already held
     // write b[(j/Ns) Ns 16 + j%Ns + q Ns], then read the next stage inputs
