@@ -179,6 +179,12 @@ struct chirp_plan {
   // copy_stream and the forward transforms follow chunk by chunk; outputs go
   // back one DM slab at a time while later DMs are searched.
   cudaStream_t copy_stream = nullptr;
+  // Full searches form the next chunk's chirp tables on side_stream while the
+  // current chunk's column passes and back-ends run (d_H holds two sets of
+  // dm_chunk tables): side_ev[0] orders side after main, side_ev[1 + set]
+  // marks a table set complete.
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t side_ev[3] = {nullptr, nullptr, nullptr};
   cudaEvent_t io_ev = nullptr;         // search stream -> copy stream ordering
   std::vector<cudaEvent_t> in_ev;      // chunk k of the input has landed
   std::vector<long long> in_t1;        // samples [0, in_t1[k]) of every antenna
@@ -281,6 +287,12 @@ void release(chirp_plan* p) {
   }
   if (p->io_ev) cudaEventDestroy(p->io_ev);
   for (cudaEvent_t e : p->in_ev) cudaEventDestroy(e);
+  if (p->side_stream) {
+    cudaStreamSynchronize(p->side_stream);
+    cudaStreamDestroy(p->side_stream);
+  }
+  for (cudaEvent_t e : p->side_ev)
+    if (e) cudaEventDestroy(e);
 }
 
 // Two-pass FFT split autotuner.  Every split Nfft = n1 * n2 with the row
@@ -658,8 +670,8 @@ int chirp_plan_create(chirp_plan** out, const chirp_config* cfg, void* stream) {
   for (auto& g : p->groups) max_nfft = std::max(max_nfft, g.geom.nfft);
   p->h_stride = max_nfft;
   if (!rc)
-    rc = dev_alloc(p, (void**)&p->d_H, (size_t)p->dm_chunk * max_nfft * sizeof(float2),
-                   "chirp tables");
+    rc = dev_alloc(p, (void**)&p->d_H, (size_t)2 * p->dm_chunk * max_nfft * sizeof(float2),
+                   "chirp tables (two sets)");
   // (the dedispersed-voltage buffer d_y is allocated on first use: ensure_y)
   if (!rc && p->n_pix > 0)
     rc = dev_alloc(p, (void**)&p->d_W, (size_t)p->n_pix * p->M * sizeof(float2), "weights");
@@ -1294,47 +1306,85 @@ int batched_backends(chirp_plan* p, Backend be, void* dout, const int* ds, int n
 // batched back-end.  With a selection: only the groups it marks dense, only
 // their DMs with a selected dump, and the back-end over the selected dumps.
 int full_search_chunked(chirp_plan* p, Backend be, void* dout, const Selection* sel = nullptr) {
+  struct Chunk {
+    int group;
+    std::vector<int> dms;
+  };
+  std::vector<Chunk> chunks;
   for (size_t gi = 0; gi < p->groups.size(); gi++) {
-    Group& grp = p->groups[gi];
     if (sel && !sel->dense_group[gi]) continue;
     std::vector<int> dms;
-    for (int d : grp.dms)
+    for (int d : p->groups[gi].dms)
       if (p->dmi[d].last >= p->dmi[d].first && (!sel || sel->n[d] > 0)) dms.push_back(d);
-    if (dms.empty()) continue;
-    int rc0 = ensure_spec(p, (int)gi);
+    for (size_t c0 = 0; c0 < dms.size(); c0 += (size_t)p->dm_chunk)
+      chunks.push_back({(int)gi, std::vector<int>(dms.begin() + c0,
+                                                   dms.begin() + std::min(dms.size(),
+                                                                          c0 + (size_t)p->dm_chunk))});
+  }
+  // The chirp tables of chunk c + 1 are formed on the side stream while
+  // chunk c's column passes and back-ends run (FP64 pipe beside FP32 and
+  // load/store work), into the table set chunk c - 1 used; in stream order
+  // instead while stage timing records the chirp stage (its events are on
+  // the plan's stream).
+  const bool overlap = chunks.size() > 1 &&
+                       !(p->timing && ((p->timing_mask >> CHIRP_STAGE_CHIRP) & 1u));
+  if (overlap && !p->side_stream) {
+    CK(cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : p->side_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  auto tables = [&](size_t c, cudaStream_t st) -> cudaError_t {
+    const Chunk& k = chunks[c];
+    double dmv[kMaxChirps];
+    for (size_t j = 0; j < k.dms.size(); j++) dmv[j] = p->dm[k.dms[j]];
+    Group& grp = p->groups[(size_t)k.group];
+    return launch_chirp_tables(grp.d_G, p->d_H + (c & 1) * (size_t)p->dm_chunk * p->h_stride,
+                               p->h_stride, dmv, (int)k.dms.size(), grp.geom, st);
+  };
+  for (size_t c = 0; c < chunks.size(); c++) {
+    const Chunk& k = chunks[c];
+    Group& grp = p->groups[(size_t)k.group];
+    int rc0 = ensure_spec(p, k.group);
     if (rc0) return rc0;
     const GroupGeom& G = grp.geom;
     const long long nq = (long long)p->M * G.n_blk;
-    for (size_t c0 = 0; c0 < dms.size(); c0 += (size_t)p->dm_chunk) {
-      const int n = (int)std::min((size_t)p->dm_chunk, dms.size() - c0);
-      double dmv[kMaxChirps];
-      for (int j = 0; j < n; j++) dmv[j] = p->dm[dms[c0 + j]];
-      int mk = mark_begin(p, CHIRP_STAGE_CHIRP);
-      CK(launch_chirp_tables(grp.d_G, p->d_H, p->h_stride, dmv, n, G, p->stream));
+    const int n = (int)k.dms.size();
+    int mk;
+    if (!overlap || c == 0) {
+      mk = mark_begin(p, CHIRP_STAGE_CHIRP);
+      CK(tables(c, p->stream));
       mark_end(p, CHIRP_STAGE_CHIRP, mk);
-      mk = mark_begin(p, CHIRP_STAGE_INV_ROWS);
-      CK(launch_inverse_rows_multi(grp.d_spec, p->d_Z, (long long)p->z_stride, p->d_H,
-                                   p->h_stride, n, nq, G, p->tw(), grp.d_rtw, p->stream));
-      mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
-      const bool batch = n > 1 && batched_backend(p, be);
-      for (int j = 0; j < n; j++) {
-        const int d = dms[c0 + j];
-        const DmInfo& I = p->dmi[d];
-        mk = mark_begin(p, CHIRP_STAGE_INV_COLS);
-        CK(column_pass(p, d, be, p->d_Z + (size_t)j * p->z_stride, 0, nq, nullptr,
-                       batch ? p->d_y + (size_t)j * p->M * p->N : nullptr));
-        mark_end(p, CHIRP_STAGE_INV_COLS, mk);
-        if (batch) continue;
-        int rc = sel ? selected_backend(p, d, be, dout, *sel)
-                     : backend_dumps(p, d, be, I.first, I.last + 1, dout);
-        if (!rc) rc = drain_dm(p, d);
-        if (rc) return rc;
-      }
-      if (batch) {
-        int rc = batched_backends(p, be, dout, dms.data() + c0, n, sel);
-        for (int j = 0; j < n && !rc; j++) rc = drain_dm(p, dms[c0 + j]);
-        if (rc) return rc;
-      }
+    } else {
+      CK(cudaStreamWaitEvent(p->stream, p->side_ev[1 + (c & 1)], 0));
+    }
+    mk = mark_begin(p, CHIRP_STAGE_INV_ROWS);
+    CK(launch_inverse_rows_multi(grp.d_spec, p->d_Z, (long long)p->z_stride,
+                                 p->d_H + (c & 1) * (size_t)p->dm_chunk * p->h_stride,
+                                 p->h_stride, n, nq, G, p->tw(), grp.d_rtw, p->stream));
+    mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
+    if (overlap && c + 1 < chunks.size()) {
+      CK(cudaEventRecord(p->side_ev[0], p->stream));
+      CK(cudaStreamWaitEvent(p->side_stream, p->side_ev[0], 0));
+      CK(tables(c + 1, p->side_stream));
+      CK(cudaEventRecord(p->side_ev[1 + ((c + 1) & 1)], p->side_stream));
+    }
+    const bool batch = n > 1 && batched_backend(p, be);
+    for (int j = 0; j < n; j++) {
+      const int d = k.dms[(size_t)j];
+      const DmInfo& I = p->dmi[d];
+      mk = mark_begin(p, CHIRP_STAGE_INV_COLS);
+      CK(column_pass(p, d, be, p->d_Z + (size_t)j * p->z_stride, 0, nq, nullptr,
+                     batch ? p->d_y + (size_t)j * p->M * p->N : nullptr));
+      mark_end(p, CHIRP_STAGE_INV_COLS, mk);
+      if (batch) continue;
+      int rc = sel ? selected_backend(p, d, be, dout, *sel)
+                   : backend_dumps(p, d, be, I.first, I.last + 1, dout);
+      if (!rc) rc = drain_dm(p, d);
+      if (rc) return rc;
+    }
+    if (batch) {
+      int rc = batched_backends(p, be, dout, k.dms.data(), n, sel);
+      for (int j = 0; j < n && !rc; j++) rc = drain_dm(p, k.dms[(size_t)j]);
+      if (rc) return rc;
     }
   }
   return CHIRP_OK;
