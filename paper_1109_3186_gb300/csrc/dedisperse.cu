@@ -143,18 +143,20 @@ __global__ void k_chirp_table(const double* __restrict__ G, float2* __restrict__
 struct ChirpDms {
   double dm[kMaxChirps];
 };
+// Grid-stride over the bins, so that a small grid can run beside other work.
 __global__ void k_chirp_tables(const double* __restrict__ G, float2* __restrict__ H,
                                long long h_stride, ChirpDms dms, int n_dm, long long nfft,
                                float inv_nfft) {
-  long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (pos >= nfft) return;
-  const double gv = G[pos];
-  for (int i = 0; i < n_dm; i++) {
-    double c = __dmul_rn(dms.dm[i], gv);
-    double r = __dsub_rn(c, rint(c));  // exact
-    float sn, cs;
-    sincospif(-2.0f * (float)r, &sn, &cs);
-    H[i * h_stride + pos] = make_float2(cs * inv_nfft, sn * inv_nfft);
+  for (long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x; pos < nfft;
+       pos += (long long)gridDim.x * blockDim.x) {
+    const double gv = G[pos];
+    for (int i = 0; i < n_dm; i++) {
+      double c = __dmul_rn(dms.dm[i], gv);
+      double r = __dsub_rn(c, rint(c));  // exact
+      float sn, cs;
+      sincospif(-2.0f * (float)r, &sn, &cs);
+      H[i * h_stride + pos] = make_float2(cs * inv_nfft, sn * inv_nfft);
+    }
   }
 }
 
@@ -478,11 +480,12 @@ cudaError_t launch_build_phase_table(double* G, const GroupGeom& g, double f0, d
 }
 
 cudaError_t launch_chirp_tables(const double* G, float2* H, long long h_stride, const double* dms,
-                                int n_dm, const GroupGeom& g, cudaStream_t st) {
+                                int n_dm, const GroupGeom& g, cudaStream_t st, int max_ctas) {
   if (n_dm < 1 || n_dm > kMaxChirps) return cudaErrorInvalidValue;
   ChirpDms d{};
   for (int i = 0; i < n_dm; i++) d.dm[i] = dms[i];
   long long blocks = (g.nfft + 255) / 256;
+  if (max_ctas > 0 && blocks > max_ctas) blocks = max_ctas;
   k_chirp_tables<<<(unsigned)blocks, 256, 0, st>>>(G, H, h_stride, d, n_dm, g.nfft,
                                                    ldexpf(1.0f, -g.log2n));
   return cudaGetLastError();

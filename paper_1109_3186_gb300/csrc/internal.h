@@ -64,8 +64,10 @@ cudaError_t launch_build_phase_table(double* G, const GroupGeom& g, double f0, d
 // (the inverse FFT's normalisation, exact: nfft is a power of two)
 // The same for n_dm <= kMaxChirps DMs at once: DM i's table at H + i h_stride.
 constexpr int kMaxChirps = 4;
+// max_ctas > 0 caps the grid (the kernel strides over the bins), e.g. to run
+// it beside other kernels without taking their CTA slots.
 cudaError_t launch_chirp_tables(const double* G, float2* H, long long h_stride, const double* dms,
-                                int n_dm, const GroupGeom& g, cudaStream_t st);
+                                int n_dm, const GroupGeom& g, cudaStream_t st, int max_ctas = 0);
 cudaError_t launch_chirp_table(const double* G, float2* H, double dm, const GroupGeom& g,
                                cudaStream_t st);
 // The inverse can run over chunks of (antenna, block) sequences [q0, q0 + nq)

@@ -185,6 +185,7 @@ struct chirp_plan {
   // marks a table set complete.
   cudaStream_t side_stream = nullptr;
   cudaEvent_t side_ev[3] = {nullptr, nullptr, nullptr};
+  int n_sm = 0;                        // SMs of the plan's device
   cudaEvent_t io_ev = nullptr;         // search stream -> copy stream ordering
   std::vector<cudaEvent_t> in_ev;      // chunk k of the input has landed
   std::vector<long long> in_t1;        // samples [0, in_t1[k]) of every antenna
@@ -1329,16 +1330,22 @@ int full_search_chunked(chirp_plan* p, Backend be, void* dout, const Selection* 
   const bool overlap = chunks.size() > 1 &&
                        !(p->timing && ((p->timing_mask >> CHIRP_STAGE_CHIRP) & 1u));
   if (overlap && !p->side_stream) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev));
     CK(cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking));
     for (cudaEvent_t& e : p->side_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
+  // (on the side stream one CTA per SM, striding over the bins, so that the
+  // column passes beside it keep their CTA slots)
   auto tables = [&](size_t c, cudaStream_t st) -> cudaError_t {
     const Chunk& k = chunks[c];
     double dmv[kMaxChirps];
     for (size_t j = 0; j < k.dms.size(); j++) dmv[j] = p->dm[k.dms[j]];
     Group& grp = p->groups[(size_t)k.group];
     return launch_chirp_tables(grp.d_G, p->d_H + (c & 1) * (size_t)p->dm_chunk * p->h_stride,
-                               p->h_stride, dmv, (int)k.dms.size(), grp.geom, st);
+                               p->h_stride, dmv, (int)k.dms.size(), grp.geom, st,
+                               st == p->side_stream ? p->n_sm : 0);
   };
   for (size_t c = 0; c < chunks.size(); c++) {
     const Chunk& k = chunks[c];
