@@ -53,7 +53,7 @@ extern "C" {
 #define CHIRP_ENOMEM (-2)      /* device or host allocation failed          */
 #define CHIRP_ECUDA (-3)       /* a CUDA runtime call or launch failed      */
 #define CHIRP_ETIMEOUT (-4)    /* a bounded device wait gave up              */
-#define CHIRP_EUNSUPPORTED (-5)/* valid request this build does not handle  */
+#define CHIRP_EUNSUPPORTED (-5)/* valid request the library does not handle */
 
 /* where a caller buffer lives */
 #define CHIRP_HOST 0
