@@ -384,22 +384,21 @@ struct VisBatch {
   VisJob job[kCorrBatchMax];
 };
 
-__global__ void __launch_bounds__(256) k_beam_from_vis(const __grid_constant__ VisBatch batch,
-                                                       int K, const float* __restrict__ B,
-                                                       int ldb, int n_pix) {
-  // this CTA's DM (grid dimension z)
-  const VisJob& job = batch.job[blockIdx.z];
-  const long long row0 = (long long)blockIdx.x * kVisBM;
+// One 64-dump x 128-pixel tile: row tile bx of DM job bz, pixel tile by.
+__device__ __forceinline__ void vis_tile(const VisBatch& batch, int K, const float* __restrict__ B,
+                                         int ldb, int n_pix, long long bx, int by, int bz,
+                                         float (&As)[2][kVisBK][kVisBM],
+                                         float (&Bs)[2][kVisBK][kVisBN]) {
+  const VisJob& job = batch.job[bz];
+  const long long row0 = bx * kVisBM;
   if (row0 >= job.n_rows) return;
   const float* __restrict__ V = reinterpret_cast<const float*>(job.V);
   float* __restrict__ pow = job.pow;
   const int* __restrict__ dump_list = job.dump_list;
   const long long first = job.first, n_rows = job.n_rows;
-  __shared__ __align__(16) float As[2][kVisBK][kVisBM];
-  __shared__ __align__(16) float Bs[2][kVisBK][kVisBN];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
-  const int p0 = blockIdx.y * kVisBN;
+  const int p0 = by * kVisBN;
   // loader coordinates: A 64 rows x 16 k (4 k per thread), B 16 k x 128 (8 per thread)
   const int a_row = tid / 4, a_k = (tid % 4) * 4;
   const long long ar = row0 + a_row;
@@ -472,11 +471,28 @@ __global__ void __launch_bounds__(256) k_beam_from_vis(const __grid_constant__ V
   }
 }
 
+// The tiles of a virtual grid of vx row tiles x vy pixel tiles x vz DMs, row
+// tile fastest; a CTA takes tiles vb = blockIdx.x, + gridDim.x, ... (one each
+// when the grid covers them all, fewer CTAs when it runs beside other work).
+__global__ void __launch_bounds__(256) k_beam_from_vis(const __grid_constant__ VisBatch batch,
+                                                       int K, const float* __restrict__ B,
+                                                       int ldb, int n_pix, long long vx, int vy,
+                                                       int vz) {
+  __shared__ __align__(16) float As[2][kVisBK][kVisBM];
+  __shared__ __align__(16) float Bs[2][kVisBK][kVisBN];
+  const long long n_tiles = vx * vy * vz;
+  for (long long vb = blockIdx.x; vb < n_tiles; vb += gridDim.x) {
+    if (vb != blockIdx.x) __syncthreads();  // the previous tile's reads of As / Bs are done
+    vis_tile(batch, K, B, ldb, n_pix, vb % vx, (int)((vb / vx) % vy), (int)(vb / (vx * vy)), As,
+             Bs);
+  }
+}
+
 int beam_vis_rows(int n_ant) { return ((n_ant * (n_ant + 1) + kVisBK - 1) / kVisBK) * kVisBK; }
 int beam_vis_ld(int n_pix) { return ((n_pix + kVisBN - 1) / kVisBN) * kVisBN; }
 
 cudaError_t launch_beam_from_vis_batch(const VisJob* jobs, int n_jobs, const float* wvis,
-                                       int n_ant, int n_pix, cudaStream_t st) {
+                                       int n_ant, int n_pix, cudaStream_t st, int max_ctas) {
   if (n_jobs < 1 || n_jobs > kCorrBatchMax) return cudaErrorInvalidValue;
   if (n_pix <= 0) return cudaSuccess;
   VisBatch b{};
@@ -487,10 +503,13 @@ cudaError_t launch_beam_from_vis_batch(const VisJob* jobs, int n_jobs, const flo
   }
   if (max_rows <= 0) return cudaSuccess;
   const long long n_x = (max_rows + kVisBM - 1) / kVisBM;
-  if (n_x >= (1LL << 31)) return cudaErrorInvalidConfiguration;
+  const int n_y = (n_pix + kVisBN - 1) / kVisBN;
+  const long long n_tiles = n_x * n_y * n_jobs;
+  if (n_tiles >= (1LL << 31)) return cudaErrorInvalidConfiguration;
   const int K = n_ant * (n_ant + 1);  // 2 n_pair real columns
-  dim3 grid((unsigned)n_x, (n_pix + kVisBN - 1) / kVisBN, (unsigned)n_jobs);
-  k_beam_from_vis<<<grid, 256, 0, st>>>(b, K, wvis, beam_vis_ld(n_pix), n_pix);
+  const long long grid = max_ctas > 0 && n_tiles > max_ctas ? max_ctas : n_tiles;
+  k_beam_from_vis<<<(unsigned)grid, 256, 0, st>>>(b, K, wvis, beam_vis_ld(n_pix), n_pix, n_x, n_y,
+                                                  n_jobs);
   return cudaGetLastError();
 }
 

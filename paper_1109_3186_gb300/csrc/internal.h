@@ -175,8 +175,9 @@ struct VisJob {
 };
 cudaError_t launch_correlate_batch(const CorrJob* jobs, int n_jobs, bool bf16, long long n_samp,
                                    int n_ant, int dump_len, cudaStream_t st);
+// max_ctas > 0: at most that many CTAs, striding over the tiles.
 cudaError_t launch_beam_from_vis_batch(const VisJob* jobs, int n_jobs, const float* wvis,
-                                       int n_ant, int n_pix, cudaStream_t st);
+                                       int n_ant, int n_pix, cudaStream_t st, int max_ctas = 0);
 // dumps m_base .. m_base + n_m - 1, or dump_list[0 .. n_m) when dump_list is a
 // device array (zeros for dumps outside [first, last])
 cudaError_t launch_correlate(const float2* y, long long n_samp, int n_ant, int dump_len,

@@ -186,6 +186,11 @@ struct chirp_plan {
   cudaStream_t side_stream = nullptr;
   cudaEvent_t side_ev[3] = {nullptr, nullptr, nullptr};
   int n_sm = 0;                        // SMs of the plan's device
+  // and (device outputs) the chunk's beams from visibilities beside the next
+  // chunk's passes: beam_ev[0] orders side after the correlator, beam_ev[1]
+  // marks the beams done (the next correlator overwrites d_V after it)
+  bool beam_side = false, beam_pending = false;
+  cudaEvent_t beam_ev[2] = {nullptr, nullptr};
   cudaEvent_t io_ev = nullptr;         // search stream -> copy stream ordering
   std::vector<cudaEvent_t> in_ev;      // chunk k of the input has landed
   std::vector<long long> in_t1;        // samples [0, in_t1[k]) of every antenna
@@ -293,6 +298,8 @@ void release(chirp_plan* p) {
     cudaStreamDestroy(p->side_stream);
   }
   for (cudaEvent_t e : p->side_ev)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->beam_ev)
     if (e) cudaEventDestroy(e);
 }
 
@@ -1289,10 +1296,20 @@ int batched_backends(chirp_plan* p, Backend be, void* dout, const int* ds, int n
     cj[j] = CorrJob{p->d_y + (size_t)j * slot, vis, I.first, n_m, I.first, I.last, dl};
     vj[j] = VisJob{vis, (float*)dout + (size_t)d * p->n_dump * p->n_pix, I.first, n_m, dl};
   }
+  if (p->beam_pending) {  // the previous chunk's beams still read d_V
+    CK(cudaStreamWaitEvent(p->stream, p->beam_ev[1], 0));
+    p->beam_pending = false;
+  }
   int mk = mark_begin(p, CHIRP_STAGE_CORRELATE);
   CK(launch_correlate_batch(cj, n, bf16_y(p, be), p->N, p->M, p->L, p->stream));
   mark_end(p, CHIRP_STAGE_CORRELATE, mk);
-  if (be == kBeams) {
+  if (be == kBeams && p->beam_side) {
+    CK(cudaEventRecord(p->beam_ev[0], p->stream));
+    CK(cudaStreamWaitEvent(p->side_stream, p->beam_ev[0], 0));
+    CK(launch_beam_from_vis_batch(vj, n, p->d_wpair, p->M, p->n_pix, p->side_stream, p->n_sm));
+    CK(cudaEventRecord(p->beam_ev[1], p->side_stream));
+    p->beam_pending = true;
+  } else if (be == kBeams) {
     mk = mark_begin(p, CHIRP_STAGE_BEAMFORM);
     CK(launch_beam_from_vis_batch(vj, n, p->d_wpair, p->M, p->n_pix, p->stream));
     mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
@@ -1335,7 +1352,12 @@ int full_search_chunked(chirp_plan* p, Backend be, void* dout, const Selection* 
     CK(cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev));
     CK(cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking));
     for (cudaEvent_t& e : p->side_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    for (cudaEvent_t& e : p->beam_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
+  // device outputs of visibility beams: each chunk's quadratic form on the
+  // side stream too, one CTA per SM, beside the next chunk's passes
+  p->beam_side = overlap && be == kBeams && vis_beams(p) && !sel && !p->drain_host &&
+                 !(p->timing && ((p->timing_mask >> CHIRP_STAGE_BEAMFORM) & 1u));
   // (on the side stream one CTA per SM, striding over the bins, so that the
   // column passes beside it keep their CTA slots)
   auto tables = [&](size_t c, cudaStream_t st) -> cudaError_t {
@@ -1393,6 +1415,11 @@ int full_search_chunked(chirp_plan* p, Backend be, void* dout, const Selection* 
       for (int j = 0; j < n && !rc; j++) rc = drain_dm(p, k.dms[(size_t)j]);
       if (rc) return rc;
     }
+  }
+  p->beam_side = false;
+  if (p->beam_pending) {  // join the last chunk's beams
+    CK(cudaStreamWaitEvent(p->stream, p->beam_ev[1], 0));
+    p->beam_pending = false;
   }
   return CHIRP_OK;
 }
@@ -1486,6 +1513,7 @@ constexpr double kDenseBlocks = 0.85;
 
 int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Backend be,
                    void* dout, size_t bytes) {
+  p->beam_side = false;
   int rc = forward_all(p, dx);
   if (rc) return rc;
   CK(cudaMemsetAsync(dout, 0, bytes, p->stream));  // invalid / unselected cells stay zero
