@@ -1405,6 +1405,10 @@ int full_search_chunked(chirp_plan* p, Backend be, void* dout, const Selection* 
                      batch ? p->d_y + (size_t)j * p->M * p->N : nullptr));
       mark_end(p, CHIRP_STAGE_INV_COLS, mk);
       if (batch) continue;
+      if (p->beam_pending) {  // the previous chunk's side-stream beams still read d_V
+        CK(cudaStreamWaitEvent(p->stream, p->beam_ev[1], 0));
+        p->beam_pending = false;
+      }
       int rc = sel ? selected_backend(p, d, be, dout, *sel)
                    : backend_dumps(p, d, be, I.first, I.last + 1, dout);
       if (!rc) rc = drain_dm(p, d);
