@@ -191,6 +191,9 @@ struct chirp_plan {
   // marks the beams done (the next correlator overwrites d_V after it)
   bool beam_side = false, beam_pending = false;
   cudaEvent_t beam_ev[2] = {nullptr, nullptr};
+  // the beams of the last batched chunk, launched on the side stream after
+  // the next chunk's row pass (so that they run beside its column passes)
+  std::vector<VisJob> beam_jobs;
   cudaEvent_t io_ev = nullptr;         // search stream -> copy stream ordering
   std::vector<cudaEvent_t> in_ev;      // chunk k of the input has landed
   std::vector<long long> in_t1;        // samples [0, in_t1[k]) of every antenna
@@ -1303,17 +1306,27 @@ int batched_backends(chirp_plan* p, Backend be, void* dout, const int* ds, int n
   int mk = mark_begin(p, CHIRP_STAGE_CORRELATE);
   CK(launch_correlate_batch(cj, n, bf16_y(p, be), p->N, p->M, p->L, p->stream));
   mark_end(p, CHIRP_STAGE_CORRELATE, mk);
-  if (be == kBeams && p->beam_side) {
-    CK(cudaEventRecord(p->beam_ev[0], p->stream));
-    CK(cudaStreamWaitEvent(p->side_stream, p->beam_ev[0], 0));
-    CK(launch_beam_from_vis_batch(vj, n, p->d_wpair, p->M, p->n_pix, p->side_stream, p->n_sm));
-    CK(cudaEventRecord(p->beam_ev[1], p->side_stream));
-    p->beam_pending = true;
+  if (be == kBeams && p->beam_side) {  // launched by side_beams after the next row pass
+    p->beam_jobs.assign(vj, vj + n);
   } else if (be == kBeams) {
     mk = mark_begin(p, CHIRP_STAGE_BEAMFORM);
     CK(launch_beam_from_vis_batch(vj, n, p->d_wpair, p->M, p->n_pix, p->stream));
     mark_end(p, CHIRP_STAGE_BEAMFORM, mk);
   }
+  return CHIRP_OK;
+}
+
+// The beams deferred by batched_backends: on the side stream, one CTA per
+// SM, ordered after everything the plan's stream has queued so far.
+int side_beams(chirp_plan* p) {
+  if (p->beam_jobs.empty()) return CHIRP_OK;
+  CK(cudaEventRecord(p->beam_ev[0], p->stream));
+  CK(cudaStreamWaitEvent(p->side_stream, p->beam_ev[0], 0));
+  CK(launch_beam_from_vis_batch(p->beam_jobs.data(), (int)p->beam_jobs.size(), p->d_wpair, p->M,
+                                p->n_pix, p->side_stream, p->n_sm));
+  CK(cudaEventRecord(p->beam_ev[1], p->side_stream));
+  p->beam_jobs.clear();
+  p->beam_pending = true;
   return CHIRP_OK;
 }
 
@@ -1390,6 +1403,10 @@ int full_search_chunked(chirp_plan* p, Backend be, void* dout, const Selection* 
                                  p->d_H + (c & 1) * (size_t)p->dm_chunk * p->h_stride,
                                  p->h_stride, n, nq, G, p->tw(), grp.d_rtw, p->stream));
     mark_end(p, CHIRP_STAGE_INV_ROWS, mk);
+    {  // the previous chunk's beams, beside this chunk's column passes
+      int rc = side_beams(p);
+      if (rc) return rc;
+    }
     if (overlap && c + 1 < chunks.size()) {
       CK(cudaEventRecord(p->side_ev[0], p->stream));
       CK(cudaStreamWaitEvent(p->side_stream, p->side_ev[0], 0));
@@ -1419,6 +1436,10 @@ int full_search_chunked(chirp_plan* p, Backend be, void* dout, const Selection* 
       for (int j = 0; j < n && !rc; j++) rc = drain_dm(p, k.dms[(size_t)j]);
       if (rc) return rc;
     }
+  }
+  {  // the last batched chunk's beams
+    int rc = side_beams(p);
+    if (rc) return rc;
   }
   p->beam_side = false;
   if (p->beam_pending) {  // join the last chunk's beams
@@ -1518,6 +1539,7 @@ constexpr double kDenseBlocks = 0.85;
 int enqueue_search(chirp_plan* p, const void* dx, const unsigned char* mask, Backend be,
                    void* dout, size_t bytes) {
   p->beam_side = false;
+  p->beam_jobs.clear();
   int rc = forward_all(p, dx);
   if (rc) return rc;
   CK(cudaMemsetAsync(dout, 0, bytes, p->stream));  // invalid / unselected cells stay zero
