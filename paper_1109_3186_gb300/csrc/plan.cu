@@ -1368,7 +1368,8 @@ int full_search_chunked(chirp_plan* p, Backend be, void* dout, const Selection* 
     for (cudaEvent_t& e : p->beam_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
   // device outputs of visibility beams: each chunk's quadratic form on the
-  // side stream too, one CTA per SM, beside the next chunk's passes
+  // side stream too, one CTA per SM, launched after the next chunk's row pass
+  // so that it runs beside that chunk's column passes (side_beams)
   p->beam_side = overlap && be == kBeams && vis_beams(p) && !sel && !p->drain_host &&
                  !(p->timing && ((p->timing_mask >> CHIRP_STAGE_BEAMFORM) & 1u));
   // (on the side stream one CTA per SM, striding over the bins, so that the
